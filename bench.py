@@ -1,0 +1,457 @@
+#!/usr/bin/env python
+"""Benchmark of the MLP-Splatting render hot path on GB300.
+
+Workload (default): the 1920x1080 "Precision" configuration -- K = 256 primitives, per-primitive
+MLP 60 -> 64 x 3 -> 4 (xyz L = 6, dir L = 4), S = 32 samples per hit interval, a batch of 8
+views on the radius-3 sphere, seeded synthetic scene (seed 0). One step = one pass of the whole
+path over the batch: weight packing, binning, intersection + sort, gather, grouped MLP with
+interval compositing, per-ray compositing, and (fwd+bwd) the reverse composite, MLP backward
+with recompute and pose-gradient chain.
+
+Prints ONE JSON line (rank 0). value = whole-job rays/s (all pixels of all views of all ranks /
+max-over-ranks time). Under torchrun every rank renders its own 8 views (weak scaling; the
+views are independent, no collective on the data path).
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded pixel sample of
+the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rays/s fwd and fwd+bwd at 1080p, BF16 vs FP32 path, at PSNR≥45dB vs oracle"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="prec")
+    ap.add_argument("--precision", default="auto", help="bf16 | fp32 | fp8 | auto (best available)")
+    ap.add_argument("--pass", dest="pass_", default="fwdbwd", choices=["fwdbwd", "fwd"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare", action="store_true",
+                    help="also time the FP32 path and forward-only passes (extra lines in 'results')")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _flush_l2(buf):
+    buf.add_(1.0)  # writes 256 MiB (> 129 MB L2) between timed steps
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_03877_gb300 import _lib, synth
+    from paper_2606_03877_gb300.render import Renderer
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = synth.CONFIGS[a.workload]
+    scene = synth.make_scene(wl, 0)
+    cams = synth.make_cameras(wl, first_view_seed=rank * wl.n_views)
+    d = {k: torch.from_numpy(v).to(dev) for k, v in scene.items()}
+    g_rgb = torch.from_numpy(synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100 + rank,
+                                             scale=0.01)).to(dev)
+    n_rays = wl.n_rays
+    flush = torch.zeros(64 * 1024 * 1024, device=dev)
+
+    def make(precision):
+        r = Renderer(wl, precision=precision, device=str(dev))
+        return r
+
+    def try_pass(r, want_bwd):
+        packed = r.pack(d["weights"])
+        out = r.forward(d["centers"], d["scales"], d["quats"], packed, cams)
+        bwd_ok = False
+        if want_bwd:
+            try:
+                r.backward(g_rgb)
+                bwd_ok = True
+            except _lib.MlpsError as e:
+                if e.status != _lib.MLPS_ERR_UNSUPPORTED:
+                    raise
+        torch.cuda.synchronize()
+        st = r.status()
+        if st != 0:
+            raise RuntimeError(f"device status {_lib.mlps_status_string(st)}")
+        return out, bwd_ok
+
+    # precision selection (auto: BF16 tensor-core path when the library supports it)
+    order = ["bf16", "fp32"] if a.precision == "auto" else [a.precision]
+    r = None
+    precision = None
+    for p in order:
+        try:
+            r = make(p)
+            out, bwd_ok = try_pass(r, a.pass_ == "fwdbwd")
+            precision = p
+            break
+        except _lib.MlpsError as e:
+            if e.status != _lib.MLPS_ERR_UNSUPPORTED:
+                raise
+    if r is None or precision is None:
+        raise RuntimeError("no supported precision")
+    do_bwd = a.pass_ == "fwdbwd" and bwd_ok
+
+    def step(rr, bwd):
+        packed = rr.pack(d["weights"], out=rr._packed_buf)
+        rr.forward(d["centers"], d["scales"], d["quats"], packed, cams, out=rr._out_buf)
+        if bwd:
+            rr.backward(g_rgb, out=rr._grad_buf)
+
+    def bind_buffers(rr):
+        rr._packed_buf = torch.empty(max(wl.K, 1) * rr.stride, dtype=torch.uint8, device=dev)
+        rr._out_buf = {"rgb": torch.empty(wl.n_views, wl.height, wl.width, 3, device=dev),
+                       "trans": torch.empty(wl.n_views, wl.height, wl.width, device=dev),
+                       "feat": torch.empty(wl.n_views, wl.height, wl.width, wl.feat_dim, device=dev)
+                       if wl.feat_dim else None}
+        rr._grad_buf = {"d_weights": torch.empty(wl.K, rr.P, device=dev), "d_centers": torch.empty(wl.K, 3, device=dev),
+                        "d_scales": torch.empty(wl.K, 3, device=dev), "d_quats": torch.empty(wl.K, 4, device=dev)}
+
+    def timed(rr, bwd, steps, warmup, sample_clocks=False, profile=False):
+        bind_buffers(rr)
+        for _ in range(warmup):
+            step(rr, bwd)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        clk = ClockSampler(local) if sample_clocks else None
+        if clk:
+            clk.start()
+            time.sleep(0.3)
+        _lib.mlps_kernel_launches(reset=True)
+        if profile:
+            _lib.mlps_profiler_read(reset=True)
+            _lib.mlps_profiler_enable(True)
+        torch.cuda.synchronize()
+        for i in range(steps):
+            _flush_l2(flush)
+            evs[i][0].record()
+            step(rr, bwd)
+            evs[i][1].record()
+        torch.cuda.synchronize()
+        launches = _lib.mlps_kernel_launches()
+        prof = None
+        if profile:
+            _lib.mlps_profiler_enable(False)
+            prof = _lib.mlps_profiler_read(reset=True)
+        clocks = clk.stop() if clk else None
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        total = torch.tensor([sum(ms)], device=dev, dtype=torch.float64)
+        if ws > 1:
+            dist.barrier()
+            dist.all_reduce(total, op=dist.ReduceOp.MAX)
+        return float(total.item()), ms, launches, prof, clocks
+
+    total_ms, ms, launches, prof, clocks = timed(r, do_bwd, a.steps, a.warmup, sample_clocks=True, profile=True)
+    n_hits = r.hit_count()
+    value = n_rays * ws * a.steps / (total_ms / 1e3)
+    results = {f"{precision}_{'fwd_bwd' if do_bwd else 'fwd'}": value}
+
+    if a.compare:
+        for p2, b2 in [("fp32", True), ("fp32", False), (precision, False)]:
+            key = f"{p2}_{'fwd_bwd' if b2 else 'fwd'}"
+            if key in results:
+                continue
+            try:
+                r2 = make(p2)
+                _, ok2 = try_pass(r2, b2)
+                if b2 and not ok2:
+                    continue
+                t2, _, _, _, _ = timed(r2, b2, max(2, a.steps // 2), 2)
+                results[key] = n_rays * ws * max(2, a.steps // 2) / (t2 / 1e3)
+                del r2
+            except _lib.MlpsError:
+                pass
+
+    # ---- roofline of the dominant kernel stage (live CUDA events on the launching stream)
+    peaks, peak_src = _peaks()
+    S = wl.samples
+    flop_per_sample = 2 * sum(i * o for i, o in wl.layer_dims())
+    stage_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1] > 0}
+    dom = max(stage_ms, key=stage_ms.get)
+    samples = n_hits * S
+    if dom in ("mlp_fwd", "mlp_bwd"):
+        flops = samples * flop_per_sample * (1 if dom == "mlp_fwd" else 2)
+        ach = flops / (stage_ms[dom] / 1e3) / 1e12
+        if precision == "fp32":
+            clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": None, "kernel": dom,
+                    "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_mhz:.0f} MHz"}
+        else:
+            peak = float(peaks["bf16_tflops_sustained"])
+            if precision == "fp8":
+                peak *= 2.0
+            roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": None, "kernel": dom, "peak_source": f"{peak_src} bf16_tflops_sustained"}
+    else:
+        roof = {"bound": "hbm", "achieved": None, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "frac": None, "traffic": None, "kernel": dom}
+    roof["stage_ms_per_launch"] = {k: round(v, 4) for k, v in stage_ms.items()}
+    roof["algorithmic"] = {"hits": n_hits, "samples": samples, "flop_per_sample_fwd": flop_per_sample}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"bf16": "bf16", "fp32": "f32", "fp8": "e4m3"}[precision],
+        "data": "synthetic (seeded scene, Kaiming-uniform MLPs, cameras on the r=3 sphere)",
+        "config": {"workload": f"{wl.name}: {wl.width}x{wl.height}, K={wl.K}, MLP {wl.input_dim}-"
+                               f"{'x'.join([str(wl.hidden_width)] * wl.hidden_layers)}-{wl.output_dim}, S={S}, "
+                               f"{wl.n_views} views/rank",
+                   "pass": "fwd+bwd" if do_bwd else "fwd", "precision": precision,
+                   "rays_per_step": n_rays * ws, "hits_per_step": n_hits,
+                   "l2": "flushed between timed steps (256 MiB write); per-step working set > L2",
+                   "parallelism": f"views sharded, {ws} rank(s), no data-path collective"},
+        "results": results,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "roofline": roof,
+    }
+    if rank == 0 and not a.no_e2e:
+        line["e2e"] = run_e2e(a, wl, scene, cams, precision, do_bwd, dev)
+    if rank == 0 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a, wl, scene, cams, do_bwd, r)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(a, wl, scene, cams, precision, do_bwd, dev):
+    """Same metric through the public API with HOST buffers: every step copies the scene
+    parameters (and dL/dC) from pinned host memory and reads the image (and gradients) back."""
+    import torch
+    from paper_2606_03877_gb300 import synth
+    from paper_2606_03877_gb300.render import Renderer
+
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in scene.items()}
+    g_host = torch.from_numpy(synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100, scale=0.01)).pin_memory()
+    dd = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()}
+    g_dev = torch.empty(g_host.shape, device=dev)
+    r = Renderer(wl, precision=precision, device=str(dev))
+    rgb_h = torch.empty(wl.n_views, wl.height, wl.width, 3).pin_memory()
+    tr_h = torch.empty(wl.n_views, wl.height, wl.width).pin_memory()
+    gw_h = torch.empty(wl.K, r.P).pin_memory()
+    gp_h = torch.empty(wl.K, 10).pin_memory()
+    bi = sum(v.numel() * v.element_size() for v in host.values()) + (g_host.numel() * 4 if do_bwd else 0)
+    bo = rgb_h.numel() * 4 + tr_h.numel() * 4 + ((gw_h.numel() + gp_h.numel()) * 4 if do_bwd else 0)
+
+    def step():
+        for k in dd:
+            dd[k].copy_(host[k], non_blocking=True)
+        packed = r.pack(dd["weights"])
+        out = r.forward(dd["centers"], dd["scales"], dd["quats"], packed, cams)
+        if do_bwd:
+            g_dev.copy_(g_host, non_blocking=True)
+            g = r.backward(g_dev)
+            gw_h.copy_(g["d_weights"], non_blocking=True)
+            gp_h[:, 0:3].copy_(g["d_centers"], non_blocking=True)
+            gp_h[:, 3:6].copy_(g["d_scales"], non_blocking=True)
+            gp_h[:, 6:10].copy_(g["d_quats"], non_blocking=True)
+        rgb_h.copy_(out["rgb"], non_blocking=True)
+        tr_h.copy_(out["trans"], non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    steps = max(3, a.steps // 2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": wl.n_rays * steps / (ms / 1e3), "unit": "rays/s", "h2d_bytes_per_step": int(bi),
+            "d2h_bytes_per_step": int(bo), "steps": steps}
+
+
+def cpu_baseline(a, wl, scene, cams, do_bwd, r=None):
+    """The FP64 oracle, as it stands, on a bounded pixel sample of the same workload."""
+    import oracle
+    from paper_2606_03877_gb300 import synth
+
+    cores = os.cpu_count() or 1
+    g = synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100, scale=0.01).reshape(-1, 3)
+
+    def run_oracle(pix):
+        t = time.perf_counter()
+        if do_bwd:
+            idx = pix[:, 0].astype(np.int64) * wl.width * wl.height + pix[:, 2] * wl.width + pix[:, 1]
+            res = oracle.render_backward(wl, scene, cams, pix, g[idx].astype(np.float64), n_threads=cores)
+            rgb = res["rgb"]
+        else:
+            rgb, _, _ = oracle.render(wl, scene, cams, pix=pix, n_threads=cores)
+        return time.perf_counter() - t, rgb
+
+    # calibrate, then size the sample to ~cpu_seconds of work
+    pix = synth.sample_pixels(wl, 4 * cores, seed=321)
+    dt, _ = run_oracle(pix)
+    per_px = dt / len(pix)
+    n = int(max(4 * cores, min(wl.n_rays, a.cpu_seconds / max(per_px, 1e-9))))
+    pix = synth.sample_pixels(wl, n, seed=322)
+    dt, rgb_o = run_oracle(pix)
+    out = {"value": len(pix) / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
+           "sample": f"{len(pix)} pixels sampled uniformly from the {wl.n_views} views "
+                     f"({'forward + reverse mode' if do_bwd else 'forward'}, FP64, {dt:.1f} s)"}
+    if r is not None and r._out_buf is not None:
+        import torch
+        rr = r._out_buf["rgb"].reshape(-1, 3)
+        idx = torch.from_numpy(pix[:, 0].astype(np.int64) * wl.width * wl.height + pix[:, 2] * wl.width + pix[:, 1]).to(rr.device)
+        got = rr[idx].double().cpu().numpy()
+        mse = float(np.mean((got - rgb_o) ** 2))
+        out["psnr_vs_oracle_on_sample"] = float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
+        out["max_abs_vs_oracle_on_sample"] = float(np.abs(got - rgb_o).max())
+    return out
+
+
+def run_reference(a):
+    """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2606_03877_gb300 import synth
+
+    wl = synth.CONFIGS[a.workload]
+    scene = synth.make_scene(wl, 0)
+    cams = synth.make_cameras(wl)
+    cores = os.cpu_count() or 1
+    do_bwd = a.pass_ == "fwdbwd"
+    g = synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100, scale=0.01).reshape(-1, 3)
+    per_step = max(cores, int(os.environ.get("MLPS_REF_PIXELS", "0")) or 0)
+
+    def one(pix):
+        if do_bwd:
+            idx = pix[:, 0].astype(np.int64) * wl.width * wl.height + pix[:, 2] * wl.width + pix[:, 1]
+            oracle.render_backward(wl, scene, cams, pix, g[idx].astype(np.float64), n_threads=cores)
+        else:
+            oracle.render(wl, scene, cams, pix=pix, n_threads=cores)
+
+    # size one step to ~8 s of host work so that steps + warmup stay within a few minutes
+    cal = synth.sample_pixels(wl, 4 * cores, seed=1)
+    t = time.perf_counter(); one(cal); dt = time.perf_counter() - t
+    budget = min(8.0, 150.0 / max(1, a.steps + a.warmup))
+    n = per_step or int(max(cores, budget / max(dt / len(cal), 1e-9)))
+    for i in range(a.warmup):
+        one(synth.sample_pixels(wl, max(cores, n // 8), seed=1000 + i))
+    tot = 0.0
+    for i in range(a.steps):
+        pix = synth.sample_pixels(wl, n, seed=2000 + i)
+        t = time.perf_counter(); one(pix); tot += time.perf_counter() - t
+    value = n * a.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": tot / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{wl.name}: {wl.width}x{wl.height}, K={wl.K}, S={wl.samples}, "
+                                   f"{wl.n_views} views", "pass": "fwd+bwd" if do_bwd else "fwd",
+                       "sample_pixels_per_step": n},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} sampled pixels per step"},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

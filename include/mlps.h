@@ -1,0 +1,217 @@
+/*
+ * mlps.h -- C ABI of the GB300 (sm_103a) MLP-Splatting renderer.
+ *
+ * MLP-Splatting represents a scene by K primitives, each a unit-Mahalanobis ellipsoid (centre
+ * mu, per-axis scale s, rotation quaternion q; Sec. 3.1) carrying its own small MLP that maps an
+ * encoded (local position, view direction) input to colour and density (Sec. 3.1-3.2). A pixel
+ * is rendered by intersecting its ray with the primitives, ordering the hit intervals by the
+ * soft contact point t* of Eq. 2 (which is the chord midpoint), placing S midpoint samples in
+ * each interval, evaluating the primitive's MLP at every sample, and compositing front to back
+ * (Eq. 6 and its sampled form in App. D.1).
+ *
+ * Conventions shared by every entry point:
+ *  - All array arguments are DEVICE pointers unless marked "host". All floats are FP32.
+ *  - The caller owns every buffer. The library never allocates or frees device memory and keeps
+ *    no state between calls (except the optional host-side profiler below). All work is
+ *    enqueued on `stream` (a cudaStream_t; NULL = legacy default stream) and is asynchronous.
+ *  - Synchronous argument errors return a status immediately and enqueue nothing.
+ *    Data-dependent errors found on the device (hit-capacity overflow, non-finite values,
+ *    bounded waits that gave up) are recorded in a status word inside the `saved` or
+ *    `scratch` region and returned by mlps_read_status(). No call traps, aborts or hangs.
+ *  - Image layouts: rgb [V, H, W, 3], trans [V, H, W], feat [V, H, W, F], all row-major,
+ *    V = n_views. Gradients dL/d* use the same layouts.
+ *  - Primitive layouts: centers [K, 3], scales [K, 3] (linear, > 0), quats [K, 4] as
+ *    (w, x, y, z) with any nonzero norm (normalised inside; gradients include the
+ *    normalisation), weights in the canonical FP32 layout [K, P] described below.
+ *  - Canonical FP32 weight layout (P = mlps_param_count floats per primitive): for each layer l
+ *    in order, W_l as [out_l, in_l] row-major, then b_l as [out_l]. Layer 0 reads the encoded
+ *    input, hidden layers have `hidden_width` outputs with ReLU, the last layer has
+ *    4 + feat_dim linear outputs ordered (r, g, b, sigma, f_0 .. f_{F-1}); colour = sigmoid,
+ *    density = softplus (Sec. 3.2), features are used as is.
+ *  - Encoding (Eq. 5): per scalar p, (sin(2^0 pi p), cos(2^0 pi p), ..., sin(2^{L-1} pi p),
+ *    cos(2^{L-1} pi p)), concatenated over the 3 components of the scale-normalised local
+ *    position x' = S^-1 R^T (x - mu) (L = xyz_freqs; raw x' when 0), then over the 3 components
+ *    of the unit world ray direction (L = dir_freqs; omitted when 0).
+ *  - Camera: pinhole, pixel centres at +0.5, OpenCV axes. world_to_cam = [R | t] row-major;
+ *    ray origin -R^T t, direction normalise(R^T ((x + .5 - cx)/fx, (y + .5 - cy)/fy, 1)).
+ */
+#ifndef MLPS_H
+#define MLPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLPS_ABI_VERSION 1
+#define MLPS_MAX_VIEWS 64
+
+typedef int32_t mlps_status;
+enum {
+  MLPS_OK = 0,
+  MLPS_ERR_INVALID_ARGUMENT = 1,   /* null pointer, bad size, non-finite config value */
+  MLPS_ERR_UNSUPPORTED = 2,        /* valid but not implemented shape/precision combination */
+  MLPS_ERR_WORKSPACE_TOO_SMALL = 3,/* saved/scratch smaller than mlps_workspace_size() */
+  MLPS_ERR_CAPACITY_OVERFLOW = 4,  /* device: a ray had > max_hits_per_ray hits, or the total
+                                      hit records exceeded the workspace capacity */
+  MLPS_ERR_TIMEOUT = 5,            /* device: a bounded wait gave up */
+  MLPS_ERR_NONFINITE = 6,          /* device: non-finite value met */
+  MLPS_ERR_CUDA = 7                /* a CUDA runtime call failed */
+};
+
+typedef int32_t mlps_precision;
+enum {
+  MLPS_FP32 = 0,      /* MLP on FP32 FMA (no TF32) */
+  MLPS_BF16 = 1,      /* MLP on tcgen05 tensor cores, BF16 operands, FP32 accumulation */
+  MLPS_FP8_E4M3 = 2   /* MLP on tcgen05 tensor cores, E4M3 operands with per-primitive scales */
+};
+
+/* Renderer configuration. Zero-initialise, then set the fields; mlps_config_default() fills the
+ * defaults for a model shape. */
+typedef struct {
+  int32_t xyz_freqs;            /* L of the local-position encoding (Eq. 5); 0 = raw x' */
+  int32_t dir_freqs;            /* L of the view-direction encoding; 0 = no direction input */
+  int32_t hidden_width;         /* hidden layer width: 32, 64 or 128 */
+  int32_t hidden_layers;        /* number of hidden (ReLU) layers, 1..6 */
+  int32_t feat_dim;             /* extra linear outputs composited like colour, 0..32 */
+  int32_t samples;              /* S midpoint samples per hit interval, 1..128 */
+  int32_t precision;            /* mlps_precision of the MLP contractions */
+  int32_t max_hits_per_ray;     /* per-ray sorted hit capacity, 1..64 */
+  float hit_capacity_per_ray;   /* hit-record capacity = ceil(rays * this), > 0 */
+  float t_eps;                  /* early termination: stop compositing once T < t_eps (0: never) */
+  int32_t tile;                 /* screen tile edge in pixels for binning (16) */
+  int32_t reserved[5];          /* must be zero */
+} mlps_config;
+
+typedef struct {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  float world_to_cam[12];       /* row-major [R | t] */
+  float near_t;                 /* samples start at max(t0, near_t); >= 0 */
+} mlps_camera;
+
+/* One scene. Pointers are device pointers. `weights` is the packed blob produced by
+ * mlps_pack_weights() for config->precision (mlps_weight_stride() bytes per primitive). */
+typedef struct {
+  int32_t K;
+  const float* centers;         /* [K, 3] */
+  const float* scales;          /* [K, 3] */
+  const float* quats;           /* [K, 4] (w, x, y, z) */
+  const void* weights;          /* [K, stride] packed, 256-byte aligned */
+} mlps_scene;
+
+/* ---------------------------------------------------------------------------------------- */
+/* Introspection                                                                              */
+
+/* ABI version (MLPS_ABI_VERSION of the build). */
+int32_t mlps_abi_version(void);
+
+/* Short English text for a status code; never NULL. */
+const char* mlps_status_string(mlps_status s);
+
+/* Fill *cfg with defaults: S = 32, FP32, max_hits_per_ray = 64, hit_capacity_per_ray = 8,
+ * t_eps = 1e-6 (early termination of Sec. B.2; the paper does not give the threshold),
+ * tile = 16. Shape fields are set from the arguments. Returns MLPS_ERR_INVALID_ARGUMENT on a
+ * NULL cfg. */
+mlps_status mlps_config_default(mlps_config* cfg, int32_t xyz_freqs, int32_t dir_freqs,
+                                int32_t hidden_width, int32_t hidden_layers, int32_t feat_dim);
+
+/* Input width of layer 0 after encoding: (xyz_freqs ? 6 xyz_freqs : 3) + 6 dir_freqs. */
+int32_t mlps_input_dim(const mlps_config* cfg);
+
+/* Floats per primitive in the canonical FP32 weight layout (P). 0 on invalid config. */
+int64_t mlps_param_count(const mlps_config* cfg);
+
+/* Bytes per primitive of the packed weight blob for cfg->precision. 0 on invalid config. */
+int64_t mlps_weight_stride(const mlps_config* cfg);
+
+/* Validates a config. MLPS_OK, or the reason it cannot be rendered. */
+mlps_status mlps_check_config(const mlps_config* cfg);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Weights                                                                                    */
+
+/* Convert canonical FP32 weights [K, P] (device) into the packed blob for cfg->precision
+ * (device, [K, mlps_weight_stride] bytes, 256-byte aligned). FP32: a copy re-laid for the SIMT
+ * kernels; BF16: operand tiles in the tensor-core shared-memory layout plus FP32 biases;
+ * FP8-E4M3: the same with per-(primitive, layer) power-of-two scales. Enqueued on `stream`. */
+mlps_status mlps_pack_weights(const mlps_config* cfg, int32_t K, const float* weights_fp32,
+                              void* packed, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Rendering                                                                                  */
+
+/* Bytes of the two workspaces a render of n_views cameras (host array) needs.
+ * `saved` carries the forward state to the backward pass; `scratch` is reused per call.
+ * Both must be 256-byte aligned device memory. */
+mlps_status mlps_workspace_size(const mlps_config* cfg, int32_t K, const mlps_camera* cams,
+                                int32_t n_views, size_t* saved_bytes, size_t* scratch_bytes);
+
+/* Forward render (Sec. 3.2-3.3). cams is a HOST array of n_views cameras (1..MLPS_MAX_VIEWS),
+ * all of the same width and height. Writes rgb [V,H,W,3] and trans [V,H,W] (final
+ * transmittance; background is black), and feat [V,H,W,feat_dim] when feat_dim > 0 (NULL
+ * allowed when feat_dim == 0). Fills `saved` for mlps_render_backward. */
+mlps_status mlps_render_forward(const mlps_config* cfg, const mlps_scene* scene,
+                                const mlps_camera* cams, int32_t n_views, float* rgb,
+                                float* trans, float* feat, void* saved, size_t saved_bytes,
+                                void* scratch, size_t scratch_bytes, void* stream);
+
+/* Backward of the forward call that filled `saved` (same cfg, scene and cams). Given dL/drgb
+ * (required), dL/dtrans and dL/dfeat (either may be NULL = zero), OVERWRITES
+ * d_weights [K, P] (canonical FP32 layout), d_centers [K,3], d_scales [K,3], d_quats [K,4].
+ * The MLP is recomputed, not stored. Hit sets and orders are piecewise constant and are not
+ * differentiated. */
+mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene,
+                                 const mlps_camera* cams, int32_t n_views, const float* d_rgb,
+                                 const float* d_trans, const float* d_feat, const void* saved,
+                                 size_t saved_bytes, float* d_weights, float* d_centers,
+                                 float* d_scales, float* d_quats, void* scratch,
+                                 size_t scratch_bytes, void* stream);
+
+/* Synchronise `stream`, return the device status word of a `saved` or `scratch` region
+ * written by the calls above (MLPS_OK if none), and clear it. */
+mlps_status mlps_read_status(const void* region, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Inspection of a forward pass (tests and tools)                                             */
+
+/* Total hit records written by the forward pass in `saved` (host int64 out). Synchronises. */
+mlps_status mlps_saved_hit_count(const void* saved, int64_t* n_hits, void* stream);
+
+/* Dense copy of the per-ray sorted hit lists held in `saved`: for every ray r (global index
+ * v*H*W + y*W + x), count[r] and, for j < min(count, max_out), prim[r*max_out + j],
+ * t0/t1 (world units, near-clipped) and tmid (Eq. 2 before its max(0, .)). Device outputs. */
+mlps_status mlps_export_hits(const mlps_config* cfg, const mlps_camera* cams, int32_t n_views,
+                             const void* saved, int32_t max_out, int32_t* count, int32_t* prim,
+                             float* t0, float* t1, float* tmid, void* stream);
+
+/* Per-tile candidate lists of the last forward pass held in `scratch` (valid until the
+ * scratch region is reused): count[v*n_tiles + t] and list[(v*n_tiles + t)*K + j], tiles in
+ * row-major order of ceil(H/tile) x ceil(W/tile). Device outputs. */
+mlps_status mlps_export_tiles(const mlps_config* cfg, int32_t K, const mlps_camera* cams,
+                              int32_t n_views, const void* scratch, int32_t* count,
+                              int32_t* list, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Optional host-side stage profiler (not thread-safe; off by default)                        */
+
+/* Number of kernels this library has launched since the last reset (all entry points);
+ * reset != 0 zeroes the counter after reading. */
+int64_t mlps_kernel_launches(int32_t reset);
+
+/* Enable (1) or disable (0). When enabled every call records CUDA events around each kernel
+ * stage on its stream. */
+void mlps_profiler_enable(int32_t on);
+
+/* Synchronise on the recorded events and return the number of stages; for i < max fill
+ * names[i] (static strings) and ms[i] (summed over calls since the last reset) and
+ * counts[i]. reset != 0 clears the table afterwards. */
+int32_t mlps_profiler_read(const char** names, float* ms, int32_t* counts, int32_t max,
+                           int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLPS_H */

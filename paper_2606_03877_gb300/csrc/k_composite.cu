@@ -1,0 +1,143 @@
+// k_composite.cu -- per-ray front-to-back compositing of the sorted hit intervals (Eq. 6), its
+// reverse pass, and the final chain of the pose gradient to (centre, scale, quaternion).
+//
+// Each hit interval j of a ray carries its partial composite (C_j, a_j) from the MLP stage:
+// C_j = sum_k T_k alpha_k c_k with T_k the transmittance inside the interval, and
+// a_j = sum_k sigma_k Delta its optical depth. Along the ray, in t* order,
+// C = sum_j T_j C_j and T_j = exp(-sum_{l<j} a_l) (log-space transmittance). Compositing stops
+// once T drops below t_eps (early termination, Sec. B.2); the rest of the ray is skipped.
+#include <cuda_runtime.h>
+
+#include "mlps_common.cuh"
+#include "mlps_kernels.h"
+
+namespace mlps {
+
+__global__ void k_composite_fwd(Work w, int F, float* __restrict__ rgb, float* __restrict__ trans,
+                                float* __restrict__ feat) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= w.n_rays) return;
+  const int n = w.ray_count[r], s = w.ray_start[r];
+  float A = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  float Fv[kMaxFeat];
+  for (int f = 0; f < F; ++f) Fv[f] = 0.f;
+  for (int j = 0; j < n; ++j) {
+    const float4 o = w.hit_out[s + j];
+    const float T = expf(-A);
+    C0 = fmaf(T, o.x, C0);
+    C1 = fmaf(T, o.y, C1);
+    C2 = fmaf(T, o.z, C2);
+    for (int f = 0; f < F; ++f) Fv[f] = fmaf(T, w.hit_feat[(size_t)(s + j) * F + f], Fv[f]);
+    A += o.w;
+    if (expf(-A) < w.t_eps) break;
+  }
+  rgb[3 * (size_t)r] = C0;
+  rgb[3 * (size_t)r + 1] = C1;
+  rgb[3 * (size_t)r + 2] = C2;
+  trans[r] = expf(-A);
+  for (int f = 0; f < F; ++f) feat[(size_t)r * F + f] = Fv[f];
+}
+
+// Reverse pass. With C = sum_j T_j C_j, T_final = exp(-sum_j a_j):
+//   dL/dC_j = T_j dL/dC,   dL/dF_j = T_j dL/dF,
+//   dL/da_j = -dL/dC . sum_{l>j} T_l C_l - dL/dF . sum_{l>j} T_l F_l - dL/dT_final T_final.
+// Intervals skipped by early termination get zero gradient.
+__global__ void k_composite_bwd(Work w, int F, const float* __restrict__ d_rgb,
+                                const float* __restrict__ d_trans,
+                                const float* __restrict__ d_feat) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= w.n_rays) return;
+  const int n = w.ray_count[r], s = w.ray_start[r];
+  float Aex[kMaxHits];
+  float A = 0.f;
+  int used = 0;
+  for (int j = 0; j < n; ++j) {
+    Aex[j] = A;
+    A += w.hit_out[s + j].w;
+    used = j + 1;
+    if (expf(-A) < w.t_eps) break;
+  }
+  const float Tfin = expf(-A);
+  const float g0 = d_rgb[3 * (size_t)r], g1 = d_rgb[3 * (size_t)r + 1], g2 = d_rgb[3 * (size_t)r + 2];
+  const float gT = d_trans ? d_trans[r] : 0.f;
+  float gF[kMaxFeat], RF[kMaxFeat];
+  for (int f = 0; f < F; ++f) {
+    gF[f] = d_feat ? d_feat[(size_t)r * F + f] : 0.f;
+    RF[f] = 0.f;
+  }
+  float R0 = 0.f, R1 = 0.f, R2 = 0.f;  // sum over later intervals of T_l C_l
+  for (int j = used - 1; j >= 0; --j) {
+    const int h = s + j;
+    const float4 o = w.hit_out[h];
+    const float T = expf(-Aex[j]);
+    float ga = -(g0 * R0 + g1 * R1 + g2 * R2) - gT * Tfin;
+    for (int f = 0; f < F; ++f) ga -= gF[f] * RF[f];
+    w.hit_grad[h] = make_float4(T * g0, T * g1, T * g2, ga);
+    for (int f = 0; f < F; ++f) {
+      const float Fj = w.hit_feat[(size_t)h * F + f];
+      w.hit_gfeat[(size_t)h * F + f] = T * gF[f];
+      RF[f] = fmaf(T, Fj, RF[f]);
+    }
+    R0 = fmaf(T, o.x, R0);
+    R1 = fmaf(T, o.y, R1);
+    R2 = fmaf(T, o.z, R2);
+  }
+  for (int j = used; j < n; ++j) {
+    w.hit_grad[s + j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int f = 0; f < F; ++f) w.hit_gfeat[(size_t)(s + j) * F + f] = 0.f;
+  }
+}
+
+// dL/dM (9) and dL/dmu (3) per primitive -> centre, scale, quaternion.
+// M_ij = R_ji / s_i with R = R(q/|q|); the quaternion gradient is projected through the
+// normalisation: dL/dq = (g - qn (qn . g)) / |q|.
+__global__ void k_pose_bwd(Work w, float* d_centers, float* d_scales, float* d_quats) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= w.K) return;
+  const PrimGeo& g = w.geo[p];
+  const float* dM = w.dgeo + 12 * (size_t)p;
+  for (int i = 0; i < 3; ++i) d_centers[3 * p + i] = dM[9 + i];
+  float dR[9];
+  for (int i = 0; i < 9; ++i) dR[i] = 0.f;
+  for (int i = 0; i < 3; ++i) {
+    float acc = 0.f;
+    for (int j = 0; j < 3; ++j) {
+      acc += dM[i * 3 + j] * (-g.R[j * 3 + i] / (g.s[i] * g.s[i]));
+      dR[j * 3 + i] += dM[i * 3 + j] / g.s[i];
+    }
+    d_scales[3 * p + i] = acc;
+  }
+  const float qw = g.qn[0], qx = g.qn[1], qy = g.qn[2], qz = g.qn[3];
+  float gq[4];
+  gq[0] = 2.f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
+  gq[1] = 2.f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - 2.f * qx * dR[4] - qw * dR[5] + qz * dR[6] +
+                 qw * dR[7] - 2.f * qx * dR[8]);
+  gq[2] = 2.f * (-2.f * qy * dR[0] + qx * dR[1] + qw * dR[2] + qx * dR[3] + qz * dR[5] - qw * dR[6] +
+                 qz * dR[7] - 2.f * qy * dR[8]);
+  gq[3] = 2.f * (-2.f * qz * dR[0] - qw * dR[1] + qx * dR[2] + qw * dR[3] - 2.f * qz * dR[4] +
+                 qy * dR[5] + qx * dR[6] + qy * dR[7]);
+  const float dot = gq[0] * qw + gq[1] * qx + gq[2] * qy + gq[3] * qz;
+  for (int i = 0; i < 4; ++i) d_quats[4 * p + i] = g.valid ? (gq[i] - g.qn[i] * dot) / g.qlen : 0.f;
+}
+
+void launch_composite_fwd(const Work& w, int F, float* rgb, float* trans, float* feat,
+                          cudaStream_t st) {
+  if (w.n_rays == 0) return;
+  k_composite_fwd<<<(w.n_rays + 255) / 256, 256, 0, st>>>(w, F, rgb, trans, feat);
+}
+
+void launch_composite_bwd(const Work& w, int F, const float* rgb, const float* trans,
+                          const float* feat, const float* d_rgb, const float* d_trans,
+                          const float* d_feat, cudaStream_t st) {
+  (void)rgb; (void)trans; (void)feat;
+  if (w.n_rays == 0) return;
+  k_composite_bwd<<<(w.n_rays + 255) / 256, 256, 0, st>>>(w, F, d_rgb, d_trans, d_feat);
+}
+
+void launch_pose_bwd(const Work& w, float* d_centers, float* d_scales, float* d_quats,
+                     cudaStream_t st) {
+  if (w.K == 0) return;
+  k_pose_bwd<<<(w.K + 127) / 128, 128, 0, st>>>(w, d_centers, d_scales, d_quats);
+}
+
+}  // namespace mlps

@@ -1,0 +1,635 @@
+// mlps_api.cu -- the C ABI of include/mlps.h: validation, workspace carving and the stage
+// sequence of the forward and backward passes.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "mlps_common.cuh"
+#include "mlps_kernels.h"
+
+using namespace mlps;
+
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// Profiler (host-side, optional)
+
+struct ProfRec {
+  int stage;
+  cudaEvent_t a, b;
+};
+const char* kStageNames[] = {"setup", "tile_lists", "intersect", "prim_scan", "scatter",
+                             "mlp_fwd", "composite_fwd", "composite_bwd", "mlp_bwd", "pose_bwd",
+                             "pack"};
+constexpr int kNumStages = sizeof(kStageNames) / sizeof(kStageNames[0]);
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_pending;
+std::vector<cudaEvent_t> g_prof_pool;
+float g_prof_ms[kNumStages];
+int g_prof_cnt[kNumStages];
+
+cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct StageTimer {
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  StageTimer(int s, cudaStream_t stream) : stage(s), st(stream) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    a = prof_event();
+    cudaEventRecord(a, st);
+  }
+  ~StageTimer() {
+    if (!a) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t b = prof_event();
+    cudaEventRecord(b, st);
+    g_prof_pending.push_back({stage, a, b});
+  }
+};
+
+std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+enum { ST_SETUP, ST_TILES, ST_INTERSECT, ST_SCAN, ST_SCATTER, ST_MLP_FWD, ST_COMP_FWD,
+       ST_COMP_BWD, ST_MLP_BWD, ST_POSE_BWD, ST_PACK };
+
+// ------------------------------------------------------------------------------------------
+// Model and packing layouts
+
+bool finite_f(float x) { return std::isfinite(x); }
+
+mlps_status check_cfg(const mlps_config* c) {
+  if (!c) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->xyz_freqs < 0 || c->xyz_freqs > 16 || c->dir_freqs < 0 || c->dir_freqs > 16)
+    return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->hidden_layers < 1 || c->hidden_layers > kMaxLayers - 1) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->feat_dim < 0 || c->feat_dim > kMaxFeat) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->samples < 1 || c->samples > 128) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->max_hits_per_ray < 1 || c->max_hits_per_ray > kMaxHits) return MLPS_ERR_INVALID_ARGUMENT;
+  if (!finite_f(c->hit_capacity_per_ray) || !(c->hit_capacity_per_ray > 0.f))
+    return MLPS_ERR_INVALID_ARGUMENT;
+  if (!finite_f(c->t_eps) || c->t_eps < 0.f || c->t_eps >= 1.f) return MLPS_ERR_INVALID_ARGUMENT;
+  for (int i = 0; i < 5; ++i)
+    if (c->reserved[i] != 0) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->hidden_width != 32 && c->hidden_width != 64 && c->hidden_width != 128)
+    return MLPS_ERR_UNSUPPORTED;
+  if (c->tile != 16 && c->tile != 8) return MLPS_ERR_UNSUPPORTED;
+  if (c->precision != MLPS_FP32 && c->precision != MLPS_BF16 && c->precision != MLPS_FP8_E4M3)
+    return MLPS_ERR_INVALID_ARGUMENT;
+  if (model_input_dim(c->xyz_freqs, c->dir_freqs) > 128) return MLPS_ERR_UNSUPPORTED;
+  return MLPS_OK;
+}
+
+Model make_model(const mlps_config* c) {
+  Model m;
+  std::memset(&m, 0, sizeof(m));
+  m.nin = model_input_dim(c->xyz_freqs, c->dir_freqs);
+  m.nout = 4 + c->feat_dim;
+  m.width = c->hidden_width;
+  m.nl = c->hidden_layers + 1;
+  m.S = c->samples;
+  m.F = c->feat_dim;
+  m.xyzL = c->xyz_freqs;
+  m.dirL = c->dir_freqs;
+  int off = 0;
+  for (int l = 0; l < m.nl; ++l) {
+    m.din[l] = l == 0 ? m.nin : m.width;
+    m.dout[l] = l == m.nl - 1 ? m.nout : m.width;
+    m.woff[l] = off;
+    off += m.din[l] * m.dout[l];
+    m.boff[l] = off;
+    off += m.dout[l];
+  }
+  m.P = off;
+  return m;
+}
+
+int r4(int x) { return (x + 3) & ~3; }
+long long r256(long long x) { return (x + 255) & ~255LL; }
+
+Packed make_packed(const mlps_config* c, const Model& m) {
+  Packed pk;
+  std::memset(&pk, 0, sizeof(pk));
+  pk.precision = c->precision;
+  int off = 0;
+  for (int l = 0; l < m.nl; ++l) {
+    pk.woff[l] = off;
+    off = r4(off + m.din[l] * m.dout[l]);
+    pk.boff[l] = off;
+    off = r4(off + m.dout[l]);
+  }
+  pk.stride = r256((long long)off * 4);
+  return pk;
+}
+
+// ------------------------------------------------------------------------------------------
+// Workspace layout
+
+struct Carve {
+  size_t off = 256;  // header first
+  template <typename T>
+  size_t take(size_t count) {
+    size_t o = off;
+    off += (count * sizeof(T) + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+struct Layout {
+  // saved
+  size_t hit_prim, hit_ray, hit_tmid, hit_r0, hit_r1, hit_p, hit_out, hit_feat, ray_start,
+      ray_count, prim_count, prim_start, chunk_start, prim_list, views, geo, pview, saved_total;
+  // scratch
+  size_t prim_cursor, tile_count, tile_list, hit_grad, hit_gfeat, dgeo, scratch_total;
+  long long hit_cap;
+  int n_tiles, ntx, nty;
+  long long n_rays;
+};
+
+bool make_layout(const mlps_config* c, int K, int V, int H, int W, Layout* L) {
+  const int F = c->feat_dim;
+  L->ntx = (W + c->tile - 1) / c->tile;
+  L->nty = (H + c->tile - 1) / c->tile;
+  L->n_tiles = L->ntx * L->nty;
+  L->n_rays = (long long)V * H * W;
+  if (L->n_rays > 0x7fffffffLL) return false;
+  double cap = std::ceil((double)L->n_rays * (double)c->hit_capacity_per_ray);
+  if (cap < 1) cap = 1;
+  if (cap > 0x7fff0000) return false;
+  L->hit_cap = (long long)cap;
+  const size_t hc = (size_t)L->hit_cap, nr = (size_t)L->n_rays;
+  Carve s;
+  L->hit_prim = s.take<int>(hc);
+  L->hit_ray = s.take<int>(hc);
+  L->hit_tmid = s.take<float>(hc);
+  L->hit_r0 = s.take<float>(hc);
+  L->hit_r1 = s.take<float>(hc);
+  L->hit_p = s.take<float>(3 * hc);
+  L->hit_out = s.take<float4>(hc);
+  L->hit_feat = s.take<float>(hc * (size_t)(F > 0 ? F : 1));
+  L->ray_start = s.take<int>(nr ? nr : 1);
+  L->ray_count = s.take<int>(nr ? nr : 1);
+  L->prim_count = s.take<int>((size_t)K + 1);
+  L->prim_start = s.take<int>((size_t)K + 1);
+  L->chunk_start = s.take<int>((size_t)K + 1);
+  L->prim_list = s.take<int>(hc);
+  L->views = s.take<ViewData>((size_t)V);
+  L->geo = s.take<PrimGeo>((size_t)K + 1);
+  L->pview = s.take<PrimView>((size_t)V * K + 1);
+  L->saved_total = s.off;
+  Carve t;
+  L->prim_cursor = t.take<int>((size_t)K + 1);
+  L->tile_count = t.take<int>((size_t)V * L->n_tiles + 1);
+  L->tile_list = t.take<int>((size_t)V * L->n_tiles * (size_t)K + 1);
+  L->hit_grad = t.take<float4>(hc);
+  L->hit_gfeat = t.take<float>(hc * (size_t)(F > 0 ? F : 1));
+  L->dgeo = t.take<float>((size_t)K * 12 + 1);
+  L->scratch_total = t.off;
+  return true;
+}
+
+Work make_work(const mlps_config* c, const Layout& L, int K, int V, int H, int W, void* saved,
+               void* scratch) {
+  Work w;
+  std::memset(&w, 0, sizeof(w));
+  char* sv = static_cast<char*>(saved);
+  char* sc = static_cast<char*>(scratch);
+  w.saved_hdr = reinterpret_cast<int*>(sv);
+  w.hit_prim = reinterpret_cast<int*>(sv + L.hit_prim);
+  w.hit_ray = reinterpret_cast<int*>(sv + L.hit_ray);
+  w.hit_tmid = reinterpret_cast<float*>(sv + L.hit_tmid);
+  w.hit_r0 = reinterpret_cast<float*>(sv + L.hit_r0);
+  w.hit_r1 = reinterpret_cast<float*>(sv + L.hit_r1);
+  w.hit_p = reinterpret_cast<float*>(sv + L.hit_p);
+  w.hit_out = reinterpret_cast<float4*>(sv + L.hit_out);
+  w.hit_feat = reinterpret_cast<float*>(sv + L.hit_feat);
+  w.ray_start = reinterpret_cast<int*>(sv + L.ray_start);
+  w.ray_count = reinterpret_cast<int*>(sv + L.ray_count);
+  w.prim_count = reinterpret_cast<int*>(sv + L.prim_count);
+  w.prim_start = reinterpret_cast<int*>(sv + L.prim_start);
+  w.chunk_start = reinterpret_cast<int*>(sv + L.chunk_start);
+  w.prim_list = reinterpret_cast<int*>(sv + L.prim_list);
+  w.views = reinterpret_cast<ViewData*>(sv + L.views);
+  w.geo = reinterpret_cast<PrimGeo*>(sv + L.geo);
+  w.pview = reinterpret_cast<PrimView*>(sv + L.pview);
+  if (sc) {
+    w.scr_hdr = reinterpret_cast<int*>(sc);
+    w.prim_cursor = reinterpret_cast<int*>(sc + L.prim_cursor);
+    w.tile_count = reinterpret_cast<int*>(sc + L.tile_count);
+    w.tile_list = reinterpret_cast<int*>(sc + L.tile_list);
+    w.hit_grad = reinterpret_cast<float4*>(sc + L.hit_grad);
+    w.hit_gfeat = reinterpret_cast<float*>(sc + L.hit_gfeat);
+    w.dgeo = reinterpret_cast<float*>(sc + L.dgeo);
+  }
+  w.K = K;
+  w.V = V;
+  w.H = H;
+  w.W = W;
+  w.tile = c->tile;
+  w.ntx = L.ntx;
+  w.nty = L.nty;
+  w.n_tiles = L.n_tiles;
+  w.n_rays = (int)L.n_rays;
+  w.hit_cap = (int)L.hit_cap;
+  w.max_hits = c->max_hits_per_ray;
+  w.ipc = (c->samples <= 128) ? 128 / c->samples : 1;
+  w.t_eps = c->t_eps;
+  return w;
+}
+
+mlps_status check_cams(const mlps_camera* cams, int V, int* H, int* W) {
+  if (!cams || V < 1 || V > kMaxViews) return MLPS_ERR_INVALID_ARGUMENT;
+  *W = cams[0].width;
+  *H = cams[0].height;
+  if (*W < 1 || *H < 1 || *W > 16384 || *H > 16384) return MLPS_ERR_INVALID_ARGUMENT;
+  for (int v = 0; v < V; ++v) {
+    const mlps_camera& c = cams[v];
+    if (c.width != *W || c.height != *H) return MLPS_ERR_UNSUPPORTED;
+    const float vals[6] = {c.fx, c.fy, c.cx, c.cy, c.near_t, 0.f};
+    for (float x : vals)
+      if (!finite_f(x)) return MLPS_ERR_INVALID_ARGUMENT;
+    for (float x : c.world_to_cam)
+      if (!finite_f(x)) return MLPS_ERR_INVALID_ARGUMENT;
+    if (c.fx == 0.f || c.fy == 0.f || c.near_t < 0.f) return MLPS_ERR_INVALID_ARGUMENT;
+  }
+  return MLPS_OK;
+}
+
+ViewArray make_views(const mlps_camera* cams, int V) {
+  ViewArray va;
+  std::memset(&va, 0, sizeof(va));
+  for (int v = 0; v < V; ++v) {
+    const mlps_camera& c = cams[v];
+    ViewData& d = va.v[v];
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) d.R[i * 3 + j] = c.world_to_cam[i * 4 + j];
+      d.t[i] = c.world_to_cam[i * 4 + 3];
+    }
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    d.near_t = c.near_t;
+    d.width = c.width;
+    d.height = c.height;
+    d.ray_base = v * c.width * c.height;
+    for (int i = 0; i < 3; ++i) {
+      // origin -R^T t in FP64, split into hi + lo
+      double o = -((double)d.R[0 * 3 + i] * d.t[0] + (double)d.R[1 * 3 + i] * d.t[1] +
+                   (double)d.R[2 * 3 + i] * d.t[2]);
+      float hi = (float)o;
+      d.o_hi[i] = hi;
+      d.o_lo[i] = (float)(o - (double)hi);
+    }
+  }
+  return va;
+}
+
+int num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  return n;
+}
+
+bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
+
+mlps_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MLPS_OK : MLPS_ERR_CUDA; }
+
+}  // namespace
+
+// ============================================================================================
+extern "C" {
+
+int32_t mlps_abi_version(void) { return MLPS_ABI_VERSION; }
+
+const char* mlps_status_string(mlps_status s) {
+  switch (s) {
+    case MLPS_OK: return "ok";
+    case MLPS_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case MLPS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MLPS_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case MLPS_ERR_CAPACITY_OVERFLOW: return "hit capacity overflow";
+    case MLPS_ERR_TIMEOUT: return "bounded wait timed out";
+    case MLPS_ERR_NONFINITE: return "non-finite value";
+    case MLPS_ERR_CUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+mlps_status mlps_config_default(mlps_config* cfg, int32_t xyz_freqs, int32_t dir_freqs,
+                                int32_t hidden_width, int32_t hidden_layers, int32_t feat_dim) {
+  if (!cfg) return MLPS_ERR_INVALID_ARGUMENT;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->xyz_freqs = xyz_freqs;
+  cfg->dir_freqs = dir_freqs;
+  cfg->hidden_width = hidden_width;
+  cfg->hidden_layers = hidden_layers;
+  cfg->feat_dim = feat_dim;
+  cfg->samples = 32;
+  cfg->precision = MLPS_FP32;
+  cfg->max_hits_per_ray = 64;
+  cfg->hit_capacity_per_ray = 8.0f;
+  cfg->t_eps = 1e-6f;
+  cfg->tile = 16;
+  return MLPS_OK;
+}
+
+int32_t mlps_input_dim(const mlps_config* cfg) {
+  if (!cfg) return 0;
+  return model_input_dim(cfg->xyz_freqs, cfg->dir_freqs);
+}
+
+int64_t mlps_param_count(const mlps_config* cfg) {
+  if (check_cfg(cfg) != MLPS_OK) return 0;
+  return make_model(cfg).P;
+}
+
+int64_t mlps_weight_stride(const mlps_config* cfg) {
+  if (check_cfg(cfg) != MLPS_OK) return 0;
+  Model m = make_model(cfg);
+  Packed pk = make_packed(cfg, m);
+  return pk.stride;
+}
+
+mlps_status mlps_check_config(const mlps_config* cfg) {
+  mlps_status s = check_cfg(cfg);
+  if (s != MLPS_OK) return s;
+  if (cfg->precision != MLPS_FP32) return MLPS_ERR_UNSUPPORTED;
+  return MLPS_OK;
+}
+
+mlps_status mlps_pack_weights(const mlps_config* cfg, int32_t K, const float* weights_fp32,
+                              void* packed, void* stream) {
+  mlps_status s = mlps_check_config(cfg);
+  if (s != MLPS_OK) return s;
+  if (K < 0 || (K > 0 && (!weights_fp32 || !packed)) || (packed && !aligned256(packed)))
+    return MLPS_ERR_INVALID_ARGUMENT;
+  Model m = make_model(cfg);
+  Packed pk = make_packed(cfg, m);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  StageTimer tm(ST_PACK, st);
+  launch_pack_fp32(m, pk, K, weights_fp32, packed, st);
+  count_launch(K > 0 ? 1 : 0);
+  return cuda_status(cudaGetLastError());
+}
+
+mlps_status mlps_workspace_size(const mlps_config* cfg, int32_t K, const mlps_camera* cams,
+                                int32_t n_views, size_t* saved_bytes, size_t* scratch_bytes) {
+  mlps_status s = mlps_check_config(cfg);
+  if (s != MLPS_OK) return s;
+  if (K < 0 || !saved_bytes || !scratch_bytes) return MLPS_ERR_INVALID_ARGUMENT;
+  int H, W;
+  s = check_cams(cams, n_views, &H, &W);
+  if (s != MLPS_OK) return s;
+  Layout L;
+  if (!make_layout(cfg, K, n_views, H, W, &L)) return MLPS_ERR_UNSUPPORTED;
+  *saved_bytes = L.saved_total;
+  *scratch_bytes = L.scratch_total;
+  return MLPS_OK;
+}
+
+mlps_status mlps_render_forward(const mlps_config* cfg, const mlps_scene* scene,
+                                const mlps_camera* cams, int32_t n_views, float* rgb,
+                                float* trans, float* feat, void* saved, size_t saved_bytes,
+                                void* scratch, size_t scratch_bytes, void* stream) {
+  mlps_status s = mlps_check_config(cfg);
+  if (s != MLPS_OK) return s;
+  if (!scene || scene->K < 0 || !rgb || !trans || !saved || !scratch)
+    return MLPS_ERR_INVALID_ARGUMENT;
+  if (cfg->feat_dim > 0 && !feat) return MLPS_ERR_INVALID_ARGUMENT;
+  const int K = scene->K;
+  if (K > 0 && (!scene->centers || !scene->scales || !scene->quats || !scene->weights))
+    return MLPS_ERR_INVALID_ARGUMENT;
+  if (!aligned256(saved) || !aligned256(scratch) || (K > 0 && !aligned256(scene->weights)))
+    return MLPS_ERR_INVALID_ARGUMENT;
+  int H, W;
+  s = check_cams(cams, n_views, &H, &W);
+  if (s != MLPS_OK) return s;
+  Layout L;
+  if (!make_layout(cfg, K, n_views, H, W, &L)) return MLPS_ERR_UNSUPPORTED;
+  if (saved_bytes < L.saved_total || scratch_bytes < L.scratch_total)
+    return MLPS_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Work w = make_work(cfg, L, K, n_views, H, W, saved, scratch);
+  Model m = make_model(cfg);
+  MlpArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.m = m;
+  a.pk = make_packed(cfg, m);
+  a.weights = static_cast<const unsigned char*>(scene->weights);
+  a.rows = 128;
+  a.resident = (a.pk.stride + 2 * 128 * 4 * (size_t)std::max(std::max(m.nin, m.width), m.nout) +
+                16 * 1024) <= 200 * 1024;
+  const int n_sm = num_sms();
+  {
+    StageTimer tm(ST_SETUP, st);
+    cudaMemsetAsync(w.saved_hdr, 0, 256, st);
+    cudaMemsetAsync(w.prim_count, 0, sizeof(int) * ((size_t)K + 1), st);
+    launch_store_views(w, make_views(cams, n_views), st);
+    launch_prim_setup(w, scene->centers, scene->scales, scene->quats, st);
+    count_launch(K > 0 ? 2 : 1);
+  }
+  {
+    StageTimer tm(ST_TILES, st);
+    launch_tile_lists(w, st);
+    count_launch(1);
+  }
+  {
+    StageTimer tm(ST_INTERSECT, st);
+    if (!launch_intersect(w, st)) return MLPS_ERR_UNSUPPORTED;
+    count_launch(1);
+  }
+  {
+    StageTimer tm(ST_SCAN, st);
+    if (K > 0) { launch_prim_scan(w, st); count_launch(1); }
+  }
+  {
+    StageTimer tm(ST_SCATTER, st);
+    if (K > 0) { launch_scatter(w, n_sm, st); count_launch(1); }
+  }
+  if (K > 0) {
+    StageTimer tm(ST_MLP_FWD, st);
+    cudaError_t e = launch_mlp_fwd_simt(w, a, n_sm, st);
+    if (e != cudaSuccess) return MLPS_ERR_CUDA;
+    count_launch(1);
+  }
+  {
+    StageTimer tm(ST_COMP_FWD, st);
+    launch_composite_fwd(w, cfg->feat_dim, rgb, trans, feat, st);
+    count_launch(w.n_rays > 0 ? 1 : 0);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene,
+                                 const mlps_camera* cams, int32_t n_views, const float* d_rgb,
+                                 const float* d_trans, const float* d_feat, const void* saved,
+                                 size_t saved_bytes, float* d_weights, float* d_centers,
+                                 float* d_scales, float* d_quats, void* scratch,
+                                 size_t scratch_bytes, void* stream) {
+  mlps_status s = mlps_check_config(cfg);
+  if (s != MLPS_OK) return s;
+  if (!scene || scene->K < 0 || !d_rgb || !saved || !scratch) return MLPS_ERR_INVALID_ARGUMENT;
+  const int K = scene->K;
+  if (K > 0 && (!scene->weights || !d_weights || !d_centers || !d_scales || !d_quats))
+    return MLPS_ERR_INVALID_ARGUMENT;
+  if (!aligned256(saved) || !aligned256(scratch)) return MLPS_ERR_INVALID_ARGUMENT;
+  int H, W;
+  s = check_cams(cams, n_views, &H, &W);
+  if (s != MLPS_OK) return s;
+  Layout L;
+  if (!make_layout(cfg, K, n_views, H, W, &L)) return MLPS_ERR_UNSUPPORTED;
+  if (saved_bytes < L.saved_total || scratch_bytes < L.scratch_total)
+    return MLPS_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Work w = make_work(cfg, L, K, n_views, H, W, const_cast<void*>(saved), scratch);
+  Model m = make_model(cfg);
+  MlpArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.m = m;
+  a.pk = make_packed(cfg, m);
+  a.weights = static_cast<const unsigned char*>(scene->weights);
+  a.d_weights = d_weights;
+  a.rows = 128;
+  a.resident = (a.pk.stride <= 64 * 1024);
+  const int n_sm = num_sms();
+  {
+    StageTimer tm(ST_COMP_BWD, st);
+    cudaMemsetAsync(w.scr_hdr, 0, 256, st);
+    if (K > 0) {
+      cudaMemsetAsync(w.dgeo, 0, sizeof(float) * 12 * (size_t)K, st);
+      cudaMemsetAsync(d_weights, 0, sizeof(float) * (size_t)m.P * K, st);
+    }
+    launch_composite_bwd(w, cfg->feat_dim, nullptr, nullptr, nullptr, d_rgb, d_trans,
+                         cfg->feat_dim > 0 ? d_feat : nullptr, st);
+    count_launch(w.n_rays > 0 ? 1 : 0);
+  }
+  if (K > 0) {
+    StageTimer tm(ST_MLP_BWD, st);
+    cudaError_t e = launch_mlp_bwd_simt(w, a, n_sm, st);
+    if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) return MLPS_ERR_CUDA;
+    count_launch(1);
+  }
+  {
+    StageTimer tm(ST_POSE_BWD, st);
+    launch_pose_bwd(w, d_centers, d_scales, d_quats, st);
+    count_launch(K > 0 ? 1 : 0);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+mlps_status mlps_read_status(const void* region, void* stream) {
+  if (!region) return MLPS_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, region, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MLPS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MLPS_ERR_CUDA;
+  if (h != 0) {
+    const int zero = 0;
+    cudaMemcpyAsync(const_cast<void*>(region), &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+  }
+  return h;
+}
+
+mlps_status mlps_saved_hit_count(const void* saved, int64_t* n_hits, void* stream) {
+  if (!saved || !n_hits) return MLPS_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h[2] = {0, 0};
+  if (cudaMemcpyAsync(h, saved, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MLPS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MLPS_ERR_CUDA;
+  *n_hits = h[1];
+  return MLPS_OK;
+}
+
+mlps_status mlps_export_hits(const mlps_config* cfg, const mlps_camera* cams, int32_t n_views,
+                             const void* saved, int32_t max_out, int32_t* count, int32_t* prim,
+                             float* t0, float* t1, float* tmid, void* stream) {
+  mlps_status s = check_cfg(cfg);
+  if (s != MLPS_OK) return s;
+  if (!saved || max_out < 1 || !count || !prim || !t0 || !t1 || !tmid)
+    return MLPS_ERR_INVALID_ARGUMENT;
+  int H, W;
+  s = check_cams(cams, n_views, &H, &W);
+  if (s != MLPS_OK) return s;
+  Layout L;
+  // K only shifts arrays after the ray arrays; the hit/ray arrays do not depend on it.
+  if (!make_layout(cfg, 0, n_views, H, W, &L)) return MLPS_ERR_UNSUPPORTED;
+  Work w = make_work(cfg, L, 0, n_views, H, W, const_cast<void*>(saved), nullptr);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (w.n_rays > 0) launch_export_hits(w, max_out, count, prim, t0, t1, tmid, st);
+  return cuda_status(cudaGetLastError());
+}
+
+mlps_status mlps_export_tiles(const mlps_config* cfg, int32_t K, const mlps_camera* cams,
+                              int32_t n_views, const void* scratch, int32_t* count,
+                              int32_t* list, void* stream) {
+  mlps_status s = check_cfg(cfg);
+  if (s != MLPS_OK) return s;
+  if (!scratch || !count || !list || K < 1) return MLPS_ERR_INVALID_ARGUMENT;
+  int H, W;
+  s = check_cams(cams, n_views, &H, &W);
+  if (s != MLPS_OK) return s;
+  Layout L;
+  if (!make_layout(cfg, K, n_views, H, W, &L)) return MLPS_ERR_UNSUPPORTED;
+  static char dummy_saved[256];
+  Work w = make_work(cfg, L, K, n_views, H, W, dummy_saved, const_cast<void*>(scratch));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  launch_export_tiles(w, count, list, st);
+  return cuda_status(cudaGetLastError());
+}
+
+int64_t mlps_kernel_launches(int32_t reset) {
+  long long v = reset ? g_launches.exchange(0) : g_launches.load();
+  return (int64_t)v;
+}
+
+void mlps_profiler_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+}
+
+int32_t mlps_profiler_read(const char** names, float* ms, int32_t* counts, int32_t max,
+                           int32_t reset) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (const ProfRec& r : g_prof_pending) {
+    float t = 0.f;
+    cudaEventSynchronize(r.b);
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      g_prof_ms[r.stage] += t;
+      g_prof_cnt[r.stage] += 1;
+    }
+    g_prof_pool.push_back(r.a);
+    g_prof_pool.push_back(r.b);
+  }
+  g_prof_pending.clear();
+  for (int i = 0; i < kNumStages && i < max; ++i) {
+    if (names) names[i] = kStageNames[i];
+    if (ms) ms[i] = g_prof_ms[i];
+    if (counts) counts[i] = g_prof_cnt[i];
+  }
+  if (reset) {
+    for (int i = 0; i < kNumStages; ++i) { g_prof_ms[i] = 0.f; g_prof_cnt[i] = 0; }
+  }
+  return kNumStages;
+}
+
+}  // extern "C"

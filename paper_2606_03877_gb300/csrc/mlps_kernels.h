@@ -1,0 +1,63 @@
+// mlps_kernels.h -- host-side launchers of the MLP-Splatting kernels (one per translation unit).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mlps_common.cuh"
+
+namespace mlps {
+
+// Packed weight blob description (per primitive, bytes from the primitive's base).
+struct Packed {
+  int precision;       // mlps_precision
+  long long stride;    // bytes per primitive (multiple of 256)
+  // FP32: per layer W^T [din][dout] then b [dout], each block starting on 16 bytes
+  int woff[kMaxLayers], boff[kMaxLayers];  // float offsets (FP32 layout)
+  // tensor-core layouts (BF16 / FP8): byte offsets of the operand tiles and FP32 biases
+  int tc_w[kMaxLayers];      // forward B operand tile: W [N=dout_pad][K=din_pad]
+  int tc_wt[kMaxLayers];     // backward B operand tile: W^T [N=din_pad][K=dout_pad]
+  int tc_b[kMaxLayers];      // FP32 bias [dout_pad]
+  int tc_scale;              // FP8: float scales [2 * nl] (forward tile, transposed tile)
+  int din_pad[kMaxLayers], dout_pad[kMaxLayers];
+};
+
+struct MlpArgs {
+  Model m;
+  Packed pk;
+  const unsigned char* weights;  // packed blob [K, stride]
+  float* d_weights;              // backward: canonical FP32 gradient [K, P]
+  int resident;                  // FP32: all layers in shared memory at once
+  int rows;                      // sample rows per chunk
+};
+
+// k_geometry.cu
+void launch_store_views(const Work& w, const ViewArray& va, cudaStream_t st);
+void launch_prim_setup(const Work& w, const float* c, const float* s, const float* q,
+                       cudaStream_t st);
+void launch_tile_lists(const Work& w, cudaStream_t st);
+bool launch_intersect(const Work& w, cudaStream_t st);
+void launch_prim_scan(const Work& w, cudaStream_t st);
+void launch_scatter(const Work& w, int n_sm, cudaStream_t st);
+void launch_export_hits(const Work& w, int max_out, int* count, int* prim, float* t0, float* t1,
+                        float* tmid, cudaStream_t st);
+void launch_export_tiles(const Work& w, int* count, int* list, cudaStream_t st);
+
+// k_mlp_simt.cu (FP32 path)
+size_t mlp_simt_smem(const MlpArgs& a, bool backward);
+cudaError_t launch_mlp_fwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st);
+cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st);
+
+// k_composite.cu
+void launch_composite_fwd(const Work& w, int F, float* rgb, float* trans, float* feat,
+                          cudaStream_t st);
+void launch_composite_bwd(const Work& w, int F, const float* rgb, const float* trans,
+                          const float* feat, const float* d_rgb, const float* d_trans,
+                          const float* d_feat, cudaStream_t st);
+void launch_pose_bwd(const Work& w, float* d_centers, float* d_scales, float* d_quats,
+                     cudaStream_t st);
+
+// k_pack.cu
+void launch_pack_fp32(const Model& m, const Packed& pk, int K, const float* w_fp32, void* out,
+                      cudaStream_t st);
+
+}  // namespace mlps

@@ -1,0 +1,163 @@
+"""Torch-facing wrapper of the CUDA renderer: workspaces, weight packing and autograd.
+
+PyTorch supplies device memory and the stream only; every step of the render runs in
+``libmlps.so`` through :mod:`paper_2606_03877_gb300._lib`.
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Optional, Sequence
+
+import torch
+
+from . import _lib
+
+
+def make_config(shape, precision: str = "fp32", t_eps: float = 1e-6, max_hits: int = 64,
+                hit_capacity: float = 8.0, tile: int = 16) -> _lib.MlpsConfig:
+    """mlps_config from any object with xyz_freqs, dir_freqs, hidden_width, hidden_layers,
+    feat_dim and samples (e.g. :class:`synth.SceneConfig`)."""
+    cfg = _lib.mlps_config_default(int(shape.xyz_freqs), int(shape.dir_freqs), int(shape.hidden_width),
+                                   int(shape.hidden_layers), int(shape.feat_dim))
+    cfg.samples = int(shape.samples)
+    cfg.precision = _lib.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    cfg.t_eps = float(t_eps)
+    cfg.max_hits_per_ray = int(max_hits)
+    cfg.hit_capacity_per_ray = float(hit_capacity)
+    cfg.tile = int(tile)
+    return cfg
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Renderer:
+    """One configuration with reusable saved/scratch workspaces (grown on demand)."""
+
+    def __init__(self, shape, precision: str = "fp32", device: str = "cuda", **kw):
+        self.shape = shape
+        self.precision = precision
+        self.cfg = make_config(shape, precision, **kw)
+        st = _lib.mlps_check_config(self.cfg)
+        if st != _lib.MLPS_OK:
+            raise _lib.MlpsError("mlps_check_config", st)
+        self.device = torch.device(device)
+        self.P = _lib.mlps_param_count(self.cfg)
+        self.stride = _lib.mlps_weight_stride(self.cfg)
+        self.F = int(shape.feat_dim)
+        self.saved: Optional[torch.Tensor] = None
+        self.scratch: Optional[torch.Tensor] = None
+        self._last = None
+
+    # -- weights -------------------------------------------------------------------------
+    def pack(self, weights: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        w = weights.detach().to(self.device, torch.float32).contiguous()
+        K = w.shape[0]
+        assert w.shape[1] == self.P, (w.shape, self.P)
+        if out is None:
+            out = torch.empty(max(K, 1) * self.stride, dtype=torch.uint8, device=self.device)
+        _lib.mlps_pack_weights(self.cfg, K, w, out, _stream())
+        return out
+
+    # -- workspaces ------------------------------------------------------------------------
+    def workspace_bytes(self, K: int, cams: Sequence[dict]):
+        cs = _lib.cameras(cams)
+        return _lib.mlps_workspace_size(self.cfg, K, cs, len(cams))
+
+    def _ensure(self, K: int, cs, V: int):
+        sb, tb = _lib.mlps_workspace_size(self.cfg, K, cs, V)
+        if self.saved is None or self.saved.numel() < sb:
+            self.saved = torch.empty(sb, dtype=torch.uint8, device=self.device)
+        if self.scratch is None or self.scratch.numel() < tb:
+            self.scratch = torch.empty(tb, dtype=torch.uint8, device=self.device)
+
+    # -- passes ----------------------------------------------------------------------------
+    def forward(self, centers, scales, quats, packed, cams: Sequence[dict],
+                out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+        cs = _lib.cameras(cams)
+        V = len(cams)
+        H, W = int(cams[0]["height"]), int(cams[0]["width"])
+        K = int(centers.shape[0])
+        self._ensure(K, cs, V)
+        if out is None:
+            out = {"rgb": torch.empty(V, H, W, 3, device=self.device),
+                   "trans": torch.empty(V, H, W, device=self.device),
+                   "feat": torch.empty(V, H, W, self.F, device=self.device) if self.F else None}
+        scene = _lib.make_scene(K, centers, scales, quats, packed)
+        _lib.mlps_render_forward(self.cfg, scene, cs, V, out["rgb"], out["trans"], out.get("feat"),
+                                 self.saved, self.saved.numel(), self.scratch, self.scratch.numel(),
+                                 _stream())
+        self._last = (scene, cs, V, K, (centers, scales, quats, packed))
+        return out
+
+    def backward(self, d_rgb, d_trans=None, d_feat=None,
+                 out: Optional[Dict[str, torch.Tensor]] = None) -> Dict[str, torch.Tensor]:
+        scene, cs, V, K, _keep = self._last
+        if out is None:
+            out = {"d_weights": torch.empty(K, self.P, device=self.device),
+                   "d_centers": torch.empty(K, 3, device=self.device),
+                   "d_scales": torch.empty(K, 3, device=self.device),
+                   "d_quats": torch.empty(K, 4, device=self.device)}
+        _lib.mlps_render_backward(self.cfg, scene, cs, V, d_rgb.contiguous(),
+                                  None if d_trans is None else d_trans.contiguous(),
+                                  None if d_feat is None else d_feat.contiguous(),
+                                  self.saved, self.saved.numel(), out["d_weights"], out["d_centers"],
+                                  out["d_scales"], out["d_quats"], self.scratch, self.scratch.numel(),
+                                  _stream())
+        return out
+
+    def status(self, region: str = "saved") -> int:
+        t = self.saved if region == "saved" else self.scratch
+        return _lib.mlps_read_status(t, _stream())
+
+    def hit_count(self) -> int:
+        return _lib.mlps_saved_hit_count(self.saved, _stream())
+
+    def hits(self, max_out: int = 64):
+        _, cs, V, K, _ = self._last
+        n_rays = V * cs[0].width * cs[0].height
+        dev = self.device
+        count = torch.empty(n_rays, dtype=torch.int32, device=dev)
+        prim = torch.full((n_rays, max_out), -1, dtype=torch.int32, device=dev)
+        t0 = torch.zeros(n_rays, max_out, device=dev)
+        t1 = torch.zeros(n_rays, max_out, device=dev)
+        tm = torch.zeros(n_rays, max_out, device=dev)
+        _lib.mlps_export_hits(self.cfg, cs, V, self.saved, max_out, count, prim, t0, t1, tm, _stream())
+        return {"count": count, "prim": prim, "t0": t0, "t1": t1, "tmid": tm}
+
+    def tiles(self):
+        _, cs, V, K, _ = self._last
+        t = int(self.cfg.tile)
+        nt = ((cs[0].width + t - 1) // t) * ((cs[0].height + t - 1) // t)
+        count = torch.empty(V * nt, dtype=torch.int32, device=self.device)
+        lst = torch.empty(V * nt * K, dtype=torch.int32, device=self.device)
+        _lib.mlps_export_tiles(self.cfg, K, cs, V, self.scratch, count, lst, _stream())
+        return count, lst.view(V * nt, K)
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, renderer: Renderer, cams, centers, scales, quats, weights):
+        packed = renderer.pack(weights)
+        out = renderer.forward(centers.detach().contiguous(), scales.detach().contiguous(),
+                               quats.detach().contiguous(), packed, cams)
+        ctx.renderer = renderer
+        ctx.keep = packed
+        ctx.mark_non_differentiable(*([] if out["feat"] is None else []))
+        feat = out["feat"] if out["feat"] is not None else torch.empty(0, device=centers.device)
+        return out["rgb"], out["trans"], feat
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_trans, g_feat):
+        r: Renderer = ctx.renderer
+        g = r.backward(g_rgb, g_trans, g_feat if r.F else None)
+        return None, None, g["d_centers"], g["d_scales"], g["d_quats"], g["d_weights"]
+
+
+def render(renderer: Renderer, cams: Sequence[dict], centers: torch.Tensor, scales: torch.Tensor,
+           quats: torch.Tensor, weights: torch.Tensor):
+    """Differentiable render: returns (rgb [V,H,W,3], trans [V,H,W], feat [V,H,W,F] or empty).
+
+    One forward pass per call; the backward pass of the same renderer must follow before the
+    next forward on it (the forward state lives in the renderer's workspace)."""
+    return _RenderFn.apply(renderer, cams, centers, scales, quats, weights)

@@ -1,0 +1,94 @@
+"""CPU-only checks of the C ABI: the library builds, loads and exports every declared symbol,
+and its host-side shape/validation logic agrees with the documented layouts. No CUDA work is
+enqueued here."""
+import os
+import re
+
+import pytest
+
+from paper_2606_03877_gb300 import _lib, build, synth
+from paper_2606_03877_gb300.render import make_config
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = build.build()
+    return _lib.load(path)
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "mlps.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mlps_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.exported_symbols())
+
+
+def test_abi_version_and_status_strings(lib):
+    assert _lib.mlps_abi_version() == 1
+    for s in range(8):
+        assert _lib.mlps_status_string(s)
+    assert _lib.mlps_status_string(4) == "hit capacity overflow"
+
+
+@pytest.mark.parametrize("name", ["pr1", "diff", "prec", "stress"])
+def test_param_count_and_stride(lib, name):
+    c = synth.CONFIGS[name]
+    cfg = make_config(c)
+    assert _lib.mlps_param_count(cfg) == c.n_params
+    assert _lib.mlps_input_dim(cfg) == c.input_dim
+    assert _lib.mlps_weight_stride(cfg) % 256 == 0
+    assert _lib.mlps_weight_stride(cfg) >= 4 * c.n_params
+    sb, tb = _lib.mlps_workspace_size(cfg, c.K, _lib.cameras(synth.make_cameras(c)), c.n_views)
+    assert sb > 0 and tb > 0 and sb % 256 == 0 and tb % 256 == 0
+
+
+def test_config_validation(lib):
+    base = synth.CONFIGS["prec"]
+    bad = [("samples", 0), ("samples", 129), ("max_hits_per_ray", 0), ("max_hits_per_ray", 65),
+           ("hidden_layers", 0), ("feat_dim", 33), ("t_eps", -1.0), ("hit_capacity_per_ray", 0.0),
+           ("precision", 7)]
+    for field, val in bad:
+        cfg = make_config(base)
+        setattr(cfg, field, val)
+        assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_INVALID_ARGUMENT, field
+    cfg = make_config(base)
+    cfg.hidden_width = 48
+    assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_UNSUPPORTED
+    cfg = make_config(base)
+    cfg.reserved[2] = 1
+    assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_INVALID_ARGUMENT
+
+
+def test_camera_validation(lib):
+    c = synth.CONFIGS["prec"]
+    cfg = make_config(c)
+    cams = synth.make_cameras(c.replace(n_views=2))
+    cams[1] = dict(cams[1], width=100)
+    with pytest.raises(_lib.MlpsError) as e:
+        _lib.mlps_workspace_size(cfg, 10, _lib.cameras(cams), 2)
+    assert e.value.status == _lib.MLPS_ERR_UNSUPPORTED
+    cams = synth.make_cameras(c.replace(n_views=1))
+    cams[0] = dict(cams[0], fx=float("nan"))
+    with pytest.raises(_lib.MlpsError):
+        _lib.mlps_workspace_size(cfg, 10, _lib.cameras(cams), 1)
+    with pytest.raises(_lib.MlpsError):
+        _lib.mlps_workspace_size(cfg, 10, _lib.cameras(synth.make_cameras(c.replace(n_views=1))), 65)
+
+
+def test_library_fails_loudly_when_missing(tmp_path):
+    saved = _lib._lib
+    try:
+        _lib._lib = None
+        with pytest.raises(RuntimeError, match="not found"):
+            _lib.load(str(tmp_path / "nope.so"))
+    finally:
+        _lib._lib = saved
