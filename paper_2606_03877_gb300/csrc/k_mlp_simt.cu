@@ -23,26 +23,15 @@
 
 #include "mlps_common.cuh"
 #include "mlps_kernels.h"
+#include "simt_common.cuh"
 
 namespace mlps {
 
-constexpr int kThreads = 256;
-constexpr int kRows = 128;
-
-struct IntervalInfo {
-  int h;
-  float p[3];
-  float r0, dt;
-  float dp[3];
-  float d[3];
-  float tmid, r1;
-};
+using namespace simt;
 
 struct SimtLayout {
   int wfloats, maxdim;
 };
-
-MLPS_HD int round4(int x) { return (x + 3) & ~3; }
 
 static SimtLayout simt_layout(const MlpArgs& a) {
   SimtLayout L;
@@ -65,124 +54,6 @@ size_t mlp_simt_smem(const MlpArgs& a, bool backward) {
     f = (size_t)L.wfloats + acts + 2 * (size_t)kRows * L.maxdim + 8 * kRows;
   }
   return f * sizeof(float) + sizeof(IntervalInfo) * kRows + 64 * sizeof(float);
-}
-
-MLPS_DEV void stage_f4(float* dst, const float* src, int count) {
-  const float4* s = reinterpret_cast<const float4*>(src);
-  float4* d = reinterpret_cast<float4*>(dst);
-  for (int i = threadIdx.x; i < count / 4; i += blockDim.x) d[i] = __ldg(s + i);
-}
-
-// Y[c][r] = act(b[c] + sum_k X[k][r] Wt[k][c]) for dout = 8 * TN columns, 128 rows.
-template <int TN>
-MLPS_DEV void dense_layer(const float* __restrict__ X, int din, const float* __restrict__ Wt,
-                          const float* __restrict__ b, float* __restrict__ Y, bool relu) {
-  constexpr int DOUT = 8 * TN;
-  const int cg = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c0 = cg * TN, r0 = lane * 4;
-  float acc[4][TN];
-#pragma unroll
-  for (int j = 0; j < TN; ++j) {
-    const float bj = b[c0 + j];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i][j] = bj;
-  }
-#pragma unroll 2
-  for (int k = 0; k < din; ++k) {
-    const float4 xv = *reinterpret_cast<const float4*>(&X[k * kRows + r0]);
-    const float xr[4] = {xv.x, xv.y, xv.z, xv.w};
-    float wr[TN];
-#pragma unroll
-    for (int j4 = 0; j4 < TN / 4; ++j4) {
-      const float4 wv = *reinterpret_cast<const float4*>(&Wt[k * DOUT + c0 + 4 * j4]);
-      wr[4 * j4] = wv.x; wr[4 * j4 + 1] = wv.y; wr[4 * j4 + 2] = wv.z; wr[4 * j4 + 3] = wv.w;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(xr[i], wr[j], acc[i][j]);
-  }
-#pragma unroll
-  for (int j = 0; j < TN; ++j) {
-    float4 o = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
-    if (relu) { o.x = fmaxf(o.x, 0.f); o.y = fmaxf(o.y, 0.f); o.z = fmaxf(o.z, 0.f); o.w = fmaxf(o.w, 0.f); }
-    *reinterpret_cast<float4*>(&Y[(c0 + j) * kRows + r0]) = o;
-  }
-}
-
-// Small output layer (dout not a multiple of 8): one dot product per (row, column).
-MLPS_DEV void dense_small(const float* __restrict__ X, int din, const float* __restrict__ Wt,
-                          const float* __restrict__ b, int dout, float* __restrict__ Y) {
-  for (int i = threadIdx.x; i < kRows * dout; i += blockDim.x) {
-    const int r = i % kRows, o = i / kRows;
-    float acc = b[o];
-    for (int k = 0; k < din; ++k) acc = fmaf(X[k * kRows + r], Wt[k * dout + o], acc);
-    Y[o * kRows + r] = acc;
-  }
-}
-
-template <int TN>
-MLPS_DEV void run_layer(const Model& m, int l, const float* X, const float* Wt, const float* b,
-                        float* Y) {
-  if (l < m.nl - 1) dense_layer<TN>(X, m.din[l], Wt, b, Y, true);
-  else dense_small(X, m.din[l], Wt, b, m.dout[l], Y);
-}
-
-// Encoding gamma (Eq. 5) of one sample into column `row` of X ([feature][kRows]).
-MLPS_DEV void encode_row(const Model& m, const float xl[3], const float d[3], float* X, int row) {
-  int f = 0;
-  if (m.xyzL == 0) {
-    for (int c = 0; c < 3; ++c) X[(f++) * kRows + row] = xl[c];
-  } else {
-    for (int c = 0; c < 3; ++c)
-      for (int l = 0; l < m.xyzL; ++l) {
-        float s, co;
-        sincospif(ldexpf(xl[c], l), &s, &co);
-        X[(f++) * kRows + row] = s;
-        X[(f++) * kRows + row] = co;
-      }
-  }
-  if (m.dirL > 0)
-    for (int c = 0; c < 3; ++c)
-      for (int l = 0; l < m.dirL; ++l) {
-        float s, co;
-        sincospif(ldexpf(d[c], l), &s, &co);
-        X[(f++) * kRows + row] = s;
-        X[(f++) * kRows + row] = co;
-      }
-}
-
-MLPS_DEV float sigmoidf_acc(float z) { return 1.0f / (1.0f + expf(-z)); }
-MLPS_DEV float softplusf_acc(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
-
-// Fill the chunk's interval table (one thread per interval).
-MLPS_DEV void load_interval(const Work& w, const Model& m, int prim, int h, IntervalInfo& I) {
-  const int ray = w.hit_ray[h];
-  const int hw = w.H * w.W;
-  const int v = ray / hw, pix = ray - v * hw;
-  const int y = pix / w.W, x = pix - y * w.W;
-  float d[3];
-  ray_dir_f(w.views[v], x, y, d);
-  const PrimGeo& g = w.geo[prim];
-  I.h = h;
-  for (int i = 0; i < 3; ++i) {
-    I.d[i] = d[i];
-    I.dp[i] = g.Mhi[i * 3] * d[0] + g.Mhi[i * 3 + 1] * d[1] + g.Mhi[i * 3 + 2] * d[2];
-    I.p[i] = w.hit_p[(size_t)i * w.hit_cap + h];
-  }
-  I.tmid = w.hit_tmid[h];
-  I.r0 = w.hit_r0[h];
-  I.r1 = w.hit_r1[h];
-  I.dt = (I.r1 - I.r0) / (float)m.S;
-}
-
-MLPS_DEV int find_prim(const Work& w, int c) {
-  int lo = 0, hi = w.K - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (w.chunk_start[mid] <= c) lo = mid; else hi = mid - 1;
-  }
-  return lo;
 }
 
 // ------------------------------------------------------------------------------------------

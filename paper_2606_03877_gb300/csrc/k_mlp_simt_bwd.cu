@@ -1,0 +1,596 @@
+// k_mlp_simt_bwd.cu -- FP32 backward of the grouped per-primitive MLP stage.
+//
+// For every chunk of hit intervals of one primitive (64 sample rows per sub-chunk):
+//  1. recompute the forward (encoding, layers) and keep every layer's input in shared memory;
+//  2. reverse the interval composite of Eq. 6 with a warp per interval: given the interval's
+//     dL/dC_j and dL/da_j from the per-ray reverse pass, with tau_k the transmittance inside
+//     the interval, w_k = tau_k alpha_k and R_k = sum_{m>k} w_m c_m,
+//       dL/dc_k = w_k dL/dC_j,
+//       dL/da_k = dL/dC_j . (tau_k e^{-a_k} c_k - R_k) + dL/da_j,   a_k = sigma_k Delta
+//     (features likewise), then through sigmoid / softplus;
+//  3. back-propagate through the layers: dgrad (register-tiled FP32 FMA, ReLU masks from the
+//     stored activations) and wgrad (each thread owns up to four 4x4 weight-gradient tiles in
+//     registers for the whole primitive segment; flushed with one atomicAdd per entry when the
+//     block moves to another primitive);
+//  4. chain dL/dx'_k (through the encoding derivative) to the primitive pose. With
+//     y_k = R S x'_k the sample's offset from the centre, the closest point p, a = |d'|^2 and
+//     h the half chord in t:
+//       dL/dM  = sum_k g_k y_k^T + g_o' y_mid^T - (g_tm p / a + g_h h d' / a) d^T,
+//       dL/dmu = -M^T (sum_k g_k + g_o'),      g_o' = -g_tm d' / a - g_h p / (a h),
+//     where g_tm, g_h are the gradients on t_mid and h collected from t_k = t0 + (k + 1/2) Delta
+//     and Delta = (t1 - t0) / S. This form has no cancellation between the ~3-unit camera
+//     distances; it is the same derivative as the one written with o' and d'.
+#include <cuda_runtime.h>
+
+#include "mlps_common.cuh"
+#include "mlps_kernels.h"
+#include "simt_common.cuh"
+
+namespace mlps {
+
+using namespace simt;
+
+namespace {
+
+constexpr int kRB = 64;          // sample rows per sub-chunk
+constexpr int kRS = kRB + 4;     // row stride of [feature][row] buffers (bank spread)
+constexpr int kMaxTiles = 4;     // 4x4 weight-gradient tiles per thread
+constexpr int kMaxBias = 3;
+
+struct BwdPlan {
+  int wt_floats;                 // packed W^T + b (resident)
+  int wc_off[kMaxLayers];        // canonical W [dout][din] per layer in shared memory
+  int wc_floats;
+  int act_off[kMaxLayers];       // input of layer l: [din_pad][kRS]
+  int din_pad[kMaxLayers], dout_pad[kMaxLayers];
+  int act_floats;
+  int gbuf;                      // one gradient buffer [maxpad][kRS]
+  int nxyz;                      // encoded local-position features
+  int tiles;                     // total 4x4 tiles over all layers
+  int tile_base[kMaxLayers + 1];
+  int ni[kMaxLayers];            // input tiles per layer (ceil(din / 4))
+  int bias_base[kMaxLayers + 1];
+};
+
+BwdPlan make_plan(const MlpArgs& a) {
+  BwdPlan P;
+  const Model& m = a.m;
+  P.wt_floats = a.pk.boff[m.nl - 1] + round4(m.dout[m.nl - 1]);
+  int off = 0, act = 0, maxpad = 0, tiles = 0, bias = 0;
+  for (int l = 0; l < m.nl; ++l) {
+    P.wc_off[l] = off;
+    off += round4(m.din[l] * m.dout[l]);
+    P.din_pad[l] = round4(m.din[l]);
+    P.dout_pad[l] = round4(m.dout[l]);
+    P.act_off[l] = act;
+    act += P.din_pad[l] * kRS;
+    maxpad = max(maxpad, max(P.din_pad[l], P.dout_pad[l]));
+    P.tile_base[l] = tiles;
+    P.ni[l] = P.din_pad[l] / 4;
+    tiles += (P.dout_pad[l] / 4) * P.ni[l];
+    P.bias_base[l] = bias;
+    bias += m.dout[l];
+  }
+  P.tile_base[m.nl] = tiles;
+  P.bias_base[m.nl] = bias;
+  P.wc_floats = off;
+  P.act_floats = act;
+  P.gbuf = maxpad * kRS;
+  P.nxyz = m.xyzL > 0 ? 6 * m.xyzL : 3;
+  P.tiles = tiles;
+  return P;
+}
+
+size_t bwd_smem(const MlpArgs& a, const BwdPlan& P) {
+  const Model& m = a.m;
+  size_t f = (size_t)P.wt_floats + P.wc_floats + P.act_floats + 3 * (size_t)P.gbuf;
+  f += 16;  // geometry accumulators
+  const int ipcb = kRB / m.S;
+  size_t bytes = f * sizeof(float) + (size_t)ipcb * (sizeof(IntervalInfo) + sizeof(float4)) +
+                 (size_t)ipcb * m.F * sizeof(float) + 64;
+  return bytes;
+}
+
+// Y[c][r] = act(b[c] + sum_k X[k][r] Wt[k][c]), dout = 8 * TN, 64 rows (2 per lane).
+template <int TN>
+MLPS_DEV void fwd_layer(const float* __restrict__ X, int din, const float* __restrict__ Wt,
+                        const float* __restrict__ b, float* __restrict__ Y, bool relu) {
+  constexpr int DOUT = 8 * TN;
+  const int cg = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = cg * TN, r0 = lane * 2;
+  float acc[2][TN];
+#pragma unroll
+  for (int j = 0; j < TN; ++j) { acc[0][j] = b[c0 + j]; acc[1][j] = b[c0 + j]; }
+#pragma unroll 2
+  for (int k = 0; k < din; ++k) {
+    const float2 xv = *reinterpret_cast<const float2*>(&X[k * kRS + r0]);
+    float wr[TN];
+#pragma unroll
+    for (int j4 = 0; j4 < TN / 4; ++j4) {
+      const float4 wv = *reinterpret_cast<const float4*>(&Wt[k * DOUT + c0 + 4 * j4]);
+      wr[4 * j4] = wv.x; wr[4 * j4 + 1] = wv.y; wr[4 * j4 + 2] = wv.z; wr[4 * j4 + 3] = wv.w;
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      acc[0][j] = fmaf(xv.x, wr[j], acc[0][j]);
+      acc[1][j] = fmaf(xv.y, wr[j], acc[1][j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    float2 o = make_float2(acc[0][j], acc[1][j]);
+    if (relu) { o.x = fmaxf(o.x, 0.f); o.y = fmaxf(o.y, 0.f); }
+    *reinterpret_cast<float2*>(&Y[(c0 + j) * kRS + r0]) = o;
+  }
+}
+
+MLPS_DEV void fwd_small(const float* __restrict__ X, int din, const float* __restrict__ Wt,
+                        const float* __restrict__ b, int dout, float* __restrict__ Y) {
+  for (int i = threadIdx.x; i < kRB * dout; i += blockDim.x) {
+    const int r = i % kRB, o = i / kRB;
+    float acc = b[o];
+    for (int k = 0; k < din; ++k) acc = fmaf(X[k * kRS + r], Wt[k * dout + o], acc);
+    Y[o * kRS + r] = acc;
+  }
+}
+
+// G[i][r] = sum_o Wc[o][i] D[o][r], masked by act[i][r] > 0; din = 8 * TN.
+template <int TN>
+MLPS_DEV void dgrad_layer(const float* __restrict__ D, int dout, const float* __restrict__ Wc,
+                          const float* __restrict__ act, float* __restrict__ G) {
+  constexpr int DIN = 8 * TN;
+  const int cg = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = cg * TN, r0 = lane * 2;
+  float acc[2][TN];
+#pragma unroll
+  for (int j = 0; j < TN; ++j) { acc[0][j] = 0.f; acc[1][j] = 0.f; }
+#pragma unroll 2
+  for (int o = 0; o < dout; ++o) {
+    const float2 dv = *reinterpret_cast<const float2*>(&D[o * kRS + r0]);
+    float wr[TN];
+#pragma unroll
+    for (int j4 = 0; j4 < TN / 4; ++j4) {
+      const float4 wv = *reinterpret_cast<const float4*>(&Wc[o * DIN + c0 + 4 * j4]);
+      wr[4 * j4] = wv.x; wr[4 * j4 + 1] = wv.y; wr[4 * j4 + 2] = wv.z; wr[4 * j4 + 3] = wv.w;
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      acc[0][j] = fmaf(dv.x, wr[j], acc[0][j]);
+      acc[1][j] = fmaf(dv.y, wr[j], acc[1][j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const float2 av = *reinterpret_cast<const float2*>(&act[(c0 + j) * kRS + r0]);
+    float2 o = make_float2(av.x > 0.f ? acc[0][j] : 0.f, av.y > 0.f ? acc[1][j] : 0.f);
+    *reinterpret_cast<float2*>(&G[(c0 + j) * kRS + r0]) = o;
+  }
+}
+
+// First-layer input gradient, local-position part only: G[f][r] for f < nx.
+MLPS_DEV void dgrad_input(const float* __restrict__ D, int dout, const float* __restrict__ Wc,
+                          int din, int nx, float* __restrict__ G) {
+  for (int i = threadIdx.x; i < kRB * nx; i += blockDim.x) {
+    const int r = i % kRB, f = i / kRB;
+    float acc = 0.f;
+    for (int o = 0; o < dout; ++o) acc = fmaf(D[o * kRS + r], Wc[o * din + f], acc);
+    G[f * kRS + r] = acc;
+  }
+}
+
+MLPS_DEV float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+MLPS_DEV float warp_excl_scan(float v, int lane) {
+  float incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  return incl - v;
+}
+
+MLPS_DEV float warp_excl_suffix(float v, int lane) {  // sum over higher lanes
+  float incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float u = __shfl_down_sync(0xffffffffu, incl, o);
+    if (lane + o < 32) incl += u;
+  }
+  return incl - v;
+}
+
+}  // namespace
+
+template <int TN>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a, BwdPlan P) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const Model& m = a.m;
+  const int S = m.S, F = m.F, nl = m.nl;
+  const int ipcb = kRB / S;
+  float* sWt = smem;
+  float* sWc = sWt + P.wt_floats;
+  float* sAct = sWc + P.wc_floats;
+  float* sG0 = sAct + P.act_floats;
+  float* sG1 = sG0 + P.gbuf;
+  float* sZ = sG1 + P.gbuf;
+  float* sGeo = sZ + P.gbuf;  // [0..8] dM, [9..11] dmu
+  float4* sGrad = reinterpret_cast<float4*>(sGeo + 16);
+  IntervalInfo* sI = reinterpret_cast<IntervalInfo*>(sGrad + ipcb);
+  float* sGF = reinterpret_cast<float*>(sI + ipcb);
+
+  const int total = w.saved_hdr[2];
+  const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
+  const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
+  if (cb >= ce) return;
+
+  // this thread's weight-gradient tiles
+  int t_layer[kMaxTiles], t_o0[kMaxTiles], t_it[kMaxTiles];
+  float acc[kMaxTiles][16];
+  float bacc[kMaxBias];
+  int nt = 0;
+  for (int t = threadIdx.x; t < P.tiles && nt < kMaxTiles; t += kThreads, ++nt) {
+    int l = 0;
+    while (t >= P.tile_base[l + 1]) ++l;
+    const int loc = t - P.tile_base[l];
+    t_layer[nt] = l;
+    t_o0[nt] = (loc / P.ni[l]) * 4;
+    t_it[nt] = loc % P.ni[l];
+  }
+  auto zero_acc = [&]() {
+#pragma unroll
+    for (int j = 0; j < kMaxTiles; ++j)
+#pragma unroll
+      for (int e = 0; e < 16; ++e) acc[j][e] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kMaxBias; ++j) bacc[j] = 0.f;
+  };
+  zero_acc();
+  if (threadIdx.x < 16) sGeo[threadIdx.x] = 0.f;
+
+  const float* wbase = reinterpret_cast<const float*>(a.weights);
+  const int wstride = (int)(a.pk.stride / 4);
+  int prim = find_prim(w, cb);
+  int loaded = -1;
+
+  auto flush = [&](int p) {
+    float* dW = a.d_weights + (size_t)p * m.P;
+#pragma unroll
+    for (int j = 0; j < kMaxTiles; ++j) {
+      if (j >= nt) break;
+      const int l = t_layer[j], din = m.din[l], dout = m.dout[l], ni = P.ni[l];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int o = t_o0[j] + (e >> 2), i = t_it[j] + ni * (e & 3);
+        if (o < dout && i < din && acc[j][e] != 0.f) atomicAdd(&dW[m.woff[l] + o * din + i], acc[j][e]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxBias; ++j) {
+      const int bi = threadIdx.x + j * kThreads;
+      if (bi < P.bias_base[nl] && bacc[j] != 0.f) {
+        int l = 0;
+        while (bi >= P.bias_base[l + 1]) ++l;
+        atomicAdd(&dW[m.boff[l] + (bi - P.bias_base[l])], bacc[j]);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+      const float v = sGeo[threadIdx.x];
+      if (v != 0.f) atomicAdd(&w.dgeo[12 * (size_t)p + threadIdx.x], v);
+      sGeo[threadIdx.x] = 0.f;
+    }
+    zero_acc();
+  };
+
+  for (int c = cb; c < ce; ++c) {
+    while (c >= w.chunk_start[prim + 1]) ++prim;
+    const int first = (c - w.chunk_start[prim]) * w.ipc;
+    const int nint_c = min(w.ipc, w.prim_count[prim] - first);
+    if (prim != loaded) {
+      if (loaded >= 0) flush(loaded);
+      __syncthreads();
+      // W^T blocks (forward) and canonical W (dgrad)
+      stage_f4(sWt, wbase + (size_t)prim * wstride, P.wt_floats);
+      const float* src = wbase + (size_t)prim * wstride;
+      for (int l = 0; l < nl; ++l) {
+        const int din = m.din[l], dout = m.dout[l];
+        for (int i = threadIdx.x; i < din * dout; i += kThreads) {
+          const int o = i / din, k = i - o * din;
+          sWc[P.wc_off[l] + i] = src[a.pk.woff[l] + k * dout + o];
+        }
+      }
+      // zero padded activation rows once (rows din..din_pad of every layer input)
+      for (int l = 0; l < nl; ++l)
+        for (int i = threadIdx.x; i < (P.din_pad[l] - m.din[l]) * kRS; i += kThreads)
+          sAct[P.act_off[l] + m.din[l] * kRS + i] = 0.f;
+      loaded = prim;
+    }
+    const PrimGeo& G = w.geo[prim];
+    for (int sub = 0; sub * ipcb < nint_c; ++sub) {
+      const int i0 = sub * ipcb;
+      const int nint = min(ipcb, nint_c - i0);
+      __syncthreads();
+      if (threadIdx.x < nint) {
+        const int h = w.prim_list[w.prim_start[prim] + first + i0 + threadIdx.x];
+        load_interval(w, m, prim, h, sI[threadIdx.x]);
+        sGrad[threadIdx.x] = w.hit_grad[h];
+        for (int f = 0; f < F; ++f) sGF[threadIdx.x * F + f] = w.hit_gfeat[(size_t)h * F + f];
+      }
+      __syncthreads();
+      // 1. encode the samples into the input of layer 0
+      float* X0 = sAct + P.act_off[0];
+      if (threadIdx.x < kRB) {
+        const int row = threadIdx.x, i = row / S, k = row - i * S;
+        if (i < nint) {
+          const IntervalInfo& I = sI[i];
+          const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+          float xl[3];
+          for (int q = 0; q < 3; ++q) xl[q] = fmaf(tr, I.dp[q], I.p[q]);
+          // encode_row writes with stride kRows; write through a local copy instead
+          int f = 0;
+          if (m.xyzL == 0) {
+            for (int q = 0; q < 3; ++q) X0[(f++) * kRS + row] = xl[q];
+          } else {
+            for (int q = 0; q < 3; ++q)
+              for (int l = 0; l < m.xyzL; ++l) {
+                float s_, c_;
+                sincospif(ldexpf(xl[q], l), &s_, &c_);
+                X0[(f++) * kRS + row] = s_;
+                X0[(f++) * kRS + row] = c_;
+              }
+          }
+          if (m.dirL > 0)
+            for (int q = 0; q < 3; ++q)
+              for (int l = 0; l < m.dirL; ++l) {
+                float s_, c_;
+                sincospif(ldexpf(I.d[q], l), &s_, &c_);
+                X0[(f++) * kRS + row] = s_;
+                X0[(f++) * kRS + row] = c_;
+              }
+        } else {
+          for (int f = 0; f < m.nin; ++f) X0[f * kRS + row] = 0.f;
+        }
+      }
+      __syncthreads();
+      // 2. forward recompute, keeping every layer's input
+      for (int l = 0; l < nl; ++l) {
+        const float* Xl = sAct + P.act_off[l];
+        const float* Wt = sWt + a.pk.woff[l];
+        const float* bb = sWt + a.pk.boff[l];
+        if (l < nl - 1) fwd_layer<TN>(Xl, m.din[l], Wt, bb, sAct + P.act_off[l + 1], true);
+        else fwd_small(Xl, m.din[l], Wt, bb, m.dout[l], sZ);
+        __syncthreads();
+      }
+      // 3. reverse of the interval composite: warp per interval -> dZ in sG0
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int i = warp; i < nint; i += kThreads / 32) {
+        const IntervalInfo& I = sI[i];
+        const float4 g = sGrad[i];
+        const float* gF = sGF + i * F;
+        const int PL = (S + 31) / 32;
+        const int k0 = min(S, lane * PL), k1 = min(S, k0 + PL);
+        const int rb = i * S;
+        float aloc = 0.f;
+        for (int k = k0; k < k1; ++k) aloc += softplusf_acc(sZ[3 * kRS + rb + k]) * I.dt;
+        const float A0 = warp_excl_scan(aloc, lane);
+        // lane totals of w c and w f for the suffix sums
+        float wc[3] = {0.f, 0.f, 0.f};
+        float A = A0;
+        for (int k = k0; k < k1; ++k) {
+          const float ak = softplusf_acc(sZ[3 * kRS + rb + k]) * I.dt;
+          const float wk = expf(-A) * -expm1f(-ak);
+          for (int q = 0; q < 3; ++q) wc[q] = fmaf(wk, sigmoidf_acc(sZ[q * kRS + rb + k]), wc[q]);
+          A += ak;
+        }
+        float R[3];
+        for (int q = 0; q < 3; ++q) R[q] = warp_excl_suffix(wc[q], lane);
+        // feature suffix sums (one scan per feature)
+        float RFl[kMaxFeat];
+        for (int f = 0; f < F; ++f) {
+          float v = 0.f;
+          float A2 = A0;
+          for (int k = k0; k < k1; ++k) {
+            const float ak = softplusf_acc(sZ[3 * kRS + rb + k]) * I.dt;
+            v = fmaf(expf(-A2) * -expm1f(-ak), sZ[(4 + f) * kRS + rb + k], v);
+            A2 += ak;
+          }
+          RFl[f] = warp_excl_suffix(v, lane);
+        }
+        // backward over the lane's samples
+        float dDelta = 0.f;
+        float Aend = A;  // exclusive prefix after the lane's last sample
+        for (int k = k1 - 1; k >= k0; --k) {
+          const float zs = sZ[3 * kRS + rb + k];
+          const float sig = softplusf_acc(zs);
+          const float ak = sig * I.dt;
+          const float Aex = Aend - ak;
+          const float tau = expf(-Aex);
+          const float ea = expf(-ak);
+          const float wk = tau * -expm1f(-ak);
+          float cq[3];
+          for (int q = 0; q < 3; ++q) cq[q] = sigmoidf_acc(sZ[q * kRS + rb + k]);
+          float ga = g.w;
+          ga += g.x * (tau * ea * cq[0] - R[0]) + g.y * (tau * ea * cq[1] - R[1]) +
+                g.z * (tau * ea * cq[2] - R[2]);
+          for (int f = 0; f < F; ++f) {
+            const float fk = sZ[(4 + f) * kRS + rb + k];
+            ga += gF[f] * (tau * ea * fk - RFl[f]);
+            RFl[f] = fmaf(wk, fk, RFl[f]);
+            sG0[(4 + f) * kRS + rb + k] = wk * gF[f];
+          }
+          const float gcs[3] = {g.x, g.y, g.z};
+          for (int q = 0; q < 3; ++q) {
+            sG0[q * kRS + rb + k] = wk * gcs[q] * cq[q] * (1.f - cq[q]);
+            R[q] = fmaf(wk, cq[q], R[q]);
+          }
+          sG0[3 * kRS + rb + k] = ga * I.dt * sigmoidf_acc(zs);
+          dDelta = fmaf(ga, sig, dDelta);
+          Aend = Aex;
+        }
+        dDelta = warp_sum(dDelta);
+        if (lane == 0) sGrad[i].w = dDelta;  // from here on: dL/dDelta of the interval
+      }
+      // rows beyond the valid intervals carry zero gradient
+      for (int i = threadIdx.x; i < m.nout * kRB; i += kThreads) {
+        const int r = i % kRB, o = i / kRB;
+        if (r >= nint * S) sG0[o * kRS + r] = 0.f;
+      }
+      for (int i = threadIdx.x; i < (P.dout_pad[nl - 1] - m.nout) * kRB; i += kThreads) {
+        const int r = i % kRB, o = m.nout + i / kRB;
+        sG0[o * kRS + r] = 0.f;
+      }
+      __syncthreads();
+      // 4. layers, last to first: wgrad (+ bias) then dgrad
+      float* D = sG0;
+      float* Gn = sG1;
+      for (int l = nl - 1; l >= 0; --l) {
+        const float* Al = sAct + P.act_off[l];
+#pragma unroll
+        for (int j = 0; j < kMaxTiles; ++j) {
+          if (j >= nt || t_layer[j] != l) continue;
+          const int o0 = t_o0[j], it = t_it[j], ni = P.ni[l];
+          for (int r = 0; r < kRB; r += 4) {
+            float4 dv[4], av[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              dv[u] = *reinterpret_cast<const float4*>(&D[(o0 + u) * kRS + r]);
+              av[u] = *reinterpret_cast<const float4*>(&Al[(it + ni * u) * kRS + r]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                float s_ = acc[j][u * 4 + v];
+                s_ = fmaf(dv[u].x, av[v].x, s_);
+                s_ = fmaf(dv[u].y, av[v].y, s_);
+                s_ = fmaf(dv[u].z, av[v].z, s_);
+                s_ = fmaf(dv[u].w, av[v].w, s_);
+                acc[j][u * 4 + v] = s_;
+              }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kMaxBias; ++j) {
+          const int bi = threadIdx.x + j * kThreads - P.bias_base[l];
+          if (bi >= 0 && bi < m.dout[l]) {
+            float s_ = 0.f;
+            for (int r = 0; r < kRB; ++r) s_ += D[bi * kRS + r];
+            bacc[j] += s_;
+          }
+        }
+        if (l > 0) {
+          dgrad_layer<TN>(D, m.dout[l], sWc + P.wc_off[l], Al, Gn);
+        } else {
+          dgrad_input(D, m.dout[0], sWc + P.wc_off[0], m.din[0], P.nxyz, Gn);
+        }
+        __syncthreads();
+        float* t = D; D = Gn; Gn = t;
+      }
+      // D now holds dL/d(encoded local position) rows [0, nxyz)
+      // 5. encoding derivative and pose chain: warp per interval
+      for (int i = warp; i < nint; i += kThreads / 32) {
+        const IntervalInfo& I = sI[i];
+        const int rb = i * S;
+        float sg[3] = {0.f, 0.f, 0.f}, gy[9], gt0 = 0.f, gt1 = 0.f;
+        for (int e = 0; e < 9; ++e) gy[e] = 0.f;
+        for (int k = lane; k < S; k += 32) {
+          const float u = ((float)k + 0.5f) / (float)S;
+          const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+          float xl[3], gx[3] = {0.f, 0.f, 0.f};
+          for (int q = 0; q < 3; ++q) xl[q] = fmaf(tr, I.dp[q], I.p[q]);
+          if (m.xyzL == 0) {
+            for (int q = 0; q < 3; ++q) gx[q] = D[q * kRS + rb + k];
+          } else {
+            int f = 0;
+            for (int q = 0; q < 3; ++q)
+              for (int l = 0; l < m.xyzL; ++l) {
+                float s_, c_;
+                sincospif(ldexpf(xl[q], l), &s_, &c_);
+                const float wq = 3.14159265358979f * ldexpf(1.f, l);
+                gx[q] += wq * (D[f * kRS + rb + k] * c_ - D[(f + 1) * kRS + rb + k] * s_);
+                f += 2;
+              }
+          }
+          // y = R S x' (offset of the sample from the centre, world frame)
+          float y[3];
+          for (int q = 0; q < 3; ++q)
+            y[q] = G.R[q * 3] * G.s[0] * xl[0] + G.R[q * 3 + 1] * G.s[1] * xl[1] + G.R[q * 3 + 2] * G.s[2] * xl[2];
+          const float gt = gx[0] * I.dp[0] + gx[1] * I.dp[1] + gx[2] * I.dp[2];
+          gt0 = fmaf(gt, 1.f - u, gt0);
+          gt1 = fmaf(gt, u, gt1);
+          for (int q = 0; q < 3; ++q) {
+            sg[q] += gx[q];
+            for (int e = 0; e < 3; ++e) gy[q * 3 + e] = fmaf(gx[q], y[e], gy[q * 3 + e]);
+          }
+        }
+        for (int q = 0; q < 3; ++q) sg[q] = warp_sum(sg[q]);
+        for (int e = 0; e < 9; ++e) gy[e] = warp_sum(gy[e]);
+        gt0 = warp_sum(gt0);
+        gt1 = warp_sum(gt1);
+        if (lane == 0) {
+          const float dDelta = sGrad[i].w;
+          gt1 += dDelta / (float)S;
+          gt0 -= dDelta / (float)S;
+          const bool clamped = I.r0 != -I.r1;
+          const float gtm = gt1 + (clamped ? 0.f : gt0);
+          const float gh = gt1 - (clamped ? 0.f : gt0);
+          const float aa = I.dp[0] * I.dp[0] + I.dp[1] * I.dp[1] + I.dp[2] * I.dp[2];
+          const float hh = I.r1;
+          float go[3], ymid[3], cd[3];
+          for (int q = 0; q < 3; ++q) {
+            go[q] = -gtm * I.dp[q] / aa - (hh > 0.f ? gh * I.p[q] / (aa * hh) : 0.f);
+            cd[q] = -(gtm * I.p[q] / aa + gh * hh * I.dp[q] / aa);
+          }
+          for (int q = 0; q < 3; ++q)
+            ymid[q] = G.R[q * 3] * G.s[0] * I.p[0] + G.R[q * 3 + 1] * G.s[1] * I.p[1] + G.R[q * 3 + 2] * G.s[2] * I.p[2];
+          for (int q = 0; q < 3; ++q)
+            for (int e = 0; e < 3; ++e)
+              atomicAdd(&sGeo[q * 3 + e], gy[q * 3 + e] + go[q] * ymid[e] + cd[q] * I.d[e]);
+          // dmu = -M^T (sum g + g_o')
+          for (int e = 0; e < 3; ++e) {
+            float acc2 = 0.f;
+            for (int q = 0; q < 3; ++q) acc2 += G.Mhi[q * 3 + e] * (sg[q] + go[q]);
+            atomicAdd(&sGeo[9 + e], -acc2);
+          }
+        }
+      }
+    }
+  }
+  if (loaded >= 0) flush(loaded);
+}
+
+cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st) {
+  const Model& m = a.m;
+  if (m.S > kRB || m.width > 64) return cudaErrorNotSupported;
+  BwdPlan P = make_plan(a);
+  if (P.tiles > kMaxTiles * kThreads || P.bias_base[m.nl] > kMaxBias * kThreads)
+    return cudaErrorNotSupported;
+  for (int l = 0; l < m.nl; ++l)
+    if (m.dout[l] % 4 != 0 && l < m.nl - 1) return cudaErrorNotSupported;
+  const size_t smem = bwd_smem(a, P);
+  if (smem > 227 * 1024) return cudaErrorNotSupported;
+  switch (m.width) {
+#define MLPS_CASE(WID)                                                                      \
+  case WID: {                                                                               \
+    auto kern = k_mlp_bwd_simt<WID / 8>;                                                    \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)smem);                                        \
+    if (e != cudaSuccess) return e;                                                         \
+    kern<<<n_sm, kThreads, smem, st>>>(w, a, P);                                            \
+    return cudaGetLastError();                                                              \
+  }
+    MLPS_CASE(32)
+    MLPS_CASE(64)
+#undef MLPS_CASE
+    default:
+      return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace mlps
