@@ -49,6 +49,9 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--width", type=int, default=0, help="override (profiling captures only)")
+    ap.add_argument("--height", type=int, default=0, help="override (profiling captures only)")
+    ap.add_argument("--views", type=int, default=0, help="override (profiling captures only)")
     ap.add_argument("--compare", action="store_true",
                     help="also time the FP32 path and forward-only passes (extra lines in 'results')")
     return ap.parse_args()
@@ -119,6 +122,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _workload(a):
+    from paper_2606_03877_gb300 import synth
+    wl = synth.CONFIGS[a.workload]
+    kw = {}
+    if a.width:
+        kw["width"] = a.width
+    if a.height:
+        kw["height"] = a.height
+    if a.views:
+        kw["n_views"] = a.views
+    return wl.replace(**kw) if kw else wl
+
+
 def _flush_l2(buf):
     buf.add_(1.0)  # writes 256 MiB (> 129 MB L2) between timed steps
 
@@ -135,7 +151,7 @@ def run_ours(a):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = synth.CONFIGS[a.workload]
+    wl = _workload(a)
     scene = synth.make_scene(wl, 0)
     cams = synth.make_cameras(wl, first_view_seed=rank * wl.n_views)
     d = {k: torch.from_numpy(v).to(dev) for k, v in scene.items()}
