@@ -169,9 +169,4 @@ cudaError_t launch_mlp_fwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaS
   }
 }
 
-cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st) {
-  (void)w; (void)a; (void)n_sm; (void)st;
-  return cudaErrorNotSupported;
-}
-
 }  // namespace mlps
