@@ -1,0 +1,497 @@
+// k_mlp_tc.cu -- grouped per-primitive MLP on the 5th-generation tensor cores (tcgen05), BF16
+// operands with FP32 accumulation in tensor memory (TMEM).
+//
+// Same work decomposition as the FP32 path: a chunk is up to ipc = 128 / S hit intervals of one
+// primitive, i.e. one M = 128 tile of sample rows; persistent blocks walk a contiguous range
+// of the primitive-major chunk list. Inside a block:
+//  * warp 8 (one elected lane) loads the primitive's weight tiles with TMA tensor copies
+//    (cp.async.bulk.tensor, 128-byte swizzle) into shared memory whenever the primitive
+//    changes, and issues every tcgen05.mma;
+//  * two epilogue warpgroups (warps 0-3 and 4-7) each own one chunk at a time, its A-operand
+//    tile in shared memory and 128 TMEM columns. A group builds the sample encodings (Eq. 5)
+//    as BF16 rows of the first A tile, then, after each layer's MMAs complete, reads its
+//    accumulator rows from TMEM (thread = sample row), adds the bias, applies ReLU, converts to
+//    BF16 and writes the next layer's A tile in place. While one group runs its epilogue the
+//    tensor core works on the other group's layer.
+//  * the last layer's epilogue applies sigmoid / softplus and composites each interval's S
+//    samples front to back (Eq. 6) with warp-level segmented scans, writing the interval's
+//    (C_j, a_j) exactly like the FP32 path.
+// Every wait is bounded by wall time; on a timeout the block raises an abort flag, finishes its
+// loops without work, waits (bounded) for its MMAs in flight, frees TMEM and reports
+// MLPS_ERR_TIMEOUT through the status word.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "mlps_common.cuh"
+#include "mlps_kernels.h"
+#include "simt_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace mlps {
+namespace tc {
+
+using simt::IntervalInfo;
+
+constexpr int kM = 128;
+constexpr int kNEG = 2;                         // epilogue groups = chunks in flight
+constexpr int kEGThreads = 128;
+constexpr int kThreadsTC = kEGThreads * kNEG + 32;
+constexpr int kMmaWarp = kNEG * 4;
+constexpr uint32_t kTmemCols = 256;             // 128 per group
+constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s
+constexpr int kMaxScanVals = 4 + kMaxFeat;
+
+struct TcSmem {
+  uint32_t w, a[kNEG], bias, itab[kNEG], scan, bars, misc, total;
+};
+
+MLPS_HD uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+MLPS_HD TcSmem tc_smem(const TcPlan& P) {
+  TcSmem L;
+  uint32_t off = 0;
+  L.w = off;
+  off = align_up(off + P.w_bytes, 1024);
+  for (int g = 0; g < kNEG; ++g) {
+    L.a[g] = off;
+    off = align_up(off + P.a_bytes, 1024);
+  }
+  L.bias = off;
+  off = align_up(off + 4 * P.bias_floats, 16);
+  for (int g = 0; g < kNEG; ++g) {
+    L.itab[g] = off;
+    off = align_up(off + (uint32_t)sizeof(IntervalInfo) * kM, 16);
+  }
+  L.scan = off;
+  off = align_up(off + 4 * kNEG * 4 * kMaxScanVals, 16);
+  L.bars = off;
+  off = align_up(off + 8 * (2 + 2 * kNEG), 16);
+  L.misc = off;
+  off = align_up(off + 16, 16);
+  L.total = off;
+  return L;
+}
+
+// Inclusive segmented scan of NV values over the 128 rows of one epilogue group. Segments
+// are [j*S, (j+1)*S). `scratch` holds 4 warps x NV floats of this group.
+template <int NV>
+MLPS_DEV void seg_scan(float (&v)[NV], int nv, int row, int S, float* scratch, int bar_id) {
+  const int lane = row & 31, wq = row >> 5;
+  const int seg0 = (row / S) * S;
+  const int lo = max(seg0, wq * 32) - wq * 32;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      if (j >= nv) break;
+      const float y = __shfl_up_sync(0xffffffffu, v[j], o);
+      if (lane - o >= lo) v[j] += y;
+    }
+  }
+  if (S <= 32 && (32 % S) == 0) return;  // segments never cross a warp
+  if (lane == 31)
+    for (int j = 0; j < nv; ++j) scratch[wq * NV + j] = v[j];
+  named_bar_sync(bar_id, kEGThreads);
+  if (seg0 < wq * 32)
+    for (int w2 = seg0 / 32; w2 < wq; ++w2)
+      for (int j = 0; j < nv; ++j) v[j] += scratch[w2 * NV + j];
+  named_bar_sync(bar_id, kEGThreads);
+}
+
+MLPS_DEV float sigmoid_fast(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+MLPS_DEV float softplus_fast(float z) { return fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z))); }
+
+struct RowWriter {  // writes one sample row of a K-major swizzled BF16 A tile, two values at a time
+  uint32_t base;
+  int row, col;
+  float pend;
+  MLPS_DEV void put(float v) {
+    if (col & 1) {
+      const int c0 = col - 1;
+      const uint32_t addr = base + (uint32_t)(c0 >> 6) * (kM * 128) + sw128_off(row, (c0 & 63) >> 3) +
+                            (uint32_t)((c0 & 7) >> 1) * 4;
+      st_shared_u32(addr, pack_bf16(pend, v));
+    } else {
+      pend = v;
+    }
+    ++col;
+  }
+  MLPS_DEV void pad_to(int n) {
+    while (col < n) put(0.f);
+  }
+};
+
+// Encoding gamma (Eq. 5) with one sincos per component and angle doubling
+// (sin 2u = 2 sin u cos u, cos 2u = 1 - 2 sin^2 u); arguments pi * p lie in [-pi, pi].
+MLPS_DEV void put_gamma(RowWriter& rw, float p, int L) {
+  float s, c;
+  __sincosf(3.14159265358979f * p, &s, &c);
+  for (int l = 0; l < L; ++l) {
+    rw.put(s);
+    rw.put(c);
+    const float s2 = 2.f * s * c;
+    c = fmaf(-2.f * s, s, 1.f);
+    s = s2;
+  }
+}
+
+template <int WIDTH>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_mlp_fwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (sbase - raw);
+  const TcSmem L = tc_smem(P);
+  const Model& m = a.m;
+  float* sBias = reinterpret_cast<float*>(gbase + L.bias);
+  float* sScan = reinterpret_cast<float*>(gbase + L.scan);
+  const uint32_t bar_w = sbase + L.bars;
+  const uint32_t bar_end = bar_w + 8;
+  auto bar_ready = [&](int g) { return bar_w + 16 + 8 * g; };
+  auto bar_done = [&](int g) { return bar_w + 16 + 8 * kNEG + 8 * g; };
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(gbase + L.misc);
+  volatile int* sAbort = reinterpret_cast<volatile int*>(gbase + L.misc + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(bar_w, 1);
+    mbar_init(bar_end, 1);
+    for (int g = 0; g < kNEG; ++g) {
+      mbar_init(bar_ready(g), kEGThreads);
+      mbar_init(bar_done(g), 1);
+    }
+    *sAbort = 0;
+    fence_mbar_init();
+  }
+  if (warp == kMmaWarp) {
+    tmem_alloc(sbase + L.misc, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+
+  const int total = w.saved_hdr[2];
+  const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
+  const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
+  const int S = m.S;
+  const int nl = m.nl;
+  const int g = warp >> 2;               // epilogue group of this warp (< kNEG)
+  const int q = warp & 3;                // TMEM lane quarter
+  const int row = q * 32 + lane;         // sample row within the chunk
+  uint32_t ph_w = 0, ph_ready[kNEG], ph_done[kNEG];
+  for (int j = 0; j < kNEG; ++j) { ph_ready[j] = 0; ph_done[j] = 0; }
+  int loaded = -1;
+  int prim = cb < ce ? simt::find_prim(w, cb) : 0;
+  int nissued = 0;
+
+  for (int c = cb; c < ce;) {
+    while (c >= w.chunk_start[prim + 1]) ++prim;
+    int cc[kNEG];
+    int nstep = 0;
+    for (int j = 0; j < kNEG; ++j) {
+      const int cj = c + j;
+      cc[j] = (cj < ce && cj < w.chunk_start[prim + 1]) ? cj : -1;
+      nstep += cc[j] >= 0;
+    }
+    if (prim != loaded) {
+      __syncthreads();  // every role is done with the previous primitive's tiles
+      if (threadIdx.x == kMmaWarp * 32 && !*sAbort) {
+        mbar_arrive_expect_tx(bar_w, (uint32_t)P.w_bytes);
+        const int row0 = prim * P.rows_per_prim;
+        for (int l = 0; l < nl; ++l)
+          for (int sl = 0; sl < P.kpad[l] / 64; ++sl)
+            for (int j = 0; j < P.npad[l] / 16; ++j)
+              tma_load_2d(sbase + L.w + P.sw_off[l] + sl * P.npad[l] * 128 + j * 2048, &tmap, 0,
+                          row0 + P.gw_row[l] + sl * P.npad[l] + j * 16, bar_w);
+      }
+      const float* gb = reinterpret_cast<const float*>(a.weights + (size_t)prim * a.pk.stride + P.gbias_byte);
+      for (int i = threadIdx.x; i < P.bias_floats; i += kThreadsTC) sBias[i] = gb[i];
+      mbar_wait(bar_w, ph_w, sAbort, kWaitNs);
+      ph_w ^= 1;
+      __syncthreads();
+      loaded = prim;
+    }
+
+    if (warp < kMmaWarp) {
+      // ------------------------------------------------------------ epilogue group g
+      if (cc[g] >= 0) {
+        const int bar_id = 1 + g;
+        IntervalInfo* T = reinterpret_cast<IntervalInfo*>(gbase + L.itab[g]);
+        const int first = (cc[g] - w.chunk_start[prim]) * w.ipc;
+        const int nint = min(w.ipc, w.prim_count[prim] - first);
+        if (row < nint)
+          simt::load_interval(w, m, prim, w.prim_list[w.prim_start[prim] + first + row], T[row]);
+        named_bar_sync(bar_id, kEGThreads);
+        const uint32_t A = sbase + L.a[g];
+        const int iv = row / S, k = row - iv * S;
+        const bool valid = iv < nint;
+        {
+          RowWriter rw{A, row, 0, 0.f};
+          if (valid) {
+            const IntervalInfo& I = T[iv];
+            const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+            float xl[3];
+            for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
+            if (m.xyzL == 0) {
+              for (int u = 0; u < 3; ++u) rw.put(xl[u]);
+            } else {
+              for (int u = 0; u < 3; ++u) put_gamma(rw, xl[u], m.xyzL);
+            }
+            if (m.dirL > 0)
+              for (int u = 0; u < 3; ++u) put_gamma(rw, I.d[u], m.dirL);
+          }
+          rw.pad_to(P.kpad[0]);
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        mbar_arrive(bar_ready(g));
+        const uint32_t trow = tmem + (uint32_t)(g * 128) + ((uint32_t)(q * 32) << 16);
+        for (int l = 0; l < nl; ++l) {
+          // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), ph_done[g], sAbort, kWaitNs));
+          ph_done[g] ^= 1;
+          tc_fence_after();
+          const float* bias = sBias + P.bias_off[l];
+          if (l < nl - 1) {
+            if (ok) {
+#pragma unroll
+              for (int half = 0; half < WIDTH / 64; ++half) {
+                uint32_t v0[32], v1[32];
+                tmem_ld32(trow + half * 64, v0);
+                tmem_ld32(trow + half * 64 + 32, v1);
+                tmem_wait_ld();
+                const uint32_t At = A + (uint32_t)half * (kM * 128);
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                  uint32_t pk[4];
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) {
+                    const int c0 = ch * 8 + 2 * e;
+                    const float x0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]) + bias[half * 64 + c0];
+                    const float x1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]) +
+                                     bias[half * 64 + c0 + 1];
+                    pk[e] = pack_bf16_relu(x0, x1);
+                  }
+                  st_shared_v4(At + sw128_off(row, ch), pk[0], pk[1], pk[2], pk[3]);
+                }
+              }
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            mbar_arrive(bar_ready(g));
+          } else {
+            // last layer: heads, then the interval composite
+            float z[48];
+            if (ok) {
+              uint32_t r32[32], r16[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) r16[j] = 0u;
+              if (P.npad[l] >= 32) {
+                tmem_ld32(trow, r32);
+                if (P.npad[l] == 48) tmem_ld16(trow + 32, r16);
+              } else {
+                tmem_ld16(trow, r16);
+              }
+              tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < 48; ++j) {
+                uint32_t bits;
+                if (P.npad[l] >= 32) bits = j < 32 ? r32[j] : r16[j - 32];
+                else bits = j < 16 ? r16[j] : 0u;
+                z[j] = (j < m.nout) ? __uint_as_float(bits) + bias[j] : 0.f;
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 48; ++j) z[j] = 0.f;
+            }
+            tc_fence_before();
+            const float dt = valid ? T[iv].dt : 0.f;
+            const float sig = softplus_fast(z[3]);
+            float A1[1] = {valid ? sig * dt : 0.f};
+            const float a_k = A1[0];
+            seg_scan<1>(A1, 1, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
+            const float Aex = A1[0] - a_k;
+            const float wk = valid ? __expf(-Aex) * (1.f - __expf(-a_k)) : 0.f;
+            float vals[kMaxScanVals];
+#pragma unroll
+            for (int j = 0; j < kMaxScanVals; ++j) vals[j] = 0.f;
+            vals[0] = wk * sigmoid_fast(z[0]);
+            vals[1] = wk * sigmoid_fast(z[1]);
+            vals[2] = wk * sigmoid_fast(z[2]);
+            vals[3] = a_k;
+#pragma unroll
+            for (int f = 0; f < kMaxFeat; ++f)
+              if (f < m.F) vals[4 + f] = wk * z[4 + f];
+            seg_scan<kMaxScanVals>(vals, 4 + m.F, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
+            if (valid && k == S - 1 && ok) {
+              const int h = T[iv].h;
+              w.hit_out[h] = make_float4(vals[0], vals[1], vals[2], vals[3]);
+              for (int f = 0; f < m.F; ++f) w.hit_feat[(size_t)h * m.F + f] = vals[4 + f];
+            }
+          }
+        }
+      }
+    } else if (lane == 0) {
+      // ------------------------------------------------------------ MMA issuer
+      for (int l = 0; l < nl; ++l) {
+        const uint32_t idesc = idesc_bf16(kM, P.npad[l]);
+        const uint32_t wl = sbase + L.w + P.sw_off[l];
+        for (int j = 0; j < kNEG; ++j) {
+          if (cc[j] < 0) continue;
+          const bool ok = mbar_wait(bar_ready(j), ph_ready[j], sAbort, kWaitNs);
+          ph_ready[j] ^= 1;
+          tc_fence_after();
+          if (ok) {
+            const uint32_t A = sbase + L.a[j];
+            const uint32_t d = tmem + (uint32_t)(j * 128);
+            for (int kk = 0; kk < P.kpad[l] / 16; ++kk) {
+              const uint32_t aa = A + (uint32_t)(kk >> 2) * (kM * 128) + (uint32_t)(kk & 3) * 32;
+              const uint32_t bb = wl + (uint32_t)(kk >> 2) * (P.npad[l] * 128) + (uint32_t)(kk & 3) * 32;
+              mma_bf16(d, sw128_desc(aa), sw128_desc(bb), idesc, kk > 0 ? 1u : 0u);
+            }
+            ++nissued;
+          }
+          mma_commit(bar_done(j));
+        }
+      }
+    }
+    c += nstep;
+  }
+
+  // teardown: make sure no MMA is still writing TMEM, then free it
+  if (warp == kMmaWarp && lane == 0) {
+    mma_commit(bar_end);
+    mbar_wait(bar_end, 0, sAbort, kWaitNs);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+  if (threadIdx.x == 0 && *sAbort) set_status(w.saved_hdr, MLPS_ERR_TIMEOUT);
+  (void)nissued;
+}
+
+// ------------------------------------------------------------------------------------------
+// Packing of canonical FP32 weights into the BF16 tensor-core blob
+
+__global__ void k_pack_bf16(Model m, TcPlan P, long long stride, int K, const float* __restrict__ src,
+                            unsigned char* __restrict__ dst) {
+  const int p = blockIdx.y;
+  if (p >= K) return;
+  const float* s = src + (size_t)p * m.P;
+  unsigned char* d = dst + (size_t)p * stride;
+  // weight tiles: element (n, k) of layer l at row gw_row + (k / 64) * npad + n, column k % 64
+  for (int l = 0; l < m.nl; ++l) {
+    const int np = P.npad[l], kp = P.kpad[l];
+    __nv_bfloat16* t = reinterpret_cast<__nv_bfloat16*>(d + (size_t)P.gw_row[l] * 128);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np * kp; i += gridDim.x * blockDim.x) {
+      const int n = i / kp, k = i - n * kp;
+      const float v = (n < m.dout[l] && k < m.din[l]) ? s[m.woff[l] + n * m.din[l] + k] : 0.f;
+      t[((k >> 6) * np + n) * 64 + (k & 63)] = __float2bfloat16_rn(v);
+    }
+  }
+  float* b = reinterpret_cast<float*>(d + P.gbias_byte);
+  for (int l = 0; l < m.nl; ++l)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.npad[l]; i += gridDim.x * blockDim.x)
+      b[P.bias_off[l] + i] = i < m.dout[l] ? s[m.boff[l] + i] : 0.f;
+}
+
+}  // namespace tc
+
+// ------------------------------------------------------------------------------------------
+// Host side
+
+static int round_up_i(int x, int a) { return (x + a - 1) / a * a; }
+
+bool tc_plan(const Model& m, TcPlan* P, long long* stride) {
+  std::memset(P, 0, sizeof(*P));
+  if (m.width != 64 && m.width != 128) return false;
+  if (m.nin > 128 || m.nout > 48 || m.S > 128) return false;
+  P->nl = m.nl;
+  int rows = 0, sw = 0, bias = 0, kmax = 0;
+  for (int l = 0; l < m.nl; ++l) {
+    P->kpad[l] = l == 0 ? round_up_i(m.nin, 64) : m.width;
+    P->npad[l] = l == m.nl - 1 ? round_up_i(m.nout, 16) : m.width;
+    P->gw_row[l] = rows;
+    rows += (P->kpad[l] / 64) * P->npad[l];
+    P->sw_off[l] = sw;
+    sw += P->kpad[l] * P->npad[l] * 2;
+    P->bias_off[l] = bias;
+    bias += P->npad[l];
+    kmax = kmax > P->kpad[l] ? kmax : P->kpad[l];
+  }
+  P->w_bytes = sw;
+  P->bias_floats = bias;
+  P->gbias_byte = rows * 128;
+  const long long bytes = (long long)rows * 128 + 4LL * bias;
+  *stride = (bytes + 1023) / 1024 * 1024;
+  P->rows_per_prim = (int)(*stride / 128);
+  P->kmax = kmax;
+  P->a_bytes = tc::kM * kmax * 2;
+  return true;
+}
+
+size_t tc_smem_bytes(const TcPlan& P) { return tc::tc_smem(P).total + 1024; }
+
+void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
+                      void* out, cudaStream_t st) {
+  if (K == 0) return;
+  dim3 grid(8, K);
+  tc::k_pack_bf16<<<grid, 256, 0, st>>>(m, P, stride, K, w, static_cast<unsigned char*>(out));
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,
+                              cudaStream_t st) {
+  auto encode = get_encode();
+  if (!encode) return cudaErrorNotSupported;
+  CUtensorMap tmap;
+  const cuuint64_t dims[2] = {64, (cuuint64_t)w.K * (cuuint64_t)P.rows_per_prim};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {64, 16};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<unsigned char*>(a.weights),
+                      dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const size_t smem = tc_smem_bytes(P);
+  if (smem > 227 * 1024) return cudaErrorNotSupported;
+  switch (a.m.width) {
+#define MLPS_CASE(WID)                                                                        \
+  case WID: {                                                                                 \
+    auto kern = tc::k_mlp_fwd_tc<WID>;                                                        \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                         (int)smem);                                          \
+    if (e != cudaSuccess) return e;                                                           \
+    kern<<<n_sm, tc::kThreadsTC, smem, st>>>(w, a, P, tmap);                                  \
+    return cudaGetLastError();                                                                \
+  }
+    MLPS_CASE(64)
+    MLPS_CASE(128)
+#undef MLPS_CASE
+    default:
+      return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace mlps

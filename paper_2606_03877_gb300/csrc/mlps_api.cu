@@ -128,6 +128,12 @@ Packed make_packed(const mlps_config* c, const Model& m) {
   Packed pk;
   std::memset(&pk, 0, sizeof(pk));
   pk.precision = c->precision;
+  if (c->precision == MLPS_BF16) {
+    TcPlan P;
+    long long stride = 0;
+    if (tc_plan(m, &P, &stride)) pk.stride = stride;
+    return pk;
+  }
   int off = 0;
   for (int l = 0; l < m.nl; ++l) {
     pk.woff[l] = off;
@@ -369,6 +375,13 @@ int64_t mlps_weight_stride(const mlps_config* cfg) {
 mlps_status mlps_check_config(const mlps_config* cfg) {
   mlps_status s = check_cfg(cfg);
   if (s != MLPS_OK) return s;
+  if (cfg->precision == MLPS_BF16) {
+    TcPlan P;
+    long long stride;
+    if (!tc_plan(make_model(cfg), &P, &stride)) return MLPS_ERR_UNSUPPORTED;
+    if (tc_smem_bytes(P) > 227 * 1024) return MLPS_ERR_UNSUPPORTED;
+    return MLPS_OK;
+  }
   if (cfg->precision != MLPS_FP32) return MLPS_ERR_UNSUPPORTED;
   return MLPS_OK;
 }
@@ -383,7 +396,14 @@ mlps_status mlps_pack_weights(const mlps_config* cfg, int32_t K, const float* we
   Packed pk = make_packed(cfg, m);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   StageTimer tm(ST_PACK, st);
-  launch_pack_fp32(m, pk, K, weights_fp32, packed, st);
+  if (cfg->precision == MLPS_BF16) {
+    TcPlan P;
+    long long stride;
+    tc_plan(m, &P, &stride);
+    launch_pack_bf16(m, P, stride, K, weights_fp32, packed, st);
+  } else {
+    launch_pack_fp32(m, pk, K, weights_fp32, packed, st);
+  }
   count_launch(K > 0 ? 1 : 0);
   return cuda_status(cudaGetLastError());
 }
@@ -464,7 +484,16 @@ mlps_status mlps_render_forward(const mlps_config* cfg, const mlps_scene* scene,
   }
   if (K > 0) {
     StageTimer tm(ST_MLP_FWD, st);
-    cudaError_t e = launch_mlp_fwd_simt(w, a, n_sm, st);
+    cudaError_t e;
+    if (cfg->precision == MLPS_BF16) {
+      TcPlan P;
+      long long stride;
+      tc_plan(m, &P, &stride);
+      e = launch_mlp_fwd_tc(w, a, P, n_sm, st);
+    } else {
+      e = launch_mlp_fwd_simt(w, a, n_sm, st);
+    }
+    if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return MLPS_ERR_CUDA;
     count_launch(1);
   }
@@ -519,6 +548,7 @@ mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene
                          cfg->feat_dim > 0 ? d_feat : nullptr, st);
     count_launch(w.n_rays > 0 ? 1 : 0);
   }
+  if (cfg->precision != MLPS_FP32) return MLPS_ERR_UNSUPPORTED;
   if (K > 0) {
     StageTimer tm(ST_MLP_BWD, st);
     cudaError_t e = launch_mlp_bwd_simt(w, a, n_sm, st);

@@ -30,6 +30,21 @@ struct MlpArgs {
   int rows;                      // sample rows per chunk
 };
 
+// Tensor-core plan: per-layer padded shapes and where the operand tiles live.
+struct TcPlan {
+  int nl;
+  int kpad[kMaxLayers], npad[kMaxLayers];  // K (inputs) and N (outputs) padded per layer
+  int sw_off[kMaxLayers];                  // shared-memory byte offset of layer l's W tile
+  int gw_row[kMaxLayers];                  // first 128-byte row of layer l's tile in a blob
+  int w_bytes;                             // all forward W tiles
+  int bias_off[kMaxLayers];                // float offset of layer l's bias
+  int bias_floats;
+  int gbias_byte;                          // byte offset of the FP32 biases in a blob
+  int rows_per_prim;                       // blob stride / 128
+  int kmax;                                // widest A tile (elements)
+  int a_bytes;                             // one A tile: 128 rows x kmax BF16
+};
+
 // k_geometry.cu
 void launch_store_views(const Work& w, const ViewArray& va, cudaStream_t st);
 void launch_prim_setup(const Work& w, const float* c, const float* s, const float* q,
@@ -46,6 +61,14 @@ void launch_export_tiles(const Work& w, int* count, int* list, cudaStream_t st);
 size_t mlp_simt_smem(const MlpArgs& a, bool backward);
 cudaError_t launch_mlp_fwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st);
 cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st);
+
+// k_mlp_tc.cu (BF16 tensor-core path)
+bool tc_plan(const Model& m, TcPlan* P, long long* stride);
+size_t tc_smem_bytes(const TcPlan& P);
+void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
+                      void* out, cudaStream_t st);
+cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,
+                              cudaStream_t st);
 
 // k_composite.cu
 void launch_composite_fwd(const Work& w, int F, float* rgb, float* trans, float* feat,
