@@ -226,6 +226,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         IntervalInfo* T = reinterpret_cast<IntervalInfo*>(gbase + L.itab[g]);
         const int first = (cc[g] - w.chunk_start[prim]) * w.ipc;
         const int nint = min(w.ipc, w.prim_count[prim] - first);
+        // every warp of the group is done with the previous chunk's interval table
+        named_bar_sync(bar_id, kEGThreads);
         if (row < nint)
           simt::load_interval(w, m, prim, w.prim_list[w.prim_start[prim] + first + row], T[row]);
         named_bar_sync(bar_id, kEGThreads);

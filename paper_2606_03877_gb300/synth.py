@@ -256,8 +256,9 @@ def sample_pixels(cfg: SceneConfig, n: int, seed: int = 0) -> np.ndarray:
     """``n`` distinct pixels as int32 triples (view, x, y), sorted by global ray index."""
     total = cfg.n_rays
     n = min(n, total)
-    b = bits(seed, STREAM_GRAD + 100, 4 * n)
-    idx = np.unique((b % np.uint64(total)).astype(np.int64))[:n]
+    b = (bits(seed, STREAM_GRAD + 100, 4 * n) % np.uint64(total)).astype(np.int64)
+    _, first = np.unique(b, return_index=True)  # distinct values, kept in draw order
+    idx = np.sort(b[np.sort(first)][:n])
     hw = cfg.width * cfg.height
     v = idx // hw
     r = idx % hw

@@ -4,6 +4,7 @@ enqueued here."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2606_03877_gb300 import _lib, build, synth
@@ -92,3 +93,11 @@ def test_library_fails_loudly_when_missing(tmp_path):
             _lib.load(str(tmp_path / "nope.so"))
     finally:
         _lib._lib = saved
+
+
+def test_sample_pixels_uniform_over_views():
+    c = synth.CONFIGS["prec"]
+    p = synth.sample_pixels(c, 4000, seed=3)
+    assert len(p) == 4000 and len(np.unique(p, axis=0)) == 4000
+    counts = np.bincount(p[:, 0], minlength=c.n_views)
+    assert counts.min() > 0.7 * 4000 / c.n_views
