@@ -430,8 +430,34 @@ __global__ void k_scatter(Work w) {
     int off = 0;
     if (lane == leader) off = atomicAdd(&w.prim_cursor[p], __popc(peers));
     off = __shfl_sync(peers, off, leader);
-    if (off + rank < w.prim_count[p]) w.prim_list[w.prim_start[p] + off + rank] = h;
-    else set_status(w.saved_hdr, MLPS_ERR_CAPACITY_OVERFLOW);
+    if (off + rank >= w.prim_count[p]) {
+      set_status(w.saved_hdr, MLPS_ERR_CAPACITY_OVERFLOW);
+      continue;
+    }
+    const int slot = w.prim_start[p] + off + rank;
+    w.prim_list[slot] = h;
+    // the interval record: everything the MLP stage needs, contiguous per chunk
+    const int ray = w.hit_ray[h];
+    const int hw = w.H * w.W;
+    const int v = ray / hw, pix = ray - v * hw;
+    const int y = pix / w.W, x = pix - y * w.W;
+    float d[3];
+    ray_dir_f(w.views[v], x, y, d);
+    const PrimGeo& g = w.geo[p];
+    IntervalRec r;
+    r.h = h;
+    for (int i = 0; i < 3; ++i) {
+      r.p[i] = w.hit_p[(size_t)i * w.hit_cap + h];
+      r.d[i] = d[i];
+      r.dp[i] = g.Mhi[i * 3] * d[0] + g.Mhi[i * 3 + 1] * d[1] + g.Mhi[i * 3 + 2] * d[2];
+    }
+    r.r0 = w.hit_r0[h];
+    r.r1 = w.hit_r1[h];
+    r.dt = (r.r1 - r.r0) / (float)w.S;
+    r.tmid = w.hit_tmid[h];
+    r.pad[0] = 0.f;
+    r.pad[1] = 0.f;
+    w.rec[slot] = r;
   }
 }
 

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fwd_simt(Work w, MlpArgs a)
       loaded = prim;
     }
     if (threadIdx.x < nint)
-      load_interval(w, m, prim, w.prim_list[w.prim_start[prim] + first + threadIdx.x], sI[threadIdx.x]);
+      load_interval(w, m, w.prim_start[prim] + first + threadIdx.x, sI[threadIdx.x]);
     __syncthreads();
     if (threadIdx.x < kRows) {
       const int row = threadIdx.x, i = row / S, k = row - i * S;

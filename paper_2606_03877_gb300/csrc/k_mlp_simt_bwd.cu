@@ -317,8 +317,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
       const int nint = min(ipcb, nint_c - i0);
       __syncthreads();
       if (threadIdx.x < nint) {
-        const int h = w.prim_list[w.prim_start[prim] + first + i0 + threadIdx.x];
-        load_interval(w, m, prim, h, sI[threadIdx.x]);
+        const int slot = w.prim_start[prim] + first + i0 + threadIdx.x;
+        load_interval(w, m, slot, sI[threadIdx.x]);
+        const int h = sI[threadIdx.x].h;
         sGrad[threadIdx.x] = w.hit_grad[h];
         for (int f = 0; f < F; ++f) sGF[threadIdx.x * F + f] = w.hit_gfeat[(size_t)h * F + f];
       }

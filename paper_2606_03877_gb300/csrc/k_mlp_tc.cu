@@ -30,21 +30,18 @@
 #include "mlps_kernels.h"
 #include "simt_common.cuh"
 #include "tc_ptx.cuh"
+#include "tc_common.cuh"
 
 namespace mlps {
 namespace tc {
 
 using simt::IntervalInfo;
 
-constexpr int kM = 128;
 constexpr int kNEG = 2;                         // epilogue groups = chunks in flight
-constexpr int kEGThreads = 128;
 constexpr int kThreadsTC = kEGThreads * kNEG + 32;
 constexpr int kMmaWarp = kNEG * 4;
 constexpr uint32_t kTmemCols = 256;             // 128 per group
 constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s
-constexpr int kMaxScanVals = 4 + kMaxFeat;
-
 struct TcSmem {
   uint32_t w, a[kNEG], bias, itab[kNEG], scan, bars, misc, total;
 };
@@ -74,69 +71,6 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P) {
   off = align_up(off + 16, 16);
   L.total = off;
   return L;
-}
-
-// Inclusive segmented scan of NV values over the 128 rows of one epilogue group. Segments
-// are [j*S, (j+1)*S). `scratch` holds 4 warps x NV floats of this group.
-template <int NV>
-MLPS_DEV void seg_scan(float (&v)[NV], int nv, int row, int S, float* scratch, int bar_id) {
-  const int lane = row & 31, wq = row >> 5;
-  const int seg0 = (row / S) * S;
-  const int lo = max(seg0, wq * 32) - wq * 32;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      if (j >= nv) break;
-      const float y = __shfl_up_sync(0xffffffffu, v[j], o);
-      if (lane - o >= lo) v[j] += y;
-    }
-  }
-  if (S <= 32 && (32 % S) == 0) return;  // segments never cross a warp
-  if (lane == 31)
-    for (int j = 0; j < nv; ++j) scratch[wq * NV + j] = v[j];
-  named_bar_sync(bar_id, kEGThreads);
-  if (seg0 < wq * 32)
-    for (int w2 = seg0 / 32; w2 < wq; ++w2)
-      for (int j = 0; j < nv; ++j) v[j] += scratch[w2 * NV + j];
-  named_bar_sync(bar_id, kEGThreads);
-}
-
-MLPS_DEV float sigmoid_fast(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
-MLPS_DEV float softplus_fast(float z) { return fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z))); }
-
-struct RowWriter {  // writes one sample row of a K-major swizzled BF16 A tile, two values at a time
-  uint32_t base;
-  int row, col;
-  float pend;
-  MLPS_DEV void put(float v) {
-    if (col & 1) {
-      const int c0 = col - 1;
-      const uint32_t addr = base + (uint32_t)(c0 >> 6) * (kM * 128) + sw128_off(row, (c0 & 63) >> 3) +
-                            (uint32_t)((c0 & 7) >> 1) * 4;
-      st_shared_u32(addr, pack_bf16(pend, v));
-    } else {
-      pend = v;
-    }
-    ++col;
-  }
-  MLPS_DEV void pad_to(int n) {
-    while (col < n) put(0.f);
-  }
-};
-
-// Encoding gamma (Eq. 5) with one sincos per component and angle doubling
-// (sin 2u = 2 sin u cos u, cos 2u = 1 - 2 sin^2 u); arguments pi * p lie in [-pi, pi].
-MLPS_DEV void put_gamma(RowWriter& rw, float p, int L) {
-  float s, c;
-  __sincosf(3.14159265358979f * p, &s, &c);
-  for (int l = 0; l < L; ++l) {
-    rw.put(s);
-    rw.put(c);
-    const float s2 = 2.f * s * c;
-    c = fmaf(-2.f * s, s, 1.f);
-    s = s2;
-  }
 }
 
 template <int WIDTH>
@@ -229,7 +163,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         // every warp of the group is done with the previous chunk's interval table
         named_bar_sync(bar_id, kEGThreads);
         if (row < nint)
-          simt::load_interval(w, m, prim, w.prim_list[w.prim_start[prim] + first + row], T[row]);
+          simt::load_interval(w, m, w.prim_start[prim] + first + row, T[row]);
         named_bar_sync(bar_id, kEGThreads);
         const uint32_t A = sbase + L.a[g];
         const int iv = row / S, k = row - iv * S;
@@ -401,6 +335,16 @@ __global__ void k_pack_bf16(Model m, TcPlan P, long long stride, int K, const fl
       t[((k >> 6) * np + n) * 64 + (k & 63)] = __float2bfloat16_rn(v);
     }
   }
+  // W^T tiles: element (i, o) = W[o][i] at row gwt_row + (o / 64) * kpad + i, column o % 64
+  for (int l = 0; l < m.nl; ++l) {
+    const int kp = P.kpad[l], ncols = ((P.npad[l] + 63) / 64) * 64;
+    __nv_bfloat16* t = reinterpret_cast<__nv_bfloat16*>(d + (size_t)P.gwt_row[l] * 128);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kp * ncols; e += gridDim.x * blockDim.x) {
+      const int i = e / ncols, o = e - i * ncols;
+      const float v = (i < m.din[l] && o < m.dout[l]) ? s[m.woff[l] + o * m.din[l] + i] : 0.f;
+      t[((o >> 6) * kp + i) * 64 + (o & 63)] = __float2bfloat16_rn(v);
+    }
+  }
   float* b = reinterpret_cast<float*>(d + P.gbias_byte);
   for (int l = 0; l < m.nl; ++l)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.npad[l]; i += gridDim.x * blockDim.x)
@@ -432,6 +376,16 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride) {
     kmax = kmax > P->kpad[l] ? kmax : P->kpad[l];
   }
   P->w_bytes = sw;
+  // W^T tiles for the backward pass: [N = kpad (inputs)] x [K = npad (outputs)], 64-column slabs
+  int swt = 0;
+  for (int l = 0; l < m.nl; ++l) {
+    P->gwt_row[l] = rows;
+    const int kslabs = (P->npad[l] + 63) / 64;
+    rows += kslabs * P->kpad[l];
+    P->swt_off[l] = swt;
+    swt += kslabs * P->kpad[l] * 128;
+  }
+  P->wt_bytes = swt;
   P->bias_floats = bias;
   P->gbias_byte = rows * 128;
   const long long bytes = (long long)rows * 128 + 4LL * bias;

@@ -1,0 +1,644 @@
+// k_mlp_tc_bwd.cu -- BF16 tensor-core (tcgen05) backward of the grouped per-primitive MLP stage.
+//
+// Per chunk of 128 sample rows of one primitive (same chunks as the forward pass), one epilogue
+// group (4 warps, thread = sample row) and the MMA warp run 2 * nl phases:
+//   F_l  (l = 0 .. nl-1): Z_l = H_l W_l^T recomputes the forward; the epilogue writes
+//        H_{l+1} = ReLU(Z_l + b_l) as BF16 into the group's tile T_{l+1};
+//   B_l  (l = nl-1 .. 0): dgrad  G = delta_l W_l          (A = delta_l, K-major; B = W_l^T tile)
+//                         wgrad  dW_l^T += H_l^T delta_l  (A = H_l, B = delta_l, both read as
+//                                MN-major views of the same swizzled tiles; M = 128: the 64
+//                                input features of H_l plus a constant "ones" atom, so that
+//                                row 64 of the accumulator collects the bias gradient
+//                                sum_rows delta_l); the epilogue forms
+//                                delta_{l-1} = G * [H_l > 0] in place of H_l.
+// delta_{nl-1} = dL/dZ comes from the last forward epilogue: the reverse of the interval
+// composite of Eq. 6 with segmented suffix scans (see k_mlp_simt_bwd.cu for the formulas).
+// The input-encoding gradient G_enc = delta_0 W_0 feeds the encoding derivative and the pose
+// chain (closest-point form, no cancellation), reduced per interval and per block.
+// The weight-gradient accumulators live in TMEM for the whole primitive segment of the block,
+// shared by both epilogue groups (their MMAs are issued in order by one thread), and are
+// flushed to global memory with one atomicAdd per entry when the primitive changes.
+// Tiles per group: T_0 (H_0, then dL/dZ, then H_0 rebuilt for the last wgrad), T_1 .. T_{nl-1}.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "mlps_common.cuh"
+#include "mlps_kernels.h"
+#include "simt_common.cuh"
+#include "tc_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace mlps {
+namespace tc {
+
+using simt::IntervalInfo;
+
+namespace {
+
+constexpr int kNG = 2;                              // epilogue groups
+constexpr int kThreadsB = kEGThreads * kNG + 32;
+constexpr int kMmaWarpB = 4 * kNG;
+constexpr uint32_t kTmemColsB = 512;
+constexpr uint64_t kWaitNsB = 2000000000ull;
+constexpr uint32_t kTile = kM * 128;                // one [128 x 64] BF16 tile
+
+struct BwdSmem {
+  uint32_t w, wt, tiles[kNG], ones, bias, itab[kNG], giv[kNG], ddel[kNG], gf[kNG], scan, geo,
+      bars, misc, total;
+};
+
+MLPS_HD uint32_t al(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F) {
+  BwdSmem L;
+  uint32_t o = 0;
+  L.w = o;
+  o = al(o + P.w_bytes, 1024);
+  L.wt = o;
+  o = al(o + P.wt_bytes, 1024);
+  for (int g = 0; g < kNG; ++g) {
+    L.tiles[g] = o;
+    o = al(o + (uint32_t)P.nl * kTile, 1024);
+  }
+  L.ones = o;  // above every group tile: the wgrad descriptors reach it with a positive offset
+  o = al(o + kTile, 1024);
+  L.bias = o;
+  o = al(o + 4 * P.bias_floats, 16);
+  for (int g = 0; g < kNG; ++g) {
+    L.itab[g] = o;
+    o = al(o + (uint32_t)sizeof(IntervalInfo) * kM, 16);
+    L.giv[g] = o;
+    o = al(o + 16 * kM, 16);
+    L.ddel[g] = o;
+    o = al(o + 4 * kM, 16);
+    L.gf[g] = o;
+    o = al(o + 4 * kM * (F > 0 ? F : 1), 16);
+  }
+  L.scan = o;
+  o = al(o + 4 * kNG * 4 * kMaxScanVals, 16);
+  L.geo = o;
+  o = al(o + 4 * 16, 16);
+  L.bars = o;
+  o = al(o + 8 * (2 + 2 * kNG), 16);
+  L.misc = o;
+  o = al(o + 16, 16);
+  L.total = o;
+  return L;
+}
+
+// MN-major 128-byte-swizzle descriptor: 8-row K groups 1024 bytes apart (SBO), MN atoms of 64
+// elements `lbo` bytes apart (LBO).
+MLPS_DEV uint64_t sw128_desc_mn(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
+// Store 64 values of one row (already BF16-packed pairs) into a swizzled tile.
+MLPS_DEV void store_row64(uint32_t tile, int row, const uint32_t (&pk)[32]) {
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch)
+    st_shared_v4(tile + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+}
+
+MLPS_DEV void ld_shared_v4(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+               : "r"(addr)
+               : "memory");
+}
+
+// Build the encoded input row (Eq. 5) of one sample into tile `A` (zeros for invalid rows).
+MLPS_DEV void build_row(const Model& m, const IntervalInfo* T, int nint, int row, uint32_t A,
+                        int kpad0) {
+  const int S = m.S;
+  const int iv = row / S, k = row - iv * S;
+  RowWriter rw{A, row, 0, 0.f};
+  if (iv < nint) {
+    const IntervalInfo& I = T[iv];
+    const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+    float xl[3];
+    for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
+    if (m.xyzL == 0) {
+      for (int u = 0; u < 3; ++u) rw.put(xl[u]);
+    } else {
+      for (int u = 0; u < 3; ++u) put_gamma(rw, xl[u], m.xyzL);
+    }
+    if (m.dirL > 0)
+      for (int u = 0; u < 3; ++u) put_gamma(rw, I.d[u], m.dirL);
+  }
+  rw.pad_to(kpad0);
+}
+
+}  // namespace
+
+template <int NF, int XL>
+__global__ void __launch_bounds__(kThreadsB, 1)
+    k_mlp_bwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  uint8_t* gb = smem_raw + (sbase - raw);
+  const Model& m = a.m;
+  const int F = m.F;
+  const BwdSmem L = bwd_layout(P, F);
+  float* sBias = reinterpret_cast<float*>(gb + L.bias);
+  float* sScan = reinterpret_cast<float*>(gb + L.scan);
+  float* sGeo = reinterpret_cast<float*>(gb + L.geo);
+  const uint32_t bar_w = sbase + L.bars, bar_end = bar_w + 8;
+  auto bar_ready = [&](int g) { return bar_w + 16 + 8 * g; };
+  auto bar_done = [&](int g) { return bar_w + 16 + 8 * kNG + 8 * g; };
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(gb + L.misc);
+  volatile int* sAbort = reinterpret_cast<volatile int*>(gb + L.misc + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nl = m.nl, S = m.S;
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar_w, 1);
+    mbar_init(bar_end, 1);
+    for (int g = 0; g < kNG; ++g) {
+      mbar_init(bar_ready(g), kEGThreads);
+      mbar_init(bar_done(g), 1);
+    }
+    *sAbort = 0;
+    fence_mbar_init();
+  }
+  // constant ones atom: element 0 of every row is 1.0 (BF16 0x3F80)
+  for (int i = threadIdx.x; i < (int)(kTile / 16); i += kThreadsB) {
+    const int r = i >> 3, ch = i & 7;
+    const uint32_t one = ((ch ^ (r & 7)) == 0) ? 0x3F80u : 0u;  // chunk 0 of row r lands at r & 7
+    st_shared_v4(sbase + L.ones + (uint32_t)i * 16, one, 0u, 0u, 0u);
+  }
+  if (threadIdx.x < 16) sGeo[threadIdx.x] = 0.f;
+  fence_proxy_async_smem();
+  if (warp == kMmaWarpB) {
+    tmem_alloc(sbase + L.misc, kTmemColsB);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+  const uint32_t tm_dw = tmem + 128;  // weight-gradient accumulators: 64 columns per layer
+
+  const int total = w.saved_hdr[2];
+  const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
+  const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
+  const int g = warp >> 2, q = warp & 3, row = q * 32 + lane;
+  uint32_t ph_w = 0, ph_ready[kNG], ph_done[kNG];
+  for (int j = 0; j < kNG; ++j) { ph_ready[j] = 0; ph_done[j] = 0; }
+  int first_wgrad[kMaxLayers];
+  for (int l = 0; l < kMaxLayers; ++l) first_wgrad[l] = 1;
+  int loaded = -1;
+  int prim = cb < ce ? simt::find_prim(w, cb) : 0;
+
+  // flush of the block's accumulated gradients of primitive p (all threads call it)
+  auto flush = [&](int p) {
+    if (warp < 4) {
+      tc_fence_after();
+      float* dW = a.d_weights + (size_t)p * m.P;
+      const uint32_t lanebase = (uint32_t)(q * 32) << 16;
+      for (int l = 0; l < nl; ++l) {
+        const int din = m.din[l], dout = m.dout[l];
+        for (int c0 = 0; c0 < 64; c0 += 32) {
+          uint32_t v[32];
+          tmem_ld32(tm_dw + (uint32_t)(l * 64 + c0) + lanebase, v);
+          tmem_wait_ld();
+          if (*sAbort) continue;
+          for (int j = 0; j < 32; ++j) {
+            const int n = c0 + j;
+            const float val = __uint_as_float(v[j]);
+            if (n >= dout || val == 0.f) continue;
+            if (row < din) atomicAdd(&dW[m.woff[l] + n * din + row], val);
+            else if (row == 64) atomicAdd(&dW[m.boff[l] + n], val);
+          }
+        }
+      }
+      tc_fence_before();
+    }
+    if (threadIdx.x < 12) {
+      const float v = sGeo[threadIdx.x];
+      if (v != 0.f) atomicAdd(&w.dgeo[12 * (size_t)p + threadIdx.x], v);
+      sGeo[threadIdx.x] = 0.f;
+    }
+  };
+
+  for (int c = cb; c < ce;) {
+    while (c >= w.chunk_start[prim + 1]) ++prim;
+    int cc[kNG];
+    int nstep = 0;
+    for (int j = 0; j < kNG; ++j) {
+      const int cj = c + j;
+      cc[j] = (cj < ce && cj < w.chunk_start[prim + 1]) ? cj : -1;
+      nstep += cc[j] >= 0;
+    }
+    if (prim != loaded) {
+      tc_fence_before();
+      __syncthreads();
+      if (loaded >= 0) flush(loaded);
+      __syncthreads();
+      if (threadIdx.x == kMmaWarpB * 32 && !*sAbort) {
+        mbar_arrive_expect_tx(bar_w, (uint32_t)(P.w_bytes + P.wt_bytes));
+        const int row0 = prim * P.rows_per_prim;
+        for (int l = 0; l < nl; ++l) {
+          for (int sl = 0; sl < P.kpad[l] / 64; ++sl)
+            for (int j = 0; j < P.npad[l] / 16; ++j)
+              tma_load_2d(sbase + L.w + P.sw_off[l] + sl * P.npad[l] * 128 + j * 2048, &tmap, 0,
+                          row0 + P.gw_row[l] + sl * P.npad[l] + j * 16, bar_w);
+          const int ks = (P.npad[l] + 63) / 64;
+          for (int sl = 0; sl < ks; ++sl)
+            for (int j = 0; j < P.kpad[l] / 16; ++j)
+              tma_load_2d(sbase + L.wt + P.swt_off[l] + sl * P.kpad[l] * 128 + j * 2048, &tmap, 0,
+                          row0 + P.gwt_row[l] + sl * P.kpad[l] + j * 16, bar_w);
+        }
+      }
+      const float* gbias = reinterpret_cast<const float*>(a.weights + (size_t)prim * a.pk.stride + P.gbias_byte);
+      for (int i = threadIdx.x; i < P.bias_floats; i += kThreadsB) sBias[i] = gbias[i];
+      mbar_wait(bar_w, ph_w, sAbort, kWaitNsB);
+      ph_w ^= 1;
+      for (int l = 0; l < kMaxLayers; ++l) first_wgrad[l] = 1;
+      __syncthreads();
+      loaded = prim;
+    }
+
+    if (warp < kMmaWarpB) {
+      // ============================================================ epilogue group g
+      if (cc[g] >= 0) {
+        const int bar_id = 1 + g;
+        IntervalInfo* T = reinterpret_cast<IntervalInfo*>(gb + L.itab[g]);
+        float4* GI = reinterpret_cast<float4*>(gb + L.giv[g]);
+        float* DD = reinterpret_cast<float*>(gb + L.ddel[g]);
+        float* GF = reinterpret_cast<float*>(gb + L.gf[g]);
+        const int first = (cc[g] - w.chunk_start[prim]) * w.ipc;
+        const int nint = min(w.ipc, w.prim_count[prim] - first);
+        named_bar_sync(bar_id, kEGThreads);
+        if (row < nint) {
+          simt::load_interval(w, m, w.prim_start[prim] + first + row, T[row]);
+          const int h = T[row].h;
+          GI[row] = w.hit_grad[h];
+          for (int f = 0; f < F; ++f) GF[row * F + f] = w.hit_gfeat[(size_t)h * F + f];
+        }
+        named_bar_sync(bar_id, kEGThreads);
+        const uint32_t tiles = sbase + L.tiles[g];
+        auto tileaddr = [&](int i) { return tiles + (uint32_t)i * kTile; };
+        const int iv = row / S, k = row - iv * S;
+        const bool valid = iv < nint;
+        const uint32_t trow = tmem + (uint32_t)(g * 64) + ((uint32_t)(q * 32) << 16);
+
+        build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        mbar_arrive(bar_ready(g));
+
+        // ---------------- forward recompute
+        for (int l = 0; l < nl; ++l) {
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), ph_done[g], sAbort, kWaitNsB));
+          ph_done[g] ^= 1;
+          tc_fence_after();
+          const float* bias = sBias + P.bias_off[l];
+          if (l < nl - 1) {
+            uint32_t pk[32];
+            if (ok) {
+              uint32_t v0[32], v1[32];
+              tmem_ld32(trow, v0);
+              tmem_ld32(trow + 32, v1);
+              tmem_wait_ld();
+#pragma unroll
+              for (int e = 0; e < 32; ++e) {
+                const int c0 = 2 * e;
+                const float x0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]) + bias[c0];
+                const float x1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]) + bias[c0 + 1];
+                pk[e] = pack_bf16_relu(x0, x1);
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 32; ++e) pk[e] = 0u;
+            }
+            store_row64(tileaddr(l + 1), row, pk);
+            fence_proxy_async_smem();
+            tc_fence_before();
+            mbar_arrive(bar_ready(g));
+          } else {
+            // ---------------- heads and reverse of the interval composite -> dL/dZ into T_0
+            float z[4 + NF];
+            {
+              uint32_t r16[16];
+              if (ok) {
+                tmem_ld16(trow, r16);
+                tmem_wait_ld();
+              } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) r16[j] = 0u;
+              }
+              uint32_t r32[32];
+#pragma unroll
+              for (int j = 0; j < 32; ++j) r32[j] = 0u;
+              if (NF > 12 && ok) {
+                tmem_ld32(trow + 16, r32);
+                tmem_wait_ld();
+              }
+#pragma unroll
+              for (int j = 0; j < 4 + NF; ++j) {
+                const uint32_t bits = j < 16 ? r16[j] : r32[(j - 16) & 31];
+                z[j] = j < m.nout ? __uint_as_float(bits) + bias[j] : 0.f;
+              }
+            }
+            tc_fence_before();
+            const IntervalInfo& I = T[valid ? iv : 0];
+            const float dt = valid ? I.dt : 0.f;
+            const float sig = softplus_fast(z[3]);
+            const float ak = valid ? sig * dt : 0.f;
+            float sc1[1] = {ak};
+            seg_scan<1>(sc1, 1, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
+            const float Aex = sc1[0] - ak;
+            const float tau = __expf(-Aex), ea = __expf(-ak);
+            const float wk = valid ? tau * (1.f - ea) : 0.f;
+            float cq[3];
+            for (int u = 0; u < 3; ++u) cq[u] = sigmoid_fast(z[u]);
+            float sv[3 + NF];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) sv[u] = wk * cq[u];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) sv[3 + f] = f < F ? wk * z[4 + f] : 0.f;
+            seg_scan_rev<3 + NF>(sv, 3 + F, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
+            const float4 gI = valid ? GI[iv] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float gcs[3] = {gI.x, gI.y, gI.z};
+            float dLda = gI.w;
+#pragma unroll
+            for (int u = 0; u < 3; ++u) dLda += gcs[u] * (tau * ea * cq[u] - (sv[u] - wk * cq[u]));
+            float dz[4 + NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              const float gf = (valid && f < F) ? GF[iv * F + f] : 0.f;
+              const float fk = z[4 + f];
+              dLda += gf * (tau * ea * fk - (sv[3 + f] - wk * fk));
+              dz[4 + f] = wk * gf;
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u) dz[u] = wk * gcs[u] * cq[u] * (1.f - cq[u]);
+            dz[3] = valid ? dLda * dt * sigmoid_fast(z[3]) : 0.f;
+            float dd[1] = {valid ? sig * dLda : 0.f};
+            seg_scan<1>(dd, 1, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
+            if (valid && k == S - 1) DD[iv] = dd[0];
+            uint32_t pk[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const float x0 = (2 * e < m.nout) ? dz[(2 * e) < 4 + NF ? 2 * e : 0] : 0.f;
+              const float x1 = (2 * e + 1 < m.nout) ? dz[(2 * e + 1) < 4 + NF ? 2 * e + 1 : 0] : 0.f;
+              pk[e] = pack_bf16(x0, x1);
+            }
+            store_row64(tileaddr(0), row, pk);
+            fence_proxy_async_smem();
+            tc_fence_before();
+            mbar_arrive(bar_ready(g));
+          }
+        }
+        // ---------------- backward phases B_{nl-1} .. B_0
+        for (int l = nl - 1; l >= 0; --l) {
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), ph_done[g], sAbort, kWaitNsB));
+          ph_done[g] ^= 1;
+          tc_fence_after();
+          if (l > 0) {
+            // delta_{l-1} = G * [H_l > 0], written over H_l in T_l
+            uint32_t v0[32], v1[32];
+            if (ok) {
+              tmem_ld32(trow, v0);
+              tmem_ld32(trow + 32, v1);
+              tmem_wait_ld();
+            } else {
+#pragma unroll
+              for (int e = 0; e < 32; ++e) { v0[e] = 0u; v1[e] = 0u; }
+            }
+            tc_fence_before();
+            const uint32_t Tl = tileaddr(l);
+            uint32_t pk[32];
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) {
+              uint32_t hq[4];
+              ld_shared_v4(Tl + sw128_off(row, ch), hq[0], hq[1], hq[2], hq[3]);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int c0 = ch * 8 + 2 * e;
+                const float g0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]);
+                const float g1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]);
+                // BF16 pair: low half = feature c0, high half = feature c0 + 1 (> 0 iff positive, non-zero)
+                const uint32_t h0 = hq[e] & 0xFFFFu, h1 = hq[e] >> 16;
+                const bool p0 = h0 != 0u && (h0 & 0x8000u) == 0u;
+                const bool p1 = h1 != 0u && (h1 & 0x8000u) == 0u;
+                pk[ch * 4 + e] = pack_bf16(valid && p0 ? g0 : 0.f, valid && p1 ? g1 : 0.f);
+              }
+            }
+            store_row64(Tl, row, pk);
+            if (l == 1) build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+            fence_proxy_async_smem();
+            tc_fence_before();
+            mbar_arrive(bar_ready(g));
+          } else {
+            // ---------------- encoding derivative and pose chain
+            float G[64];
+            {
+              uint32_t v0[32], v1[32];
+              if (ok) {
+                tmem_ld32(trow, v0);
+                tmem_ld32(trow + 32, v1);
+                tmem_wait_ld();
+              } else {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) { v0[e] = 0u; v1[e] = 0u; }
+              }
+#pragma unroll
+              for (int e = 0; e < 32; ++e) { G[e] = __uint_as_float(v0[e]); G[32 + e] = __uint_as_float(v1[e]); }
+            }
+            tc_fence_before();
+            float red[14];
+#pragma unroll
+            for (int e = 0; e < 14; ++e) red[e] = 0.f;
+            if (valid) {
+              const IntervalInfo& I = T[iv];
+              const PrimGeo& Gp = w.geo[prim];
+              const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+              float xl[3], gx[3] = {0.f, 0.f, 0.f};
+              for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
+              if (XL == 0) {
+                for (int u = 0; u < 3; ++u) gx[u] = G[u];
+              } else {
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                  float s_, c_;
+                  __sincosf(3.14159265358979f * xl[u], &s_, &c_);
+                  float wq = 3.14159265358979f;
+#pragma unroll
+                  for (int l2 = 0; l2 < XL; ++l2) {
+                    const int f = 2 * (u * XL + l2);
+                    gx[u] += wq * (G[f] * c_ - G[f + 1] * s_);
+                    const float s2 = 2.f * s_ * c_;
+                    c_ = fmaf(-2.f * s_, s_, 1.f);
+                    s_ = s2;
+                    wq *= 2.f;
+                  }
+                }
+              }
+              float y[3];
+              for (int u = 0; u < 3; ++u)
+                y[u] = Gp.R[u * 3] * Gp.s[0] * xl[0] + Gp.R[u * 3 + 1] * Gp.s[1] * xl[1] + Gp.R[u * 3 + 2] * Gp.s[2] * xl[2];
+              const float uu = ((float)k + 0.5f) / (float)S;
+              const float gt = gx[0] * I.dp[0] + gx[1] * I.dp[1] + gx[2] * I.dp[2];
+              for (int u = 0; u < 3; ++u) {
+                red[u] = gx[u];
+                for (int e = 0; e < 3; ++e) red[3 + u * 3 + e] = gx[u] * y[e];
+              }
+              red[12] = gt * (1.f - uu);
+              red[13] = gt * uu;
+            }
+            seg_scan<14>(red, 14, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
+            if (valid && k == S - 1) {
+              const IntervalInfo& I = T[iv];
+              const PrimGeo& Gp = w.geo[prim];
+              const float dDelta = DD[iv];
+              float gt0 = red[12] - dDelta / (float)S, gt1 = red[13] + dDelta / (float)S;
+              const bool clamped = I.r0 != -I.r1;
+              const float gtm = gt1 + (clamped ? 0.f : gt0);
+              const float gh = gt1 - (clamped ? 0.f : gt0);
+              const float aa = I.dp[0] * I.dp[0] + I.dp[1] * I.dp[1] + I.dp[2] * I.dp[2];
+              const float hh = I.r1;
+              float go[3], cd[3], ymid[3];
+              for (int u = 0; u < 3; ++u) {
+                go[u] = -gtm * I.dp[u] / aa - (hh > 0.f ? gh * I.p[u] / (aa * hh) : 0.f);
+                cd[u] = -(gtm * I.p[u] / aa + gh * hh * I.dp[u] / aa);
+              }
+              for (int u = 0; u < 3; ++u)
+                ymid[u] = Gp.R[u * 3] * Gp.s[0] * I.p[0] + Gp.R[u * 3 + 1] * Gp.s[1] * I.p[1] + Gp.R[u * 3 + 2] * Gp.s[2] * I.p[2];
+              for (int u = 0; u < 3; ++u)
+                for (int e = 0; e < 3; ++e)
+                  atomicAdd(&sGeo[u * 3 + e], red[3 + u * 3 + e] + go[u] * ymid[e] + cd[u] * I.d[e]);
+              for (int e = 0; e < 3; ++e) {
+                float acc2 = 0.f;
+                for (int u = 0; u < 3; ++u) acc2 += Gp.Mhi[u * 3 + e] * (red[u] + go[u]);
+                atomicAdd(&sGeo[9 + e], -acc2);
+              }
+            }
+          }
+        }
+      }
+    } else if (warp == kMmaWarpB && lane == 0) {
+      // ============================================================ MMA issuer
+      for (int ph = 0; ph < 2 * nl; ++ph) {
+        for (int j = 0; j < kNG; ++j) {
+          if (cc[j] < 0) continue;
+          const bool ok = mbar_wait(bar_ready(j), ph_ready[j], sAbort, kWaitNsB);
+          ph_ready[j] ^= 1;
+          tc_fence_after();
+          if (ok) {
+            const uint32_t tiles = sbase + L.tiles[j];
+            const uint32_t acc = tmem + (uint32_t)(j * 64);
+            if (ph < nl) {
+              const int l = ph;  // F_l
+              const uint32_t A = tiles + (uint32_t)l * kTile;
+              const uint32_t B = sbase + L.w + P.sw_off[l];
+              const uint32_t idesc = idesc_bf16(kM, P.npad[l]);
+              for (int kk = 0; kk < P.kpad[l] / 16; ++kk)
+                mma_bf16(acc, sw128_desc(A + (uint32_t)(kk & 3) * 32), sw128_desc(B + (uint32_t)(kk & 3) * 32),
+                         idesc, kk > 0 ? 1u : 0u);
+            } else {
+              const int l = 2 * nl - 1 - ph;  // B_l
+              const uint32_t Dl = tiles + (uint32_t)(l == nl - 1 ? 0 : l + 1) * kTile;  // delta_l
+              const uint32_t Hl = tiles + (uint32_t)l * kTile;                          // H_l
+              // dgrad: G = delta_l W_l, K = npad[l] (outputs), N = kpad[l] (inputs)
+              const uint32_t Bt = sbase + L.wt + P.swt_off[l];
+              const uint32_t id_d = idesc_bf16(kM, P.kpad[l]);
+              for (int kk = 0; kk < P.npad[l] / 16; ++kk)
+                mma_bf16(acc, sw128_desc(Dl + (uint32_t)(kk & 3) * 32), sw128_desc(Bt + (uint32_t)(kk & 3) * 32),
+                         id_d, kk > 0 ? 1u : 0u);
+              // wgrad: dW_l^T[in(+ones)][out] += H_l^T delta_l over the 128 rows
+              const uint32_t id_w = idesc_bf16(kM, 64) | (1u << 15) | (1u << 16);
+              const uint32_t lbo = (sbase + L.ones) - Hl;
+              for (int kk = 0; kk < kM / 16; ++kk) {
+                const uint32_t acc_flag = (first_wgrad[l] && kk == 0) ? 0u : 1u;
+                mma_bf16(tm_dw + (uint32_t)(l * 64), sw128_desc_mn(Hl + (uint32_t)kk * 2048, lbo),
+                         sw128_desc_mn(Dl + (uint32_t)kk * 2048, 16), id_w, acc_flag);
+              }
+              first_wgrad[l] = 0;
+            }
+          }
+          mma_commit(bar_done(j));
+        }
+      }
+    }
+    c += nstep;
+  }
+  // final flush and teardown
+  if (warp == kMmaWarpB && lane == 0) {
+    mma_commit(bar_end);
+    mbar_wait(bar_end, 0, sAbort, kWaitNsB);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (loaded >= 0) flush(loaded);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kMmaWarpB) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemColsB);
+  }
+  if (threadIdx.x == 0 && *sAbort) set_status(w.scr_hdr, MLPS_ERR_TIMEOUT);
+}
+
+}  // namespace tc
+
+// ------------------------------------------------------------------------------------------
+bool tc_bwd_supported(const Model& m, const TcPlan& P) {
+  if (m.width != 64) return false;
+  if (m.xyzL != 0 && m.xyzL != 6) return false;
+  if (P.kpad[0] != 64) return false;
+  if (m.nl > 6) return false;
+  if (m.F > 12) return false;
+  for (int l = 0; l < m.nl; ++l)
+    if (P.npad[l] > 64) return false;
+  const size_t smem = tc::bwd_layout(P, m.F).total + 1024;
+  return smem <= 227 * 1024;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode_b() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,
+                              cudaStream_t st) {
+  if (!tc_bwd_supported(a.m, P)) return cudaErrorNotSupported;
+  auto encode = get_encode_b();
+  if (!encode) return cudaErrorNotSupported;
+  CUtensorMap tmap;
+  const cuuint64_t dims[2] = {64, (cuuint64_t)w.K * (cuuint64_t)P.rows_per_prim};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {64, 16};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<unsigned char*>(a.weights),
+                      dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const size_t smem = tc::bwd_layout(P, a.m.F).total + 1024;
+  auto kern = a.m.F > 0 ? (a.m.xyzL == 6 ? tc::k_mlp_bwd_tc<12, 6> : tc::k_mlp_bwd_tc<12, 0>)
+                        : (a.m.xyzL == 6 ? tc::k_mlp_bwd_tc<0, 6> : tc::k_mlp_bwd_tc<0, 0>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<n_sm, tc::kThreadsB, smem, st>>>(w, a, P, tmap);
+  return cudaGetLastError();
+}
+
+}  // namespace mlps

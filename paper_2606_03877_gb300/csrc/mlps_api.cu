@@ -161,7 +161,7 @@ struct Carve {
 struct Layout {
   // saved
   size_t hit_prim, hit_ray, hit_tmid, hit_r0, hit_r1, hit_p, hit_out, hit_feat, ray_start,
-      ray_count, prim_count, prim_start, chunk_start, prim_list, views, geo, pview, saved_total;
+      ray_count, prim_count, prim_start, chunk_start, prim_list, rec, views, geo, pview, saved_total;
   // scratch
   size_t prim_cursor, tile_count, tile_list, hit_grad, hit_gfeat, dgeo, scratch_total;
   long long hit_cap;
@@ -196,6 +196,7 @@ bool make_layout(const mlps_config* c, int K, int V, int H, int W, Layout* L) {
   L->prim_start = s.take<int>((size_t)K + 1);
   L->chunk_start = s.take<int>((size_t)K + 1);
   L->prim_list = s.take<int>(hc);
+  L->rec = s.take<IntervalRec>(hc);
   L->views = s.take<ViewData>((size_t)V);
   L->geo = s.take<PrimGeo>((size_t)K + 1);
   L->pview = s.take<PrimView>((size_t)V * K + 1);
@@ -232,6 +233,7 @@ Work make_work(const mlps_config* c, const Layout& L, int K, int V, int H, int W
   w.prim_start = reinterpret_cast<int*>(sv + L.prim_start);
   w.chunk_start = reinterpret_cast<int*>(sv + L.chunk_start);
   w.prim_list = reinterpret_cast<int*>(sv + L.prim_list);
+  w.rec = reinterpret_cast<IntervalRec*>(sv + L.rec);
   w.views = reinterpret_cast<ViewData*>(sv + L.views);
   w.geo = reinterpret_cast<PrimGeo*>(sv + L.geo);
   w.pview = reinterpret_cast<PrimView*>(sv + L.pview);
@@ -256,6 +258,7 @@ Work make_work(const mlps_config* c, const Layout& L, int K, int V, int H, int W
   w.hit_cap = (int)L.hit_cap;
   w.max_hits = c->max_hits_per_ray;
   w.ipc = (c->samples <= 128) ? 128 / c->samples : 1;
+  w.S = c->samples;
   w.t_eps = c->t_eps;
   return w;
 }
@@ -548,10 +551,17 @@ mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene
                          cfg->feat_dim > 0 ? d_feat : nullptr, st);
     count_launch(w.n_rays > 0 ? 1 : 0);
   }
-  if (cfg->precision != MLPS_FP32) return MLPS_ERR_UNSUPPORTED;
+  TcPlan P;
+  long long tc_stride = 0;
+  if (cfg->precision == MLPS_BF16) {
+    if (!tc_plan(m, &P, &tc_stride) || !tc_bwd_supported(m, P)) return MLPS_ERR_UNSUPPORTED;
+  } else if (cfg->precision != MLPS_FP32) {
+    return MLPS_ERR_UNSUPPORTED;
+  }
   if (K > 0) {
     StageTimer tm(ST_MLP_BWD, st);
-    cudaError_t e = launch_mlp_bwd_simt(w, a, n_sm, st);
+    cudaError_t e = cfg->precision == MLPS_BF16 ? launch_mlp_bwd_tc(w, a, P, n_sm, st)
+                                                 : launch_mlp_bwd_simt(w, a, n_sm, st);
     if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return MLPS_ERR_CUDA;
     count_launch(1);

@@ -180,6 +180,20 @@ MLPS_DEV void ray_dir_f(const ViewData& V, int x, int y, float d[3]) {
   for (int i = 0; i < 3; ++i) d[i] *= inv;
 }
 
+// One hit interval as the MLP stage consumes it (64 bytes, written in primitive order by the
+// gather stage so that a chunk's intervals are one contiguous block).
+struct IntervalRec {
+  int h;            // hit record index
+  float p[3];       // closest point o' + t_mid d' (normalised frame)
+  float r0, r1;     // t0 - t_mid, t1 - t_mid
+  float dt;         // sample step Delta = (t1 - t0) / S (world units)
+  float tmid;       // t_mid
+  float dp[3];      // d' = M d
+  float d[3];       // unit world ray direction
+  float pad[2];
+};
+static_assert(sizeof(IntervalRec) == 64, "interval record is 64 bytes");
+
 // ------------------------------------------------------------------------------------------
 // Model shape (derived from mlps_config)
 struct Model {
@@ -218,6 +232,7 @@ struct Work {
   int* prim_start;       // [K + 1]
   int* chunk_start;      // [K + 1]
   int* prim_list;        // [cap] hit ids grouped by primitive
+  IntervalRec* rec;      // [cap] interval records in the same (primitive-major) order
   ViewData* views;       // [V]
   PrimGeo* geo;          // [K]
   PrimView* pview;       // [V, K]
@@ -236,6 +251,7 @@ struct Work {
   int hit_cap;
   int max_hits;
   int ipc;               // intervals per MLP chunk
+  int S;                 // samples per interval
   float t_eps;
 };
 

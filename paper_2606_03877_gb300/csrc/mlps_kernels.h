@@ -37,6 +37,9 @@ struct TcPlan {
   int sw_off[kMaxLayers];                  // shared-memory byte offset of layer l's W tile
   int gw_row[kMaxLayers];                  // first 128-byte row of layer l's tile in a blob
   int w_bytes;                             // all forward W tiles
+  int gwt_row[kMaxLayers];                 // first row of layer l's W^T tile (dgrad B operand)
+  int swt_off[kMaxLayers];                 // its shared-memory byte offset (after the W tiles)
+  int wt_bytes;                            // all W^T tiles
   int bias_off[kMaxLayers];                // float offset of layer l's bias
   int bias_floats;
   int gbias_byte;                          // byte offset of the FP32 biases in a blob
@@ -68,6 +71,10 @@ size_t tc_smem_bytes(const TcPlan& P);
 void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
                       void* out, cudaStream_t st);
 cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,
+                              cudaStream_t st);
+// k_mlp_tc_bwd.cu (BF16 tensor-core backward)
+bool tc_bwd_supported(const Model& m, const TcPlan& P);
+cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,
                               cudaStream_t st);
 
 // k_composite.cu

@@ -112,25 +112,20 @@ MLPS_DEV void encode_row(const Model& m, const float xl[3], const float d[3], fl
 MLPS_DEV float sigmoidf_acc(float z) { return 1.0f / (1.0f + expf(-z)); }
 MLPS_DEV float softplusf_acc(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
 
-// Fill the chunk's interval table (one thread per interval).
-MLPS_DEV void load_interval(const Work& w, const Model& m, int prim, int h, IntervalInfo& I) {
-  const int ray = w.hit_ray[h];
-  const int hw = w.H * w.W;
-  const int v = ray / hw, pix = ray - v * hw;
-  const int y = pix / w.W, x = pix - y * w.W;
-  float d[3];
-  ray_dir_f(w.views[v], x, y, d);
-  const PrimGeo& g = w.geo[prim];
-  I.h = h;
+// Fill one entry of a chunk's interval table from its record (slot in primitive order).
+MLPS_DEV void load_interval(const Work& w, const Model& m, int slot, IntervalInfo& I) {
+  (void)m;
+  const IntervalRec& r = w.rec[slot];
+  I.h = r.h;
   for (int i = 0; i < 3; ++i) {
-    I.d[i] = d[i];
-    I.dp[i] = g.Mhi[i * 3] * d[0] + g.Mhi[i * 3 + 1] * d[1] + g.Mhi[i * 3 + 2] * d[2];
-    I.p[i] = w.hit_p[(size_t)i * w.hit_cap + h];
+    I.d[i] = r.d[i];
+    I.dp[i] = r.dp[i];
+    I.p[i] = r.p[i];
   }
-  I.tmid = w.hit_tmid[h];
-  I.r0 = w.hit_r0[h];
-  I.r1 = w.hit_r1[h];
-  I.dt = (I.r1 - I.r0) / (float)m.S;
+  I.tmid = r.tmid;
+  I.r0 = r.r0;
+  I.r1 = r.r1;
+  I.dt = r.dt;
 }
 
 MLPS_DEV int find_prim(const Work& w, int c) {

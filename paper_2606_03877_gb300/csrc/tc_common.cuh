@@ -1,0 +1,108 @@
+// tc_common.cuh -- device helpers shared by the tensor-core MLP kernels: segmented scans over
+// a 128-row epilogue group, BF16 operand-row writers and the angle-doubling encoding.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mlps_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace mlps {
+namespace tc {
+
+constexpr int kM = 128;
+constexpr int kEGThreads = 128;
+constexpr int kMaxScanVals = 4 + kMaxFeat;
+
+// Inclusive segmented scan of NV values over the 128 rows of one epilogue group. Segments
+// are [j*S, (j+1)*S). `scratch` holds 4 warps x NV floats of this group.
+template <int NV>
+MLPS_DEV void seg_scan(float (&v)[NV], int nv, int row, int S, float* scratch, int bar_id) {
+  const int lane = row & 31, wq = row >> 5;
+  const int seg0 = (row / S) * S;
+  const int lo = max(seg0, wq * 32) - wq * 32;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      if (j >= nv) break;
+      const float y = __shfl_up_sync(0xffffffffu, v[j], o);
+      if (lane - o >= lo) v[j] += y;
+    }
+  }
+  if (S <= 32 && (32 % S) == 0) return;  // segments never cross a warp
+  if (lane == 31)
+    for (int j = 0; j < nv; ++j) scratch[wq * NV + j] = v[j];
+  named_bar_sync(bar_id, kEGThreads);
+  if (seg0 < wq * 32)
+    for (int w2 = seg0 / 32; w2 < wq; ++w2)
+      for (int j = 0; j < nv; ++j) v[j] += scratch[w2 * NV + j];
+  named_bar_sync(bar_id, kEGThreads);
+}
+
+MLPS_DEV float sigmoid_fast(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+MLPS_DEV float softplus_fast(float z) { return fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z))); }
+
+struct RowWriter {  // writes one sample row of a K-major swizzled BF16 A tile, two values at a time
+  uint32_t base;
+  int row, col;
+  float pend;
+  MLPS_DEV void put(float v) {
+    if (col & 1) {
+      const int c0 = col - 1;
+      const uint32_t addr = base + (uint32_t)(c0 >> 6) * (kM * 128) + sw128_off(row, (c0 & 63) >> 3) +
+                            (uint32_t)((c0 & 7) >> 1) * 4;
+      st_shared_u32(addr, pack_bf16(pend, v));
+    } else {
+      pend = v;
+    }
+    ++col;
+  }
+  MLPS_DEV void pad_to(int n) {
+    while (col < n) put(0.f);
+  }
+};
+
+// Encoding gamma (Eq. 5) with one sincos per component and angle doubling
+// (sin 2u = 2 sin u cos u, cos 2u = 1 - 2 sin^2 u); arguments pi * p lie in [-pi, pi].
+MLPS_DEV void put_gamma(RowWriter& rw, float p, int L) {
+  float s, c;
+  __sincosf(3.14159265358979f * p, &s, &c);
+  for (int l = 0; l < L; ++l) {
+    rw.put(s);
+    rw.put(c);
+    const float s2 = 2.f * s * c;
+    c = fmaf(-2.f * s, s, 1.f);
+    s = s2;
+  }
+}
+
+
+// Suffix (reverse) segmented scan: v[j] becomes the sum over rows r' >= row of the same segment.
+template <int NV>
+MLPS_DEV void seg_scan_rev(float (&v)[NV], int nv, int row, int S, float* scratch, int bar_id) {
+  const int lane = row & 31, wq = row >> 5;
+  const int seg0 = (row / S) * S;
+  const int seg1 = seg0 + S - 1;                     // last row of the segment
+  const int hi = min(seg1, wq * 32 + 31) - wq * 32;  // last lane of the segment in this warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      if (j >= nv) break;
+      const float y = __shfl_down_sync(0xffffffffu, v[j], o);
+      if (lane + o <= hi) v[j] += y;
+    }
+  }
+  if (S <= 32 && (32 % S) == 0) return;
+  if (lane == 0)
+    for (int j = 0; j < nv; ++j) scratch[wq * NV + j] = v[j];
+  named_bar_sync(bar_id, kEGThreads);
+  if (seg1 > wq * 32 + 31)
+    for (int w2 = wq + 1; w2 <= seg1 / 32; ++w2)
+      for (int j = 0; j < nv; ++j) v[j] += scratch[w2 * NV + j];
+  named_bar_sync(bar_id, kEGThreads);
+}
+
+}  // namespace tc
+}  // namespace mlps

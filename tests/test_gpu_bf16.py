@@ -82,3 +82,72 @@ def test_bf16_full_size_prec_sampled_psnr():
     for v in range(cfg.n_views):
         sel = pix[:, 0] == v
         assert psnr(rgb[sel], rgb_o[sel]) >= 45.0, v
+
+
+# ------------------------------------------------------------------------------------------
+# Backward (tensor-core dgrad / wgrad with TMEM accumulation); bar: relative L2 <= 2e-2 per
+# parameter group against the oracle's reverse mode.
+
+def _bf16_grads(cfg, scene, cams, g_rgb, g_T=None, g_F=None):
+    import torch
+    from paper_2606_03877_gb300.render import Renderer
+    from helpers import to_dev
+    r = Renderer(cfg, precision="bf16")
+    d = to_dev(scene)
+    packed = r.pack(d["weights"])
+    r.forward(d["centers"], d["scales"], d["quats"], packed, cams)
+    g = r.backward(torch.from_numpy(g_rgb).cuda(), None if g_T is None else torch.from_numpy(g_T).cuda(),
+                   None if g_F is None else torch.from_numpy(g_F).cuda())
+    torch.cuda.synchronize()
+    assert r.status() == 0 and r.status("scratch") == 0
+    return {k: v.cpu().numpy() for k, v in g.items()}
+
+
+def _check_bf16_grads(cfg, scene, cams, g_rgb, g_T=None, g_F=None, tol=2e-2):
+    from helpers import rel_l2
+    got = _bf16_grads(cfg, scene, cams, g_rgb, g_T, g_F)
+    pix = oracle.all_pixels(cams)
+    ref = oracle.render_backward(cfg, scene, cams, pix, g_rgb.reshape(-1, 3),
+                                 None if g_T is None else g_T.reshape(-1),
+                                 None if g_F is None else g_F.reshape(-1, cfg.feat_dim))
+    errs = {k: rel_l2(got[k], ref[k]) for k in ("d_weights", "d_centers", "d_scales", "d_quats")}
+    print("bf16 gradient rel-L2:", errs)
+    for k, e in errs.items():
+        assert e < tol, (k, errs)
+    return errs
+
+
+@pytest.mark.parametrize("S", [32, 16, 48])
+def test_bf16_backward_prec_shape(S):
+    cfg = synth.CONFIGS["prec"].replace(width=64, height=48, K=12, n_views=2, samples=S)
+    scene = scaled_scene(cfg, 1, 2.0)
+    cams = synth.make_cameras(cfg, first_view_seed=1)
+    g = synth.make_grad((2, 48, 64, 3), seed=5)
+    gT = synth.make_grad((2, 48, 64), seed=6)
+    _check_bf16_grads(cfg, scene, cams, g, gT)
+
+
+def test_bf16_backward_feature_head():
+    cfg = synth.SceneConfig("f", 40, 32, 10, 1, 6, 4, 64, 2, 8, 16)
+    scene = scaled_scene(cfg, 7, 2.0)
+    cams = synth.make_cameras(cfg, first_view_seed=7)
+    g = synth.make_grad((1, 32, 40, 3), seed=1)
+    gF = synth.make_grad((1, 32, 40, 8), seed=2)
+    _check_bf16_grads(cfg, scene, cams, g, None, gF)
+
+
+def test_bf16_backward_many_chunks_per_primitive():
+    """Enough hits per primitive that each block accumulates many chunks (and several
+    primitive segments) in tensor memory before flushing."""
+    cfg = synth.CONFIGS["prec"].replace(width=320, height=240, K=6, n_views=2)
+    scene = scaled_scene(cfg, 11, 3.0)
+    cams = synth.make_cameras(cfg, first_view_seed=11)
+    pix = synth.sample_pixels(cfg, 1500, seed=4)
+    g = np.zeros((2, 240, 320, 3), np.float32)
+    idx = pixel_index(cfg.width, cfg.height, pix)
+    g.reshape(-1, 3)[idx] = synth.make_grad((len(pix), 3), seed=8)
+    from helpers import rel_l2
+    got = _bf16_grads(cfg, scene, cams, g)
+    ref = oracle.render_backward(cfg, scene, cams, pix, g.reshape(-1, 3)[idx])
+    for k in ("d_weights", "d_centers", "d_scales", "d_quats"):
+        assert rel_l2(got[k], ref[k]) < 2e-2, k
