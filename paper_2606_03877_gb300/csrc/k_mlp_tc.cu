@@ -335,16 +335,6 @@ __global__ void k_pack_bf16(Model m, TcPlan P, long long stride, int K, const fl
       t[((k >> 6) * np + n) * 64 + (k & 63)] = __float2bfloat16_rn(v);
     }
   }
-  // W^T tiles: element (i, o) = W[o][i] at row gwt_row + (o / 64) * kpad + i, column o % 64
-  for (int l = 0; l < m.nl; ++l) {
-    const int kp = P.kpad[l], ncols = ((P.npad[l] + 63) / 64) * 64;
-    __nv_bfloat16* t = reinterpret_cast<__nv_bfloat16*>(d + (size_t)P.gwt_row[l] * 128);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kp * ncols; e += gridDim.x * blockDim.x) {
-      const int i = e / ncols, o = e - i * ncols;
-      const float v = (i < m.din[l] && o < m.dout[l]) ? s[m.woff[l] + o * m.din[l] + i] : 0.f;
-      t[((o >> 6) * kp + i) * 64 + (o & 63)] = __float2bfloat16_rn(v);
-    }
-  }
   float* b = reinterpret_cast<float*>(d + P.gbias_byte);
   for (int l = 0; l < m.nl; ++l)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.npad[l]; i += gridDim.x * blockDim.x)
@@ -376,16 +366,9 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride) {
     kmax = kmax > P->kpad[l] ? kmax : P->kpad[l];
   }
   P->w_bytes = sw;
-  // W^T tiles for the backward pass: [N = kpad (inputs)] x [K = npad (outputs)], 64-column slabs
-  int swt = 0;
-  for (int l = 0; l < m.nl; ++l) {
-    P->gwt_row[l] = rows;
-    const int kslabs = (P->npad[l] + 63) / 64;
-    rows += kslabs * P->kpad[l];
-    P->swt_off[l] = swt;
-    swt += kslabs * P->kpad[l] * 128;
-  }
-  P->wt_bytes = swt;
+  // the backward pass reads the same W tiles as MN-major operands: no transposed copies
+  for (int l = 0; l < m.nl; ++l) { P->gwt_row[l] = 0; P->swt_off[l] = 0; }
+  P->wt_bytes = 0;
   P->bias_floats = bias;
   P->gbias_byte = rows * 128;
   const long long bytes = (long long)rows * 128 + 4LL * bias;

@@ -4,7 +4,8 @@
 // group (4 warps, thread = sample row) and the MMA warp run 2 * nl phases:
 //   F_l  (l = 0 .. nl-1): Z_l = H_l W_l^T recomputes the forward; the epilogue writes
 //        H_{l+1} = ReLU(Z_l + b_l) as BF16 into the group's tile T_{l+1};
-//   B_l  (l = nl-1 .. 0): dgrad  G = delta_l W_l          (A = delta_l, K-major; B = W_l^T tile)
+//   B_l  (l = nl-1 .. 0): dgrad  G = delta_l W_l          (A = delta_l, K-major; B = the forward
+//                                W_l tile read MN-major)
 //                         wgrad  dW_l^T += H_l^T delta_l  (A = H_l, B = delta_l, both read as
 //                                MN-major views of the same swizzled tiles; M = 128: the 64
 //                                input features of H_l plus a constant "ones" atom, so that
@@ -59,10 +60,9 @@ MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F) {
   L.w = o;
   o = al(o + P.w_bytes, 1024);
   L.wt = o;
-  o = al(o + P.wt_bytes, 1024);
   for (int g = 0; g < kNG; ++g) {
     L.tiles[g] = o;
-    o = al(o + (uint32_t)P.nl * kTile, 1024);
+    o = al(o + (uint32_t)P.nl * kTile, 1024);  // T_0 .. T_{nl-1}
   }
   L.ones = o;  // above every group tile: the wgrad descriptors reach it with a positive offset
   o = al(o + kTile, 1024);
@@ -246,19 +246,13 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       if (loaded >= 0) flush(loaded);
       __syncthreads();
       if (threadIdx.x == kMmaWarpB * 32 && !*sAbort) {
-        mbar_arrive_expect_tx(bar_w, (uint32_t)(P.w_bytes + P.wt_bytes));
+        mbar_arrive_expect_tx(bar_w, (uint32_t)P.w_bytes);
         const int row0 = prim * P.rows_per_prim;
-        for (int l = 0; l < nl; ++l) {
+        for (int l = 0; l < nl; ++l)
           for (int sl = 0; sl < P.kpad[l] / 64; ++sl)
             for (int j = 0; j < P.npad[l] / 16; ++j)
               tma_load_2d(sbase + L.w + P.sw_off[l] + sl * P.npad[l] * 128 + j * 2048, &tmap, 0,
                           row0 + P.gw_row[l] + sl * P.npad[l] + j * 16, bar_w);
-          const int ks = (P.npad[l] + 63) / 64;
-          for (int sl = 0; sl < ks; ++sl)
-            for (int j = 0; j < P.kpad[l] / 16; ++j)
-              tma_load_2d(sbase + L.wt + P.swt_off[l] + sl * P.kpad[l] * 128 + j * 2048, &tmap, 0,
-                          row0 + P.gwt_row[l] + sl * P.kpad[l] + j * 16, bar_w);
-        }
       }
       const float* gbias = reinterpret_cast<const float*>(a.weights + (size_t)prim * a.pk.stride + P.gbias_byte);
       for (int i = threadIdx.x; i < P.bias_floats; i += kThreadsB) sBias[i] = gbias[i];
@@ -551,12 +545,13 @@ __global__ void __launch_bounds__(kThreadsB, 1)
               const int l = 2 * nl - 1 - ph;  // B_l
               const uint32_t Dl = tiles + (uint32_t)(l == nl - 1 ? 0 : l + 1) * kTile;  // delta_l
               const uint32_t Hl = tiles + (uint32_t)l * kTile;                          // H_l
-              // dgrad: G = delta_l W_l, K = npad[l] (outputs), N = kpad[l] (inputs)
-              const uint32_t Bt = sbase + L.wt + P.swt_off[l];
-              const uint32_t id_d = idesc_bf16(kM, P.kpad[l]);
+              // dgrad: G = delta_l W_l with K = npad[l] (outputs), N = kpad[l] (inputs); B is the
+              // forward W_l tile read as an MN-major operand (inputs contiguous, outputs = K rows)
+              const uint32_t Wl = sbase + L.w + P.sw_off[l];
+              const uint32_t id_d = idesc_bf16(kM, P.kpad[l]) | (1u << 16);
               for (int kk = 0; kk < P.npad[l] / 16; ++kk)
-                mma_bf16(acc, sw128_desc(Dl + (uint32_t)(kk & 3) * 32), sw128_desc(Bt + (uint32_t)(kk & 3) * 32),
-                         id_d, kk > 0 ? 1u : 0u);
+                mma_bf16(acc, sw128_desc(Dl + (uint32_t)(kk & 3) * 32),
+                         sw128_desc_mn(Wl + (uint32_t)kk * 2048, 16), id_d, kk > 0 ? 1u : 0u);
               // wgrad: dW_l^T[in(+ones)][out] += H_l^T delta_l over the 128 rows
               const uint32_t id_w = idesc_bf16(kM, 64) | (1u << 15) | (1u << 16);
               const uint32_t lbo = (sbase + L.ones) - Hl;

@@ -37,9 +37,9 @@ struct TcPlan {
   int sw_off[kMaxLayers];                  // shared-memory byte offset of layer l's W tile
   int gw_row[kMaxLayers];                  // first 128-byte row of layer l's tile in a blob
   int w_bytes;                             // all forward W tiles
-  int gwt_row[kMaxLayers];                 // first row of layer l's W^T tile (dgrad B operand)
-  int swt_off[kMaxLayers];                 // its shared-memory byte offset (after the W tiles)
-  int wt_bytes;                            // all W^T tiles
+  int gwt_row[kMaxLayers];                 // unused (0): the backward reads the W tiles MN-major
+  int swt_off[kMaxLayers];                 // unused (0)
+  int wt_bytes;                            // 0
   int bias_off[kMaxLayers];                // float offset of layer l's bias
   int bias_floats;
   int gbias_byte;                          // byte offset of the FP32 biases in a blob
