@@ -170,6 +170,27 @@ mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene
                                  float* d_scales, float* d_quats, void* scratch,
                                  size_t scratch_bytes, void* stream);
 
+/* Forward render like mlps_render_forward, for callers that cannot allocate device memory
+ * (for example code whose device memory belongs to another allocator, or a frame loop that must
+ * not call cudaMalloc / cudaFree because they can synchronise the device or fail mid-frame).
+ * The paper has no counterpart; this is a convenience of this library.
+ * Instead of caller-provided `saved` / `scratch` buffers it uses one fixed workspace of 32 MiB
+ * held in a static device array of the library (every GPU that loads the library keeps it
+ * until the process exits). Renders whose mlps_workspace_size() total (saved rounded up to 256
+ * bytes, plus scratch) exceeds 32 MiB are rejected with MLPS_ERR_WORKSPACE_TOO_SMALL before
+ * anything is enqueued. It allocates nothing and calls no allocating routine.
+ * The first call on a device looks up the array's device address with that device current;
+ * make that first call before any stream capture. All calls share the one array and it keeps
+ * the last call's contents (each call clears what it needs), so calls that overlap on the GPU
+ * (other streams, other host threads) race; serialise them. There is no backward pass for this
+ * variant. If `device_status` (device pointer, may be NULL) is given, the call's device status
+ * word (MLPS_OK or the device-detected error, as mlps_read_status would return) is copied
+ * there asynchronously on `stream` at the end of the call. */
+mlps_status mlps_render_forward_static(const mlps_config* cfg, const mlps_scene* scene,
+                                       const mlps_camera* cams, int32_t n_views, float* rgb,
+                                       float* trans, float* feat, int32_t* device_status,
+                                       void* stream);
+
 /* Synchronise `stream`, return the device status word of a `saved` or `scratch` region
  * written by the calls above (MLPS_OK if none), and clear it. */
 mlps_status mlps_read_status(const void* region, void* stream);

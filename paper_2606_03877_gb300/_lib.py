@@ -83,6 +83,8 @@ _SIGS = [
     ("mlps_render_backward", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _P(MlpsCamera),
                                               ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                               _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    ("mlps_render_forward_static", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _P(MlpsCamera),
+                                                    ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
     ("mlps_read_status", ctypes.c_int32, [_vp, _vp]),
     ("mlps_saved_hit_count", ctypes.c_int32, [_vp, _P(ctypes.c_int64), _vp]),
     ("mlps_export_hits", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsCamera), ctypes.c_int32, _vp,
@@ -210,6 +212,13 @@ def mlps_render_backward(cfg, scene: MlpsScene, cams, n_views, d_rgb, d_trans, d
         ctypes.byref(cfg), ctypes.byref(scene), cams, int(n_views), _ptr(d_rgb), _ptr(d_trans), _ptr(d_feat),
         _ptr(saved), int(saved_bytes), _ptr(d_weights), _ptr(d_centers), _ptr(d_scales), _ptr(d_quats),
         _ptr(scratch), int(scratch_bytes), stream or None))
+
+
+def mlps_render_forward_static(cfg, scene: MlpsScene, cams, n_views, rgb, trans, feat,
+                               device_status=None, stream: int = 0):
+    _check("mlps_render_forward_static", load().mlps_render_forward_static(
+        ctypes.byref(cfg), ctypes.byref(scene), cams, int(n_views), _ptr(rgb), _ptr(trans), _ptr(feat),
+        _ptr(device_status), stream or None))
 
 
 def mlps_read_status(region, stream: int = 0) -> int:
