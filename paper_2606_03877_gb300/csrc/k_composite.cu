@@ -41,7 +41,9 @@ __global__ void k_composite_fwd(Work w, int F, float* __restrict__ rgb, float* _
 // Reverse pass. With C = sum_j T_j C_j, T_final = exp(-sum_j a_j):
 //   dL/dC_j = T_j dL/dC,   dL/dF_j = T_j dL/dF,
 //   dL/da_j = -dL/dC . sum_{l>j} T_l C_l - dL/dF . sum_{l>j} T_l F_l - dL/dT_final T_final.
-// Intervals skipped by early termination get zero gradient.
+// Intervals skipped by early termination get zero gradient. The per-interval gradients are
+// written in the primitive-major order of the interval records, so that the MLP backward
+// reads one contiguous block per chunk.
 __global__ void k_composite_bwd(Work w, int F, const float* __restrict__ d_rgb,
                                 const float* __restrict__ d_trans,
                                 const float* __restrict__ d_feat) {
@@ -72,10 +74,11 @@ __global__ void k_composite_bwd(Work w, int F, const float* __restrict__ d_rgb,
     const float T = expf(-Aex[j]);
     float ga = -(g0 * R0 + g1 * R1 + g2 * R2) - gT * Tfin;
     for (int f = 0; f < F; ++f) ga -= gF[f] * RF[f];
-    w.hit_grad[h] = make_float4(T * g0, T * g1, T * g2, ga);
+    const int sl = w.slot_of[h];
+    w.hit_grad[sl] = make_float4(T * g0, T * g1, T * g2, ga);
     for (int f = 0; f < F; ++f) {
       const float Fj = w.hit_feat[(size_t)h * F + f];
-      w.hit_gfeat[(size_t)h * F + f] = T * gF[f];
+      w.hit_gfeat[(size_t)sl * F + f] = T * gF[f];
       RF[f] = fmaf(T, Fj, RF[f]);
     }
     R0 = fmaf(T, o.x, R0);
@@ -83,8 +86,9 @@ __global__ void k_composite_bwd(Work w, int F, const float* __restrict__ d_rgb,
     R2 = fmaf(T, o.z, R2);
   }
   for (int j = used; j < n; ++j) {
-    w.hit_grad[s + j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int f = 0; f < F; ++f) w.hit_gfeat[(size_t)(s + j) * F + f] = 0.f;
+    const int sl = w.slot_of[s + j];
+    w.hit_grad[sl] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int f = 0; f < F; ++f) w.hit_gfeat[(size_t)sl * F + f] = 0.f;
   }
 }
 

@@ -436,6 +436,7 @@ __global__ void k_scatter(Work w) {
     }
     const int slot = w.prim_start[p] + off + rank;
     w.prim_list[slot] = h;
+    w.slot_of[h] = slot;
     // the interval record: everything the MLP stage needs, contiguous per chunk
     const int ray = w.hit_ray[h];
     const int hw = w.H * w.W;

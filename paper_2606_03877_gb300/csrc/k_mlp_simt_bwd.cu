@@ -319,9 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
       if (threadIdx.x < nint) {
         const int slot = w.prim_start[prim] + first + i0 + threadIdx.x;
         load_interval(w, m, slot, sI[threadIdx.x]);
-        const int h = sI[threadIdx.x].h;
-        sGrad[threadIdx.x] = w.hit_grad[h];
-        for (int f = 0; f < F; ++f) sGF[threadIdx.x * F + f] = w.hit_gfeat[(size_t)h * F + f];
+        sGrad[threadIdx.x] = w.hit_grad[slot];
+        for (int f = 0; f < F; ++f) sGF[threadIdx.x * F + f] = w.hit_gfeat[(size_t)slot * F + f];
       }
       __syncthreads();
       // 1. encode the samples into the input of layer 0

@@ -61,7 +61,7 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P) {
   off = align_up(off + 4 * P.bias_floats, 16);
   for (int g = 0; g < kNEG; ++g) {
     L.itab[g] = off;
-    off = align_up(off + (uint32_t)sizeof(IntervalInfo) * kM, 16);
+    off = align_up(off + (uint32_t)sizeof(IntervalRec) * kM, 16);
   }
   L.scan = off;
   off = align_up(off + 4 * kNEG * 4 * kMaxScanVals, 16);
@@ -73,7 +73,7 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P) {
   return L;
 }
 
-template <int WIDTH>
+template <int WIDTH, int XL, int DL>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_mlp_fwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -125,15 +125,19 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   int prim = cb < ce ? simt::find_prim(w, cb) : 0;
   int nissued = 0;
 
-  for (int c = cb; c < ce;) {
-    while (c >= w.chunk_start[prim + 1]) ++prim;
-    int cc[kNEG];
-    int nstep = 0;
-    for (int j = 0; j < kNEG; ++j) {
-      const int cj = c + j;
-      cc[j] = (cj < ce && cj < w.chunk_start[prim + 1]) ? cj : -1;
-      nstep += cc[j] >= 0;
-    }
+  ChunkStep<kNEG> cur = chunk_step<kNEG>(w, cb, ce, prim);
+  RecPrefetch pre;
+  pre.valid = 0;
+  if (warp < kMmaWarp && cur.n > 0 && cur.cc[g] >= 0) {
+    const int f0 = (cur.cc[g] - w.chunk_start[cur.prim]) * w.ipc;
+    if (row < min(w.ipc, w.prim_count[cur.prim] - f0)) rec_prefetch(w, w.prim_start[cur.prim] + f0 + row, false, pre);
+  }
+  while (cur.c0 < ce) {
+    prim = cur.prim;
+    const ChunkStep<kNEG> nxt = chunk_step<kNEG>(w, cur.c0 + cur.n, ce, prim);
+    const int* cc = cur.cc;
+    const int nstep = cur.n;
+    const int c = cur.c0;
     if (prim != loaded) {
       __syncthreads();  // every role is done with the previous primitive's tiles
       if (threadIdx.x == kMmaWarp * 32 && !*sAbort) {
@@ -155,23 +159,49 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 
     if (warp < kMmaWarp) {
       // ------------------------------------------------------------ epilogue group g
+      if (cc[g] < 0 && nxt.n > 0 && nxt.cc[g] >= 0) {  // idle this step: still prefetch
+        const int f1 = (nxt.cc[g] - w.chunk_start[nxt.prim]) * w.ipc;
+        if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
+          rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, false, pre);
+      }
       if (cc[g] >= 0) {
         const int bar_id = 1 + g;
-        IntervalInfo* T = reinterpret_cast<IntervalInfo*>(gbase + L.itab[g]);
+        IntervalRec* T = reinterpret_cast<IntervalRec*>(gbase + L.itab[g]);
         const int first = (cc[g] - w.chunk_start[prim]) * w.ipc;
         const int nint = min(w.ipc, w.prim_count[prim] - first);
         // every warp of the group is done with the previous chunk's interval table
         named_bar_sync(bar_id, kEGThreads);
-        if (row < nint)
-          simt::load_interval(w, m, w.prim_start[prim] + first + row, T[row]);
+        if (row < nint) rec_store(pre, T, row);  // prefetched during the previous step
         named_bar_sync(bar_id, kEGThreads);
+        pre.valid = 0;
+        if (nxt.n > 0 && nxt.cc[g] >= 0) {  // start loading the next chunk's records now
+          const int f1 = (nxt.cc[g] - w.chunk_start[nxt.prim]) * w.ipc;
+          if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
+            rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, false, pre);
+        }
         const uint32_t A = sbase + L.a[g];
         const int iv = row / S, k = row - iv * S;
         const bool valid = iv < nint;
-        {
+        if (XL >= 0) {
+          // compile-time encoding (the configurations' shapes)
+          uint32_t pk[32];
+          if (valid) {
+            const IntervalRec& I = T[iv];
+            const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+            float xl[3], dd[3];
+            for (int u = 0; u < 3; ++u) { xl[u] = fmaf(tr, I.dp[u], I.p[u]); dd[u] = I.d[u]; }
+            encode_pairs64<(XL > 0 ? XL : 0), (DL > 0 ? DL : 0)>(xl, dd, pk);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) pk[e] = 0u;
+          }
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch)
+            st_shared_v4(A + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+        } else {
           RowWriter rw{A, row, 0, 0.f};
           if (valid) {
-            const IntervalInfo& I = T[iv];
+            const IntervalRec& I = T[iv];
             const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
             float xl[3];
             for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
@@ -298,7 +328,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
       }
     }
-    c += nstep;
+    (void)c; (void)nstep;
+    cur = nxt;
   }
 
   // teardown: make sure no MMA is still writing TMEM, then free it
@@ -415,22 +446,17 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const size_t smem = tc_smem_bytes(P);
   if (smem > 227 * 1024) return cudaErrorNotSupported;
-  switch (a.m.width) {
-#define MLPS_CASE(WID)                                                                        \
-  case WID: {                                                                                 \
-    auto kern = tc::k_mlp_fwd_tc<WID>;                                                        \
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                         (int)smem);                                          \
-    if (e != cudaSuccess) return e;                                                           \
-    kern<<<n_sm, tc::kThreadsTC, smem, st>>>(w, a, P, tmap);                                  \
-    return cudaGetLastError();                                                                \
-  }
-    MLPS_CASE(64)
-    MLPS_CASE(128)
-#undef MLPS_CASE
-    default:
-      return cudaErrorNotSupported;
-  }
+  const int xl = a.m.xyzL, dl = a.m.dirL;
+  const bool fast64 = xl == 6 && dl == 4 && P.kpad[0] == 64;
+  const bool raw = xl == 0 && dl == 0 && P.kpad[0] == 64;
+  decltype(&tc::k_mlp_fwd_tc<64, 6, 4>) kern;
+  if (a.m.width == 64) kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4> : raw ? tc::k_mlp_fwd_tc<64, 0, 0> : tc::k_mlp_fwd_tc<64, -1, -1>;
+  else if (a.m.width == 128) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4> : raw ? tc::k_mlp_fwd_tc<128, 0, 0> : tc::k_mlp_fwd_tc<128, -1, -1>;
+  else return cudaErrorNotSupported;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<n_sm, tc::kThreadsTC, smem, st>>>(w, a, P, tmap);
+  return cudaGetLastError();
 }
 
 }  // namespace mlps

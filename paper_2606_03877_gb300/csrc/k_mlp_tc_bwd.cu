@@ -70,7 +70,7 @@ MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F) {
   o = al(o + 4 * P.bias_floats, 16);
   for (int g = 0; g < kNG; ++g) {
     L.itab[g] = o;
-    o = al(o + (uint32_t)sizeof(IntervalInfo) * kM, 16);
+    o = al(o + (uint32_t)sizeof(IntervalRec) * kM, 16);
     L.giv[g] = o;
     o = al(o + 16 * kM, 16);
     L.ddel[g] = o;
@@ -117,13 +117,32 @@ MLPS_DEV void ld_shared_v4(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c,
 }
 
 // Build the encoded input row (Eq. 5) of one sample into tile `A` (zeros for invalid rows).
-MLPS_DEV void build_row(const Model& m, const IntervalInfo* T, int nint, int row, uint32_t A,
+template <int XL, int DL>
+MLPS_DEV void build_row_fast(const IntervalRec* T, int nint, int S, int row, uint32_t A) {
+  const int iv = row / S, k = row - iv * S;
+  uint32_t pk[32];
+  if (iv < nint) {
+    const IntervalRec& I = T[iv];
+    const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+    float xl[3], d[3];
+    for (int u = 0; u < 3; ++u) { xl[u] = fmaf(tr, I.dp[u], I.p[u]); d[u] = I.d[u]; }
+    encode_pairs64<XL, DL>(xl, d, pk);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 32; ++e) pk[e] = 0u;
+  }
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch)
+    st_shared_v4(A + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+}
+
+MLPS_DEV void build_row(const Model& m, const IntervalRec* T, int nint, int row, uint32_t A,
                         int kpad0) {
   const int S = m.S;
   const int iv = row / S, k = row - iv * S;
   RowWriter rw{A, row, 0, 0.f};
   if (iv < nint) {
-    const IntervalInfo& I = T[iv];
+    const IntervalRec& I = T[iv];
     const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
     float xl[3];
     for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
@@ -140,7 +159,7 @@ MLPS_DEV void build_row(const Model& m, const IntervalInfo* T, int nint, int row
 
 }  // namespace
 
-template <int NF, int XL>
+template <int NF, int XL, int DL>
 __global__ void __launch_bounds__(kThreadsB, 1)
     k_mlp_bwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -231,15 +250,17 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     }
   };
 
-  for (int c = cb; c < ce;) {
-    while (c >= w.chunk_start[prim + 1]) ++prim;
-    int cc[kNG];
-    int nstep = 0;
-    for (int j = 0; j < kNG; ++j) {
-      const int cj = c + j;
-      cc[j] = (cj < ce && cj < w.chunk_start[prim + 1]) ? cj : -1;
-      nstep += cc[j] >= 0;
-    }
+  ChunkStep<kNG> cur = chunk_step<kNG>(w, cb, ce, prim);
+  RecPrefetch pre;
+  pre.valid = 0;
+  if (warp < kMmaWarpB && cur.n > 0 && cur.cc[g] >= 0) {
+    const int f0 = (cur.cc[g] - w.chunk_start[cur.prim]) * w.ipc;
+    if (row < min(w.ipc, w.prim_count[cur.prim] - f0)) rec_prefetch(w, w.prim_start[cur.prim] + f0 + row, true, pre);
+  }
+  while (cur.c0 < ce) {
+    prim = cur.prim;
+    const ChunkStep<kNG> nxt = chunk_step<kNG>(w, cur.c0 + cur.n, ce, prim);
+    const int* cc = cur.cc;
     if (prim != loaded) {
       tc_fence_before();
       __syncthreads();
@@ -265,9 +286,14 @@ __global__ void __launch_bounds__(kThreadsB, 1)
 
     if (warp < kMmaWarpB) {
       // ============================================================ epilogue group g
+      if (cc[g] < 0 && nxt.n > 0 && nxt.cc[g] >= 0) {  // idle this step: still prefetch
+        const int f1 = (nxt.cc[g] - w.chunk_start[nxt.prim]) * w.ipc;
+        if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
+          rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, true, pre);
+      }
       if (cc[g] >= 0) {
         const int bar_id = 1 + g;
-        IntervalInfo* T = reinterpret_cast<IntervalInfo*>(gb + L.itab[g]);
+        IntervalRec* T = reinterpret_cast<IntervalRec*>(gb + L.itab[g]);
         float4* GI = reinterpret_cast<float4*>(gb + L.giv[g]);
         float* DD = reinterpret_cast<float*>(gb + L.ddel[g]);
         float* GF = reinterpret_cast<float*>(gb + L.gf[g]);
@@ -275,19 +301,26 @@ __global__ void __launch_bounds__(kThreadsB, 1)
         const int nint = min(w.ipc, w.prim_count[prim] - first);
         named_bar_sync(bar_id, kEGThreads);
         if (row < nint) {
-          simt::load_interval(w, m, w.prim_start[prim] + first + row, T[row]);
-          const int h = T[row].h;
-          GI[row] = w.hit_grad[h];
-          for (int f = 0; f < F; ++f) GF[row * F + f] = w.hit_gfeat[(size_t)h * F + f];
+          rec_store(pre, T, row);  // prefetched during the previous step
+          GI[row] = pre.g;
+          const size_t slot = (size_t)w.prim_start[prim] + first + row;
+          for (int f = 0; f < F; ++f) GF[row * F + f] = w.hit_gfeat[slot * F + f];
         }
         named_bar_sync(bar_id, kEGThreads);
+        pre.valid = 0;
+        if (nxt.n > 0 && nxt.cc[g] >= 0) {  // start loading the next chunk's records now
+          const int f1 = (nxt.cc[g] - w.chunk_start[nxt.prim]) * w.ipc;
+          if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
+            rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, true, pre);
+        }
         const uint32_t tiles = sbase + L.tiles[g];
         auto tileaddr = [&](int i) { return tiles + (uint32_t)i * kTile; };
         const int iv = row / S, k = row - iv * S;
         const bool valid = iv < nint;
         const uint32_t trow = tmem + (uint32_t)(g * 64) + ((uint32_t)(q * 32) << 16);
 
-        build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+        if (DL >= 0) build_row_fast<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
+        else build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
         fence_proxy_async_smem();
         tc_fence_before();
         mbar_arrive(bar_ready(g));
@@ -346,7 +379,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
               }
             }
             tc_fence_before();
-            const IntervalInfo& I = T[valid ? iv : 0];
+            const IntervalRec& I = T[valid ? iv : 0];
             const float dt = valid ? I.dt : 0.f;
             const float sig = softplus_fast(z[3]);
             const float ak = valid ? sig * dt : 0.f;
@@ -431,7 +464,10 @@ __global__ void __launch_bounds__(kThreadsB, 1)
               }
             }
             store_row64(Tl, row, pk);
-            if (l == 1) build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+            if (l == 1) {
+              if (DL >= 0) build_row_fast<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
+              else build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+            }
             fence_proxy_async_smem();
             tc_fence_before();
             mbar_arrive(bar_ready(g));
@@ -456,7 +492,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
 #pragma unroll
             for (int e = 0; e < 14; ++e) red[e] = 0.f;
             if (valid) {
-              const IntervalInfo& I = T[iv];
+              const IntervalRec& I = T[iv];
               const PrimGeo& Gp = w.geo[prim];
               const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
               float xl[3], gx[3] = {0.f, 0.f, 0.f};
@@ -494,7 +530,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
             }
             seg_scan<14>(red, 14, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
             if (valid && k == S - 1) {
-              const IntervalInfo& I = T[iv];
+              const IntervalRec& I = T[iv];
               const PrimGeo& Gp = w.geo[prim];
               const float dDelta = DD[iv];
               float gt0 = red[12] - dDelta / (float)S, gt1 = red[13] + dDelta / (float)S;
@@ -567,7 +603,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
         }
       }
     }
-    c += nstep;
+    cur = nxt;
   }
   // final flush and teardown
   if (warp == kMmaWarpB && lane == 0) {
@@ -628,8 +664,15 @@ cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const size_t smem = tc::bwd_layout(P, a.m.F).total + 1024;
-  auto kern = a.m.F > 0 ? (a.m.xyzL == 6 ? tc::k_mlp_bwd_tc<12, 6> : tc::k_mlp_bwd_tc<12, 0>)
-                        : (a.m.xyzL == 6 ? tc::k_mlp_bwd_tc<0, 6> : tc::k_mlp_bwd_tc<0, 0>);
+  // compile-time encodings for the configurations' shapes (xyz L = 6 with dir L = 4, raw xyz
+  // without direction); anything else builds rows through the generic writer (DL = -1)
+  const bool f = a.m.F > 0;
+  const int xl = a.m.xyzL, dl = a.m.dirL;
+  decltype(&tc::k_mlp_bwd_tc<0, 6, 4>) kern;
+  if (xl == 6 && dl == 4) kern = f ? tc::k_mlp_bwd_tc<12, 6, 4> : tc::k_mlp_bwd_tc<0, 6, 4>;
+  else if (xl == 0 && dl == 0) kern = f ? tc::k_mlp_bwd_tc<12, 0, 0> : tc::k_mlp_bwd_tc<0, 0, 0>;
+  else if (xl == 6) kern = f ? tc::k_mlp_bwd_tc<12, 6, -1> : tc::k_mlp_bwd_tc<0, 6, -1>;
+  else kern = f ? tc::k_mlp_bwd_tc<12, 0, -1> : tc::k_mlp_bwd_tc<0, 0, -1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<n_sm, tc::kThreadsB, smem, st>>>(w, a, P, tmap);

@@ -161,7 +161,8 @@ struct Carve {
 struct Layout {
   // saved
   size_t hit_prim, hit_ray, hit_tmid, hit_r0, hit_r1, hit_p, hit_out, hit_feat, ray_start,
-      ray_count, prim_count, prim_start, chunk_start, prim_list, rec, views, geo, pview, saved_total;
+      ray_count, prim_count, prim_start, chunk_start, prim_list, rec, slot_of, views, geo, pview,
+      saved_total;
   // scratch
   size_t prim_cursor, tile_count, tile_list, hit_grad, hit_gfeat, dgeo, scratch_total;
   long long hit_cap;
@@ -197,6 +198,7 @@ bool make_layout(const mlps_config* c, int K, int V, int H, int W, Layout* L) {
   L->chunk_start = s.take<int>((size_t)K + 1);
   L->prim_list = s.take<int>(hc);
   L->rec = s.take<IntervalRec>(hc);
+  L->slot_of = s.take<int>(hc);
   L->views = s.take<ViewData>((size_t)V);
   L->geo = s.take<PrimGeo>((size_t)K + 1);
   L->pview = s.take<PrimView>((size_t)V * K + 1);
@@ -234,6 +236,7 @@ Work make_work(const mlps_config* c, const Layout& L, int K, int V, int H, int W
   w.chunk_start = reinterpret_cast<int*>(sv + L.chunk_start);
   w.prim_list = reinterpret_cast<int*>(sv + L.prim_list);
   w.rec = reinterpret_cast<IntervalRec*>(sv + L.rec);
+  w.slot_of = reinterpret_cast<int*>(sv + L.slot_of);
   w.views = reinterpret_cast<ViewData*>(sv + L.views);
   w.geo = reinterpret_cast<PrimGeo*>(sv + L.geo);
   w.pview = reinterpret_cast<PrimView*>(sv + L.pview);

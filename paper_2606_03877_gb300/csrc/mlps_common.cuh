@@ -233,6 +233,7 @@ struct Work {
   int* chunk_start;      // [K + 1]
   int* prim_list;        // [cap] hit ids grouped by primitive
   IntervalRec* rec;      // [cap] interval records in the same (primitive-major) order
+  int* slot_of;          // [cap] hit index -> position in that order
   ViewData* views;       // [V]
   PrimGeo* geo;          // [K]
   PrimView* pview;       // [V, K]
@@ -241,8 +242,8 @@ struct Work {
   int* prim_cursor;      // [K]
   int* tile_count;       // [V, n_tiles]
   int* tile_list;        // [V, n_tiles, K]
-  float4* hit_grad;      // [cap] (dL/dC_j, dL/da_j) per interval
-  float* hit_gfeat;      // [cap, F]
+  float4* hit_grad;      // [cap] (dL/dC_j, dL/da_j) per interval, in primitive-major order
+  float* hit_gfeat;      // [cap, F], same order
   float* dgeo;           // [K, 12] dL/dM (9) and dL/dmu (3)
   // sizes
   int K, V, H, W;

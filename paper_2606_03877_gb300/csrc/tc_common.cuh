@@ -104,5 +104,100 @@ MLPS_DEV void seg_scan_rev(float (&v)[NV], int nv, int row, int S, float* scratc
   named_bar_sync(bar_id, kEGThreads);
 }
 
+// One step of a block's chunk schedule: up to NG consecutive chunks of the same primitive,
+// one per epilogue group. Every role evaluates the same schedule.
+template <int NG>
+struct ChunkStep {
+  int c0, prim, n;
+  int cc[NG];
+};
+
+template <int NG>
+MLPS_DEV ChunkStep<NG> chunk_step(const Work& w, int c, int ce, int prim) {
+  ChunkStep<NG> s;
+  s.c0 = c;
+  s.n = 0;
+  if (c < ce)
+    while (c >= w.chunk_start[prim + 1]) ++prim;
+  s.prim = prim;
+#pragma unroll
+  for (int j = 0; j < NG; ++j) {
+    const int cj = c + j;
+    s.cc[j] = (cj < ce && cj < w.chunk_start[prim + 1]) ? cj : -1;
+    s.n += s.cc[j] >= 0;
+  }
+  return s;
+}
+
+// Interval record (and, for the backward pass, its gradient) of one chunk row, loaded one
+// chunk ahead into registers.
+struct RecPrefetch {
+  float4 v[4];
+  float4 g;
+  int valid;
+};
+
+MLPS_DEV void rec_store(const RecPrefetch& r, IntervalRec* T, int row) {
+  float4* dst = reinterpret_cast<float4*>(T + row);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) dst[i] = r.v[i];
+}
+
+MLPS_DEV void rec_prefetch(const Work& w, int slot, bool want_grad, RecPrefetch& r) {
+  // independent loads only: they stay in flight while the current chunk is processed
+  const float4* src = reinterpret_cast<const float4*>(w.rec + slot);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.v[i] = __ldg(src + i);
+  r.valid = 1;
+  if (want_grad) r.g = w.hit_grad[slot];
+}
+
+// Encoded input row (Eq. 5) with the frequency counts known at compile time: all values are
+// produced in registers, packed to BF16 pairs and written with 16-byte stores. XL = 0 means the
+// raw local position; DL = 0 means no direction input. Columns past the encoding are zero.
+template <int XL, int DL>
+MLPS_DEV void encode_pairs64(const float (&xl)[3], const float (&d)[3], uint32_t (&pk)[32]) {
+  constexpr int NX = XL > 0 ? 6 * XL : 3;
+  constexpr int NIN = NX + (DL > 0 ? 6 * DL : 0);
+  static_assert(NIN <= 64, "encoded input wider than one 64-column tile");
+  float v[64];
+#pragma unroll
+  for (int j = 0; j < 64; ++j) v[j] = 0.f;
+  if (XL == 0) {
+    v[0] = xl[0]; v[1] = xl[1]; v[2] = xl[2];
+  } else {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      float s, c;
+      __sincosf(3.14159265358979f * xl[u], &s, &c);
+#pragma unroll
+      for (int l = 0; l < (XL > 0 ? XL : 1); ++l) {
+        v[2 * (u * XL + l)] = s;
+        v[2 * (u * XL + l) + 1] = c;
+        const float s2 = 2.f * s * c;
+        c = fmaf(-2.f * s, s, 1.f);
+        s = s2;
+      }
+    }
+  }
+  if (DL > 0) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      float s, c;
+      __sincosf(3.14159265358979f * d[u], &s, &c);
+#pragma unroll
+      for (int l = 0; l < (DL > 0 ? DL : 1); ++l) {
+        v[NX + 2 * (u * DL + l)] = s;
+        v[NX + 2 * (u * DL + l) + 1] = c;
+        const float s2 = 2.f * s * c;
+        c = fmaf(-2.f * s, s, 1.f);
+        s = s2;
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 32; ++e) pk[e] = pack_bf16(v[2 * e], v[2 * e + 1]);
+}
+
 }  // namespace tc
 }  // namespace mlps
