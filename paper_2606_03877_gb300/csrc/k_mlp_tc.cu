@@ -37,18 +37,17 @@ namespace tc {
 
 using simt::IntervalInfo;
 
-constexpr int kNEG = 2;                         // epilogue groups = chunks in flight
-constexpr int kThreadsTC = kEGThreads * kNEG + 32;
-constexpr int kMmaWarp = kNEG * 4;
-constexpr uint32_t kTmemCols = 256;             // 128 per group
+constexpr int kMaxNEG = 3;                      // epilogue groups = chunks in flight (<= 3)
+constexpr int threads_tc(int neg) { return kEGThreads * neg + 32; }
+constexpr uint32_t kTmemCols = 512;             // 128 per group
 constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s
 struct TcSmem {
-  uint32_t w, a[kNEG], bias, itab[kNEG], scan, bars, misc, total;
+  uint32_t w, a[kMaxNEG], bias, itab[kMaxNEG], scan, bars, misc, total;
 };
 
 MLPS_HD uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-MLPS_HD TcSmem tc_smem(const TcPlan& P) {
+MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG) {
   TcSmem L;
   uint32_t off = 0;
   L.w = off;
@@ -73,14 +72,16 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P) {
   return L;
 }
 
-template <int WIDTH, int XL, int DL>
-__global__ void __launch_bounds__(kThreadsTC, 1)
+template <int WIDTH, int XL, int DL, int NF, int kNEG>
+__global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
     k_mlp_fwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
+  constexpr int kThreadsTC = kEGThreads * kNEG + 32;
+  constexpr int kMmaWarp = kNEG * 4;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (sbase - raw);
-  const TcSmem L = tc_smem(P);
+  const TcSmem L = tc_smem(P, kNEG);
   const Model& m = a.m;
   float* sBias = reinterpret_cast<float*>(gbase + L.bias);
   float* sScan = reinterpret_cast<float*>(gbase + L.scan);
@@ -119,8 +120,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   const int g = warp >> 2;               // epilogue group of this warp (< kNEG)
   const int q = warp & 3;                // TMEM lane quarter
   const int row = q * 32 + lane;         // sample row within the chunk
-  uint32_t ph_w = 0, ph_ready[kNEG], ph_done[kNEG];
-  for (int j = 0; j < kNEG; ++j) { ph_ready[j] = 0; ph_done[j] = 0; }
+  // mbarrier phase parities, one bit per group (registers, no local memory)
+  uint32_t ph_w = 0, ph_ready = 0, ph_done = 0;
   int loaded = -1;
   int prim = cb < ce ? simt::find_prim(w, cb) : 0;
   int nissued = 0;
@@ -128,8 +129,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   ChunkStep<kNEG> cur = chunk_step<kNEG>(w, cb, ce, prim);
   RecPrefetch pre;
   pre.valid = 0;
-  if (warp < kMmaWarp && cur.n > 0 && cur.cc[g] >= 0) {
-    const int f0 = (cur.cc[g] - w.chunk_start[cur.prim]) * w.ipc;
+  int my_first = cur.cc[0];
+#pragma unroll
+  for (int j = 1; j < kNEG; ++j) my_first = (g == j) ? cur.cc[j] : my_first;
+  if (warp < kMmaWarp && cur.n > 0 && my_first >= 0) {
+    const int f0 = (my_first - w.chunk_start[cur.prim]) * w.ipc;
     if (row < min(w.ipc, w.prim_count[cur.prim] - f0)) rec_prefetch(w, w.prim_start[cur.prim] + f0 + row, false, pre);
   }
   while (cur.c0 < ce) {
@@ -138,6 +142,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const int* cc = cur.cc;
     const int nstep = cur.n;
     const int c = cur.c0;
+    int my_cc = cur.cc[0];  // this warp's chunk (register select, no dynamic indexing)
+#pragma unroll
+    for (int j = 1; j < kNEG; ++j) my_cc = (g == j) ? cur.cc[j] : my_cc;
+    int my_nx = nxt.cc[0];
+#pragma unroll
+    for (int j = 1; j < kNEG; ++j) my_nx = (g == j) ? nxt.cc[j] : my_nx;
     if (prim != loaded) {
       __syncthreads();  // every role is done with the previous primitive's tiles
       if (threadIdx.x == kMmaWarp * 32 && !*sAbort) {
@@ -159,23 +169,23 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 
     if (warp < kMmaWarp) {
       // ------------------------------------------------------------ epilogue group g
-      if (cc[g] < 0 && nxt.n > 0 && nxt.cc[g] >= 0) {  // idle this step: still prefetch
-        const int f1 = (nxt.cc[g] - w.chunk_start[nxt.prim]) * w.ipc;
+      if (my_cc < 0 && nxt.n > 0 && my_nx >= 0) {  // idle this step: still prefetch
+        const int f1 = (my_nx - w.chunk_start[nxt.prim]) * w.ipc;
         if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
           rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, false, pre);
       }
-      if (cc[g] >= 0) {
+      if (my_cc >= 0) {
         const int bar_id = 1 + g;
         IntervalRec* T = reinterpret_cast<IntervalRec*>(gbase + L.itab[g]);
-        const int first = (cc[g] - w.chunk_start[prim]) * w.ipc;
+        const int first = (my_cc - w.chunk_start[prim]) * w.ipc;
         const int nint = min(w.ipc, w.prim_count[prim] - first);
         // every warp of the group is done with the previous chunk's interval table
         named_bar_sync(bar_id, kEGThreads);
         if (row < nint) rec_store(pre, T, row);  // prefetched during the previous step
         named_bar_sync(bar_id, kEGThreads);
         pre.valid = 0;
-        if (nxt.n > 0 && nxt.cc[g] >= 0) {  // start loading the next chunk's records now
-          const int f1 = (nxt.cc[g] - w.chunk_start[nxt.prim]) * w.ipc;
+        if (nxt.n > 0 && my_nx >= 0) {  // start loading the next chunk's records now
+          const int f1 = (my_nx - w.chunk_start[nxt.prim]) * w.ipc;
           if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
             rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, false, pre);
         }
@@ -221,8 +231,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const uint32_t trow = tmem + (uint32_t)(g * 128) + ((uint32_t)(q * 32) << 16);
         for (int l = 0; l < nl; ++l) {
           // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
-          const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), ph_done[g], sAbort, kWaitNs));
-          ph_done[g] ^= 1;
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), (ph_done >> g) & 1u, sAbort, kWaitNs));
+          ph_done ^= 1u << g;
           tc_fence_after();
           const float* bias = sBias + P.bias_off[l];
           if (l < nl - 1) {
@@ -234,15 +244,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 tmem_ld32(trow + half * 64 + 32, v1);
                 tmem_wait_ld();
                 const uint32_t At = A + (uint32_t)half * (kM * 128);
+                const float4* b4 = reinterpret_cast<const float4*>(bias + half * 64);
 #pragma unroll
                 for (int ch = 0; ch < 8; ++ch) {
+                  const float4 ba = b4[2 * ch], bb = b4[2 * ch + 1];
+                  const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
                   uint32_t pk[4];
 #pragma unroll
                   for (int e = 0; e < 4; ++e) {
                     const int c0 = ch * 8 + 2 * e;
-                    const float x0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]) + bias[half * 64 + c0];
-                    const float x1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]) +
-                                     bias[half * 64 + c0 + 1];
+                    const float x0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]) + bv[2 * e];
+                    const float x1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]) + bv[2 * e + 1];
                     pk[e] = pack_bf16_relu(x0, x1);
                   }
                   st_shared_v4(At + sw128_off(row, ch), pk[0], pk[1], pk[2], pk[3]);
@@ -253,8 +265,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             tc_fence_before();
             mbar_arrive(bar_ready(g));
           } else {
-            // last layer: heads, then the interval composite
-            float z[48];
+            // last layer: heads, then the interval composite (NF = largest feature count)
+            constexpr int NZ = 4 + NF;
+            float z[NZ];
             if (ok) {
               uint32_t r32[32], r16[16];
 #pragma unroll
@@ -267,15 +280,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
               }
               tmem_wait_ld();
 #pragma unroll
-              for (int j = 0; j < 48; ++j) {
+              for (int j = 0; j < NZ; ++j) {
                 uint32_t bits;
-                if (P.npad[l] >= 32) bits = j < 32 ? r32[j] : r16[j - 32];
+                if (P.npad[l] >= 32) bits = j < 32 ? r32[j] : r16[(j - 32) & 15];
                 else bits = j < 16 ? r16[j] : 0u;
                 z[j] = (j < m.nout) ? __uint_as_float(bits) + bias[j] : 0.f;
               }
             } else {
 #pragma unroll
-              for (int j = 0; j < 48; ++j) z[j] = 0.f;
+              for (int j = 0; j < NZ; ++j) z[j] = 0.f;
             }
             tc_fence_before();
             const float dt = valid ? T[iv].dt : 0.f;
@@ -285,21 +298,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             seg_scan<1>(A1, 1, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
             const float Aex = A1[0] - a_k;
             const float wk = valid ? __expf(-Aex) * (1.f - __expf(-a_k)) : 0.f;
-            float vals[kMaxScanVals];
-#pragma unroll
-            for (int j = 0; j < kMaxScanVals; ++j) vals[j] = 0.f;
+            float vals[NZ];
             vals[0] = wk * sigmoid_fast(z[0]);
             vals[1] = wk * sigmoid_fast(z[1]);
             vals[2] = wk * sigmoid_fast(z[2]);
             vals[3] = a_k;
 #pragma unroll
-            for (int f = 0; f < kMaxFeat; ++f)
-              if (f < m.F) vals[4 + f] = wk * z[4 + f];
-            seg_scan<kMaxScanVals>(vals, 4 + m.F, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
+            for (int f = 0; f < NF; ++f) vals[4 + f] = f < m.F ? wk * z[4 + f] : 0.f;
+            seg_scan<NZ>(vals, 4 + m.F, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
             if (valid && k == S - 1 && ok) {
               const int h = T[iv].h;
               w.hit_out[h] = make_float4(vals[0], vals[1], vals[2], vals[3]);
-              for (int f = 0; f < m.F; ++f) w.hit_feat[(size_t)h * m.F + f] = vals[4 + f];
+#pragma unroll
+              for (int f = 0; f < NF; ++f)
+                if (f < m.F) w.hit_feat[(size_t)h * m.F + f] = vals[4 + f];
             }
           }
         }
@@ -309,10 +321,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       for (int l = 0; l < nl; ++l) {
         const uint32_t idesc = idesc_bf16(kM, P.npad[l]);
         const uint32_t wl = sbase + L.w + P.sw_off[l];
+#pragma unroll
         for (int j = 0; j < kNEG; ++j) {
-          if (cc[j] < 0) continue;
-          const bool ok = mbar_wait(bar_ready(j), ph_ready[j], sAbort, kWaitNs);
-          ph_ready[j] ^= 1;
+          if (cur.cc[j] < 0) continue;
+          const bool ok = mbar_wait(bar_ready(j), (ph_ready >> j) & 1u, sAbort, kWaitNs);
+          ph_ready ^= 1u << j;
           tc_fence_after();
           if (ok) {
             const uint32_t A = sbase + L.a[j];
@@ -410,7 +423,12 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride) {
   return true;
 }
 
-size_t tc_smem_bytes(const TcPlan& P) { return tc::tc_smem(P).total + 1024; }
+static int fwd_groups(int width) { return width == 64 ? 3 : 2; }
+
+size_t tc_smem_bytes(const TcPlan& P) {
+  const int width = P.npad[0];  // hidden width = N of layer 0
+  return tc::tc_smem(P, fwd_groups(width)).total + 1024;
+}
 
 void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
                       void* out, cudaStream_t st) {
@@ -449,13 +467,23 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
   const int xl = a.m.xyzL, dl = a.m.dirL;
   const bool fast64 = xl == 6 && dl == 4 && P.kpad[0] == 64;
   const bool raw = xl == 0 && dl == 0 && P.kpad[0] == 64;
-  decltype(&tc::k_mlp_fwd_tc<64, 6, 4>) kern;
-  if (a.m.width == 64) kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4> : raw ? tc::k_mlp_fwd_tc<64, 0, 0> : tc::k_mlp_fwd_tc<64, -1, -1>;
-  else if (a.m.width == 128) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4> : raw ? tc::k_mlp_fwd_tc<128, 0, 0> : tc::k_mlp_fwd_tc<128, -1, -1>;
-  else return cudaErrorNotSupported;
+  decltype(&tc::k_mlp_fwd_tc<64, 6, 4, 0, 3>) kern;
+  const bool feat = a.m.F > 0;
+  int neg = 0;
+  if (a.m.width == 64) {
+    neg = 3;
+    if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, 0, 3> : raw ? tc::k_mlp_fwd_tc<64, 0, 0, 0, 3> : tc::k_mlp_fwd_tc<64, -1, -1, 0, 3>;
+    else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, 44, 3> : tc::k_mlp_fwd_tc<64, -1, -1, 44, 3>;
+  } else if (a.m.width == 128) {
+    neg = 2;
+    if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 0, 2> : tc::k_mlp_fwd_tc<128, -1, -1, 0, 2>;
+    else kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 44, 2> : tc::k_mlp_fwd_tc<128, -1, -1, 44, 2>;
+  } else {
+    return cudaErrorNotSupported;
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<n_sm, tc::kThreadsTC, smem, st>>>(w, a, P, tmap);
+  kern<<<n_sm, tc::threads_tc(neg), smem, st>>>(w, a, P, tmap);
   return cudaGetLastError();
 }
 

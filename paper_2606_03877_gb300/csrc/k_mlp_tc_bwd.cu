@@ -212,10 +212,9 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   const int g = warp >> 2, q = warp & 3, row = q * 32 + lane;
-  uint32_t ph_w = 0, ph_ready[kNG], ph_done[kNG];
-  for (int j = 0; j < kNG; ++j) { ph_ready[j] = 0; ph_done[j] = 0; }
-  int first_wgrad[kMaxLayers];
-  for (int l = 0; l < kMaxLayers; ++l) first_wgrad[l] = 1;
+  // mbarrier phase parities and first-wgrad flags as bit sets (registers, no local memory)
+  uint32_t ph_w = 0, ph_ready = 0, ph_done = 0;
+  uint32_t first_wgrad = 0xFFu;
   int loaded = -1;
   int prim = cb < ce ? simt::find_prim(w, cb) : 0;
 
@@ -253,14 +252,22 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   ChunkStep<kNG> cur = chunk_step<kNG>(w, cb, ce, prim);
   RecPrefetch pre;
   pre.valid = 0;
-  if (warp < kMmaWarpB && cur.n > 0 && cur.cc[g] >= 0) {
-    const int f0 = (cur.cc[g] - w.chunk_start[cur.prim]) * w.ipc;
+  int my_first = cur.cc[0];
+#pragma unroll
+  for (int j = 1; j < kNG; ++j) my_first = (g == j) ? cur.cc[j] : my_first;
+  if (warp < kMmaWarpB && cur.n > 0 && my_first >= 0) {
+    const int f0 = (my_first - w.chunk_start[cur.prim]) * w.ipc;
     if (row < min(w.ipc, w.prim_count[cur.prim] - f0)) rec_prefetch(w, w.prim_start[cur.prim] + f0 + row, true, pre);
   }
   while (cur.c0 < ce) {
     prim = cur.prim;
     const ChunkStep<kNG> nxt = chunk_step<kNG>(w, cur.c0 + cur.n, ce, prim);
-    const int* cc = cur.cc;
+    int my_cc = cur.cc[0];  // this warp's chunk (register select, no dynamic indexing)
+#pragma unroll
+    for (int j = 1; j < kNG; ++j) my_cc = (g == j) ? cur.cc[j] : my_cc;
+    int my_nx = nxt.cc[0];
+#pragma unroll
+    for (int j = 1; j < kNG; ++j) my_nx = (g == j) ? nxt.cc[j] : my_nx;
     if (prim != loaded) {
       tc_fence_before();
       __syncthreads();
@@ -279,25 +286,25 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       for (int i = threadIdx.x; i < P.bias_floats; i += kThreadsB) sBias[i] = gbias[i];
       mbar_wait(bar_w, ph_w, sAbort, kWaitNsB);
       ph_w ^= 1;
-      for (int l = 0; l < kMaxLayers; ++l) first_wgrad[l] = 1;
+      first_wgrad = 0xFFu;
       __syncthreads();
       loaded = prim;
     }
 
     if (warp < kMmaWarpB) {
       // ============================================================ epilogue group g
-      if (cc[g] < 0 && nxt.n > 0 && nxt.cc[g] >= 0) {  // idle this step: still prefetch
-        const int f1 = (nxt.cc[g] - w.chunk_start[nxt.prim]) * w.ipc;
+      if (my_cc < 0 && nxt.n > 0 && my_nx >= 0) {  // idle this step: still prefetch
+        const int f1 = (my_nx - w.chunk_start[nxt.prim]) * w.ipc;
         if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
           rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, true, pre);
       }
-      if (cc[g] >= 0) {
+      if (my_cc >= 0) {
         const int bar_id = 1 + g;
         IntervalRec* T = reinterpret_cast<IntervalRec*>(gb + L.itab[g]);
         float4* GI = reinterpret_cast<float4*>(gb + L.giv[g]);
         float* DD = reinterpret_cast<float*>(gb + L.ddel[g]);
         float* GF = reinterpret_cast<float*>(gb + L.gf[g]);
-        const int first = (cc[g] - w.chunk_start[prim]) * w.ipc;
+        const int first = (my_cc - w.chunk_start[prim]) * w.ipc;
         const int nint = min(w.ipc, w.prim_count[prim] - first);
         named_bar_sync(bar_id, kEGThreads);
         if (row < nint) {
@@ -308,8 +315,8 @@ __global__ void __launch_bounds__(kThreadsB, 1)
         }
         named_bar_sync(bar_id, kEGThreads);
         pre.valid = 0;
-        if (nxt.n > 0 && nxt.cc[g] >= 0) {  // start loading the next chunk's records now
-          const int f1 = (nxt.cc[g] - w.chunk_start[nxt.prim]) * w.ipc;
+        if (nxt.n > 0 && my_nx >= 0) {  // start loading the next chunk's records now
+          const int f1 = (my_nx - w.chunk_start[nxt.prim]) * w.ipc;
           if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
             rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, true, pre);
         }
@@ -327,8 +334,8 @@ __global__ void __launch_bounds__(kThreadsB, 1)
 
         // ---------------- forward recompute
         for (int l = 0; l < nl; ++l) {
-          const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), ph_done[g], sAbort, kWaitNsB));
-          ph_done[g] ^= 1;
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), (ph_done >> g) & 1u, sAbort, kWaitNsB));
+          ph_done ^= 1u << g;
           tc_fence_after();
           const float* bias = sBias + P.bias_off[l];
           if (l < nl - 1) {
@@ -338,12 +345,17 @@ __global__ void __launch_bounds__(kThreadsB, 1)
               tmem_ld32(trow, v0);
               tmem_ld32(trow + 32, v1);
               tmem_wait_ld();
+              const float4* b4 = reinterpret_cast<const float4*>(bias);
 #pragma unroll
-              for (int e = 0; e < 32; ++e) {
-                const int c0 = 2 * e;
-                const float x0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]) + bias[c0];
-                const float x1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]) + bias[c0 + 1];
-                pk[e] = pack_bf16_relu(x0, x1);
+              for (int e4 = 0; e4 < 16; ++e4) {
+                const float4 bq = b4[e4];
+                const int c0 = 4 * e4;
+                const float x0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]) + bq.x;
+                const float x1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]) + bq.y;
+                const float x2 = __uint_as_float(c0 + 2 < 32 ? v0[c0 + 2] : v1[c0 + 2 - 32]) + bq.z;
+                const float x3 = __uint_as_float(c0 + 3 < 32 ? v0[c0 + 3] : v1[c0 + 3 - 32]) + bq.w;
+                pk[2 * e4] = pack_bf16_relu(x0, x1);
+                pk[2 * e4 + 1] = pack_bf16_relu(x2, x3);
               }
             } else {
 #pragma unroll
@@ -430,8 +442,8 @@ __global__ void __launch_bounds__(kThreadsB, 1)
         }
         // ---------------- backward phases B_{nl-1} .. B_0
         for (int l = nl - 1; l >= 0; --l) {
-          const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), ph_done[g], sAbort, kWaitNsB));
-          ph_done[g] ^= 1;
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), (ph_done >> g) & 1u, sAbort, kWaitNsB));
+          ph_done ^= 1u << g;
           tc_fence_after();
           if (l > 0) {
             // delta_{l-1} = G * [H_l > 0], written over H_l in T_l
@@ -561,10 +573,11 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     } else if (warp == kMmaWarpB && lane == 0) {
       // ============================================================ MMA issuer
       for (int ph = 0; ph < 2 * nl; ++ph) {
+#pragma unroll
         for (int j = 0; j < kNG; ++j) {
-          if (cc[j] < 0) continue;
-          const bool ok = mbar_wait(bar_ready(j), ph_ready[j], sAbort, kWaitNsB);
-          ph_ready[j] ^= 1;
+          if (cur.cc[j] < 0) continue;
+          const bool ok = mbar_wait(bar_ready(j), (ph_ready >> j) & 1u, sAbort, kWaitNsB);
+          ph_ready ^= 1u << j;
           tc_fence_after();
           if (ok) {
             const uint32_t tiles = sbase + L.tiles[j];
@@ -592,11 +605,11 @@ __global__ void __launch_bounds__(kThreadsB, 1)
               const uint32_t id_w = idesc_bf16(kM, 64) | (1u << 15) | (1u << 16);
               const uint32_t lbo = (sbase + L.ones) - Hl;
               for (int kk = 0; kk < kM / 16; ++kk) {
-                const uint32_t acc_flag = (first_wgrad[l] && kk == 0) ? 0u : 1u;
+                const uint32_t acc_flag = (((first_wgrad >> l) & 1u) && kk == 0) ? 0u : 1u;
                 mma_bf16(tm_dw + (uint32_t)(l * 64), sw128_desc_mn(Hl + (uint32_t)kk * 2048, lbo),
                          sw128_desc_mn(Dl + (uint32_t)kk * 2048, 16), id_w, acc_flag);
               }
-              first_wgrad[l] = 0;
+              first_wgrad &= ~(1u << l);
             }
           }
           mma_commit(bar_done(j));

@@ -160,24 +160,25 @@ MLPS_DEV void encode_pairs64(const float (&xl)[3], const float (&d)[3], uint32_t
   constexpr int NX = XL > 0 ? 6 * XL : 3;
   constexpr int NIN = NX + (DL > 0 ? 6 * DL : 0);
   static_assert(NIN <= 64, "encoded input wider than one 64-column tile");
-  float v[64];
+  static_assert(XL > 0 || DL == 0, "raw position with a direction encoding is not a fast path");
 #pragma unroll
-  for (int j = 0; j < 64; ++j) v[j] = 0.f;
+  for (int e = 0; e < 32; ++e) pk[e] = 0u;
   if (XL == 0) {
-    v[0] = xl[0]; v[1] = xl[1]; v[2] = xl[2];
-  } else {
+    pk[0] = pack_bf16(xl[0], xl[1]);
+    pk[1] = pack_bf16(xl[2], 0.f);
+    return;
+  }
+  // every (sin, cos) pair of one frequency is exactly one BF16x2 word
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      float s, c;
-      __sincosf(3.14159265358979f * xl[u], &s, &c);
+  for (int u = 0; u < 3; ++u) {
+    float s, c;
+    __sincosf(3.14159265358979f * xl[u], &s, &c);
 #pragma unroll
-      for (int l = 0; l < (XL > 0 ? XL : 1); ++l) {
-        v[2 * (u * XL + l)] = s;
-        v[2 * (u * XL + l) + 1] = c;
-        const float s2 = 2.f * s * c;
-        c = fmaf(-2.f * s, s, 1.f);
-        s = s2;
-      }
+    for (int l = 0; l < (XL > 0 ? XL : 1); ++l) {
+      pk[u * XL + l] = pack_bf16(s, c);
+      const float s2 = 2.f * s * c;
+      c = fmaf(-2.f * s, s, 1.f);
+      s = s2;
     }
   }
   if (DL > 0) {
@@ -187,16 +188,13 @@ MLPS_DEV void encode_pairs64(const float (&xl)[3], const float (&d)[3], uint32_t
       __sincosf(3.14159265358979f * d[u], &s, &c);
 #pragma unroll
       for (int l = 0; l < (DL > 0 ? DL : 1); ++l) {
-        v[NX + 2 * (u * DL + l)] = s;
-        v[NX + 2 * (u * DL + l) + 1] = c;
+        pk[NX / 2 + u * DL + l] = pack_bf16(s, c);
         const float s2 = 2.f * s * c;
         c = fmaf(-2.f * s, s, 1.f);
         s = s2;
       }
     }
   }
-#pragma unroll
-  for (int e = 0; e < 32; ++e) pk[e] = pack_bf16(v[2 * e], v[2 * e + 1]);
 }
 
 }  // namespace tc
