@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
     k_mlp_fwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
   constexpr int kThreadsTC = kEGThreads * kNEG + 32;
   constexpr int kMmaWarp = kNEG * 4;
+  static_assert(4 + NF <= kMaxScanVals, "scan scratch holds kMaxScanVals values per warp");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -473,11 +474,11 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
   if (a.m.width == 64) {
     neg = 3;
     if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, 0, 3> : raw ? tc::k_mlp_fwd_tc<64, 0, 0, 0, 3> : tc::k_mlp_fwd_tc<64, -1, -1, 0, 3>;
-    else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, 44, 3> : tc::k_mlp_fwd_tc<64, -1, -1, 44, 3>;
+    else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, kMaxFeat, 3> : tc::k_mlp_fwd_tc<64, -1, -1, kMaxFeat, 3>;
   } else if (a.m.width == 128) {
     neg = 2;
     if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 0, 2> : tc::k_mlp_fwd_tc<128, -1, -1, 0, 2>;
-    else kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 44, 2> : tc::k_mlp_fwd_tc<128, -1, -1, 44, 2>;
+    else kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, kMaxFeat, 2> : tc::k_mlp_fwd_tc<128, -1, -1, kMaxFeat, 2>;
   } else {
     return cudaErrorNotSupported;
   }

@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   uint8_t* gb = smem_raw + (sbase - raw);
   const Model& m = a.m;
   const int F = m.F;
+  static_assert(14 <= kMaxScanVals && 3 + NF <= kMaxScanVals, "scan scratch holds kMaxScanVals values per warp");
   const BwdSmem L = bwd_layout(P, F);
   float* sBias = reinterpret_cast<float*>(gb + L.bias);
   float* sScan = reinterpret_cast<float*>(gb + L.scan);
