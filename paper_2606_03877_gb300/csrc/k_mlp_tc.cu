@@ -41,8 +41,10 @@ constexpr int kMaxNEG = 3;                      // epilogue groups = chunks in f
 constexpr int threads_tc(int neg) { return kEGThreads * neg + 32; }
 constexpr uint32_t kTmemCols = 512;             // 128 per group
 constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s
+// Byte offsets in dynamic shared memory; per-group regions are base + g * stride (plain
+// arithmetic, so that nothing is indexed at run time).
 struct TcSmem {
-  uint32_t w, a[kMaxNEG], bias, itab[kMaxNEG], scan, bars, misc, total;
+  uint32_t w, a0, a_stride, bias, itab0, itab_stride, scan, bars, misc, total;
 };
 
 MLPS_HD uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -52,16 +54,14 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG) {
   uint32_t off = 0;
   L.w = off;
   off = align_up(off + P.w_bytes, 1024);
-  for (int g = 0; g < kNEG; ++g) {
-    L.a[g] = off;
-    off = align_up(off + P.a_bytes, 1024);
-  }
+  L.a0 = off;
+  L.a_stride = align_up(P.a_bytes, 1024);
+  off += L.a_stride * kNEG;
   L.bias = off;
   off = align_up(off + 4 * P.bias_floats, 16);
-  for (int g = 0; g < kNEG; ++g) {
-    L.itab[g] = off;
-    off = align_up(off + (uint32_t)sizeof(IntervalRec) * kM, 16);
-  }
+  L.itab0 = off;
+  L.itab_stride = align_up((uint32_t)sizeof(IntervalRec) * kM, 16);
+  off += L.itab_stride * kNEG;
   L.scan = off;
   off = align_up(off + 4 * kNEG * 4 * kMaxScanVals, 16);
   L.bars = off;
@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
   float* sScan = reinterpret_cast<float*>(gbase + L.scan);
   const uint32_t bar_w = sbase + L.bars;
   const uint32_t bar_end = bar_w + 8;
-  auto bar_ready = [&](int g) { return bar_w + 16 + 8 * g; };
-  auto bar_done = [&](int g) { return bar_w + 16 + 8 * kNEG + 8 * g; };
+#define bar_ready(G) (bar_w + 16u + 8u * (uint32_t)(G))
+#define bar_done(G) (bar_w + 16u + 8u * (uint32_t)(kNEG) + 8u * (uint32_t)(G))
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(gbase + L.misc);
   volatile int* sAbort = reinterpret_cast<volatile int*>(gbase + L.misc + 4);
 
@@ -130,9 +130,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
   ChunkStep<kNEG> cur = chunk_step<kNEG>(w, cb, ce, prim);
   RecPrefetch pre;
   pre.valid = 0;
-  int my_first = cur.cc[0];
-#pragma unroll
-  for (int j = 1; j < kNEG; ++j) my_first = (g == j) ? cur.cc[j] : my_first;
+  const int my_first = step_chunk(cur, g);
   if (warp < kMmaWarp && cur.n > 0 && my_first >= 0) {
     const int f0 = (my_first - w.chunk_start[cur.prim]) * w.ipc;
     if (row < min(w.ipc, w.prim_count[cur.prim] - f0)) rec_prefetch(w, w.prim_start[cur.prim] + f0 + row, false, pre);
@@ -140,15 +138,8 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
   while (cur.c0 < ce) {
     prim = cur.prim;
     const ChunkStep<kNEG> nxt = chunk_step<kNEG>(w, cur.c0 + cur.n, ce, prim);
-    const int* cc = cur.cc;
-    const int nstep = cur.n;
-    const int c = cur.c0;
-    int my_cc = cur.cc[0];  // this warp's chunk (register select, no dynamic indexing)
-#pragma unroll
-    for (int j = 1; j < kNEG; ++j) my_cc = (g == j) ? cur.cc[j] : my_cc;
-    int my_nx = nxt.cc[0];
-#pragma unroll
-    for (int j = 1; j < kNEG; ++j) my_nx = (g == j) ? nxt.cc[j] : my_nx;
+    const int my_cc = step_chunk(cur, g);  // this warp's chunk this step and the next
+    const int my_nx = step_chunk(nxt, g);
     if (prim != loaded) {
       __syncthreads();  // every role is done with the previous primitive's tiles
       if (threadIdx.x == kMmaWarp * 32 && !*sAbort) {
@@ -177,7 +168,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
       }
       if (my_cc >= 0) {
         const int bar_id = 1 + g;
-        IntervalRec* T = reinterpret_cast<IntervalRec*>(gbase + L.itab[g]);
+        IntervalRec* T = reinterpret_cast<IntervalRec*>(gbase + L.itab0 + (uint32_t)g * L.itab_stride);
         const int first = (my_cc - w.chunk_start[prim]) * w.ipc;
         const int nint = min(w.ipc, w.prim_count[prim] - first);
         // every warp of the group is done with the previous chunk's interval table
@@ -190,7 +181,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
           if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
             rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, false, pre);
         }
-        const uint32_t A = sbase + L.a[g];
+        const uint32_t A = sbase + L.a0 + (uint32_t)g * L.a_stride;
         const int iv = row / S, k = row - iv * S;
         const bool valid = iv < nint;
         if (XL >= 0) {
@@ -324,12 +315,12 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
         const uint32_t wl = sbase + L.w + P.sw_off[l];
 #pragma unroll
         for (int j = 0; j < kNEG; ++j) {
-          if (cur.cc[j] < 0) continue;
+          if (step_chunk(cur, j) < 0) continue;
           const bool ok = mbar_wait(bar_ready(j), (ph_ready >> j) & 1u, sAbort, kWaitNs);
           ph_ready ^= 1u << j;
           tc_fence_after();
           if (ok) {
-            const uint32_t A = sbase + L.a[j];
+            const uint32_t A = sbase + L.a0 + (uint32_t)j * L.a_stride;
             const uint32_t d = tmem + (uint32_t)(j * 128);
             for (int kk = 0; kk < P.kpad[l] / 16; ++kk) {
               const uint32_t aa = A + (uint32_t)(kk >> 2) * (kM * 128) + (uint32_t)(kk & 3) * 32;
@@ -342,7 +333,6 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
         }
       }
     }
-    (void)c; (void)nstep;
     cur = nxt;
   }
 
@@ -358,6 +348,8 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
     tmem_dealloc(tmem, kTmemCols);
   }
   if (threadIdx.x == 0 && *sAbort) set_status(w.saved_hdr, MLPS_ERR_TIMEOUT);
+#undef bar_ready
+#undef bar_done
   (void)nissued;
 }
 

@@ -47,9 +47,10 @@ constexpr uint32_t kTmemColsB = 512;
 constexpr uint64_t kWaitNsB = 2000000000ull;
 constexpr uint32_t kTile = kM * 128;                // one [128 x 64] BF16 tile
 
+// Byte offsets in dynamic shared memory; per-group regions are base + g * stride.
 struct BwdSmem {
-  uint32_t w, wt, tiles[kNG], ones, bias, itab[kNG], giv[kNG], ddel[kNG], gf[kNG], scan, geo,
-      bars, misc, total;
+  uint32_t w, wt, tiles0, tiles_stride, ones, bias, grp0, grp_stride, itab, giv, ddel, gf, scan,
+      geo, pgeo, bars, misc, total;  // itab/giv/ddel/gf: offsets inside one group's block
 };
 
 MLPS_HD uint32_t al(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -60,28 +61,31 @@ MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F) {
   L.w = o;
   o = al(o + P.w_bytes, 1024);
   L.wt = o;
-  for (int g = 0; g < kNG; ++g) {
-    L.tiles[g] = o;
-    o = al(o + (uint32_t)P.nl * kTile, 1024);  // T_0 .. T_{nl-1}
-  }
+  L.tiles0 = o;
+  L.tiles_stride = al((uint32_t)P.nl * kTile, 1024);  // T_0 .. T_{nl-1}
+  o += L.tiles_stride * kNG;
   L.ones = o;  // above every group tile: the wgrad descriptors reach it with a positive offset
   o = al(o + kTile, 1024);
   L.bias = o;
   o = al(o + 4 * P.bias_floats, 16);
-  for (int g = 0; g < kNG; ++g) {
-    L.itab[g] = o;
-    o = al(o + (uint32_t)sizeof(IntervalRec) * kM, 16);
-    L.giv[g] = o;
-    o = al(o + 16 * kM, 16);
-    L.ddel[g] = o;
-    o = al(o + 4 * kM, 16);
-    L.gf[g] = o;
-    o = al(o + 4 * kM * (F > 0 ? F : 1), 16);
-  }
+  uint32_t q = 0;
+  L.itab = q;
+  q = al(q + (uint32_t)sizeof(IntervalRec) * kM, 16);
+  L.giv = q;
+  q = al(q + 16 * kM, 16);
+  L.ddel = q;
+  q = al(q + 4 * kM, 16);
+  L.gf = q;
+  q = al(q + 4 * kM * (F > 0 ? F : 1), 16);
+  L.grp0 = o;
+  L.grp_stride = q;
+  o += q * kNG;
   L.scan = o;
   o = al(o + 4 * kNG * 4 * kMaxScanVals, 16);
   L.geo = o;
   o = al(o + 4 * 16, 16);
+  L.pgeo = o;  // the current primitive's geometry (staged at every primitive change)
+  o = al(o + (uint32_t)sizeof(PrimGeo), 16);
   L.bars = o;
   o = al(o + 8 * (2 + 2 * kNG), 16);
   L.misc = o;
@@ -174,8 +178,8 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   float* sScan = reinterpret_cast<float*>(gb + L.scan);
   float* sGeo = reinterpret_cast<float*>(gb + L.geo);
   const uint32_t bar_w = sbase + L.bars, bar_end = bar_w + 8;
-  auto bar_ready = [&](int g) { return bar_w + 16 + 8 * g; };
-  auto bar_done = [&](int g) { return bar_w + 16 + 8 * kNG + 8 * g; };
+#define bar_ready(G) (bar_w + 16u + 8u * (uint32_t)(G))
+#define bar_done(G) (bar_w + 16u + 8u * (uint32_t)(kNG) + 8u * (uint32_t)(G))
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(gb + L.misc);
   volatile int* sAbort = reinterpret_cast<volatile int*>(gb + L.misc + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -253,9 +257,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   ChunkStep<kNG> cur = chunk_step<kNG>(w, cb, ce, prim);
   RecPrefetch pre;
   pre.valid = 0;
-  int my_first = cur.cc[0];
-#pragma unroll
-  for (int j = 1; j < kNG; ++j) my_first = (g == j) ? cur.cc[j] : my_first;
+  const int my_first = step_chunk(cur, g);
   if (warp < kMmaWarpB && cur.n > 0 && my_first >= 0) {
     const int f0 = (my_first - w.chunk_start[cur.prim]) * w.ipc;
     if (row < min(w.ipc, w.prim_count[cur.prim] - f0)) rec_prefetch(w, w.prim_start[cur.prim] + f0 + row, true, pre);
@@ -263,12 +265,8 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   while (cur.c0 < ce) {
     prim = cur.prim;
     const ChunkStep<kNG> nxt = chunk_step<kNG>(w, cur.c0 + cur.n, ce, prim);
-    int my_cc = cur.cc[0];  // this warp's chunk (register select, no dynamic indexing)
-#pragma unroll
-    for (int j = 1; j < kNG; ++j) my_cc = (g == j) ? cur.cc[j] : my_cc;
-    int my_nx = nxt.cc[0];
-#pragma unroll
-    for (int j = 1; j < kNG; ++j) my_nx = (g == j) ? nxt.cc[j] : my_nx;
+    const int my_cc = step_chunk(cur, g);  // this warp's chunk this step and the next
+    const int my_nx = step_chunk(nxt, g);
     if (prim != loaded) {
       tc_fence_before();
       __syncthreads();
@@ -285,6 +283,11 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       }
       const float* gbias = reinterpret_cast<const float*>(a.weights + (size_t)prim * a.pk.stride + P.gbias_byte);
       for (int i = threadIdx.x; i < P.bias_floats; i += kThreadsB) sBias[i] = gbias[i];
+      {
+        const int* src = reinterpret_cast<const int*>(w.geo + prim);
+        int* dst = reinterpret_cast<int*>(gb + L.pgeo);
+        for (int i = threadIdx.x; i < (int)(sizeof(PrimGeo) / 4); i += kThreadsB) dst[i] = src[i];
+      }
       mbar_wait(bar_w, ph_w, sAbort, kWaitNsB);
       ph_w ^= 1;
       first_wgrad = 0xFFu;
@@ -301,10 +304,11 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       }
       if (my_cc >= 0) {
         const int bar_id = 1 + g;
-        IntervalRec* T = reinterpret_cast<IntervalRec*>(gb + L.itab[g]);
-        float4* GI = reinterpret_cast<float4*>(gb + L.giv[g]);
-        float* DD = reinterpret_cast<float*>(gb + L.ddel[g]);
-        float* GF = reinterpret_cast<float*>(gb + L.gf[g]);
+        uint8_t* grp = gb + L.grp0 + (uint32_t)g * L.grp_stride;
+        IntervalRec* T = reinterpret_cast<IntervalRec*>(grp + L.itab);
+        float4* GI = reinterpret_cast<float4*>(grp + L.giv);
+        float* DD = reinterpret_cast<float*>(grp + L.ddel);
+        float* GF = reinterpret_cast<float*>(grp + L.gf);
         const int first = (my_cc - w.chunk_start[prim]) * w.ipc;
         const int nint = min(w.ipc, w.prim_count[prim] - first);
         named_bar_sync(bar_id, kEGThreads);
@@ -321,8 +325,8 @@ __global__ void __launch_bounds__(kThreadsB, 1)
           if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
             rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, true, pre);
         }
-        const uint32_t tiles = sbase + L.tiles[g];
-        auto tileaddr = [&](int i) { return tiles + (uint32_t)i * kTile; };
+        const uint32_t tiles = sbase + L.tiles0 + (uint32_t)g * L.tiles_stride;
+#define tileaddr(I) (tiles + (uint32_t)(I) * kTile)
         const int iv = row / S, k = row - iv * S;
         const bool valid = iv < nint;
         const uint32_t trow = tmem + (uint32_t)(g * 64) + ((uint32_t)(q * 32) << 16);
@@ -506,7 +510,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
             for (int e = 0; e < 14; ++e) red[e] = 0.f;
             if (valid) {
               const IntervalRec& I = T[iv];
-              const PrimGeo& Gp = w.geo[prim];
+              const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
               const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
               float xl[3], gx[3] = {0.f, 0.f, 0.f};
               for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
@@ -544,7 +548,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
             seg_scan<14>(red, 14, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
             if (valid && k == S - 1) {
               const IntervalRec& I = T[iv];
-              const PrimGeo& Gp = w.geo[prim];
+              const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
               const float dDelta = DD[iv];
               float gt0 = red[12] - dDelta / (float)S, gt1 = red[13] + dDelta / (float)S;
               const bool clamped = I.r0 != -I.r1;
@@ -576,12 +580,12 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       for (int ph = 0; ph < 2 * nl; ++ph) {
 #pragma unroll
         for (int j = 0; j < kNG; ++j) {
-          if (cur.cc[j] < 0) continue;
+          if (step_chunk(cur, j) < 0) continue;
           const bool ok = mbar_wait(bar_ready(j), (ph_ready >> j) & 1u, sAbort, kWaitNsB);
           ph_ready ^= 1u << j;
           tc_fence_after();
           if (ok) {
-            const uint32_t tiles = sbase + L.tiles[j];
+            const uint32_t tiles = sbase + L.tiles0 + (uint32_t)j * L.tiles_stride;
             const uint32_t acc = tmem + (uint32_t)(j * 64);
             if (ph < nl) {
               const int l = ph;  // F_l
@@ -634,6 +638,9 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     tmem_dealloc(tmem, kTmemColsB);
   }
   if (threadIdx.x == 0 && *sAbort) set_status(w.scr_hdr, MLPS_ERR_TIMEOUT);
+#undef bar_ready
+#undef bar_done
+#undef tileaddr
 }
 
 }  // namespace tc

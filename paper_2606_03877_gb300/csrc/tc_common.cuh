@@ -31,12 +31,18 @@ MLPS_DEV void seg_scan(float (&v)[NV], int nv, int row, int S, float* scratch, i
     }
   }
   if (S <= 32 && (32 % S) == 0) return;  // segments never cross a warp
-  if (lane == 31)
-    for (int j = 0; j < nv; ++j) scratch[wq * NV + j] = v[j];
+  if (lane == 31) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      if (j < nv) scratch[wq * NV + j] = v[j];
+  }
   named_bar_sync(bar_id, kEGThreads);
   if (seg0 < wq * 32)
-    for (int w2 = seg0 / 32; w2 < wq; ++w2)
-      for (int j = 0; j < nv; ++j) v[j] += scratch[w2 * NV + j];
+    for (int w2 = seg0 / 32; w2 < wq; ++w2) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j)
+        if (j < nv) v[j] += scratch[w2 * NV + j];
+    }
   named_bar_sync(bar_id, kEGThreads);
 }
 
@@ -95,12 +101,18 @@ MLPS_DEV void seg_scan_rev(float (&v)[NV], int nv, int row, int S, float* scratc
     }
   }
   if (S <= 32 && (32 % S) == 0) return;
-  if (lane == 0)
-    for (int j = 0; j < nv; ++j) scratch[wq * NV + j] = v[j];
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      if (j < nv) scratch[wq * NV + j] = v[j];
+  }
   named_bar_sync(bar_id, kEGThreads);
   if (seg1 > wq * 32 + 31)
-    for (int w2 = wq + 1; w2 <= seg1 / 32; ++w2)
-      for (int j = 0; j < nv; ++j) v[j] += scratch[w2 * NV + j];
+    for (int w2 = wq + 1; w2 <= seg1 / 32; ++w2) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j)
+        if (j < nv) v[j] += scratch[w2 * NV + j];
+    }
   named_bar_sync(bar_id, kEGThreads);
 }
 
@@ -109,24 +121,29 @@ MLPS_DEV void seg_scan_rev(float (&v)[NV], int nv, int row, int S, float* scratc
 template <int NG>
 struct ChunkStep {
   int c0, prim, n;
-  int cc[NG];
+  int c[3];  // chunk per group (-1: none); accessed with compile-time indices only
 };
 
 template <int NG>
 MLPS_DEV ChunkStep<NG> chunk_step(const Work& w, int c, int ce, int prim) {
+  static_assert(NG >= 1 && NG <= 3, "at most three epilogue groups");
   ChunkStep<NG> s;
   s.c0 = c;
-  s.n = 0;
   if (c < ce)
     while (c >= w.chunk_start[prim + 1]) ++prim;
   s.prim = prim;
-#pragma unroll
-  for (int j = 0; j < NG; ++j) {
-    const int cj = c + j;
-    s.cc[j] = (cj < ce && cj < w.chunk_start[prim + 1]) ? cj : -1;
-    s.n += s.cc[j] >= 0;
-  }
+  const int lim = min(ce, w.chunk_start[prim + 1]);
+  s.c[0] = c < lim ? c : -1;
+  s.c[1] = (NG > 1 && c + 1 < lim) ? c + 1 : -1;
+  s.c[2] = (NG > 2 && c + 2 < lim) ? c + 2 : -1;
+  s.n = (s.c[0] >= 0) + (s.c[1] >= 0) + (s.c[2] >= 0);
   return s;
+}
+
+// Chunk of group g in a step (register selects; no dynamic indexing).
+template <int NG>
+MLPS_DEV int step_chunk(const ChunkStep<NG>& s, int g) {
+  return g == 0 ? s.c[0] : (g == 1 ? s.c[1] : s.c[2]);
 }
 
 // Interval record (and, for the backward pass, its gradient) of one chunk row, loaded one
