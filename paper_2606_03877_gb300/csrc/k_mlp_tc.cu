@@ -4,15 +4,16 @@
 // Same work decomposition as the FP32 path: a chunk is up to ipc = 128 / S hit intervals of one
 // primitive, i.e. one M = 128 tile of sample rows; persistent blocks walk a contiguous range
 // of the primitive-major chunk list. Inside a block:
-//  * warp 8 (one elected lane) loads the primitive's weight tiles with TMA tensor copies
-//    (cp.async.bulk.tensor, 128-byte swizzle) into shared memory whenever the primitive
-//    changes, and issues every tcgen05.mma;
-//  * two epilogue warpgroups (warps 0-3 and 4-7) each own one chunk at a time, its A-operand
-//    tile in shared memory and 128 TMEM columns. A group builds the sample encodings (Eq. 5)
-//    as BF16 rows of the first A tile, then, after each layer's MMAs complete, reads its
-//    accumulator rows from TMEM (thread = sample row), adds the bias, applies ReLU, converts to
-//    BF16 and writes the next layer's A tile in place. While one group runs its epilogue the
-//    tensor core works on the other group's layer.
+//  * the last warp allocates tensor memory and loads the primitive's weight tiles with TMA
+//    tensor copies (cp.async.bulk.tensor, 128-byte swizzle) into shared memory whenever the
+//    primitive changes;
+//  * epilogue warpgroups (three for width 64, two for width 128) each own one chunk at a time,
+//    its A-operand tile in shared memory and 128 TMEM columns. A group builds the sample
+//    encodings (Eq. 5) as BF16 rows of the first A tile; its first thread issues the layer's
+//    tcgen05.mma and commits them to the group's mbarrier; once they complete, the group reads
+//    its accumulator rows from TMEM (thread = sample row), adds the bias, applies ReLU,
+//    converts to BF16 and writes the next layer's A tile in place. Groups run independently,
+//    so the tensor core works on one group's layer while the others run epilogues.
 //  * the last layer's epilogue applies sigmoid / softplus and composites each interval's S
 //    samples front to back (Eq. 6) with warp-level segmented scans, writing the interval's
 //    (C_j, a_j) exactly like the FP32 path.
@@ -88,7 +89,6 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
   float* sScan = reinterpret_cast<float*>(gbase + L.scan);
   const uint32_t bar_w = sbase + L.bars;
   const uint32_t bar_end = bar_w + 8;
-#define bar_ready(G) (bar_w + 16u + 8u * (uint32_t)(G))
 #define bar_done(G) (bar_w + 16u + 8u * (uint32_t)(kNEG) + 8u * (uint32_t)(G))
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(gbase + L.misc);
   volatile int* sAbort = reinterpret_cast<volatile int*>(gbase + L.misc + 4);
@@ -98,7 +98,6 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
     mbar_init(bar_w, 1);
     mbar_init(bar_end, 1);
     for (int g = 0; g < kNEG; ++g) {
-      mbar_init(bar_ready(g), kEGThreads);
       mbar_init(bar_done(g), 1);
     }
     *sAbort = 0;
@@ -122,10 +121,9 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
   const int q = warp & 3;                // TMEM lane quarter
   const int row = q * 32 + lane;         // sample row within the chunk
   // mbarrier phase parities, one bit per group (registers, no local memory)
-  uint32_t ph_w = 0, ph_ready = 0, ph_done = 0;
+  uint32_t ph_w = 0, ph_done = 0;
   int loaded = -1;
   int prim = cb < ce ? simt::find_prim(w, cb) : 0;
-  int nissued = 0;
 
   ChunkStep<kNEG> cur = chunk_step<kNEG>(w, cb, ce, prim);
   RecPrefetch pre;
@@ -219,7 +217,13 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
         }
         fence_proxy_async_smem();
         tc_fence_before();
-        mbar_arrive(bar_ready(g));
+        named_bar_sync(bar_id, kEGThreads);  // the whole A tile is written
+        const uint32_t dacc = tmem + (uint32_t)(g * 128);
+        if (row == 0) {  // this group issues its own MMAs
+          tc_fence_after();
+          if (!*sAbort) issue_fwd_layer(A, sbase + L.w + P.sw_off[0], dacc, P.kpad[0], P.npad[0]);
+          mma_commit(bar_done(g));
+        }
         const uint32_t trow = tmem + (uint32_t)(g * 128) + ((uint32_t)(q * 32) << 16);
         for (int l = 0; l < nl; ++l) {
           // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
@@ -255,7 +259,12 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
             }
             fence_proxy_async_smem();
             tc_fence_before();
-            mbar_arrive(bar_ready(g));
+            named_bar_sync(bar_id, kEGThreads);
+            if (row == 0) {
+              tc_fence_after();
+              if (!*sAbort) issue_fwd_layer(A, sbase + L.w + P.sw_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1]);
+              mma_commit(bar_done(g));
+            }
           } else {
             // last layer: heads, then the interval composite (NF = largest feature count)
             constexpr int NZ = 4 + NF;
@@ -308,30 +317,6 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
           }
         }
       }
-    } else if (lane == 0) {
-      // ------------------------------------------------------------ MMA issuer
-      for (int l = 0; l < nl; ++l) {
-        const uint32_t idesc = idesc_bf16(kM, P.npad[l]);
-        const uint32_t wl = sbase + L.w + P.sw_off[l];
-#pragma unroll
-        for (int j = 0; j < kNEG; ++j) {
-          if (step_chunk(cur, j) < 0) continue;
-          const bool ok = mbar_wait(bar_ready(j), (ph_ready >> j) & 1u, sAbort, kWaitNs);
-          ph_ready ^= 1u << j;
-          tc_fence_after();
-          if (ok) {
-            const uint32_t A = sbase + L.a0 + (uint32_t)j * L.a_stride;
-            const uint32_t d = tmem + (uint32_t)(j * 128);
-            for (int kk = 0; kk < P.kpad[l] / 16; ++kk) {
-              const uint32_t aa = A + (uint32_t)(kk >> 2) * (kM * 128) + (uint32_t)(kk & 3) * 32;
-              const uint32_t bb = wl + (uint32_t)(kk >> 2) * (P.npad[l] * 128) + (uint32_t)(kk & 3) * 32;
-              mma_bf16(d, sw128_desc(aa), sw128_desc(bb), idesc, kk > 0 ? 1u : 0u);
-            }
-            ++nissued;
-          }
-          mma_commit(bar_done(j));
-        }
-      }
     }
     cur = nxt;
   }
@@ -348,9 +333,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
     tmem_dealloc(tmem, kTmemCols);
   }
   if (threadIdx.x == 0 && *sAbort) set_status(w.saved_hdr, MLPS_ERR_TIMEOUT);
-#undef bar_ready
 #undef bar_done
-  (void)nissued;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -161,6 +161,27 @@ MLPS_DEV void build_row(const Model& m, const IntervalRec* T, int nint, int row,
   rw.pad_to(kpad0);
 }
 
+// Backward phase B_l of one chunk, issued by one thread of its group: dgrad into the group's
+// accumulator and wgrad into the block's shared weight-gradient accumulator of layer l
+// (always accumulating: it is cleared when the block starts a primitive).
+MLPS_DEV void issue_bwd_phase(uint32_t tiles, int l, int nl, uint32_t wtile, uint32_t acc,
+                              uint32_t dw_l, uint32_t ones, int kpad, int npad) {
+  const uint32_t Dl = tiles + (uint32_t)(l == nl - 1 ? 0 : l + 1) * kTile;  // delta_l
+  const uint32_t Hl = tiles + (uint32_t)l * kTile;                          // H_l
+  // dgrad: G = delta_l W_l with K = npad (outputs), N = kpad (inputs); B is the forward W_l
+  // tile read as an MN-major operand (inputs contiguous, outputs = K rows)
+  const uint32_t id_d = idesc_bf16(kM, kpad) | (1u << 16);
+  for (int kk = 0; kk < npad / 16; ++kk)
+    mma_bf16(acc, sw128_desc(Dl + (uint32_t)(kk & 3) * 32), sw128_desc_mn(wtile + (uint32_t)kk * 2048, 16),
+             id_d, kk > 0 ? 1u : 0u);
+  // wgrad: dW_l^T[in(+ones)][out] += H_l^T delta_l over the 128 rows
+  const uint32_t id_w = idesc_bf16(kM, 64) | (1u << 15) | (1u << 16);
+  const uint32_t lbo = ones - Hl;
+  for (int kk = 0; kk < kM / 16; ++kk)
+    mma_bf16(dw_l, sw128_desc_mn(Hl + (uint32_t)kk * 2048, lbo), sw128_desc_mn(Dl + (uint32_t)kk * 2048, 16),
+             id_w, 1u);
+}
+
 }  // namespace
 
 template <int NF, int XL, int DL>
@@ -178,7 +199,6 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   float* sScan = reinterpret_cast<float*>(gb + L.scan);
   float* sGeo = reinterpret_cast<float*>(gb + L.geo);
   const uint32_t bar_w = sbase + L.bars, bar_end = bar_w + 8;
-#define bar_ready(G) (bar_w + 16u + 8u * (uint32_t)(G))
 #define bar_done(G) (bar_w + 16u + 8u * (uint32_t)(kNG) + 8u * (uint32_t)(G))
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(gb + L.misc);
   volatile int* sAbort = reinterpret_cast<volatile int*>(gb + L.misc + 4);
@@ -189,7 +209,6 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     mbar_init(bar_w, 1);
     mbar_init(bar_end, 1);
     for (int g = 0; g < kNG; ++g) {
-      mbar_init(bar_ready(g), kEGThreads);
       mbar_init(bar_done(g), 1);
     }
     *sAbort = 0;
@@ -218,8 +237,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   const int g = warp >> 2, q = warp & 3, row = q * 32 + lane;
   // mbarrier phase parities and first-wgrad flags as bit sets (registers, no local memory)
-  uint32_t ph_w = 0, ph_ready = 0, ph_done = 0;
-  uint32_t first_wgrad = 0xFFu;
+  uint32_t ph_w = 0, ph_done = 0;
   int loaded = -1;
   int prim = cb < ce ? simt::find_prim(w, cb) : 0;
 
@@ -271,6 +289,12 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       tc_fence_before();
       __syncthreads();
       if (loaded >= 0) flush(loaded);
+      if (warp < 4) {  // clear the weight-gradient accumulators for the new primitive
+        const uint32_t lanebase = (uint32_t)(q * 32) << 16;
+        for (int c0 = 0; c0 < nl * 64; c0 += 32) tmem_st32_zero(tm_dw + (uint32_t)c0 + lanebase);
+        tmem_wait_st();
+      }
+      tc_fence_before();
       __syncthreads();
       if (threadIdx.x == kMmaWarpB * 32 && !*sAbort) {
         mbar_arrive_expect_tx(bar_w, (uint32_t)P.w_bytes);
@@ -290,7 +314,6 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       }
       mbar_wait(bar_w, ph_w, sAbort, kWaitNsB);
       ph_w ^= 1;
-      first_wgrad = 0xFFu;
       __syncthreads();
       loaded = prim;
     }
@@ -329,13 +352,19 @@ __global__ void __launch_bounds__(kThreadsB, 1)
 #define tileaddr(I) (tiles + (uint32_t)(I) * kTile)
         const int iv = row / S, k = row - iv * S;
         const bool valid = iv < nint;
-        const uint32_t trow = tmem + (uint32_t)(g * 64) + ((uint32_t)(q * 32) << 16);
+        const uint32_t acc = tmem + (uint32_t)(g * 64);  // this group's dgrad / forward accumulator
+        const uint32_t trow = acc + ((uint32_t)(q * 32) << 16);
 
         if (DL >= 0) build_row_fast<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
         else build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
         fence_proxy_async_smem();
         tc_fence_before();
-        mbar_arrive(bar_ready(g));
+        named_bar_sync(bar_id, kEGThreads);
+        if (row == 0) {  // this group issues its own MMAs
+          tc_fence_after();
+          if (!*sAbort) issue_fwd_layer(tileaddr(0), sbase + L.w + P.sw_off[0], acc, P.kpad[0], P.npad[0]);
+          mma_commit(bar_done(g));
+        }
 
         // ---------------- forward recompute
         for (int l = 0; l < nl; ++l) {
@@ -369,7 +398,13 @@ __global__ void __launch_bounds__(kThreadsB, 1)
             store_row64(tileaddr(l + 1), row, pk);
             fence_proxy_async_smem();
             tc_fence_before();
-            mbar_arrive(bar_ready(g));
+            named_bar_sync(bar_id, kEGThreads);
+            if (row == 0) {
+              tc_fence_after();
+              if (!*sAbort)
+                issue_fwd_layer(tileaddr(l + 1), sbase + L.w + P.sw_off[l + 1], acc, P.kpad[l + 1], P.npad[l + 1]);
+              mma_commit(bar_done(g));
+            }
           } else {
             // ---------------- heads and reverse of the interval composite -> dL/dZ into T_0
             float z[4 + NF];
@@ -442,7 +477,14 @@ __global__ void __launch_bounds__(kThreadsB, 1)
             store_row64(tileaddr(0), row, pk);
             fence_proxy_async_smem();
             tc_fence_before();
-            mbar_arrive(bar_ready(g));
+            named_bar_sync(bar_id, kEGThreads);
+            if (row == 0) {
+              tc_fence_after();
+              if (!*sAbort)
+                issue_bwd_phase(tiles, nl - 1, nl, sbase + L.w + P.sw_off[nl - 1], acc, tm_dw + (uint32_t)((nl - 1) * 64),
+                                sbase + L.ones, P.kpad[nl - 1], P.npad[nl - 1]);
+              mma_commit(bar_done(g));
+            }
           }
         }
         // ---------------- backward phases B_{nl-1} .. B_0
@@ -487,7 +529,14 @@ __global__ void __launch_bounds__(kThreadsB, 1)
             }
             fence_proxy_async_smem();
             tc_fence_before();
-            mbar_arrive(bar_ready(g));
+            named_bar_sync(bar_id, kEGThreads);
+            if (row == 0) {
+              tc_fence_after();
+              if (!*sAbort)
+                issue_bwd_phase(tiles, l - 1, nl, sbase + L.w + P.sw_off[l - 1], acc, tm_dw + (uint32_t)((l - 1) * 64),
+                                sbase + L.ones, P.kpad[l - 1], P.npad[l - 1]);
+              mma_commit(bar_done(g));
+            }
           } else {
             // ---------------- encoding derivative and pose chain
             float G[64];
@@ -575,51 +624,6 @@ __global__ void __launch_bounds__(kThreadsB, 1)
           }
         }
       }
-    } else if (warp == kMmaWarpB && lane == 0) {
-      // ============================================================ MMA issuer
-      for (int ph = 0; ph < 2 * nl; ++ph) {
-#pragma unroll
-        for (int j = 0; j < kNG; ++j) {
-          if (step_chunk(cur, j) < 0) continue;
-          const bool ok = mbar_wait(bar_ready(j), (ph_ready >> j) & 1u, sAbort, kWaitNsB);
-          ph_ready ^= 1u << j;
-          tc_fence_after();
-          if (ok) {
-            const uint32_t tiles = sbase + L.tiles0 + (uint32_t)j * L.tiles_stride;
-            const uint32_t acc = tmem + (uint32_t)(j * 64);
-            if (ph < nl) {
-              const int l = ph;  // F_l
-              const uint32_t A = tiles + (uint32_t)l * kTile;
-              const uint32_t B = sbase + L.w + P.sw_off[l];
-              const uint32_t idesc = idesc_bf16(kM, P.npad[l]);
-              for (int kk = 0; kk < P.kpad[l] / 16; ++kk)
-                mma_bf16(acc, sw128_desc(A + (uint32_t)(kk & 3) * 32), sw128_desc(B + (uint32_t)(kk & 3) * 32),
-                         idesc, kk > 0 ? 1u : 0u);
-            } else {
-              const int l = 2 * nl - 1 - ph;  // B_l
-              const uint32_t Dl = tiles + (uint32_t)(l == nl - 1 ? 0 : l + 1) * kTile;  // delta_l
-              const uint32_t Hl = tiles + (uint32_t)l * kTile;                          // H_l
-              // dgrad: G = delta_l W_l with K = npad[l] (outputs), N = kpad[l] (inputs); B is the
-              // forward W_l tile read as an MN-major operand (inputs contiguous, outputs = K rows)
-              const uint32_t Wl = sbase + L.w + P.sw_off[l];
-              const uint32_t id_d = idesc_bf16(kM, P.kpad[l]) | (1u << 16);
-              for (int kk = 0; kk < P.npad[l] / 16; ++kk)
-                mma_bf16(acc, sw128_desc(Dl + (uint32_t)(kk & 3) * 32),
-                         sw128_desc_mn(Wl + (uint32_t)kk * 2048, 16), id_d, kk > 0 ? 1u : 0u);
-              // wgrad: dW_l^T[in(+ones)][out] += H_l^T delta_l over the 128 rows
-              const uint32_t id_w = idesc_bf16(kM, 64) | (1u << 15) | (1u << 16);
-              const uint32_t lbo = (sbase + L.ones) - Hl;
-              for (int kk = 0; kk < kM / 16; ++kk) {
-                const uint32_t acc_flag = (((first_wgrad >> l) & 1u) && kk == 0) ? 0u : 1u;
-                mma_bf16(tm_dw + (uint32_t)(l * 64), sw128_desc_mn(Hl + (uint32_t)kk * 2048, lbo),
-                         sw128_desc_mn(Dl + (uint32_t)kk * 2048, 16), id_w, acc_flag);
-              }
-              first_wgrad &= ~(1u << l);
-            }
-          }
-          mma_commit(bar_done(j));
-        }
-      }
     }
     cur = nxt;
   }
@@ -638,7 +642,6 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     tmem_dealloc(tmem, kTmemColsB);
   }
   if (threadIdx.x == 0 && *sAbort) set_status(w.scr_hdr, MLPS_ERR_TIMEOUT);
-#undef bar_ready
 #undef bar_done
 #undef tileaddr
 }

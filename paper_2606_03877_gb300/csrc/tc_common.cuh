@@ -116,6 +116,17 @@ MLPS_DEV void seg_scan_rev(float (&v)[NV], int nv, int row, int S, float* scratc
   named_bar_sync(bar_id, kEGThreads);
 }
 
+// MMAs of one forward layer of a 128-row chunk: D[128 x npad] = A[128 x kpad] W^T, A and W in
+// the K-major swizzled layout, K in 64-column slabs. Issued by one thread.
+MLPS_DEV void issue_fwd_layer(uint32_t A, uint32_t W, uint32_t d, int kpad, int npad) {
+  const uint32_t idesc = idesc_bf16(kM, npad);
+  for (int kk = 0; kk < kpad / 16; ++kk) {
+    const uint32_t aa = A + (uint32_t)(kk >> 2) * (kM * 128) + (uint32_t)(kk & 3) * 32;
+    const uint32_t bb = W + (uint32_t)(kk >> 2) * (uint32_t)(npad * 128) + (uint32_t)(kk & 3) * 32;
+    mma_bf16(d, sw128_desc(aa), sw128_desc(bb), idesc, kk > 0 ? 1u : 0u);
+  }
+}
+
 // One step of a block's chunk schedule: up to NG consecutive chunks of the same primitive,
 // one per epilogue group. Every role evaluates the same schedule.
 template <int NG>
