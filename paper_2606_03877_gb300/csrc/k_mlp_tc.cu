@@ -4,10 +4,11 @@
 // Same work decomposition as the FP32 path: a chunk is up to ipc = 128 / S hit intervals of one
 // primitive, i.e. one M = 128 tile of sample rows; persistent blocks walk a contiguous range
 // of the primitive-major chunk list. Inside a block:
-//  * the last warp allocates tensor memory and loads the primitive's weight tiles with TMA
+//  * warp 0 allocates tensor memory; thread 0 loads the primitive's weight tiles with TMA
 //    tensor copies (cp.async.bulk.tensor, 128-byte swizzle) into shared memory whenever the
 //    primitive changes;
-//  * epilogue warpgroups (three for width 64, two for width 128) each own one chunk at a time,
+//  * epilogue warpgroups (four for width 64, three with a feature head, two for width 128;
+//    every warp of the block belongs to one) each own one chunk at a time,
 //    its A-operand tile in shared memory and 128 TMEM columns. A group builds the sample
 //    encodings (Eq. 5) as BF16 rows of the first A tile; its first thread issues the layer's
 //    tcgen05.mma and commits them to the group's mbarrier; once they complete, the group reads
@@ -38,9 +39,8 @@ namespace tc {
 
 using simt::IntervalInfo;
 
-constexpr int kMaxNEG = 3;                      // epilogue groups = chunks in flight (<= 3)
-constexpr int threads_tc(int neg) { return kEGThreads * neg + 32; }
-constexpr uint32_t kTmemCols = 512;             // 128 per group
+constexpr int threads_tc(int neg) { return kEGThreads * neg; }
+constexpr uint32_t kTmemCols = 512;             // 128 per group (at most four groups)
 constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s
 // Byte offsets in dynamic shared memory; per-group regions are base + g * stride (plain
 // arithmetic, so that nothing is indexed at run time).
@@ -74,10 +74,10 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG) {
 }
 
 template <int WIDTH, int XL, int DL, int NF, int kNEG>
-__global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
+__global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     k_mlp_fwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
-  constexpr int kThreadsTC = kEGThreads * kNEG + 32;
-  constexpr int kMmaWarp = kNEG * 4;
+  constexpr int kThreadsTC = kEGThreads * kNEG;
+  static_assert(kNEG >= 1 && kNEG <= 4 && kNEG * WIDTH <= 4 * 128, "TMEM holds 512 columns");
   static_assert(4 + NF <= kMaxScanVals, "scan scratch holds kMaxScanVals values per warp");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
   float* sBias = reinterpret_cast<float*>(gbase + L.bias);
   float* sScan = reinterpret_cast<float*>(gbase + L.scan);
   const uint32_t bar_w = sbase + L.bars;
-  const uint32_t bar_end = bar_w + 8;
+#define bar_end(G) (bar_w + 16u + 8u * (uint32_t)(G))
 #define bar_done(G) (bar_w + 16u + 8u * (uint32_t)(kNEG) + 8u * (uint32_t)(G))
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(gbase + L.misc);
   volatile int* sAbort = reinterpret_cast<volatile int*>(gbase + L.misc + 4);
@@ -96,14 +96,14 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(bar_w, 1);
-    mbar_init(bar_end, 1);
     for (int g = 0; g < kNEG; ++g) {
       mbar_init(bar_done(g), 1);
+      mbar_init(bar_end(g), 1);
     }
     *sAbort = 0;
     fence_mbar_init();
   }
-  if (warp == kMmaWarp) {
+  if (warp == 0) {
     tmem_alloc(sbase + L.misc, kTmemCols);
     tmem_relinquish();
   }
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
   RecPrefetch pre;
   pre.valid = 0;
   const int my_first = step_chunk(cur, g);
-  if (warp < kMmaWarp && cur.n > 0 && my_first >= 0) {
+  if (cur.n > 0 && my_first >= 0) {
     const int f0 = (my_first - w.chunk_start[cur.prim]) * w.ipc;
     if (row < min(w.ipc, w.prim_count[cur.prim] - f0)) rec_prefetch(w, w.prim_start[cur.prim] + f0 + row, false, pre);
   }
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
     const int my_nx = step_chunk(nxt, g);
     if (prim != loaded) {
       __syncthreads();  // every role is done with the previous primitive's tiles
-      if (threadIdx.x == kMmaWarp * 32 && !*sAbort) {
+      if (threadIdx.x == 0 && !*sAbort) {
         mbar_arrive_expect_tx(bar_w, (uint32_t)P.w_bytes);
         const int row0 = prim * P.rows_per_prim;
         for (int l = 0; l < nl; ++l)
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
       loaded = prim;
     }
 
-    if (warp < kMmaWarp) {
+    {
       // ------------------------------------------------------------ epilogue group g
       if (my_cc < 0 && nxt.n > 0 && my_nx >= 0) {  // idle this step: still prefetch
         const int f1 = (my_nx - w.chunk_start[nxt.prim]) * w.ipc;
@@ -321,19 +321,21 @@ __global__ void __launch_bounds__(kEGThreads * kNEG + 32, 1)
     cur = nxt;
   }
 
-  // teardown: make sure no MMA is still writing TMEM, then free it
-  if (warp == kMmaWarp && lane == 0) {
-    mma_commit(bar_end);
-    mbar_wait(bar_end, 0, sAbort, kWaitNs);
+  // teardown: make sure none of this group's MMAs still writes TMEM (after an abort a group
+  // may have stopped waiting for them), then free it
+  if ((threadIdx.x & (kEGThreads - 1)) == 0) {
+    mma_commit(bar_end(g));
+    mbar_wait_limit(bar_end(g), 0, kWaitNs);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == kMmaWarp) {
+  if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, kTmemCols);
   }
   if (threadIdx.x == 0 && *sAbort) set_status(w.saved_hdr, MLPS_ERR_TIMEOUT);
 #undef bar_done
+#undef bar_end
 }
 
 // ------------------------------------------------------------------------------------------
@@ -399,11 +401,14 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride) {
   return true;
 }
 
-static int fwd_groups(int width) { return width == 64 ? 3 : 2; }
+// Epilogue groups of the forward kernel: registers cap the feature-head variants at three
+// groups (the head keeps 4 + 32 values per thread), TMEM caps width 128 at four and shared
+// memory (a 32 KB operand tile per group) at two.
+static int fwd_groups(int width, int F) { return width == 64 ? (F > 0 ? 3 : 4) : 2; }
 
-size_t tc_smem_bytes(const TcPlan& P) {
+size_t tc_smem_bytes(const TcPlan& P, int F) {
   const int width = P.npad[0];  // hidden width = N of layer 0
-  return tc::tc_smem(P, fwd_groups(width)).total + 1024;
+  return tc::tc_smem(P, fwd_groups(width, F)).total + 1024;
 }
 
 void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
@@ -438,20 +443,18 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes(P);
+  const size_t smem = tc_smem_bytes(P, a.m.F);
   if (smem > 227 * 1024) return cudaErrorNotSupported;
   const int xl = a.m.xyzL, dl = a.m.dirL;
   const bool fast64 = xl == 6 && dl == 4 && P.kpad[0] == 64;
   const bool raw = xl == 0 && dl == 0 && P.kpad[0] == 64;
-  decltype(&tc::k_mlp_fwd_tc<64, 6, 4, 0, 3>) kern;
+  decltype(&tc::k_mlp_fwd_tc<64, 6, 4, 0, 4>) kern;
   const bool feat = a.m.F > 0;
-  int neg = 0;
+  const int neg = fwd_groups(a.m.width, a.m.F);
   if (a.m.width == 64) {
-    neg = 3;
-    if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, 0, 3> : raw ? tc::k_mlp_fwd_tc<64, 0, 0, 0, 3> : tc::k_mlp_fwd_tc<64, -1, -1, 0, 3>;
+    if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, 0, 4> : raw ? tc::k_mlp_fwd_tc<64, 0, 0, 0, 4> : tc::k_mlp_fwd_tc<64, -1, -1, 0, 4>;
     else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, kMaxFeat, 3> : tc::k_mlp_fwd_tc<64, -1, -1, kMaxFeat, 3>;
   } else if (a.m.width == 128) {
-    neg = 2;
     if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 0, 2> : tc::k_mlp_fwd_tc<128, -1, -1, 0, 2>;
     else kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, kMaxFeat, 2> : tc::k_mlp_fwd_tc<128, -1, -1, kMaxFeat, 2>;
   } else {

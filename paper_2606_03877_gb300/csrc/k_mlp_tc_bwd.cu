@@ -1,7 +1,9 @@
 // k_mlp_tc_bwd.cu -- BF16 tensor-core (tcgen05) backward of the grouped per-primitive MLP stage.
 //
 // Per chunk of 128 sample rows of one primitive (same chunks as the forward pass), one epilogue
-// group (4 warps, thread = sample row) and the MMA warp run 2 * nl phases:
+// group runs 2 * nl phases. A group is 8 warps: warp (q, h) owns TMEM lane quarter q (sample
+// rows 32q .. 32q + 31) and column half h of every 64-wide operand row, so each thread handles
+// one sample row and 32 of its columns. Phases:
 //   F_l  (l = 0 .. nl-1): Z_l = H_l W_l^T recomputes the forward; the epilogue writes
 //        H_{l+1} = ReLU(Z_l + b_l) as BF16 into the group's tile T_{l+1};
 //   B_l  (l = nl-1 .. 0): dgrad  G = delta_l W_l          (A = delta_l, K-major; B = the forward
@@ -12,14 +14,21 @@
 //                                row 64 of the accumulator collects the bias gradient
 //                                sum_rows delta_l); the epilogue forms
 //                                delta_{l-1} = G * [H_l > 0] in place of H_l.
+// The MMAs of a phase are issued by the group's first thread right after a group-local barrier.
+// dgrad and wgrad are committed separately: the epilogue of B_l starts once its dgrad is done and
+// waits for the wgrad (which still reads H_l) only before it overwrites T_l.
 // delta_{nl-1} = dL/dZ comes from the last forward epilogue: the reverse of the interval
-// composite of Eq. 6 with segmented suffix scans (see k_mlp_simt_bwd.cu for the formulas).
+// composite of Eq. 6 with segmented suffix scans (see k_mlp_simt_bwd.cu for the formulas),
+// computed by the column-half-0 warps of the group (one thread per sample row).
 // The input-encoding gradient G_enc = delta_0 W_0 feeds the encoding derivative and the pose
 // chain (closest-point form, no cancellation), reduced per interval and per block.
-// The weight-gradient accumulators live in TMEM for the whole primitive segment of the block,
-// shared by both epilogue groups (their MMAs are issued in order by one thread), and are
-// flushed to global memory with one atomicAdd per entry when the primitive changes.
-// Tiles per group: T_0 (H_0, then dL/dZ, then H_0 rebuilt for the last wgrad), T_1 .. T_{nl-1}.
+// The weight-gradient accumulators live in TMEM for the whole primitive segment of the block and
+// are shared by both groups: they are cleared with tcgen05.st when the block starts a primitive,
+// every wgrad MMA accumulates into them, and they are flushed to global memory with one
+// atomicAdd per entry when the primitive changes.
+// Tiles per group: T_0 = H_0 (the encoded input), T_l = H_l, E = dL/dZ; delta_{l-1} replaces H_l
+// in T_l. The per-interval sums of the pose chain reduce to two 3-vectors per interval, because
+// the sample positions are affine in the sample index.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -40,17 +49,19 @@ using simt::IntervalInfo;
 
 namespace {
 
-constexpr int kNG = 2;                              // epilogue groups
-constexpr int kThreadsB = kEGThreads * kNG + 32;
-constexpr int kMmaWarpB = 4 * kNG;
-constexpr uint32_t kTmemColsB = 512;
+constexpr int kNG = 2;                              // epilogue groups (chunks in flight)
+constexpr int kGW = 8;                              // warps per group: 4 lane quarters x 2 column halves
+constexpr int kGThreads = 32 * kGW;
+constexpr int kThreadsB = kGThreads * kNG;
+constexpr uint32_t kTmemColsB = 512;                // 64 per group + 64 per layer (weight gradients)
 constexpr uint64_t kWaitNsB = 2000000000ull;
 constexpr uint32_t kTile = kM * 128;                // one [128 x 64] BF16 tile
+constexpr uint32_t kOnes = 2048;                    // 16 rows of the MN-major ones atom (one K step)
 
 // Byte offsets in dynamic shared memory; per-group regions are base + g * stride.
 struct BwdSmem {
-  uint32_t w, wt, tiles0, tiles_stride, ones, bias, grp0, grp_stride, itab, giv, ddel, gf, scan,
-      geo, pgeo, bars, misc, total;  // itab/giv/ddel/gf: offsets inside one group's block
+  uint32_t w, wt, tiles0, tiles_stride, ones, bias, grp0, grp_stride, itab, giv, ddel, gf, xch,
+      scan, geo, pgeo, bars, misc, total;  // itab/giv/ddel/gf/xch: offsets inside one group's block
 };
 
 MLPS_HD uint32_t al(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -62,10 +73,10 @@ MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F) {
   o = al(o + P.w_bytes, 1024);
   L.wt = o;
   L.tiles0 = o;
-  L.tiles_stride = al((uint32_t)P.nl * kTile, 1024);  // T_0 .. T_{nl-1}
+  L.tiles_stride = al((uint32_t)(P.nl + 1) * kTile, 1024);  // T_0 .. T_{nl-1} and E
   o += L.tiles_stride * kNG;
   L.ones = o;  // above every group tile: the wgrad descriptors reach it with a positive offset
-  o = al(o + kTile, 1024);
+  o = al(o + kOnes, 1024);
   L.bias = o;
   o = al(o + 4 * P.bias_floats, 16);
   uint32_t q = 0;
@@ -77,6 +88,8 @@ MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F) {
   q = al(q + 4 * kM, 16);
   L.gf = q;
   q = al(q + 4 * kM * (F > 0 ? F : 1), 16);
+  L.xch = q;  // column half 1 -> half 0 exchange of the encoding-gradient partial sums
+  q = al(q + 4 * kM, 16);
   L.grp0 = o;
   L.grp_stride = q;
   o += q * kNG;
@@ -87,7 +100,7 @@ MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F) {
   L.pgeo = o;  // the current primitive's geometry (staged at every primitive change)
   o = al(o + (uint32_t)sizeof(PrimGeo), 16);
   L.bars = o;
-  o = al(o + 8 * (2 + 2 * kNG), 16);
+  o = al(o + 8 * (2 + 3 * kNG), 16);
   L.misc = o;
   o = al(o + 16, 16);
   L.total = o;
@@ -106,11 +119,12 @@ MLPS_DEV uint64_t sw128_desc_mn(uint32_t saddr, uint32_t lbo) {
   return d;
 }
 
-// Store 64 values of one row (already BF16-packed pairs) into a swizzled tile.
-MLPS_DEV void store_row64(uint32_t tile, int row, const uint32_t (&pk)[32]) {
+// Store one column half (32 values, BF16-packed pairs) of one row into a swizzled tile.
+MLPS_DEV void store_half(uint32_t tile, int row, int half, const uint32_t (&pk)[16]) {
 #pragma unroll
-  for (int ch = 0; ch < 8; ++ch)
-    st_shared_v4(tile + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+  for (int ch = 0; ch < 4; ++ch)
+    st_shared_v4(tile + sw128_off(row, 4 * half + ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2],
+                 pk[4 * ch + 3]);
 }
 
 MLPS_DEV void ld_shared_v4(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
@@ -120,24 +134,99 @@ MLPS_DEV void ld_shared_v4(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c,
                : "memory");
 }
 
-// Build the encoded input row (Eq. 5) of one sample into tile `A` (zeros for invalid rows).
+// Column half H (BF16 pairs 16H .. 16H + 15) of the encoded input row (Eq. 5) with compile-time
+// frequency counts; same angle-doubling recurrence and pair order as the forward kernel.
+template <int XL, int DL, int H>
+MLPS_DEV void encode_half(const float (&xl)[3], const float (&d)[3], uint32_t (&pk)[16]) {
+  constexpr int NX = XL > 0 ? 6 * XL : 3;
+  static_assert(NX + (DL > 0 ? 6 * DL : 0) <= 64, "encoded input wider than one 64-column tile");
+#pragma unroll
+  for (int e = 0; e < 16; ++e) pk[e] = 0u;
+  if (XL == 0) {
+    if (H == 0) {
+      pk[0] = pack_bf16(xl[0], xl[1]);
+      pk[1] = pack_bf16(xl[2], 0.f);
+    }
+    return;
+  }
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    if ((u + 1) * XL <= 16 * H || u * XL >= 16 * H + 16) continue;  // no pair of u in this half
+    float sn, cs;
+    __sincosf(3.14159265358979f * xl[u], &sn, &cs);
+#pragma unroll
+    for (int l = 0; l < (XL > 0 ? XL : 1); ++l) {
+      const int idx = u * XL + l - 16 * H;
+      if (idx >= 0 && idx < 16) pk[idx] = pack_bf16(sn, cs);
+      const float s2 = 2.f * sn * cs;
+      cs = fmaf(-2.f * sn, sn, 1.f);
+      sn = s2;
+    }
+  }
+  if (DL > 0) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      if (NX / 2 + (u + 1) * DL <= 16 * H || NX / 2 + u * DL >= 16 * H + 16) continue;
+      float sn, cs;
+      __sincosf(3.14159265358979f * d[u], &sn, &cs);
+#pragma unroll
+      for (int l = 0; l < (DL > 0 ? DL : 1); ++l) {
+        const int idx = NX / 2 + u * DL + l - 16 * H;
+        if (idx >= 0 && idx < 16) pk[idx] = pack_bf16(sn, cs);
+        const float s2 = 2.f * sn * cs;
+        cs = fmaf(-2.f * sn, sn, 1.f);
+        sn = s2;
+      }
+    }
+  }
+}
+
+// Build column half `half` of the encoded input row of one sample into tile `A` (zeros for
+// rows past the chunk's intervals).
 template <int XL, int DL>
-MLPS_DEV void build_row_fast(const IntervalRec* T, int nint, int S, int row, uint32_t A) {
+MLPS_DEV void build_half(const IntervalRec* T, int nint, int S, int row, int half, uint32_t A) {
   const int iv = row / S, k = row - iv * S;
-  uint32_t pk[32];
+  uint32_t pk[16];
   if (iv < nint) {
     const IntervalRec& I = T[iv];
     const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
     float xl[3], d[3];
     for (int u = 0; u < 3; ++u) { xl[u] = fmaf(tr, I.dp[u], I.p[u]); d[u] = I.d[u]; }
-    encode_pairs64<XL, DL>(xl, d, pk);
+    if (half == 0) encode_half<XL, DL, 0>(xl, d, pk);
+    else encode_half<XL, DL, 1>(xl, d, pk);
   } else {
 #pragma unroll
-    for (int e = 0; e < 32; ++e) pk[e] = 0u;
+    for (int e = 0; e < 16; ++e) pk[e] = 0u;
+  }
+  store_half(A, row, half, pk);
+}
+
+// Contribution of column half H of dL/dX (32 values in registers) to dL/dx_local through the
+// encoding of Eq. 5: d/dx [sin(2^l pi x), cos(2^l pi x)] = 2^l pi [cos, -sin].
+template <int XL, int H>
+MLPS_DEV void enc_grad_half(const float (&xl)[3], const uint32_t (&v)[32], float (&gx)[3]) {
+  if (XL == 0) {
+    if (H == 0)
+      for (int u = 0; u < 3; ++u) gx[u] += __uint_as_float(v[u]);
+    return;
   }
 #pragma unroll
-  for (int ch = 0; ch < 8; ++ch)
-    st_shared_v4(A + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+  for (int u = 0; u < 3; ++u) {
+    if ((u + 1) * XL <= 16 * H || u * XL >= 16 * H + 16) continue;
+    float sn, cs;
+    __sincosf(3.14159265358979f * xl[u], &sn, &cs);
+    float wq = 3.14159265358979f;
+#pragma unroll
+    for (int l = 0; l < (XL > 0 ? XL : 1); ++l) {
+      const int col = 2 * (u * XL + l) - 32 * H;
+      if (col >= 0 && col < 32)
+        gx[u] += wq * (__uint_as_float(v[col]) * cs - __uint_as_float(v[col + 1]) * sn);
+      const float s2 = 2.f * sn * cs;
+      cs = fmaf(-2.f * sn, sn, 1.f);
+      sn = s2;
+      wq *= 2.f;
+    }
+  }
 }
 
 MLPS_DEV void build_row(const Model& m, const IntervalRec* T, int nint, int row, uint32_t A,
@@ -161,25 +250,26 @@ MLPS_DEV void build_row(const Model& m, const IntervalRec* T, int nint, int row,
   rw.pad_to(kpad0);
 }
 
-// Backward phase B_l of one chunk, issued by one thread of its group: dgrad into the group's
-// accumulator and wgrad into the block's shared weight-gradient accumulator of layer l
-// (always accumulating: it is cleared when the block starts a primitive).
-MLPS_DEV void issue_bwd_phase(uint32_t tiles, int l, int nl, uint32_t wtile, uint32_t acc,
-                              uint32_t dw_l, uint32_t ones, int kpad, int npad) {
-  const uint32_t Dl = tiles + (uint32_t)(l == nl - 1 ? 0 : l + 1) * kTile;  // delta_l
-  const uint32_t Hl = tiles + (uint32_t)l * kTile;                          // H_l
-  // dgrad: G = delta_l W_l with K = npad (outputs), N = kpad (inputs); B is the forward W_l
-  // tile read as an MN-major operand (inputs contiguous, outputs = K rows)
-  const uint32_t id_d = idesc_bf16(kM, kpad) | (1u << 16);
+// dgrad of phase B_l, issued by one thread of the group: G = delta_l W_l into the group's
+// accumulator, K = npad (outputs of layer l), N = kpad (its inputs). A = delta_l (K-major tile);
+// B = the forward W_l tile read as an MN-major operand (inputs contiguous, outputs = K rows).
+MLPS_DEV void issue_dgrad(uint32_t Dl, uint32_t wtile, uint32_t acc, int kpad, int npad) {
+  const uint32_t id = idesc_bf16(kM, kpad) | (1u << 16);
   for (int kk = 0; kk < npad / 16; ++kk)
-    mma_bf16(acc, sw128_desc(Dl + (uint32_t)(kk & 3) * 32), sw128_desc_mn(wtile + (uint32_t)kk * 2048, 16),
-             id_d, kk > 0 ? 1u : 0u);
-  // wgrad: dW_l^T[in(+ones)][out] += H_l^T delta_l over the 128 rows
-  const uint32_t id_w = idesc_bf16(kM, 64) | (1u << 15) | (1u << 16);
-  const uint32_t lbo = ones - Hl;
-  for (int kk = 0; kk < kM / 16; ++kk)
-    mma_bf16(dw_l, sw128_desc_mn(Hl + (uint32_t)kk * 2048, lbo), sw128_desc_mn(Dl + (uint32_t)kk * 2048, 16),
-             id_w, 1u);
+    mma_bf16(acc, sw128_desc(Dl + (uint32_t)(kk & 3) * 32), sw128_desc_mn(wtile + (uint32_t)kk * 2048, 16), id,
+             kk > 0 ? 1u : 0u);
+}
+
+// wgrad of phase B_l: dW_l^T[in (+ones)][out] += H_l^T delta_l over the 128 rows (K = rows).
+// A = [H_l | ones] as MN-major atoms (the ones atom's offset is given per K step, so a single
+// 16-row ones block serves every step); B = delta_l MN-major, N = npad (outputs of layer l).
+// Always accumulates: the accumulator is cleared when the block starts a primitive.
+MLPS_DEV void issue_wgrad(uint32_t Hl, uint32_t Dl, uint32_t dw_l, uint32_t ones, int npad) {
+  const uint32_t id = idesc_bf16(kM, npad) | (1u << 15) | (1u << 16);
+  for (int kk = 0; kk < kM / 16; ++kk) {
+    const uint32_t ha = Hl + (uint32_t)kk * 2048;
+    mma_bf16(dw_l, sw128_desc_mn(ha, ones - ha), sw128_desc_mn(Dl + (uint32_t)kk * 2048, 16), id, 1u);
+  }
 }
 
 }  // namespace
@@ -194,35 +284,45 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   const Model& m = a.m;
   const int F = m.F;
   static_assert(14 <= kMaxScanVals && 3 + NF <= kMaxScanVals, "scan scratch holds kMaxScanVals values per warp");
+  static_assert(4 + NF <= 16 && NF % 2 == 0, "the head's outputs lie in the first 16 columns");
+  static_assert(XL <= 8, "the x and y encoding columns lie in column half 0");
   const BwdSmem L = bwd_layout(P, F);
   float* sBias = reinterpret_cast<float*>(gb + L.bias);
   float* sScan = reinterpret_cast<float*>(gb + L.scan);
   float* sGeo = reinterpret_cast<float*>(gb + L.geo);
-  const uint32_t bar_w = sbase + L.bars, bar_end = bar_w + 8;
+  const uint32_t bar_w = sbase + L.bars;
+#define bar_end(G) (bar_w + 16u + 8u * (uint32_t)(G))
 #define bar_done(G) (bar_w + 16u + 8u * (uint32_t)(kNG) + 8u * (uint32_t)(G))
+#define bar_wg(G) (bar_w + 16u + 16u * (uint32_t)(kNG) + 8u * (uint32_t)(G))
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(gb + L.misc);
   volatile int* sAbort = reinterpret_cast<volatile int*>(gb + L.misc + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nl = m.nl, S = m.S;
+  const int g = warp / kGW, wg = warp - g * kGW;  // group, warp within the group
+  const int q = wg & 3, half = wg >> 2;           // TMEM lane quarter, column half
+  const int row = q * 32 + lane;                  // sample row within the chunk
+  const int gbar = 1 + g, hbar = 1 + kNG + g;     // named barriers: whole group, half 0
+  const bool issuer = wg == 0 && lane == 0;       // issues the group's MMAs
 
   if (threadIdx.x == 0) {
     mbar_init(bar_w, 1);
-    mbar_init(bar_end, 1);
-    for (int g = 0; g < kNG; ++g) {
-      mbar_init(bar_done(g), 1);
+    for (int gg = 0; gg < kNG; ++gg) {
+      mbar_init(bar_done(gg), 1);
+      mbar_init(bar_wg(gg), 1);
+      mbar_init(bar_end(gg), 1);
     }
     *sAbort = 0;
     fence_mbar_init();
   }
   // constant ones atom: element 0 of every row is 1.0 (BF16 0x3F80)
-  for (int i = threadIdx.x; i < (int)(kTile / 16); i += kThreadsB) {
+  for (int i = threadIdx.x; i < (int)(kOnes / 16); i += kThreadsB) {
     const int r = i >> 3, ch = i & 7;
     const uint32_t one = ((ch ^ (r & 7)) == 0) ? 0x3F80u : 0u;  // chunk 0 of row r lands at r & 7
     st_shared_v4(sbase + L.ones + (uint32_t)i * 16, one, 0u, 0u, 0u);
   }
   if (threadIdx.x < 16) sGeo[threadIdx.x] = 0.f;
   fence_proxy_async_smem();
-  if (warp == kMmaWarpB) {
+  if (warp == 0) {
     tmem_alloc(sbase + L.misc, kTmemColsB);
     tmem_relinquish();
   }
@@ -230,14 +330,17 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
-  const uint32_t tm_dw = tmem + 128;  // weight-gradient accumulators: 64 columns per layer
+  const uint32_t tm_dw = tmem + 64 * kNG;  // weight-gradient accumulators: 64 columns per layer
 
   const int total = w.saved_hdr[2];
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
-  const int g = warp >> 2, q = warp & 3, row = q * 32 + lane;
-  // mbarrier phase parities and first-wgrad flags as bit sets (registers, no local memory)
-  uint32_t ph_w = 0, ph_done = 0;
+  // mbarrier phase parities as bit sets (registers, no local memory)
+  // phase parities of bar_w and of this group's bar_done (forward layers and dgrad) and bar_wg
+  // (wgrad). Each barrier gets its next commit only after its previous phase was waited for, so
+  // it is never two phases ahead of its waiters (a parity wait could not tell those apart).
+  uint32_t ph_w = 0, ph = 0, ph_g = 0;
+  const float invS = 1.f / (float)S;
   int loaded = -1;
   int prim = cb < ce ? simt::find_prim(w, cb) : 0;
 
@@ -246,7 +349,8 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     if (warp < 4) {
       tc_fence_after();
       float* dW = a.d_weights + (size_t)p * m.P;
-      const uint32_t lanebase = (uint32_t)(q * 32) << 16;
+      const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
+      const int frow = warp * 32 + lane;
       for (int l = 0; l < nl; ++l) {
         const int din = m.din[l], dout = m.dout[l];
         for (int c0 = 0; c0 < 64; c0 += 32) {
@@ -258,8 +362,8 @@ __global__ void __launch_bounds__(kThreadsB, 1)
             const int n = c0 + j;
             const float val = __uint_as_float(v[j]);
             if (n >= dout || val == 0.f) continue;
-            if (row < din) atomicAdd(&dW[m.woff[l] + n * din + row], val);
-            else if (row == 64) atomicAdd(&dW[m.boff[l] + n], val);
+            if (frow < din) atomicAdd(&dW[m.woff[l] + n * din + frow], val);
+            else if (frow == 64) atomicAdd(&dW[m.boff[l] + n], val);
           }
         }
       }
@@ -271,32 +375,38 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       sGeo[threadIdx.x] = 0.f;
     }
   };
+  // the next chunk's interval records (half 0) and interval gradients (half 1), one step ahead
+  auto prefetch = [&](const ChunkStep<kNG>& st, int c, RecPrefetch& r) {
+    const int f = (c - w.chunk_start[st.prim]) * w.ipc;
+    if (row < min(w.ipc, w.prim_count[st.prim] - f)) {
+      const int slot = w.prim_start[st.prim] + f + row;
+      if (half == 0) rec_prefetch(w, slot, false, r);
+      else r.g = w.hit_grad[slot];
+    }
+  };
 
   ChunkStep<kNG> cur = chunk_step<kNG>(w, cb, ce, prim);
   RecPrefetch pre;
   pre.valid = 0;
   const int my_first = step_chunk(cur, g);
-  if (warp < kMmaWarpB && cur.n > 0 && my_first >= 0) {
-    const int f0 = (my_first - w.chunk_start[cur.prim]) * w.ipc;
-    if (row < min(w.ipc, w.prim_count[cur.prim] - f0)) rec_prefetch(w, w.prim_start[cur.prim] + f0 + row, true, pre);
-  }
+  if (cur.n > 0 && my_first >= 0) prefetch(cur, my_first, pre);
   while (cur.c0 < ce) {
     prim = cur.prim;
     const ChunkStep<kNG> nxt = chunk_step<kNG>(w, cur.c0 + cur.n, ce, prim);
-    const int my_cc = step_chunk(cur, g);  // this warp's chunk this step and the next
+    const int my_cc = step_chunk(cur, g);  // this group's chunk this step and the next
     const int my_nx = step_chunk(nxt, g);
     if (prim != loaded) {
       tc_fence_before();
       __syncthreads();
       if (loaded >= 0) flush(loaded);
       if (warp < 4) {  // clear the weight-gradient accumulators for the new primitive
-        const uint32_t lanebase = (uint32_t)(q * 32) << 16;
+        const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
         for (int c0 = 0; c0 < nl * 64; c0 += 32) tmem_st32_zero(tm_dw + (uint32_t)c0 + lanebase);
         tmem_wait_st();
       }
       tc_fence_before();
       __syncthreads();
-      if (threadIdx.x == kMmaWarpB * 32 && !*sAbort) {
+      if (threadIdx.x == 0 && !*sAbort) {
         mbar_arrive_expect_tx(bar_w, (uint32_t)P.w_bytes);
         const int row0 = prim * P.rows_per_prim;
         for (int l = 0; l < nl; ++l)
@@ -318,332 +428,296 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       loaded = prim;
     }
 
-    if (warp < kMmaWarpB) {
-      // ============================================================ epilogue group g
-      if (my_cc < 0 && nxt.n > 0 && my_nx >= 0) {  // idle this step: still prefetch
-        const int f1 = (my_nx - w.chunk_start[nxt.prim]) * w.ipc;
-        if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
-          rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, true, pre);
+    if (my_cc < 0) {
+      if (nxt.n > 0 && my_nx >= 0) prefetch(nxt, my_nx, pre);  // idle this step: still prefetch
+      cur = nxt;
+      continue;
+    }
+    // ============================================================ epilogue group g
+    uint8_t* grp = gb + L.grp0 + (uint32_t)g * L.grp_stride;
+    IntervalRec* T = reinterpret_cast<IntervalRec*>(grp + L.itab);
+    float4* GI = reinterpret_cast<float4*>(grp + L.giv);
+    float* DD = reinterpret_cast<float*>(grp + L.ddel);
+    float* GF = reinterpret_cast<float*>(grp + L.gf);
+    float* XC = reinterpret_cast<float*>(grp + L.xch);
+    const int first = (my_cc - w.chunk_start[prim]) * w.ipc;
+    const int nint = min(w.ipc, w.prim_count[prim] - first);
+    named_bar_sync(gbar, kGThreads);  // the group is done with the previous chunk's tables
+    if (row < nint) {
+      if (half == 0) {
+        rec_store(pre, T, row);  // prefetched during the previous step
+      } else {
+        GI[row] = pre.g;
+        const size_t slot = (size_t)w.prim_start[prim] + first + row;
+        for (int f = 0; f < F; ++f) GF[row * F + f] = w.hit_gfeat[slot * F + f];
       }
-      if (my_cc >= 0) {
-        const int bar_id = 1 + g;
-        uint8_t* grp = gb + L.grp0 + (uint32_t)g * L.grp_stride;
-        IntervalRec* T = reinterpret_cast<IntervalRec*>(grp + L.itab);
-        float4* GI = reinterpret_cast<float4*>(grp + L.giv);
-        float* DD = reinterpret_cast<float*>(grp + L.ddel);
-        float* GF = reinterpret_cast<float*>(grp + L.gf);
-        const int first = (my_cc - w.chunk_start[prim]) * w.ipc;
-        const int nint = min(w.ipc, w.prim_count[prim] - first);
-        named_bar_sync(bar_id, kEGThreads);
-        if (row < nint) {
-          rec_store(pre, T, row);  // prefetched during the previous step
-          GI[row] = pre.g;
-          const size_t slot = (size_t)w.prim_start[prim] + first + row;
-          for (int f = 0; f < F; ++f) GF[row * F + f] = w.hit_gfeat[slot * F + f];
-        }
-        named_bar_sync(bar_id, kEGThreads);
-        pre.valid = 0;
-        if (nxt.n > 0 && my_nx >= 0) {  // start loading the next chunk's records now
-          const int f1 = (my_nx - w.chunk_start[nxt.prim]) * w.ipc;
-          if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
-            rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, true, pre);
-        }
-        const uint32_t tiles = sbase + L.tiles0 + (uint32_t)g * L.tiles_stride;
+    }
+    named_bar_sync(gbar, kGThreads);
+    if (nxt.n > 0 && my_nx >= 0) prefetch(nxt, my_nx, pre);  // start loading the next chunk now
+    const uint32_t tiles = sbase + L.tiles0 + (uint32_t)g * L.tiles_stride;
 #define tileaddr(I) (tiles + (uint32_t)(I) * kTile)
-        const int iv = row / S, k = row - iv * S;
-        const bool valid = iv < nint;
-        const uint32_t acc = tmem + (uint32_t)(g * 64);  // this group's dgrad / forward accumulator
-        const uint32_t trow = acc + ((uint32_t)(q * 32) << 16);
+    const int iv = row / S, k = row - iv * S;
+    const bool valid = iv < nint;
+    const uint32_t acc = tmem + (uint32_t)(g * 64);  // this group's dgrad / forward accumulator
+    const uint32_t tcol = acc + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 32);
 
-        if (DL >= 0) build_row_fast<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
-        else build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+    if (DL >= 0) build_half<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, half, tileaddr(0));
+    else if (half == 0) build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    named_bar_sync(gbar, kGThreads);
+    if (issuer) {
+      tc_fence_after();
+      if (!*sAbort) issue_fwd_layer(tileaddr(0), sbase + L.w + P.sw_off[0], acc, P.kpad[0], P.npad[0]);
+      mma_commit(bar_done(g));
+    }
+
+    // ---------------- forward recompute
+    // the next completion of the group's MMAs (warp-uniform: tcgen05.ld is a warp instruction)
+    auto wait_mma = [&]() -> bool {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), ph, sAbort, kWaitNsB));
+      ph ^= 1u;
+      tc_fence_after();
+      return ok;
+    };
+    auto wait_wgrad = [&]() -> bool {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_wg(g), ph_g, sAbort, kWaitNsB));
+      ph_g ^= 1u;
+      tc_fence_after();
+      return ok;
+    };
+    for (int l = 0; l < nl; ++l) {
+      const bool ok = wait_mma();
+      const float* bias = sBias + P.bias_off[l];
+      if (l < nl - 1) {
+        uint32_t pk[16];
+        if (ok) {
+          uint32_t v[32];
+          tmem_ld32(tcol, v);
+          tmem_wait_ld();
+          const float4* b4 = reinterpret_cast<const float4*>(bias + 32 * half);
+#pragma unroll
+          for (int e4 = 0; e4 < 8; ++e4) {
+            const float4 bq = b4[e4];
+            pk[2 * e4] = pack_bf16_relu(__uint_as_float(v[4 * e4]) + bq.x, __uint_as_float(v[4 * e4 + 1]) + bq.y);
+            pk[2 * e4 + 1] = pack_bf16_relu(__uint_as_float(v[4 * e4 + 2]) + bq.z, __uint_as_float(v[4 * e4 + 3]) + bq.w);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) pk[e] = 0u;
+        }
+        store_half(tileaddr(l + 1), row, half, pk);
         fence_proxy_async_smem();
         tc_fence_before();
-        named_bar_sync(bar_id, kEGThreads);
-        if (row == 0) {  // this group issues its own MMAs
+        named_bar_sync(gbar, kGThreads);
+        if (issuer) {
           tc_fence_after();
-          if (!*sAbort) issue_fwd_layer(tileaddr(0), sbase + L.w + P.sw_off[0], acc, P.kpad[0], P.npad[0]);
+          if (!*sAbort)
+            issue_fwd_layer(tileaddr(l + 1), sbase + L.w + P.sw_off[l + 1], acc, P.kpad[l + 1], P.npad[l + 1]);
           mma_commit(bar_done(g));
         }
-
-        // ---------------- forward recompute
-        for (int l = 0; l < nl; ++l) {
-          const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), (ph_done >> g) & 1u, sAbort, kWaitNsB));
-          ph_done ^= 1u << g;
-          tc_fence_after();
-          const float* bias = sBias + P.bias_off[l];
-          if (l < nl - 1) {
-            uint32_t pk[32];
-            if (ok) {
-              uint32_t v0[32], v1[32];
-              tmem_ld32(trow, v0);
-              tmem_ld32(trow + 32, v1);
-              tmem_wait_ld();
-              const float4* b4 = reinterpret_cast<const float4*>(bias);
+      } else {
+        // ---------------- heads and reverse of the interval composite -> dL/dZ into E
+        uint32_t pk[16];
 #pragma unroll
-              for (int e4 = 0; e4 < 16; ++e4) {
-                const float4 bq = b4[e4];
-                const int c0 = 4 * e4;
-                const float x0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]) + bq.x;
-                const float x1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]) + bq.y;
-                const float x2 = __uint_as_float(c0 + 2 < 32 ? v0[c0 + 2] : v1[c0 + 2 - 32]) + bq.z;
-                const float x3 = __uint_as_float(c0 + 3 < 32 ? v0[c0 + 3] : v1[c0 + 3 - 32]) + bq.w;
-                pk[2 * e4] = pack_bf16_relu(x0, x1);
-                pk[2 * e4 + 1] = pack_bf16_relu(x2, x3);
-              }
+        for (int e = 0; e < 16; ++e) pk[e] = 0u;
+        if (half == 0) {
+          float z[4 + NF];
+          {
+            uint32_t r16[16];
+            if (ok) {
+              tmem_ld16(acc + ((uint32_t)(q * 32) << 16), r16);
+              tmem_wait_ld();
             } else {
 #pragma unroll
-              for (int e = 0; e < 32; ++e) pk[e] = 0u;
-            }
-            store_row64(tileaddr(l + 1), row, pk);
-            fence_proxy_async_smem();
-            tc_fence_before();
-            named_bar_sync(bar_id, kEGThreads);
-            if (row == 0) {
-              tc_fence_after();
-              if (!*sAbort)
-                issue_fwd_layer(tileaddr(l + 1), sbase + L.w + P.sw_off[l + 1], acc, P.kpad[l + 1], P.npad[l + 1]);
-              mma_commit(bar_done(g));
-            }
-          } else {
-            // ---------------- heads and reverse of the interval composite -> dL/dZ into T_0
-            float z[4 + NF];
-            {
-              uint32_t r16[16];
-              if (ok) {
-                tmem_ld16(trow, r16);
-                tmem_wait_ld();
-              } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) r16[j] = 0u;
-              }
-              uint32_t r32[32];
-#pragma unroll
-              for (int j = 0; j < 32; ++j) r32[j] = 0u;
-              if (NF > 12 && ok) {
-                tmem_ld32(trow + 16, r32);
-                tmem_wait_ld();
-              }
-#pragma unroll
-              for (int j = 0; j < 4 + NF; ++j) {
-                const uint32_t bits = j < 16 ? r16[j] : r32[(j - 16) & 31];
-                z[j] = j < m.nout ? __uint_as_float(bits) + bias[j] : 0.f;
-              }
-            }
-            tc_fence_before();
-            const IntervalRec& I = T[valid ? iv : 0];
-            const float dt = valid ? I.dt : 0.f;
-            const float sig = softplus_fast(z[3]);
-            const float ak = valid ? sig * dt : 0.f;
-            float sc1[1] = {ak};
-            seg_scan<1>(sc1, 1, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
-            const float Aex = sc1[0] - ak;
-            const float tau = __expf(-Aex), ea = __expf(-ak);
-            const float wk = valid ? tau * (1.f - ea) : 0.f;
-            float cq[3];
-            for (int u = 0; u < 3; ++u) cq[u] = sigmoid_fast(z[u]);
-            float sv[3 + NF];
-#pragma unroll
-            for (int u = 0; u < 3; ++u) sv[u] = wk * cq[u];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) sv[3 + f] = f < F ? wk * z[4 + f] : 0.f;
-            seg_scan_rev<3 + NF>(sv, 3 + F, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
-            const float4 gI = valid ? GI[iv] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float gcs[3] = {gI.x, gI.y, gI.z};
-            float dLda = gI.w;
-#pragma unroll
-            for (int u = 0; u < 3; ++u) dLda += gcs[u] * (tau * ea * cq[u] - (sv[u] - wk * cq[u]));
-            float dz[4 + NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-              const float gf = (valid && f < F) ? GF[iv * F + f] : 0.f;
-              const float fk = z[4 + f];
-              dLda += gf * (tau * ea * fk - (sv[3 + f] - wk * fk));
-              dz[4 + f] = wk * gf;
+              for (int j = 0; j < 16; ++j) r16[j] = 0u;
             }
 #pragma unroll
-            for (int u = 0; u < 3; ++u) dz[u] = wk * gcs[u] * cq[u] * (1.f - cq[u]);
-            dz[3] = valid ? dLda * dt * sigmoid_fast(z[3]) : 0.f;
-            float dd[1] = {valid ? sig * dLda : 0.f};
-            seg_scan<1>(dd, 1, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
-            if (valid && k == S - 1) DD[iv] = dd[0];
-            uint32_t pk[32];
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const float x0 = (2 * e < m.nout) ? dz[(2 * e) < 4 + NF ? 2 * e : 0] : 0.f;
-              const float x1 = (2 * e + 1 < m.nout) ? dz[(2 * e + 1) < 4 + NF ? 2 * e + 1 : 0] : 0.f;
-              pk[e] = pack_bf16(x0, x1);
-            }
-            store_row64(tileaddr(0), row, pk);
-            fence_proxy_async_smem();
-            tc_fence_before();
-            named_bar_sync(bar_id, kEGThreads);
-            if (row == 0) {
-              tc_fence_after();
-              if (!*sAbort)
-                issue_bwd_phase(tiles, nl - 1, nl, sbase + L.w + P.sw_off[nl - 1], acc, tm_dw + (uint32_t)((nl - 1) * 64),
-                                sbase + L.ones, P.kpad[nl - 1], P.npad[nl - 1]);
-              mma_commit(bar_done(g));
-            }
+            for (int j = 0; j < 4 + NF; ++j) z[j] = j < m.nout ? __uint_as_float(r16[j]) + bias[j] : 0.f;
           }
+          tc_fence_before();
+          const IntervalRec& I = T[valid ? iv : 0];
+          const float dt = valid ? I.dt : 0.f;
+          const float sig = softplus_fast(z[3]);
+          const float ak = valid ? sig * dt : 0.f;
+          float sc1[1] = {ak};
+          seg_scan<1>(sc1, 1, row, S, sScan + g * 4 * kMaxScanVals, hbar);
+          const float Aex = sc1[0] - ak;
+          const float tau = __expf(-Aex), ea = __expf(-ak);
+          const float wk = valid ? tau * (1.f - ea) : 0.f;
+          float cq[3];
+          for (int u = 0; u < 3; ++u) cq[u] = sigmoid_fast(z[u]);
+          float sv[3 + NF];
+#pragma unroll
+          for (int u = 0; u < 3; ++u) sv[u] = wk * cq[u];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) sv[3 + f] = f < F ? wk * z[4 + f] : 0.f;
+          seg_scan_rev<3 + NF>(sv, 3 + F, row, S, sScan + g * 4 * kMaxScanVals, hbar);
+          const float4 gI = valid ? GI[iv] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float gcs[3] = {gI.x, gI.y, gI.z};
+          float dLda = gI.w;
+#pragma unroll
+          for (int u = 0; u < 3; ++u) dLda += gcs[u] * (tau * ea * cq[u] - (sv[u] - wk * cq[u]));
+          float dz[4 + NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            const float gf = (valid && f < F) ? GF[iv * F + f] : 0.f;
+            const float fk = z[4 + f];
+            dLda += gf * (tau * ea * fk - (sv[3 + f] - wk * fk));
+            dz[4 + f] = wk * gf;
+          }
+#pragma unroll
+          for (int u = 0; u < 3; ++u) dz[u] = wk * gcs[u] * cq[u] * (1.f - cq[u]);
+          dz[3] = valid ? dLda * dt * sigmoid_fast(z[3]) : 0.f;
+          float dd[1] = {valid ? sig * dLda : 0.f};
+          seg_scan<1>(dd, 1, row, S, sScan + g * 4 * kMaxScanVals, hbar);
+          if (valid && k == S - 1) DD[iv] = dd[0];
+#pragma unroll
+          for (int e = 0; e < (4 + NF) / 2; ++e)
+            pk[e] = pack_bf16(2 * e < m.nout ? dz[2 * e] : 0.f, 2 * e + 1 < m.nout ? dz[2 * e + 1] : 0.f);
         }
-        // ---------------- backward phases B_{nl-1} .. B_0
-        for (int l = nl - 1; l >= 0; --l) {
-          const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), (ph_done >> g) & 1u, sAbort, kWaitNsB));
-          ph_done ^= 1u << g;
+        store_half(tileaddr(nl), row, half, pk);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        named_bar_sync(gbar, kGThreads);
+        if (issuer) {  // B_{nl-1}: dgrad, then wgrad, each with its own completion
           tc_fence_after();
-          if (l > 0) {
-            // delta_{l-1} = G * [H_l > 0], written over H_l in T_l
-            uint32_t v0[32], v1[32];
-            if (ok) {
-              tmem_ld32(trow, v0);
-              tmem_ld32(trow + 32, v1);
-              tmem_wait_ld();
-            } else {
-#pragma unroll
-              for (int e = 0; e < 32; ++e) { v0[e] = 0u; v1[e] = 0u; }
-            }
-            tc_fence_before();
-            const uint32_t Tl = tileaddr(l);
-            uint32_t pk[32];
-#pragma unroll
-            for (int ch = 0; ch < 8; ++ch) {
-              uint32_t hq[4];
-              ld_shared_v4(Tl + sw128_off(row, ch), hq[0], hq[1], hq[2], hq[3]);
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const int c0 = ch * 8 + 2 * e;
-                const float g0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]);
-                const float g1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]);
-                // BF16 pair: low half = feature c0, high half = feature c0 + 1 (> 0 iff positive, non-zero)
-                const uint32_t h0 = hq[e] & 0xFFFFu, h1 = hq[e] >> 16;
-                const bool p0 = h0 != 0u && (h0 & 0x8000u) == 0u;
-                const bool p1 = h1 != 0u && (h1 & 0x8000u) == 0u;
-                pk[ch * 4 + e] = pack_bf16(valid && p0 ? g0 : 0.f, valid && p1 ? g1 : 0.f);
-              }
-            }
-            store_row64(Tl, row, pk);
-            if (l == 1) {
-              if (DL >= 0) build_row_fast<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
-              else build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
-            }
-            fence_proxy_async_smem();
-            tc_fence_before();
-            named_bar_sync(bar_id, kEGThreads);
-            if (row == 0) {
-              tc_fence_after();
-              if (!*sAbort)
-                issue_bwd_phase(tiles, l - 1, nl, sbase + L.w + P.sw_off[l - 1], acc, tm_dw + (uint32_t)((l - 1) * 64),
-                                sbase + L.ones, P.kpad[l - 1], P.npad[l - 1]);
-              mma_commit(bar_done(g));
-            }
-          } else {
-            // ---------------- encoding derivative and pose chain
-            float G[64];
-            {
-              uint32_t v0[32], v1[32];
-              if (ok) {
-                tmem_ld32(trow, v0);
-                tmem_ld32(trow + 32, v1);
-                tmem_wait_ld();
-              } else {
-#pragma unroll
-                for (int e = 0; e < 32; ++e) { v0[e] = 0u; v1[e] = 0u; }
-              }
-#pragma unroll
-              for (int e = 0; e < 32; ++e) { G[e] = __uint_as_float(v0[e]); G[32 + e] = __uint_as_float(v1[e]); }
-            }
-            tc_fence_before();
-            float red[14];
-#pragma unroll
-            for (int e = 0; e < 14; ++e) red[e] = 0.f;
-            if (valid) {
-              const IntervalRec& I = T[iv];
-              const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
-              const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
-              float xl[3], gx[3] = {0.f, 0.f, 0.f};
-              for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
-              if (XL == 0) {
-                for (int u = 0; u < 3; ++u) gx[u] = G[u];
-              } else {
-#pragma unroll
-                for (int u = 0; u < 3; ++u) {
-                  float s_, c_;
-                  __sincosf(3.14159265358979f * xl[u], &s_, &c_);
-                  float wq = 3.14159265358979f;
-#pragma unroll
-                  for (int l2 = 0; l2 < XL; ++l2) {
-                    const int f = 2 * (u * XL + l2);
-                    gx[u] += wq * (G[f] * c_ - G[f + 1] * s_);
-                    const float s2 = 2.f * s_ * c_;
-                    c_ = fmaf(-2.f * s_, s_, 1.f);
-                    s_ = s2;
-                    wq *= 2.f;
-                  }
-                }
-              }
-              float y[3];
-              for (int u = 0; u < 3; ++u)
-                y[u] = Gp.R[u * 3] * Gp.s[0] * xl[0] + Gp.R[u * 3 + 1] * Gp.s[1] * xl[1] + Gp.R[u * 3 + 2] * Gp.s[2] * xl[2];
-              const float uu = ((float)k + 0.5f) / (float)S;
-              const float gt = gx[0] * I.dp[0] + gx[1] * I.dp[1] + gx[2] * I.dp[2];
-              for (int u = 0; u < 3; ++u) {
-                red[u] = gx[u];
-                for (int e = 0; e < 3; ++e) red[3 + u * 3 + e] = gx[u] * y[e];
-              }
-              red[12] = gt * (1.f - uu);
-              red[13] = gt * uu;
-            }
-            seg_scan<14>(red, 14, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
-            if (valid && k == S - 1) {
-              const IntervalRec& I = T[iv];
-              const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
-              const float dDelta = DD[iv];
-              float gt0 = red[12] - dDelta / (float)S, gt1 = red[13] + dDelta / (float)S;
-              const bool clamped = I.r0 != -I.r1;
-              const float gtm = gt1 + (clamped ? 0.f : gt0);
-              const float gh = gt1 - (clamped ? 0.f : gt0);
-              const float aa = I.dp[0] * I.dp[0] + I.dp[1] * I.dp[1] + I.dp[2] * I.dp[2];
-              const float hh = I.r1;
-              float go[3], cd[3], ymid[3];
-              for (int u = 0; u < 3; ++u) {
-                go[u] = -gtm * I.dp[u] / aa - (hh > 0.f ? gh * I.p[u] / (aa * hh) : 0.f);
-                cd[u] = -(gtm * I.p[u] / aa + gh * hh * I.dp[u] / aa);
-              }
-              for (int u = 0; u < 3; ++u)
-                ymid[u] = Gp.R[u * 3] * Gp.s[0] * I.p[0] + Gp.R[u * 3 + 1] * Gp.s[1] * I.p[1] + Gp.R[u * 3 + 2] * Gp.s[2] * I.p[2];
-              for (int u = 0; u < 3; ++u)
-                for (int e = 0; e < 3; ++e)
-                  atomicAdd(&sGeo[u * 3 + e], red[3 + u * 3 + e] + go[u] * ymid[e] + cd[u] * I.d[e]);
-              for (int e = 0; e < 3; ++e) {
-                float acc2 = 0.f;
-                for (int u = 0; u < 3; ++u) acc2 += Gp.Mhi[u * 3 + e] * (red[u] + go[u]);
-                atomicAdd(&sGeo[9 + e], -acc2);
-              }
-            }
-          }
+          if (!*sAbort)
+            issue_dgrad(tileaddr(nl), sbase + L.w + P.sw_off[nl - 1], acc, P.kpad[nl - 1], P.npad[nl - 1]);
+          mma_commit(bar_done(g));
+          if (!*sAbort)
+            issue_wgrad(tileaddr(nl - 1), tileaddr(nl), tm_dw + (uint32_t)((nl - 1) * 64), sbase + L.ones, P.npad[nl - 1]);
+          mma_commit(bar_wg(g));
         }
       }
     }
+    // ---------------- backward phases B_{nl-1} .. B_0 (delta_l lives in T_{l+1}, dL/dZ in E)
+    for (int l = nl - 1; l >= 0; --l) {
+      bool ok = wait_mma();  // dgrad of B_l
+      uint32_t v[32];
+      if (ok) {
+        tmem_ld32(tcol, v);
+        tmem_wait_ld();
+      } else {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = 0u;
+      }
+      tc_fence_before();
+      if (l > 0) {
+        // delta_{l-1} = G * [H_l > 0], written over H_l in T_l once the wgrad of B_l has read it
+        const uint32_t Tl = tileaddr(l);
+        uint32_t pk[16];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          uint32_t hq[4];
+          ld_shared_v4(Tl + sw128_off(row, 4 * half + ch), hq[0], hq[1], hq[2], hq[3]);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int c0 = ch * 8 + 2 * e;
+            // BF16 pair: low half = feature c0, high half = feature c0 + 1 (> 0 iff positive, non-zero)
+            const uint32_t h0 = hq[e] & 0xFFFFu, h1 = hq[e] >> 16;
+            const bool p0 = h0 != 0u && (h0 & 0x8000u) == 0u;
+            const bool p1 = h1 != 0u && (h1 & 0x8000u) == 0u;
+            pk[ch * 4 + e] = pack_bf16(valid && p0 ? __uint_as_float(v[c0]) : 0.f,
+                                       valid && p1 ? __uint_as_float(v[c0 + 1]) : 0.f);
+          }
+        }
+        ok = wait_wgrad() && ok;  // wgrad of B_l: T_l is free
+        store_half(Tl, row, half, pk);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        named_bar_sync(gbar, kGThreads);
+        if (issuer) {
+          tc_fence_after();
+          if (!*sAbort) issue_dgrad(Tl, sbase + L.w + P.sw_off[l - 1], acc, P.kpad[l - 1], P.npad[l - 1]);
+          mma_commit(bar_done(g));
+          if (!*sAbort) issue_wgrad(tileaddr(l - 1), Tl, tm_dw + (uint32_t)((l - 1) * 64), sbase + L.ones, P.npad[l - 1]);
+          mma_commit(bar_wg(g));
+        }
+      } else {
+        // ---------------- encoding derivative and pose chain
+        // With x_k = p + t_k dp and t_k = tm + c_k (r1 - r0), c_k = (k + 1/2) / S - 1/2, every
+        // per-interval sum the chain needs follows from A = sum_k gx_k and B = sum_k c_k gx_k.
+        float gx[3] = {0.f, 0.f, 0.f};
+        const IntervalRec& I = T[valid ? iv : 0];
+        const float ck = ((float)k + 0.5f) * invS - 0.5f;
+        if (valid) {
+          const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+          float xl[3];
+          for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
+          if (half == 0) enc_grad_half<XL, 0>(xl, v, gx);
+          else enc_grad_half<XL, 1>(xl, v, gx);
+        }
+        if (half == 1) XC[row] = gx[2];  // columns 32 .. 63 only reach the z component
+        named_bar_sync(gbar, kGThreads);
+        if (half == 0) {
+          gx[2] += XC[row];
+          float red[6] = {gx[0], gx[1], gx[2], ck * gx[0], ck * gx[1], ck * gx[2]};
+          seg_scan<6>(red, 6, row, S, sScan + g * 4 * kMaxScanVals, hbar);
+          if (valid && k == S - 1) {
+            const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
+            const float span = I.r1 - I.r0, tm = I.r0 + 0.5f * span;
+            const float dA = red[0] * I.dp[0] + red[1] * I.dp[1] + red[2] * I.dp[2];
+            const float dB = red[3] * I.dp[0] + red[4] * I.dp[1] + red[5] * I.dp[2];
+            const float dDelta = DD[iv];
+            // end-point gradients: sum_k gt_k (1 - u_k), sum_k gt_k u_k, plus the width term
+            const float gt0 = 0.5f * dA - dB - dDelta * invS, gt1 = 0.5f * dA + dB + dDelta * invS;
+            const bool clamped = I.r0 != -I.r1;
+            const float gtm = gt1 + (clamped ? 0.f : gt0);
+            const float gh = gt1 - (clamped ? 0.f : gt0);
+            const float aa = I.dp[0] * I.dp[0] + I.dp[1] * I.dp[1] + I.dp[2] * I.dp[2];
+            const float inv_a = 1.f / aa;
+            const float hh = I.r1;
+            const float gh_ah = hh > 0.f ? gh * inv_a / hh : 0.f;
+            float go[3], cd[3], rs[9];
+            for (int u = 0; u < 3; ++u) {
+              go[u] = -gtm * I.dp[u] * inv_a - gh_ah * I.p[u];
+              cd[u] = -(gtm * I.p[u] + gh * hh * I.dp[u]) * inv_a;
+            }
+            for (int e = 0; e < 3; ++e)
+              for (int j = 0; j < 3; ++j) rs[e * 3 + j] = Gp.R[e * 3 + j] * Gp.s[j];  // y = R diag(s) x
+            for (int u = 0; u < 3; ++u) {
+              const float ta = tm * red[u] + span * red[3 + u];  // sum_k t_k gx_k[u]
+              float X[3];  // sum_k gx_k[u] x_k
+              for (int j = 0; j < 3; ++j) X[j] = red[u] * I.p[j] + ta * I.dp[j];
+              for (int e = 0; e < 3; ++e) {
+                const float gy = rs[e * 3] * X[0] + rs[e * 3 + 1] * X[1] + rs[e * 3 + 2] * X[2];
+                const float ym = rs[e * 3] * I.p[0] + rs[e * 3 + 1] * I.p[1] + rs[e * 3 + 2] * I.p[2];
+                atomicAdd(&sGeo[u * 3 + e], gy + go[u] * ym + cd[u] * I.d[e]);
+              }
+            }
+            for (int e = 0; e < 3; ++e) {
+              float acc2 = 0.f;
+              for (int u = 0; u < 3; ++u) acc2 += Gp.Mhi[u * 3 + e] * (red[u] + go[u]);
+              atomicAdd(&sGeo[9 + e], -acc2);
+            }
+          }
+        }
+        (void)wait_wgrad();  // wgrad of B_0: T_0 and T_1 are free for the next chunk
+      }
+    }
+#undef tileaddr
     cur = nxt;
   }
-  // final flush and teardown
-  if (warp == kMmaWarpB && lane == 0) {
-    mma_commit(bar_end);
-    mbar_wait(bar_end, 0, sAbort, kWaitNsB);
+  // teardown: none of this group's MMAs may still write TMEM (after an abort a group may have
+  // stopped waiting for them); then the final flush, and TMEM is freed
+  if (issuer) {
+    mma_commit(bar_end(g));
+    mbar_wait_limit(bar_end(g), 0, kWaitNsB);
   }
   tc_fence_before();
   __syncthreads();
   if (loaded >= 0) flush(loaded);
   tc_fence_before();
   __syncthreads();
-  if (warp == kMmaWarpB) {
+  if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, kTmemColsB);
   }
   if (threadIdx.x == 0 && *sAbort) set_status(w.scr_hdr, MLPS_ERR_TIMEOUT);
 #undef bar_done
-#undef tileaddr
+#undef bar_wg
+#undef bar_end
 }
 
 }  // namespace tc

@@ -385,7 +385,7 @@ mlps_status mlps_check_config(const mlps_config* cfg) {
     TcPlan P;
     long long stride;
     if (!tc_plan(make_model(cfg), &P, &stride)) return MLPS_ERR_UNSUPPORTED;
-    if (tc_smem_bytes(P) > 227 * 1024) return MLPS_ERR_UNSUPPORTED;
+    if (tc_smem_bytes(P, cfg->feat_dim) > 227 * 1024) return MLPS_ERR_UNSUPPORTED;
     return MLPS_OK;
   }
   if (cfg->precision != MLPS_FP32) return MLPS_ERR_UNSUPPORTED;

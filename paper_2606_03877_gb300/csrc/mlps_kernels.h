@@ -67,7 +67,7 @@ cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaS
 
 // k_mlp_tc.cu (BF16 tensor-core path)
 bool tc_plan(const Model& m, TcPlan* P, long long* stride);
-size_t tc_smem_bytes(const TcPlan& P);
+size_t tc_smem_bytes(const TcPlan& P, int F);
 void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
                       void* out, cudaStream_t st);
 cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,

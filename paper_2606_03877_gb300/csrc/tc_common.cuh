@@ -132,12 +132,12 @@ MLPS_DEV void issue_fwd_layer(uint32_t A, uint32_t W, uint32_t d, int kpad, int 
 template <int NG>
 struct ChunkStep {
   int c0, prim, n;
-  int c[3];  // chunk per group (-1: none); accessed with compile-time indices only
+  int c[4];  // chunk per group (-1: none); accessed with compile-time indices only
 };
 
 template <int NG>
 MLPS_DEV ChunkStep<NG> chunk_step(const Work& w, int c, int ce, int prim) {
-  static_assert(NG >= 1 && NG <= 3, "at most three epilogue groups");
+  static_assert(NG >= 1 && NG <= 4, "at most four epilogue groups");
   ChunkStep<NG> s;
   s.c0 = c;
   if (c < ce)
@@ -147,14 +147,15 @@ MLPS_DEV ChunkStep<NG> chunk_step(const Work& w, int c, int ce, int prim) {
   s.c[0] = c < lim ? c : -1;
   s.c[1] = (NG > 1 && c + 1 < lim) ? c + 1 : -1;
   s.c[2] = (NG > 2 && c + 2 < lim) ? c + 2 : -1;
-  s.n = (s.c[0] >= 0) + (s.c[1] >= 0) + (s.c[2] >= 0);
+  s.c[3] = (NG > 3 && c + 3 < lim) ? c + 3 : -1;
+  s.n = (s.c[0] >= 0) + (s.c[1] >= 0) + (s.c[2] >= 0) + (s.c[3] >= 0);
   return s;
 }
 
 // Chunk of group g in a step (register selects; no dynamic indexing).
 template <int NG>
 MLPS_DEV int step_chunk(const ChunkStep<NG>& s, int g) {
-  return g == 0 ? s.c[0] : (g == 1 ? s.c[1] : s.c[2]);
+  return g == 0 ? s.c[0] : (g == 1 ? s.c[1] : (g == 2 ? s.c[2] : s.c[3]));
 }
 
 // Interval record (and, for the backward pass, its gradient) of one chunk row, loaded one

@@ -81,6 +81,17 @@ MLPS_DEV bool mbar_wait(uint32_t addr, uint32_t parity, volatile int* abort_flag
   }
 }
 
+// Wait for phase `parity` with a wall-time limit only (teardown: must not be cut short by the
+// abort flag, because TMEM can only be freed once no MMA writes it any more).
+MLPS_DEV bool mbar_wait_limit(uint32_t addr, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(addr, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(addr, parity)) return true;
+    if ((it & 63u) == 0u && globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
 // ---------------------------------------------------------------- fences / barriers
 MLPS_DEV void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
