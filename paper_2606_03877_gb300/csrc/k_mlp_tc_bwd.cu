@@ -255,20 +255,27 @@ MLPS_DEV void build_row(const Model& m, const IntervalRec* T, int nint, int row,
 // B = the forward W_l tile read as an MN-major operand (inputs contiguous, outputs = K rows).
 MLPS_DEV void issue_dgrad(uint32_t Dl, uint32_t wtile, uint32_t acc, int kpad, int npad) {
   const uint32_t id = idesc_bf16(kM, kpad) | (1u << 16);
-  for (int kk = 0; kk < npad / 16; ++kk)
-    mma_bf16(acc, sw128_desc(Dl + (uint32_t)(kk & 3) * 32), sw128_desc_mn(wtile + (uint32_t)kk * 2048, 16), id,
-             kk > 0 ? 1u : 0u);
+  const uint64_t da = sw128_desc(Dl), db = sw128_desc_mn(wtile, 16);
+  const int nk = npad / 16;  // npad <= 64
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    if (kk >= nk) break;
+    mma_bf16(acc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 128), id, kk > 0 ? 1u : 0u);
+  }
 }
 
 // wgrad of phase B_l: dW_l^T[in (+ones)][out] += H_l^T delta_l over the 128 rows (K = rows).
 // A = [H_l | ones] as MN-major atoms (the ones atom's offset is given per K step, so a single
 // 16-row ones block serves every step); B = delta_l MN-major, N = npad (outputs of layer l).
-// Always accumulates: the accumulator is cleared when the block starts a primitive.
+// Always accumulates: the accumulator is cleared when the block starts a primitive. Stepping K
+// moves A's start address up and its atom offset (LBO, descriptor bits 16..29) down by 2 KB.
 MLPS_DEV void issue_wgrad(uint32_t Hl, uint32_t Dl, uint32_t dw_l, uint32_t ones, int npad) {
   const uint32_t id = idesc_bf16(kM, npad) | (1u << 15) | (1u << 16);
+  const uint64_t da = sw128_desc_mn(Hl, ones - Hl), db = sw128_desc_mn(Dl, 16);
+#pragma unroll
   for (int kk = 0; kk < kM / 16; ++kk) {
-    const uint32_t ha = Hl + (uint32_t)kk * 2048;
-    mma_bf16(dw_l, sw128_desc_mn(ha, ones - ha), sw128_desc_mn(Dl + (uint32_t)kk * 2048, 16), id, 1u);
+    const uint64_t step = (uint64_t)(kk * 128);
+    mma_bf16(dw_l, da + step - (step << 16), db + step, id, 1u);
   }
 }
 

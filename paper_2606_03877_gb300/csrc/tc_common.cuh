@@ -117,13 +117,19 @@ MLPS_DEV void seg_scan_rev(float (&v)[NV], int nv, int row, int S, float* scratc
 }
 
 // MMAs of one forward layer of a 128-row chunk: D[128 x npad] = A[128 x kpad] W^T, A and W in
-// the K-major swizzled layout, K in 64-column slabs. Issued by one thread.
+// the K-major swizzled layout, K in 64-column slabs (kpad <= 128). Issued by one thread. The
+// descriptors are built once; stepping K only moves their start-address field (address >> 4).
 MLPS_DEV void issue_fwd_layer(uint32_t A, uint32_t W, uint32_t d, int kpad, int npad) {
   const uint32_t idesc = idesc_bf16(kM, npad);
-  for (int kk = 0; kk < kpad / 16; ++kk) {
-    const uint32_t aa = A + (uint32_t)(kk >> 2) * (kM * 128) + (uint32_t)(kk & 3) * 32;
-    const uint32_t bb = W + (uint32_t)(kk >> 2) * (uint32_t)(npad * 128) + (uint32_t)(kk & 3) * 32;
-    mma_bf16(d, sw128_desc(aa), sw128_desc(bb), idesc, kk > 0 ? 1u : 0u);
+  const uint64_t da = sw128_desc(A), db = sw128_desc(W);
+  const uint32_t wslab = (uint32_t)npad * 8;  // (npad * 128 bytes) >> 4: one 64-column slab of W
+  const int nk = kpad / 16;
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    if (kk >= nk) break;
+    const uint32_t oa = (uint32_t)(kk >> 2) * (kM * 8) + (uint32_t)(kk & 3) * 2;
+    const uint32_t ob = (uint32_t)(kk >> 2) * wslab + (uint32_t)(kk & 3) * 2;
+    mma_bf16(d, da + oa, db + ob, idesc, kk > 0 ? 1u : 0u);
   }
 }
 
