@@ -24,6 +24,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -50,16 +51,16 @@ struct TcSmem {
 
 MLPS_HD uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG) {
+MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG, bool e4m3) {
   TcSmem L;
   uint32_t off = 0;
   L.w = off;
-  off = align_up(off + P.w_bytes, 1024);
+  off = align_up(off + (e4m3 ? P.w8_bytes : P.w_bytes), 1024);
   L.a0 = off;
   L.a_stride = align_up(P.a_bytes, 1024);
   off += L.a_stride * kNEG;
-  L.bias = off;
-  off = align_up(off + 4 * P.bias_floats, 16);
+  L.bias = off;  // biases, then (E4M3) the per-output weight scales
+  off = align_up(off + 4 * P.bias_floats * (e4m3 ? 2 : 1), 16);
   L.itab0 = off;
   L.itab_stride = align_up((uint32_t)sizeof(IntervalRec) * kM, 16);
   off += L.itab_stride * kNEG;
@@ -73,7 +74,11 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG) {
   return L;
 }
 
-template <int WIDTH, int XL, int DL, int NF, int kNEG>
+// F8: E4M3 operands (kind::f8f6f4). Activation rows are stored divided by a per-row power-of-two
+// scale (the encoded input by 1/256, each hidden row by the smallest 2^e that keeps its largest
+// value <= 448); weights by a per-output scale from the packing. The epilogue multiplies the
+// FP32 accumulator back by (row scale x weight scale) before the bias.
+template <int WIDTH, int XL, int DL, int NF, int kNEG, bool F8>
 __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     k_mlp_fwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
   constexpr int kThreadsTC = kEGThreads * kNEG;
@@ -83,7 +88,8 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (sbase - raw);
-  const TcSmem L = tc_smem(P, kNEG);
+  const TcSmem L = tc_smem(P, kNEG, F8);
+  constexpr float kInMul = 256.f;  // E4M3 encoded input: values in [-1, 1] stored times 256
   const Model& m = a.m;
   float* sBias = reinterpret_cast<float*>(gbase + L.bias);
   float* sScan = reinterpret_cast<float*>(gbase + L.scan);
@@ -141,16 +147,27 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     if (prim != loaded) {
       __syncthreads();  // every role is done with the previous primitive's tiles
       if (threadIdx.x == 0 && !*sAbort) {
-        mbar_arrive_expect_tx(bar_w, (uint32_t)P.w_bytes);
+        mbar_arrive_expect_tx(bar_w, (uint32_t)(F8 ? P.w8_bytes : P.w_bytes));
         const int row0 = prim * P.rows_per_prim;
-        for (int l = 0; l < nl; ++l)
-          for (int sl = 0; sl < P.kpad[l] / 64; ++sl)
+        for (int l = 0; l < nl; ++l) {
+          if (F8) {
             for (int j = 0; j < P.npad[l] / 16; ++j)
-              tma_load_2d(sbase + L.w + P.sw_off[l] + sl * P.npad[l] * 128 + j * 2048, &tmap, 0,
-                          row0 + P.gw_row[l] + sl * P.npad[l] + j * 16, bar_w);
+              tma_load_2d(sbase + L.w + P.s8_off[l] + j * 2048, &tmap, 0, row0 + P.g8_row[l] + j * 16, bar_w);
+          } else {
+            for (int sl = 0; sl < P.kpad[l] / 64; ++sl)
+              for (int j = 0; j < P.npad[l] / 16; ++j)
+                tma_load_2d(sbase + L.w + P.sw_off[l] + sl * P.npad[l] * 128 + j * 2048, &tmap, 0,
+                            row0 + P.gw_row[l] + sl * P.npad[l] + j * 16, bar_w);
+          }
+        }
       }
-      const float* gb = reinterpret_cast<const float*>(a.weights + (size_t)prim * a.pk.stride + P.gbias_byte);
+      const unsigned char* blob = a.weights + (size_t)prim * a.pk.stride;
+      const float* gb = reinterpret_cast<const float*>(blob + P.gbias_byte);
       for (int i = threadIdx.x; i < P.bias_floats; i += kThreadsTC) sBias[i] = gb[i];
+      if (F8) {
+        const float* gs = reinterpret_cast<const float*>(blob + P.gscale_byte);
+        for (int i = threadIdx.x; i < P.bias_floats; i += kThreadsTC) sBias[P.bias_floats + i] = gs[i];
+      }
       mbar_wait(bar_w, ph_w, sAbort, kWaitNs);
       ph_w ^= 1;
       __syncthreads();
@@ -182,7 +199,39 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
         const uint32_t A = sbase + L.a0 + (uint32_t)g * L.a_stride;
         const int iv = row / S, k = row - iv * S;
         const bool valid = iv < nint;
-        if (XL >= 0) {
+        float srow = 1.f / kInMul;  // E4M3: scale of this row of the current A tile
+        if (F8 && XL >= 0) {
+          uint32_t pk[16];
+          if (valid) {
+            const IntervalRec& I = T[iv];
+            const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+            float xl[3], dd[3];
+            for (int u = 0; u < 3; ++u) { xl[u] = fmaf(tr, I.dp[u], I.p[u]); dd[u] = I.d[u]; }
+            encode_e4m3_64<(XL > 0 ? XL : 0), (DL > 0 ? DL : 0)>(xl, dd, kInMul, pk);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) pk[e] = 0u;
+          }
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch)
+            st_shared_v4(A + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+        } else if (F8) {
+          RowWriter8 rw{A, row, 0, 0.f, kInMul};
+          if (valid) {
+            const IntervalRec& I = T[iv];
+            const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+            float xl[3];
+            for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
+            if (m.xyzL == 0) {
+              for (int u = 0; u < 3; ++u) rw.put(xl[u]);
+            } else {
+              for (int u = 0; u < 3; ++u) put_gamma8(rw, xl[u], m.xyzL);
+            }
+            if (m.dirL > 0)
+              for (int u = 0; u < 3; ++u) put_gamma8(rw, I.d[u], m.dirL);
+          }
+          rw.pad_to(P.kpad[0]);
+        } else if (XL >= 0) {
           // compile-time encoding (the configurations' shapes)
           uint32_t pk[32];
           if (valid) {
@@ -221,7 +270,10 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
         const uint32_t dacc = tmem + (uint32_t)(g * 128);
         if (row == 0) {  // this group issues its own MMAs
           tc_fence_after();
-          if (!*sAbort) issue_fwd_layer(A, sbase + L.w + P.sw_off[0], dacc, P.kpad[0], P.npad[0]);
+          if (!*sAbort) {
+            if (F8) issue_fwd_layer_e4m3(A, sbase + L.w + P.s8_off[0], dacc, P.kpad[0], P.npad[0]);
+            else issue_fwd_layer(A, sbase + L.w + P.sw_off[0], dacc, P.kpad[0], P.npad[0]);
+          }
           mma_commit(bar_done(g));
         }
         const uint32_t trow = tmem + (uint32_t)(g * 128) + ((uint32_t)(q * 32) << 16);
@@ -232,7 +284,47 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
           tc_fence_after();
           const float* bias = sBias + P.bias_off[l];
           if (l < nl - 1) {
-            if (ok) {
+            if (ok && F8) {
+              // pass 1: H = ReLU(acc * srow * c_n + b_n) and its row maximum; pass 2: store H / 2^e
+              const float* wsc = sBias + P.bias_floats + P.bias_off[l];
+              float amax = 0.f;
+#pragma unroll
+              for (int half = 0; half < WIDTH / 64; ++half) {
+                uint32_t v0[32], v1[32];
+                tmem_ld32(trow + half * 64, v0);
+                tmem_ld32(trow + half * 64 + 32, v1);
+                tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < 64; ++c) {
+                  const int n = half * 64 + c;
+                  amax = fmaxf(amax, fmaf(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * srow, wsc[n], bias[n]));
+                }
+              }
+              const float sn = e4m3_row_scale(amax), inv = __frcp_rn(sn);
+#pragma unroll
+              for (int half = 0; half < WIDTH / 64; ++half) {
+                uint32_t v0[32], v1[32];
+                tmem_ld32(trow + half * 64, v0);
+                tmem_ld32(trow + half * 64 + 32, v1);
+                tmem_wait_ld();
+                uint32_t pk[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                  float h[4];
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) {
+                    const int n = half * 64 + 4 * e + j;
+                    const int c = 4 * e + j;
+                    h[j] = fmaxf(fmaf(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * srow, wsc[n], bias[n]), 0.f) * inv;
+                  }
+                  pk[e] = pack_e4m3(h[0], h[1]) | (pack_e4m3(h[2], h[3]) << 16);
+                }
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch)
+                  st_shared_v4(A + sw128_off(row, 4 * half + ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+              }
+              srow = sn;
+            } else if (ok) {
 #pragma unroll
               for (int half = 0; half < WIDTH / 64; ++half) {
                 uint32_t v0[32], v1[32];
@@ -262,7 +354,10 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
             named_bar_sync(bar_id, kEGThreads);
             if (row == 0) {
               tc_fence_after();
-              if (!*sAbort) issue_fwd_layer(A, sbase + L.w + P.sw_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1]);
+              if (!*sAbort) {
+                if (F8) issue_fwd_layer_e4m3(A, sbase + L.w + P.s8_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1]);
+                else issue_fwd_layer(A, sbase + L.w + P.sw_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1]);
+              }
               mma_commit(bar_done(g));
             }
           } else {
@@ -285,7 +380,8 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
                 uint32_t bits;
                 if (P.npad[l] >= 32) bits = j < 32 ? r32[j] : r16[(j - 32) & 15];
                 else bits = j < 16 ? r16[j] : 0u;
-                z[j] = (j < m.nout) ? __uint_as_float(bits) + bias[j] : 0.f;
+                if (F8) z[j] = (j < m.nout) ? fmaf(__uint_as_float(bits) * srow, sBias[P.bias_floats + P.bias_off[l] + j], bias[j]) : 0.f;
+                else z[j] = (j < m.nout) ? __uint_as_float(bits) + bias[j] : 0.f;
               }
             } else {
 #pragma unroll
@@ -361,6 +457,23 @@ __global__ void k_pack_bf16(Model m, TcPlan P, long long stride, int K, const fl
   for (int l = 0; l < m.nl; ++l)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.npad[l]; i += gridDim.x * blockDim.x)
       b[P.bias_off[l] + i] = i < m.dout[l] ? s[m.boff[l] + i] : 0.f;
+  if (P.w8_bytes == 0) return;
+  // E4M3 copy: output n of layer l is stored as W[n][k] / c_n with c_n = max_k |W[n][k]| / 448
+  float* scl = reinterpret_cast<float*>(d + P.gscale_byte);
+  for (int l = 0; l < m.nl; ++l) {
+    const int din = m.din[l];
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < P.npad[l]; n += gridDim.x * blockDim.x) {
+      const bool live = n < m.dout[l];
+      float amax = 0.f;
+      if (live)
+        for (int k = 0; k < din; ++k) amax = fmaxf(amax, fabsf(s[m.woff[l] + n * din + k]));
+      const float c = amax > 0.f ? amax / 448.f : 1.f;
+      scl[P.bias_off[l] + n] = c;
+      unsigned char* r = d + (size_t)(P.g8_row[l] + n) * 128;
+      for (int k = 0; k < 128; ++k)
+        r[k] = (live && k < din) ? __nv_cvt_float_to_fp8(s[m.woff[l] + n * din + k] / c, __NV_SATFINITE, __NV_E4M3) : 0;
+    }
+  }
 }
 
 }  // namespace tc
@@ -370,7 +483,7 @@ __global__ void k_pack_bf16(Model m, TcPlan P, long long stride, int K, const fl
 
 static int round_up_i(int x, int a) { return (x + a - 1) / a * a; }
 
-bool tc_plan(const Model& m, TcPlan* P, long long* stride) {
+bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3) {
   std::memset(P, 0, sizeof(*P));
   if (m.width != 64 && m.width != 128) return false;
   if (m.nin > 128 || m.nout > 48 || m.S > 128) return false;
@@ -388,12 +501,25 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride) {
     kmax = kmax > P->kpad[l] ? kmax : P->kpad[l];
   }
   P->w_bytes = sw;
-  // the backward pass reads the same W tiles as MN-major operands: no transposed copies
-  for (int l = 0; l < m.nl; ++l) { P->gwt_row[l] = 0; P->swt_off[l] = 0; }
-  P->wt_bytes = 0;
+  // (the backward pass reads the same W tiles as MN-major operands: no transposed copies)
   P->bias_floats = bias;
   P->gbias_byte = rows * 128;
-  const long long bytes = (long long)rows * 128 + 4LL * bias;
+  long long bytes = (long long)rows * 128 + 4LL * bias;
+  if (e4m3) {
+    // E4M3 copy after the biases: one 128-byte row per output, then the FP32 weight scales.
+    // The BF16 tiles stay in the blob: the backward pass of the FP8 precision uses them.
+    if (kmax > 128) return false;
+    int r8 = (int)((bytes + 127) / 128), s8 = 0;
+    for (int l = 0; l < m.nl; ++l) {
+      P->g8_row[l] = r8;
+      r8 += P->npad[l];
+      P->s8_off[l] = s8;
+      s8 += P->npad[l] * 128;
+    }
+    P->w8_bytes = s8;
+    P->gscale_byte = r8 * 128;
+    bytes = (long long)r8 * 128 + 4LL * bias;
+  }
   *stride = (bytes + 1023) / 1024 * 1024;
   P->rows_per_prim = (int)(*stride / 128);
   P->kmax = kmax;
@@ -408,7 +534,7 @@ static int fwd_groups(int width, int F) { return width == 64 ? (F > 0 ? 3 : 4) :
 
 size_t tc_smem_bytes(const TcPlan& P, int F) {
   const int width = P.npad[0];  // hidden width = N of layer 0
-  return tc::tc_smem(P, fwd_groups(width, F)).total + 1024;
+  return tc::tc_smem(P, fwd_groups(width, F), P.w8_bytes > 0).total + 1024;
 }
 
 void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
@@ -448,15 +574,25 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
   const int xl = a.m.xyzL, dl = a.m.dirL;
   const bool fast64 = xl == 6 && dl == 4 && P.kpad[0] == 64;
   const bool raw = xl == 0 && dl == 0 && P.kpad[0] == 64;
-  decltype(&tc::k_mlp_fwd_tc<64, 6, 4, 0, 4>) kern;
+  decltype(&tc::k_mlp_fwd_tc<64, 6, 4, 0, 4, false>) kern;
   const bool feat = a.m.F > 0;
   const int neg = fwd_groups(a.m.width, a.m.F);
-  if (a.m.width == 64) {
-    if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, 0, 4> : raw ? tc::k_mlp_fwd_tc<64, 0, 0, 0, 4> : tc::k_mlp_fwd_tc<64, -1, -1, 0, 4>;
-    else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, kMaxFeat, 3> : tc::k_mlp_fwd_tc<64, -1, -1, kMaxFeat, 3>;
+  if (P.w8_bytes > 0) {  // E4M3
+    if (a.m.width == 64) {
+      if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, 0, 4, true> : tc::k_mlp_fwd_tc<64, -1, -1, 0, 4, true>;
+      else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, kMaxFeat, 3, true> : tc::k_mlp_fwd_tc<64, -1, -1, kMaxFeat, 3, true>;
+    } else if (a.m.width == 128) {
+      if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 0, 2, true> : tc::k_mlp_fwd_tc<128, -1, -1, 0, 2, true>;
+      else kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, kMaxFeat, 2, true> : tc::k_mlp_fwd_tc<128, -1, -1, kMaxFeat, 2, true>;
+    } else {
+      return cudaErrorNotSupported;
+    }
+  } else if (a.m.width == 64) {
+    if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, 0, 4, false> : raw ? tc::k_mlp_fwd_tc<64, 0, 0, 0, 4, false> : tc::k_mlp_fwd_tc<64, -1, -1, 0, 4, false>;
+    else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, kMaxFeat, 3, false> : tc::k_mlp_fwd_tc<64, -1, -1, kMaxFeat, 3, false>;
   } else if (a.m.width == 128) {
-    if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 0, 2> : tc::k_mlp_fwd_tc<128, -1, -1, 0, 2>;
-    else kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, kMaxFeat, 2> : tc::k_mlp_fwd_tc<128, -1, -1, kMaxFeat, 2>;
+    if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 0, 2, false> : tc::k_mlp_fwd_tc<128, -1, -1, 0, 2, false>;
+    else kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, kMaxFeat, 2, false> : tc::k_mlp_fwd_tc<128, -1, -1, kMaxFeat, 2, false>;
   } else {
     return cudaErrorNotSupported;
   }

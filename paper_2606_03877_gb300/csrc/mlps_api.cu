@@ -128,10 +128,10 @@ Packed make_packed(const mlps_config* c, const Model& m) {
   Packed pk;
   std::memset(&pk, 0, sizeof(pk));
   pk.precision = c->precision;
-  if (c->precision == MLPS_BF16) {
+  if (c->precision == MLPS_BF16 || c->precision == MLPS_FP8_E4M3) {
     TcPlan P;
     long long stride = 0;
-    if (tc_plan(m, &P, &stride)) pk.stride = stride;
+    if (tc_plan(m, &P, &stride, c->precision == MLPS_FP8_E4M3)) pk.stride = stride;
     return pk;
   }
   int off = 0;
@@ -381,10 +381,10 @@ int64_t mlps_weight_stride(const mlps_config* cfg) {
 mlps_status mlps_check_config(const mlps_config* cfg) {
   mlps_status s = check_cfg(cfg);
   if (s != MLPS_OK) return s;
-  if (cfg->precision == MLPS_BF16) {
+  if (cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3) {
     TcPlan P;
     long long stride;
-    if (!tc_plan(make_model(cfg), &P, &stride)) return MLPS_ERR_UNSUPPORTED;
+    if (!tc_plan(make_model(cfg), &P, &stride, cfg->precision == MLPS_FP8_E4M3)) return MLPS_ERR_UNSUPPORTED;
     if (tc_smem_bytes(P, cfg->feat_dim) > 227 * 1024) return MLPS_ERR_UNSUPPORTED;
     return MLPS_OK;
   }
@@ -402,10 +402,10 @@ mlps_status mlps_pack_weights(const mlps_config* cfg, int32_t K, const float* we
   Packed pk = make_packed(cfg, m);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   StageTimer tm(ST_PACK, st);
-  if (cfg->precision == MLPS_BF16) {
+  if (cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3) {
     TcPlan P;
     long long stride;
-    tc_plan(m, &P, &stride);
+    tc_plan(m, &P, &stride, cfg->precision == MLPS_FP8_E4M3);
     launch_pack_bf16(m, P, stride, K, weights_fp32, packed, st);
   } else {
     launch_pack_fp32(m, pk, K, weights_fp32, packed, st);
@@ -491,10 +491,10 @@ mlps_status mlps_render_forward(const mlps_config* cfg, const mlps_scene* scene,
   if (K > 0) {
     StageTimer tm(ST_MLP_FWD, st);
     cudaError_t e;
-    if (cfg->precision == MLPS_BF16) {
+    if (cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3) {
       TcPlan P;
       long long stride;
-      tc_plan(m, &P, &stride);
+      tc_plan(m, &P, &stride, cfg->precision == MLPS_FP8_E4M3);
       e = launch_mlp_fwd_tc(w, a, P, n_sm, st);
     } else {
       e = launch_mlp_fwd_simt(w, a, n_sm, st);
@@ -556,15 +556,17 @@ mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene
   }
   TcPlan P;
   long long tc_stride = 0;
-  if (cfg->precision == MLPS_BF16) {
-    if (!tc_plan(m, &P, &tc_stride) || !tc_bwd_supported(m, P)) return MLPS_ERR_UNSUPPORTED;
+  // FP8 precision: the backward recomputes the MLP in BF16 from the BF16 tiles of the same blob
+  const bool tc = cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3;
+  if (tc) {
+    if (!tc_plan(m, &P, &tc_stride, cfg->precision == MLPS_FP8_E4M3) || !tc_bwd_supported(m, P))
+      return MLPS_ERR_UNSUPPORTED;
   } else if (cfg->precision != MLPS_FP32) {
     return MLPS_ERR_UNSUPPORTED;
   }
   if (K > 0) {
     StageTimer tm(ST_MLP_BWD, st);
-    cudaError_t e = cfg->precision == MLPS_BF16 ? launch_mlp_bwd_tc(w, a, P, n_sm, st)
-                                                 : launch_mlp_bwd_simt(w, a, n_sm, st);
+    cudaError_t e = tc ? launch_mlp_bwd_tc(w, a, P, n_sm, st) : launch_mlp_bwd_simt(w, a, n_sm, st);
     if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return MLPS_ERR_CUDA;
     count_launch(1);

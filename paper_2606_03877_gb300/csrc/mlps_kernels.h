@@ -13,10 +13,6 @@ struct Packed {
   long long stride;    // bytes per primitive (multiple of 256)
   // FP32: per layer W^T [din][dout] then b [dout], each block starting on 16 bytes
   int woff[kMaxLayers], boff[kMaxLayers];  // float offsets (FP32 layout)
-  // tensor-core layouts (BF16 / FP8): byte offsets of the operand tiles and FP32 biases
-  int tc_w[kMaxLayers];      // forward B operand tile: W [N=dout_pad][K=din_pad]
-  int tc_wt[kMaxLayers];     // backward B operand tile: W^T [N=din_pad][K=dout_pad]
-  int tc_b[kMaxLayers];      // FP32 bias [dout_pad]
   int tc_scale;              // FP8: float scales [2 * nl] (forward tile, transposed tile)
   int din_pad[kMaxLayers], dout_pad[kMaxLayers];
 };
@@ -37,9 +33,12 @@ struct TcPlan {
   int sw_off[kMaxLayers];                  // shared-memory byte offset of layer l's W tile
   int gw_row[kMaxLayers];                  // first 128-byte row of layer l's tile in a blob
   int w_bytes;                             // all forward W tiles
-  int gwt_row[kMaxLayers];                 // unused (0): the backward reads the W tiles MN-major
-  int swt_off[kMaxLayers];                 // unused (0)
-  int wt_bytes;                            // 0
+  // E4M3 copy (FP8 precision only; w8_bytes = 0 otherwise): layer l's tile W [npad][kpad] as
+  // one 128-byte row per output (kpad <= 128), and FP32 per-output weight scales
+  int g8_row[kMaxLayers];                  // first 128-byte row of layer l's E4M3 tile in a blob
+  int s8_off[kMaxLayers];                  // shared-memory byte offset of layer l's E4M3 tile
+  int w8_bytes;                            // all E4M3 tiles
+  int gscale_byte;                         // byte offset of the FP32 weight scales (bias_off indexing)
   int bias_off[kMaxLayers];                // float offset of layer l's bias
   int bias_floats;
   int gbias_byte;                          // byte offset of the FP32 biases in a blob
@@ -66,7 +65,7 @@ cudaError_t launch_mlp_fwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaS
 cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st);
 
 // k_mlp_tc.cu (BF16 tensor-core path)
-bool tc_plan(const Model& m, TcPlan* P, long long* stride);
+bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3 = false);
 size_t tc_smem_bytes(const TcPlan& P, int F);
 void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
                       void* out, cudaStream_t st);

@@ -133,6 +133,59 @@ MLPS_DEV void issue_fwd_layer(uint32_t A, uint32_t W, uint32_t d, int kpad, int 
   }
 }
 
+// FP8 (E4M3) forward layer: same operand tiles (128-byte K-major swizzled rows, here holding up
+// to 128 one-byte elements), K = 32 per instruction; kpad <= 128.
+MLPS_DEV void issue_fwd_layer_e4m3(uint32_t A, uint32_t W, uint32_t d, int kpad, int npad) {
+  const uint32_t idesc = idesc_e4m3(kM, npad);
+  const uint64_t da = sw128_desc(A), db = sw128_desc(W);
+  const int nk = kpad / 32;
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    if (kk >= nk) break;
+    mma_e4m3(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, kk > 0 ? 1u : 0u);
+  }
+}
+
+// Power-of-two scale s with amax / s <= 448 (the largest finite E4M3 value), s = 1 when amax is
+// zero or not finite: dividing by s is exact, so the scale adds no rounding of its own.
+MLPS_DEV float e4m3_row_scale(float amax) {
+  const float q = amax * (1.0f / 448.0f);
+  if (!(q > 1e-30f) || !(q < 1e30f)) return 1.0f;
+  return __uint_as_float((__float_as_uint(q) + 0x007FFFFFu) & 0x7F800000u);  // round up to 2^e
+}
+
+// Writes one sample row of an E4M3 A tile (one byte per column, 128-byte swizzled rows), two
+// values at a time.
+struct RowWriter8 {
+  uint32_t base;
+  int row, col;
+  float pend, mul;
+  MLPS_DEV void put(float v) {
+    if (col & 1) {
+      const int c0 = col - 1;
+      st_shared_u16(base + sw128_off(row, c0 >> 4) + (uint32_t)(c0 & 15), pack_e4m3(pend * mul, v * mul));
+    } else {
+      pend = v;
+    }
+    ++col;
+  }
+  MLPS_DEV void pad_to(int n) {
+    while (col < n) put(0.f);
+  }
+};
+
+MLPS_DEV void put_gamma8(RowWriter8& rw, float p, int L) {
+  float s, c;
+  __sincosf(3.14159265358979f * p, &s, &c);
+  for (int l = 0; l < L; ++l) {
+    rw.put(s);
+    rw.put(c);
+    const float s2 = 2.f * s * c;
+    c = fmaf(-2.f * s, s, 1.f);
+    s = s2;
+  }
+}
+
 // One step of a block's chunk schedule: up to NG consecutive chunks of the same primitive,
 // one per epilogue group. Every role evaluates the same schedule.
 template <int NG>
@@ -224,6 +277,51 @@ MLPS_DEV void encode_pairs64(const float (&xl)[3], const float (&d)[3], uint32_t
 #pragma unroll
       for (int l = 0; l < (DL > 0 ? DL : 1); ++l) {
         pk[NX / 2 + u * DL + l] = pack_bf16(s, c);
+        const float s2 = 2.f * s * c;
+        c = fmaf(-2.f * s, s, 1.f);
+        s = s2;
+      }
+    }
+  }
+}
+
+// Encoded input row as E4M3 bytes (values times `mul`), compile-time frequency counts, same
+// order as encode_pairs64: word e holds columns 4e .. 4e + 3 (low byte first).
+template <int XL, int DL>
+MLPS_DEV void encode_e4m3_64(const float (&xl)[3], const float (&d)[3], float mul, uint32_t (&pk)[16]) {
+  constexpr int NX = XL > 0 ? 6 * XL : 3;
+  constexpr int NIN = NX + (DL > 0 ? 6 * DL : 0);
+  static_assert(NIN <= 64, "encoded input wider than one 64-column tile");
+  static_assert(XL > 0 || DL == 0, "raw position with a direction encoding is not a fast path");
+#pragma unroll
+  for (int e = 0; e < 16; ++e) pk[e] = 0u;
+  if (XL == 0) {
+    pk[0] = pack_e4m3(xl[0] * mul, xl[1] * mul) | (pack_e4m3(xl[2] * mul, 0.f) << 16);
+    return;
+  }
+  // pair p (one frequency's sin, cos) is the 16-bit half p & 1 of word p >> 1
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    float s, c;
+    __sincosf(3.14159265358979f * xl[u], &s, &c);
+#pragma unroll
+    for (int l = 0; l < (XL > 0 ? XL : 1); ++l) {
+      const int p = u * XL + l;
+      pk[p >> 1] |= pack_e4m3(s * mul, c * mul) << (16 * (p & 1));
+      const float s2 = 2.f * s * c;
+      c = fmaf(-2.f * s, s, 1.f);
+      s = s2;
+    }
+  }
+  if (DL > 0) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      float s, c;
+      __sincosf(3.14159265358979f * d[u], &s, &c);
+#pragma unroll
+      for (int l = 0; l < (DL > 0 ? DL : 1); ++l) {
+        const int p = NX / 2 + u * DL + l;
+        pk[p >> 1] |= pack_e4m3(s * mul, c * mul) << (16 * (p & 1));
         const float s2 = 2.f * s * c;
         c = fmaf(-2.f * s, s, 1.f);
         s = s2;

@@ -10,6 +10,7 @@
 // and threads writing operands apply the same XOR.
 #pragma once
 
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -188,6 +189,23 @@ MLPS_DEV void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t
       : "memory");
 }
 
+// Instruction descriptor of kind::f8f6f4 with E4M3 A and B (format code 0 in [7, 10) and
+// [10, 13)), FP32 accumulation (1 in [4, 6)), both operands K-major; N >> 3 in [17, 23),
+// M >> 4 in [24, 29). One instruction covers K = 32 (32 bytes of each operand row).
+MLPS_HD uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+MLPS_DEV void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Arrive on the mbarrier once all previously issued tcgen05.mma of this thread have completed.
 MLPS_DEV void mma_commit(uint32_t mbar) {
   asm volatile(
@@ -226,6 +244,15 @@ MLPS_DEV void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, ui
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
                "r"(d)
                : "memory");
+}
+
+// Two floats to a pair of E4M3 bytes (round to nearest, saturating): `lo` in the low byte.
+MLPS_DEV uint32_t pack_e4m3(float lo, float hi) {
+  return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(lo, hi), __NV_SATFINITE, __NV_E4M3);
+}
+
+MLPS_DEV void st_shared_u16(uint32_t addr, uint32_t a) {
+  asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr), "h"((unsigned short)a) : "memory");
 }
 
 MLPS_DEV void st_shared_u32(uint32_t addr, uint32_t a) {
