@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MLPS_ABI_VERSION 1
+#define MLPS_ABI_VERSION 2
 #define MLPS_MAX_VIEWS 64
 
 typedef int32_t mlps_status;
@@ -190,6 +190,48 @@ mlps_status mlps_render_forward_static(const mlps_config* cfg, const mlps_scene*
                                        const mlps_camera* cams, int32_t n_views, float* rgb,
                                        float* trans, float* feat, int32_t* device_status,
                                        void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Batched rendering: many scenes (primitive sets) and resolutions in one call                */
+/*
+ * The renderer of Sec. 3.2-3.3 applied to a batch of independent items, each one view of one
+ * scene. The scenes' primitives are passed as ONE set of scene arrays (mlps_scene with the
+ * scenes' primitives concatenated, K = their total, weights packed with mlps_pack_weights);
+ * item i renders primitives [prim_offset, prim_offset + prim_count) of those arrays through its
+ * own camera at the camera's own resolution. Items may share primitives (several views of one
+ * scene). Every stage runs as one launch over all items: the MLP stage is one persistent launch
+ * over the chunks of every primitive of every scene. No call synchronises, allocates or reads
+ * device memory on the host, so a batch (forward and backward) can be captured in a CUDA graph
+ * and replayed; the item table is read on the host at call time and baked into the launches.
+ *
+ * Image layout: items are concatenated in order. Item i's pixels start at
+ * P_i = sum_{j < i} width_j * height_j; rgb [P, 3], trans [P], feat [P, F] and their gradients,
+ * each item row-major inside its block (pixel P_i + y * width_i + x). Gradients dL/dweights,
+ * dL/dcenters, ... cover all K primitives (zero for primitives no item renders). At most
+ * MLPS_MAX_VIEWS items. */
+typedef struct {
+  int32_t prim_offset;  /* first primitive of the item's scene in the batch's scene arrays */
+  int32_t prim_count;   /* its primitives; prim_offset + prim_count <= K */
+  mlps_camera cam;      /* the item's view (host struct), any resolution */
+} mlps_batch_item;
+
+/* Workspace of a batch (host items[n_items]); same meaning as mlps_workspace_size. */
+mlps_status mlps_batch_workspace_size(const mlps_config* cfg, int32_t K, const mlps_batch_item* items,
+                                      int32_t n_items, size_t* saved_bytes, size_t* scratch_bytes);
+
+/* Forward render of a batch; arguments as mlps_render_forward with the batch image layout. */
+mlps_status mlps_render_batch_forward(const mlps_config* cfg, const mlps_scene* scene,
+                                      const mlps_batch_item* items, int32_t n_items, float* rgb,
+                                      float* trans, float* feat, void* saved, size_t saved_bytes,
+                                      void* scratch, size_t scratch_bytes, void* stream);
+
+/* Backward of a batch (same items and `saved` as the forward call); as mlps_render_backward. */
+mlps_status mlps_render_batch_backward(const mlps_config* cfg, const mlps_scene* scene,
+                                       const mlps_batch_item* items, int32_t n_items, const float* d_rgb,
+                                       const float* d_trans, const float* d_feat, const void* saved,
+                                       size_t saved_bytes, float* d_weights, float* d_centers,
+                                       float* d_scales, float* d_quats, void* scratch,
+                                       size_t scratch_bytes, void* stream);
 
 /* Synchronise `stream`, return the device status word of a `saved` or `scratch` region
  * written by the calls above (MLPS_OK if none), and clear it. */

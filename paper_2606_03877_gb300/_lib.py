@@ -48,6 +48,10 @@ class MlpsCamera(ctypes.Structure):
                 ("world_to_cam", ctypes.c_float * 12), ("near_t", ctypes.c_float)]
 
 
+class MlpsBatchItem(ctypes.Structure):
+    _fields_ = [("prim_offset", ctypes.c_int32), ("prim_count", ctypes.c_int32), ("cam", MlpsCamera)]
+
+
 class MlpsScene(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("centers", ctypes.c_void_p), ("scales", ctypes.c_void_p),
                 ("quats", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
@@ -83,6 +87,14 @@ _SIGS = [
     ("mlps_render_backward", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _P(MlpsCamera),
                                               ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                               _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    ("mlps_batch_workspace_size", ctypes.c_int32, [_P(MlpsConfig), ctypes.c_int32, _P(MlpsBatchItem),
+                                                   ctypes.c_int32, _P(ctypes.c_size_t), _P(ctypes.c_size_t)]),
+    ("mlps_render_batch_forward", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _P(MlpsBatchItem),
+                                                   ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                                   _vp, ctypes.c_size_t, _vp]),
+    ("mlps_render_batch_backward", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _P(MlpsBatchItem),
+                                                    ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                                    _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     ("mlps_render_forward_static", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _P(MlpsCamera),
                                                     ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
     ("mlps_read_status", ctypes.c_int32, [_vp, _vp]),
@@ -210,6 +222,40 @@ def mlps_render_backward(cfg, scene: MlpsScene, cams, n_views, d_rgb, d_trans, d
                          d_weights, d_centers, d_scales, d_quats, scratch, scratch_bytes, stream: int = 0):
     _check("mlps_render_backward", load().mlps_render_backward(
         ctypes.byref(cfg), ctypes.byref(scene), cams, int(n_views), _ptr(d_rgb), _ptr(d_trans), _ptr(d_feat),
+        _ptr(saved), int(saved_bytes), _ptr(d_weights), _ptr(d_centers), _ptr(d_scales), _ptr(d_quats),
+        _ptr(scratch), int(scratch_bytes), stream or None))
+
+
+def batch_items(items: Sequence[tuple]):
+    """Host array of mlps_batch_item from (prim_offset, prim_count, camera dict) tuples."""
+    arr = (MlpsBatchItem * len(items))()
+    for i, (off, cnt, cam) in enumerate(items):
+        arr[i].prim_offset = int(off)
+        arr[i].prim_count = int(cnt)
+        arr[i].cam = cameras([cam])[0]
+    return arr
+
+
+def mlps_batch_workspace_size(cfg: MlpsConfig, K: int, items, n_items: int):
+    s = ctypes.c_size_t()
+    t = ctypes.c_size_t()
+    _check("mlps_batch_workspace_size", load().mlps_batch_workspace_size(
+        ctypes.byref(cfg), int(K), items, int(n_items), ctypes.byref(s), ctypes.byref(t)))
+    return int(s.value), int(t.value)
+
+
+def mlps_render_batch_forward(cfg, scene: MlpsScene, items, n_items, rgb, trans, feat, saved, saved_bytes,
+                              scratch, scratch_bytes, stream: int = 0):
+    _check("mlps_render_batch_forward", load().mlps_render_batch_forward(
+        ctypes.byref(cfg), ctypes.byref(scene), items, int(n_items), _ptr(rgb), _ptr(trans), _ptr(feat),
+        _ptr(saved), int(saved_bytes), _ptr(scratch), int(scratch_bytes), stream or None))
+
+
+def mlps_render_batch_backward(cfg, scene: MlpsScene, items, n_items, d_rgb, d_trans, d_feat, saved,
+                               saved_bytes, d_weights, d_centers, d_scales, d_quats, scratch, scratch_bytes,
+                               stream: int = 0):
+    _check("mlps_render_batch_backward", load().mlps_render_batch_backward(
+        ctypes.byref(cfg), ctypes.byref(scene), items, int(n_items), _ptr(d_rgb), _ptr(d_trans), _ptr(d_feat),
         _ptr(saved), int(saved_bytes), _ptr(d_weights), _ptr(d_centers), _ptr(d_scales), _ptr(d_quats),
         _ptr(scratch), int(scratch_bytes), stream or None))
 

@@ -30,7 +30,7 @@ __global__ void k_store_views(Work w, ViewArray va) {
 
 MLPS_DEV bool finitef(float x) { return isfinite(x); }
 
-__global__ void k_prim_setup(Work w, const float* __restrict__ centers,
+__global__ void k_prim_geo(Work w, const float* __restrict__ centers,
                              const float* __restrict__ scales, const float* __restrict__ quats) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= w.K) return;
@@ -75,9 +75,31 @@ __global__ void k_prim_setup(Work w, const float* __restrict__ centers,
   g.valid = ok ? 1 : 0;
   w.geo[p] = g;
   if (!ok) set_status(w.saved_hdr, MLPS_ERR_NONFINITE);
+}
 
-  for (int v = 0; v < w.V; ++v) {
-    const ViewData& V = w.views[v];
+// Per (view, primitive) record: o' = M (o - mu) in double-float and the conservative tile range.
+__global__ void k_prim_view(Work w) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= w.n_pairs) return;
+  int v = 0;
+  {
+    int lo = 0, hi = w.V - 1;  // the view whose record range holds j (views in pair order)
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (w.views[mid].pv_base <= j) lo = mid;
+      else hi = mid - 1;
+    }
+    v = lo;
+  }
+  const ViewData& V = w.views[v];
+  const int p = V.prim_base + (j - V.pv_base);
+  const PrimGeo& g = w.geo[p];
+  const bool ok = g.valid != 0;
+  float s[3], mu[3];
+  dfl M[9];
+  for (int i = 0; i < 3; ++i) { s[i] = g.s[i]; mu[i] = g.mu[i]; }
+  for (int i = 0; i < 9; ++i) M[i] = {g.Mhi[i], g.Mlo[i]};
+  {
     PrimView pv;
     // o' = M (o - mu) in double-float
     dfl rel[3];
@@ -107,7 +129,7 @@ __global__ void k_prim_setup(Work w, const float* __restrict__ centers,
         for (int k = 0; k < 3; ++k) acc += s[k] * s[k] * cols[k][i] * cols[k][j];
         Sg[i][j] = acc;
       }
-    int tx0 = 0, ty0 = 0, tx1 = w.ntx - 1, ty1 = w.nty - 1;
+    int tx0 = 0, ty0 = 0, tx1 = V.ntx - 1, ty1 = V.nty - 1;
     float sz = sqrtf(fmaxf(Sg[2][2], 0.f));
     if (!ok || c[2] + sz <= 0.0f) {
       tx0 = 1; tx1 = 0;  // entirely behind the camera: culled
@@ -129,7 +151,7 @@ __global__ void k_prim_setup(Work w, const float* __restrict__ centers,
         lim[ax][1] = u1 + pad;
       }
       if (good) {
-        int n[2] = {w.ntx, w.nty};
+        int n[2] = {V.ntx, V.nty};
         int lo[2], hi[2];
         for (int ax = 0; ax < 2; ++ax) {
           float a = floorf(lim[ax][0] / (float)w.tile);
@@ -142,9 +164,10 @@ __global__ void k_prim_setup(Work w, const float* __restrict__ centers,
       }
     }
     pv.tx0 = tx0; pv.tx1 = tx1; pv.ty0 = ty0; pv.ty1 = ty1;
-    w.pview[(size_t)v * w.K + p] = pv;
+    w.pview[j] = pv;
   }
 }
+
 
 // ------------------------------------------------------------------------------------------
 // Tile candidate lists: one warp per (view, tile), primitives in index order.
@@ -155,17 +178,20 @@ constexpr int kRectBatch = 512;
 __global__ void __launch_bounds__(kTileBlock) k_tile_lists(Work w) {
   __shared__ int4 srect[kRectBatch];
   const int v = blockIdx.y;
+  const ViewData& V = w.views[v];
+  const int ntx = V.ntx, n_tiles = V.ntx * V.nty, K = V.prim_n;
+  if ((int)blockIdx.x * (kTileBlock / 32) >= n_tiles) return;  // block-uniform
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * (kTileBlock / 32) + warp;
-  const bool active = t < w.n_tiles;
-  const int tx = active ? t % w.ntx : 0, ty = active ? t / w.ntx : 0;
+  const bool active = t < n_tiles;
+  const int tx = active ? t % ntx : 0, ty = active ? t / ntx : 0;
   int count = 0;
-  int* list = w.tile_list + ((size_t)v * w.n_tiles + (active ? t : 0)) * w.K;
-  for (int base = 0; base < w.K; base += kRectBatch) {
-    int nb = min(kRectBatch, w.K - base);
+  int* list = w.tile_list + V.cand_base + (size_t)(active ? t : 0) * K;
+  for (int base = 0; base < K; base += kRectBatch) {
+    int nb = min(kRectBatch, K - base);
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += kTileBlock) {
-      const PrimView& pv = w.pview[(size_t)v * w.K + base + i];
+      const PrimView& pv = w.pview[V.pv_base + base + i];
       srect[i] = make_int4(pv.tx0, pv.ty0, pv.tx1, pv.ty1);
     }
     __syncthreads();
@@ -178,11 +204,11 @@ __global__ void __launch_bounds__(kTileBlock) k_tile_lists(Work w) {
         in = tx >= r.x && tx <= r.z && ty >= r.y && ty <= r.w;
       }
       unsigned m = __ballot_sync(0xffffffffu, in);
-      if (in) list[count + __popc(m & ((1u << lane) - 1u))] = base + i;
+      if (in) list[count + __popc(m & ((1u << lane) - 1u))] = V.prim_base + base + i;
       count += __popc(m);
     }
   }
-  if (active && lane == 0) w.tile_count[(size_t)v * w.n_tiles + t] = count;
+  if (active && lane == 0) w.tile_count[V.tile_base + t] = count;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -250,13 +276,16 @@ __global__ void __launch_bounds__(TILE* TILE) k_intersect(Work w) {
   __shared__ int sbase;
   __shared__ ViewData sv;
   const int v = blockIdx.y, t = blockIdx.x;
-  const int tx = t % w.ntx, ty = t / w.ntx;
+  const ViewData& Vg = w.views[v];
+  if (t >= Vg.ntx * Vg.nty) return;  // block-uniform: this view has fewer tiles
+  const int tx = t % Vg.ntx, ty = t / Vg.ntx;
   const int x = tx * TILE + (int)(threadIdx.x % TILE);
   const int y = ty * TILE + (int)(threadIdx.x / TILE);
-  const bool inside = x < w.W && y < w.H;
-  if (threadIdx.x == 0) sv = w.views[v];
-  const int ncand = w.tile_count[(size_t)v * w.n_tiles + t];
-  const int* cand = w.tile_list + ((size_t)v * w.n_tiles + t) * w.K;
+  const bool inside = x < Vg.width && y < Vg.height;
+  if (threadIdx.x == 0) sv = Vg;
+  const int ncand = w.tile_count[Vg.tile_base + t];
+  const int* cand = w.tile_list + Vg.cand_base + (size_t)t * Vg.prim_n;
+  const int pv_off = Vg.pv_base - Vg.prim_base;  // pview index of global primitive p: pv_off + p
   for (int i = threadIdx.x; i < kHist; i += NT) shist[i] = 0;
   __syncthreads();
   dfl d[3];
@@ -273,7 +302,7 @@ __global__ void __launch_bounds__(TILE* TILE) k_intersect(Work w) {
     for (int i = threadIdx.x; i < nb; i += NT) {
       int p = cand[base + i];
       const PrimGeo& g = w.geo[p];
-      const PrimView& pv = w.pview[(size_t)v * w.K + p];
+      const PrimView& pv = w.pview[pv_off + p];
       CandGeo cg;
       for (int k = 0; k < 9; ++k) { cg.Mhi[k] = g.Mhi[k]; cg.Mlo[k] = g.Mlo[k]; }
       for (int k = 0; k < 3; ++k) { cg.op_hi[k] = pv.op_hi[k]; cg.op_lo[k] = pv.op_lo[k]; }
@@ -325,7 +354,7 @@ __global__ void __launch_bounds__(TILE* TILE) k_intersect(Work w) {
   if (base < 0)
     for (int h = swarp[0] + threadIdx.x; h < swarp[1]; h += NT) w.hit_prim[h] = -1;
   const int excl = incl - n + swarp[warp];
-  const int ray = sv.ray_base + y * w.W + x;
+  const int ray = sv.ray_base + y * sv.width + x;
   if (inside) {
     if (base < 0) {
       w.ray_start[ray] = 0;
@@ -338,7 +367,7 @@ __global__ void __launch_bounds__(TILE* TILE) k_intersect(Work w) {
         const int c = lc[j];
         const int p = cand[c];
         const PrimGeo& g = w.geo[p];
-        const PrimView& pv = w.pview[(size_t)v * w.K + p];
+        const PrimView& pv = w.pview[pv_off + p];
         HitGeom hg = intersect_df(g.Mhi, g.Mlo, pv.op_hi, pv.op_lo, d, near_t);
         const int h = start + j;
         w.hit_prim[h] = p;
@@ -439,9 +468,9 @@ __global__ void k_scatter(Work w) {
     w.slot_of[h] = slot;
     // the interval record: everything the MLP stage needs, contiguous per chunk
     const int ray = w.hit_ray[h];
-    const int hw = w.H * w.W;
-    const int v = ray / hw, pix = ray - v * hw;
-    const int y = pix / w.W, x = pix - y * w.W;
+    const int v = view_of_ray(w, ray);
+    const int pix = ray - w.views[v].ray_base, vw = w.views[v].width;
+    const int y = pix / vw, x = pix - y * vw;
     float d[3];
     ray_dir_f(w.views[v], x, y, d);
     const PrimGeo& g = w.geo[p];
@@ -500,19 +529,22 @@ void launch_store_views(const Work& w, const ViewArray& va, cudaStream_t st) {
   k_store_views<<<1, kMaxViews, 0, st>>>(w, va);
 }
 
-void launch_prim_setup(const Work& w, const float* c, const float* s, const float* q,
-                       cudaStream_t st) {
-  if (w.K == 0) return;
-  k_prim_setup<<<(w.K + 127) / 128, 128, 0, st>>>(w, c, s, q);
+int launch_prim_setup(const Work& w, const float* c, const float* s, const float* q,
+                      cudaStream_t st) {
+  if (w.K == 0) return 0;
+  k_prim_geo<<<(w.K + 127) / 128, 128, 0, st>>>(w, c, s, q);
+  if (w.n_pairs == 0) return 1;
+  k_prim_view<<<(w.n_pairs + 127) / 128, 128, 0, st>>>(w);
+  return 2;
 }
 
 void launch_tile_lists(const Work& w, cudaStream_t st) {
-  dim3 grid((w.n_tiles + kTileBlock / 32 - 1) / (kTileBlock / 32), w.V);
+  dim3 grid((w.max_view_tiles + kTileBlock / 32 - 1) / (kTileBlock / 32), w.V);
   k_tile_lists<<<grid, kTileBlock, 0, st>>>(w);
 }
 
 bool launch_intersect(const Work& w, cudaStream_t st) {
-  dim3 grid(w.n_tiles, w.V);
+  dim3 grid(w.max_view_tiles, w.V);
   if (w.tile == 16) k_intersect<16><<<grid, 256, 0, st>>>(w);
   else if (w.tile == 8) k_intersect<8><<<grid, 64, 0, st>>>(w);
   else return false;

@@ -288,6 +288,35 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
               // pass 1: H = ReLU(acc * srow * c_n + b_n) and its row maximum; pass 2: store H / 2^e
               const float* wsc = sBias + P.bias_floats + P.bias_off[l];
               float amax = 0.f;
+              if (WIDTH == 64) {  // one pass: the row's 64 values stay in registers
+                uint32_t v0[32], v1[32];
+                tmem_ld32(trow, v0);
+                tmem_ld32(trow + 32, v1);
+                tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < 64; ++c) {
+                  const float h = fmaxf(fmaf(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * srow, wsc[c], bias[c]), 0.f);
+                  amax = fmaxf(amax, h);
+                  if (c < 32) v0[c] = __float_as_uint(h);
+                  else v1[c - 32] = __float_as_uint(h);
+                }
+                const float sn = e4m3_row_scale(amax), inv = __frcp_rn(sn);
+                uint32_t pk[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                  float h[4];
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) {
+                    const int c = 4 * e + j;
+                    h[j] = __uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv;
+                  }
+                  pk[e] = pack_e4m3(h[0], h[1]) | (pack_e4m3(h[2], h[3]) << 16);
+                }
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch)
+                  st_shared_v4(A + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+                srow = sn;
+              } else {
 #pragma unroll
               for (int half = 0; half < WIDTH / 64; ++half) {
                 uint32_t v0[32], v1[32];
@@ -324,6 +353,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
                   st_shared_v4(A + sw128_off(row, 4 * half + ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
               }
               srow = sn;
+              }
             } else if (ok) {
 #pragma unroll
               for (int half = 0; half < WIDTH / 64; ++half) {

@@ -158,6 +158,13 @@ struct Carve {
   }
 };
 
+// One view of a call: its camera and the primitives it renders (a single-scene call gives every
+// view the whole scene; a batch gives each item its own range, at its own resolution).
+struct ViewSpec {
+  mlps_camera cam;
+  int prim_base, prim_n;
+};
+
 struct Layout {
   // saved
   size_t hit_prim, hit_ray, hit_tmid, hit_r0, hit_r1, hit_p, hit_out, hit_feat, ray_start,
@@ -166,17 +173,29 @@ struct Layout {
   // scratch
   size_t prim_cursor, tile_count, tile_list, hit_grad, hit_gfeat, dgeo, scratch_total;
   long long hit_cap;
-  int n_tiles, ntx, nty;
-  long long n_rays;
+  long long n_rays, n_pairs, n_tiles_all, n_cand;
+  int max_view_tiles;
+  int H0, W0, ntx0, nty0;  // view 0
 };
 
-bool make_layout(const mlps_config* c, int K, int V, int H, int W, Layout* L) {
+bool make_layout(const mlps_config* c, int K, const ViewSpec* vs, int V, Layout* L) {
   const int F = c->feat_dim;
-  L->ntx = (W + c->tile - 1) / c->tile;
-  L->nty = (H + c->tile - 1) / c->tile;
-  L->n_tiles = L->ntx * L->nty;
-  L->n_rays = (long long)V * H * W;
-  if (L->n_rays > 0x7fffffffLL) return false;
+  L->n_rays = L->n_pairs = L->n_tiles_all = L->n_cand = 0;
+  L->max_view_tiles = 0;
+  for (int v = 0; v < V; ++v) {
+    const long long ntx = (vs[v].cam.width + c->tile - 1) / c->tile;
+    const long long nty = (vs[v].cam.height + c->tile - 1) / c->tile;
+    L->n_rays += (long long)vs[v].cam.width * vs[v].cam.height;
+    L->n_pairs += vs[v].prim_n;
+    L->n_tiles_all += ntx * nty;
+    L->n_cand += ntx * nty * vs[v].prim_n;
+    L->max_view_tiles = std::max(L->max_view_tiles, (int)(ntx * nty));
+  }
+  L->W0 = vs[0].cam.width;
+  L->H0 = vs[0].cam.height;
+  L->ntx0 = (L->W0 + c->tile - 1) / c->tile;
+  L->nty0 = (L->H0 + c->tile - 1) / c->tile;
+  if (L->n_rays > 0x7fffffffLL || L->n_pairs > 0x7fffffffLL) return false;
   double cap = std::ceil((double)L->n_rays * (double)c->hit_capacity_per_ray);
   if (cap < 1) cap = 1;
   if (cap > 0x7fff0000) return false;
@@ -201,12 +220,12 @@ bool make_layout(const mlps_config* c, int K, int V, int H, int W, Layout* L) {
   L->slot_of = s.take<int>(hc);
   L->views = s.take<ViewData>((size_t)V);
   L->geo = s.take<PrimGeo>((size_t)K + 1);
-  L->pview = s.take<PrimView>((size_t)V * K + 1);
+  L->pview = s.take<PrimView>((size_t)L->n_pairs + 1);
   L->saved_total = s.off;
   Carve t;
   L->prim_cursor = t.take<int>((size_t)K + 1);
-  L->tile_count = t.take<int>((size_t)V * L->n_tiles + 1);
-  L->tile_list = t.take<int>((size_t)V * L->n_tiles * (size_t)K + 1);
+  L->tile_count = t.take<int>((size_t)L->n_tiles_all + 1);
+  L->tile_list = t.take<int>((size_t)L->n_cand + 1);
   L->hit_grad = t.take<float4>(hc);
   L->hit_gfeat = t.take<float>(hc * (size_t)(F > 0 ? F : 1));
   L->dgeo = t.take<float>((size_t)K * 12 + 1);
@@ -214,8 +233,7 @@ bool make_layout(const mlps_config* c, int K, int V, int H, int W, Layout* L) {
   return true;
 }
 
-Work make_work(const mlps_config* c, const Layout& L, int K, int V, int H, int W, void* saved,
-               void* scratch) {
+Work make_work(const mlps_config* c, const Layout& L, int K, int V, void* saved, void* scratch) {
   Work w;
   std::memset(&w, 0, sizeof(w));
   char* sv = static_cast<char*>(saved);
@@ -251,12 +269,14 @@ Work make_work(const mlps_config* c, const Layout& L, int K, int V, int H, int W
   }
   w.K = K;
   w.V = V;
-  w.H = H;
-  w.W = W;
+  w.H = L.H0;
+  w.W = L.W0;
+  w.ntx = L.ntx0;
+  w.nty = L.nty0;
+  w.n_tiles = L.ntx0 * L.nty0;
   w.tile = c->tile;
-  w.ntx = L.ntx;
-  w.nty = L.nty;
-  w.n_tiles = L.n_tiles;
+  w.n_pairs = (int)L.n_pairs;
+  w.max_view_tiles = L.max_view_tiles;
   w.n_rays = (int)L.n_rays;
   w.hit_cap = (int)L.hit_cap;
   w.max_hits = c->max_hits_per_ray;
@@ -266,29 +286,52 @@ Work make_work(const mlps_config* c, const Layout& L, int K, int V, int H, int W
   return w;
 }
 
-mlps_status check_cams(const mlps_camera* cams, int V, int* H, int* W) {
-  if (!cams || V < 1 || V > kMaxViews) return MLPS_ERR_INVALID_ARGUMENT;
-  *W = cams[0].width;
-  *H = cams[0].height;
-  if (*W < 1 || *H < 1 || *W > 16384 || *H > 16384) return MLPS_ERR_INVALID_ARGUMENT;
+mlps_status check_cam(const mlps_camera& c) {
+  if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return MLPS_ERR_INVALID_ARGUMENT;
+  const float vals[5] = {c.fx, c.fy, c.cx, c.cy, c.near_t};
+  for (float x : vals)
+    if (!finite_f(x)) return MLPS_ERR_INVALID_ARGUMENT;
+  for (float x : c.world_to_cam)
+    if (!finite_f(x)) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c.fx == 0.f || c.fy == 0.f || c.near_t < 0.f) return MLPS_ERR_INVALID_ARGUMENT;
+  return MLPS_OK;
+}
+
+// Single-scene call: every view renders all K primitives; all views share one resolution (the
+// output arrays are [V, H, W, ...]).
+mlps_status specs_from_cams(const mlps_camera* cams, int V, int K, std::vector<ViewSpec>* out) {
+  if (!cams || V < 1 || V > kMaxViews || K < 0) return MLPS_ERR_INVALID_ARGUMENT;
+  out->resize(V);
   for (int v = 0; v < V; ++v) {
-    const mlps_camera& c = cams[v];
-    if (c.width != *W || c.height != *H) return MLPS_ERR_UNSUPPORTED;
-    const float vals[6] = {c.fx, c.fy, c.cx, c.cy, c.near_t, 0.f};
-    for (float x : vals)
-      if (!finite_f(x)) return MLPS_ERR_INVALID_ARGUMENT;
-    for (float x : c.world_to_cam)
-      if (!finite_f(x)) return MLPS_ERR_INVALID_ARGUMENT;
-    if (c.fx == 0.f || c.fy == 0.f || c.near_t < 0.f) return MLPS_ERR_INVALID_ARGUMENT;
+    mlps_status s = check_cam(cams[v]);
+    if (s != MLPS_OK) return s;
+    if (cams[v].width != cams[0].width || cams[v].height != cams[0].height) return MLPS_ERR_UNSUPPORTED;
+    (*out)[v] = ViewSpec{cams[v], 0, K};
   }
   return MLPS_OK;
 }
 
-ViewArray make_views(const mlps_camera* cams, int V) {
+// Batch: item i renders primitives [prim_offset, prim_offset + prim_count) of the scene arrays.
+mlps_status specs_from_items(const mlps_batch_item* items, int n, int K, std::vector<ViewSpec>* out) {
+  if (!items || n < 1 || n > kMaxViews || K < 0) return MLPS_ERR_INVALID_ARGUMENT;
+  out->resize(n);
+  for (int i = 0; i < n; ++i) {
+    mlps_status s = check_cam(items[i].cam);
+    if (s != MLPS_OK) return s;
+    const long long b = items[i].prim_offset, c = items[i].prim_count;
+    if (b < 0 || c < 0 || b + c > K) return MLPS_ERR_INVALID_ARGUMENT;
+    (*out)[i] = ViewSpec{items[i].cam, (int)b, (int)c};
+  }
+  return MLPS_OK;
+}
+
+ViewArray make_views(const ViewSpec* vs, int V, int tile) {
   ViewArray va;
   std::memset(&va, 0, sizeof(va));
+  int ray_base = 0, pv_base = 0, tile_base = 0;
+  long long cand_base = 0;
   for (int v = 0; v < V; ++v) {
-    const mlps_camera& c = cams[v];
+    const mlps_camera& c = vs[v].cam;
     ViewData& d = va.v[v];
     for (int i = 0; i < 3; ++i) {
       for (int j = 0; j < 3; ++j) d.R[i * 3 + j] = c.world_to_cam[i * 4 + j];
@@ -298,7 +341,18 @@ ViewArray make_views(const mlps_camera* cams, int V) {
     d.near_t = c.near_t;
     d.width = c.width;
     d.height = c.height;
-    d.ray_base = v * c.width * c.height;
+    d.ray_base = ray_base;
+    d.prim_base = vs[v].prim_base;
+    d.prim_n = vs[v].prim_n;
+    d.pv_base = pv_base;
+    d.ntx = (c.width + tile - 1) / tile;
+    d.nty = (c.height + tile - 1) / tile;
+    d.tile_base = tile_base;
+    d.cand_base = cand_base;
+    ray_base += c.width * c.height;
+    pv_base += vs[v].prim_n;
+    tile_base += d.ntx * d.nty;
+    cand_base += (long long)d.ntx * d.nty * vs[v].prim_n;
     for (int i = 0; i < 3; ++i) {
       // origin -R^T t in FP64, split into hi + lo
       double o = -((double)d.R[0 * 3 + i] * d.t[0] + (double)d.R[1 * 3 + i] * d.t[1] +
@@ -321,6 +375,157 @@ int num_sms() {
 bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
 
 mlps_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MLPS_OK : MLPS_ERR_CUDA; }
+
+mlps_status workspace_impl(const mlps_config* cfg, int K, const std::vector<ViewSpec>& vs,
+                           size_t* saved_bytes, size_t* scratch_bytes) {
+  Layout L;
+  if (!make_layout(cfg, K, vs.data(), (int)vs.size(), &L)) return MLPS_ERR_UNSUPPORTED;
+  *saved_bytes = L.saved_total;
+  *scratch_bytes = L.scratch_total;
+  return MLPS_OK;
+}
+
+// Forward over views `vs` (validated cameras and primitive ranges).
+mlps_status forward_impl(const mlps_config* cfg, const mlps_scene* scene, const std::vector<ViewSpec>& vs,
+                         float* rgb, float* trans, float* feat, void* saved, size_t saved_bytes,
+                         void* scratch, size_t scratch_bytes, void* stream) {
+  if (!scene || scene->K < 0 || !rgb || !trans || !saved || !scratch)
+    return MLPS_ERR_INVALID_ARGUMENT;
+  if (cfg->feat_dim > 0 && !feat) return MLPS_ERR_INVALID_ARGUMENT;
+  const int K = scene->K;
+  if (K > 0 && (!scene->centers || !scene->scales || !scene->quats || !scene->weights))
+    return MLPS_ERR_INVALID_ARGUMENT;
+  if (!aligned256(saved) || !aligned256(scratch) || (K > 0 && !aligned256(scene->weights)))
+    return MLPS_ERR_INVALID_ARGUMENT;
+  const int n_views = (int)vs.size();
+  Layout L;
+  if (!make_layout(cfg, K, vs.data(), n_views, &L)) return MLPS_ERR_UNSUPPORTED;
+  if (saved_bytes < L.saved_total || scratch_bytes < L.scratch_total)
+    return MLPS_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Work w = make_work(cfg, L, K, n_views, saved, scratch);
+  Model m = make_model(cfg);
+  MlpArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.m = m;
+  a.pk = make_packed(cfg, m);
+  a.weights = static_cast<const unsigned char*>(scene->weights);
+  a.rows = 128;
+  a.resident = (a.pk.stride + 2 * 128 * 4 * (size_t)std::max(std::max(m.nin, m.width), m.nout) +
+                16 * 1024) <= 200 * 1024;
+  const int n_sm = num_sms();
+  {
+    StageTimer tm(ST_SETUP, st);
+    cudaMemsetAsync(w.saved_hdr, 0, 256, st);
+    cudaMemsetAsync(w.prim_count, 0, sizeof(int) * ((size_t)K + 1), st);
+    launch_store_views(w, make_views(vs.data(), n_views, cfg->tile), st);
+    count_launch(1 + launch_prim_setup(w, scene->centers, scene->scales, scene->quats, st));
+  }
+  {
+    StageTimer tm(ST_TILES, st);
+    launch_tile_lists(w, st);
+    count_launch(1);
+  }
+  {
+    StageTimer tm(ST_INTERSECT, st);
+    if (!launch_intersect(w, st)) return MLPS_ERR_UNSUPPORTED;
+    count_launch(1);
+  }
+  {
+    StageTimer tm(ST_SCAN, st);
+    if (K > 0) { launch_prim_scan(w, st); count_launch(1); }
+  }
+  {
+    StageTimer tm(ST_SCATTER, st);
+    if (K > 0) { launch_scatter(w, n_sm, st); count_launch(1); }
+  }
+  if (K > 0) {
+    StageTimer tm(ST_MLP_FWD, st);
+    cudaError_t e;
+    if (cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3) {
+      TcPlan P;
+      long long stride;
+      tc_plan(m, &P, &stride, cfg->precision == MLPS_FP8_E4M3);
+      e = launch_mlp_fwd_tc(w, a, P, n_sm, st);
+    } else {
+      e = launch_mlp_fwd_simt(w, a, n_sm, st);
+    }
+    if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) return MLPS_ERR_CUDA;
+    count_launch(1);
+  }
+  {
+    StageTimer tm(ST_COMP_FWD, st);
+    launch_composite_fwd(w, cfg->feat_dim, rgb, trans, feat, st);
+    count_launch(w.n_rays > 0 ? 1 : 0);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+
+// Backward over views `vs` (the same views as the forward call that filled `saved`).
+mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const std::vector<ViewSpec>& vs,
+                          const float* d_rgb, const float* d_trans, const float* d_feat, const void* saved,
+                          size_t saved_bytes, float* d_weights, float* d_centers, float* d_scales,
+                          float* d_quats, void* scratch, size_t scratch_bytes, void* stream) {
+  if (!scene || scene->K < 0 || !d_rgb || !saved || !scratch) return MLPS_ERR_INVALID_ARGUMENT;
+  const int K = scene->K;
+  if (K > 0 && (!scene->weights || !d_weights || !d_centers || !d_scales || !d_quats))
+    return MLPS_ERR_INVALID_ARGUMENT;
+  if (!aligned256(saved) || !aligned256(scratch)) return MLPS_ERR_INVALID_ARGUMENT;
+  const int n_views = (int)vs.size();
+  Layout L;
+  if (!make_layout(cfg, K, vs.data(), n_views, &L)) return MLPS_ERR_UNSUPPORTED;
+  if (saved_bytes < L.saved_total || scratch_bytes < L.scratch_total)
+    return MLPS_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Work w = make_work(cfg, L, K, n_views, const_cast<void*>(saved), scratch);
+  Model m = make_model(cfg);
+  MlpArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.m = m;
+  a.pk = make_packed(cfg, m);
+  a.weights = static_cast<const unsigned char*>(scene->weights);
+  a.d_weights = d_weights;
+  a.rows = 128;
+  a.resident = (a.pk.stride <= 64 * 1024);
+  TcPlan P;
+  long long tc_stride = 0;
+  // FP8 precision: the backward recomputes the MLP in BF16 from the BF16 tiles of the same blob
+  const bool tc = cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3;
+  if (tc) {
+    if (!tc_plan(m, &P, &tc_stride, cfg->precision == MLPS_FP8_E4M3) || !tc_bwd_supported(m, P))
+      return MLPS_ERR_UNSUPPORTED;
+  } else if (cfg->precision != MLPS_FP32) {
+    return MLPS_ERR_UNSUPPORTED;
+  }
+  const int n_sm = num_sms();
+  {
+    StageTimer tm(ST_COMP_BWD, st);
+    cudaMemsetAsync(w.scr_hdr, 0, 256, st);
+    if (K > 0) {
+      cudaMemsetAsync(w.dgeo, 0, sizeof(float) * 12 * (size_t)K, st);
+      cudaMemsetAsync(d_weights, 0, sizeof(float) * (size_t)m.P * K, st);
+    }
+    launch_composite_bwd(w, cfg->feat_dim, nullptr, nullptr, nullptr, d_rgb, d_trans,
+                         cfg->feat_dim > 0 ? d_feat : nullptr, st);
+    count_launch(w.n_rays > 0 ? 1 : 0);
+  }
+  if (K > 0) {
+    StageTimer tm(ST_MLP_BWD, st);
+    cudaError_t e = tc ? launch_mlp_bwd_tc(w, a, P, n_sm, st) : launch_mlp_bwd_simt(w, a, n_sm, st);
+    if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) return MLPS_ERR_CUDA;
+    count_launch(1);
+  }
+  {
+    StageTimer tm(ST_POSE_BWD, st);
+    launch_pose_bwd(w, d_centers, d_scales, d_quats, st);
+    count_launch(K > 0 ? 1 : 0);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
 
 }  // namespace
 
@@ -419,14 +624,21 @@ mlps_status mlps_workspace_size(const mlps_config* cfg, int32_t K, const mlps_ca
   mlps_status s = mlps_check_config(cfg);
   if (s != MLPS_OK) return s;
   if (K < 0 || !saved_bytes || !scratch_bytes) return MLPS_ERR_INVALID_ARGUMENT;
-  int H, W;
-  s = check_cams(cams, n_views, &H, &W);
+  std::vector<ViewSpec> vs;
+  s = specs_from_cams(cams, n_views, K, &vs);
   if (s != MLPS_OK) return s;
-  Layout L;
-  if (!make_layout(cfg, K, n_views, H, W, &L)) return MLPS_ERR_UNSUPPORTED;
-  *saved_bytes = L.saved_total;
-  *scratch_bytes = L.scratch_total;
-  return MLPS_OK;
+  return workspace_impl(cfg, K, vs, saved_bytes, scratch_bytes);
+}
+
+mlps_status mlps_batch_workspace_size(const mlps_config* cfg, int32_t K, const mlps_batch_item* items,
+                                      int32_t n_items, size_t* saved_bytes, size_t* scratch_bytes) {
+  mlps_status s = mlps_check_config(cfg);
+  if (s != MLPS_OK) return s;
+  if (K < 0 || !saved_bytes || !scratch_bytes) return MLPS_ERR_INVALID_ARGUMENT;
+  std::vector<ViewSpec> vs;
+  s = specs_from_items(items, n_items, K, &vs);
+  if (s != MLPS_OK) return s;
+  return workspace_impl(cfg, K, vs, saved_bytes, scratch_bytes);
 }
 
 mlps_status mlps_render_forward(const mlps_config* cfg, const mlps_scene* scene,
@@ -435,80 +647,24 @@ mlps_status mlps_render_forward(const mlps_config* cfg, const mlps_scene* scene,
                                 void* scratch, size_t scratch_bytes, void* stream) {
   mlps_status s = mlps_check_config(cfg);
   if (s != MLPS_OK) return s;
-  if (!scene || scene->K < 0 || !rgb || !trans || !saved || !scratch)
-    return MLPS_ERR_INVALID_ARGUMENT;
-  if (cfg->feat_dim > 0 && !feat) return MLPS_ERR_INVALID_ARGUMENT;
-  const int K = scene->K;
-  if (K > 0 && (!scene->centers || !scene->scales || !scene->quats || !scene->weights))
-    return MLPS_ERR_INVALID_ARGUMENT;
-  if (!aligned256(saved) || !aligned256(scratch) || (K > 0 && !aligned256(scene->weights)))
-    return MLPS_ERR_INVALID_ARGUMENT;
-  int H, W;
-  s = check_cams(cams, n_views, &H, &W);
+  if (!scene || scene->K < 0) return MLPS_ERR_INVALID_ARGUMENT;
+  std::vector<ViewSpec> vs;
+  s = specs_from_cams(cams, n_views, scene->K, &vs);
   if (s != MLPS_OK) return s;
-  Layout L;
-  if (!make_layout(cfg, K, n_views, H, W, &L)) return MLPS_ERR_UNSUPPORTED;
-  if (saved_bytes < L.saved_total || scratch_bytes < L.scratch_total)
-    return MLPS_ERR_WORKSPACE_TOO_SMALL;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Work w = make_work(cfg, L, K, n_views, H, W, saved, scratch);
-  Model m = make_model(cfg);
-  MlpArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.m = m;
-  a.pk = make_packed(cfg, m);
-  a.weights = static_cast<const unsigned char*>(scene->weights);
-  a.rows = 128;
-  a.resident = (a.pk.stride + 2 * 128 * 4 * (size_t)std::max(std::max(m.nin, m.width), m.nout) +
-                16 * 1024) <= 200 * 1024;
-  const int n_sm = num_sms();
-  {
-    StageTimer tm(ST_SETUP, st);
-    cudaMemsetAsync(w.saved_hdr, 0, 256, st);
-    cudaMemsetAsync(w.prim_count, 0, sizeof(int) * ((size_t)K + 1), st);
-    launch_store_views(w, make_views(cams, n_views), st);
-    launch_prim_setup(w, scene->centers, scene->scales, scene->quats, st);
-    count_launch(K > 0 ? 2 : 1);
-  }
-  {
-    StageTimer tm(ST_TILES, st);
-    launch_tile_lists(w, st);
-    count_launch(1);
-  }
-  {
-    StageTimer tm(ST_INTERSECT, st);
-    if (!launch_intersect(w, st)) return MLPS_ERR_UNSUPPORTED;
-    count_launch(1);
-  }
-  {
-    StageTimer tm(ST_SCAN, st);
-    if (K > 0) { launch_prim_scan(w, st); count_launch(1); }
-  }
-  {
-    StageTimer tm(ST_SCATTER, st);
-    if (K > 0) { launch_scatter(w, n_sm, st); count_launch(1); }
-  }
-  if (K > 0) {
-    StageTimer tm(ST_MLP_FWD, st);
-    cudaError_t e;
-    if (cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3) {
-      TcPlan P;
-      long long stride;
-      tc_plan(m, &P, &stride, cfg->precision == MLPS_FP8_E4M3);
-      e = launch_mlp_fwd_tc(w, a, P, n_sm, st);
-    } else {
-      e = launch_mlp_fwd_simt(w, a, n_sm, st);
-    }
-    if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
-    if (e != cudaSuccess) return MLPS_ERR_CUDA;
-    count_launch(1);
-  }
-  {
-    StageTimer tm(ST_COMP_FWD, st);
-    launch_composite_fwd(w, cfg->feat_dim, rgb, trans, feat, st);
-    count_launch(w.n_rays > 0 ? 1 : 0);
-  }
-  return cuda_status(cudaGetLastError());
+  return forward_impl(cfg, scene, vs, rgb, trans, feat, saved, saved_bytes, scratch, scratch_bytes, stream);
+}
+
+mlps_status mlps_render_batch_forward(const mlps_config* cfg, const mlps_scene* scene,
+                                      const mlps_batch_item* items, int32_t n_items, float* rgb,
+                                      float* trans, float* feat, void* saved, size_t saved_bytes,
+                                      void* scratch, size_t scratch_bytes, void* stream) {
+  mlps_status s = mlps_check_config(cfg);
+  if (s != MLPS_OK) return s;
+  if (!scene || scene->K < 0) return MLPS_ERR_INVALID_ARGUMENT;
+  std::vector<ViewSpec> vs;
+  s = specs_from_items(items, n_items, scene->K, &vs);
+  if (s != MLPS_OK) return s;
+  return forward_impl(cfg, scene, vs, rgb, trans, feat, saved, saved_bytes, scratch, scratch_bytes, stream);
 }
 
 mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene,
@@ -519,64 +675,28 @@ mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene
                                  size_t scratch_bytes, void* stream) {
   mlps_status s = mlps_check_config(cfg);
   if (s != MLPS_OK) return s;
-  if (!scene || scene->K < 0 || !d_rgb || !saved || !scratch) return MLPS_ERR_INVALID_ARGUMENT;
-  const int K = scene->K;
-  if (K > 0 && (!scene->weights || !d_weights || !d_centers || !d_scales || !d_quats))
-    return MLPS_ERR_INVALID_ARGUMENT;
-  if (!aligned256(saved) || !aligned256(scratch)) return MLPS_ERR_INVALID_ARGUMENT;
-  int H, W;
-  s = check_cams(cams, n_views, &H, &W);
+  if (!scene || scene->K < 0) return MLPS_ERR_INVALID_ARGUMENT;
+  std::vector<ViewSpec> vs;
+  s = specs_from_cams(cams, n_views, scene->K, &vs);
   if (s != MLPS_OK) return s;
-  Layout L;
-  if (!make_layout(cfg, K, n_views, H, W, &L)) return MLPS_ERR_UNSUPPORTED;
-  if (saved_bytes < L.saved_total || scratch_bytes < L.scratch_total)
-    return MLPS_ERR_WORKSPACE_TOO_SMALL;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Work w = make_work(cfg, L, K, n_views, H, W, const_cast<void*>(saved), scratch);
-  Model m = make_model(cfg);
-  MlpArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.m = m;
-  a.pk = make_packed(cfg, m);
-  a.weights = static_cast<const unsigned char*>(scene->weights);
-  a.d_weights = d_weights;
-  a.rows = 128;
-  a.resident = (a.pk.stride <= 64 * 1024);
-  const int n_sm = num_sms();
-  {
-    StageTimer tm(ST_COMP_BWD, st);
-    cudaMemsetAsync(w.scr_hdr, 0, 256, st);
-    if (K > 0) {
-      cudaMemsetAsync(w.dgeo, 0, sizeof(float) * 12 * (size_t)K, st);
-      cudaMemsetAsync(d_weights, 0, sizeof(float) * (size_t)m.P * K, st);
-    }
-    launch_composite_bwd(w, cfg->feat_dim, nullptr, nullptr, nullptr, d_rgb, d_trans,
-                         cfg->feat_dim > 0 ? d_feat : nullptr, st);
-    count_launch(w.n_rays > 0 ? 1 : 0);
-  }
-  TcPlan P;
-  long long tc_stride = 0;
-  // FP8 precision: the backward recomputes the MLP in BF16 from the BF16 tiles of the same blob
-  const bool tc = cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3;
-  if (tc) {
-    if (!tc_plan(m, &P, &tc_stride, cfg->precision == MLPS_FP8_E4M3) || !tc_bwd_supported(m, P))
-      return MLPS_ERR_UNSUPPORTED;
-  } else if (cfg->precision != MLPS_FP32) {
-    return MLPS_ERR_UNSUPPORTED;
-  }
-  if (K > 0) {
-    StageTimer tm(ST_MLP_BWD, st);
-    cudaError_t e = tc ? launch_mlp_bwd_tc(w, a, P, n_sm, st) : launch_mlp_bwd_simt(w, a, n_sm, st);
-    if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
-    if (e != cudaSuccess) return MLPS_ERR_CUDA;
-    count_launch(1);
-  }
-  {
-    StageTimer tm(ST_POSE_BWD, st);
-    launch_pose_bwd(w, d_centers, d_scales, d_quats, st);
-    count_launch(K > 0 ? 1 : 0);
-  }
-  return cuda_status(cudaGetLastError());
+  return backward_impl(cfg, scene, vs, d_rgb, d_trans, d_feat, saved, saved_bytes, d_weights, d_centers,
+                       d_scales, d_quats, scratch, scratch_bytes, stream);
+}
+
+mlps_status mlps_render_batch_backward(const mlps_config* cfg, const mlps_scene* scene,
+                                       const mlps_batch_item* items, int32_t n_items, const float* d_rgb,
+                                       const float* d_trans, const float* d_feat, const void* saved,
+                                       size_t saved_bytes, float* d_weights, float* d_centers,
+                                       float* d_scales, float* d_quats, void* scratch,
+                                       size_t scratch_bytes, void* stream) {
+  mlps_status s = mlps_check_config(cfg);
+  if (s != MLPS_OK) return s;
+  if (!scene || scene->K < 0) return MLPS_ERR_INVALID_ARGUMENT;
+  std::vector<ViewSpec> vs;
+  s = specs_from_items(items, n_items, scene->K, &vs);
+  if (s != MLPS_OK) return s;
+  return backward_impl(cfg, scene, vs, d_rgb, d_trans, d_feat, saved, saved_bytes, d_weights, d_centers,
+                       d_scales, d_quats, scratch, scratch_bytes, stream);
 }
 
 mlps_status mlps_read_status(const void* region, void* stream) {
@@ -612,13 +732,13 @@ mlps_status mlps_export_hits(const mlps_config* cfg, const mlps_camera* cams, in
   if (s != MLPS_OK) return s;
   if (!saved || max_out < 1 || !count || !prim || !t0 || !t1 || !tmid)
     return MLPS_ERR_INVALID_ARGUMENT;
-  int H, W;
-  s = check_cams(cams, n_views, &H, &W);
+  std::vector<ViewSpec> vs;
+  // K only shifts arrays after the ray arrays; the hit/ray arrays do not depend on it.
+  s = specs_from_cams(cams, n_views, 0, &vs);
   if (s != MLPS_OK) return s;
   Layout L;
-  // K only shifts arrays after the ray arrays; the hit/ray arrays do not depend on it.
-  if (!make_layout(cfg, 0, n_views, H, W, &L)) return MLPS_ERR_UNSUPPORTED;
-  Work w = make_work(cfg, L, 0, n_views, H, W, const_cast<void*>(saved), nullptr);
+  if (!make_layout(cfg, 0, vs.data(), n_views, &L)) return MLPS_ERR_UNSUPPORTED;
+  Work w = make_work(cfg, L, 0, n_views, const_cast<void*>(saved), nullptr);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (w.n_rays > 0) launch_export_hits(w, max_out, count, prim, t0, t1, tmid, st);
   return cuda_status(cudaGetLastError());
@@ -630,13 +750,13 @@ mlps_status mlps_export_tiles(const mlps_config* cfg, int32_t K, const mlps_came
   mlps_status s = check_cfg(cfg);
   if (s != MLPS_OK) return s;
   if (!scratch || !count || !list || K < 1) return MLPS_ERR_INVALID_ARGUMENT;
-  int H, W;
-  s = check_cams(cams, n_views, &H, &W);
+  std::vector<ViewSpec> vs;
+  s = specs_from_cams(cams, n_views, K, &vs);
   if (s != MLPS_OK) return s;
   Layout L;
-  if (!make_layout(cfg, K, n_views, H, W, &L)) return MLPS_ERR_UNSUPPORTED;
+  if (!make_layout(cfg, K, vs.data(), n_views, &L)) return MLPS_ERR_UNSUPPORTED;
   static char dummy_saved[256];
-  Work w = make_work(cfg, L, K, n_views, H, W, dummy_saved, const_cast<void*>(scratch));
+  Work w = make_work(cfg, L, K, n_views, dummy_saved, const_cast<void*>(scratch));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   launch_export_tiles(w, count, list, st);
   return cuda_status(cudaGetLastError());

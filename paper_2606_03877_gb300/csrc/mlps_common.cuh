@@ -117,6 +117,8 @@ MLPS_DEV dfl df_dot3(const dfl* a, const dfl* b) {
 // Per-view and per-primitive data computed once per call
 
 // Camera of one view (host-computed; the origin is split into hi + lo of its FP64 value).
+// One view of a render call. In a batch every view (item) renders its own primitive range of
+// the scene arrays at its own resolution; a single-scene call has prim_base 0 and prim_n K.
 struct ViewData {
   float R[9];       // world -> camera rotation block, row-major
   float t[3];
@@ -124,8 +126,13 @@ struct ViewData {
   float near_t;
   float o_hi[3], o_lo[3];  // ray origin -R^T t
   int width, height;
-  int ray_base;            // v * H * W
+  int ray_base;            // first global ray (pixel) of this view
+  int prim_base, prim_n;   // the view's primitives [prim_base, prim_base + prim_n)
+  int pv_base;             // first (view, primitive) record of this view in pview
+  int ntx, nty;            // its screen tiles
+  int tile_base;           // first tile of this view in tile_count
   int pad;
+  long long cand_base;     // first candidate slot of this view in tile_list (tiles x prim_n)
 };
 
 struct ViewArray {
@@ -236,18 +243,21 @@ struct Work {
   int* slot_of;          // [cap] hit index -> position in that order
   ViewData* views;       // [V]
   PrimGeo* geo;          // [K]
-  PrimView* pview;       // [V, K]
+  PrimView* pview;       // [n_pairs]: per view, its primitives in order
   // scratch region
   int* scr_hdr;          // [0] status
   int* prim_cursor;      // [K]
-  int* tile_count;       // [V, n_tiles]
-  int* tile_list;        // [V, n_tiles, K]
+  int* tile_count;       // [n_tiles_all]: per view, its tiles in row-major order
+  int* tile_list;        // per view and tile, prim_n candidate slots (global primitive ids)
   float4* hit_grad;      // [cap] (dL/dC_j, dL/da_j) per interval, in primitive-major order
   float* hit_gfeat;      // [cap, F], same order
   float* dgeo;           // [K, 12] dL/dM (9) and dL/dmu (3)
   // sizes
-  int K, V, H, W;
-  int tile, ntx, nty, n_tiles;
+  int K, V;
+  int H, W, ntx, nty, n_tiles;  // view 0's sizes (the single-scene inspection calls use them)
+  int tile;
+  int n_pairs;           // sum over views of prim_n
+  int max_view_tiles;    // largest tile count of a view (grid size of the per-tile kernels)
   int n_rays;
   int hit_cap;
   int max_hits;
@@ -255,5 +265,16 @@ struct Work {
   int S;                 // samples per interval
   float t_eps;
 };
+
+// View of a global ray (views are stored in ray order; at most kMaxViews, binary search).
+MLPS_DEV int view_of_ray(const Work& w, int ray) {
+  int lo = 0, hi = w.V - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (w.views[mid].ray_base <= ray) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 }  // namespace mlps

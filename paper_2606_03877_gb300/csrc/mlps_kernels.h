@@ -49,8 +49,9 @@ struct TcPlan {
 
 // k_geometry.cu
 void launch_store_views(const Work& w, const ViewArray& va, cudaStream_t st);
-void launch_prim_setup(const Work& w, const float* c, const float* s, const float* q,
-                       cudaStream_t st);
+// returns the number of kernels launched
+int launch_prim_setup(const Work& w, const float* c, const float* s, const float* q,
+                      cudaStream_t st);
 void launch_tile_lists(const Work& w, cudaStream_t st);
 bool launch_intersect(const Work& w, cudaStream_t st);
 void launch_prim_scan(const Work& w, cudaStream_t st);

@@ -161,3 +161,86 @@ def render(renderer: Renderer, cams: Sequence[dict], centers: torch.Tensor, scal
     One forward pass per call; the backward pass of the same renderer must follow before the
     next forward on it (the forward state lives in the renderer's workspace)."""
     return _RenderFn.apply(renderer, cams, centers, scales, quats, weights)
+
+
+class BatchRenderer:
+    """Many scenes of uneven primitive counts and resolutions in one call (mlps_render_batch_*).
+
+    ``items`` are (prim_offset, prim_count, camera) tuples over ONE concatenated set of scene
+    arrays with ``K`` primitives in total; item i renders its primitive range through its camera at
+    the camera's own resolution. Outputs are concatenated in item order (``split`` gives per-item
+    views). Workspaces are allocated here, once, so forward/backward can be captured in a CUDA
+    graph and replayed."""
+
+    def __init__(self, shape, items: Sequence[tuple], K: int, precision: str = "bf16",
+                 device: str = "cuda", **kw):
+        self.shape = shape
+        self.precision = precision
+        self.cfg = make_config(shape, precision, **kw)
+        st = _lib.mlps_check_config(self.cfg)
+        if st != _lib.MLPS_OK:
+            raise _lib.MlpsError("mlps_check_config", st)
+        self.device = torch.device(device)
+        self.P = _lib.mlps_param_count(self.cfg)
+        self.stride = _lib.mlps_weight_stride(self.cfg)
+        self.F = int(shape.feat_dim)
+        self.K = int(K)
+        self.items = _lib.batch_items(items)
+        self.n = len(items)
+        self.sizes = [(int(c["height"]), int(c["width"])) for _, _, c in items]
+        self.offsets = [0]
+        for h, w in self.sizes:
+            self.offsets.append(self.offsets[-1] + h * w)
+        self.n_pixels = self.offsets[-1]
+        sb, tb = _lib.mlps_batch_workspace_size(self.cfg, self.K, self.items, self.n)
+        self.saved = torch.empty(sb, dtype=torch.uint8, device=self.device)
+        self.scratch = torch.empty(tb, dtype=torch.uint8, device=self.device)
+        self._scene = None
+
+    def pack(self, weights: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        w = weights.detach().to(self.device, torch.float32).contiguous()
+        assert w.shape == (self.K, self.P), (w.shape, self.K, self.P)
+        if out is None:
+            out = torch.empty(max(self.K, 1) * self.stride, dtype=torch.uint8, device=self.device)
+        _lib.mlps_pack_weights(self.cfg, self.K, w, out, _stream())
+        return out
+
+    def new_outputs(self) -> Dict[str, torch.Tensor]:
+        P, dev = self.n_pixels, self.device
+        return {"rgb": torch.empty(P, 3, device=dev), "trans": torch.empty(P, device=dev),
+                "feat": torch.empty(P, self.F, device=dev) if self.F else None}
+
+    def new_grads(self) -> Dict[str, torch.Tensor]:
+        K, dev = self.K, self.device
+        return {"d_weights": torch.empty(K, self.P, device=dev), "d_centers": torch.empty(K, 3, device=dev),
+                "d_scales": torch.empty(K, 3, device=dev), "d_quats": torch.empty(K, 4, device=dev)}
+
+    def forward(self, centers, scales, quats, packed, out: Optional[Dict[str, torch.Tensor]] = None):
+        if out is None:
+            out = self.new_outputs()
+        self._scene = _lib.make_scene(self.K, centers, scales, quats, packed)
+        self._keep = (centers, scales, quats, packed)
+        _lib.mlps_render_batch_forward(self.cfg, self._scene, self.items, self.n, out["rgb"], out["trans"],
+                                       out.get("feat"), self.saved, self.saved.numel(), self.scratch,
+                                       self.scratch.numel(), _stream())
+        return out
+
+    def backward(self, d_rgb, d_trans=None, d_feat=None, out: Optional[Dict[str, torch.Tensor]] = None):
+        if out is None:
+            out = self.new_grads()
+        _lib.mlps_render_batch_backward(self.cfg, self._scene, self.items, self.n, d_rgb.contiguous(),
+                                        None if d_trans is None else d_trans.contiguous(),
+                                        None if d_feat is None else d_feat.contiguous(),
+                                        self.saved, self.saved.numel(), out["d_weights"], out["d_centers"],
+                                        out["d_scales"], out["d_quats"], self.scratch, self.scratch.numel(),
+                                        _stream())
+        return out
+
+    def split(self, t: torch.Tensor) -> List[torch.Tensor]:
+        """Per-item [H_i, W_i, ...] views of a concatenated per-pixel tensor."""
+        return [t[self.offsets[i]:self.offsets[i + 1]].view(h, w, *t.shape[1:])
+                for i, (h, w) in enumerate(self.sizes)]
+
+    def status(self, region: str = "saved") -> int:
+        t = self.saved if region == "saved" else self.scratch
+        return _lib.mlps_read_status(t, _stream())

@@ -32,7 +32,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import Dict, List, Optional
+from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
@@ -155,6 +155,21 @@ def batch_configs(n_scenes: int = BATCH_SCENES, seed: int = 0) -> List[SceneConf
         w, h = BATCH_RESOLUTIONS[int(u[2 * i + 1] * len(BATCH_RESOLUTIONS))]
         out.append(SceneConfig(f"batch{i}", w, h, K, 1, 6, 4, 64, 3, 0, 32, "bf16"))
     return out
+
+
+def make_batch(cfgs: Sequence[SceneConfig], first_seed: int = 0):
+    """A batch of independent scenes: scene i (seed first_seed + i) seen by one camera (view
+    seed first_seed + i) at cfgs[i]'s resolution. Returns (scene arrays of all scenes
+    concatenated, items as (prim_offset, prim_count, camera), per-scene scenes). All scenes must
+    share the MLP shape."""
+    scenes, items, off = [], [], 0
+    for i, c in enumerate(cfgs):
+        sc = make_scene(c, first_seed + i)
+        scenes.append(sc)
+        items.append((off, c.K, make_camera(c.width, c.height, first_seed + i)))
+        off += c.K
+    cat = {k: np.concatenate([sc[k] for sc in scenes], axis=0) for k in scenes[0]}
+    return cat, items, scenes
 
 
 def make_scene(cfg: SceneConfig, seed: int = 0) -> Dict[str, np.ndarray]:

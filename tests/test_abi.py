@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert _lib.mlps_abi_version() == 1
+    assert _lib.mlps_abi_version() == 2
     for s in range(8):
         assert _lib.mlps_status_string(s)
     assert _lib.mlps_status_string(4) == "hit capacity overflow"
@@ -101,3 +101,30 @@ def test_sample_pixels_uniform_over_views():
     assert len(p) == 4000 and len(np.unique(p, axis=0)) == 4000
     counts = np.bincount(p[:, 0], minlength=c.n_views)
     assert counts.min() > 0.7 * 4000 / c.n_views
+
+
+def test_batch_workspace_matches_single_scene_layout(lib):
+    """A batch whose items all render the whole scene at one resolution is the single-scene
+    multi-view call: same workspace."""
+    c = synth.CONFIGS["prec"].replace(width=320, height=200, n_views=3)
+    cfg = make_config(c)
+    cams = synth.make_cameras(c)
+    single = _lib.mlps_workspace_size(cfg, c.K, _lib.cameras(cams), 3)
+    items = _lib.batch_items([(0, c.K, cam) for cam in cams])
+    assert _lib.mlps_batch_workspace_size(cfg, c.K, items, 3) == single
+
+
+def test_batch_item_validation(lib):
+    c = synth.CONFIGS["prec"].replace(width=64, height=48, n_views=2)
+    cfg = make_config(c)
+    cams = synth.make_cameras(c)
+    ok = _lib.batch_items([(0, 10, cams[0]), (10, 20, cams[1])])
+    sb, tb = _lib.mlps_batch_workspace_size(cfg, 30, ok, 2)
+    assert sb > 0 and tb > 0
+    for bad in ([(0, 10, cams[0]), (25, 10, cams[1])], [(-1, 5, cams[0])], [(0, -2, cams[0])]):
+        with pytest.raises(_lib.MlpsError) as e:
+            _lib.mlps_batch_workspace_size(cfg, 30, _lib.batch_items(bad), len(bad))
+        assert e.value.status == _lib.MLPS_ERR_INVALID_ARGUMENT
+    # mixed resolutions are allowed in a batch
+    big = dict(cams[1], width=128, height=96, cx=64.0, cy=48.0)
+    _lib.mlps_batch_workspace_size(cfg, 30, _lib.batch_items([(0, 10, cams[0]), (10, 20, big)]), 2)

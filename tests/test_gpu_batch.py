@@ -1,0 +1,160 @@
+"""Batched rendering (many scenes of uneven primitive counts and resolutions in one call) on the
+GPU: every item against the oracle, against the single-scene call, gradients, shared primitive
+ranges and CUDA-graph capture and replay."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2606_03877_gb300 import synth
+from paper_2606_03877_gb300.render import BatchRenderer
+
+from helpers import gpu_render, psnr, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = synth.CONFIGS["prec"]  # MLP shape shared by the batch (60-64x64x64-4, S = 32)
+
+
+def _small_batch(first_seed=20):
+    sizes = [(64, 48, 12), (40, 40, 30), (80, 60, 7), (48, 64, 21), (32, 24, 16)]
+    cfgs = [SHAPE.replace(width=w, height=h, K=k, n_views=1) for w, h, k in sizes]
+    cat, items, scenes = synth.make_batch(cfgs, first_seed)
+    cat = dict(cat, scales=(cat["scales"] * 2.0).astype(np.float32))  # more hits per ray
+    scenes = [dict(sc, scales=(sc["scales"] * 2.0).astype(np.float32)) for sc in scenes]
+    return cfgs, cat, items, scenes
+
+
+def _batch_forward(precision, cat, items, **kw):
+    K = cat["centers"].shape[0]
+    br = BatchRenderer(SHAPE, items, K, precision=precision, **kw)
+    d = to_dev(cat)
+    packed = br.pack(d["weights"])
+    out = br.forward(d["centers"], d["scales"], d["quats"], packed)
+    torch.cuda.synchronize()
+    assert br.status() == 0
+    return br, out, d, packed
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_batch_items_match_oracle(precision):
+    cfgs, cat, items, scenes = _small_batch()
+    br, out, _, _ = _batch_forward(precision, cat, items)
+    for i, (c, sc, it) in enumerate(zip(cfgs, scenes, items)):
+        rgb_o, T_o, _ = oracle.render(c, sc, [it[2]])
+        rgb = br.split(out["rgb"])[i].cpu().numpy().reshape(-1, 3)
+        T = br.split(out["trans"])[i].cpu().numpy().reshape(-1)
+        if precision == "fp32":
+            assert np.abs(rgb - rgb_o).max() < 1e-4, i
+            assert np.abs(T - T_o).max() < 1e-4, i
+        else:
+            assert psnr(rgb, rgb_o) >= 45.0, i
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_batch_forward_is_bit_identical_to_single_scene_calls(precision):
+    """Each sample row's MLP result and each interval's composite depend only on that interval,
+    so batching changes no output bit."""
+    cfgs, cat, items, scenes = _small_batch(30)
+    br, out, _, _ = _batch_forward(precision, cat, items)
+    for i, (c, sc, it) in enumerate(zip(cfgs, scenes, items)):
+        _, o1, _, _ = gpu_render(c, sc, [it[2]], precision)
+        assert np.array_equal(br.split(out["rgb"])[i].cpu().numpy(), o1["rgb"][0]), i
+        assert np.array_equal(br.split(out["trans"])[i].cpu().numpy(), o1["trans"][0]), i
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_batch_backward_matches_single_scene_calls(precision):
+    from paper_2606_03877_gb300.render import Renderer
+    cfgs, cat, items, scenes = _small_batch(40)
+    br, out, d, packed = _batch_forward(precision, cat, items)
+    g = torch.from_numpy(synth.make_grad((br.n_pixels, 3), seed=9)).cuda()
+    gb = br.backward(g)
+    torch.cuda.synchronize()
+    assert br.status("scratch") == 0
+    gs = br.split(g)
+    for i, (c, sc, it) in enumerate(zip(cfgs, scenes, items)):
+        r = Renderer(c, precision=precision)
+        ds = to_dev(sc)
+        pk = r.pack(ds["weights"])
+        r.forward(ds["centers"], ds["scales"], ds["quats"], pk, [it[2]])
+        g1 = r.backward(gs[i].reshape(1, c.height, c.width, 3))
+        torch.cuda.synchronize()
+        o, n = it[0], it[1]
+        for k in ("d_weights", "d_centers", "d_scales", "d_quats"):
+            e = rel_l2(gb[k][o:o + n].cpu().numpy(), g1[k].cpu().numpy())
+            assert e < (1e-5 if precision == "fp32" else 1e-4), (i, k, e)
+
+
+def test_batch_fp32_gradients_match_oracle():
+    """L = 1/2 sum (C - C*)^2 per item with C* the oracle render of the item's scene perturbed
+    with seed 1 (the differentiation workload's loss)."""
+    cfgs, cat, items, scenes = _small_batch(50)
+    br, out, d, packed = _batch_forward("fp32", cat, items)
+    gs = []
+    for c, sc, it in zip(cfgs, scenes, items):
+        cur, _, _ = oracle.render(c, sc, [it[2]])
+        tgt, _, _ = oracle.render(c, synth.perturb_scene(sc, c, 1), [it[2]])
+        gs.append((cur - tgt).astype(np.float32))
+    g = torch.from_numpy(np.concatenate(gs, axis=0)).cuda()
+    gb = br.backward(g)
+    torch.cuda.synchronize()
+    for i in (0, 2):
+        c, sc, it = cfgs[i], scenes[i], items[i]
+        ref = oracle.render_backward(c, sc, [it[2]], oracle.all_pixels([it[2]]), gs[i].reshape(-1, 3))
+        o, n = it[0], it[1]
+        for k in ("d_weights", "d_centers", "d_scales", "d_quats"):
+            e = rel_l2(gb[k][o:o + n].cpu().numpy(), ref[k])
+            assert e < 1e-3, (i, k, e)
+
+
+def test_batch_items_sharing_primitives_equal_multiview_call():
+    c = SHAPE.replace(width=56, height=40, K=20, n_views=3)
+    sc = synth.make_scene(c, 7)
+    sc = dict(sc, scales=(sc["scales"] * 2.0).astype(np.float32))
+    cams = synth.make_cameras(c, first_view_seed=7)
+    _, o1, _, _ = gpu_render(c, sc, cams, "bf16")
+    br, out, _, _ = _batch_forward("bf16", sc, [(0, c.K, cam) for cam in cams])
+    assert np.array_equal(out["rgb"].cpu().numpy().reshape(o1["rgb"].shape), o1["rgb"])
+
+
+def test_batch_cuda_graph_capture_and_replay():
+    """Forward + backward of a batch captured once in a CUDA graph; replays match eager calls,
+    also after the scene parameters are changed in place."""
+    cfgs, cat, items, scenes = _small_batch(60)
+    K = cat["centers"].shape[0]
+    br = BatchRenderer(SHAPE, items, K, precision="bf16")
+    d = to_dev(cat)
+    w = d["weights"]
+    packed = torch.empty(K * br.stride, dtype=torch.uint8, device="cuda")
+    out = br.new_outputs()
+    grads = br.new_grads()
+    g = torch.from_numpy(synth.make_grad((br.n_pixels, 3), seed=2)).cuda()
+
+    def step():
+        br.pack(w, out=packed)
+        br.forward(d["centers"], d["scales"], d["quats"], packed, out=out)
+        br.backward(g, out=grads)
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()  # warm-up outside capture (kernel attributes, driver entry points)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for trial in range(2):
+        if trial == 1:
+            with torch.no_grad():
+                d["centers"].mul_(1.01)  # new inputs, same buffers
+        graph.replay()
+        torch.cuda.synchronize()
+        assert br.status() == 0 and br.status("scratch") == 0
+        rgb_g = out["rgb"].clone()
+        gw = grads["d_weights"].clone()
+        step()  # eager
+        torch.cuda.synchronize()
+        assert torch.equal(rgb_g, out["rgb"])
+        assert rel_l2(gw.cpu().numpy(), grads["d_weights"].cpu().numpy()) < 1e-5
