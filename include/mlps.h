@@ -81,8 +81,12 @@ typedef struct {
   int32_t max_hits_per_ray;     /* per-ray sorted hit capacity, 1..64 */
   float hit_capacity_per_ray;   /* hit-record capacity = ceil(rays * this), > 0 */
   float t_eps;                  /* early termination: stop compositing once T < t_eps (0: never) */
-  int32_t tile;                 /* screen tile edge in pixels for binning (16) */
-  int32_t reserved[5];          /* must be zero */
+  int32_t tile;                 /* screen tile edge in pixels for binning: 16 (default) or 8 */
+  int32_t mlp_groups;           /* chunks of 128 sample rows in flight per CTA in the forward
+                                   tensor-core MLP (2..4 at width 64, 3 with a feature head,
+                                   2 at width 128); 0 = library default. mlps_autotune_batch
+                                   picks it together with `tile`. */
+  int32_t reserved[4];          /* must be zero */
 } mlps_config;
 
 typedef struct {
@@ -232,6 +236,30 @@ mlps_status mlps_render_batch_backward(const mlps_config* cfg, const mlps_scene*
                                        size_t saved_bytes, float* d_weights, float* d_centers,
                                        float* d_scales, float* d_quats, void* scratch,
                                        size_t scratch_bytes, void* stream);
+
+/* Autotuner (no counterpart in the paper): picks `tile` (16 or 8) and `mlp_groups` (samples per
+ * CTA of the forward tensor-core MLP: 2, 3 or 4 chunks of 128 rows, width-64 models without a
+ * feature head; other shapes keep their default) for this batch by running every candidate
+ * `reps` times (after one warm-up run) on the caller's arguments, as mlps_render_batch_forward
+ * (+ mlps_render_batch_backward with dL/drgb = d_rgb when do_backward), timed with CUDA events
+ * on `stream`. Candidates whose workspace exceeds saved_bytes / scratch_bytes are skipped.
+ * Writes *tuned = *cfg with the fastest tile and mlp_groups and *best_ms (mean ms per run;
+ * 0 when the decision came from the cache). Decisions are cached per batch shape (model, S,
+ * precision, max hits, each item's primitive count and resolution, do_backward) for the life of
+ * the process. Optional outputs (host, capacity 8, may be NULL): the candidates' tile, groups
+ * and ms (negative = did not run). Synchronises `stream`; do not call it during stream capture.
+ * The output and gradient buffers are overwritten. Returns MLPS_ERR_UNSUPPORTED if no
+ * candidate ran. */
+mlps_status mlps_autotune_batch(const mlps_config* cfg, const mlps_scene* scene, const mlps_batch_item* items,
+                                int32_t n_items, int32_t do_backward, const float* d_rgb, float* rgb,
+                                float* trans, float* feat, void* saved, size_t saved_bytes, void* scratch,
+                                size_t scratch_bytes, float* d_weights, float* d_centers, float* d_scales,
+                                float* d_quats, int32_t reps, mlps_config* tuned, float* best_ms,
+                                int32_t* n_candidates, int32_t* cand_tile, int32_t* cand_groups,
+                                float* cand_ms, void* stream);
+
+/* Forget every cached autotuner decision. */
+void mlps_autotune_clear(void);
 
 /* Synchronise `stream`, return the device status word of a `saved` or `scratch` region
  * written by the calls above (MLPS_OK if none), and clear it. */

@@ -38,7 +38,8 @@ class MlpsConfig(ctypes.Structure):
                 ("feat_dim", ctypes.c_int32), ("samples", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_hits_per_ray", ctypes.c_int32),
                 ("hit_capacity_per_ray", ctypes.c_float), ("t_eps", ctypes.c_float),
-                ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("tile", ctypes.c_int32), ("mlp_groups", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class MlpsCamera(ctypes.Structure):
@@ -95,6 +96,12 @@ _SIGS = [
     ("mlps_render_batch_backward", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _P(MlpsBatchItem),
                                                     ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                                     _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    ("mlps_autotune_batch", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _P(MlpsBatchItem), ctypes.c_int32,
+                                             ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp,
+                                             ctypes.c_size_t, _vp, _vp, _vp, _vp, ctypes.c_int32,
+                                             _P(MlpsConfig), _P(ctypes.c_float), _P(ctypes.c_int32),
+                                             _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_float), _vp]),
+    ("mlps_autotune_clear", None, []),
     ("mlps_render_forward_static", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _P(MlpsCamera),
                                                     ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
     ("mlps_read_status", ctypes.c_int32, [_vp, _vp]),
@@ -258,6 +265,28 @@ def mlps_render_batch_backward(cfg, scene: MlpsScene, items, n_items, d_rgb, d_t
         ctypes.byref(cfg), ctypes.byref(scene), items, int(n_items), _ptr(d_rgb), _ptr(d_trans), _ptr(d_feat),
         _ptr(saved), int(saved_bytes), _ptr(d_weights), _ptr(d_centers), _ptr(d_scales), _ptr(d_quats),
         _ptr(scratch), int(scratch_bytes), stream or None))
+
+
+def mlps_autotune_batch(cfg, scene: MlpsScene, items, n_items, do_backward, d_rgb, rgb, trans, feat, saved,
+                        saved_bytes, scratch, scratch_bytes, d_weights, d_centers, d_scales, d_quats,
+                        reps: int = 3, stream: int = 0):
+    """Returns (tuned MlpsConfig, best ms, [(tile, groups, ms), ...] candidates timed)."""
+    tuned = MlpsConfig()
+    best = ctypes.c_float()
+    nc = ctypes.c_int32()
+    ct = (ctypes.c_int32 * 8)()
+    cg = (ctypes.c_int32 * 8)()
+    cm = (ctypes.c_float * 8)()
+    _check("mlps_autotune_batch", load().mlps_autotune_batch(
+        ctypes.byref(cfg), ctypes.byref(scene), items, int(n_items), int(do_backward), _ptr(d_rgb), _ptr(rgb),
+        _ptr(trans), _ptr(feat), _ptr(saved), int(saved_bytes), _ptr(scratch), int(scratch_bytes),
+        _ptr(d_weights), _ptr(d_centers), _ptr(d_scales), _ptr(d_quats), int(reps), ctypes.byref(tuned),
+        ctypes.byref(best), ctypes.byref(nc), ct, cg, cm, stream or None))
+    return tuned, float(best.value), [(int(ct[i]), int(cg[i]), float(cm[i])) for i in range(nc.value)]
+
+
+def mlps_autotune_clear():
+    load().mlps_autotune_clear()
 
 
 def mlps_render_forward_static(cfg, scene: MlpsScene, cams, n_views, rgb, trans, feat,

@@ -557,14 +557,21 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3) {
   return true;
 }
 
-// Epilogue groups of the forward kernel: registers cap the feature-head variants at three
-// groups (the head keeps 4 + 32 values per thread), TMEM caps width 128 at four and shared
-// memory (a 32 KB operand tile per group) at two.
-static int fwd_groups(int width, int F) { return width == 64 ? (F > 0 ? 3 : 4) : 2; }
+// Epilogue groups of the forward kernel (chunks of 128 sample rows in flight per CTA). Default:
+// registers cap the feature-head variants at three groups (the head keeps 4 + 32 values per
+// thread), TMEM caps width 128 at four and shared memory (a 32 KB operand tile per group) at
+// two. Width 64 without a feature head also runs with 2 or 3 (the autotuner's choices).
+int tc_fwd_groups(int width, int F, int groups) {
+  const int def = width == 64 ? (F > 0 ? 3 : 4) : 2;
+  if (groups == 0) return def;
+  if (width == 64 && F == 0) return (groups >= 2 && groups <= 4) ? groups : 0;
+  return groups == def ? groups : 0;
+}
 
-size_t tc_smem_bytes(const TcPlan& P, int F) {
+size_t tc_smem_bytes(const TcPlan& P, int F, int groups) {
   const int width = P.npad[0];  // hidden width = N of layer 0
-  return tc::tc_smem(P, fwd_groups(width, F), P.w8_bytes > 0).total + 1024;
+  const int neg = tc_fwd_groups(width, F, groups);
+  return tc::tc_smem(P, neg > 0 ? neg : 4, P.w8_bytes > 0).total + 1024;
 }
 
 void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
@@ -599,17 +606,21 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes(P, a.m.F);
+  const int neg = tc_fwd_groups(a.m.width, a.m.F, a.groups);
+  if (neg == 0) return cudaErrorNotSupported;
+  const size_t smem = tc_smem_bytes(P, a.m.F, a.groups);
   if (smem > 227 * 1024) return cudaErrorNotSupported;
   const int xl = a.m.xyzL, dl = a.m.dirL;
   const bool fast64 = xl == 6 && dl == 4 && P.kpad[0] == 64;
   const bool raw = xl == 0 && dl == 0 && P.kpad[0] == 64;
   decltype(&tc::k_mlp_fwd_tc<64, 6, 4, 0, 4, false>) kern;
   const bool feat = a.m.F > 0;
-  const int neg = fwd_groups(a.m.width, a.m.F);
+#define MLPS_BY_GROUPS(W, XL, DL, F8) \
+  (neg == 2 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 2, F8> : neg == 3 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 3, F8> \
+            : tc::k_mlp_fwd_tc<W, XL, DL, 0, 4, F8>)
   if (P.w8_bytes > 0) {  // E4M3
     if (a.m.width == 64) {
-      if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, 0, 4, true> : tc::k_mlp_fwd_tc<64, -1, -1, 0, 4, true>;
+      if (!feat) kern = fast64 ? MLPS_BY_GROUPS(64, 6, 4, true) : MLPS_BY_GROUPS(64, -1, -1, true);
       else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, kMaxFeat, 3, true> : tc::k_mlp_fwd_tc<64, -1, -1, kMaxFeat, 3, true>;
     } else if (a.m.width == 128) {
       if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 0, 2, true> : tc::k_mlp_fwd_tc<128, -1, -1, 0, 2, true>;
@@ -618,7 +629,9 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
       return cudaErrorNotSupported;
     }
   } else if (a.m.width == 64) {
-    if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, 0, 4, false> : raw ? tc::k_mlp_fwd_tc<64, 0, 0, 0, 4, false> : tc::k_mlp_fwd_tc<64, -1, -1, 0, 4, false>;
+    if (!feat)
+      kern = fast64 ? MLPS_BY_GROUPS(64, 6, 4, false)
+                    : (raw && neg == 4) ? tc::k_mlp_fwd_tc<64, 0, 0, 0, 4, false> : MLPS_BY_GROUPS(64, -1, -1, false);
     else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, kMaxFeat, 3, false> : tc::k_mlp_fwd_tc<64, -1, -1, kMaxFeat, 3, false>;
   } else if (a.m.width == 128) {
     if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 0, 2, false> : tc::k_mlp_fwd_tc<128, -1, -1, 0, 2, false>;
@@ -626,6 +639,7 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
   } else {
     return cudaErrorNotSupported;
   }
+#undef MLPS_BY_GROUPS
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<n_sm, tc::threads_tc(neg), smem, st>>>(w, a, P, tmap);

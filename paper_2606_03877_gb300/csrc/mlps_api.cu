@@ -86,8 +86,9 @@ mlps_status check_cfg(const mlps_config* c) {
   if (!finite_f(c->hit_capacity_per_ray) || !(c->hit_capacity_per_ray > 0.f))
     return MLPS_ERR_INVALID_ARGUMENT;
   if (!finite_f(c->t_eps) || c->t_eps < 0.f || c->t_eps >= 1.f) return MLPS_ERR_INVALID_ARGUMENT;
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 4; ++i)
     if (c->reserved[i] != 0) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->mlp_groups != 0 && (c->mlp_groups < 2 || c->mlp_groups > 4)) return MLPS_ERR_INVALID_ARGUMENT;
   if (c->hidden_width != 32 && c->hidden_width != 64 && c->hidden_width != 128)
     return MLPS_ERR_UNSUPPORTED;
   if (c->tile != 16 && c->tile != 8) return MLPS_ERR_UNSUPPORTED;
@@ -411,6 +412,7 @@ mlps_status forward_impl(const mlps_config* cfg, const mlps_scene* scene, const 
   a.pk = make_packed(cfg, m);
   a.weights = static_cast<const unsigned char*>(scene->weights);
   a.rows = 128;
+  a.groups = cfg->mlp_groups;
   a.resident = (a.pk.stride + 2 * 128 * 4 * (size_t)std::max(std::max(m.nin, m.width), m.nout) +
                 16 * 1024) <= 200 * 1024;
   const int n_sm = num_sms();
@@ -589,8 +591,10 @@ mlps_status mlps_check_config(const mlps_config* cfg) {
   if (cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3) {
     TcPlan P;
     long long stride;
-    if (!tc_plan(make_model(cfg), &P, &stride, cfg->precision == MLPS_FP8_E4M3)) return MLPS_ERR_UNSUPPORTED;
-    if (tc_smem_bytes(P, cfg->feat_dim) > 227 * 1024) return MLPS_ERR_UNSUPPORTED;
+    const Model m = make_model(cfg);
+    if (!tc_plan(m, &P, &stride, cfg->precision == MLPS_FP8_E4M3)) return MLPS_ERR_UNSUPPORTED;
+    if (tc_fwd_groups(m.width, m.F, cfg->mlp_groups) == 0) return MLPS_ERR_UNSUPPORTED;
+    if (tc_smem_bytes(P, cfg->feat_dim, cfg->mlp_groups) > 227 * 1024) return MLPS_ERR_UNSUPPORTED;
     return MLPS_OK;
   }
   if (cfg->precision != MLPS_FP32) return MLPS_ERR_UNSUPPORTED;

@@ -24,6 +24,7 @@ struct MlpArgs {
   float* d_weights;              // backward: canonical FP32 gradient [K, P]
   int resident;                  // FP32: all layers in shared memory at once
   int rows;                      // sample rows per chunk
+  int groups;                    // forward tensor-core MLP: chunks in flight per CTA (0 = default)
 };
 
 // Tensor-core plan: per-layer padded shapes and where the operand tiles live.
@@ -67,7 +68,9 @@ cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaS
 
 // k_mlp_tc.cu (BF16 tensor-core path)
 bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3 = false);
-size_t tc_smem_bytes(const TcPlan& P, int F);
+size_t tc_smem_bytes(const TcPlan& P, int F, int groups = 0);
+// forward tensor-core MLP: the groups a configuration runs with (0 if `groups` is not allowed)
+int tc_fwd_groups(int width, int F, int groups);
 void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
                       void* out, cudaStream_t st);
 cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,

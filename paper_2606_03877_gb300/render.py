@@ -13,7 +13,7 @@ from . import _lib
 
 
 def make_config(shape, precision: str = "fp32", t_eps: float = 1e-6, max_hits: int = 64,
-                hit_capacity: float = 8.0, tile: int = 16) -> _lib.MlpsConfig:
+                hit_capacity: float = 8.0, tile: int = 16, mlp_groups: int = 0) -> _lib.MlpsConfig:
     """mlps_config from any object with xyz_freqs, dir_freqs, hidden_width, hidden_layers,
     feat_dim and samples (e.g. :class:`synth.SceneConfig`)."""
     cfg = _lib.mlps_config_default(int(shape.xyz_freqs), int(shape.dir_freqs), int(shape.hidden_width),
@@ -24,6 +24,7 @@ def make_config(shape, precision: str = "fp32", t_eps: float = 1e-6, max_hits: i
     cfg.max_hits_per_ray = int(max_hits)
     cfg.hit_capacity_per_ray = float(hit_capacity)
     cfg.tile = int(tile)
+    cfg.mlp_groups = int(mlp_groups)
     return cfg
 
 
@@ -192,10 +193,34 @@ class BatchRenderer:
         for h, w in self.sizes:
             self.offsets.append(self.offsets[-1] + h * w)
         self.n_pixels = self.offsets[-1]
-        sb, tb = _lib.mlps_batch_workspace_size(self.cfg, self.K, self.items, self.n)
+        # workspaces large enough for either tile edge, so the autotuner can try both
+        sizes = []
+        for t in (16, 8):
+            c = make_config(shape, precision, **dict(kw, tile=t))
+            sizes.append(_lib.mlps_batch_workspace_size(c, self.K, self.items, self.n))
+        sb = max(x[0] for x in sizes)
+        tb = max(x[1] for x in sizes)
         self.saved = torch.empty(sb, dtype=torch.uint8, device=self.device)
         self.scratch = torch.empty(tb, dtype=torch.uint8, device=self.device)
         self._scene = None
+        self.tuning = None
+
+    def autotune(self, centers, scales, quats, packed, d_rgb=None, reps: int = 3):
+        """Pick tile edge and samples per CTA for this batch (mlps_autotune_batch) and use them
+        from now on. Times the forward pass, or forward + backward when d_rgb is given.
+        Synchronises; call it before capturing a graph."""
+        out = self.new_outputs()
+        grads = self.new_grads()
+        scene = _lib.make_scene(self.K, centers, scales, quats, packed)
+        tuned, best, cands = _lib.mlps_autotune_batch(
+            self.cfg, scene, self.items, self.n, 1 if d_rgb is not None else 0,
+            None if d_rgb is None else d_rgb.contiguous(), out["rgb"], out["trans"], out.get("feat"),
+            self.saved, self.saved.numel(), self.scratch, self.scratch.numel(), grads["d_weights"],
+            grads["d_centers"], grads["d_scales"], grads["d_quats"], reps, _stream())
+        self.cfg = tuned
+        self.tuning = {"tile": int(tuned.tile), "mlp_groups": int(tuned.mlp_groups), "best_ms": best,
+                       "candidates": cands}
+        return self.tuning
 
     def pack(self, weights: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         w = weights.detach().to(self.device, torch.float32).contiguous()

@@ -128,3 +128,16 @@ def test_batch_item_validation(lib):
     # mixed resolutions are allowed in a batch
     big = dict(cams[1], width=128, height=96, cx=64.0, cy=48.0)
     _lib.mlps_batch_workspace_size(cfg, 30, _lib.batch_items([(0, 10, cams[0]), (10, 20, big)]), 2)
+
+
+def test_mlp_groups_validation(lib):
+    base = synth.CONFIGS["prec"]
+    for g, want in ((1, _lib.MLPS_ERR_INVALID_ARGUMENT), (5, _lib.MLPS_ERR_INVALID_ARGUMENT),
+                    (2, _lib.MLPS_OK), (3, _lib.MLPS_OK), (4, _lib.MLPS_OK)):
+        assert _lib.mlps_check_config(make_config(base, "bf16", mlp_groups=g)) == want, g
+    # wider models and feature heads run with their default only
+    assert _lib.mlps_check_config(make_config(synth.CONFIGS["stress"], "bf16", mlp_groups=3)) == \
+        _lib.MLPS_ERR_UNSUPPORTED
+    assert _lib.mlps_check_config(make_config(synth.CONFIGS["stress"], "bf16", mlp_groups=2)) == _lib.MLPS_OK
+    # the FP32 path has no groups; the field is accepted and ignored
+    assert _lib.mlps_check_config(make_config(base, "fp32", mlp_groups=3)) == _lib.MLPS_OK

@@ -158,3 +158,26 @@ def test_batch_cuda_graph_capture_and_replay():
         torch.cuda.synchronize()
         assert torch.equal(rgb_g, out["rgb"])
         assert rel_l2(gw.cpu().numpy(), grads["d_weights"].cpu().numpy()) < 1e-5
+
+
+def test_autotuner_picks_a_candidate_and_changes_no_output_bit():
+    """The tuner times tile 16/8 x samples-per-CTA 4/3/2 on this batch, returns the fastest, caches
+    it, and the tuned configuration renders the same image bit for bit (tile edge and groups
+    change scheduling only)."""
+    from paper_2606_03877_gb300 import _lib
+    _lib.mlps_autotune_clear()
+    cfgs, cat, items, scenes = _small_batch(70)
+    br, out0, d, packed = _batch_forward("bf16", cat, items)
+    ref = out0["rgb"].clone()
+    g = torch.from_numpy(synth.make_grad((br.n_pixels, 3), seed=4)).cuda()
+    tun = br.autotune(d["centers"], d["scales"], d["quats"], packed, d_rgb=g, reps=2)
+    print("autotune", tun)
+    assert len(tun["candidates"]) == 6 and all(ms > 0 for _, _, ms in tun["candidates"])
+    assert (tun["tile"], tun["mlp_groups"]) in [(t, gg) for t, gg, _ in tun["candidates"]]
+    assert tun["best_ms"] == min(ms for _, _, ms in tun["candidates"])
+    out = br.forward(d["centers"], d["scales"], d["quats"], packed)
+    torch.cuda.synchronize()
+    assert br.status() == 0
+    assert torch.equal(out["rgb"], ref)
+    again = br.autotune(d["centers"], d["scales"], d["quats"], packed, d_rgb=g, reps=2)
+    assert again["best_ms"] == 0.0 and (again["tile"], again["mlp_groups"]) == (tun["tile"], tun["mlp_groups"])
