@@ -135,6 +135,24 @@ def _workload(a):
     return wl.replace(**kw) if kw else wl
 
 
+def _traffic(stage, precision, workload):
+    """DRAM bytes per launch of `stage` from the committed ncu summary (profiles/traffic.json),
+    or None when there is none for this precision and workload or the kernel's sources changed
+    since the capture."""
+    import hashlib
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        e = d[stage]
+        if precision not in e["precision"] or workload != e["workload"]:
+            return None
+        for p, h in e["sources"].items():
+            if hashlib.sha256(open(os.path.join(ROOT, p), "rb").read()).hexdigest()[:16] != h:
+                return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def _flush_l2(buf):
     buf.add_(1.0)  # writes 256 MiB (> 129 MB L2) between timed steps
 
@@ -298,6 +316,7 @@ def run_ours(a):
     else:
         roof = {"bound": "hbm", "achieved": None, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                 "frac": None, "traffic": None, "kernel": dom}
+    roof["traffic"] = _traffic(dom, precision, wl.name)
     roof["stage_ms_per_launch"] = {k: round(v, 4) for k, v in stage_ms.items()}
     roof["algorithmic"] = {"hits": n_hits, "samples": samples, "flop_per_sample_fwd": flop_per_sample}
 
