@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   // (wgrad). Each barrier gets its next commit only after its previous phase was waited for, so
   // it is never two phases ahead of its waiters (a parity wait could not tell those apart).
   uint32_t ph_w = 0, ph = 0, ph_g = 0;
+  float geo_acc = 0.f;  // pose-chain output `lane` (< 12) of the current primitive, this warp's share
   const float invS = 1.f / (float)S;
   int loaded = -1;
   int prim = cb < ce ? simt::find_prim(w, cb) : 0;
@@ -403,6 +404,8 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     const int my_cc = step_chunk(cur, g);  // this group's chunk this step and the next
     const int my_nx = step_chunk(nxt, g);
     if (prim != loaded) {
+      if (geo_acc != 0.f) atomicAdd(&sGeo[lane], geo_acc);  // nonzero only on lanes < 12
+      geo_acc = 0.f;
       tc_fence_before();
       __syncthreads();
       if (loaded >= 0) flush(loaded);
@@ -661,42 +664,59 @@ __global__ void __launch_bounds__(kThreadsB, 1)
           gx[2] += XC[row];
           float red[6] = {gx[0], gx[1], gx[2], ck * gx[0], ck * gx[1], ck * gx[2]};
           seg_scan<6>(red, 6, row, S, sScan + g * 4 * kMaxScanVals, hbar);
-          if (valid && k == S - 1) {
-            const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
-            const float span = I.r1 - I.r0, tm = I.r0 + 0.5f * span;
-            const float dA = red[0] * I.dp[0] + red[1] * I.dp[1] + red[2] * I.dp[2];
-            const float dB = red[3] * I.dp[0] + red[4] * I.dp[1] + red[5] * I.dp[2];
-            const float dDelta = DD[iv];
-            // end-point gradients: sum_k gt_k (1 - u_k), sum_k gt_k u_k, plus the width term
-            const float gt0 = 0.5f * dA - dB - dDelta * invS, gt1 = 0.5f * dA + dB + dDelta * invS;
-            const bool clamped = I.r0 != -I.r1;
-            const float gtm = gt1 + (clamped ? 0.f : gt0);
-            const float gh = gt1 - (clamped ? 0.f : gt0);
-            const float aa = I.dp[0] * I.dp[0] + I.dp[1] * I.dp[1] + I.dp[2] * I.dp[2];
-            const float inv_a = 1.f / aa;
-            const float hh = I.r1;
-            const float gh_ah = hh > 0.f ? gh * inv_a / hh : 0.f;
-            float go[3], cd[3], rs[9];
-            for (int u = 0; u < 3; ++u) {
-              go[u] = -gtm * I.dp[u] * inv_a - gh_ah * I.p[u];
-              cd[u] = -(gtm * I.p[u] + gh * hh * I.dp[u]) * inv_a;
-            }
-            for (int e = 0; e < 3; ++e)
-              for (int j = 0; j < 3; ++j) rs[e * 3 + j] = Gp.R[e * 3 + j] * Gp.s[j];  // y = R diag(s) x
-            for (int u = 0; u < 3; ++u) {
-              const float ta = tm * red[u] + span * red[3 + u];  // sum_k t_k gx_k[u]
-              float X[3];  // sum_k gx_k[u] x_k
-              for (int j = 0; j < 3; ++j) X[j] = red[u] * I.p[j] + ta * I.dp[j];
-              for (int e = 0; e < 3; ++e) {
-                const float gy = rs[e * 3] * X[0] + rs[e * 3 + 1] * X[1] + rs[e * 3 + 2] * X[2];
-                const float ym = rs[e * 3] * I.p[0] + rs[e * 3 + 1] * I.p[1] + rs[e * 3 + 2] * I.p[2];
-                atomicAdd(&sGeo[u * 3 + e], gy + go[u] * ym + cd[u] * I.d[e]);
+          // Tail of the chain, per interval ending in this warp: the segment totals are
+          // broadcast from the interval's last row and lane j < 12 computes output j (dL/dM_{u,e}
+          // for j = 3u + e < 9, dL/dmu_{j-9} otherwise), accumulated in a register until the
+          // block's primitive changes (no shared-memory atomics per interval).
+          const int wrow0 = row - lane;
+          for (int r_end = (wrow0 / S + 1) * S - 1; r_end < wrow0 + 32; r_end += S) {
+            const int ive = r_end / S;
+            if (ive >= nint) break;  // warp-uniform
+            float rr[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) rr[j] = __shfl_sync(0xffffffffu, red[j], r_end - wrow0);
+            if (lane < 12) {
+              const IntervalRec& Ie = T[ive];
+              const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
+              const float span = Ie.r1 - Ie.r0, tm = Ie.r0 + 0.5f * span;
+              const float dA = rr[0] * Ie.dp[0] + rr[1] * Ie.dp[1] + rr[2] * Ie.dp[2];
+              const float dB = rr[3] * Ie.dp[0] + rr[4] * Ie.dp[1] + rr[5] * Ie.dp[2];
+              const float dDelta = DD[ive];
+              // end-point gradients: sum_k gt_k (1 - u_k), sum_k gt_k u_k, plus the width term
+              const float gt0 = 0.5f * dA - dB - dDelta * invS, gt1 = 0.5f * dA + dB + dDelta * invS;
+              const bool clamped = Ie.r0 != -Ie.r1;
+              const float gtm = gt1 + (clamped ? 0.f : gt0);
+              const float gh = gt1 - (clamped ? 0.f : gt0);
+              const float aa = Ie.dp[0] * Ie.dp[0] + Ie.dp[1] * Ie.dp[1] + Ie.dp[2] * Ie.dp[2];
+              const float inv_a = 1.f / aa;
+              const float hh = Ie.r1;
+              const float gh_ah = hh > 0.f ? gh * inv_a / hh : 0.f;
+              if (lane < 9) {
+                const int u = lane / 3, e = lane - 3 * u;
+                const float ru = u == 0 ? rr[0] : (u == 1 ? rr[1] : rr[2]);
+                const float rbu = u == 0 ? rr[3] : (u == 1 ? rr[4] : rr[5]);
+                const float pu = Ie.p[u], dpu = Ie.dp[u];
+                const float go_u = -gtm * dpu * inv_a - gh_ah * pu;
+                const float cd_u = -(gtm * pu + gh * hh * dpu) * inv_a;
+                const float ta = tm * ru + span * rbu;  // sum_k t_k gx_k[u]
+                float gy = 0.f, ym = 0.f;               // y = R diag(s) x
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                  const float rsj = Gp.R[e * 3 + j] * Gp.s[j];
+                  gy = fmaf(rsj, ru * Ie.p[j] + ta * Ie.dp[j], gy);
+                  ym = fmaf(rsj, Ie.p[j], ym);
+                }
+                geo_acc += gy + go_u * ym + cd_u * Ie.d[e];
+              } else {
+                const int e = lane - 9;
+                float acc2 = 0.f;
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                  const float go_u = -gtm * Ie.dp[u] * inv_a - gh_ah * Ie.p[u];
+                  acc2 = fmaf(Gp.Mhi[u * 3 + e], rr[u] + go_u, acc2);
+                }
+                geo_acc -= acc2;
               }
-            }
-            for (int e = 0; e < 3; ++e) {
-              float acc2 = 0.f;
-              for (int u = 0; u < 3; ++u) acc2 += Gp.Mhi[u * 3 + e] * (red[u] + go[u]);
-              atomicAdd(&sGeo[9 + e], -acc2);
             }
           }
         }
@@ -712,6 +732,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     mma_commit(bar_end(g));
     mbar_wait_limit(bar_end(g), 0, kWaitNsB);
   }
+  if (geo_acc != 0.f) atomicAdd(&sGeo[lane], geo_acc);
   tc_fence_before();
   __syncthreads();
   if (loaded >= 0) flush(loaded);
