@@ -1,9 +1,8 @@
 // k_mlp_tc_bwd.cu -- BF16 tensor-core (tcgen05) backward of the grouped per-primitive MLP stage.
 //
 // Per chunk of 128 sample rows of one primitive (same chunks as the forward pass), one epilogue
-// group runs 2 * nl phases. A group is 8 warps: warp (q, h) owns TMEM lane quarter q (sample
-// rows 32q .. 32q + 31) and column half h of every 64-wide operand row, so each thread handles
-// one sample row and 32 of its columns. Phases:
+// group (4 warps, thread = sample row; three groups, i.e. three chunks in flight per SM) runs
+// 2 * nl phases:
 //   F_l  (l = 0 .. nl-1): Z_l = H_l W_l^T recomputes the forward; the epilogue writes
 //        H_{l+1} = ReLU(Z_l + b_l) as BF16 into the group's tile T_{l+1};
 //   B_l  (l = nl-1 .. 0): dgrad  G = delta_l W_l          (A = delta_l, K-major; B = the forward
@@ -15,20 +14,21 @@
 //                                sum_rows delta_l); the epilogue forms
 //                                delta_{l-1} = G * [H_l > 0] in place of H_l.
 // The MMAs of a phase are issued by the group's first thread right after a group-local barrier.
-// dgrad and wgrad are committed separately: the epilogue of B_l starts once its dgrad is done and
-// waits for the wgrad (which still reads H_l) only before it overwrites T_l.
+// dgrad and wgrad complete on separate mbarriers: the epilogue of B_l starts once its dgrad is
+// done and waits for the wgrad (which still reads H_l) only before delta_{l-1} overwrites H_l.
 // delta_{nl-1} = dL/dZ comes from the last forward epilogue: the reverse of the interval
-// composite of Eq. 6 with segmented suffix scans (see k_mlp_simt_bwd.cu for the formulas),
-// computed by the column-half-0 warps of the group (one thread per sample row).
+// composite of Eq. 6 with segmented suffix scans (see k_mlp_simt_bwd.cu for the formulas).
 // The input-encoding gradient G_enc = delta_0 W_0 feeds the encoding derivative and the pose
 // chain (closest-point form, no cancellation), reduced per interval and per block.
 // The weight-gradient accumulators live in TMEM for the whole primitive segment of the block and
-// are shared by both groups: they are cleared with tcgen05.st when the block starts a primitive,
+// are shared by the groups: they are cleared with tcgen05.st when the block starts a primitive,
 // every wgrad MMA accumulates into them, and they are flushed to global memory with one
 // atomicAdd per entry when the primitive changes.
-// Tiles per group: T_0 = H_0 (the encoded input), T_l = H_l, E = dL/dZ; delta_{l-1} replaces H_l
-// in T_l. The per-interval sums of the pose chain reduce to two 3-vectors per interval, because
-// the sample positions are affine in the sample index.
+// Tiles per group (nl of them, so that three chunks fit in shared memory): T_0 = H_0 (the
+// encoded input), then dL/dZ once the forward is done, then H_0 again (rebuilt for the last
+// wgrad once dL/dZ has been consumed); T_l = H_l, then delta_{l-1}. The per-interval sums of the
+// pose chain reduce to two 3-vectors per interval, because the sample positions are affine in
+// the sample index.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -49,31 +49,30 @@ using simt::IntervalInfo;
 
 namespace {
 
-constexpr int kNG = 2;                              // epilogue groups (chunks in flight)
-constexpr int kGW = 8;                              // warps per group: 4 lane quarters x 2 column halves
-constexpr int kGThreads = 32 * kGW;
+constexpr int kNG = 3;                              // epilogue groups (chunks in flight)
+constexpr int kGThreads = kEGThreads;               // 4 warps, one per TMEM lane quarter
 constexpr int kThreadsB = kGThreads * kNG;
 constexpr uint32_t kTmemColsB = 512;                // 64 per group + 64 per layer (weight gradients)
 constexpr uint64_t kWaitNsB = 2000000000ull;
 constexpr uint32_t kTile = kM * 128;                // one [128 x 64] BF16 tile
 constexpr uint32_t kOnes = 2048;                    // 16 rows of the MN-major ones atom (one K step)
 
-// Byte offsets in dynamic shared memory; per-group regions are base + g * stride.
+// Byte offsets in dynamic shared memory; per-group regions are base + g * stride. The group's
+// interval tables hold ipc = 128 / S entries.
 struct BwdSmem {
-  uint32_t w, wt, tiles0, tiles_stride, ones, bias, grp0, grp_stride, itab, giv, ddel, gf, xch,
-      scan, geo, pgeo, bars, misc, total;  // itab/giv/ddel/gf/xch: offsets inside one group's block
+  uint32_t w, tiles0, tiles_stride, ones, bias, grp0, grp_stride, itab, giv, ddel, gf, scan, geo,
+      pgeo, bars, misc, total;  // itab/giv/ddel/gf: offsets inside one group's block
 };
 
 MLPS_HD uint32_t al(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F) {
+MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F, int ipc) {
   BwdSmem L;
   uint32_t o = 0;
   L.w = o;
   o = al(o + P.w_bytes, 1024);
-  L.wt = o;
   L.tiles0 = o;
-  L.tiles_stride = al((uint32_t)(P.nl + 1) * kTile, 1024);  // T_0 .. T_{nl-1} and E
+  L.tiles_stride = al((uint32_t)P.nl * kTile, 1024);  // T_0 .. T_{nl-1}
   o += L.tiles_stride * kNG;
   L.ones = o;  // above every group tile: the wgrad descriptors reach it with a positive offset
   o = al(o + kOnes, 1024);
@@ -81,15 +80,13 @@ MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F) {
   o = al(o + 4 * P.bias_floats, 16);
   uint32_t q = 0;
   L.itab = q;
-  q = al(q + (uint32_t)sizeof(IntervalRec) * kM, 16);
+  q = al(q + (uint32_t)sizeof(IntervalRec) * ipc, 16);
   L.giv = q;
-  q = al(q + 16 * kM, 16);
+  q = al(q + 16 * ipc, 16);
   L.ddel = q;
-  q = al(q + 4 * kM, 16);
+  q = al(q + 4 * ipc, 16);
   L.gf = q;
-  q = al(q + 4 * kM * (F > 0 ? F : 1), 16);
-  L.xch = q;  // column half 1 -> half 0 exchange of the encoding-gradient partial sums
-  q = al(q + 4 * kM, 16);
+  q = al(q + 4 * ipc * (F > 0 ? F : 1), 16);
   L.grp0 = o;
   L.grp_stride = q;
   o += q * kNG;
@@ -119,12 +116,11 @@ MLPS_DEV uint64_t sw128_desc_mn(uint32_t saddr, uint32_t lbo) {
   return d;
 }
 
-// Store one column half (32 values, BF16-packed pairs) of one row into a swizzled tile.
-MLPS_DEV void store_half(uint32_t tile, int row, int half, const uint32_t (&pk)[16]) {
+// Store 64 values of one row (BF16-packed pairs) into a swizzled tile.
+MLPS_DEV void store_row64(uint32_t tile, int row, const uint32_t (&pk)[32]) {
 #pragma unroll
-  for (int ch = 0; ch < 4; ++ch)
-    st_shared_v4(tile + sw128_off(row, 4 * half + ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2],
-                 pk[4 * ch + 3]);
+  for (int ch = 0; ch < 8; ++ch)
+    st_shared_v4(tile + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
 }
 
 MLPS_DEV void ld_shared_v4(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
@@ -134,98 +130,51 @@ MLPS_DEV void ld_shared_v4(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c,
                : "memory");
 }
 
-// Column half H (BF16 pairs 16H .. 16H + 15) of the encoded input row (Eq. 5) with compile-time
-// frequency counts; same angle-doubling recurrence and pair order as the forward kernel.
-template <int XL, int DL, int H>
-MLPS_DEV void encode_half(const float (&xl)[3], const float (&d)[3], uint32_t (&pk)[16]) {
-  constexpr int NX = XL > 0 ? 6 * XL : 3;
-  static_assert(NX + (DL > 0 ? 6 * DL : 0) <= 64, "encoded input wider than one 64-column tile");
-#pragma unroll
-  for (int e = 0; e < 16; ++e) pk[e] = 0u;
-  if (XL == 0) {
-    if (H == 0) {
-      pk[0] = pack_bf16(xl[0], xl[1]);
-      pk[1] = pack_bf16(xl[2], 0.f);
-    }
-    return;
-  }
-#pragma unroll
-  for (int u = 0; u < 3; ++u) {
-    if ((u + 1) * XL <= 16 * H || u * XL >= 16 * H + 16) continue;  // no pair of u in this half
-    float sn, cs;
-    __sincosf(3.14159265358979f * xl[u], &sn, &cs);
-#pragma unroll
-    for (int l = 0; l < (XL > 0 ? XL : 1); ++l) {
-      const int idx = u * XL + l - 16 * H;
-      if (idx >= 0 && idx < 16) pk[idx] = pack_bf16(sn, cs);
-      const float s2 = 2.f * sn * cs;
-      cs = fmaf(-2.f * sn, sn, 1.f);
-      sn = s2;
-    }
-  }
-  if (DL > 0) {
-#pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      if (NX / 2 + (u + 1) * DL <= 16 * H || NX / 2 + u * DL >= 16 * H + 16) continue;
-      float sn, cs;
-      __sincosf(3.14159265358979f * d[u], &sn, &cs);
-#pragma unroll
-      for (int l = 0; l < (DL > 0 ? DL : 1); ++l) {
-        const int idx = NX / 2 + u * DL + l - 16 * H;
-        if (idx >= 0 && idx < 16) pk[idx] = pack_bf16(sn, cs);
-        const float s2 = 2.f * sn * cs;
-        cs = fmaf(-2.f * sn, sn, 1.f);
-        sn = s2;
-      }
-    }
-  }
-}
-
-// Build column half `half` of the encoded input row of one sample into tile `A` (zeros for
-// rows past the chunk's intervals).
+// Encoded input row (Eq. 5) of one sample into tile `A` with compile-time frequency counts
+// (zeros for rows past the chunk's intervals).
 template <int XL, int DL>
-MLPS_DEV void build_half(const IntervalRec* T, int nint, int S, int row, int half, uint32_t A) {
+MLPS_DEV void build_row64(const IntervalRec* T, int nint, int S, int row, uint32_t A) {
   const int iv = row / S, k = row - iv * S;
-  uint32_t pk[16];
+  uint32_t pk[32];
   if (iv < nint) {
     const IntervalRec& I = T[iv];
     const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
     float xl[3], d[3];
     for (int u = 0; u < 3; ++u) { xl[u] = fmaf(tr, I.dp[u], I.p[u]); d[u] = I.d[u]; }
-    if (half == 0) encode_half<XL, DL, 0>(xl, d, pk);
-    else encode_half<XL, DL, 1>(xl, d, pk);
+    encode_pairs64<XL, DL>(xl, d, pk);
   } else {
 #pragma unroll
-    for (int e = 0; e < 16; ++e) pk[e] = 0u;
+    for (int e = 0; e < 32; ++e) pk[e] = 0u;
   }
-  store_half(A, row, half, pk);
+  store_row64(A, row, pk);
 }
 
-// Contribution of column half H of dL/dX (32 values in registers) to dL/dx_local through the
-// encoding of Eq. 5: d/dx [sin(2^l pi x), cos(2^l pi x)] = 2^l pi [cos, -sin].
-template <int XL, int H>
-MLPS_DEV void enc_grad_half(const float (&xl)[3], const uint32_t (&v)[32], float (&gx)[3]) {
+// dL/dx_local of one sample from dL/dX (64 values in registers) through the encoding of Eq. 5:
+// d/dx [sin(2^l pi x), cos(2^l pi x)] = 2^l pi [cos, -sin].
+template <int XL>
+MLPS_DEV void enc_grad64(const float (&xl)[3], const uint32_t (&v0)[32], const uint32_t (&v1)[32],
+                         float (&gx)[3]) {
   if (XL == 0) {
-    if (H == 0)
-      for (int u = 0; u < 3; ++u) gx[u] += __uint_as_float(v[u]);
+    for (int u = 0; u < 3; ++u) gx[u] = __uint_as_float(v0[u]);
     return;
   }
 #pragma unroll
   for (int u = 0; u < 3; ++u) {
-    if ((u + 1) * XL <= 16 * H || u * XL >= 16 * H + 16) continue;
     float sn, cs;
     __sincosf(3.14159265358979f * xl[u], &sn, &cs);
-    float wq = 3.14159265358979f;
+    float wq = 3.14159265358979f, acc = 0.f;
 #pragma unroll
     for (int l = 0; l < (XL > 0 ? XL : 1); ++l) {
-      const int col = 2 * (u * XL + l) - 32 * H;
-      if (col >= 0 && col < 32)
-        gx[u] += wq * (__uint_as_float(v[col]) * cs - __uint_as_float(v[col + 1]) * sn);
+      const int c = 2 * (u * XL + l);
+      const float g0 = __uint_as_float(c < 32 ? v0[c] : v1[(c - 32) & 31]);
+      const float g1 = __uint_as_float(c + 1 < 32 ? v0[c + 1] : v1[(c + 1 - 32) & 31]);
+      acc += wq * (g0 * cs - g1 * sn);
       const float s2 = 2.f * sn * cs;
       cs = fmaf(-2.f * sn, sn, 1.f);
       sn = s2;
       wq *= 2.f;
     }
+    gx[u] = acc;
   }
 }
 
@@ -292,8 +241,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   const int F = m.F;
   static_assert(14 <= kMaxScanVals && 3 + NF <= kMaxScanVals, "scan scratch holds kMaxScanVals values per warp");
   static_assert(4 + NF <= 16 && NF % 2 == 0, "the head's outputs lie in the first 16 columns");
-  static_assert(XL <= 8, "the x and y encoding columns lie in column half 0");
-  const BwdSmem L = bwd_layout(P, F);
+  const BwdSmem L = bwd_layout(P, F, w.ipc);
   float* sBias = reinterpret_cast<float*>(gb + L.bias);
   float* sScan = reinterpret_cast<float*>(gb + L.scan);
   float* sGeo = reinterpret_cast<float*>(gb + L.geo);
@@ -305,11 +253,10 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   volatile int* sAbort = reinterpret_cast<volatile int*>(gb + L.misc + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nl = m.nl, S = m.S;
-  const int g = warp / kGW, wg = warp - g * kGW;  // group, warp within the group
-  const int q = wg & 3, half = wg >> 2;           // TMEM lane quarter, column half
+  const int g = warp >> 2, q = warp & 3;          // group, TMEM lane quarter
   const int row = q * 32 + lane;                  // sample row within the chunk
-  const int gbar = 1 + g, hbar = 1 + kNG + g;     // named barriers: whole group, half 0
-  const bool issuer = wg == 0 && lane == 0;       // issues the group's MMAs
+  const int gbar = 1 + g;                         // the group's named barrier
+  const bool issuer = row == 0;                   // issues the group's MMAs
 
   if (threadIdx.x == 0) {
     mbar_init(bar_w, 1);
@@ -342,7 +289,6 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   const int total = w.saved_hdr[2];
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
-  // mbarrier phase parities as bit sets (registers, no local memory)
   // phase parities of bar_w and of this group's bar_done (forward layers and dgrad) and bar_wg
   // (wgrad). Each barrier gets its next commit only after its previous phase was waited for, so
   // it is never two phases ahead of its waiters (a parity wait could not tell those apart).
@@ -383,14 +329,10 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       sGeo[threadIdx.x] = 0.f;
     }
   };
-  // the next chunk's interval records (half 0) and interval gradients (half 1), one step ahead
+  // the next chunk's interval record and interval gradient, one step ahead, in registers
   auto prefetch = [&](const ChunkStep<kNG>& st, int c, RecPrefetch& r) {
     const int f = (c - w.chunk_start[st.prim]) * w.ipc;
-    if (row < min(w.ipc, w.prim_count[st.prim] - f)) {
-      const int slot = w.prim_start[st.prim] + f + row;
-      if (half == 0) rec_prefetch(w, slot, false, r);
-      else r.g = w.hit_grad[slot];
-    }
+    if (row < min(w.ipc, w.prim_count[st.prim] - f)) rec_prefetch(w, w.prim_start[st.prim] + f + row, true, r);
   };
 
   ChunkStep<kNG> cur = chunk_step<kNG>(w, cb, ce, prim);
@@ -449,18 +391,14 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     float4* GI = reinterpret_cast<float4*>(grp + L.giv);
     float* DD = reinterpret_cast<float*>(grp + L.ddel);
     float* GF = reinterpret_cast<float*>(grp + L.gf);
-    float* XC = reinterpret_cast<float*>(grp + L.xch);
     const int first = (my_cc - w.chunk_start[prim]) * w.ipc;
     const int nint = min(w.ipc, w.prim_count[prim] - first);
     named_bar_sync(gbar, kGThreads);  // the group is done with the previous chunk's tables
     if (row < nint) {
-      if (half == 0) {
-        rec_store(pre, T, row);  // prefetched during the previous step
-      } else {
-        GI[row] = pre.g;
-        const size_t slot = (size_t)w.prim_start[prim] + first + row;
-        for (int f = 0; f < F; ++f) GF[row * F + f] = w.hit_gfeat[slot * F + f];
-      }
+      rec_store(pre, T, row);  // prefetched during the previous step
+      GI[row] = pre.g;
+      const size_t slot = (size_t)w.prim_start[prim] + first + row;
+      for (int f = 0; f < F; ++f) GF[row * F + f] = w.hit_gfeat[slot * F + f];
     }
     named_bar_sync(gbar, kGThreads);
     if (nxt.n > 0 && my_nx >= 0) prefetch(nxt, my_nx, pre);  // start loading the next chunk now
@@ -469,10 +407,10 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     const int iv = row / S, k = row - iv * S;
     const bool valid = iv < nint;
     const uint32_t acc = tmem + (uint32_t)(g * 64);  // this group's dgrad / forward accumulator
-    const uint32_t tcol = acc + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 32);
+    const uint32_t trow = acc + ((uint32_t)(q * 32) << 16);
 
-    if (DL >= 0) build_half<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, half, tileaddr(0));
-    else if (half == 0) build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+    if (DL >= 0) build_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
+    else build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
     fence_proxy_async_smem();
     tc_fence_before();
     named_bar_sync(gbar, kGThreads);
@@ -481,8 +419,6 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       if (!*sAbort) issue_fwd_layer(tileaddr(0), sbase + L.w + P.sw_off[0], acc, P.kpad[0], P.npad[0]);
       mma_commit(bar_done(g));
     }
-
-    // ---------------- forward recompute
     // the next completion of the group's MMAs (warp-uniform: tcgen05.ld is a warp instruction)
     auto wait_mma = [&]() -> bool {
       const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), ph, sAbort, kWaitNsB));
@@ -496,27 +432,35 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       tc_fence_after();
       return ok;
     };
+
+    // ---------------- forward recompute
     for (int l = 0; l < nl; ++l) {
       const bool ok = wait_mma();
       const float* bias = sBias + P.bias_off[l];
       if (l < nl - 1) {
-        uint32_t pk[16];
+        uint32_t pk[32];
         if (ok) {
-          uint32_t v[32];
-          tmem_ld32(tcol, v);
+          uint32_t v0[32], v1[32];
+          tmem_ld32(trow, v0);
+          tmem_ld32(trow + 32, v1);
           tmem_wait_ld();
-          const float4* b4 = reinterpret_cast<const float4*>(bias + 32 * half);
+          const float4* b4 = reinterpret_cast<const float4*>(bias);
 #pragma unroll
-          for (int e4 = 0; e4 < 8; ++e4) {
+          for (int e4 = 0; e4 < 16; ++e4) {
             const float4 bq = b4[e4];
-            pk[2 * e4] = pack_bf16_relu(__uint_as_float(v[4 * e4]) + bq.x, __uint_as_float(v[4 * e4 + 1]) + bq.y);
-            pk[2 * e4 + 1] = pack_bf16_relu(__uint_as_float(v[4 * e4 + 2]) + bq.z, __uint_as_float(v[4 * e4 + 3]) + bq.w);
+            const int c0 = 4 * e4;
+            const float x0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]) + bq.x;
+            const float x1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]) + bq.y;
+            const float x2 = __uint_as_float(c0 + 2 < 32 ? v0[c0 + 2] : v1[c0 + 2 - 32]) + bq.z;
+            const float x3 = __uint_as_float(c0 + 3 < 32 ? v0[c0 + 3] : v1[c0 + 3 - 32]) + bq.w;
+            pk[2 * e4] = pack_bf16_relu(x0, x1);
+            pk[2 * e4 + 1] = pack_bf16_relu(x2, x3);
           }
         } else {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) pk[e] = 0u;
+          for (int e = 0; e < 32; ++e) pk[e] = 0u;
         }
-        store_half(tileaddr(l + 1), row, half, pk);
+        store_row64(tileaddr(l + 1), row, pk);
         fence_proxy_async_smem();
         tc_fence_before();
         named_bar_sync(gbar, kGThreads);
@@ -527,113 +471,117 @@ __global__ void __launch_bounds__(kThreadsB, 1)
           mma_commit(bar_done(g));
         }
       } else {
-        // ---------------- heads and reverse of the interval composite -> dL/dZ into E
-        uint32_t pk[16];
+        // ---------------- heads and reverse of the interval composite -> dL/dZ into T_0
+        float z[4 + NF];
+        {
+          uint32_t r16[16];
+          if (ok) {
+            tmem_ld16(trow, r16);
+            tmem_wait_ld();
+          } else {
 #pragma unroll
-        for (int e = 0; e < 16; ++e) pk[e] = 0u;
-        if (half == 0) {
-          float z[4 + NF];
-          {
-            uint32_t r16[16];
-            if (ok) {
-              tmem_ld16(acc + ((uint32_t)(q * 32) << 16), r16);
-              tmem_wait_ld();
-            } else {
-#pragma unroll
-              for (int j = 0; j < 16; ++j) r16[j] = 0u;
-            }
-#pragma unroll
-            for (int j = 0; j < 4 + NF; ++j) z[j] = j < m.nout ? __uint_as_float(r16[j]) + bias[j] : 0.f;
-          }
-          tc_fence_before();
-          const IntervalRec& I = T[valid ? iv : 0];
-          const float dt = valid ? I.dt : 0.f;
-          const float sig = softplus_fast(z[3]);
-          const float ak = valid ? sig * dt : 0.f;
-          float sc1[1] = {ak};
-          seg_scan<1>(sc1, 1, row, S, sScan + g * 4 * kMaxScanVals, hbar);
-          const float Aex = sc1[0] - ak;
-          const float tau = __expf(-Aex), ea = __expf(-ak);
-          const float wk = valid ? tau * (1.f - ea) : 0.f;
-          float cq[3];
-          for (int u = 0; u < 3; ++u) cq[u] = sigmoid_fast(z[u]);
-          float sv[3 + NF];
-#pragma unroll
-          for (int u = 0; u < 3; ++u) sv[u] = wk * cq[u];
-#pragma unroll
-          for (int f = 0; f < NF; ++f) sv[3 + f] = f < F ? wk * z[4 + f] : 0.f;
-          seg_scan_rev<3 + NF>(sv, 3 + F, row, S, sScan + g * 4 * kMaxScanVals, hbar);
-          const float4 gI = valid ? GI[iv] : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float gcs[3] = {gI.x, gI.y, gI.z};
-          float dLda = gI.w;
-#pragma unroll
-          for (int u = 0; u < 3; ++u) dLda += gcs[u] * (tau * ea * cq[u] - (sv[u] - wk * cq[u]));
-          float dz[4 + NF];
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            const float gf = (valid && f < F) ? GF[iv * F + f] : 0.f;
-            const float fk = z[4 + f];
-            dLda += gf * (tau * ea * fk - (sv[3 + f] - wk * fk));
-            dz[4 + f] = wk * gf;
+            for (int j = 0; j < 16; ++j) r16[j] = 0u;
           }
 #pragma unroll
-          for (int u = 0; u < 3; ++u) dz[u] = wk * gcs[u] * cq[u] * (1.f - cq[u]);
-          dz[3] = valid ? dLda * dt * sigmoid_fast(z[3]) : 0.f;
-          float dd[1] = {valid ? sig * dLda : 0.f};
-          seg_scan<1>(dd, 1, row, S, sScan + g * 4 * kMaxScanVals, hbar);
-          if (valid && k == S - 1) DD[iv] = dd[0];
-#pragma unroll
-          for (int e = 0; e < (4 + NF) / 2; ++e)
-            pk[e] = pack_bf16(2 * e < m.nout ? dz[2 * e] : 0.f, 2 * e + 1 < m.nout ? dz[2 * e + 1] : 0.f);
+          for (int j = 0; j < 4 + NF; ++j) z[j] = j < m.nout ? __uint_as_float(r16[j]) + bias[j] : 0.f;
         }
-        store_half(tileaddr(nl), row, half, pk);
+        tc_fence_before();
+        const IntervalRec& I = T[valid ? iv : 0];
+        const float dt = valid ? I.dt : 0.f;
+        const float sig = softplus_fast(z[3]);
+        const float ak = valid ? sig * dt : 0.f;
+        float sc1[1] = {ak};
+        seg_scan<1>(sc1, 1, row, S, sScan + g * 4 * kMaxScanVals, gbar);
+        const float Aex = sc1[0] - ak;
+        const float tau = __expf(-Aex), ea = __expf(-ak);
+        const float wk = valid ? tau * (1.f - ea) : 0.f;
+        float cq[3];
+        for (int u = 0; u < 3; ++u) cq[u] = sigmoid_fast(z[u]);
+        float sv[3 + NF];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) sv[u] = wk * cq[u];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) sv[3 + f] = f < F ? wk * z[4 + f] : 0.f;
+        seg_scan_rev<3 + NF>(sv, 3 + F, row, S, sScan + g * 4 * kMaxScanVals, gbar);
+        const float4 gI = valid ? GI[iv] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float gcs[3] = {gI.x, gI.y, gI.z};
+        float dLda = gI.w;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) dLda += gcs[u] * (tau * ea * cq[u] - (sv[u] - wk * cq[u]));
+        float dz[4 + NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const float gf = (valid && f < F) ? GF[iv * F + f] : 0.f;
+          const float fk = z[4 + f];
+          dLda += gf * (tau * ea * fk - (sv[3 + f] - wk * fk));
+          dz[4 + f] = wk * gf;
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) dz[u] = wk * gcs[u] * cq[u] * (1.f - cq[u]);
+        dz[3] = valid ? dLda * dt * sigmoid_fast(z[3]) : 0.f;
+        float dd[1] = {valid ? sig * dLda : 0.f};
+        seg_scan<1>(dd, 1, row, S, sScan + g * 4 * kMaxScanVals, gbar);
+        if (valid && k == S - 1) DD[iv] = dd[0];
+        uint32_t pk[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) pk[e] = 0u;
+#pragma unroll
+        for (int e = 0; e < (4 + NF) / 2; ++e)
+          pk[e] = pack_bf16(2 * e < m.nout ? dz[2 * e] : 0.f, 2 * e + 1 < m.nout ? dz[2 * e + 1] : 0.f);
+        store_row64(tileaddr(0), row, pk);  // X is dead (F_0 done); it is rebuilt for the last wgrad
         fence_proxy_async_smem();
         tc_fence_before();
         named_bar_sync(gbar, kGThreads);
         if (issuer) {  // B_{nl-1}: dgrad, then wgrad, each with its own completion
           tc_fence_after();
           if (!*sAbort)
-            issue_dgrad(tileaddr(nl), sbase + L.w + P.sw_off[nl - 1], acc, P.kpad[nl - 1], P.npad[nl - 1]);
+            issue_dgrad(tileaddr(0), sbase + L.w + P.sw_off[nl - 1], acc, P.kpad[nl - 1], P.npad[nl - 1]);
           mma_commit(bar_done(g));
           if (!*sAbort)
-            issue_wgrad(tileaddr(nl - 1), tileaddr(nl), tm_dw + (uint32_t)((nl - 1) * 64), sbase + L.ones, P.npad[nl - 1]);
+            issue_wgrad(tileaddr(nl - 1), tileaddr(0), tm_dw + (uint32_t)((nl - 1) * 64), sbase + L.ones, P.npad[nl - 1]);
           mma_commit(bar_wg(g));
         }
       }
     }
-    // ---------------- backward phases B_{nl-1} .. B_0 (delta_l lives in T_{l+1}, dL/dZ in E)
+    // ---------------- backward phases B_{nl-1} .. B_0 (delta_l in T_{l+1}; dL/dZ in T_0)
     for (int l = nl - 1; l >= 0; --l) {
       bool ok = wait_mma();  // dgrad of B_l
-      uint32_t v[32];
+      uint32_t v0[32], v1[32];
       if (ok) {
-        tmem_ld32(tcol, v);
+        tmem_ld32(trow, v0);
+        tmem_ld32(trow + 32, v1);
         tmem_wait_ld();
       } else {
 #pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = 0u;
+        for (int e = 0; e < 32; ++e) { v0[e] = 0u; v1[e] = 0u; }
       }
       tc_fence_before();
       if (l > 0) {
         // delta_{l-1} = G * [H_l > 0], written over H_l in T_l once the wgrad of B_l has read it
         const uint32_t Tl = tileaddr(l);
-        uint32_t pk[16];
+        uint32_t pk[32];
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
+        for (int ch = 0; ch < 8; ++ch) {
           uint32_t hq[4];
-          ld_shared_v4(Tl + sw128_off(row, 4 * half + ch), hq[0], hq[1], hq[2], hq[3]);
+          ld_shared_v4(Tl + sw128_off(row, ch), hq[0], hq[1], hq[2], hq[3]);
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int c0 = ch * 8 + 2 * e;
+            const float g0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]);
+            const float g1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]);
             // BF16 pair: low half = feature c0, high half = feature c0 + 1 (> 0 iff positive, non-zero)
             const uint32_t h0 = hq[e] & 0xFFFFu, h1 = hq[e] >> 16;
             const bool p0 = h0 != 0u && (h0 & 0x8000u) == 0u;
             const bool p1 = h1 != 0u && (h1 & 0x8000u) == 0u;
-            pk[ch * 4 + e] = pack_bf16(valid && p0 ? __uint_as_float(v[c0]) : 0.f,
-                                       valid && p1 ? __uint_as_float(v[c0 + 1]) : 0.f);
+            pk[ch * 4 + e] = pack_bf16(valid && p0 ? g0 : 0.f, valid && p1 ? g1 : 0.f);
           }
         }
         ok = wait_wgrad() && ok;  // wgrad of B_l: T_l is free
-        store_half(Tl, row, half, pk);
+        store_row64(Tl, row, pk);
+        if (l == 1) {  // dL/dZ in T_0 was consumed by B_{nl-1}: rebuild H_0 there for the last wgrad
+          if (DL >= 0) build_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
+          else build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+        }
         fence_proxy_async_smem();
         tc_fence_before();
         named_bar_sync(gbar, kGThreads);
@@ -655,68 +603,62 @@ __global__ void __launch_bounds__(kThreadsB, 1)
           const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
           float xl[3];
           for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
-          if (half == 0) enc_grad_half<XL, 0>(xl, v, gx);
-          else enc_grad_half<XL, 1>(xl, v, gx);
+          enc_grad64<XL>(xl, v0, v1, gx);
         }
-        if (half == 1) XC[row] = gx[2];  // columns 32 .. 63 only reach the z component
-        named_bar_sync(gbar, kGThreads);
-        if (half == 0) {
-          gx[2] += XC[row];
-          float red[6] = {gx[0], gx[1], gx[2], ck * gx[0], ck * gx[1], ck * gx[2]};
-          seg_scan<6>(red, 6, row, S, sScan + g * 4 * kMaxScanVals, hbar);
-          // Tail of the chain, per interval ending in this warp: the segment totals are
-          // broadcast from the interval's last row and lane j < 12 computes output j (dL/dM_{u,e}
-          // for j = 3u + e < 9, dL/dmu_{j-9} otherwise), accumulated in a register until the
-          // block's primitive changes (no shared-memory atomics per interval).
-          const int wrow0 = row - lane;
-          for (int r_end = (wrow0 / S + 1) * S - 1; r_end < wrow0 + 32; r_end += S) {
-            const int ive = r_end / S;
-            if (ive >= nint) break;  // warp-uniform
-            float rr[6];
+        float red[6] = {gx[0], gx[1], gx[2], ck * gx[0], ck * gx[1], ck * gx[2]};
+        seg_scan<6>(red, 6, row, S, sScan + g * 4 * kMaxScanVals, gbar);
+        // Tail of the chain, per interval ending in this warp: the segment totals are
+        // broadcast from the interval's last row and lane j < 12 computes output j (dL/dM_{u,e}
+        // for j = 3u + e < 9, dL/dmu_{j-9} otherwise), accumulated in a register until the
+        // block's primitive changes (no shared-memory atomics per interval).
+        const int wrow0 = row - lane;
+        for (int r_end = (wrow0 / S + 1) * S - 1; r_end < wrow0 + 32; r_end += S) {
+          const int ive = r_end / S;
+          if (ive >= nint) break;  // warp-uniform
+          float rr[6];
 #pragma unroll
-            for (int j = 0; j < 6; ++j) rr[j] = __shfl_sync(0xffffffffu, red[j], r_end - wrow0);
-            if (lane < 12) {
-              const IntervalRec& Ie = T[ive];
-              const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
-              const float span = Ie.r1 - Ie.r0, tm = Ie.r0 + 0.5f * span;
-              const float dA = rr[0] * Ie.dp[0] + rr[1] * Ie.dp[1] + rr[2] * Ie.dp[2];
-              const float dB = rr[3] * Ie.dp[0] + rr[4] * Ie.dp[1] + rr[5] * Ie.dp[2];
-              const float dDelta = DD[ive];
-              // end-point gradients: sum_k gt_k (1 - u_k), sum_k gt_k u_k, plus the width term
-              const float gt0 = 0.5f * dA - dB - dDelta * invS, gt1 = 0.5f * dA + dB + dDelta * invS;
-              const bool clamped = Ie.r0 != -Ie.r1;
-              const float gtm = gt1 + (clamped ? 0.f : gt0);
-              const float gh = gt1 - (clamped ? 0.f : gt0);
-              const float aa = Ie.dp[0] * Ie.dp[0] + Ie.dp[1] * Ie.dp[1] + Ie.dp[2] * Ie.dp[2];
-              const float inv_a = 1.f / aa;
-              const float hh = Ie.r1;
-              const float gh_ah = hh > 0.f ? gh * inv_a / hh : 0.f;
-              if (lane < 9) {
-                const int u = lane / 3, e = lane - 3 * u;
-                const float ru = u == 0 ? rr[0] : (u == 1 ? rr[1] : rr[2]);
-                const float rbu = u == 0 ? rr[3] : (u == 1 ? rr[4] : rr[5]);
-                const float pu = Ie.p[u], dpu = Ie.dp[u];
-                const float go_u = -gtm * dpu * inv_a - gh_ah * pu;
-                const float cd_u = -(gtm * pu + gh * hh * dpu) * inv_a;
-                const float ta = tm * ru + span * rbu;  // sum_k t_k gx_k[u]
-                float gy = 0.f, ym = 0.f;               // y = R diag(s) x
+          for (int j = 0; j < 6; ++j) rr[j] = __shfl_sync(0xffffffffu, red[j], r_end - wrow0);
+          if (lane < 12) {
+            const IntervalRec& Ie = T[ive];
+            const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
+            const float span = Ie.r1 - Ie.r0, tm = Ie.r0 + 0.5f * span;
+            const float dA = rr[0] * Ie.dp[0] + rr[1] * Ie.dp[1] + rr[2] * Ie.dp[2];
+            const float dB = rr[3] * Ie.dp[0] + rr[4] * Ie.dp[1] + rr[5] * Ie.dp[2];
+            const float dDelta = DD[ive];
+            // end-point gradients: sum_k gt_k (1 - u_k), sum_k gt_k u_k, plus the width term
+            const float gt0 = 0.5f * dA - dB - dDelta * invS, gt1 = 0.5f * dA + dB + dDelta * invS;
+            const bool clamped = Ie.r0 != -Ie.r1;
+            const float gtm = gt1 + (clamped ? 0.f : gt0);
+            const float gh = gt1 - (clamped ? 0.f : gt0);
+            const float aa = Ie.dp[0] * Ie.dp[0] + Ie.dp[1] * Ie.dp[1] + Ie.dp[2] * Ie.dp[2];
+            const float inv_a = 1.f / aa;
+            const float hh = Ie.r1;
+            const float gh_ah = hh > 0.f ? gh * inv_a / hh : 0.f;
+            if (lane < 9) {
+              const int u = lane / 3, e = lane - 3 * u;
+              const float ru = u == 0 ? rr[0] : (u == 1 ? rr[1] : rr[2]);
+              const float rbu = u == 0 ? rr[3] : (u == 1 ? rr[4] : rr[5]);
+              const float pu = Ie.p[u], dpu = Ie.dp[u];
+              const float go_u = -gtm * dpu * inv_a - gh_ah * pu;
+              const float cd_u = -(gtm * pu + gh * hh * dpu) * inv_a;
+              const float ta = tm * ru + span * rbu;  // sum_k t_k gx_k[u]
+              float gy = 0.f, ym = 0.f;               // y = R diag(s) x
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                  const float rsj = Gp.R[e * 3 + j] * Gp.s[j];
-                  gy = fmaf(rsj, ru * Ie.p[j] + ta * Ie.dp[j], gy);
-                  ym = fmaf(rsj, Ie.p[j], ym);
-                }
-                geo_acc += gy + go_u * ym + cd_u * Ie.d[e];
-              } else {
-                const int e = lane - 9;
-                float acc2 = 0.f;
-#pragma unroll
-                for (int u = 0; u < 3; ++u) {
-                  const float go_u = -gtm * Ie.dp[u] * inv_a - gh_ah * Ie.p[u];
-                  acc2 = fmaf(Gp.Mhi[u * 3 + e], rr[u] + go_u, acc2);
-                }
-                geo_acc -= acc2;
+              for (int j = 0; j < 3; ++j) {
+                const float rsj = Gp.R[e * 3 + j] * Gp.s[j];
+                gy = fmaf(rsj, ru * Ie.p[j] + ta * Ie.dp[j], gy);
+                ym = fmaf(rsj, Ie.p[j], ym);
               }
+              geo_acc += gy + go_u * ym + cd_u * Ie.d[e];
+            } else {
+              const int e = lane - 9;
+              float acc2 = 0.f;
+#pragma unroll
+              for (int u = 0; u < 3; ++u) {
+                const float go_u = -gtm * Ie.dp[u] * inv_a - gh_ah * Ie.p[u];
+                acc2 = fmaf(Gp.Mhi[u * 3 + e], rr[u] + go_u, acc2);
+              }
+              geo_acc -= acc2;
             }
           }
         }
@@ -755,11 +697,11 @@ bool tc_bwd_supported(const Model& m, const TcPlan& P) {
   if (m.width != 64) return false;
   if (m.xyzL != 0 && m.xyzL != 6) return false;
   if (P.kpad[0] != 64) return false;
-  if (m.nl > 6) return false;
+  if (64 * tc::kNG + 64 * m.nl > (int)tc::kTmemColsB) return false;  // TMEM: groups + weight gradients
   if (m.F > 12) return false;
   for (int l = 0; l < m.nl; ++l)
     if (P.npad[l] > 64) return false;
-  const size_t smem = tc::bwd_layout(P, m.F).total + 1024;
+  const size_t smem = tc::bwd_layout(P, m.F, m.S <= 128 ? 128 / m.S : 1).total + 1024;
   return smem <= 227 * 1024;
 }
 
@@ -789,7 +731,7 @@ cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const size_t smem = tc::bwd_layout(P, a.m.F).total + 1024;
+  const size_t smem = tc::bwd_layout(P, a.m.F, w.ipc).total + 1024;
   // compile-time encodings for the configurations' shapes (xyz L = 6 with dir L = 4, raw xyz
   // without direction); anything else builds rows through the generic writer (DL = -1)
   const bool f = a.m.F > 0;
