@@ -51,7 +51,7 @@ struct TcSmem {
 
 MLPS_HD uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG, bool e4m3) {
+MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG, bool e4m3, int ipc) {
   TcSmem L;
   uint32_t off = 0;
   L.w = off;
@@ -62,7 +62,8 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG, bool e4m3) {
   L.bias = off;  // biases, then (E4M3) the per-output weight scales
   off = align_up(off + 4 * P.bias_floats * (e4m3 ? 2 : 1), 16);
   L.itab0 = off;
-  L.itab_stride = align_up((uint32_t)sizeof(IntervalRec) * kM, 16);
+  // two buffers of ipc interval records: the current chunk's and the next chunk's (in flight)
+  L.itab_stride = align_up(2 * (uint32_t)sizeof(IntervalRec) * ipc, 16);
   off += L.itab_stride * kNEG;
   L.scan = off;
   off = align_up(off + 4 * kNEG * 4 * kMaxScanVals, 16);
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (sbase - raw);
-  const TcSmem L = tc_smem(P, kNEG, F8);
+  const TcSmem L = tc_smem(P, kNEG, F8, w.ipc);
   constexpr float kInMul = 256.f;  // E4M3 encoded input: values in [-1, 1] stored times 256
   const Model& m = a.m;
   float* sBias = reinterpret_cast<float*>(gbase + L.bias);
@@ -131,14 +132,19 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
   int loaded = -1;
   int prim = cb < ce ? simt::find_prim(w, cb) : 0;
 
+  // the next chunk's interval records, copied one step ahead (cp.async) into the group's
+  // pending table buffer `pb`
+  const uint32_t itab_s = sbase + L.itab0 + (uint32_t)g * L.itab_stride;
+  int pb = 0;
+  auto prefetch = [&](const ChunkStep<kNEG>& st, int c) {
+    const int f = (c - w.chunk_start[st.prim]) * w.ipc;
+    if (row < min(w.ipc, w.prim_count[st.prim] - f))
+      rec_copy_async(w, w.prim_start[st.prim] + f + row,
+                     itab_s + (uint32_t)((pb * w.ipc + row) * sizeof(IntervalRec)), 0u);
+  };
   ChunkStep<kNEG> cur = chunk_step<kNEG>(w, cb, ce, prim);
-  RecPrefetch pre;
-  pre.valid = 0;
   const int my_first = step_chunk(cur, g);
-  if (cur.n > 0 && my_first >= 0) {
-    const int f0 = (my_first - w.chunk_start[cur.prim]) * w.ipc;
-    if (row < min(w.ipc, w.prim_count[cur.prim] - f0)) rec_prefetch(w, w.prim_start[cur.prim] + f0 + row, false, pre);
-  }
+  if (cur.n > 0 && my_first >= 0) prefetch(cur, my_first);
   while (cur.c0 < ce) {
     prim = cur.prim;
     const ChunkStep<kNEG> nxt = chunk_step<kNEG>(w, cur.c0 + cur.n, ce, prim);
@@ -176,26 +182,17 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
 
     {
       // ------------------------------------------------------------ epilogue group g
-      if (my_cc < 0 && nxt.n > 0 && my_nx >= 0) {  // idle this step: still prefetch
-        const int f1 = (my_nx - w.chunk_start[nxt.prim]) * w.ipc;
-        if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
-          rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, false, pre);
-      }
+      if (my_cc < 0 && nxt.n > 0 && my_nx >= 0) prefetch(nxt, my_nx);  // idle this step: still prefetch
       if (my_cc >= 0) {
         const int bar_id = 1 + g;
-        IntervalRec* T = reinterpret_cast<IntervalRec*>(gbase + L.itab0 + (uint32_t)g * L.itab_stride);
         const int first = (my_cc - w.chunk_start[prim]) * w.ipc;
         const int nint = min(w.ipc, w.prim_count[prim] - first);
-        // every warp of the group is done with the previous chunk's interval table
-        named_bar_sync(bar_id, kEGThreads);
-        if (row < nint) rec_store(pre, T, row);  // prefetched during the previous step
-        named_bar_sync(bar_id, kEGThreads);
-        pre.valid = 0;
-        if (nxt.n > 0 && my_nx >= 0) {  // start loading the next chunk's records now
-          const int f1 = (my_nx - w.chunk_start[nxt.prim]) * w.ipc;
-          if (row < min(w.ipc, w.prim_count[nxt.prim] - f1))
-            rec_prefetch(w, w.prim_start[nxt.prim] + f1 + row, false, pre);
-        }
+        cp_async_wait_all();                  // this thread's copies of the chunk's records landed
+        named_bar_sync(bar_id, kEGThreads);   // everyone's did; the other buffer is no longer read
+        const IntervalRec* T = reinterpret_cast<const IntervalRec*>(
+            gbase + L.itab0 + (uint32_t)g * L.itab_stride + pb * w.ipc * sizeof(IntervalRec));
+        pb ^= 1;
+        if (nxt.n > 0 && my_nx >= 0) prefetch(nxt, my_nx);  // start loading the next chunk now
         const uint32_t A = sbase + L.a0 + (uint32_t)g * L.a_stride;
         const int iv = row / S, k = row - iv * S;
         const bool valid = iv < nint;
@@ -447,8 +444,9 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     cur = nxt;
   }
 
-  // teardown: make sure none of this group's MMAs still writes TMEM (after an abort a group
-  // may have stopped waiting for them), then free it
+  // teardown: no copy may still be in flight, and none of this group's MMAs may still write
+  // TMEM (after an abort a group may have stopped waiting for them); then TMEM is freed
+  cp_async_wait_all();
   if ((threadIdx.x & (kEGThreads - 1)) == 0) {
     mma_commit(bar_end(g));
     mbar_wait_limit(bar_end(g), 0, kWaitNs);
@@ -568,10 +566,10 @@ int tc_fwd_groups(int width, int F, int groups) {
   return groups == def ? groups : 0;
 }
 
-size_t tc_smem_bytes(const TcPlan& P, int F, int groups) {
+size_t tc_smem_bytes(const TcPlan& P, int F, int groups, int S) {
   const int width = P.npad[0];  // hidden width = N of layer 0
   const int neg = tc_fwd_groups(width, F, groups);
-  return tc::tc_smem(P, neg > 0 ? neg : 4, P.w8_bytes > 0).total + 1024;
+  return tc::tc_smem(P, neg > 0 ? neg : 4, P.w8_bytes > 0, S <= 128 ? 128 / S : 1).total + 1024;
 }
 
 void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
@@ -608,7 +606,7 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const int neg = tc_fwd_groups(a.m.width, a.m.F, a.groups);
   if (neg == 0) return cudaErrorNotSupported;
-  const size_t smem = tc_smem_bytes(P, a.m.F, a.groups);
+  const size_t smem = tc_smem_bytes(P, a.m.F, a.groups, a.m.S);
   if (smem > 227 * 1024) return cudaErrorNotSupported;
   const int xl = a.m.xyzL, dl = a.m.dirL;
   const bool fast64 = xl == 6 && dl == 4 && P.kpad[0] == 64;

@@ -49,9 +49,9 @@ using simt::IntervalInfo;
 
 namespace {
 
-constexpr int kNG = 3;                              // epilogue groups (chunks in flight)
+// Epilogue groups (chunks in flight per SM): 3 where their tiles fit in shared memory and their
+// accumulators next to the weight gradients in TMEM, else 2 (template parameter NG).
 constexpr int kGThreads = kEGThreads;               // 4 warps, one per TMEM lane quarter
-constexpr int kThreadsB = kGThreads * kNG;
 constexpr uint32_t kTmemColsB = 512;                // 64 per group + 64 per layer (weight gradients)
 constexpr uint64_t kWaitNsB = 2000000000ull;
 constexpr uint32_t kTile = kM * 128;                // one [128 x 64] BF16 tile
@@ -66,7 +66,10 @@ struct BwdSmem {
 
 MLPS_HD uint32_t al(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F, int ipc) {
+// Values per warp of the widest segmented scan (pose chain: 6; reverse composite: 3 + NF).
+MLPS_HD int scan_vals(int F) { return F > 0 ? 3 + 12 : 6; }
+
+MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F, int ipc, int kNG) {
   BwdSmem L;
   uint32_t o = 0;
   L.w = o;
@@ -90,8 +93,8 @@ MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F, int ipc) {
   L.grp0 = o;
   L.grp_stride = q;
   o += q * kNG;
-  L.scan = o;
-  o = al(o + 4 * kNG * 4 * kMaxScanVals, 16);
+  L.scan = o;  // per group and warp, the widest scan of the kernel: 6 values, or 3 + 12 with features
+  o = al(o + 4 * kNG * 4 * scan_vals(F), 16);
   L.geo = o;
   o = al(o + 4 * 16, 16);
   L.pgeo = o;  // the current primitive's geometry (staged at every primitive change)
@@ -230,9 +233,10 @@ MLPS_DEV void issue_wgrad(uint32_t Hl, uint32_t Dl, uint32_t dw_l, uint32_t ones
 
 }  // namespace
 
-template <int NF, int XL, int DL>
-__global__ void __launch_bounds__(kThreadsB, 1)
+template <int NF, int XL, int DL, int kNG>
+__global__ void __launch_bounds__(kGThreads * kNG, 1)
     k_mlp_bwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
+  constexpr int kThreadsB = kGThreads * kNG;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -241,7 +245,9 @@ __global__ void __launch_bounds__(kThreadsB, 1)
   const int F = m.F;
   static_assert(14 <= kMaxScanVals && 3 + NF <= kMaxScanVals, "scan scratch holds kMaxScanVals values per warp");
   static_assert(4 + NF <= 16 && NF % 2 == 0, "the head's outputs lie in the first 16 columns");
-  const BwdSmem L = bwd_layout(P, F, w.ipc);
+  constexpr int kScanNV = NF > 0 ? 3 + 12 : 6;  // = scan_vals(F) of the layout
+  static_assert(NF == 0 || NF == 12, "feature heads are instantiated with NF = 12");
+  const BwdSmem L = bwd_layout(P, F, w.ipc, kNG);
   float* sBias = reinterpret_cast<float*>(gb + L.bias);
   float* sScan = reinterpret_cast<float*>(gb + L.scan);
   float* sGeo = reinterpret_cast<float*>(gb + L.geo);
@@ -330,16 +336,17 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     }
   };
   // the next chunk's interval record and interval gradient, one step ahead, in registers
-  auto prefetch = [&](const ChunkStep<kNG>& st, int c, RecPrefetch& r) {
+  uint8_t* grp = gb + L.grp0 + (uint32_t)g * L.grp_stride;
+  RecPrefetch pre;
+  pre.valid = 0;
+  auto prefetch = [&](const ChunkStep<kNG>& st, int c) {
     const int f = (c - w.chunk_start[st.prim]) * w.ipc;
-    if (row < min(w.ipc, w.prim_count[st.prim] - f)) rec_prefetch(w, w.prim_start[st.prim] + f + row, true, r);
+    if (row < min(w.ipc, w.prim_count[st.prim] - f)) rec_prefetch(w, w.prim_start[st.prim] + f + row, true, pre);
   };
 
   ChunkStep<kNG> cur = chunk_step<kNG>(w, cb, ce, prim);
-  RecPrefetch pre;
-  pre.valid = 0;
   const int my_first = step_chunk(cur, g);
-  if (cur.n > 0 && my_first >= 0) prefetch(cur, my_first, pre);
+  if (cur.n > 0 && my_first >= 0) prefetch(cur, my_first);
   while (cur.c0 < ce) {
     prim = cur.prim;
     const ChunkStep<kNG> nxt = chunk_step<kNG>(w, cur.c0 + cur.n, ce, prim);
@@ -381,18 +388,17 @@ __global__ void __launch_bounds__(kThreadsB, 1)
     }
 
     if (my_cc < 0) {
-      if (nxt.n > 0 && my_nx >= 0) prefetch(nxt, my_nx, pre);  // idle this step: still prefetch
+      if (nxt.n > 0 && my_nx >= 0) prefetch(nxt, my_nx);  // idle this step: still prefetch
       cur = nxt;
       continue;
     }
     // ============================================================ epilogue group g
-    uint8_t* grp = gb + L.grp0 + (uint32_t)g * L.grp_stride;
+    const int first = (my_cc - w.chunk_start[prim]) * w.ipc;
+    const int nint = min(w.ipc, w.prim_count[prim] - first);
     IntervalRec* T = reinterpret_cast<IntervalRec*>(grp + L.itab);
     float4* GI = reinterpret_cast<float4*>(grp + L.giv);
     float* DD = reinterpret_cast<float*>(grp + L.ddel);
     float* GF = reinterpret_cast<float*>(grp + L.gf);
-    const int first = (my_cc - w.chunk_start[prim]) * w.ipc;
-    const int nint = min(w.ipc, w.prim_count[prim] - first);
     named_bar_sync(gbar, kGThreads);  // the group is done with the previous chunk's tables
     if (row < nint) {
       rec_store(pre, T, row);  // prefetched during the previous step
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
       for (int f = 0; f < F; ++f) GF[row * F + f] = w.hit_gfeat[slot * F + f];
     }
     named_bar_sync(gbar, kGThreads);
-    if (nxt.n > 0 && my_nx >= 0) prefetch(nxt, my_nx, pre);  // start loading the next chunk now
+    if (nxt.n > 0 && my_nx >= 0) prefetch(nxt, my_nx);  // start loading the next chunk now
     const uint32_t tiles = sbase + L.tiles0 + (uint32_t)g * L.tiles_stride;
 #define tileaddr(I) (tiles + (uint32_t)(I) * kTile)
     const int iv = row / S, k = row - iv * S;
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
         const float sig = softplus_fast(z[3]);
         const float ak = valid ? sig * dt : 0.f;
         float sc1[1] = {ak};
-        seg_scan<1>(sc1, 1, row, S, sScan + g * 4 * kMaxScanVals, gbar);
+        seg_scan<1>(sc1, 1, row, S, sScan + g * 4 * kScanNV, gbar);
         const float Aex = sc1[0] - ak;
         const float tau = __expf(-Aex), ea = __expf(-ak);
         const float wk = valid ? tau * (1.f - ea) : 0.f;
@@ -502,7 +508,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
         for (int u = 0; u < 3; ++u) sv[u] = wk * cq[u];
 #pragma unroll
         for (int f = 0; f < NF; ++f) sv[3 + f] = f < F ? wk * z[4 + f] : 0.f;
-        seg_scan_rev<3 + NF>(sv, 3 + F, row, S, sScan + g * 4 * kMaxScanVals, gbar);
+        seg_scan_rev<3 + NF>(sv, 3 + F, row, S, sScan + g * 4 * kScanNV, gbar);
         const float4 gI = valid ? GI[iv] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float gcs[3] = {gI.x, gI.y, gI.z};
         float dLda = gI.w;
@@ -520,7 +526,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
         for (int u = 0; u < 3; ++u) dz[u] = wk * gcs[u] * cq[u] * (1.f - cq[u]);
         dz[3] = valid ? dLda * dt * sigmoid_fast(z[3]) : 0.f;
         float dd[1] = {valid ? sig * dLda : 0.f};
-        seg_scan<1>(dd, 1, row, S, sScan + g * 4 * kMaxScanVals, gbar);
+        seg_scan<1>(dd, 1, row, S, sScan + g * 4 * kScanNV, gbar);
         if (valid && k == S - 1) DD[iv] = dd[0];
         uint32_t pk[32];
 #pragma unroll
@@ -606,7 +612,7 @@ __global__ void __launch_bounds__(kThreadsB, 1)
           enc_grad64<XL>(xl, v0, v1, gx);
         }
         float red[6] = {gx[0], gx[1], gx[2], ck * gx[0], ck * gx[1], ck * gx[2]};
-        seg_scan<6>(red, 6, row, S, sScan + g * 4 * kMaxScanVals, gbar);
+        seg_scan<6>(red, 6, row, S, sScan + g * 4 * kScanNV, gbar);
         // Tail of the chain, per interval ending in this warp: the segment totals are
         // broadcast from the interval's last row and lane j < 12 computes output j (dL/dM_{u,e}
         // for j = 3u + e < 9, dL/dmu_{j-9} otherwise), accumulated in a register until the
@@ -693,16 +699,25 @@ __global__ void __launch_bounds__(kThreadsB, 1)
 }  // namespace tc
 
 // ------------------------------------------------------------------------------------------
+// Groups of the backward kernel for this model: 3 when their tiles fit in shared memory and
+// their accumulators in TMEM, else 2; 0 when not even 2 fit.
+static int bwd_groups(const Model& m, const TcPlan& P) {
+  const int ipc = m.S <= 128 ? 128 / m.S : 1;
+  for (int ng = 3; ng >= 2; --ng) {
+    if (64 * ng + 64 * m.nl > (int)tc::kTmemColsB) continue;  // TMEM: groups + weight gradients
+    if (tc::bwd_layout(P, m.F, ipc, ng).total + 1024 <= 227 * 1024) return ng;
+  }
+  return 0;
+}
+
 bool tc_bwd_supported(const Model& m, const TcPlan& P) {
   if (m.width != 64) return false;
   if (m.xyzL != 0 && m.xyzL != 6) return false;
   if (P.kpad[0] != 64) return false;
-  if (64 * tc::kNG + 64 * m.nl > (int)tc::kTmemColsB) return false;  // TMEM: groups + weight gradients
   if (m.F > 12) return false;
   for (int l = 0; l < m.nl; ++l)
     if (P.npad[l] > 64) return false;
-  const size_t smem = tc::bwd_layout(P, m.F, m.S <= 128 ? 128 / m.S : 1).total + 1024;
-  return smem <= 227 * 1024;
+  return bwd_groups(m, P) > 0;
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode_b() {
@@ -731,19 +746,22 @@ cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const size_t smem = tc::bwd_layout(P, a.m.F, w.ipc).total + 1024;
+  const int ng = bwd_groups(a.m, P);
+  const size_t smem = tc::bwd_layout(P, a.m.F, w.ipc, ng).total + 1024;
   // compile-time encodings for the configurations' shapes (xyz L = 6 with dir L = 4, raw xyz
   // without direction); anything else builds rows through the generic writer (DL = -1)
   const bool f = a.m.F > 0;
   const int xl = a.m.xyzL, dl = a.m.dirL;
-  decltype(&tc::k_mlp_bwd_tc<0, 6, 4>) kern;
-  if (xl == 6 && dl == 4) kern = f ? tc::k_mlp_bwd_tc<12, 6, 4> : tc::k_mlp_bwd_tc<0, 6, 4>;
-  else if (xl == 0 && dl == 0) kern = f ? tc::k_mlp_bwd_tc<12, 0, 0> : tc::k_mlp_bwd_tc<0, 0, 0>;
-  else if (xl == 6) kern = f ? tc::k_mlp_bwd_tc<12, 6, -1> : tc::k_mlp_bwd_tc<0, 6, -1>;
-  else kern = f ? tc::k_mlp_bwd_tc<12, 0, -1> : tc::k_mlp_bwd_tc<0, 0, -1>;
+#define MLPS_BWD_KERN(NG)                                                                        \
+  ((xl == 6 && dl == 4)   ? (f ? tc::k_mlp_bwd_tc<12, 6, 4, NG> : tc::k_mlp_bwd_tc<0, 6, 4, NG>)   \
+   : (xl == 0 && dl == 0) ? (f ? tc::k_mlp_bwd_tc<12, 0, 0, NG> : tc::k_mlp_bwd_tc<0, 0, 0, NG>)   \
+   : (xl == 6)            ? (f ? tc::k_mlp_bwd_tc<12, 6, -1, NG> : tc::k_mlp_bwd_tc<0, 6, -1, NG>) \
+                          : (f ? tc::k_mlp_bwd_tc<12, 0, -1, NG> : tc::k_mlp_bwd_tc<0, 0, -1, NG>))
+  decltype(&tc::k_mlp_bwd_tc<0, 6, 4, 3>) kern = ng == 3 ? MLPS_BWD_KERN(3) : MLPS_BWD_KERN(2);
+#undef MLPS_BWD_KERN
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<n_sm, tc::kThreadsB, smem, st>>>(w, a, P, tmap);
+  kern<<<n_sm, tc::kGThreads * ng, smem, st>>>(w, a, P, tmap);
   return cudaGetLastError();
 }
 

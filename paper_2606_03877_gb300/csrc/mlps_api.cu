@@ -594,7 +594,7 @@ mlps_status mlps_check_config(const mlps_config* cfg) {
     const Model m = make_model(cfg);
     if (!tc_plan(m, &P, &stride, cfg->precision == MLPS_FP8_E4M3)) return MLPS_ERR_UNSUPPORTED;
     if (tc_fwd_groups(m.width, m.F, cfg->mlp_groups) == 0) return MLPS_ERR_UNSUPPORTED;
-    if (tc_smem_bytes(P, cfg->feat_dim, cfg->mlp_groups) > 227 * 1024) return MLPS_ERR_UNSUPPORTED;
+    if (tc_smem_bytes(P, cfg->feat_dim, cfg->mlp_groups, cfg->samples) > 227 * 1024) return MLPS_ERR_UNSUPPORTED;
     return MLPS_OK;
   }
   if (cfg->precision != MLPS_FP32) return MLPS_ERR_UNSUPPORTED;

@@ -240,6 +240,24 @@ MLPS_DEV void rec_prefetch(const Work& w, int slot, bool want_grad, RecPrefetch&
   if (want_grad) r.g = w.hit_grad[slot];
 }
 
+// Asynchronous global -> shared copies (cp.async, 16 bytes each): the next chunk's interval
+// records travel to shared memory while the current chunk is processed, holding no registers.
+MLPS_DEV void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+MLPS_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+MLPS_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Start copying interval record `slot` (64 bytes) to shared address `dst_rec` and, when
+// `dst_grad` is nonzero, its interval gradient (16 bytes) to `dst_grad`.
+MLPS_DEV void rec_copy_async(const Work& w, int slot, uint32_t dst_rec, uint32_t dst_grad) {
+  const char* src = reinterpret_cast<const char*>(w.rec + slot);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) cp_async16(dst_rec + 16u * i, src + 16 * i);
+  if (dst_grad) cp_async16(dst_grad, w.hit_grad + slot);
+  cp_async_commit();
+}
+
 // Encoded input row (Eq. 5) with the frequency counts known at compile time: all values are
 // produced in registers, packed to BF16 pairs and written with 16-byte stores. XL = 0 means the
 // raw local position; DL = 0 means no direction input. Columns past the encoding are zero.
