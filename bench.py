@@ -64,6 +64,33 @@ def _dist():
     return ws, rank, local
 
 
+def rank_view_seed(rank: int, n_views: int) -> int:
+    """First camera seed of a rank: under weak scaling every rank renders its own n_views views
+    (seeds rank * n_views ..), so the ranks' views are disjoint and their union is the job."""
+    return rank * n_views
+
+
+def rank_scene_seed(rank: int, n_scenes: int = 32) -> int:
+    """First scene seed of a rank's batch in the batching workload (disjoint per rank)."""
+    return n_scenes * rank
+
+
+def max_over_ranks(ms: float, ws: int, device=None) -> float:
+    """The job's time: the slowest rank's (MAX all-reduce; no-op for one rank)."""
+    if ws <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rays_per_s(rays_per_rank: int, ws: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: the rays of all ranks and steps over the max-over-ranks time."""
+    return rays_per_rank * ws * steps / (total_ms / 1e3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -171,7 +198,7 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     wl = _workload(a)
     scene = synth.make_scene(wl, 0)
-    cams = synth.make_cameras(wl, first_view_seed=rank * wl.n_views)
+    cams = synth.make_cameras(wl, first_view_seed=rank_view_seed(rank, wl.n_views))
     d = {k: torch.from_numpy(v).to(dev) for k, v in scene.items()}
     g_rgb = torch.from_numpy(synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100 + rank,
                                              scale=0.01)).to(dev)
@@ -261,15 +288,13 @@ def run_ours(a):
             prof = _lib.mlps_profiler_read(reset=True)
         clocks = clk.stop() if clk else None
         ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-        total = torch.tensor([sum(ms)], device=dev, dtype=torch.float64)
         if ws > 1:
             dist.barrier()
-            dist.all_reduce(total, op=dist.ReduceOp.MAX)
-        return float(total.item()), ms, launches, prof, clocks
+        return max_over_ranks(sum(ms), ws, dev), ms, launches, prof, clocks
 
     total_ms, ms, launches, prof, clocks = timed(r, do_bwd, a.steps, a.warmup, sample_clocks=True, profile=True)
     n_hits = r.hit_count()
-    value = n_rays * ws * a.steps / (total_ms / 1e3)
+    value = job_rays_per_s(n_rays, ws, a.steps, total_ms)
     results = {f"{precision}_{'fwd_bwd' if do_bwd else 'fwd'}": value}
 
     if a.compare:
@@ -503,7 +528,7 @@ def run_batch(a):
     precision = "bf16" if a.precision == "auto" else a.precision
     do_bwd = a.pass_ == "fwdbwd"
     cfgs = synth.batch_configs(seed=0)
-    cat, items, _ = synth.make_batch(cfgs, first_seed=32 * rank)
+    cat, items, _ = synth.make_batch(cfgs, first_seed=rank_scene_seed(rank))
     K = cat["centers"].shape[0]
     shape = synth.CONFIGS["prec"]
     br = BatchRenderer(shape, items, K, precision=precision, device=str(dev))
@@ -562,14 +587,10 @@ def run_batch(a):
     if ws > 1:
         dist.barrier()
     clocks = clk.stop()
-    total_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev), ws, dev)
     if br.status() != 0:
         raise RuntimeError("device status after the timed replays")
-    value = br.n_pixels * ws * a.steps / (total_ms / 1e3)
+    value = job_rays_per_s(br.n_pixels, ws, a.steps, total_ms)
     n_hits = _lib.mlps_saved_hit_count(br.saved)
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1] > 0}
     peaks, peak_src = _peaks()

@@ -565,16 +565,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
   if (loaded >= 0) flush(loaded);
 }
 
+bool simt_bwd_supported(const MlpArgs& a) {
+  const Model& m = a.m;
+  if (m.S > kRB || (m.width != 32 && m.width != 64)) return false;
+  BwdPlan P = make_plan(a);
+  if (P.tiles > kMaxTiles * kThreads || P.bias_base[m.nl] > kMaxBias * kThreads) return false;
+  for (int l = 0; l < m.nl; ++l)
+    if (m.dout[l] % 4 != 0 && l < m.nl - 1) return false;
+  return bwd_smem(a, P) <= 227 * 1024;
+}
+
 cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st) {
   const Model& m = a.m;
-  if (m.S > kRB || m.width > 64) return cudaErrorNotSupported;
+  if (!simt_bwd_supported(a)) return cudaErrorNotSupported;
   BwdPlan P = make_plan(a);
-  if (P.tiles > kMaxTiles * kThreads || P.bias_base[m.nl] > kMaxBias * kThreads)
-    return cudaErrorNotSupported;
-  for (int l = 0; l < m.nl; ++l)
-    if (m.dout[l] % 4 != 0 && l < m.nl - 1) return cudaErrorNotSupported;
   const size_t smem = bwd_smem(a, P);
-  if (smem > 227 * 1024) return cudaErrorNotSupported;
   switch (m.width) {
 #define MLPS_CASE(WID)                                                                      \
   case WID: {                                                                               \

@@ -498,7 +498,7 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
   if (tc) {
     if (!tc_plan(m, &P, &tc_stride, cfg->precision == MLPS_FP8_E4M3) || !tc_bwd_supported(m, P))
       return MLPS_ERR_UNSUPPORTED;
-  } else if (cfg->precision != MLPS_FP32) {
+  } else if (cfg->precision != MLPS_FP32 || !simt_bwd_supported(a)) {
     return MLPS_ERR_UNSUPPORTED;
   }
   const int n_sm = num_sms();

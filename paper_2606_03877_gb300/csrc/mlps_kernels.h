@@ -64,6 +64,7 @@ void launch_export_tiles(const Work& w, int* count, int* list, cudaStream_t st);
 // k_mlp_simt.cu (FP32 path)
 size_t mlp_simt_smem(const MlpArgs& a, bool backward);
 cudaError_t launch_mlp_fwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st);
+bool simt_bwd_supported(const MlpArgs& a);
 cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st);
 
 // k_mlp_tc.cu (BF16 tensor-core path)
