@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--width", type=int, default=0, help="override (profiling captures only)")
     ap.add_argument("--height", type=int, default=0, help="override (profiling captures only)")
     ap.add_argument("--views", type=int, default=0, help="override (profiling captures only)")
+    ap.add_argument("--mlp-groups", type=int, default=0,
+                    help="forward tensor-core MLP samples per CTA in 128-row chunks (0 = library default)")
     ap.add_argument("--compare", action="store_true",
                     help="also time the FP32 path and forward-only passes (extra lines in 'results')")
     return ap.parse_args()
@@ -206,7 +208,8 @@ def run_ours(a):
     flush = torch.zeros(64 * 1024 * 1024, device=dev)
 
     def make(precision):
-        r = Renderer(wl, precision=precision, device=str(dev))
+        kw = {"mlp_groups": a.mlp_groups} if a.mlp_groups and precision != "fp32" else {}
+        r = Renderer(wl, precision=precision, device=str(dev), **kw)
         return r
 
     def try_pass(r, want_bwd):

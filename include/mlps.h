@@ -83,7 +83,7 @@ typedef struct {
   float t_eps;                  /* early termination: stop compositing once T < t_eps (0: never) */
   int32_t tile;                 /* screen tile edge in pixels for binning: 16 (default) or 8 */
   int32_t mlp_groups;           /* chunks of 128 sample rows in flight per CTA in the forward
-                                   tensor-core MLP (2..4 at width 64, 3 with a feature head,
+                                   tensor-core MLP (2..6 at width 64, 3 with a feature head,
                                    2 at width 128); 0 = library default. mlps_autotune_batch
                                    picks it together with `tile`. */
   int32_t reserved[4];          /* must be zero */
@@ -238,7 +238,7 @@ mlps_status mlps_render_batch_backward(const mlps_config* cfg, const mlps_scene*
                                        size_t scratch_bytes, void* stream);
 
 /* Autotuner (no counterpart in the paper): picks `tile` (16 or 8) and `mlp_groups` (samples per
- * CTA of the forward tensor-core MLP: 2, 3 or 4 chunks of 128 rows, width-64 models without a
+ * CTA of the forward tensor-core MLP: 2 to 6 chunks of 128 rows, width-64 models without a
  * feature head; other shapes keep their default) for this batch by running every candidate
  * `reps` times (after one warm-up run) on the caller's arguments, as mlps_render_batch_forward
  * (+ mlps_render_batch_backward with dL/drgb = d_rgb when do_backward), timed with CUDA events
@@ -246,7 +246,7 @@ mlps_status mlps_render_batch_backward(const mlps_config* cfg, const mlps_scene*
  * Writes *tuned = *cfg with the fastest tile and mlp_groups and *best_ms (mean ms per run;
  * 0 when the decision came from the cache). Decisions are cached per batch shape (model, S,
  * precision, max hits, each item's primitive count and resolution, do_backward) for the life of
- * the process. Optional outputs (host, capacity 8, may be NULL): the candidates' tile, groups
+ * the process. Optional outputs (host, capacity 16, may be NULL): the candidates' tile, groups
  * and ms (negative = did not run). Synchronises `stream`; do not call it during stream capture.
  * The output and gradient buffers are overwritten. Returns MLPS_ERR_UNSUPPORTED if no
  * candidate ran. */

@@ -274,9 +274,9 @@ def mlps_autotune_batch(cfg, scene: MlpsScene, items, n_items, do_backward, d_rg
     tuned = MlpsConfig()
     best = ctypes.c_float()
     nc = ctypes.c_int32()
-    ct = (ctypes.c_int32 * 8)()
-    cg = (ctypes.c_int32 * 8)()
-    cm = (ctypes.c_float * 8)()
+    ct = (ctypes.c_int32 * 16)()
+    cg = (ctypes.c_int32 * 16)()
+    cm = (ctypes.c_float * 16)()
     _check("mlps_autotune_batch", load().mlps_autotune_batch(
         ctypes.byref(cfg), ctypes.byref(scene), items, int(n_items), int(do_backward), _ptr(d_rgb), _ptr(rgb),
         _ptr(trans), _ptr(feat), _ptr(saved), int(saved_bytes), _ptr(scratch), int(scratch_bytes),

@@ -41,7 +41,7 @@ namespace tc {
 using simt::IntervalInfo;
 
 constexpr int threads_tc(int neg) { return kEGThreads * neg; }
-constexpr uint32_t kTmemCols = 512;             // 128 per group (at most four groups)
+constexpr uint32_t kTmemCols = 512;             // WIDTH columns per group
 constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s
 // Byte offsets in dynamic shared memory; per-group regions are base + g * stride (plain
 // arithmetic, so that nothing is indexed at run time).
@@ -83,7 +83,7 @@ template <int WIDTH, int XL, int DL, int NF, int kNEG, bool F8>
 __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     k_mlp_fwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
   constexpr int kThreadsTC = kEGThreads * kNEG;
-  static_assert(kNEG >= 1 && kNEG <= 4 && kNEG * WIDTH <= 4 * 128, "TMEM holds 512 columns");
+  static_assert(kNEG >= 1 && kNEG <= 6 && kNEG * WIDTH <= 512, "TMEM holds 512 columns");
   static_assert(4 + NF <= kMaxScanVals, "scan scratch holds kMaxScanVals values per warp");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
         fence_proxy_async_smem();
         tc_fence_before();
         named_bar_sync(bar_id, kEGThreads);  // the whole A tile is written
-        const uint32_t dacc = tmem + (uint32_t)(g * 128);
+        const uint32_t dacc = tmem + (uint32_t)(g * WIDTH);
         if (row == 0) {  // this group issues its own MMAs
           tc_fence_after();
           if (!*sAbort) {
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
           }
           mma_commit(bar_done(g));
         }
-        const uint32_t trow = tmem + (uint32_t)(g * 128) + ((uint32_t)(q * 32) << 16);
+        const uint32_t trow = tmem + (uint32_t)(g * WIDTH) + ((uint32_t)(q * 32) << 16);
         for (int l = 0; l < nl; ++l) {
           // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
           const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), (ph_done >> g) & 1u, sAbort, kWaitNs));
@@ -352,27 +352,24 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
               srow = sn;
               }
             } else if (ok) {
+              // 32 columns at a time: fewer live registers, so more groups fit on the SM
 #pragma unroll
-              for (int half = 0; half < WIDTH / 64; ++half) {
-                uint32_t v0[32], v1[32];
-                tmem_ld32(trow + half * 64, v0);
-                tmem_ld32(trow + half * 64 + 32, v1);
+              for (int h32 = 0; h32 < WIDTH / 32; ++h32) {
+                uint32_t v[32];
+                tmem_ld32(trow + h32 * 32, v);
                 tmem_wait_ld();
-                const uint32_t At = A + (uint32_t)half * (kM * 128);
-                const float4* b4 = reinterpret_cast<const float4*>(bias + half * 64);
+                const uint32_t At = A + (uint32_t)(h32 >> 1) * (kM * 128);
+                const float4* b4 = reinterpret_cast<const float4*>(bias + h32 * 32);
 #pragma unroll
-                for (int ch = 0; ch < 8; ++ch) {
-                  const float4 ba = b4[2 * ch], bb = b4[2 * ch + 1];
+                for (int c4 = 0; c4 < 4; ++c4) {
+                  const float4 ba = b4[2 * c4], bb = b4[2 * c4 + 1];
                   const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
                   uint32_t pk[4];
 #pragma unroll
-                  for (int e = 0; e < 4; ++e) {
-                    const int c0 = ch * 8 + 2 * e;
-                    const float x0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]) + bv[2 * e];
-                    const float x1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]) + bv[2 * e + 1];
-                    pk[e] = pack_bf16_relu(x0, x1);
-                  }
-                  st_shared_v4(At + sw128_off(row, ch), pk[0], pk[1], pk[2], pk[3]);
+                  for (int e = 0; e < 4; ++e)
+                    pk[e] = pack_bf16_relu(__uint_as_float(v[8 * c4 + 2 * e]) + bv[2 * e],
+                                           __uint_as_float(v[8 * c4 + 2 * e + 1]) + bv[2 * e + 1]);
+                  st_shared_v4(At + sw128_off(row, 4 * (h32 & 1) + c4), pk[0], pk[1], pk[2], pk[3]);
                 }
               }
             }
@@ -558,18 +555,20 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3) {
 // Epilogue groups of the forward kernel (chunks of 128 sample rows in flight per CTA). Default:
 // registers cap the feature-head variants at three groups (the head keeps 4 + 32 values per
 // thread), TMEM caps width 128 at four and shared memory (a 32 KB operand tile per group) at
-// two. Width 64 without a feature head also runs with 2 or 3 (the autotuner's choices).
-int tc_fwd_groups(int width, int F, int groups) {
-  const int def = width == 64 ? (F > 0 ? 3 : 4) : 2;
+// two. Width 64 without a feature head runs with 2 to 6 (the autotuner's choices).
+int tc_fwd_groups(int width, int F, int groups, bool e4m3) {
+  // BF16 at width 64 runs five groups in 96 registers; E4M3 keeps each row's 64 values live for
+  // its scale, so it stays at four
+  const int def = width == 64 ? (F > 0 ? 3 : (e4m3 ? 4 : 5)) : 2;
   if (groups == 0) return def;
-  if (width == 64 && F == 0) return (groups >= 2 && groups <= 4) ? groups : 0;
+  if (width == 64 && F == 0) return (groups >= 2 && groups <= 6) ? groups : 0;
   return groups == def ? groups : 0;
 }
 
 size_t tc_smem_bytes(const TcPlan& P, int F, int groups, int S) {
   const int width = P.npad[0];  // hidden width = N of layer 0
-  const int neg = tc_fwd_groups(width, F, groups);
-  return tc::tc_smem(P, neg > 0 ? neg : 4, P.w8_bytes > 0, S <= 128 ? 128 / S : 1).total + 1024;
+  const int neg = tc_fwd_groups(width, F, groups, P.w8_bytes > 0);
+  return tc::tc_smem(P, neg > 0 ? neg : 5, P.w8_bytes > 0, S <= 128 ? 128 / S : 1).total + 1024;
 }
 
 void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
@@ -604,7 +603,7 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const int neg = tc_fwd_groups(a.m.width, a.m.F, a.groups);
+  const int neg = tc_fwd_groups(a.m.width, a.m.F, a.groups, P.w8_bytes > 0);
   if (neg == 0) return cudaErrorNotSupported;
   const size_t smem = tc_smem_bytes(P, a.m.F, a.groups, a.m.S);
   if (smem > 227 * 1024) return cudaErrorNotSupported;
@@ -615,7 +614,8 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
   const bool feat = a.m.F > 0;
 #define MLPS_BY_GROUPS(W, XL, DL, F8) \
   (neg == 2 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 2, F8> : neg == 3 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 3, F8> \
-            : tc::k_mlp_fwd_tc<W, XL, DL, 0, 4, F8>)
+            : neg == 4 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 4, F8> : neg == 5 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 5, F8> \
+            : tc::k_mlp_fwd_tc<W, XL, DL, 0, 6, F8>)
   if (P.w8_bytes > 0) {  // E4M3
     if (a.m.width == 64) {
       if (!feat) kern = fast64 ? MLPS_BY_GROUPS(64, 6, 4, true) : MLPS_BY_GROUPS(64, -1, -1, true);

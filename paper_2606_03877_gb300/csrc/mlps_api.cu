@@ -88,7 +88,7 @@ mlps_status check_cfg(const mlps_config* c) {
   if (!finite_f(c->t_eps) || c->t_eps < 0.f || c->t_eps >= 1.f) return MLPS_ERR_INVALID_ARGUMENT;
   for (int i = 0; i < 4; ++i)
     if (c->reserved[i] != 0) return MLPS_ERR_INVALID_ARGUMENT;
-  if (c->mlp_groups != 0 && (c->mlp_groups < 2 || c->mlp_groups > 4)) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->mlp_groups != 0 && (c->mlp_groups < 2 || c->mlp_groups > 6)) return MLPS_ERR_INVALID_ARGUMENT;
   if (c->hidden_width != 32 && c->hidden_width != 64 && c->hidden_width != 128)
     return MLPS_ERR_UNSUPPORTED;
   if (c->tile != 16 && c->tile != 8) return MLPS_ERR_UNSUPPORTED;
@@ -593,7 +593,8 @@ mlps_status mlps_check_config(const mlps_config* cfg) {
     long long stride;
     const Model m = make_model(cfg);
     if (!tc_plan(m, &P, &stride, cfg->precision == MLPS_FP8_E4M3)) return MLPS_ERR_UNSUPPORTED;
-    if (tc_fwd_groups(m.width, m.F, cfg->mlp_groups) == 0) return MLPS_ERR_UNSUPPORTED;
+    if (tc_fwd_groups(m.width, m.F, cfg->mlp_groups, cfg->precision == MLPS_FP8_E4M3) == 0)
+      return MLPS_ERR_UNSUPPORTED;
     if (tc_smem_bytes(P, cfg->feat_dim, cfg->mlp_groups, cfg->samples) > 227 * 1024) return MLPS_ERR_UNSUPPORTED;
     return MLPS_OK;
   }

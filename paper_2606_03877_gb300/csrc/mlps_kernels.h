@@ -71,7 +71,7 @@ cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaS
 bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3 = false);
 size_t tc_smem_bytes(const TcPlan& P, int F, int groups, int S);
 // forward tensor-core MLP: the groups a configuration runs with (0 if `groups` is not allowed)
-int tc_fwd_groups(int width, int F, int groups);
+int tc_fwd_groups(int width, int F, int groups, bool e4m3);
 void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, const float* w,
                       void* out, cudaStream_t st);
 cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,

@@ -1,6 +1,6 @@
 // mlps_tune.cu -- autotuner of the batched render: picks the screen-tile edge of the binning and
 // intersection stages (16 or 8 pixels) and the samples per CTA of the forward tensor-core MLP
-// (2, 3 or 4 chunks of 128 sample rows in flight) by timing every candidate on the caller's own
+// (2 to 6 chunks of 128 sample rows in flight) by timing every candidate on the caller's own
 // batch with CUDA events. Decisions are cached per batch shape (MLP shape, precision, samples,
 // and every item's primitive count and resolution) for the life of the process.
 //
@@ -112,7 +112,7 @@ extern "C" mlps_status mlps_autotune_batch(
                scratch, scratch_bytes, d_weights, d_centers, d_scales, d_quats, stream};
   const bool tc = cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3;
   std::vector<int> groups = {0};
-  if (tc && cfg->hidden_width == 64 && cfg->feat_dim == 0) groups = {4, 3, 2};
+  if (tc && cfg->hidden_width == 64 && cfg->feat_dim == 0) groups = {6, 5, 4, 3, 2};
   float best = -1.f;
   int best_tile = cfg->tile, best_groups = cfg->mlp_groups, nc = 0;
   for (int tile : {16, 8}) {
@@ -122,7 +122,7 @@ extern "C" mlps_status mlps_autotune_batch(
       c.mlp_groups = g;
       if (mlps_check_config(&c) != MLPS_OK) continue;
       const float ms = time_candidate(&c, a, reps);
-      if (nc < 8) {
+      if (nc < 16) {
         if (cand_tile) cand_tile[nc] = tile;
         if (cand_groups) cand_groups[nc] = g;
         if (cand_ms) cand_ms[nc] = ms;
@@ -135,7 +135,7 @@ extern "C" mlps_status mlps_autotune_batch(
       }
     }
   }
-  if (n_candidates) *n_candidates = nc < 8 ? nc : 8;
+  if (n_candidates) *n_candidates = nc < 16 ? nc : 16;
   if (best < 0.f) return MLPS_ERR_UNSUPPORTED;  // no candidate ran
   *tuned = *cfg;
   tuned->tile = best_tile;

@@ -191,12 +191,12 @@ MLPS_DEV void put_gamma8(RowWriter8& rw, float p, int L) {
 template <int NG>
 struct ChunkStep {
   int c0, prim, n;
-  int c[4];  // chunk per group (-1: none); accessed with compile-time indices only
+  int c[6];  // chunk per group (-1: none); accessed with compile-time indices only
 };
 
 template <int NG>
 MLPS_DEV ChunkStep<NG> chunk_step(const Work& w, int c, int ce, int prim) {
-  static_assert(NG >= 1 && NG <= 4, "at most four epilogue groups");
+  static_assert(NG >= 1 && NG <= 6, "at most six epilogue groups");
   ChunkStep<NG> s;
   s.c0 = c;
   if (c < ce)
@@ -207,14 +207,16 @@ MLPS_DEV ChunkStep<NG> chunk_step(const Work& w, int c, int ce, int prim) {
   s.c[1] = (NG > 1 && c + 1 < lim) ? c + 1 : -1;
   s.c[2] = (NG > 2 && c + 2 < lim) ? c + 2 : -1;
   s.c[3] = (NG > 3 && c + 3 < lim) ? c + 3 : -1;
-  s.n = (s.c[0] >= 0) + (s.c[1] >= 0) + (s.c[2] >= 0) + (s.c[3] >= 0);
+  s.c[4] = (NG > 4 && c + 4 < lim) ? c + 4 : -1;
+  s.c[5] = (NG > 5 && c + 5 < lim) ? c + 5 : -1;
+  s.n = (s.c[0] >= 0) + (s.c[1] >= 0) + (s.c[2] >= 0) + (s.c[3] >= 0) + (s.c[4] >= 0) + (s.c[5] >= 0);
   return s;
 }
 
 // Chunk of group g in a step (register selects; no dynamic indexing).
 template <int NG>
 MLPS_DEV int step_chunk(const ChunkStep<NG>& s, int g) {
-  return g == 0 ? s.c[0] : (g == 1 ? s.c[1] : (g == 2 ? s.c[2] : s.c[3]));
+  return g == 0 ? s.c[0] : g == 1 ? s.c[1] : g == 2 ? s.c[2] : g == 3 ? s.c[3] : g == 4 ? s.c[4] : s.c[5];
 }
 
 // Interval record (and, for the backward pass, its gradient) of one chunk row, loaded one

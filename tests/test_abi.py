@@ -132,8 +132,8 @@ def test_batch_item_validation(lib):
 
 def test_mlp_groups_validation(lib):
     base = synth.CONFIGS["prec"]
-    for g, want in ((1, _lib.MLPS_ERR_INVALID_ARGUMENT), (5, _lib.MLPS_ERR_INVALID_ARGUMENT),
-                    (2, _lib.MLPS_OK), (3, _lib.MLPS_OK), (4, _lib.MLPS_OK)):
+    for g, want in ((1, _lib.MLPS_ERR_INVALID_ARGUMENT), (7, _lib.MLPS_ERR_INVALID_ARGUMENT),
+                    (2, _lib.MLPS_OK), (3, _lib.MLPS_OK), (4, _lib.MLPS_OK), (5, _lib.MLPS_OK), (6, _lib.MLPS_OK)):
         assert _lib.mlps_check_config(make_config(base, "bf16", mlp_groups=g)) == want, g
     # wider models and feature heads run with their default only
     assert _lib.mlps_check_config(make_config(synth.CONFIGS["stress"], "bf16", mlp_groups=3)) == \
