@@ -565,6 +565,7 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
       if (l > 0) {
         // delta_{l-1} = G * [H_l > 0], written over H_l in T_l once the wgrad of B_l has read it
         const uint32_t Tl = tileaddr(l);
+        const uint32_t vmask = valid ? 0xFFFFFFFFu : 0u;
         uint32_t pk[32];
 #pragma unroll
         for (int ch = 0; ch < 8; ++ch) {
@@ -575,11 +576,9 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
             const int c0 = ch * 8 + 2 * e;
             const float g0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]);
             const float g1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]);
-            // BF16 pair: low half = feature c0, high half = feature c0 + 1 (> 0 iff positive, non-zero)
-            const uint32_t h0 = hq[e] & 0xFFFFu, h1 = hq[e] >> 16;
-            const bool p0 = h0 != 0u && (h0 & 0x8000u) == 0u;
-            const bool p1 = h1 != 0u && (h1 & 0x8000u) == 0u;
-            pk[ch * 4 + e] = pack_bf16(valid && p0 ? g0 : 0.f, valid && p1 ? g1 : 0.f);
+            // H_l was written by the ReLU pack, so each BF16 half is +0 or positive: H > 0 iff its
+            // 16 bits are nonzero, and __vcmpne2 gives both halves' masks at once
+            pk[ch * 4 + e] = pack_bf16(g0, g1) & __vcmpne2(hq[e], 0u) & vmask;
           }
         }
         ok = wait_wgrad() && ok;  // wgrad of B_l: T_l is free
