@@ -52,7 +52,14 @@ namespace {
 // Epilogue groups (chunks in flight per SM): 3 where their tiles fit in shared memory and their
 // accumulators next to the weight gradients in TMEM, else 2 (template parameter NG).
 constexpr int kGThreads = kEGThreads;               // 4 warps, one per TMEM lane quarter
-constexpr uint32_t kTmemColsB = 512;                // 64 per group + 64 per layer (weight gradients)
+constexpr uint32_t kTmemColsB = 512;  // per group 64 (accumulator) [+ 32 (H_0 stash)], per layer 64
+                                      // of weight gradients (16 for the head layer)
+
+// TMEM columns of the weight gradients: 64 per layer, the head layer (npad <= 16) last with 16.
+MLPS_HD int dw_cols(int nl) { return (nl - 1) * 64 + 16; }
+// Whether the groups' encoded inputs H_0 also fit in TMEM (32 columns each, after the weight
+// gradients rounded up to 32 columns): then the last wgrad reloads H_0 instead of re-encoding it.
+MLPS_HD bool x_stash_fits(int nl, int ng) { return 64 * ng + (dw_cols(nl) + 31) / 32 * 32 + 32 * ng <= 512; }
 constexpr uint64_t kWaitNsB = 2000000000ull;
 constexpr uint32_t kTile = kM * 128;                // one [128 x 64] BF16 tile
 constexpr uint32_t kOnes = 2048;                    // 16 rows of the MN-major ones atom (one K step)
@@ -136,9 +143,8 @@ MLPS_DEV void ld_shared_v4(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c,
 // Encoded input row (Eq. 5) of one sample into tile `A` with compile-time frequency counts
 // (zeros for rows past the chunk's intervals).
 template <int XL, int DL>
-MLPS_DEV void build_row64(const IntervalRec* T, int nint, int S, int row, uint32_t A) {
+MLPS_DEV void encode_row64(const IntervalRec* T, int nint, int S, int row, uint32_t (&pk)[32]) {
   const int iv = row / S, k = row - iv * S;
-  uint32_t pk[32];
   if (iv < nint) {
     const IntervalRec& I = T[iv];
     const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
@@ -149,6 +155,12 @@ MLPS_DEV void build_row64(const IntervalRec* T, int nint, int S, int row, uint32
 #pragma unroll
     for (int e = 0; e < 32; ++e) pk[e] = 0u;
   }
+}
+
+template <int XL, int DL>
+MLPS_DEV void build_row64(const IntervalRec* T, int nint, int S, int row, uint32_t A) {
+  uint32_t pk[32];
+  encode_row64<XL, DL>(T, nint, S, row, pk);
   store_row64(A, row, pk);
 }
 
@@ -291,6 +303,8 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
   tc_fence_after();
   const uint32_t tmem = *sTmem;
   const uint32_t tm_dw = tmem + 64 * kNG;  // weight-gradient accumulators: 64 columns per layer
+  const bool xstash = DL >= 0 && x_stash_fits(nl, kNG);
+  const uint32_t tm_x = tm_dw + (uint32_t)((dw_cols(nl) + 31) / 32 * 32);  // H_0 stash of group 0
 
   const int total = w.saved_hdr[2];
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
@@ -313,9 +327,16 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
       const int frow = warp * 32 + lane;
       for (int l = 0; l < nl; ++l) {
         const int din = m.din[l], dout = m.dout[l];
-        for (int c0 = 0; c0 < 64; c0 += 32) {
+        for (int c0 = 0; c0 < (l == nl - 1 ? 16 : 64); c0 += 32) {
           uint32_t v[32];
-          tmem_ld32(tm_dw + (uint32_t)(l * 64 + c0) + lanebase, v);
+          if (l == nl - 1) {  // the head layer's 16 columns
+            uint32_t v16[16];
+            tmem_ld16(tm_dw + (uint32_t)(l * 64) + lanebase, v16);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = j < 16 ? v16[j & 15] : 0u;
+          } else {
+            tmem_ld32(tm_dw + (uint32_t)(l * 64 + c0) + lanebase, v);
+          }
           tmem_wait_ld();
           if (*sAbort) continue;
           for (int j = 0; j < 32; ++j) {
@@ -360,7 +381,8 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
       if (loaded >= 0) flush(loaded);
       if (warp < 4) {  // clear the weight-gradient accumulators for the new primitive
         const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
-        for (int c0 = 0; c0 < nl * 64; c0 += 32) tmem_st32_zero(tm_dw + (uint32_t)c0 + lanebase);
+        for (int c0 = 0; c0 < (nl - 1) * 64; c0 += 32) tmem_st32_zero(tm_dw + (uint32_t)c0 + lanebase);
+        tmem_st16_zero(tm_dw + (uint32_t)((nl - 1) * 64) + lanebase);
         tmem_wait_st();
       }
       tc_fence_before();
@@ -415,8 +437,17 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
     const uint32_t acc = tmem + (uint32_t)(g * 64);  // this group's dgrad / forward accumulator
     const uint32_t trow = acc + ((uint32_t)(q * 32) << 16);
 
-    if (DL >= 0) build_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
-    else build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+    if (DL >= 0) {
+      uint32_t pk[32];
+      encode_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, pk);
+      store_row64(tileaddr(0), row, pk);
+      if (xstash) {  // keep H_0 for the last wgrad
+        tmem_st32(tm_x + (uint32_t)(32 * g) + ((uint32_t)(q * 32) << 16), pk);
+        tmem_wait_st();
+      }
+    } else {
+      build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+    }
     fence_proxy_async_smem();
     tc_fence_before();
     named_bar_sync(gbar, kGThreads);
@@ -583,9 +614,17 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
         }
         ok = wait_wgrad() && ok;  // wgrad of B_l: T_l is free
         store_row64(Tl, row, pk);
-        if (l == 1) {  // dL/dZ in T_0 was consumed by B_{nl-1}: rebuild H_0 there for the last wgrad
-          if (DL >= 0) build_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
-          else build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+        if (l == 1) {  // dL/dZ in T_0 was consumed by B_{nl-1}: restore H_0 there for the last wgrad
+          if (xstash) {
+            uint32_t xv[32];
+            tmem_ld32(tm_x + (uint32_t)(32 * g) + ((uint32_t)(q * 32) << 16), xv);
+            tmem_wait_ld();
+            store_row64(tileaddr(0), row, xv);
+          } else if (DL >= 0) {
+            build_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
+          } else {
+            build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+          }
         }
         fence_proxy_async_smem();
         tc_fence_before();
@@ -703,7 +742,7 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
 static int bwd_groups(const Model& m, const TcPlan& P) {
   const int ipc = m.S <= 128 ? 128 / m.S : 1;
   for (int ng = 3; ng >= 2; --ng) {
-    if (64 * ng + 64 * m.nl > (int)tc::kTmemColsB) continue;  // TMEM: groups + weight gradients
+    if (64 * ng + tc::dw_cols(m.nl) > (int)tc::kTmemColsB) continue;  // TMEM: groups + weight gradients
     if (tc::bwd_layout(P, m.F, ipc, ng).total + 1024 <= 227 * 1024) return ng;
   }
   return 0;
