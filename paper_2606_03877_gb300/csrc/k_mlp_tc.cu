@@ -46,7 +46,7 @@ constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s
 // Byte offsets in dynamic shared memory; per-group regions are base + g * stride (plain
 // arithmetic, so that nothing is indexed at run time).
 struct TcSmem {
-  uint32_t w, a0, a_stride, bias, itab0, itab_stride, scan, bars, misc, total;
+  uint32_t w, ones, a0, a_stride, bias, itab0, itab_stride, scan, bars, misc, total;
 };
 
 MLPS_HD uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -55,7 +55,9 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG, bool e4m3, int ipc) {
   TcSmem L;
   uint32_t off = 0;
   L.w = off;
-  off = align_up(off + (e4m3 ? P.w8_bytes : P.w_bytes), 1024);
+  off = align_up(off + (e4m3 ? P.w8_bytes : P.w_bytes + P.bt_bytes), 1024);
+  L.ones = off;  // folded bias: A tile whose every row is (1, 0, ..., 0)
+  off += (!e4m3 && P.fold > 0) ? (uint32_t)kM * 128 : 0u;
   L.a0 = off;
   L.a_stride = align_up(P.a_bytes, 1024);
   off += L.a_stride * kNEG;
@@ -110,6 +112,13 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     *sAbort = 0;
     fence_mbar_init();
   }
+  if (!F8 && P.fold > 0) {  // ones tile of the folded bias: element 0 of every row is 1.0
+    for (int i = threadIdx.x; i < kM * 8; i += kThreadsTC) {
+      const int r = i >> 3, ch = i & 7;
+      st_shared_v4(sbase + L.ones + (uint32_t)i * 16, ((ch ^ (r & 7)) == 0) ? 0x3F80u : 0u, 0u, 0u, 0u);
+    }
+    fence_proxy_async_smem();
+  }
   if (warp == 0) {
     tmem_alloc(sbase + L.misc, kTmemCols);
     tmem_relinquish();
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     if (prim != loaded) {
       __syncthreads();  // every role is done with the previous primitive's tiles
       if (threadIdx.x == 0 && !*sAbort) {
-        mbar_arrive_expect_tx(bar_w, (uint32_t)(F8 ? P.w8_bytes : P.w_bytes));
+        mbar_arrive_expect_tx(bar_w, (uint32_t)(F8 ? P.w8_bytes : P.w_bytes + P.bt_bytes));
         const int row0 = prim * P.rows_per_prim;
         for (int l = 0; l < nl; ++l) {
           if (F8) {
@@ -166,6 +175,9 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
                             row0 + P.gw_row[l] + sl * P.npad[l] + j * 16, bar_w);
           }
         }
+        if (!F8 && P.fold > 0)
+          for (int j = 0; j < 4; ++j)
+            tma_load_2d(sbase + L.w + P.sbt_off + j * 2048, &tmap, 0, row0 + P.gbt_row + j * 16, bar_w);
       }
       const unsigned char* blob = a.weights + (size_t)prim * a.pk.stride;
       const float* gb = reinterpret_cast<const float*>(blob + P.gbias_byte);
@@ -269,7 +281,8 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
           tc_fence_after();
           if (!*sAbort) {
             if (F8) issue_fwd_layer_e4m3(A, sbase + L.w + P.s8_off[0], dacc, P.kpad[0], P.npad[0]);
-            else issue_fwd_layer(A, sbase + L.w + P.sw_off[0], dacc, P.kpad[0], P.npad[0]);
+            else issue_fwd_layer(A, sbase + L.w + P.sw_off[0], dacc, P.kpad[0], P.npad[0], sbase + L.ones,
+                                 P.fold > 0 ? sbase + L.w + P.sbt_off : 0u);
           }
           mma_commit(bar_done(g));
         }
@@ -351,6 +364,22 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
               }
               srow = sn;
               }
+            } else if (ok && l < P.fold) {  // bias already added by the MMA
+#pragma unroll
+              for (int h32 = 0; h32 < WIDTH / 32; ++h32) {
+                uint32_t v[32];
+                tmem_ld32(trow + h32 * 32, v);
+                tmem_wait_ld();
+                const uint32_t At = A + (uint32_t)(h32 >> 1) * (kM * 128);
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                  uint32_t pk[4];
+#pragma unroll
+                  for (int e = 0; e < 4; ++e)
+                    pk[e] = pack_bf16_relu(__uint_as_float(v[8 * c4 + 2 * e]), __uint_as_float(v[8 * c4 + 2 * e + 1]));
+                  st_shared_v4(At + sw128_off(row, 4 * (h32 & 1) + c4), pk[0], pk[1], pk[2], pk[3]);
+                }
+              }
             } else if (ok) {
               // 32 columns at a time: fewer live registers, so more groups fit on the SM
 #pragma unroll
@@ -380,7 +409,8 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
               tc_fence_after();
               if (!*sAbort) {
                 if (F8) issue_fwd_layer_e4m3(A, sbase + L.w + P.s8_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1]);
-                else issue_fwd_layer(A, sbase + L.w + P.sw_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1]);
+                else issue_fwd_layer(A, sbase + L.w + P.sw_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1],
+                                     sbase + L.ones, l + 1 < P.fold ? sbase + L.w + P.sbt_off + 32u * (l + 1) : 0u);
               }
               mma_commit(bar_done(g));
             }
@@ -482,6 +512,14 @@ __global__ void k_pack_bf16(Model m, TcPlan P, long long stride, int K, const fl
   for (int l = 0; l < m.nl; ++l)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.npad[l]; i += gridDim.x * blockDim.x)
       b[P.bias_off[l] + i] = i < m.dout[l] ? s[m.boff[l] + i] : 0.f;
+  if (P.fold > 0) {  // bias tile: row n, column 16 l = bias of output n of layer l
+    __nv_bfloat16* bt = reinterpret_cast<__nv_bfloat16*>(d + (size_t)P.gbt_row * 128);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 64 * 64; i += gridDim.x * blockDim.x) {
+      const int n = i >> 6, k = i & 63, l = k >> 4;
+      const float v = ((k & 15) == 0 && l < P.fold && n < m.dout[l]) ? s[m.boff[l] + n] : 0.f;
+      bt[i] = __float2bfloat16_rn(v);
+    }
+  }
   if (P.w8_bytes == 0) return;
   // E4M3 copy: output n of layer l is stored as W[n][k] / c_n with c_n = max_k |W[n][k]| / 448
   float* scl = reinterpret_cast<float*>(d + P.gscale_byte);
@@ -527,6 +565,13 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3) {
   }
   P->w_bytes = sw;
   // (the backward pass reads the same W tiles as MN-major operands: no transposed copies)
+  if (m.width == 64 && m.nl - 1 >= 1 && m.nl - 1 <= 4) {  // hidden-layer biases folded (BF16 forward)
+    P->fold = m.nl - 1;
+    P->gbt_row = rows;
+    rows += 64;
+    P->sbt_off = sw;
+    P->bt_bytes = 64 * 128;
+  }
   P->bias_floats = bias;
   P->gbias_byte = rows * 128;
   long long bytes = (long long)rows * 128 + 4LL * bias;

@@ -34,6 +34,13 @@ struct TcPlan {
   int sw_off[kMaxLayers];                  // shared-memory byte offset of layer l's W tile
   int gw_row[kMaxLayers];                  // first 128-byte row of layer l's tile in a blob
   int w_bytes;                             // all forward W tiles
+  // bias folding of the BF16 forward (0 = none): the biases of layers 0 .. fold-1 are a K-major
+  // B tile of 64 rows x 64 columns (layer l's bias in column 16 l), multiplied by a constant
+  // "ones" A tile in one extra K step per layer, so the epilogue adds no bias
+  int fold;
+  int gbt_row;                             // first 128-byte row of the bias tile in a blob
+  int sbt_off;                             // its shared-memory byte offset (after the W tiles)
+  int bt_bytes;                            // 8192 when fold > 0
   // E4M3 copy (FP8 precision only; w8_bytes = 0 otherwise): layer l's tile W [npad][kpad] as
   // one 128-byte row per output (kpad <= 128), and FP32 per-output weight scales
   int g8_row[kMaxLayers];                  // first 128-byte row of layer l's E4M3 tile in a blob

@@ -119,7 +119,10 @@ MLPS_DEV void seg_scan_rev(float (&v)[NV], int nv, int row, int S, float* scratc
 // MMAs of one forward layer of a 128-row chunk: D[128 x npad] = A[128 x kpad] W^T, A and W in
 // the K-major swizzled layout, K in 64-column slabs (kpad <= 128). Issued by one thread. The
 // descriptors are built once; stepping K only moves their start-address field (address >> 4).
-MLPS_DEV void issue_fwd_layer(uint32_t A, uint32_t W, uint32_t d, int kpad, int npad) {
+// With `bt` nonzero one more K step adds the bias: A = the `ones` tile (every row (1, 0, ...)),
+// B = the K step of the bias tile that holds this layer's bias in its first column.
+MLPS_DEV void issue_fwd_layer(uint32_t A, uint32_t W, uint32_t d, int kpad, int npad, uint32_t ones = 0u,
+                              uint32_t bt = 0u) {
   const uint32_t idesc = idesc_bf16(kM, npad);
   const uint64_t da = sw128_desc(A), db = sw128_desc(W);
   const uint32_t wslab = (uint32_t)npad * 8;  // (npad * 128 bytes) >> 4: one 64-column slab of W
@@ -131,6 +134,7 @@ MLPS_DEV void issue_fwd_layer(uint32_t A, uint32_t W, uint32_t d, int kpad, int 
     const uint32_t ob = (uint32_t)(kk >> 2) * wslab + (uint32_t)(kk & 3) * 2;
     mma_bf16(d, da + oa, db + ob, idesc, kk > 0 ? 1u : 0u);
   }
+  if (bt) mma_bf16(d, sw128_desc(ones), sw128_desc(bt), idesc, 1u);
 }
 
 // FP8 (E4M3) forward layer: same operand tiles (128-byte K-major swizzled rows, here holding up
