@@ -478,7 +478,7 @@ def run_reference(a):
     cores = os.cpu_count() or 1
     do_bwd = a.pass_ == "fwdbwd"
     g = synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100, scale=0.01).reshape(-1, 3)
-    per_step = max(cores, int(os.environ.get("MLPS_REF_PIXELS", "0")) or 0)
+    per_step = int(os.environ.get("MLPS_REF_PIXELS", "0"))  # 0: size the sample by calibration
 
     def one(pix):
         if do_bwd:
@@ -487,8 +487,10 @@ def run_reference(a):
         else:
             oracle.render(wl, scene, cams, pix=pix, n_threads=cores)
 
-    # size one step to ~8 s of host work so that steps + warmup stay within a few minutes
-    cal = synth.sample_pixels(wl, 4 * cores, seed=1)
+    # size one step to ~8 s of host work so that steps + warmup stay within a few minutes; the
+    # first call (library load, thread start) is not part of the calibration
+    one(synth.sample_pixels(wl, cores, seed=0))
+    cal = synth.sample_pixels(wl, max(256, 16 * cores), seed=1)
     t = time.perf_counter(); one(cal); dt = time.perf_counter() - t
     budget = min(8.0, 150.0 / max(1, a.steps + a.warmup))
     n = per_step or int(max(cores, budget / max(dt / len(cal), 1e-9)))
