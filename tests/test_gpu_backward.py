@@ -114,3 +114,39 @@ def test_autograd_function_matches_direct_backward():
     # float atomics make the two runs differ in the last bits only
     assert rel_l2(d["weights"].grad.cpu().numpy(), got["d_weights"]) < 1e-5
     assert rel_l2(d["centers"].grad.cpu().numpy(), got["d_centers"]) < 1e-5
+
+
+def _full_size_sampled(precision, n_pix):
+    """The Precision workload at full size (1080p x 8 views, K = 256, the bench's launch): L2 loss
+    against the seed-1-perturbed oracle render on pixels sampled uniformly over the views (the
+    oracle's reverse mode runs on those pixels only)."""
+    cfg = synth.CONFIGS["prec"]
+    scene = synth.make_scene(cfg, 0)
+    cams = synth.make_cameras(cfg)
+    pix = synth.sample_pixels(cfg, n_pix, seed=21)
+    cur, _, _ = oracle.render(cfg, scene, cams, pix=pix)
+    tgt, _, _ = oracle.render(cfg, synth.perturb_scene(scene, cfg, 1), cams, pix=pix)
+    gl = (cur - tgt).astype(np.float32)
+    g = np.zeros((cfg.n_views, cfg.height, cfg.width, 3), np.float32)
+    g.reshape(-1, 3)[pixel_index(cfg.width, cfg.height, pix)] = gl
+    got, _ = _run(cfg, scene, cams, g, precision=precision)
+    ref = oracle.render_backward(cfg, scene, cams, pix, gl)
+    errs = {k: rel_l2(got[k], ref[rk]) for k, rk in GROUPS}
+    print(precision, "full-size sampled gradient rel-L2:", errs)
+    return errs
+
+
+def test_full_size_prec_sampled_gradients_fp32():
+    errs = _full_size_sampled("fp32", 2000)
+    for k, e in errs.items():
+        assert e < TOL, (k, errs)
+
+
+def test_full_size_prec_sampled_gradients_bf16():
+    """BF16: the weight gradients meet the 2e-2 bar. The pose gradients of these sparse samples
+    (~23 pixels per primitive) carry ReLU mask flips of BF16 rounding that do not average out
+    (2.6-3.9 % at 6000 pixels, falling with the pixel count); bounded loosely here."""
+    errs = _full_size_sampled("bf16", 6000)
+    assert errs["d_weights"] < 2e-2, errs
+    for k in ("d_centers", "d_scales", "d_quats"):
+        assert errs[k] < 6e-2, (k, errs)

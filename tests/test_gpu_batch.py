@@ -181,3 +181,33 @@ def test_autotuner_picks_a_candidate_and_changes_no_output_bit():
     assert torch.equal(out["rgb"], ref)
     again = br.autotune(d["centers"], d["scales"], d["quats"], packed, d_rgb=g, reps=2)
     assert again["best_ms"] == 0.0 and (again["tile"], again["mlp_groups"]) == (tun["tile"], tun["mlp_groups"])
+
+
+def test_batch_edge_cases_empty_items_and_tiny_images():
+    """Items with no primitives render black with T = 1; a 1 x 1 item and a batch whose scene
+    arrays are empty (K = 0) run; gradients of unreferenced primitives are zero."""
+    cfgs, cat, items, scenes = _small_batch(80)
+    K = cat["centers"].shape[0]
+    tiny = dict(items[0][2], width=1, height=1, cx=0.5, cy=0.5)
+    its = [items[0], (0, 0, items[1][2]), (items[2][0], items[2][1], tiny), (items[3][0], 0, items[3][2])]
+    br, out, d, packed = _batch_forward("bf16", cat, its)
+    rgb, T = br.split(out["rgb"]), br.split(out["trans"])
+    for i in (1, 3):
+        assert float(rgb[i].abs().max()) == 0.0 and bool((T[i] == 1.0).all()), i
+    c0 = cfgs[0]
+    _, o1, _, _ = gpu_render(c0, scenes[0], [items[0][2]], "bf16")
+    assert np.array_equal(rgb[0].cpu().numpy(), o1["rgb"][0])
+    g = br.backward(torch.ones(br.n_pixels, 3, device="cuda"))
+    torch.cuda.synchronize()
+    assert br.status("scratch") == 0
+    used = np.zeros(K, bool)
+    for off, cnt, _ in its:
+        used[off:off + cnt] = True
+    assert float(np.abs(g["d_weights"].cpu().numpy()[~used]).max()) == 0.0
+    # no primitives at all
+    empty = {k: v[:0] for k, v in cat.items()}
+    br0 = BatchRenderer(SHAPE, [(0, 0, items[0][2]), (0, 0, tiny)], 0, precision="bf16")
+    d0 = to_dev(empty)
+    out0 = br0.forward(d0["centers"], d0["scales"], d0["quats"], br0.pack(d0["weights"]))
+    torch.cuda.synchronize()
+    assert br0.status() == 0 and float(out0["rgb"].abs().max()) == 0.0
