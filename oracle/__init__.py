@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY: the test suite, the package smoke check and the benchmark's
 CPU-baseline leg are the only callers. The CUDA library and its Python binding never import
 this package, and this package imports nothing from them: configs are taken by duck typing
-(any object with ``xyz_freqs, dir_freqs, hidden_width, hidden_layers, feat_dim, samples``) and
+(any object with ``xyz_freqs, dir_freqs, hidden_width, hidden_layers, feat_dim, samples`` and
+an optional ``contact``) and
 scenes / cameras as plain numpy arrays and dicts.
 
 All inputs are converted to float64 before the call; outputs are float64.
@@ -28,7 +29,8 @@ _lib = None
 
 class _Cfg(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
-                ("xyz_freqs", "dir_freqs", "hidden_width", "hidden_layers", "feat_dim", "samples")]
+                ("xyz_freqs", "dir_freqs", "hidden_width", "hidden_layers", "feat_dim", "samples",
+                 "contact")]
 
 
 class _Cam(ctypes.Structure):
@@ -79,7 +81,7 @@ def _load():
 
 def _cfg(c) -> _Cfg:
     return _Cfg(int(c.xyz_freqs), int(c.dir_freqs), int(c.hidden_width), int(c.hidden_layers),
-                int(c.feat_dim), int(c.samples))
+                int(c.feat_dim), int(c.samples), int(getattr(c, "contact", 0)))
 
 
 def _cam(c: Dict) -> _Cam:

@@ -34,6 +34,13 @@
  *     dL/dC, dL/dT_final and dL/dF). Hit sets and orders are piecewise constant and are not
  *     differentiated.
  *
+ * Contact-point mode (contact = 1, the paper's own formulation of Sec. 3.2): one sample per hit
+ * (S = 1), whose MLP input is not the sample position but the 6-vector x = [d; delta] of Eq. 4:
+ * the unit view direction d and the residual delta = mu - p* from the soft contact point
+ * p* = o + t* d, t* = max(0, d^T Lambda (mu - o) / d^T Lambda d) (Eq. 2-3), each component
+ * encoded by gamma (L = dir_freqs for d, xyz_freqs for delta; 0 = raw). The alpha of the hit is
+ * still 1 - exp(-sigma * chord length).
+ *
  * Readings of points the paper leaves open (scalar delta of Eq. 6 = the sample step, support
  * = unit-Mahalanobis ellipsoid, falloff off, interval-by-interval compositing, tie-break,
  * camera model, background) are listed with the design notes of the repository.
@@ -56,6 +63,7 @@ typedef struct {
   int hidden_layers;
   int feat_dim;      /* extra linear outputs, composited like colour */
   int samples;       /* S midpoint samples per hit interval */
+  int contact;       /* 1: contact-point mode (S = 1, input gamma([d; delta])) */
 } orc_cfg;
 
 typedef struct {
@@ -98,6 +106,7 @@ static int cfg_valid(const orc_cfg* c) {
   if (c->xyz_freqs < 0 || c->dir_freqs < 0 || c->hidden_width <= 0 || c->hidden_layers < 0 ||
       c->feat_dim < 0 || c->samples <= 0)
     return 0;
+  if (c->contact != 0 && (c->contact != 1 || c->samples != 1)) return 0;
   if (orc_num_layers(c) > ORC_MAX_LAYERS) return 0;
   return 1;
 }
@@ -239,6 +248,52 @@ static void encode_backward(const orc_cfg* c, const double* xl, const double* ge
       gx[i] += ge[n] * w * cos(f) - ge[n + 1] * w * sin(f);
       n += 2;
     }
+}
+
+/* gamma of one 3-vector with L frequencies (raw when L = 0), appended at e[n]. */
+static int encode_vec(int L, const double* v, double* e, int n) {
+  if (L == 0) {
+    for (int i = 0; i < 3; ++i) e[n++] = v[i];
+    return n;
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int l = 0; l < L; ++l) {
+      double f = ldexp(M_PI, l) * v[i];
+      e[n++] = sin(f);
+      e[n++] = cos(f);
+    }
+  return n;
+}
+
+/* Contact-point mode input gamma([d; delta]) (Eq. 4-5): direction first, then the residual. */
+static int encode_contact(const orc_cfg* c, const double* d, const double* delta, double* e) {
+  int n = 0;
+  if (c->dir_freqs > 0) n = encode_vec(c->dir_freqs, d, e, n);
+  return encode_vec(c->xyz_freqs, delta, e, n);
+}
+
+/* dL/d delta from the gradient on the contact-mode encoding. */
+static void encode_contact_backward(const orc_cfg* c, const double* delta, const double* ge, double* gdelta) {
+  int n = c->dir_freqs > 0 ? 6 * c->dir_freqs : 0;
+  if (c->xyz_freqs == 0) {
+    for (int i = 0; i < 3; ++i) gdelta[i] = ge[n + i];
+    return;
+  }
+  for (int i = 0; i < 3; ++i) {
+    gdelta[i] = 0;
+    for (int l = 0; l < c->xyz_freqs; ++l) {
+      double w = ldexp(M_PI, l);
+      double f = w * delta[i];
+      gdelta[i] += ge[n] * w * cos(f) - ge[n + 1] * w * sin(f);
+      n += 2;
+    }
+  }
+}
+
+/* delta = mu - p*, p* = o + t* d, t* = max(0, t_mid) (Eq. 2-3). */
+static void contact_delta(const double* mu, const double* o, const double* d, double tmid, double* delta) {
+  double ts = tmid > 0 ? tmid : 0;
+  for (int i = 0; i < 3; ++i) delta[i] = mu[i] - (o[i] + ts * d[i]);
 }
 
 typedef struct {
@@ -383,14 +438,20 @@ static void scratch_free(scratch_t* s) {
   free(s->buf_a); free(s->buf_b); free(s->gout); free(s->samp);
 }
 
-/* Evaluate sample k of a hit: encodes, runs the MLP into s->acts, returns x' in xl. */
-static void eval_sample(const job_t* j, const hit_t* h, const double* d, int k, scratch_t* s,
-                        double* xl, double* tk_out) {
+/* Evaluate sample k of a hit: encodes, runs the MLP into s->acts, returns x' in xl (contact
+ * mode: the residual delta of Eq. 3 in xl). */
+static void eval_sample(const job_t* j, const hit_t* h, const double* o, const double* d, int k,
+                        scratch_t* s, double* xl, double* tk_out) {
   int S = j->cfg->samples;
   double delta = (h->t1 - h->t0) / S;
   double tk = h->t0 + (k + 0.5) * delta;
-  for (int i = 0; i < 3; ++i) xl[i] = h->op[i] + tk * h->dp[i];
-  encode(j->cfg, xl, d, s->acts);
+  if (j->cfg->contact) {
+    contact_delta(j->geo[h->prim].mu, o, d, h->tmid, xl);
+    encode_contact(j->cfg, d, xl, s->acts);
+  } else {
+    for (int i = 0; i < 3; ++i) xl[i] = h->op[i] + tk * h->dp[i];
+    encode(j->cfg, xl, d, s->acts);
+  }
   mlp_forward(&j->model, j->weights + (long)h->prim * j->model.P, s->acts);
   if (tk_out) *tk_out = tk;
 }
@@ -426,7 +487,7 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
     const hit_t* h = &s->hits[hi];
     double delta = (h->t1 - h->t0) / S;
     for (int k = 0; k < S; ++k) {
-      eval_sample(j, h, d, k, s, xl, NULL);
+      eval_sample(j, h, o, d, k, s, xl, NULL);
       double* r = s->samp + ((long)hi * S + k) * rec;
       r[0] = sigmoid(out[0]); r[1] = sigmoid(out[1]); r[2] = sigmoid(out[2]);
       r[3] = softplus(out[3]);
@@ -461,6 +522,7 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
     double delta = (h->t1 - h->t0) / S;
     memset(s->gw, 0, sizeof(double) * (size_t)m->P);
     double g_op[3] = {0, 0, 0}, g_dp[3] = {0, 0, 0}, g_t0 = 0, g_t1 = 0, g_delta = 0;
+    double g_mu_direct[3] = {0, 0, 0}, g_tmid_direct = 0; /* contact mode */
     for (int k = S - 1; k >= 0; --k) {
       double* r = s->samp + ((long)hi * S + k) * rec;
       double a = r[NO], T = r[NO + 1];
@@ -478,14 +540,22 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
       g_delta += ga * r[3];
       /* recompute the MLP for this sample */
       double tk;
-      eval_sample(j, h, d, k, s, xl, &tk);
+      eval_sample(j, h, o, d, k, s, xl, &tk);
       for (int ch = 0; ch < 3; ++ch) s->gout[ch] = w * gC[ch] * r[ch] * (1.0 - r[ch]);
       s->gout[3] = gsigma * sigmoid(out[3]);
       for (int f = 0; f < F; ++f) s->gout[4 + f] = gF ? w * gF[f] : 0.0;
       mlp_backward(m, j->weights + (long)P * m->P, s->acts, s->gout, s->gw, s->enc_g, s->buf_a,
                    s->buf_b);
       double gx[3] = {0, 0, 0};
-      encode_backward(c, xl, s->enc_g, gx);
+      if (c->contact) {
+        /* delta = mu - o - t* d: dL/dmu directly, and through t* = t_mid when t_mid > 0 */
+        double gd[3];
+        encode_contact_backward(c, xl, s->enc_g, gd);
+        for (int i = 0; i < 3; ++i) g_mu_direct[i] += gd[i];
+        if (h->tmid > 0) g_tmid_direct -= gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+      } else {
+        encode_backward(c, xl, s->enc_g, gx);
+      }
       /* x' = o' + t_k d',  t_k = t0 + (k + 1/2)(t1 - t0)/S */
       double gt = 0;
       for (int i = 0; i < 3; ++i) {
@@ -500,7 +570,7 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
     g_t0 -= g_delta / S;
     g_t1 += g_delta / S;
     /* t0 = t_mid - h (unless clipped at near), t1 = t_mid + h */
-    double g_tmid = g_t1 + (h->clamped ? 0.0 : g_t0);
+    double g_tmid = g_t1 + (h->clamped ? 0.0 : g_t0) + g_tmid_direct;
     double g_h = g_t1 - (h->clamped ? 0.0 : g_t0);
     const double* op = h->op;
     const double* dp = h->dp;
@@ -523,7 +593,8 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
     for (int r = 0; r < 3; ++r)
       for (int cc = 0; cc < 3; ++cc) dM[r * 3 + cc] = g_op[r] * rel[cc] + g_dp[r] * d[cc];
     for (int cc = 0; cc < 3; ++cc)
-      dmu[cc] = -(g->M[0 * 3 + cc] * g_op[0] + g->M[1 * 3 + cc] * g_op[1] + g->M[2 * 3 + cc] * g_op[2]);
+      dmu[cc] = -(g->M[0 * 3 + cc] * g_op[0] + g->M[1 * 3 + cc] * g_op[1] + g->M[2 * 3 + cc] * g_op[2]) +
+                g_mu_direct[cc];
     pthread_mutex_lock(&j->locks[P]);
     double* dW = j->d_weights + (long)P * m->P;
     for (long i = 0; i < m->P; ++i) dW[i] += s->gw[i];
@@ -730,8 +801,10 @@ int orc_pixel_ray(const orc_cam* cam, int x, int y, double* o, double* d) {
   return 0;
 }
 
-/* Encoding of one (local position, direction) pair, for tests. Returns its length. */
+/* Encoding of one (local position, direction) pair, for tests; in contact-point mode xl is the
+ * residual delta and the result is gamma([d; delta]). Returns its length. */
 int orc_encode(const orc_cfg* cfg, const double* xl, const double* d, double* out) {
+  if (cfg->contact) return encode_contact(cfg, d, xl, out);
   return encode(cfg, xl, d, out);
 }
 

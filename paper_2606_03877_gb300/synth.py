@@ -107,6 +107,7 @@ class SceneConfig:
     feat_dim: int
     samples: int  # S midpoint samples per hit interval
     precision: str = "fp32"
+    contact: int = 0  # 1: contact-point input gamma([d; mu - p*]), one sample per hit (S = 1)
 
     @property
     def input_dim(self) -> int:
@@ -140,6 +141,8 @@ CONFIGS: Dict[str, SceneConfig] = {
     "diff": SceneConfig("diff", 800, 800, 64, 1, 6, 4, 64, 3, 0, 32, "fp32"),
     "prec": SceneConfig("prec", 1920, 1080, 256, 8, 6, 4, 64, 3, 0, 32, "bf16"),
     "stress": SceneConfig("stress", 1920, 1080, 1024, 4, 6, 4, 128, 4, 16, 48, "fp8"),
+    # the paper's own per-primitive model: gamma([d; delta]) with L = 6 (72 inputs), 32 x 2, S = 1
+    "contact": SceneConfig("contact", 800, 800, 64, 1, 6, 6, 32, 2, 0, 1, "fp32", 1),
 }
 
 # Batched workload: 32 scenes, K ~ U{16..512}, resolution uniform over these four.

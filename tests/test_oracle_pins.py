@@ -111,15 +111,33 @@ def _np_mlp(cfg, w, e):
     return h
 
 
+def _np_encode_contact(cfg, d, delta):
+    """gamma([d; delta]) of Eq. 4-5: the direction block first, then the residual."""
+    parts = []
+    if cfg.dir_freqs > 0:
+        for c in range(3):
+            for l in range(cfg.dir_freqs):
+                parts += [math.sin((2 ** l) * math.pi * d[c]), math.cos((2 ** l) * math.pi * d[c])]
+    if cfg.xyz_freqs == 0:
+        parts += list(delta)
+    else:
+        for c in range(3):
+            for l in range(cfg.xyz_freqs):
+                parts += [math.sin((2 ** l) * math.pi * delta[c]), math.cos((2 ** l) * math.pi * delta[c])]
+    return np.array(parts)
+
+
 def _np_render_pixel(cfg, scene, cam, x, y):
     """Independent restatement: quadratic roots, library rotations, matmul MLP, and the
-    product form T_j = prod_{l<j} (1 - alpha_l) of the discrete operator (App. D.1)."""
+    product form T_j = prod_{l<j} (1 - alpha_l) of the discrete operator (App. D.1). In
+    contact-point mode the input is gamma([d; mu - p*]) with p* = o + max(0, t*) d and t* in
+    Eq. 2's world-frame form d^T Lambda (mu - o) / d^T Lambda d."""
     o, d, hits = _np_hits(scene, cam, x, y)
     C = np.zeros(3)
     F = np.zeros(cfg.feat_dim)
     T = 1.0
     S = cfg.samples
-    for key, t0, i, t1, _, _ in hits:
+    for key, t0, i, t1, tstar, _ in hits:
         mu = scene["centers"][i].astype(np.float64)
         s = scene["scales"][i].astype(np.float64)
         R = _rot(scene["quats"][i])
@@ -128,7 +146,10 @@ def _np_render_pixel(cfg, scene, cam, x, y):
         for k in range(S):
             t = t0 + (k + 0.5) * dt
             xl = (R.T @ (o + t * d - mu)) / s
-            z = _np_mlp(cfg, w, _np_encode(cfg, xl, d))
+            if getattr(cfg, "contact", 0):
+                z = _np_mlp(cfg, w, _np_encode_contact(cfg, d, mu - (o + max(0.0, tstar) * d)))
+            else:
+                z = _np_mlp(cfg, w, _np_encode(cfg, xl, d))
             c = 1.0 / (1.0 + np.exp(-z[:3]))
             sigma = np.logaddexp(0.0, z[3])
             alpha = 1.0 - math.exp(-sigma * dt)
@@ -307,6 +328,58 @@ def test_oracle_matches_independent_restatement(name, xyzL, dirL, width, layers,
     assert hit > 20
 
 
+@pytest.mark.parametrize("xyzL,dirL,width,layers,feat", [
+    (6, 6, 32, 2, 0),   # the paper's 72-32-32-4 model
+    (0, 0, 16, 1, 0),   # raw residual, no direction
+    (3, 2, 12, 2, 4),   # with a feature head
+])
+def test_contact_mode_matches_independent_restatement(xyzL, dirL, width, layers, feat):
+    """Contact-point mode (Sec. 3.2, Eq. 2-5) against the numpy restatement, on random scenes
+    with one camera outside every primitive and one inside a large primitive (t* < 0, so
+    p* = o and delta = mu - o)."""
+    cfg = synth.SceneConfig("k", 20, 14, 10, 1, xyzL, dirL, width, layers, feat, 1, contact=1)
+    scene = synth.make_scene(cfg, 5)
+    scene = dict(scene, scales=scene["scales"] * 2.0)
+    cam_out = synth.make_camera(20, 14, 4, radius=3.0)
+    rgb, T, F = oracle.render(cfg, scene, [cam_out])
+    hit = 0
+    for n, (v, x, y) in enumerate(oracle.all_pixels([cam_out])):
+        C2, T2, F2 = _np_render_pixel(cfg, scene, cam_out, x, y)
+        assert np.allclose(rgb[n], C2, atol=1e-10), (x, y)
+        assert abs(T[n] - T2) < 1e-10
+        if feat:
+            assert np.allclose(F[n], F2, atol=1e-10)
+        hit += T2 < 1
+    assert hit > 20
+    # camera inside primitive 0: it is hit from the near plane on, with t* < 0 on most rays
+    cam_in = synth.make_camera(20, 14, 6, radius=2.0)
+    o_in, _ = _ray_np(cam_in, 10, 7)
+    big = {k: v.copy() for k, v in scene.items()}
+    big["centers"][0] = o_in + np.array([0.05, -0.04, 0.03])
+    big["scales"][0] = [0.8, 0.6, 0.7]
+    rgb, T, _ = oracle.render(cfg, big, [cam_in])
+    neg = 0
+    for n, (v, x, y) in enumerate(oracle.all_pixels([cam_in])):
+        C2, T2, _ = _np_render_pixel(cfg, big, cam_in, x, y)
+        assert np.allclose(rgb[n], C2, atol=1e-10), (x, y)
+        assert abs(T[n] - T2) < 1e-10
+        neg += any(h[4] < 0 for h in _np_hits(big, cam_in, x, y)[2])
+    assert neg > 20
+
+
+def test_contact_mode_single_sample_and_input_dim():
+    """Contact-point mode needs S = 1 and keeps the 72-wide input of Sec. 4.1 at L = 6."""
+    cfg = synth.CONFIGS["contact"]
+    assert cfg.samples == 1 and cfg.input_dim == 72
+    scene = synth.make_scene(cfg.replace(K=2), 0)
+    cam = synth.make_camera(4, 4, 0)
+    with pytest.raises(RuntimeError):
+        oracle.render(cfg.replace(samples=2, K=2), scene, [cam])
+    enc = oracle.encode(cfg, [0.1, -0.2, 0.3], [0.6, 0.0, 0.8])
+    assert enc.shape == (72,)
+    assert np.allclose(enc, _np_encode_contact(cfg, [0.6, 0.0, 0.8], [0.1, -0.2, 0.3]), atol=1e-15)
+
+
 def test_encoding_order_probe():
     """An MLP that routes exactly one encoded input j to the density recovers gamma_j from T;
     gamma_j must equal sin/cos(2^l pi p) of the expected component (Eq. 5: per scalar,
@@ -481,31 +554,31 @@ def _loss(cfg, scene, cams, pix, g_rgb, g_T, g_F):
     return L
 
 
-@pytest.mark.parametrize("feat,xyzL", [(0, 6), (3, 0)])
-def test_gradients_central_differences(feat, xyzL):
-    cfg = synth.SceneConfig("g", 14, 10, 3, 1, xyzL, 2, 8, 2, feat, 4)
-    scene = synth.make_scene(cfg, 13)
-    scene = {k: v.astype(np.float64) for k, v in scene.items()}
-    scene["centers"] = scene["centers"] * 0.4
-    scene["scales"] = scene["scales"] * 0.0 + np.array([[0.55, 0.4, 0.5], [0.35, 0.6, 0.45], [0.5, 0.5, 0.3]])
-    cams = [synth.make_camera(14, 10, 6, radius=2.2)]
+def _check_central_differences(cfg, scene, cams, contact_kink=False):
+    """Analytic reverse mode against central differences of the forward loss L = <g, outputs>
+    on the pose (all of centres, scales, quaternions) and 40 random weights."""
+    feat = cfg.feat_dim
     pix = oracle.all_pixels(cams)
     n = pix.shape[0]
-    # stay away from tangency so that no step changes a hit set or an order
+    # stay away from tangency (and, in contact mode, from t* = 0, where max(0, t*) has a kink)
+    # so that no step changes a hit set, an order or a branch
     for (v, x, y) in pix:
-        m2, _ = oracle.ray_m2(scene, cams[v], x, y)
+        m2, tm = oracle.ray_m2(scene, cams[v], x, y)
         assert np.all(np.abs(m2 - 1) > 1e-4)
+        if contact_kink:
+            assert np.all(np.abs(tm[m2 < 1]) > 1e-3)
     g_rgb = synth.make_grad((n, 3), seed=1).astype(np.float64)
     g_T = synth.make_grad((n,), seed=2).astype(np.float64)
     g_F = synth.make_grad((n, max(feat, 1)), seed=3).astype(np.float64)[:, :feat]
     res = oracle.render_backward(cfg, scene, cams, pix, g_rgb, g_T, g_F if feat else None)
     assert np.any(res["trans"] < 0.9)
     h = 1e-6
+    K = scene["centers"].shape[0]
     rng = np.random.RandomState(1)
-    checks = [("centers", i) for i in range(9)] + [("scales", i) for i in range(9)] + \
-             [("quats", i) for i in range(12)] + [("weights", int(i)) for i in rng.choice(3 * cfg.n_params, 40, replace=False)]
+    checks = [("centers", i) for i in range(3 * K)] + [("scales", i) for i in range(3 * K)] + \
+             [("quats", i) for i in range(4 * K)] + \
+             [("weights", int(i)) for i in rng.choice(K * cfg.n_params, 40, replace=False)]
     key = {"centers": "d_centers", "scales": "d_scales", "quats": "d_quats", "weights": "d_weights"}
-    worst = 0.0
     for name, flat in checks:
         sp = {k: v.copy() for k, v in scene.items()}
         sm = {k: v.copy() for k, v in scene.items()}
@@ -514,5 +587,46 @@ def test_gradients_central_differences(feat, xyzL):
         fd = (_loss(cfg, sp, cams, pix, g_rgb, g_T, g_F) - _loss(cfg, sm, cams, pix, g_rgb, g_T, g_F)) / (2 * h)
         an = res[key[name]].reshape(-1)[flat]
         err = abs(fd - an) / max(1e-3, abs(fd), abs(an))
-        worst = max(worst, err)
         assert err < 2e-5, (name, flat, fd, an)
+
+
+def _grad_scene(cfg):
+    scene = synth.make_scene(cfg, 13)
+    scene = {k: v.astype(np.float64) for k, v in scene.items()}
+    scene["centers"] = scene["centers"] * 0.4
+    scene["scales"] = scene["scales"] * 0.0 + np.array([[0.55, 0.4, 0.5], [0.35, 0.6, 0.45], [0.5, 0.5, 0.3]])
+    return scene
+
+
+@pytest.mark.parametrize("feat,xyzL", [(0, 6), (3, 0)])
+def test_gradients_central_differences(feat, xyzL):
+    cfg = synth.SceneConfig("g", 14, 10, 3, 1, xyzL, 2, 8, 2, feat, 4)
+    _check_central_differences(cfg, _grad_scene(cfg), [synth.make_camera(14, 10, 6, radius=2.2)])
+
+
+@pytest.mark.parametrize("feat,xyzL,dirL", [(0, 6, 6), (2, 0, 2)])
+def test_gradients_central_differences_contact_mode(feat, xyzL, dirL):
+    """Contact-point mode: delta = mu - o - max(0, t*) d adds dL/dmu directly and, through t*,
+    the chain of Eq. 2 into the pose."""
+    cfg = synth.SceneConfig("g", 14, 10, 3, 1, xyzL, dirL, 8, 2, feat, 1, contact=1)
+    _check_central_differences(cfg, _grad_scene(cfg), [synth.make_camera(14, 10, 6, radius=2.2)],
+                               contact_kink=True)
+
+
+def test_gradients_central_differences_contact_mode_camera_inside():
+    """Contact-point mode with the camera inside a primitive: rays on which t* < 0 feed
+    delta = mu - o, whose only pose gradient is the direct dL/dmu."""
+    cfg = synth.SceneConfig("g", 10, 8, 2, 1, 3, 2, 8, 2, 0, 1, contact=1)
+    cam = synth.make_camera(10, 8, 6, radius=2.2)
+    o, d = _ray_np(cam, 5, 4)
+    scene = _grad_scene(cfg.replace(K=3))
+    scene = {k: v[:2].copy() for k, v in scene.items()}
+    scene["centers"][0] = o + np.array([0.21, -0.13, 0.0]) - 0.17 * d  # centre behind the camera
+    scene["scales"][0] = [0.9, 0.8, 1.0]
+    scene["centers"][1] = o + 1.6 * d
+    m2s = []
+    for (v, x, y) in oracle.all_pixels([cam]):
+        m2, tm = oracle.ray_m2(scene, cam, x, y)
+        m2s.append(tm[0])
+    assert min(m2s) < 0  # some rays meet primitive 0 with t* < 0
+    _check_central_differences(cfg, scene, [cam], contact_kink=True)
