@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define MLPS_ABI_VERSION 2
+#define MLPS_ABI_VERSION 3
 #define MLPS_MAX_VIEWS 64
 
 typedef int32_t mlps_status;
@@ -86,7 +86,14 @@ typedef struct {
                                    tensor-core MLP (2..6 at width 64, 3 with a feature head,
                                    2 at width 128); 0 = library default. mlps_autotune_batch
                                    picks it together with `tile`. */
-  int32_t reserved[4];          /* must be zero */
+  int32_t contact;              /* 0: S midpoint samples of the local position per hit interval;
+                                   1: contact-point mode of Sec. 3.2 (Eq. 2-4): one sample per
+                                   hit (samples must be 1) whose MLP input is gamma([d; delta]),
+                                   d the unit ray direction and delta = mu - p* the offset from
+                                   the contact point p* = o + max(0, t*) d to the centre (Eq. 3);
+                                   the hit's alpha uses its chord length. FP32 only
+                                   (MLPS_ERR_UNSUPPORTED otherwise). */
+  int32_t reserved[3];          /* must be zero */
 } mlps_config;
 
 typedef struct {

@@ -39,7 +39,7 @@ class MlpsConfig(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("max_hits_per_ray", ctypes.c_int32),
                 ("hit_capacity_per_ray", ctypes.c_float), ("t_eps", ctypes.c_float),
                 ("tile", ctypes.c_int32), ("mlp_groups", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("contact", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class MlpsCamera(ctypes.Structure):

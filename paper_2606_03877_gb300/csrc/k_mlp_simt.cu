@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fwd_simt(Work w, MlpArgs a)
         const IntervalInfo& I = sI[i];
         const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
         float xl[3];
-        for (int q = 0; q < 3; ++q) xl[q] = fmaf(tr, I.dp[q], I.p[q]);
+        if (m.contact) contact_residual(w.geo[prim], I.p, I.tmid, I.d, xl);
+        else for (int q = 0; q < 3; ++q) xl[q] = fmaf(tr, I.dp[q], I.p[q]);
         encode_row(m, xl, I.d, sA, row);
       } else {
         for (int f = 0; f < m.nin; ++f) sA[f * kRows + row] = 0.f;

@@ -45,7 +45,8 @@ struct BwdPlan {
   int din_pad[kMaxLayers], dout_pad[kMaxLayers];
   int act_floats;
   int gbuf;                      // one gradient buffer [maxpad][kRS]
-  int nxyz;                      // encoded local-position features
+  int nxyz;                      // encoded local-position (contact mode: residual) features
+  int x0;                        // their first input row (after the direction in contact mode)
   int tiles;                     // total 4x4 tiles over all layers
   int tile_base[kMaxLayers + 1];
   int ni[kMaxLayers];            // input tiles per layer (ceil(din / 4))
@@ -77,6 +78,7 @@ BwdPlan make_plan(const MlpArgs& a) {
   P.act_floats = act;
   P.gbuf = maxpad * kRS;
   P.nxyz = m.xyzL > 0 ? 6 * m.xyzL : 3;
+  P.x0 = m.contact && m.dirL > 0 ? 6 * m.dirL : 0;
   P.tiles = tiles;
   return P;
 }
@@ -169,11 +171,11 @@ MLPS_DEV void dgrad_layer(const float* __restrict__ D, int dout, const float* __
 
 // First-layer input gradient, local-position part only: G[f][r] for f < nx.
 MLPS_DEV void dgrad_input(const float* __restrict__ D, int dout, const float* __restrict__ Wc,
-                          int din, int nx, float* __restrict__ G) {
+                          int din, int x0, int nx, float* __restrict__ G) {
   for (int i = threadIdx.x; i < kRB * nx; i += blockDim.x) {
     const int r = i % kRB, f = i / kRB;
     float acc = 0.f;
-    for (int o = 0; o < dout; ++o) acc = fmaf(D[o * kRS + r], Wc[o * din + f], acc);
+    for (int o = 0; o < dout; ++o) acc = fmaf(D[o * kRS + r], Wc[o * din + x0 + f], acc);
     G[f * kRS + r] = acc;
   }
 }
@@ -331,28 +333,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
           const IntervalInfo& I = sI[i];
           const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
           float xl[3];
-          for (int q = 0; q < 3; ++q) xl[q] = fmaf(tr, I.dp[q], I.p[q]);
-          // encode_row writes with stride kRows; write through a local copy instead
-          int f = 0;
-          if (m.xyzL == 0) {
-            for (int q = 0; q < 3; ++q) X0[(f++) * kRS + row] = xl[q];
-          } else {
-            for (int q = 0; q < 3; ++q)
-              for (int l = 0; l < m.xyzL; ++l) {
-                float s_, c_;
-                sincospif(ldexpf(xl[q], l), &s_, &c_);
-                X0[(f++) * kRS + row] = s_;
-                X0[(f++) * kRS + row] = c_;
-              }
-          }
-          if (m.dirL > 0)
-            for (int q = 0; q < 3; ++q)
-              for (int l = 0; l < m.dirL; ++l) {
-                float s_, c_;
-                sincospif(ldexpf(I.d[q], l), &s_, &c_);
-                X0[(f++) * kRS + row] = s_;
-                X0[(f++) * kRS + row] = c_;
-              }
+          if (m.contact) contact_residual(G, I.p, I.tmid, I.d, xl);
+          else for (int q = 0; q < 3; ++q) xl[q] = fmaf(tr, I.dp[q], I.p[q]);
+          encode_row(m, xl, I.d, X0, row, kRS);
         } else {
           for (int f = 0; f < m.nin; ++f) X0[f * kRS + row] = 0.f;
         }
@@ -487,19 +470,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
         if (l > 0) {
           dgrad_layer<TN>(D, m.dout[l], sWc + P.wc_off[l], Al, Gn);
         } else {
-          dgrad_input(D, m.dout[0], sWc + P.wc_off[0], m.din[0], P.nxyz, Gn);
+          dgrad_input(D, m.dout[0], sWc + P.wc_off[0], m.din[0], P.x0, P.nxyz, Gn);
         }
         __syncthreads();
         float* t = D; D = Gn; Gn = t;
       }
-      // D now holds dL/d(encoded local position) rows [0, nxyz)
+      // D now holds dL/d(encoded local position), or dL/d(encoded delta), rows [0, nxyz)
       // 5. encoding derivative and pose chain: warp per interval
       for (int i = warp; i < nint; i += kThreads / 32) {
         const IntervalInfo& I = sI[i];
         const int rb = i * S;
-        float sg[3] = {0.f, 0.f, 0.f}, gy[9], gt0 = 0.f, gt1 = 0.f;
+        float sg[3] = {0.f, 0.f, 0.f}, gy[9], gt0 = 0.f, gt1 = 0.f, gdel[3] = {0.f, 0.f, 0.f};
         for (int e = 0; e < 9; ++e) gy[e] = 0.f;
-        for (int k = lane; k < S; k += 32) {
+        if (m.contact && lane == 0) {
+          // delta = mu - o - max(0, t_mid) d (Eq. 3): dL/d delta from gamma's derivative
+          float del[3];
+          contact_residual(G, I.p, I.tmid, I.d, del);
+          if (m.xyzL == 0) {
+            for (int q = 0; q < 3; ++q) gdel[q] = D[q * kRS + rb];
+          } else {
+            int f = 0;
+            for (int q = 0; q < 3; ++q)
+              for (int l = 0; l < m.xyzL; ++l) {
+                float s_, c_;
+                sincospif(ldexpf(del[q], l), &s_, &c_);
+                const float wq = 3.14159265358979f * ldexpf(1.f, l);
+                gdel[q] += wq * (D[f * kRS + rb] * c_ - D[(f + 1) * kRS + rb] * s_);
+                f += 2;
+              }
+          }
+        }
+        for (int k = lane; k < S && !m.contact; k += 32) {
           const float u = ((float)k + 0.5f) / (float)S;
           const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
           float xl[3], gx[3] = {0.f, 0.f, 0.f};
@@ -538,7 +539,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
           gt1 += dDelta / (float)S;
           gt0 -= dDelta / (float)S;
           const bool clamped = I.r0 != -I.r1;
-          const float gtm = gt1 + (clamped ? 0.f : gt0);
+          // contact mode: t* = t_mid when t_mid > 0 moves p* along d
+          const float gtd = I.tmid > 0.f ? -(gdel[0] * I.d[0] + gdel[1] * I.d[1] + gdel[2] * I.d[2]) : 0.f;
+          const float gtm = gt1 + (clamped ? 0.f : gt0) + gtd;
           const float gh = gt1 - (clamped ? 0.f : gt0);
           const float aa = I.dp[0] * I.dp[0] + I.dp[1] * I.dp[1] + I.dp[2] * I.dp[2];
           const float hh = I.r1;
@@ -552,11 +555,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
           for (int q = 0; q < 3; ++q)
             for (int e = 0; e < 3; ++e)
               atomicAdd(&sGeo[q * 3 + e], gy[q * 3 + e] + go[q] * ymid[e] + cd[q] * I.d[e]);
-          // dmu = -M^T (sum g + g_o')
+          // dmu = -M^T (sum g + g_o') (+ dL/d delta in contact mode)
           for (int e = 0; e < 3; ++e) {
             float acc2 = 0.f;
             for (int q = 0; q < 3; ++q) acc2 += G.Mhi[q * 3 + e] * (sg[q] + go[q]);
-            atomicAdd(&sGeo[9 + e], -acc2);
+            atomicAdd(&sGeo[9 + e], gdel[e] - acc2);
           }
         }
       }

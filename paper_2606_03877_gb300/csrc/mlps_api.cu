@@ -86,8 +86,9 @@ mlps_status check_cfg(const mlps_config* c) {
   if (!finite_f(c->hit_capacity_per_ray) || !(c->hit_capacity_per_ray > 0.f))
     return MLPS_ERR_INVALID_ARGUMENT;
   if (!finite_f(c->t_eps) || c->t_eps < 0.f || c->t_eps >= 1.f) return MLPS_ERR_INVALID_ARGUMENT;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (c->reserved[i] != 0) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->contact != 0 && (c->contact != 1 || c->samples != 1)) return MLPS_ERR_INVALID_ARGUMENT;
   if (c->mlp_groups != 0 && (c->mlp_groups < 2 || c->mlp_groups > 6)) return MLPS_ERR_INVALID_ARGUMENT;
   if (c->hidden_width != 32 && c->hidden_width != 64 && c->hidden_width != 128)
     return MLPS_ERR_UNSUPPORTED;
@@ -109,6 +110,7 @@ Model make_model(const mlps_config* c) {
   m.F = c->feat_dim;
   m.xyzL = c->xyz_freqs;
   m.dirL = c->dir_freqs;
+  m.contact = c->contact;
   int off = 0;
   for (int l = 0; l < m.nl; ++l) {
     m.din[l] = l == 0 ? m.nin : m.width;
@@ -589,6 +591,7 @@ mlps_status mlps_check_config(const mlps_config* cfg) {
   mlps_status s = check_cfg(cfg);
   if (s != MLPS_OK) return s;
   if (cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3) {
+    if (cfg->contact) return MLPS_ERR_UNSUPPORTED;  // the tensor-core encoders take x' only
     TcPlan P;
     long long stride;
     const Model m = make_model(cfg);

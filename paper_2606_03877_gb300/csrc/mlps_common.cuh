@@ -211,6 +211,7 @@ struct Model {
   int S;            // samples per interval
   int F;            // feature outputs
   int xyzL, dirL;   // encoding frequencies
+  int contact;      // 1: contact-point input gamma([d; delta]), S = 1 (Sec. 3.2)
   int P;            // canonical params per primitive
   int din[kMaxLayers], dout[kMaxLayers];
   int woff[kMaxLayers], boff[kMaxLayers];

@@ -85,28 +85,47 @@ MLPS_DEV void run_layer(const Model& m, int l, const float* X, const float* Wt, 
   else dense_small(X, m.din[l], Wt, b, m.dout[l], Y);
 }
 
-// Encoding gamma (Eq. 5) of one sample into column `row` of X ([feature][kRows]).
-MLPS_DEV void encode_row(const Model& m, const float xl[3], const float d[3], float* X, int row) {
-  int f = 0;
-  if (m.xyzL == 0) {
-    for (int c = 0; c < 3; ++c) X[(f++) * kRows + row] = xl[c];
-  } else {
-    for (int c = 0; c < 3; ++c)
-      for (int l = 0; l < m.xyzL; ++l) {
-        float s, co;
-        sincospif(ldexpf(xl[c], l), &s, &co);
-        X[(f++) * kRows + row] = s;
-        X[(f++) * kRows + row] = co;
-      }
+// gamma (Eq. 5) of one 3-vector with L frequencies (raw when L = 0) into rows f.. of column
+// `row` of X ([feature][stride]); returns the next free feature row.
+MLPS_DEV int encode_vec(int L, const float v[3], float* X, int row, int stride, int f) {
+  if (L == 0) {
+    for (int c = 0; c < 3; ++c) X[(f++) * stride + row] = v[c];
+    return f;
   }
-  if (m.dirL > 0)
-    for (int c = 0; c < 3; ++c)
-      for (int l = 0; l < m.dirL; ++l) {
-        float s, co;
-        sincospif(ldexpf(d[c], l), &s, &co);
-        X[(f++) * kRows + row] = s;
-        X[(f++) * kRows + row] = co;
-      }
+  for (int c = 0; c < 3; ++c)
+    for (int l = 0; l < L; ++l) {
+      float s, co;
+      sincospif(ldexpf(v[c], l), &s, &co);
+      X[(f++) * stride + row] = s;
+      X[(f++) * stride + row] = co;
+    }
+  return f;
+}
+
+// Encoding of one sample into column `row` of X ([feature][stride]): gamma(x') then gamma(d)
+// (Eq. 5), or in contact-point mode gamma(d) then gamma(delta) (Eq. 4), `xl` holding delta.
+MLPS_DEV void encode_row(const Model& m, const float xl[3], const float d[3], float* X, int row,
+                         int stride = kRows) {
+  if (m.contact) {
+    const int f = m.dirL > 0 ? encode_vec(m.dirL, d, X, row, stride, 0) : 0;
+    encode_vec(m.xyzL, xl, X, row, stride, f);
+    return;
+  }
+  const int f = encode_vec(m.xyzL, xl, X, row, stride, 0);
+  if (m.dirL > 0) encode_vec(m.dirL, d, X, row, stride, f);
+}
+
+// Contact-point residual delta = mu - p* with p* = o + max(0, t_mid) d (Eq. 3), from the
+// interval's closest point p = M (o + t_mid d - mu) in the normalised frame: R S p is the world
+// offset o + t_mid d - mu, so delta = -R S p + min(t_mid, 0) d, free of the cancellation of
+// mu - o - t* d.
+MLPS_DEV void contact_residual(const PrimGeo& G, const float p[3], float tmid, const float d[3],
+                               float delta[3]) {
+  const float tn = fminf(tmid, 0.f);
+  for (int q = 0; q < 3; ++q) {
+    const float y = G.R[q * 3] * G.s[0] * p[0] + G.R[q * 3 + 1] * G.s[1] * p[1] + G.R[q * 3 + 2] * G.s[2] * p[2];
+    delta[q] = fmaf(tn, d[q], -y);
+  }
 }
 
 MLPS_DEV float sigmoidf_acc(float z) { return 1.0f / (1.0f + expf(-z)); }

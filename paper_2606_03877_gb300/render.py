@@ -15,7 +15,7 @@ from . import _lib
 def make_config(shape, precision: str = "fp32", t_eps: float = 1e-6, max_hits: int = 64,
                 hit_capacity: float = 8.0, tile: int = 16, mlp_groups: int = 0) -> _lib.MlpsConfig:
     """mlps_config from any object with xyz_freqs, dir_freqs, hidden_width, hidden_layers,
-    feat_dim and samples (e.g. :class:`synth.SceneConfig`)."""
+    feat_dim, samples and optionally contact (e.g. :class:`synth.SceneConfig`)."""
     cfg = _lib.mlps_config_default(int(shape.xyz_freqs), int(shape.dir_freqs), int(shape.hidden_width),
                                    int(shape.hidden_layers), int(shape.feat_dim))
     cfg.samples = int(shape.samples)
@@ -25,6 +25,7 @@ def make_config(shape, precision: str = "fp32", t_eps: float = 1e-6, max_hits: i
     cfg.hit_capacity_per_ray = float(hit_capacity)
     cfg.tile = int(tile)
     cfg.mlp_groups = int(mlp_groups)
+    cfg.contact = int(getattr(shape, "contact", 0))
     return cfg
 
 

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert _lib.mlps_abi_version() == 2
+    assert _lib.mlps_abi_version() == 3
     for s in range(8):
         assert _lib.mlps_status_string(s)
     assert _lib.mlps_status_string(4) == "hit capacity overflow"
@@ -128,6 +128,20 @@ def test_batch_item_validation(lib):
     # mixed resolutions are allowed in a batch
     big = dict(cams[1], width=128, height=96, cx=64.0, cy=48.0)
     _lib.mlps_batch_workspace_size(cfg, 30, _lib.batch_items([(0, 10, cams[0]), (10, 20, big)]), 2)
+
+
+def test_contact_mode_validation(lib):
+    """Contact-point mode (Sec. 3.2) takes one sample per hit and runs on the FP32 path."""
+    c = synth.CONFIGS["contact"]
+    assert _lib.mlps_check_config(make_config(c)) == _lib.MLPS_OK
+    assert _lib.mlps_check_config(make_config(c.replace(samples=2))) == _lib.MLPS_ERR_INVALID_ARGUMENT
+    cfg = make_config(c)
+    cfg.contact = 2
+    assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_INVALID_ARGUMENT
+    for prec in ("bf16", "fp8"):
+        assert _lib.mlps_check_config(make_config(c.replace(hidden_width=64), prec)) == \
+            _lib.MLPS_ERR_UNSUPPORTED
+    assert _lib.mlps_param_count(make_config(c)) == 72 * 32 + 32 + 32 * 32 + 32 + 32 * 4 + 4
 
 
 def test_mlp_groups_validation(lib):
