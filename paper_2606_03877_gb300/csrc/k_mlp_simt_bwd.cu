@@ -206,6 +206,96 @@ MLPS_DEV float warp_excl_suffix(float v, int lane) {  // sum over higher lanes
   return incl - v;
 }
 
+// Per-interval sums of the chain from the encoded inputs to the pose: sum_k g_k, sum_k g_k y_k^T,
+// the t0 / t1 weights of the sample positions (midpoint mode), and dL/d delta (contact mode).
+struct ChainAcc {
+  float sg[3], gy[9], gt0, gt1, gdel[3];
+};
+
+MLPS_DEV void chain_zero(ChainAcc& c) {
+  for (int q = 0; q < 3; ++q) c.sg[q] = c.gdel[q] = 0.f;
+  for (int e = 0; e < 9; ++e) c.gy[e] = 0.f;
+  c.gt0 = c.gt1 = 0.f;
+}
+
+// d gamma(v) / d v applied to rows [f0, f0 + 6 L) (or 3 raw rows) of column `col` of D.
+MLPS_DEV void encode_grad(int L, const float v[3], const float* D, int col, float g[3]) {
+  if (L == 0) {
+    for (int q = 0; q < 3; ++q) g[q] = D[q * kRS + col];
+    return;
+  }
+  int f = 0;
+  for (int q = 0; q < 3; ++q) {
+    g[q] = 0.f;
+    for (int l = 0; l < L; ++l) {
+      float s_, c_;
+      sincospif(ldexpf(v[q], l), &s_, &c_);
+      const float wq = 3.14159265358979f * ldexpf(1.f, l);
+      g[q] += wq * (D[f * kRS + col] * c_ - D[(f + 1) * kRS + col] * s_);
+      f += 2;
+    }
+  }
+}
+
+// Sample k of S (column `col` of D) in midpoint mode: x'_k = p + (r0 + (k + 1/2) Delta) d'.
+MLPS_DEV void chain_sample(const Model& m, const PrimGeo& G, const IntervalInfo& I, const float* D,
+                           int col, int k, int S, ChainAcc& c) {
+  const float u = ((float)k + 0.5f) / (float)S;
+  const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+  float xl[3], gx[3];
+  for (int q = 0; q < 3; ++q) xl[q] = fmaf(tr, I.dp[q], I.p[q]);
+  encode_grad(m.xyzL, xl, D, col, gx);
+  // y = R S x' (offset of the sample from the centre, world frame)
+  float y[3];
+  for (int q = 0; q < 3; ++q)
+    y[q] = G.R[q * 3] * G.s[0] * xl[0] + G.R[q * 3 + 1] * G.s[1] * xl[1] + G.R[q * 3 + 2] * G.s[2] * xl[2];
+  const float gt = gx[0] * I.dp[0] + gx[1] * I.dp[1] + gx[2] * I.dp[2];
+  c.gt0 = fmaf(gt, 1.f - u, c.gt0);
+  c.gt1 = fmaf(gt, u, c.gt1);
+  for (int q = 0; q < 3; ++q) {
+    c.sg[q] += gx[q];
+    for (int e = 0; e < 3; ++e) c.gy[q * 3 + e] = fmaf(gx[q], y[e], c.gy[q * 3 + e]);
+  }
+}
+
+// Contact mode: delta = mu - o - max(0, t_mid) d (Eq. 3), dL/d delta from gamma's derivative.
+MLPS_DEV void chain_contact(const Model& m, const PrimGeo& G, const IntervalInfo& I, const float* D,
+                            int col, ChainAcc& c) {
+  float del[3];
+  contact_residual(G, I.p, I.tmid, I.d, del);
+  encode_grad(m.xyzL, del, D, col, c.gdel);
+}
+
+// The interval's 12 pose-gradient contributions (dL/dM row-major, then dL/dmu) from the summed
+// chain, dL/dDelta and the geometry of the interval (the formulas in the file header).
+MLPS_DEV void chain_pose(const PrimGeo& G, const IntervalInfo& I, const ChainAcc& c, float dDelta,
+                         int S, float out[12]) {
+  const float gt1 = c.gt1 + dDelta / (float)S;
+  const float gt0 = c.gt0 - dDelta / (float)S;
+  const bool clamped = I.r0 != -I.r1;
+  // contact mode: t* = t_mid when t_mid > 0 moves p* along d
+  const float gtd = I.tmid > 0.f ? -(c.gdel[0] * I.d[0] + c.gdel[1] * I.d[1] + c.gdel[2] * I.d[2]) : 0.f;
+  const float gtm = gt1 + (clamped ? 0.f : gt0) + gtd;
+  const float gh = gt1 - (clamped ? 0.f : gt0);
+  const float aa = I.dp[0] * I.dp[0] + I.dp[1] * I.dp[1] + I.dp[2] * I.dp[2];
+  const float hh = I.r1;
+  float go[3], ymid[3], cd[3];
+  for (int q = 0; q < 3; ++q) {
+    go[q] = -gtm * I.dp[q] / aa - (hh > 0.f ? gh * I.p[q] / (aa * hh) : 0.f);
+    cd[q] = -(gtm * I.p[q] / aa + gh * hh * I.dp[q] / aa);
+  }
+  for (int q = 0; q < 3; ++q)
+    ymid[q] = G.R[q * 3] * G.s[0] * I.p[0] + G.R[q * 3 + 1] * G.s[1] * I.p[1] + G.R[q * 3 + 2] * G.s[2] * I.p[2];
+  for (int q = 0; q < 3; ++q)
+    for (int e = 0; e < 3; ++e) out[q * 3 + e] = c.gy[q * 3 + e] + go[q] * ymid[e] + cd[q] * I.d[e];
+  // dmu = -M^T (sum g + g_o') (+ dL/d delta in contact mode)
+  for (int e = 0; e < 3; ++e) {
+    float acc2 = 0.f;
+    for (int q = 0; q < 3; ++q) acc2 += G.Mhi[q * 3 + e] * (c.sg[q] + go[q]);
+    out[9 + e] = c.gdel[e] - acc2;
+  }
+}
+
 }  // namespace
 
 template <int TN>
@@ -350,9 +440,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
         else fwd_small(Xl, m.din[l], Wt, bb, m.dout[l], sZ);
         __syncthreads();
       }
-      // 3. reverse of the interval composite: warp per interval -> dZ in sG0
+      // 3. reverse of the interval composite -> dZ in sG0: thread per interval for S = 1
+      //    (tau = 1 and no later samples inside the interval), else warp per interval
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      for (int i = warp; i < nint; i += kThreads / 32) {
+      if (S == 1 && threadIdx.x < nint) {
+        const int i = threadIdx.x;
+        const float dt = sI[i].dt;
+        const float4 g = sGrad[i];
+        const float* gF = sGF + i * F;
+        const float zs = sZ[3 * kRS + i];
+        const float sig = softplusf_acc(zs);
+        const float ak = sig * dt;
+        const float ea = expf(-ak);
+        const float wk = -expm1f(-ak);
+        float cq[3];
+        for (int q = 0; q < 3; ++q) cq[q] = sigmoidf_acc(sZ[q * kRS + i]);
+        float ga = g.w;
+        ga += g.x * (ea * cq[0]) + g.y * (ea * cq[1]) + g.z * (ea * cq[2]);
+        for (int f = 0; f < F; ++f) {
+          ga += gF[f] * (ea * sZ[(4 + f) * kRS + i]);
+          sG0[(4 + f) * kRS + i] = wk * gF[f];
+        }
+        const float gcs[3] = {g.x, g.y, g.z};
+        for (int q = 0; q < 3; ++q) sG0[q * kRS + i] = wk * gcs[q] * cq[q] * (1.f - cq[q]);
+        sG0[3 * kRS + i] = ga * dt * sigmoidf_acc(zs);
+        sGrad[i].w = ga * sig;  // from here on: dL/dDelta of the interval
+      }
+      for (int i = warp; i < nint && S > 1; i += kThreads / 32) {
         const IntervalInfo& I = sI[i];
         const float4 g = sGrad[i];
         const float* gF = sGF + i * F;
@@ -476,90 +590,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
         float* t = D; D = Gn; Gn = t;
       }
       // D now holds dL/d(encoded local position), or dL/d(encoded delta), rows [0, nxyz)
-      // 5. encoding derivative and pose chain: warp per interval
-      for (int i = warp; i < nint; i += kThreads / 32) {
-        const IntervalInfo& I = sI[i];
-        const int rb = i * S;
-        float sg[3] = {0.f, 0.f, 0.f}, gy[9], gt0 = 0.f, gt1 = 0.f, gdel[3] = {0.f, 0.f, 0.f};
-        for (int e = 0; e < 9; ++e) gy[e] = 0.f;
-        if (m.contact && lane == 0) {
-          // delta = mu - o - max(0, t_mid) d (Eq. 3): dL/d delta from gamma's derivative
-          float del[3];
-          contact_residual(G, I.p, I.tmid, I.d, del);
-          if (m.xyzL == 0) {
-            for (int q = 0; q < 3; ++q) gdel[q] = D[q * kRS + rb];
-          } else {
-            int f = 0;
-            for (int q = 0; q < 3; ++q)
-              for (int l = 0; l < m.xyzL; ++l) {
-                float s_, c_;
-                sincospif(ldexpf(del[q], l), &s_, &c_);
-                const float wq = 3.14159265358979f * ldexpf(1.f, l);
-                gdel[q] += wq * (D[f * kRS + rb] * c_ - D[(f + 1) * kRS + rb] * s_);
-                f += 2;
-              }
+      // 5. encoding derivative and pose chain: thread per interval for S = 1 (warp sums of
+      //    the 12 contributions), else warp per interval with a lane per sample
+      if (S == 1) {
+        if (warp * 32 < nint) {
+          const int i = threadIdx.x;
+          float out[12];
+          for (int e = 0; e < 12; ++e) out[e] = 0.f;
+          if (i < nint) {
+            const IntervalInfo& I = sI[i];
+            ChainAcc c;
+            chain_zero(c);
+            if (m.contact) chain_contact(m, G, I, D, i, c);
+            else chain_sample(m, G, I, D, i, 0, 1, c);
+            chain_pose(G, I, c, sGrad[i].w, 1, out);
+          }
+          for (int e = 0; e < 12; ++e) {
+            const float v = warp_sum(out[e]);
+            if (lane == 0) atomicAdd(&sGeo[e], v);
           }
         }
-        for (int k = lane; k < S && !m.contact; k += 32) {
-          const float u = ((float)k + 0.5f) / (float)S;
-          const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
-          float xl[3], gx[3] = {0.f, 0.f, 0.f};
-          for (int q = 0; q < 3; ++q) xl[q] = fmaf(tr, I.dp[q], I.p[q]);
-          if (m.xyzL == 0) {
-            for (int q = 0; q < 3; ++q) gx[q] = D[q * kRS + rb + k];
-          } else {
-            int f = 0;
-            for (int q = 0; q < 3; ++q)
-              for (int l = 0; l < m.xyzL; ++l) {
-                float s_, c_;
-                sincospif(ldexpf(xl[q], l), &s_, &c_);
-                const float wq = 3.14159265358979f * ldexpf(1.f, l);
-                gx[q] += wq * (D[f * kRS + rb + k] * c_ - D[(f + 1) * kRS + rb + k] * s_);
-                f += 2;
-              }
-          }
-          // y = R S x' (offset of the sample from the centre, world frame)
-          float y[3];
-          for (int q = 0; q < 3; ++q)
-            y[q] = G.R[q * 3] * G.s[0] * xl[0] + G.R[q * 3 + 1] * G.s[1] * xl[1] + G.R[q * 3 + 2] * G.s[2] * xl[2];
-          const float gt = gx[0] * I.dp[0] + gx[1] * I.dp[1] + gx[2] * I.dp[2];
-          gt0 = fmaf(gt, 1.f - u, gt0);
-          gt1 = fmaf(gt, u, gt1);
-          for (int q = 0; q < 3; ++q) {
-            sg[q] += gx[q];
-            for (int e = 0; e < 3; ++e) gy[q * 3 + e] = fmaf(gx[q], y[e], gy[q * 3 + e]);
-          }
-        }
-        for (int q = 0; q < 3; ++q) sg[q] = warp_sum(sg[q]);
-        for (int e = 0; e < 9; ++e) gy[e] = warp_sum(gy[e]);
-        gt0 = warp_sum(gt0);
-        gt1 = warp_sum(gt1);
-        if (lane == 0) {
-          const float dDelta = sGrad[i].w;
-          gt1 += dDelta / (float)S;
-          gt0 -= dDelta / (float)S;
-          const bool clamped = I.r0 != -I.r1;
-          // contact mode: t* = t_mid when t_mid > 0 moves p* along d
-          const float gtd = I.tmid > 0.f ? -(gdel[0] * I.d[0] + gdel[1] * I.d[1] + gdel[2] * I.d[2]) : 0.f;
-          const float gtm = gt1 + (clamped ? 0.f : gt0) + gtd;
-          const float gh = gt1 - (clamped ? 0.f : gt0);
-          const float aa = I.dp[0] * I.dp[0] + I.dp[1] * I.dp[1] + I.dp[2] * I.dp[2];
-          const float hh = I.r1;
-          float go[3], ymid[3], cd[3];
-          for (int q = 0; q < 3; ++q) {
-            go[q] = -gtm * I.dp[q] / aa - (hh > 0.f ? gh * I.p[q] / (aa * hh) : 0.f);
-            cd[q] = -(gtm * I.p[q] / aa + gh * hh * I.dp[q] / aa);
-          }
-          for (int q = 0; q < 3; ++q)
-            ymid[q] = G.R[q * 3] * G.s[0] * I.p[0] + G.R[q * 3 + 1] * G.s[1] * I.p[1] + G.R[q * 3 + 2] * G.s[2] * I.p[2];
-          for (int q = 0; q < 3; ++q)
-            for (int e = 0; e < 3; ++e)
-              atomicAdd(&sGeo[q * 3 + e], gy[q * 3 + e] + go[q] * ymid[e] + cd[q] * I.d[e]);
-          // dmu = -M^T (sum g + g_o') (+ dL/d delta in contact mode)
-          for (int e = 0; e < 3; ++e) {
-            float acc2 = 0.f;
-            for (int q = 0; q < 3; ++q) acc2 += G.Mhi[q * 3 + e] * (sg[q] + go[q]);
-            atomicAdd(&sGeo[9 + e], gdel[e] - acc2);
+      } else {
+        for (int i = warp; i < nint; i += kThreads / 32) {
+          const IntervalInfo& I = sI[i];
+          const int rb = i * S;
+          ChainAcc c;
+          chain_zero(c);
+          for (int k = lane; k < S; k += 32) chain_sample(m, G, I, D, rb + k, k, S, c);
+          for (int q = 0; q < 3; ++q) c.sg[q] = warp_sum(c.sg[q]);
+          for (int e = 0; e < 9; ++e) c.gy[e] = warp_sum(c.gy[e]);
+          c.gt0 = warp_sum(c.gt0);
+          c.gt1 = warp_sum(c.gt1);
+          if (lane == 0) {
+            float out[12];
+            chain_pose(G, I, c, sGrad[i].w, S, out);
+            for (int e = 0; e < 12; ++e) atomicAdd(&sGeo[e], out[e]);
           }
         }
       }

@@ -141,8 +141,9 @@ CONFIGS: Dict[str, SceneConfig] = {
     "diff": SceneConfig("diff", 800, 800, 64, 1, 6, 4, 64, 3, 0, 32, "fp32"),
     "prec": SceneConfig("prec", 1920, 1080, 256, 8, 6, 4, 64, 3, 0, 32, "bf16"),
     "stress": SceneConfig("stress", 1920, 1080, 1024, 4, 6, 4, 128, 4, 16, 48, "fp8"),
-    # the paper's own per-primitive model: gamma([d; delta]) with L = 6 (72 inputs), 32 x 2, S = 1
-    "contact": SceneConfig("contact", 800, 800, 64, 1, 6, 6, 32, 2, 0, 1, "fp32", 1),
+    # the paper's own per-primitive model: gamma([d; delta]) with L = 6 (72 inputs), 32 x 2, S = 1,
+    # on the views and primitives of the precision workload
+    "contact": SceneConfig("contact", 1920, 1080, 256, 8, 6, 6, 32, 2, 0, 1, "fp32", 1),
 }
 
 # Batched workload: 32 scenes, K ~ U{16..512}, resolution uniform over these four.

@@ -113,13 +113,44 @@ def test_contact_gradients_camera_inside():
     _grad_check(cfg, _inside_scene(cfg, cam), [cam])
 
 
+def test_midpoint_mode_single_sample_gradients():
+    """S = 1 without the contact input (one midpoint sample per hit at t*): the thread-per-
+    interval reverse of the FP32 backward against the oracle."""
+    cfg = CONTACT.replace(width=80, height=60, K=14, n_views=1, contact=0, xyz_freqs=4, dir_freqs=2)
+    _grad_check(cfg, scaled_scene(cfg, 9, 2.0), synth.make_cameras(cfg, first_view_seed=9))
+
+
 def test_contact_full_size_sampled():
-    """800 x 800, K = 64 (the contact workload): colour and T on sampled pixels."""
+    """1920 x 1080 x 8 views, K = 256 (the contact workload): colour and T on sampled pixels."""
     cfg = CONTACT
     scene = synth.make_scene(cfg, 0)
     cams = synth.make_cameras(cfg)
     pix = synth.sample_pixels(cfg, 3000, seed=17)
     print("contact full-size sampled max err", _forward_check(cfg, scene, cams, pix=pix))
+
+
+def test_contact_equals_midpoint_mode_when_the_mlp_ignores_its_input():
+    """S = 1, W_0 = 0: both modes evaluate the same input-independent MLP once per hit, so the
+    images are bit-identical and the pose gradients agree."""
+    cfg = CONTACT.replace(width=64, height=48, K=12, n_views=1)
+    scene = scaled_scene(cfg, 8, 2.0)
+    n0 = cfg.layer_dims()[0][0] * cfg.layer_dims()[0][1]
+    scene["weights"] = scene["weights"].copy()
+    scene["weights"][:, :n0] = 0.0
+    cams = synth.make_cameras(cfg, first_view_seed=8)
+    g = torch.from_numpy(synth.make_grad((1, cfg.height, cfg.width, 3), seed=8)).cuda()
+    res = []
+    for c in (cfg, cfg.replace(contact=0)):
+        r, o, _, _ = gpu_render(c, scene, cams, "fp32")
+        gr = r.backward(g)
+        torch.cuda.synchronize()
+        assert r.status("scratch") == 0
+        res.append((o, {k: v.cpu().numpy() for k, v in gr.items()}))
+    (o1, g1), (o0, g0) = res
+    assert np.array_equal(o1["rgb"], o0["rgb"]) and np.array_equal(o1["trans"], o0["trans"])
+    for k in ("d_centers", "d_scales", "d_quats"):
+        assert rel_l2(g1[k], g0[k]) < 1e-5, k
+    assert rel_l2(g1["d_weights"][:, n0:], g0["d_weights"][:, n0:]) < 1e-5
 
 
 def test_contact_differs_from_midpoint_sampling():

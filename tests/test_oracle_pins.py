@@ -367,6 +367,31 @@ def test_contact_mode_matches_independent_restatement(xyzL, dirL, width, layers,
     assert neg > 20
 
 
+def test_contact_mode_reduces_to_midpoint_mode_when_the_mlp_ignores_its_input():
+    """With S = 1 and a zero first-layer weight matrix the MLP output no longer depends on its
+    input, so the contact-point mode and the midpoint mode (whose one sample is also at t*) must
+    give the same image bit for bit, and the same gradients for every parameter but W_0."""
+    cfg = synth.SceneConfig("k", 20, 14, 10, 1, 6, 6, 16, 2, 0, 1, contact=1)
+    scene = synth.make_scene(cfg, 9)
+    scene = dict(scene, scales=scene["scales"] * 2.0)
+    ws, bs, _, _ = _layout(cfg)[0]
+    scene["weights"] = scene["weights"].copy()
+    scene["weights"][:, ws] = 0.0
+    scene["weights"][:, bs] = np.linspace(-0.5, 0.5, bs.stop - bs.start)
+    cam = synth.make_camera(20, 14, 4, radius=3.0)
+    rgb1, T1, _ = oracle.render(cfg, scene, [cam])
+    rgb0, T0, _ = oracle.render(cfg.replace(contact=0), scene, [cam])
+    assert np.array_equal(rgb1, rgb0) and np.array_equal(T1, T0) and T1.min() < 0.9
+    pix = oracle.all_pixels([cam])
+    g = synth.make_grad((pix.shape[0], 3), seed=3).astype(np.float64)
+    r1 = oracle.render_backward(cfg, scene, [cam], pix, g)
+    r0 = oracle.render_backward(cfg.replace(contact=0), scene, [cam], pix, g)
+    for k in ("d_centers", "d_scales", "d_quats"):
+        assert np.allclose(r1[k], r0[k], rtol=1e-12, atol=1e-14), k
+    assert np.allclose(r1["d_weights"][:, bs.start:], r0["d_weights"][:, bs.start:], rtol=1e-12, atol=1e-14)
+    assert not np.allclose(r1["d_weights"][:, ws], r0["d_weights"][:, ws])  # the inputs differ
+
+
 def test_contact_mode_single_sample_and_input_dim():
     """Contact-point mode needs S = 1 and keeps the 72-wide input of Sec. 4.1 at L = 6."""
     cfg = synth.CONFIGS["contact"]
