@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: the test suite, the package smoke check and the benchm
 CPU-baseline leg are the only callers. The CUDA library and its Python binding never import
 this package, and this package imports nothing from them: configs are taken by duck typing
 (any object with ``xyz_freqs, dir_freqs, hidden_width, hidden_layers, feat_dim, samples`` and
-an optional ``contact``) and
+optional ``contact`` and ``slot_dim``) and
 scenes / cameras as plain numpy arrays and dicts.
 
 All inputs are converted to float64 before the call; outputs are float64.
@@ -30,7 +30,7 @@ _lib = None
 class _Cfg(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("xyz_freqs", "dir_freqs", "hidden_width", "hidden_layers", "feat_dim", "samples",
-                 "contact")]
+                 "contact", "slot_dim")]
 
 
 class _Cam(ctypes.Structure):
@@ -75,13 +75,15 @@ def _load():
             lib.orc_pixel_ray.argtypes = [P(_Cam), ctypes.c_int, ctypes.c_int, d, d]
             lib.orc_encode.argtypes = [P(_Cfg), d, d, d]
             lib.orc_mlp.argtypes = [P(_Cfg), d, d, d]
+            lib.orc_slot_weights.argtypes = [d, d]
             _lib = lib
     return _lib
 
 
 def _cfg(c) -> _Cfg:
     return _Cfg(int(c.xyz_freqs), int(c.dir_freqs), int(c.hidden_width), int(c.hidden_layers),
-                int(c.feat_dim), int(c.samples), int(getattr(c, "contact", 0)))
+                int(c.feat_dim), int(c.samples), int(getattr(c, "contact", 0)),
+                int(getattr(c, "slot_dim", 0)))
 
 
 def _cam(c: Dict) -> _Cam:
@@ -127,21 +129,40 @@ def param_count(cfg) -> int:
     return int(_load().orc_param_count(ctypes.byref(_cfg(cfg))))
 
 
+def _feat_width(cfg) -> int:
+    return int(cfg.feat_dim) + int(getattr(cfg, "slot_dim", 0))
+
+
+def _weights(cfg, scene, K) -> np.ndarray:
+    w = _f64(scene["weights"]).reshape(K, -1) if K > 0 else np.zeros((0, param_count(cfg)))
+    if w.shape[1] != param_count(cfg):
+        raise ValueError(f"weights have {w.shape[1]} parameters per primitive, the config {param_count(cfg)}")
+    return np.ascontiguousarray(w)
+
+
+def slot_weights(u) -> np.ndarray:
+    """softmax_k(a_k . u) over the four tetrahedral directions (Sec. 3.4)."""
+    g = np.zeros(4)
+    _load().orc_slot_weights(_dp(_f64(u)), _dp(g))
+    return g
+
+
 def render(cfg, scene, cams: Sequence[Dict], pix: Optional[np.ndarray] = None, n_threads: int = 0):
     """Render listed pixels (int32 [n, 3] of (view, x, y); all pixels when None).
 
-    Returns (rgb [n, 3], trans [n], feat [n, F] or None) in float64."""
+    Returns (rgb [n, 3], trans [n], feat [n, F + slot_dim] or None) in float64: the MLP's extra
+    outputs, then the slot features."""
     lib = _load()
     if pix is None:
         pix = all_pixels(cams)
     pix = np.ascontiguousarray(pix, dtype=np.int32)
     n = pix.shape[0]
     c, s, q = _geom(scene)
-    w = _f64(scene["weights"])
+    w = _weights(cfg, scene, c.shape[0])
     K = c.shape[0]
     rgb = np.zeros((n, 3))
     trans = np.zeros(n)
-    F = int(cfg.feat_dim)
+    F = _feat_width(cfg)
     feat = np.zeros((n, F)) if F > 0 else None
     cam_arr = _cams(cams)
     st = lib.orc_render(ctypes.byref(_cfg(cfg)), K, _dp(c), _dp(s), _dp(q), _dp(w), len(cams), cam_arr,
@@ -163,12 +184,12 @@ def render_backward(cfg, scene, cams: Sequence[Dict], pix: Optional[np.ndarray],
     pix = np.ascontiguousarray(pix, dtype=np.int32)
     n = pix.shape[0]
     c, s, q = _geom(scene)
-    w = _f64(scene["weights"])
     K = c.shape[0]
-    P = w.shape[1] if w.ndim == 2 else 0
+    w = _weights(cfg, scene, K)
+    P = w.shape[1]
     gr = _f64(g_rgb).reshape(n, 3)
     gt = None if g_trans is None else _f64(g_trans).reshape(n)
-    F = int(cfg.feat_dim)
+    F = _feat_width(cfg)
     gf = None if (g_feat is None or F == 0) else _f64(g_feat).reshape(n, F)
     rgb = np.zeros((n, 3)); trans = np.zeros(n)
     feat = np.zeros((n, F)) if F > 0 else None

@@ -41,6 +41,14 @@
  * encoded by gamma (L = dir_freqs for d, xyz_freqs for delta; 0 = raw). The alpha of the hit is
  * still 1 - exp(-sigma * chord length).
  *
+ * Feature slots (slot_dim = C > 0, Sec. 3.4): every primitive also carries four slot embeddings
+ * e_k in R^C, stored after its MLP parameters. A hit's slot feature is f = sum_k g_k e_k with
+ * g = softmax_k(a_k . u), u = clip_[-1,1]^3(R^T delta / s) the scale-normalised offset of the
+ * centre from the contact point (delta = mu - p* as above) and a_k the unit vertices of a
+ * regular tetrahedron. The rendered slot feature map is F_slot = sum_i w_i f_i with w_i the
+ * hit's compositing weight (the sum of T alpha over its samples; T_i alpha_i for S = 1). It is
+ * returned after the MLP's extra outputs.
+ *
  * Readings of points the paper leaves open (scalar delta of Eq. 6 = the sample step, support
  * = unit-Mahalanobis ellipsoid, falloff off, interval-by-interval compositing, tie-break,
  * camera model, background) are listed with the design notes of the repository.
@@ -64,6 +72,7 @@ typedef struct {
   int feat_dim;      /* extra linear outputs, composited like colour */
   int samples;       /* S midpoint samples per hit interval */
   int contact;       /* 1: contact-point mode (S = 1, input gamma([d; delta])) */
+  int slot_dim;      /* C of the four slot embeddings per primitive (Sec. 3.4); 0 = none */
 } orc_cfg;
 
 typedef struct {
@@ -99,7 +108,7 @@ long orc_param_count(const orc_cfg* c) {
     layer_dims(c, l, &fi, &fo);
     n += (long)fi * fo + fo;
   }
-  return n;
+  return n + 4L * c->slot_dim;
 }
 
 static int cfg_valid(const orc_cfg* c) {
@@ -107,6 +116,7 @@ static int cfg_valid(const orc_cfg* c) {
       c->feat_dim < 0 || c->samples <= 0)
     return 0;
   if (c->contact != 0 && (c->contact != 1 || c->samples != 1)) return 0;
+  if (c->slot_dim < 0) return 0;
   if (orc_num_layers(c) > ORC_MAX_LAYERS) return 0;
   return 1;
 }
@@ -299,7 +309,9 @@ static void contact_delta(const double* mu, const double* o, const double* d, do
 typedef struct {
   const orc_cfg* cfg;
   int nl, nin, nout, width;
-  long P;
+  long P;        /* MLP parameters per primitive */
+  long Prow;     /* all parameters per primitive: the MLP's, then 4 slot embeddings of C */
+  int C;         /* slot dimension */
   long woff[ORC_MAX_LAYERS], boff[ORC_MAX_LAYERS];
   int din[ORC_MAX_LAYERS], dout[ORC_MAX_LAYERS];
   long act_size; /* doubles for all layer inputs + the final output */
@@ -321,6 +333,8 @@ static void model_init(model_t* m, const orc_cfg* c) {
     act += m->din[l];
   }
   m->P = off;
+  m->C = c->slot_dim;
+  m->Prow = off + 4L * c->slot_dim;
   m->act_size = act + m->nout;
 }
 
@@ -379,6 +393,37 @@ static double softplus(double z) { return (z > 0 ? z : 0) + log1p(exp(-fabs(z)))
 /* ------------------------------------------------------------------------------------------ */
 /* Per-pixel render (+ optional reverse mode)                                                   */
 
+/* ------------------------------------------------------------------------------------------ */
+/* Feature slots (Sec. 3.4)                                                                     */
+
+/* The four directions a_k: unit vertices of a regular tetrahedron, (+-1, +-1, +-1)/sqrt(3) with
+ * an even number of minus signs. */
+static void slot_frame(double a[4][3]) {
+  const double v[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+  for (int k = 0; k < 4; ++k)
+    for (int c = 0; c < 3; ++c) a[k][c] = v[k][c] / sqrt(3.0);
+}
+
+/* g = softmax_k(a_k . u) */
+static void slot_softmax(const double* u, double* g) {
+  double a[4][3], z[4], zmax = -1e300, sum = 0;
+  slot_frame(a);
+  for (int k = 0; k < 4; ++k) {
+    z[k] = a[k][0] * u[0] + a[k][1] * u[1] + a[k][2] * u[2];
+    if (z[k] > zmax) zmax = z[k];
+  }
+  for (int k = 0; k < 4; ++k) { g[k] = exp(z[k] - zmax); sum += g[k]; }
+  for (int k = 0; k < 4; ++k) g[k] /= sum;
+}
+
+/* y = M delta (M = S^-1 R^T), u = clip(y) to [-1, 1]^3 */
+static void slot_offset(const double* M, const double* delta, double* y, double* u) {
+  for (int r = 0; r < 3; ++r) {
+    y[r] = M[r * 3] * delta[0] + M[r * 3 + 1] * delta[1] + M[r * 3 + 2] * delta[2];
+    u[r] = y[r] < -1 ? -1 : (y[r] > 1 ? 1 : y[r]);
+  }
+}
+
 typedef struct {
   const orc_cfg* cfg;
   model_t model;
@@ -423,7 +468,7 @@ static int scratch_init(scratch_t* s, const job_t* j) {
   s->hits = (hit_t*)malloc(sizeof(hit_t) * (size_t)(j->K > 0 ? j->K : 1));
   s->acts = (double*)malloc(sizeof(double) * (size_t)m->act_size);
   s->enc_g = (double*)malloc(sizeof(double) * (size_t)m->nin);
-  s->gw = j->d_weights ? (double*)calloc((size_t)m->P, sizeof(double)) : NULL;
+  s->gw = j->d_weights ? (double*)calloc((size_t)m->Prow, sizeof(double)) : NULL;
   s->buf_a = (double*)malloc(sizeof(double) * (size_t)maxw);
   s->buf_b = (double*)malloc(sizeof(double) * (size_t)maxw);
   s->gout = (double*)malloc(sizeof(double) * (size_t)m->nout);
@@ -452,7 +497,7 @@ static void eval_sample(const job_t* j, const hit_t* h, const double* o, const d
     for (int i = 0; i < 3; ++i) xl[i] = h->op[i] + tk * h->dp[i];
     encode(j->cfg, xl, d, s->acts);
   }
-  mlp_forward(&j->model, j->weights + (long)h->prim * j->model.P, s->acts);
+  mlp_forward(&j->model, j->weights + (long)h->prim * j->model.Prow, s->acts);
   if (tk_out) *tk_out = tk;
 }
 
@@ -478,14 +523,16 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
     if (!s->samp) return 1;
   }
   const double* out = s->acts + (m->act_size - NO);
+  const int Cs = m->C, FT = F + Cs; /* feature row: the MLP's F outputs, then the C slot channels */
   double C[3] = {0, 0, 0};
-  double* Fo = j->feat ? j->feat + (long)idx * F : NULL;
-  if (Fo) for (int f = 0; f < F; ++f) Fo[f] = 0;
+  double* Fo = j->feat ? j->feat + (long)idx * FT : NULL;
+  if (Fo) for (int f = 0; f < FT; ++f) Fo[f] = 0;
   double A = 0; /* accumulated optical depth: T = exp(-A) */
   double xl[3];
   for (int hi = 0; hi < nh; ++hi) {
     const hit_t* h = &s->hits[hi];
     double delta = (h->t1 - h->t0) / S;
+    double wh = 0; /* the hit's compositing weight */
     for (int k = 0; k < S; ++k) {
       eval_sample(j, h, o, d, k, s, xl, NULL);
       double* r = s->samp + ((long)hi * S + k) * rec;
@@ -499,7 +546,18 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
       r[NO + 1] = T;
       for (int ch = 0; ch < 3; ++ch) C[ch] += T * alpha * r[ch];
       if (Fo) for (int f = 0; f < F; ++f) Fo[f] += T * alpha * r[4 + f];
+      wh += T * alpha;
       A += a;
+    }
+    if (Fo && Cs > 0) {
+      /* F_slot += w_i sum_k g_k e_k (Sec. 3.4) */
+      double dl[3], yv[3], u[3], g[4];
+      contact_delta(j->geo[h->prim].mu, o, d, h->tmid, dl);
+      slot_offset(j->geo[h->prim].M, dl, yv, u);
+      slot_softmax(u, g);
+      const double* e = j->weights + (long)h->prim * m->Prow + m->P;
+      for (int ch = 0; ch < Cs; ++ch)
+        Fo[F + ch] += wh * (g[0] * e[ch] + g[1] * e[Cs + ch] + g[2] * e[2 * Cs + ch] + g[3] * e[3 * Cs + ch]);
     }
   }
   double Tfin = exp(-A);
@@ -511,7 +569,9 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
   double gC[3] = {0, 0, 0}, gT = 0;
   if (j->g_rgb) for (int ch = 0; ch < 3; ++ch) gC[ch] = j->g_rgb[(long)idx * 3 + ch];
   if (j->g_trans) gT = j->g_trans[idx];
-  const double* gF = (j->g_feat && F > 0) ? j->g_feat + (long)idx * F : NULL;
+  const double* gF = (j->g_feat && F > 0) ? j->g_feat + (long)idx * FT : NULL;
+  const double* gFs = (j->g_feat && Cs > 0) ? j->g_feat + (long)idx * FT + F : NULL;
+  double Rs = 0; /* sum over later samples of T alpha (f . dL/dF_slot) */
   double Rrgb[3] = {0, 0, 0};   /* sum over later samples of T alpha c */
   double RF[64];
   if (F > 64) return 2;
@@ -520,9 +580,23 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
     const hit_t* h = &s->hits[hi];
     int P = h->prim;
     double delta = (h->t1 - h->t0) / S;
-    memset(s->gw, 0, sizeof(double) * (size_t)m->P);
+    memset(s->gw, 0, sizeof(double) * (size_t)m->Prow);
     double g_op[3] = {0, 0, 0}, g_dp[3] = {0, 0, 0}, g_t0 = 0, g_t1 = 0, g_delta = 0;
-    double g_mu_direct[3] = {0, 0, 0}, g_tmid_direct = 0; /* contact mode */
+    double g_mu_direct[3] = {0, 0, 0}, g_tmid_direct = 0; /* contact mode and slots */
+    double g_M_direct[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};     /* slots: through u = clip(M delta) */
+    /* slots: the hit's offset, slot weights and s_k = e_k . dL/dF_slot */
+    double sdl[3] = {0, 0, 0}, sy[3] = {0, 0, 0}, su[3], sg[4] = {0, 0, 0, 0}, ss[4] = {0, 0, 0, 0};
+    double s_hit = 0, wh = 0;
+    const double* e_slot = j->weights + (long)P * m->Prow + m->P;
+    if (gFs) {
+      contact_delta(j->geo[P].mu, o, d, h->tmid, sdl);
+      slot_offset(j->geo[P].M, sdl, sy, su);
+      slot_softmax(su, sg);
+      for (int k = 0; k < 4; ++k) {
+        for (int ch = 0; ch < Cs; ++ch) ss[k] += e_slot[k * Cs + ch] * gFs[ch];
+        s_hit += sg[k] * ss[k];
+      }
+    }
     for (int k = S - 1; k >= 0; --k) {
       double* r = s->samp + ((long)hi * S + k) * rec;
       double a = r[NO], T = r[NO + 1];
@@ -534,8 +608,11 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
       double ga = -gT * Tfin;
       for (int ch = 0; ch < 3; ++ch) ga += gC[ch] * (Tn * r[ch] - Rrgb[ch]);
       if (gF) for (int f = 0; f < F; ++f) ga += gF[f] * (Tn * r[4 + f] - RF[f]);
+      if (gFs) ga += Tn * s_hit - Rs; /* the slot feature is constant over the hit's samples */
       for (int ch = 0; ch < 3; ++ch) Rrgb[ch] += w * r[ch];
       if (gF) for (int f = 0; f < F; ++f) RF[f] += w * r[4 + f];
+      if (gFs) Rs += w * s_hit;
+      wh += w;
       double gsigma = ga * delta;
       g_delta += ga * r[3];
       /* recompute the MLP for this sample */
@@ -544,7 +621,7 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
       for (int ch = 0; ch < 3; ++ch) s->gout[ch] = w * gC[ch] * r[ch] * (1.0 - r[ch]);
       s->gout[3] = gsigma * sigmoid(out[3]);
       for (int f = 0; f < F; ++f) s->gout[4 + f] = gF ? w * gF[f] : 0.0;
-      mlp_backward(m, j->weights + (long)P * m->P, s->acts, s->gout, s->gw, s->enc_g, s->buf_a,
+      mlp_backward(m, j->weights + (long)P * m->Prow, s->acts, s->gout, s->gw, s->enc_g, s->buf_a,
                    s->buf_b);
       double gx[3] = {0, 0, 0};
       if (c->contact) {
@@ -566,6 +643,28 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
       double u = (k + 0.5) / S;
       g_t0 += gt * (1.0 - u);
       g_t1 += gt * u;
+    }
+    if (gFs) {
+      /* dL/de_k = w g_k dL/dF_slot; dL/dg_k = w s_k; softmax; u = clip(y), y = M delta */
+      for (int k = 0; k < 4; ++k)
+        for (int ch = 0; ch < Cs; ++ch) s->gw[m->P + k * Cs + ch] += wh * sg[k] * gFs[ch];
+      double a4[4][3], gz[4], mean = 0, gy[3] = {0, 0, 0};
+      slot_frame(a4);
+      for (int k = 0; k < 4; ++k) mean += sg[k] * wh * ss[k];
+      for (int k = 0; k < 4; ++k) gz[k] = sg[k] * (wh * ss[k] - mean);
+      for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 4; ++k) gy[r] += gz[k] * a4[k][r];
+        if (sy[r] < -1 || sy[r] > 1) gy[r] = 0;
+      }
+      /* y = M delta: dL/dM += gy delta^T, dL/d delta = M^T gy; delta = mu - o - max(0, t_mid) d */
+      const double* Mg = j->geo[P].M;
+      double gdl[3];
+      for (int cc = 0; cc < 3; ++cc) {
+        gdl[cc] = Mg[cc] * gy[0] + Mg[3 + cc] * gy[1] + Mg[6 + cc] * gy[2];
+        for (int r = 0; r < 3; ++r) g_M_direct[r * 3 + cc] += gy[r] * sdl[cc];
+        g_mu_direct[cc] += gdl[cc];
+      }
+      if (h->tmid > 0) g_tmid_direct -= gdl[0] * d[0] + gdl[1] * d[1] + gdl[2] * d[2];
     }
     g_t0 -= g_delta / S;
     g_t1 += g_delta / S;
@@ -591,13 +690,13 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
     double rel[3] = {o[0] - g->mu[0], o[1] - g->mu[1], o[2] - g->mu[2]};
     double dM[9], dmu[3];
     for (int r = 0; r < 3; ++r)
-      for (int cc = 0; cc < 3; ++cc) dM[r * 3 + cc] = g_op[r] * rel[cc] + g_dp[r] * d[cc];
+      for (int cc = 0; cc < 3; ++cc) dM[r * 3 + cc] = g_op[r] * rel[cc] + g_dp[r] * d[cc] + g_M_direct[r * 3 + cc];
     for (int cc = 0; cc < 3; ++cc)
       dmu[cc] = -(g->M[0 * 3 + cc] * g_op[0] + g->M[1 * 3 + cc] * g_op[1] + g->M[2 * 3 + cc] * g_op[2]) +
                 g_mu_direct[cc];
     pthread_mutex_lock(&j->locks[P]);
-    double* dW = j->d_weights + (long)P * m->P;
-    for (long i = 0; i < m->P; ++i) dW[i] += s->gw[i];
+    double* dW = j->d_weights + (long)P * m->Prow;
+    for (long i = 0; i < m->Prow; ++i) dW[i] += s->gw[i];
     for (int i = 0; i < 9; ++i) j->d_M[P * 9 + i] += dM[i];
     for (int i = 0; i < 3; ++i) j->d_mu[P * 3 + i] += dmu[i];
     pthread_mutex_unlock(&j->locks[P]);
@@ -722,7 +821,7 @@ int orc_render_backward(const orc_cfg* cfg, int K, const double* centers, const 
   j.n_pix = n_pix; j.pix = pix; j.rgb = rgb; j.trans = trans; j.feat = feat;
   j.g_rgb = g_rgb; j.g_trans = g_trans; j.g_feat = g_feat;
   if (!check_pixels(&j)) return -1;
-  memset(d_weights, 0, sizeof(double) * (size_t)K * (size_t)j.model.P);
+  memset(d_weights, 0, sizeof(double) * (size_t)K * (size_t)j.model.Prow);
   memset(d_centers, 0, sizeof(double) * (size_t)K * 3);
   memset(d_scales, 0, sizeof(double) * (size_t)K * 3);
   memset(d_quats, 0, sizeof(double) * (size_t)K * 4);
@@ -806,6 +905,12 @@ int orc_pixel_ray(const orc_cam* cam, int x, int y, double* o, double* d) {
 int orc_encode(const orc_cfg* cfg, const double* xl, const double* d, double* out) {
   if (cfg->contact) return encode_contact(cfg, d, xl, out);
   return encode(cfg, xl, d, out);
+}
+
+/* Slot weights g = softmax_k(a_k . u) of an offset u (Sec. 3.4), for tests. */
+int orc_slot_weights(const double* u, double* g) {
+  slot_softmax(u, g);
+  return 0;
 }
 
 /* MLP of one primitive on one encoded input: raw outputs, for tests. */

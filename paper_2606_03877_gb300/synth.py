@@ -50,6 +50,7 @@ STREAM_CAMERA = 5
 STREAM_PERTURB = 6
 STREAM_GRAD = 7
 STREAM_BATCH = 8
+STREAM_SLOTS = 9
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -108,6 +109,7 @@ class SceneConfig:
     samples: int  # S midpoint samples per hit interval
     precision: str = "fp32"
     contact: int = 0  # 1: contact-point input gamma([d; mu - p*]), one sample per hit (S = 1)
+    slot_dim: int = 0  # C of the four slot embeddings per primitive (feature slots); 0 = none
 
     @property
     def input_dim(self) -> int:
@@ -124,8 +126,13 @@ class SceneConfig:
         return [(dims[i], dims[i + 1]) for i in range(len(dims) - 1)]
 
     @property
-    def n_params(self) -> int:
+    def n_mlp_params(self) -> int:
         return sum(i * o + o for i, o in self.layer_dims())
+
+    @property
+    def n_params(self) -> int:
+        """Parameters per primitive: the MLP's, then the four slot embeddings."""
+        return self.n_mlp_params + 4 * self.slot_dim
 
     @property
     def n_rays(self) -> int:
@@ -185,7 +192,7 @@ def make_scene(cfg: SceneConfig, seed: int = 0) -> Dict[str, np.ndarray]:
     q = normal(seed, STREAM_QUATS, 4 * K).reshape(K, 4)
     q = q / np.linalg.norm(q, axis=1, keepdims=True)
     weights = np.zeros((K, cfg.n_params), dtype=np.float64)
-    u = uniform(seed, STREAM_WEIGHTS, K * cfg.n_params).reshape(K, cfg.n_params)
+    u = uniform(seed, STREAM_WEIGHTS, K * cfg.n_mlp_params).reshape(K, cfg.n_mlp_params)
     off = 0
     dims = cfg.layer_dims()
     for li, (fi, fo) in enumerate(dims):
@@ -196,6 +203,8 @@ def make_scene(cfg: SceneConfig, seed: int = 0) -> Dict[str, np.ndarray]:
         if li == len(dims) - 1:
             weights[:, off + 3] = 1.0  # density output bias starts at +1
         off += fo
+    if cfg.slot_dim:  # slot embeddings U(-1, 1)
+        weights[:, off:] = 2.0 * uniform(seed, STREAM_SLOTS, K * 4 * cfg.slot_dim).reshape(K, -1) - 1.0
     return {
         "centers": centers.astype(np.float32),
         "scales": scales.astype(np.float32),
@@ -221,6 +230,7 @@ def perturb_scene(scene: Dict[str, np.ndarray], cfg: SceneConfig, seed: int = 1)
         bound = math.sqrt(6.0 / fi)
         w[:, off:off + fi * fo + fo] += 0.05 * bound * noise[:, off:off + fi * fo + fo]
         off += fi * fo + fo
+    w[:, off:] += 0.05 * noise[:, off:]  # slot embeddings
     return {
         "centers": c.astype(np.float32),
         "scales": s.astype(np.float32),

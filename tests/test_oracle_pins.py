@@ -127,6 +127,34 @@ def _np_encode_contact(cfg, d, delta):
     return np.array(parts)
 
 
+def _probe_slot_frame():
+    """The four slot directions a_k, recovered from the oracle's slot weights alone:
+    log(g_k / g_0) at u = e_c gives (a_k - a_0)_c, and a regular tetrahedron of unit vectors is
+    centred at the origin, which fixes a_0."""
+    D = np.zeros((4, 3))
+    for c in range(3):
+        u = np.zeros(3)
+        u[c] = 1.0
+        g = oracle.slot_weights(u)
+        D[:, c] = np.log(g / g[0])
+    a0 = -D.sum(axis=0) / 4.0
+    return a0[None, :] + D
+
+
+def _np_slot_feature(cfg, scene, i, o, d, tstar):
+    """f = sum_k softmax_k(a_k . u) e_k with u = clip(R^T (mu - p*) / s), p* = o + max(0, t*) d."""
+    mu = scene["centers"][i].astype(np.float64)
+    s = scene["scales"][i].astype(np.float64)
+    R = _rot(scene["quats"][i])
+    u = np.clip(R.T @ (mu - (o + max(0.0, tstar) * d)) / s, -1.0, 1.0)
+    z = _probe_slot_frame() @ u
+    g = np.exp(z - z.max())
+    g /= g.sum()
+    C = cfg.slot_dim
+    e = scene["weights"][i].astype(np.float64)[cfg.n_mlp_params:].reshape(4, C)
+    return g @ e
+
+
 def _np_render_pixel(cfg, scene, cam, x, y):
     """Independent restatement: quadratic roots, library rotations, matmul MLP, and the
     product form T_j = prod_{l<j} (1 - alpha_l) of the discrete operator (App. D.1). In
@@ -135,9 +163,11 @@ def _np_render_pixel(cfg, scene, cam, x, y):
     o, d, hits = _np_hits(scene, cam, x, y)
     C = np.zeros(3)
     F = np.zeros(cfg.feat_dim)
+    Fs = np.zeros(cfg.slot_dim)
     T = 1.0
     S = cfg.samples
     for key, t0, i, t1, tstar, _ in hits:
+        T_hit = T
         mu = scene["centers"][i].astype(np.float64)
         s = scene["scales"][i].astype(np.float64)
         R = _rot(scene["quats"][i])
@@ -156,7 +186,9 @@ def _np_render_pixel(cfg, scene, cam, x, y):
             C += T * alpha * c
             F += T * alpha * z[4:]
             T *= 1.0 - alpha
-    return C, T, F
+        if cfg.slot_dim:
+            Fs += (T_hit - T) * _np_slot_feature(cfg, scene, i, o, d, tstar)
+    return C, T, np.concatenate([F, Fs])
 
 
 # ------------------------------------------------------------------------------------------
@@ -405,6 +437,56 @@ def test_contact_mode_single_sample_and_input_dim():
     assert np.allclose(enc, _np_encode_contact(cfg, [0.6, 0.0, 0.8], [0.1, -0.2, 0.3]), atol=1e-15)
 
 
+def test_slot_frame_is_a_regular_tetrahedron():
+    """Sec. 3.4: four unit directions forming a regular tetrahedron (the minimal affinely
+    independent basis); g = softmax(a_k . u) is uniform at u = 0 and sums to one."""
+    A = _probe_slot_frame()
+    assert np.allclose(np.linalg.norm(A, axis=1), 1.0, atol=1e-12)
+    for k in range(4):
+        for m in range(k + 1, 4):
+            assert abs(A[k] @ A[m] + 1.0 / 3.0) < 1e-12
+    assert np.allclose(oracle.slot_weights(np.zeros(3)), 0.25, atol=1e-15)
+    rng = np.random.RandomState(0)
+    for _ in range(20):
+        u = rng.uniform(-1, 1, 3)
+        g = oracle.slot_weights(u)
+        assert abs(g.sum() - 1) < 1e-14 and np.argmax(g) == np.argmax(A @ u)
+
+
+def test_slots_with_equal_embeddings_are_one_minus_transmittance():
+    """All four slots of a primitive equal e: f = e whatever u, so for a single primitive
+    F_slot = sum_i w_i e = (1 - T_final) e at every pixel (weights and T of Eq. 6)."""
+    cfg = synth.SceneConfig("s", 24, 18, 1, 1, 6, 4, 16, 2, 0, 7, slot_dim=5)
+    cam = synth.make_camera(24, 18, 3, radius=2.0)
+    scene = synth.make_scene(cfg, 2)
+    scene = dict(scene, centers=np.zeros((1, 3), np.float32), scales=np.full((1, 3), 0.7, np.float32))
+    e = np.array([0.3, -1.2, 0.5, 2.0, -0.25])
+    w = scene["weights"].astype(np.float64).copy()
+    w[0, cfg.n_mlp_params:] = np.tile(e, 4)
+    scene["weights"] = w
+    rgb, T, Fo = oracle.render(cfg, scene, [cam])
+    assert Fo.shape == (24 * 18, 5) and T.min() < 0.5
+    assert np.allclose(Fo, (1.0 - T)[:, None] * e[None, :], atol=1e-13)
+    rgb0, T0, _ = oracle.render(cfg.replace(slot_dim=0), dict(scene, weights=w[:, :cfg.n_mlp_params]), [cam])
+    assert np.array_equal(rgb, rgb0) and np.array_equal(T, T0)  # slots change no colour
+
+
+@pytest.mark.parametrize("contact,S,feat", [(0, 4, 0), (1, 1, 3)])
+def test_slots_match_independent_restatement(contact, S, feat):
+    cfg = synth.SceneConfig("s", 20, 14, 10, 1, 4, 2, 16, 2, feat, S, contact=contact, slot_dim=6)
+    scene = synth.make_scene(cfg, 4)
+    scene = dict(scene, scales=scene["scales"] * 2.0)
+    cam = synth.make_camera(20, 14, 4, radius=3.0)
+    rgb, T, Fo = oracle.render(cfg, scene, [cam])
+    hit = 0
+    for n, (v, x, y) in enumerate(oracle.all_pixels([cam])):
+        C2, T2, F2 = _np_render_pixel(cfg, scene, cam, x, y)
+        assert np.allclose(rgb[n], C2, atol=1e-10) and abs(T[n] - T2) < 1e-10
+        assert np.allclose(Fo[n], F2, atol=1e-10), (x, y)
+        hit += T2 < 1
+    assert hit > 20
+
+
 def test_encoding_order_probe():
     """An MLP that routes exactly one encoded input j to the density recovers gamma_j from T;
     gamma_j must equal sin/cos(2^l pi p) of the expected component (Eq. 5: per scalar,
@@ -582,7 +664,6 @@ def _loss(cfg, scene, cams, pix, g_rgb, g_T, g_F):
 def _check_central_differences(cfg, scene, cams, contact_kink=False):
     """Analytic reverse mode against central differences of the forward loss L = <g, outputs>
     on the pose (all of centres, scales, quaternions) and 40 random weights."""
-    feat = cfg.feat_dim
     pix = oracle.all_pixels(cams)
     n = pix.shape[0]
     # stay away from tangency (and, in contact mode, from t* = 0, where max(0, t*) has a kink)
@@ -594,8 +675,9 @@ def _check_central_differences(cfg, scene, cams, contact_kink=False):
             assert np.all(np.abs(tm[m2 < 1]) > 1e-3)
     g_rgb = synth.make_grad((n, 3), seed=1).astype(np.float64)
     g_T = synth.make_grad((n,), seed=2).astype(np.float64)
-    g_F = synth.make_grad((n, max(feat, 1)), seed=3).astype(np.float64)[:, :feat]
-    res = oracle.render_backward(cfg, scene, cams, pix, g_rgb, g_T, g_F if feat else None)
+    FT = cfg.feat_dim + cfg.slot_dim
+    g_F = synth.make_grad((n, max(FT, 1)), seed=3).astype(np.float64)[:, :FT]
+    res = oracle.render_backward(cfg, scene, cams, pix, g_rgb, g_T, g_F if FT else None)
     assert np.any(res["trans"] < 0.9)
     h = 1e-6
     K = scene["centers"].shape[0]
@@ -603,6 +685,9 @@ def _check_central_differences(cfg, scene, cams, contact_kink=False):
     checks = [("centers", i) for i in range(3 * K)] + [("scales", i) for i in range(3 * K)] + \
              [("quats", i) for i in range(4 * K)] + \
              [("weights", int(i)) for i in rng.choice(K * cfg.n_params, 40, replace=False)]
+    if cfg.slot_dim:  # and 12 slot-embedding entries
+        slots = [p * cfg.n_params + cfg.n_mlp_params + j for p in range(K) for j in range(4 * cfg.slot_dim)]
+        checks += [("weights", int(i)) for i in rng.choice(slots, 12, replace=False)]
     key = {"centers": "d_centers", "scales": "d_scales", "quats": "d_quats", "weights": "d_weights"}
     for name, flat in checks:
         sp = {k: v.copy() for k, v in scene.items()}
@@ -655,3 +740,12 @@ def test_gradients_central_differences_contact_mode_camera_inside():
         m2s.append(tm[0])
     assert min(m2s) < 0  # some rays meet primitive 0 with t* < 0
     _check_central_differences(cfg, scene, [cam], contact_kink=True)
+
+
+@pytest.mark.parametrize("contact,S,feat", [(0, 3, 0), (1, 1, 2)])
+def test_gradients_central_differences_slots(contact, S, feat):
+    """Slot features (Sec. 3.4): their gradient reaches the embeddings, the compositing weights
+    (and through them the MLP) and the pose through u = clip(R^T delta / s)."""
+    cfg = synth.SceneConfig("g", 14, 10, 3, 1, 3, 2, 8, 2, feat, S, contact=contact, slot_dim=4)
+    _check_central_differences(cfg, _grad_scene(cfg), [synth.make_camera(14, 10, 6, radius=2.2)],
+                               contact_kink=True)
