@@ -19,7 +19,8 @@
  *    bounded waits that gave up) are recorded in a status word inside the `saved` or
  *    `scratch` region and returned by mlps_read_status(). No call traps, aborts or hangs.
  *  - Image layouts: rgb [V, H, W, 3], trans [V, H, W], feat [V, H, W, F], all row-major,
- *    V = n_views. Gradients dL/d* use the same layouts.
+ *    V = n_views, F = feat_dim + slot_dim (the MLP's extra outputs, then the slot channels).
+ *    Gradients dL/d* use the same layouts.
  *  - Primitive layouts: centers [K, 3], scales [K, 3] (linear, > 0), quats [K, 4] as
  *    (w, x, y, z) with any nonzero norm (normalised inside; gradients include the
  *    normalisation), weights in the canonical FP32 layout [K, P] described below.
@@ -27,7 +28,8 @@
  *    in order, W_l as [out_l, in_l] row-major, then b_l as [out_l]. Layer 0 reads the encoded
  *    input, hidden layers have `hidden_width` outputs with ReLU, the last layer has
  *    4 + feat_dim linear outputs ordered (r, g, b, sigma, f_0 .. f_{F-1}); colour = sigmoid,
- *    density = softplus (Sec. 3.2), features are used as is.
+ *    density = softplus (Sec. 3.2), features are used as is. With slot_dim = C > 0 the four
+ *    slot embeddings follow as [4, C] (Sec. 3.4).
  *  - Encoding (Eq. 5): per scalar p, (sin(2^0 pi p), cos(2^0 pi p), ..., sin(2^{L-1} pi p),
  *    cos(2^{L-1} pi p)), concatenated over the 3 components of the scale-normalised local
  *    position x' = S^-1 R^T (x - mu) (L = xyz_freqs; raw x' when 0), then over the 3 components
@@ -45,7 +47,7 @@
 extern "C" {
 #endif
 
-#define MLPS_ABI_VERSION 3
+#define MLPS_ABI_VERSION 4
 #define MLPS_MAX_VIEWS 64
 
 typedef int32_t mlps_status;
@@ -93,7 +95,18 @@ typedef struct {
                                    the contact point p* = o + max(0, t*) d to the centre (Eq. 3);
                                    the hit's alpha uses its chord length. FP32 only
                                    (MLPS_ERR_UNSUPPORTED otherwise). */
-  int32_t reserved[3];          /* must be zero */
+  int32_t slot_dim;             /* C of the feature slots of Sec. 3.4 (0 = none; a multiple of 4,
+                                   <= 2048): every primitive also carries four slot embeddings
+                                   e_k in R^C, stored after its MLP parameters (canonical weights
+                                   [K, mlps_param_count] = MLP, then e_0..e_3). A hit's feature is
+                                   f = sum_k g_k e_k with g = softmax_k(a_k . u),
+                                   u = clip_[-1,1]^3(R^T (mu - p*) / s) and a_k the unit vertices
+                                   (+-1, +-1, +-1)/sqrt(3) (even number of minus signs) of a
+                                   regular tetrahedron; the rendered map
+                                   F_slot = sum_i w_i f_i uses each hit's compositing weight w_i
+                                   and is returned in the `feat` rows after the feat_dim MLP
+                                   outputs (rows of feat_dim + slot_dim floats). */
+  int32_t reserved[2];          /* must be zero */
 } mlps_config;
 
 typedef struct {
@@ -162,8 +175,8 @@ mlps_status mlps_workspace_size(const mlps_config* cfg, int32_t K, const mlps_ca
 
 /* Forward render (Sec. 3.2-3.3). cams is a HOST array of n_views cameras (1..MLPS_MAX_VIEWS),
  * all of the same width and height. Writes rgb [V,H,W,3] and trans [V,H,W] (final
- * transmittance; background is black), and feat [V,H,W,feat_dim] when feat_dim > 0 (NULL
- * allowed when feat_dim == 0). Fills `saved` for mlps_render_backward. */
+ * transmittance; background is black), and feat [V,H,W,feat_dim + slot_dim] when that is > 0
+ * (NULL allowed when it is 0). Fills `saved` for mlps_render_backward. */
 mlps_status mlps_render_forward(const mlps_config* cfg, const mlps_scene* scene,
                                 const mlps_camera* cams, int32_t n_views, float* rgb,
                                 float* trans, float* feat, void* saved, size_t saved_bytes,
@@ -171,7 +184,9 @@ mlps_status mlps_render_forward(const mlps_config* cfg, const mlps_scene* scene,
 
 /* Backward of the forward call that filled `saved` (same cfg, scene and cams). Given dL/drgb
  * (required), dL/dtrans and dL/dfeat (either may be NULL = zero), OVERWRITES
- * d_weights [K, P] (canonical FP32 layout), d_centers [K,3], d_scales [K,3], d_quats [K,4].
+ * d_weights [K, P] (canonical FP32 layout, slot embeddings included), d_centers [K,3],
+ * d_scales [K,3], d_quats [K,4]. The slot features' gradient reaches the embeddings, the
+ * compositing weights (and through them the MLP) and the pose (through u).
  * The MLP is recomputed, not stored. Hit sets and orders are piecewise constant and are not
  * differentiated. */
 mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene,

@@ -39,7 +39,8 @@ class MlpsConfig(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("max_hits_per_ray", ctypes.c_int32),
                 ("hit_capacity_per_ray", ctypes.c_float), ("t_eps", ctypes.c_float),
                 ("tile", ctypes.c_int32), ("mlp_groups", ctypes.c_int32),
-                ("contact", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("contact", ctypes.c_int32), ("slot_dim", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class MlpsCamera(ctypes.Structure):

@@ -13,7 +13,7 @@
 
 namespace mlps {
 
-__global__ void k_composite_fwd(Work w, int F, float* __restrict__ rgb, float* __restrict__ trans,
+__global__ void k_composite_fwd(Work w, int F, int FT, float* __restrict__ rgb, float* __restrict__ trans,
                                 float* __restrict__ feat) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= w.n_rays) return;
@@ -35,7 +35,7 @@ __global__ void k_composite_fwd(Work w, int F, float* __restrict__ rgb, float* _
   rgb[3 * (size_t)r + 1] = C1;
   rgb[3 * (size_t)r + 2] = C2;
   trans[r] = expf(-A);
-  for (int f = 0; f < F; ++f) feat[(size_t)r * F + f] = Fv[f];
+  for (int f = 0; f < F; ++f) feat[(size_t)r * FT + f] = Fv[f];
 }
 
 // Reverse pass. With C = sum_j T_j C_j, T_final = exp(-sum_j a_j):
@@ -43,10 +43,12 @@ __global__ void k_composite_fwd(Work w, int F, float* __restrict__ rgb, float* _
 //   dL/da_j = -dL/dC . sum_{l>j} T_l C_l - dL/dF . sum_{l>j} T_l F_l - dL/dT_final T_final.
 // Intervals skipped by early termination get zero gradient. The per-interval gradients are
 // written in the primitive-major order of the interval records, so that the MLP backward
-// reads one contiguous block per chunk.
-__global__ void k_composite_bwd(Work w, int F, const float* __restrict__ d_rgb,
+// reads one contiguous block per chunk. With feature slots, `slot_ga` adds the slot features'
+// own dL/da_j per interval (hit order).
+__global__ void k_composite_bwd(Work w, int F, int FT, const float* __restrict__ d_rgb,
                                 const float* __restrict__ d_trans,
-                                const float* __restrict__ d_feat) {
+                                const float* __restrict__ d_feat,
+                                const float* __restrict__ slot_ga) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= w.n_rays) return;
   const int n = w.ray_count[r], s = w.ray_start[r];
@@ -64,7 +66,7 @@ __global__ void k_composite_bwd(Work w, int F, const float* __restrict__ d_rgb,
   const float gT = d_trans ? d_trans[r] : 0.f;
   float gF[kMaxFeat], RF[kMaxFeat];
   for (int f = 0; f < F; ++f) {
-    gF[f] = d_feat ? d_feat[(size_t)r * F + f] : 0.f;
+    gF[f] = d_feat ? d_feat[(size_t)r * FT + f] : 0.f;
     RF[f] = 0.f;
   }
   float R0 = 0.f, R1 = 0.f, R2 = 0.f;  // sum over later intervals of T_l C_l
@@ -74,6 +76,7 @@ __global__ void k_composite_bwd(Work w, int F, const float* __restrict__ d_rgb,
     const float T = expf(-Aex[j]);
     float ga = -(g0 * R0 + g1 * R1 + g2 * R2) - gT * Tfin;
     for (int f = 0; f < F; ++f) ga -= gF[f] * RF[f];
+    if (slot_ga) ga += slot_ga[h];
     const int sl = w.slot_of[h];
     w.hit_grad[sl] = make_float4(T * g0, T * g1, T * g2, ga);
     for (int f = 0; f < F; ++f) {
@@ -124,18 +127,16 @@ __global__ void k_pose_bwd(Work w, float* d_centers, float* d_scales, float* d_q
   for (int i = 0; i < 4; ++i) d_quats[4 * p + i] = g.valid ? (gq[i] - g.qn[i] * dot) / g.qlen : 0.f;
 }
 
-void launch_composite_fwd(const Work& w, int F, float* rgb, float* trans, float* feat,
+void launch_composite_fwd(const Work& w, int F, int FT, float* rgb, float* trans, float* feat,
                           cudaStream_t st) {
   if (w.n_rays == 0) return;
-  k_composite_fwd<<<(w.n_rays + 255) / 256, 256, 0, st>>>(w, F, rgb, trans, feat);
+  k_composite_fwd<<<(w.n_rays + 255) / 256, 256, 0, st>>>(w, F, FT, rgb, trans, feat);
 }
 
-void launch_composite_bwd(const Work& w, int F, const float* rgb, const float* trans,
-                          const float* feat, const float* d_rgb, const float* d_trans,
-                          const float* d_feat, cudaStream_t st) {
-  (void)rgb; (void)trans; (void)feat;
+void launch_composite_bwd(const Work& w, int F, int FT, const float* d_rgb, const float* d_trans,
+                          const float* d_feat, const float* slot_ga, cudaStream_t st) {
   if (w.n_rays == 0) return;
-  k_composite_bwd<<<(w.n_rays + 255) / 256, 256, 0, st>>>(w, F, d_rgb, d_trans, d_feat);
+  k_composite_bwd<<<(w.n_rays + 255) / 256, 256, 0, st>>>(w, F, FT, d_rgb, d_trans, d_feat, slot_ga);
 }
 
 void launch_pose_bwd(const Work& w, float* d_centers, float* d_scales, float* d_quats,

@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
   int loaded = -1;
 
   auto flush = [&](int p) {
-    float* dW = a.d_weights + (size_t)p * m.P;
+    float* dW = a.d_weights + (size_t)p * m.Prow;
 #pragma unroll
     for (int j = 0; j < kMaxTiles; ++j) {
       if (j >= nt) break;

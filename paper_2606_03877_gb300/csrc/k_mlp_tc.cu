@@ -496,8 +496,12 @@ __global__ void k_pack_bf16(Model m, TcPlan P, long long stride, int K, const fl
                             unsigned char* __restrict__ dst) {
   const int p = blockIdx.y;
   if (p >= K) return;
-  const float* s = src + (size_t)p * m.P;
+  const float* s = src + (size_t)p * m.Prow;
   unsigned char* d = dst + (size_t)p * stride;
+  if (m.C > 0) {  // slot embeddings, unchanged
+    float* e = reinterpret_cast<float*>(d + P.slot_byte);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * m.C; i += gridDim.x * blockDim.x) e[i] = s[m.P + i];
+  }
   // weight tiles: element (n, k) of layer l at row gw_row + (k / 64) * npad + n, column k % 64
   for (int l = 0; l < m.nl; ++l) {
     const int np = P.npad[l], kp = P.kpad[l];
@@ -589,6 +593,11 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3) {
     P->w8_bytes = s8;
     P->gscale_byte = r8 * 128;
     bytes = (long long)r8 * 128 + 4LL * bias;
+  }
+  if (m.C > 0) {  // FP32 slot embeddings [4][C] after everything the MLP kernels read
+    bytes = (bytes + 15) / 16 * 16;
+    P->slot_byte = (int)bytes;
+    bytes += 16LL * m.C;
   }
   *stride = (bytes + 1023) / 1024 * 1024;
   P->rows_per_prim = (int)(*stride / 128);

@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
   auto flush = [&](int p) {
     if (warp < 4) {
       tc_fence_after();
-      float* dW = a.d_weights + (size_t)p * m.P;
+      float* dW = a.d_weights + (size_t)p * m.Prow;
       const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
       const int frow = warp * 32 + lane;
       for (int l = 0; l < nl; ++l) {

@@ -15,8 +15,9 @@ __global__ void k_pack_fp32(Model m, Packed pk, int K, const float* __restrict__
                             float* __restrict__ dst) {
   const int p = blockIdx.y;
   if (p >= K) return;
-  const float* s = src + (size_t)p * m.P;
+  const float* s = src + (size_t)p * m.Prow;
   float* d = dst + (size_t)p * (pk.stride / 4);
+  const int slot0 = (int)(pk.slot_byte / 4);
   const int total = (int)(pk.stride / 4);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     float v = 0.f;
@@ -30,6 +31,7 @@ __global__ void k_pack_fp32(Model m, Packed pk, int K, const float* __restrict__
         v = s[m.boff[l] + (i - pk.boff[l])];
       }
     }
+    if (m.C > 0 && i >= slot0 && i < slot0 + 4 * m.C) v = s[m.P + (i - slot0)];
     d[i] = v;
   }
 }

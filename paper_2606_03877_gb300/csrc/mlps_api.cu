@@ -25,7 +25,7 @@ struct ProfRec {
 };
 const char* kStageNames[] = {"setup", "tile_lists", "intersect", "prim_scan", "scatter",
                              "mlp_fwd", "composite_fwd", "composite_bwd", "mlp_bwd", "pose_bwd",
-                             "pack"};
+                             "pack", "slots_fwd", "slots_bwd"};
 constexpr int kNumStages = sizeof(kStageNames) / sizeof(kStageNames[0]);
 std::mutex g_prof_mu;
 bool g_prof_on = false;
@@ -68,12 +68,17 @@ std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 enum { ST_SETUP, ST_TILES, ST_INTERSECT, ST_SCAN, ST_SCATTER, ST_MLP_FWD, ST_COMP_FWD,
-       ST_COMP_BWD, ST_MLP_BWD, ST_POSE_BWD, ST_PACK };
+       ST_COMP_BWD, ST_MLP_BWD, ST_POSE_BWD, ST_PACK, ST_SLOTS_FWD, ST_SLOTS_BWD };
 
 // ------------------------------------------------------------------------------------------
 // Model and packing layouts
 
 bool finite_f(float x) { return std::isfinite(x); }
+
+// Bytes of a packed blob that the MLP kernels read (the slot embeddings follow them).
+size_t mlp_bytes(const Model& m, const Packed& pk) {
+  return (size_t)(m.C > 0 ? pk.slot_byte : pk.stride);
+}
 
 mlps_status check_cfg(const mlps_config* c) {
   if (!c) return MLPS_ERR_INVALID_ARGUMENT;
@@ -86,9 +91,11 @@ mlps_status check_cfg(const mlps_config* c) {
   if (!finite_f(c->hit_capacity_per_ray) || !(c->hit_capacity_per_ray > 0.f))
     return MLPS_ERR_INVALID_ARGUMENT;
   if (!finite_f(c->t_eps) || c->t_eps < 0.f || c->t_eps >= 1.f) return MLPS_ERR_INVALID_ARGUMENT;
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 2; ++i)
     if (c->reserved[i] != 0) return MLPS_ERR_INVALID_ARGUMENT;
   if (c->contact != 0 && (c->contact != 1 || c->samples != 1)) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->slot_dim < 0 || c->slot_dim > kMaxSlotDim) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->slot_dim % 4 != 0) return MLPS_ERR_UNSUPPORTED;  // float4 channel groups
   if (c->mlp_groups != 0 && (c->mlp_groups < 2 || c->mlp_groups > 6)) return MLPS_ERR_INVALID_ARGUMENT;
   if (c->hidden_width != 32 && c->hidden_width != 64 && c->hidden_width != 128)
     return MLPS_ERR_UNSUPPORTED;
@@ -111,6 +118,7 @@ Model make_model(const mlps_config* c) {
   m.xyzL = c->xyz_freqs;
   m.dirL = c->dir_freqs;
   m.contact = c->contact;
+  m.C = c->slot_dim;
   int off = 0;
   for (int l = 0; l < m.nl; ++l) {
     m.din[l] = l == 0 ? m.nin : m.width;
@@ -121,6 +129,7 @@ Model make_model(const mlps_config* c) {
     off += m.dout[l];
   }
   m.P = off;
+  m.Prow = off + 4 * m.C;
   return m;
 }
 
@@ -134,7 +143,10 @@ Packed make_packed(const mlps_config* c, const Model& m) {
   if (c->precision == MLPS_BF16 || c->precision == MLPS_FP8_E4M3) {
     TcPlan P;
     long long stride = 0;
-    if (tc_plan(m, &P, &stride, c->precision == MLPS_FP8_E4M3)) pk.stride = stride;
+    if (tc_plan(m, &P, &stride, c->precision == MLPS_FP8_E4M3)) {
+      pk.stride = stride;
+      pk.slot_byte = P.slot_byte;
+    }
     return pk;
   }
   int off = 0;
@@ -144,6 +156,8 @@ Packed make_packed(const mlps_config* c, const Model& m) {
     pk.boff[l] = off;
     off = r4(off + m.dout[l]);
   }
+  pk.slot_byte = (long long)off * 4;  // FP32 slot embeddings [4][C] after the layers
+  off += 4 * m.C;
   pk.stride = r256((long long)off * 4);
   return pk;
 }
@@ -174,7 +188,7 @@ struct Layout {
       ray_count, prim_count, prim_start, chunk_start, prim_list, rec, slot_of, views, geo, pview,
       saved_total;
   // scratch
-  size_t prim_cursor, tile_count, tile_list, hit_grad, hit_gfeat, dgeo, scratch_total;
+  size_t prim_cursor, tile_count, tile_list, hit_grad, hit_gfeat, dgeo, slot_ga, slot_gu, scratch_total;
   long long hit_cap;
   long long n_rays, n_pairs, n_tiles_all, n_cand;
   int max_view_tiles;
@@ -232,6 +246,8 @@ bool make_layout(const mlps_config* c, int K, const ViewSpec* vs, int V, Layout*
   L->hit_grad = t.take<float4>(hc);
   L->hit_gfeat = t.take<float>(hc * (size_t)(F > 0 ? F : 1));
   L->dgeo = t.take<float>((size_t)K * 12 + 1);
+  L->slot_ga = t.take<float>(c->slot_dim > 0 ? hc : 1);
+  L->slot_gu = t.take<float4>(c->slot_dim > 0 ? hc : 1);
   L->scratch_total = t.off;
   return true;
 }
@@ -269,6 +285,10 @@ Work make_work(const mlps_config* c, const Layout& L, int K, int V, void* saved,
     w.hit_grad = reinterpret_cast<float4*>(sc + L.hit_grad);
     w.hit_gfeat = reinterpret_cast<float*>(sc + L.hit_gfeat);
     w.dgeo = reinterpret_cast<float*>(sc + L.dgeo);
+    if (c->slot_dim > 0) {
+      w.slot_ga = reinterpret_cast<float*>(sc + L.slot_ga);
+      w.slot_gu = reinterpret_cast<float4*>(sc + L.slot_gu);
+    }
   }
   w.K = K;
   w.V = V;
@@ -394,7 +414,7 @@ mlps_status forward_impl(const mlps_config* cfg, const mlps_scene* scene, const 
                          void* scratch, size_t scratch_bytes, void* stream) {
   if (!scene || scene->K < 0 || !rgb || !trans || !saved || !scratch)
     return MLPS_ERR_INVALID_ARGUMENT;
-  if (cfg->feat_dim > 0 && !feat) return MLPS_ERR_INVALID_ARGUMENT;
+  if (cfg->feat_dim + cfg->slot_dim > 0 && !feat) return MLPS_ERR_INVALID_ARGUMENT;
   const int K = scene->K;
   if (K > 0 && (!scene->centers || !scene->scales || !scene->quats || !scene->weights))
     return MLPS_ERR_INVALID_ARGUMENT;
@@ -415,7 +435,7 @@ mlps_status forward_impl(const mlps_config* cfg, const mlps_scene* scene, const 
   a.weights = static_cast<const unsigned char*>(scene->weights);
   a.rows = 128;
   a.groups = cfg->mlp_groups;
-  a.resident = (a.pk.stride + 2 * 128 * 4 * (size_t)std::max(std::max(m.nin, m.width), m.nout) +
+  a.resident = (mlp_bytes(m, a.pk) + 2 * 128 * 4 * (size_t)std::max(std::max(m.nin, m.width), m.nout) +
                 16 * 1024) <= 200 * 1024;
   const int n_sm = num_sms();
   {
@@ -460,7 +480,12 @@ mlps_status forward_impl(const mlps_config* cfg, const mlps_scene* scene, const 
   }
   {
     StageTimer tm(ST_COMP_FWD, st);
-    launch_composite_fwd(w, cfg->feat_dim, rgb, trans, feat, st);
+    launch_composite_fwd(w, cfg->feat_dim, cfg->feat_dim + cfg->slot_dim, rgb, trans, feat, st);
+    count_launch(w.n_rays > 0 ? 1 : 0);
+  }
+  if (m.C > 0) {
+    StageTimer tm(ST_SLOTS_FWD, st);
+    launch_slots_fwd(w, m, a.pk, a.weights, feat + cfg->feat_dim, cfg->feat_dim + m.C, st);
     count_launch(w.n_rays > 0 ? 1 : 0);
   }
   return cuda_status(cudaGetLastError());
@@ -492,7 +517,7 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
   a.weights = static_cast<const unsigned char*>(scene->weights);
   a.d_weights = d_weights;
   a.rows = 128;
-  a.resident = (a.pk.stride <= 64 * 1024);
+  a.resident = (mlp_bytes(m, a.pk) <= 64 * 1024);
   TcPlan P;
   long long tc_stride = 0;
   // FP8 precision: the backward recomputes the MLP in BF16 from the BF16 tiles of the same blob
@@ -509,10 +534,22 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
     cudaMemsetAsync(w.scr_hdr, 0, 256, st);
     if (K > 0) {
       cudaMemsetAsync(w.dgeo, 0, sizeof(float) * 12 * (size_t)K, st);
-      cudaMemsetAsync(d_weights, 0, sizeof(float) * (size_t)m.P * K, st);
+      cudaMemsetAsync(d_weights, 0, sizeof(float) * (size_t)m.Prow * K, st);
     }
-    launch_composite_bwd(w, cfg->feat_dim, nullptr, nullptr, nullptr, d_rgb, d_trans,
-                         cfg->feat_dim > 0 ? d_feat : nullptr, st);
+  }
+  const int FT = cfg->feat_dim + m.C;  // feature row: the MLP's outputs, then the slot channels
+  const bool slot_grad = m.C > 0 && d_feat != nullptr;
+  if (slot_grad) {
+    // the slot features' gradient on each interval's optical depth (read by the composite
+    // reverse) and on u (read by the per-primitive pass after the MLP backward)
+    StageTimer tm(ST_SLOTS_BWD, st);
+    launch_slots_bwd_ray(w, m, a.pk, a.weights, d_feat + cfg->feat_dim, FT, st);
+    count_launch(w.n_rays > 0 ? 1 : 0);
+  }
+  {
+    StageTimer tm(ST_COMP_BWD, st);
+    launch_composite_bwd(w, cfg->feat_dim, FT, d_rgb, d_trans, cfg->feat_dim > 0 ? d_feat : nullptr,
+                         slot_grad ? w.slot_ga : nullptr, st);
     count_launch(w.n_rays > 0 ? 1 : 0);
   }
   if (K > 0) {
@@ -520,6 +557,11 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
     cudaError_t e = tc ? launch_mlp_bwd_tc(w, a, P, n_sm, st) : launch_mlp_bwd_simt(w, a, n_sm, st);
     if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return MLPS_ERR_CUDA;
+    count_launch(1);
+  }
+  if (slot_grad && K > 0) {
+    StageTimer tm(ST_SLOTS_BWD, st);
+    launch_slots_bwd_prim(w, m, a.pk, a.weights, d_feat + cfg->feat_dim, FT, d_weights, n_sm, st);
     count_launch(1);
   }
   {
@@ -577,7 +619,7 @@ int32_t mlps_input_dim(const mlps_config* cfg) {
 
 int64_t mlps_param_count(const mlps_config* cfg) {
   if (check_cfg(cfg) != MLPS_OK) return 0;
-  return make_model(cfg).P;
+  return make_model(cfg).Prow;
 }
 
 int64_t mlps_weight_stride(const mlps_config* cfg) {

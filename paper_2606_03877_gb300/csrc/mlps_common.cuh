@@ -28,6 +28,7 @@ namespace mlps {
 constexpr int kMaxHits = 64;       // per-ray sorted-hit capacity limit
 constexpr int kMaxLayers = 8;      // hidden_layers + 1
 constexpr int kMaxFeat = 32;
+constexpr int kMaxSlotDim = 2048;  // feature-slot channels (Sec. 3.4)
 constexpr int kMaxViews = MLPS_MAX_VIEWS;
 
 // ------------------------------------------------------------------------------------------
@@ -212,7 +213,9 @@ struct Model {
   int F;            // feature outputs
   int xyzL, dirL;   // encoding frequencies
   int contact;      // 1: contact-point input gamma([d; delta]), S = 1 (Sec. 3.2)
-  int P;            // canonical params per primitive
+  int C;            // slot-embedding dimension (Sec. 3.4); 0 = no feature slots
+  int P;            // canonical MLP params per primitive
+  int Prow;         // canonical params per primitive: the MLP's, then 4 slot embeddings of C
   int din[kMaxLayers], dout[kMaxLayers];
   int woff[kMaxLayers], boff[kMaxLayers];
 };
@@ -253,6 +256,8 @@ struct Work {
   float4* hit_grad;      // [cap] (dL/dC_j, dL/da_j) per interval, in primitive-major order
   float* hit_gfeat;      // [cap, F], same order
   float* dgeo;           // [K, 12] dL/dM (9) and dL/dmu (3)
+  float* slot_ga;        // [cap] feature slots: dL/da_j of each interval (hit order)
+  float4* slot_gu;       // [cap] feature slots: (dL/du, compositing weight w_j) (hit order)
   // sizes
   int K, V;
   int H, W, ntx, nty, n_tiles;  // view 0's sizes (the single-scene inspection calls use them)

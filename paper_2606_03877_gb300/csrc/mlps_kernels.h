@@ -15,13 +15,14 @@ struct Packed {
   int woff[kMaxLayers], boff[kMaxLayers];  // float offsets (FP32 layout)
   int tc_scale;              // FP8: float scales [2 * nl] (forward tile, transposed tile)
   int din_pad[kMaxLayers], dout_pad[kMaxLayers];
+  long long slot_byte;       // the four FP32 slot embeddings [4][C] (16-byte aligned), if C > 0
 };
 
 struct MlpArgs {
   Model m;
   Packed pk;
   const unsigned char* weights;  // packed blob [K, stride]
-  float* d_weights;              // backward: canonical FP32 gradient [K, P]
+  float* d_weights;              // backward: canonical FP32 gradient [K, Prow]
   int resident;                  // FP32: all layers in shared memory at once
   int rows;                      // sample rows per chunk
   int groups;                    // forward tensor-core MLP: chunks in flight per CTA (0 = default)
@@ -50,6 +51,7 @@ struct TcPlan {
   int bias_off[kMaxLayers];                // float offset of layer l's bias
   int bias_floats;
   int gbias_byte;                          // byte offset of the FP32 biases in a blob
+  int slot_byte;                           // byte offset of the FP32 slot embeddings (C > 0)
   int rows_per_prim;                       // blob stride / 128
   int kmax;                                // widest A tile (elements)
   int a_bytes;                             // one A tile: 128 rows x kmax BF16
@@ -67,6 +69,14 @@ void launch_scatter(const Work& w, int n_sm, cudaStream_t st);
 void launch_export_hits(const Work& w, int max_out, int* count, int* prim, float* t0, float* t1,
                         float* tmid, cudaStream_t st);
 void launch_export_tiles(const Work& w, int* count, int* list, cudaStream_t st);
+
+// k_slots.cu (feature slots, Sec. 3.4)
+void launch_slots_fwd(const Work& w, const Model& m, const Packed& pk, const unsigned char* weights,
+                      float* feat, int row_stride, cudaStream_t st);
+void launch_slots_bwd_ray(const Work& w, const Model& m, const Packed& pk, const unsigned char* weights,
+                          const float* d_feat, int row_stride, cudaStream_t st);
+void launch_slots_bwd_prim(const Work& w, const Model& m, const Packed& pk, const unsigned char* weights,
+                           const float* d_feat, int row_stride, float* d_weights, int n_sm, cudaStream_t st);
 
 // k_mlp_simt.cu (FP32 path)
 size_t mlp_simt_smem(const MlpArgs& a, bool backward);
@@ -89,11 +99,11 @@ cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
                               cudaStream_t st);
 
 // k_composite.cu
-void launch_composite_fwd(const Work& w, int F, float* rgb, float* trans, float* feat,
+// F MLP feature channels in rows of FT floats (FT = F + slot channels)
+void launch_composite_fwd(const Work& w, int F, int FT, float* rgb, float* trans, float* feat,
                           cudaStream_t st);
-void launch_composite_bwd(const Work& w, int F, const float* rgb, const float* trans,
-                          const float* feat, const float* d_rgb, const float* d_trans,
-                          const float* d_feat, cudaStream_t st);
+void launch_composite_bwd(const Work& w, int F, int FT, const float* d_rgb, const float* d_trans,
+                          const float* d_feat, const float* slot_ga, cudaStream_t st);
 void launch_pose_bwd(const Work& w, float* d_centers, float* d_scales, float* d_quats,
                      cudaStream_t st);
 

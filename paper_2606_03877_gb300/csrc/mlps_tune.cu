@@ -24,7 +24,8 @@ std::map<std::string, std::pair<int, int>> g_tune_cache;  // key -> (tile, mlp_g
 std::string tune_key(const mlps_config* c, const mlps_batch_item* items, int n, int do_backward) {
   std::string k;
   const int32_t head[] = {c->xyz_freqs, c->dir_freqs, c->hidden_width, c->hidden_layers, c->feat_dim,
-                          c->samples, c->precision, c->max_hits_per_ray, c->contact, do_backward};
+                          c->samples, c->precision, c->max_hits_per_ray, c->contact, c->slot_dim,
+                          do_backward};
   k.append(reinterpret_cast<const char*>(head), sizeof(head));
   for (int i = 0; i < n; ++i) {
     const int32_t it[] = {items[i].prim_count, items[i].cam.width, items[i].cam.height};

@@ -15,7 +15,7 @@ from . import _lib
 def make_config(shape, precision: str = "fp32", t_eps: float = 1e-6, max_hits: int = 64,
                 hit_capacity: float = 8.0, tile: int = 16, mlp_groups: int = 0) -> _lib.MlpsConfig:
     """mlps_config from any object with xyz_freqs, dir_freqs, hidden_width, hidden_layers,
-    feat_dim, samples and optionally contact (e.g. :class:`synth.SceneConfig`)."""
+    feat_dim, samples and optionally contact and slot_dim (e.g. :class:`synth.SceneConfig`)."""
     cfg = _lib.mlps_config_default(int(shape.xyz_freqs), int(shape.dir_freqs), int(shape.hidden_width),
                                    int(shape.hidden_layers), int(shape.feat_dim))
     cfg.samples = int(shape.samples)
@@ -26,6 +26,7 @@ def make_config(shape, precision: str = "fp32", t_eps: float = 1e-6, max_hits: i
     cfg.tile = int(tile)
     cfg.mlp_groups = int(mlp_groups)
     cfg.contact = int(getattr(shape, "contact", 0))
+    cfg.slot_dim = int(getattr(shape, "slot_dim", 0))
     return cfg
 
 
@@ -46,7 +47,8 @@ class Renderer:
         self.device = torch.device(device)
         self.P = _lib.mlps_param_count(self.cfg)
         self.stride = _lib.mlps_weight_stride(self.cfg)
-        self.F = int(shape.feat_dim)
+        # feature row: the MLP's extra outputs, then the slot channels
+        self.F = int(shape.feat_dim) + int(getattr(shape, "slot_dim", 0))
         self.saved: Optional[torch.Tensor] = None
         self.scratch: Optional[torch.Tensor] = None
         self._last = None
@@ -185,7 +187,8 @@ class BatchRenderer:
         self.device = torch.device(device)
         self.P = _lib.mlps_param_count(self.cfg)
         self.stride = _lib.mlps_weight_stride(self.cfg)
-        self.F = int(shape.feat_dim)
+        # feature row: the MLP's extra outputs, then the slot channels
+        self.F = int(shape.feat_dim) + int(getattr(shape, "slot_dim", 0))
         self.K = int(K)
         self.items = _lib.batch_items(items)
         self.n = len(items)
