@@ -182,6 +182,27 @@ def _traffic(stage, precision, workload):
         return None
 
 
+FEAT_GRAD_ROWS = 4099  # distinct seeded rows of the synthetic dL/dF, repeated over the rays
+
+
+def feat_grad_rows(wl, idx):
+    """Synthetic dL/dF of the feature row (MLP outputs + slot channels) of global rays `idx`:
+    row idx mod 4099 of a seeded table (a full-size table would be GBs of host memory)."""
+    from paper_2606_03877_gb300 import synth
+    FT = wl.feat_dim + wl.slot_dim
+    table = synth.make_grad((FEAT_GRAD_ROWS, FT), seed=200, scale=0.01)
+    return table[np.asarray(idx, dtype=np.int64) % FEAT_GRAD_ROWS]
+
+
+def feat_grad_device(wl, dev):
+    import torch
+    from paper_2606_03877_gb300 import synth
+    FT = wl.feat_dim + wl.slot_dim
+    table = torch.from_numpy(synth.make_grad((FEAT_GRAD_ROWS, FT), seed=200, scale=0.01)).to(dev)
+    idx = torch.arange(wl.n_rays, device=dev) % FEAT_GRAD_ROWS
+    return table[idx].reshape(wl.n_views, wl.height, wl.width, FT)
+
+
 def _flush_l2(buf):
     buf.add_(1.0)  # writes 256 MiB (> 129 MB L2) between timed steps
 
@@ -204,6 +225,8 @@ def run_ours(a):
     d = {k: torch.from_numpy(v).to(dev) for k, v in scene.items()}
     g_rgb = torch.from_numpy(synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100 + rank,
                                              scale=0.01)).to(dev)
+    FT = wl.feat_dim + wl.slot_dim  # feature row: MLP outputs, then slot channels
+    g_feat = feat_grad_device(wl, dev) if FT else None
     n_rays = wl.n_rays
     flush = torch.zeros(64 * 1024 * 1024, device=dev)
 
@@ -218,7 +241,7 @@ def run_ours(a):
         bwd_ok = False
         if want_bwd:
             try:
-                r.backward(g_rgb)
+                r.backward(g_rgb, None, g_feat)
                 bwd_ok = True
             except _lib.MlpsError as e:
                 if e.status != _lib.MLPS_ERR_UNSUPPORTED:
@@ -250,14 +273,14 @@ def run_ours(a):
         packed = rr.pack(d["weights"], out=rr._packed_buf)
         rr.forward(d["centers"], d["scales"], d["quats"], packed, cams, out=rr._out_buf)
         if bwd:
-            rr.backward(g_rgb, out=rr._grad_buf)
+            rr.backward(g_rgb, None, g_feat, out=rr._grad_buf)
 
     def bind_buffers(rr):
         rr._packed_buf = torch.empty(max(wl.K, 1) * rr.stride, dtype=torch.uint8, device=dev)
         rr._out_buf = {"rgb": torch.empty(wl.n_views, wl.height, wl.width, 3, device=dev),
                        "trans": torch.empty(wl.n_views, wl.height, wl.width, device=dev),
-                       "feat": torch.empty(wl.n_views, wl.height, wl.width, wl.feat_dim, device=dev)
-                       if wl.feat_dim else None}
+                       "feat": torch.empty(wl.n_views, wl.height, wl.width, FT, device=dev)
+                       if FT else None}
         rr._grad_buf = {"d_weights": torch.empty(wl.K, rr.P, device=dev), "d_centers": torch.empty(wl.K, 3, device=dev),
                         "d_scales": torch.empty(wl.K, 3, device=dev), "d_quats": torch.empty(wl.K, 4, device=dev)}
 
@@ -344,6 +367,24 @@ def run_ours(a):
     else:
         roof = {"bound": "hbm", "achieved": None, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                 "frac": None, "traffic": None, "kernel": dom}
+    if wl.slot_dim and "slots_fwd" in stage_ms:
+        # feature slots: HBM-bound; algorithmic bytes = the slot map written (forward) and its
+        # gradient read (backward), 4 C bytes per ray, plus 64 B of records per hit
+        C = wl.slot_dim
+        fwd_b = n_rays * 4 * C + n_hits * 64
+        slots = {"bound": "hbm", "unit": "GB/s", "peak": float(peaks["hbm_gbs"]),
+                 "fwd_ms": stage_ms["slots_fwd"],
+                 "fwd_achieved": fwd_b / (stage_ms["slots_fwd"] / 1e3) / 1e9,
+                 "bytes_per_ray": 4 * C, "bytes_per_hit": 64}
+        slots["fwd_frac"] = slots["fwd_achieved"] / slots["peak"]
+        if "slots_bwd" in stage_ms:
+            n_bwd = prof["slots_bwd"][1] / max(prof["slots_fwd"][1], 1)  # launches per step (2)
+            bwd_ms = stage_ms["slots_bwd"] * n_bwd
+            slots["bwd_ms"] = bwd_ms
+            slots["bwd_achieved"] = fwd_b / (bwd_ms / 1e3) / 1e9
+            slots["bwd_frac"] = slots["bwd_achieved"] / slots["peak"]
+    else:
+        slots = None
     roof["traffic"] = _traffic(dom, precision, wl.name)
     roof["stage_ms_per_launch"] = {k: round(v, 4) for k, v in stage_ms.items()}
     roof["algorithmic"] = {"hits": n_hits, "samples": samples, "flop_per_sample_fwd": flop_per_sample}
@@ -355,6 +396,8 @@ def run_ours(a):
         "data": "synthetic (seeded scene, Kaiming-uniform MLPs, cameras on the r=3 sphere)",
         "config": {"workload": f"{wl.name}: {wl.width}x{wl.height}, K={wl.K}, MLP {wl.input_dim}-"
                                f"{'x'.join([str(wl.hidden_width)] * wl.hidden_layers)}-{wl.output_dim}, S={S}, "
+                               f"{'contact-point input, ' if wl.contact else ''}"
+                               f"{f'4 x {wl.slot_dim} feature slots, ' if wl.slot_dim else ''}"
                                f"{wl.n_views} views/rank",
                    "pass": "fwd+bwd" if do_bwd else "fwd", "precision": precision,
                    "rays_per_step": n_rays * ws, "hits_per_step": n_hits,
@@ -365,6 +408,8 @@ def run_ours(a):
         "gpu_launches": int(launches),
         "roofline": roof,
     }
+    if slots:
+        line["slots_roofline"] = slots
     if rank == 0 and not a.no_e2e:
         line["e2e"] = run_e2e(a, wl, scene, cams, precision, do_bwd, dev)
     if rank == 0 and not a.no_cpu_baseline:
@@ -390,10 +435,16 @@ def run_e2e(a, wl, scene, cams, precision, do_bwd, dev):
     r = Renderer(wl, precision=precision, device=str(dev))
     rgb_h = torch.empty(wl.n_views, wl.height, wl.width, 3).pin_memory()
     tr_h = torch.empty(wl.n_views, wl.height, wl.width).pin_memory()
+    FT = wl.feat_dim + wl.slot_dim
+    ft_h = torch.empty(wl.n_views, wl.height, wl.width, FT).pin_memory() if FT else None
+    gf_host = feat_grad_device(wl, dev).cpu().pin_memory() if FT else None
+    gf_dev = torch.empty(gf_host.shape, device=dev) if FT else None
     gw_h = torch.empty(wl.K, r.P).pin_memory()
     gp_h = torch.empty(wl.K, 10).pin_memory()
     bi = sum(v.numel() * v.element_size() for v in host.values()) + (g_host.numel() * 4 if do_bwd else 0)
+    bi += gf_host.numel() * 4 if (do_bwd and FT) else 0
     bo = rgb_h.numel() * 4 + tr_h.numel() * 4 + ((gw_h.numel() + gp_h.numel()) * 4 if do_bwd else 0)
+    bo += ft_h.numel() * 4 if FT else 0
 
     def step():
         for k in dd:
@@ -402,13 +453,17 @@ def run_e2e(a, wl, scene, cams, precision, do_bwd, dev):
         out = r.forward(dd["centers"], dd["scales"], dd["quats"], packed, cams)
         if do_bwd:
             g_dev.copy_(g_host, non_blocking=True)
-            g = r.backward(g_dev)
+            if FT:
+                gf_dev.copy_(gf_host, non_blocking=True)
+            g = r.backward(g_dev, None, gf_dev)
             gw_h.copy_(g["d_weights"], non_blocking=True)
             gp_h[:, 0:3].copy_(g["d_centers"], non_blocking=True)
             gp_h[:, 3:6].copy_(g["d_scales"], non_blocking=True)
             gp_h[:, 6:10].copy_(g["d_quats"], non_blocking=True)
         rgb_h.copy_(out["rgb"], non_blocking=True)
         tr_h.copy_(out["trans"], non_blocking=True)
+        if FT:
+            ft_h.copy_(out["feat"], non_blocking=True)
 
     for _ in range(2):
         step()
@@ -432,12 +487,14 @@ def cpu_baseline(a, wl, scene, cams, do_bwd, r=None):
 
     cores = os.cpu_count() or 1
     g = synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100, scale=0.01).reshape(-1, 3)
+    FT = wl.feat_dim + wl.slot_dim
 
     def run_oracle(pix):
         t = time.perf_counter()
         if do_bwd:
             idx = pix[:, 0].astype(np.int64) * wl.width * wl.height + pix[:, 2] * wl.width + pix[:, 1]
-            res = oracle.render_backward(wl, scene, cams, pix, g[idx].astype(np.float64), n_threads=cores)
+            res = oracle.render_backward(wl, scene, cams, pix, g[idx].astype(np.float64), None,
+                                         feat_grad_rows(wl, idx).astype(np.float64) if FT else None, n_threads=cores)
             rgb = res["rgb"]
         else:
             rgb, _, _ = oracle.render(wl, scene, cams, pix=pix, n_threads=cores)
@@ -478,12 +535,14 @@ def run_reference(a):
     cores = os.cpu_count() or 1
     do_bwd = a.pass_ == "fwdbwd"
     g = synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100, scale=0.01).reshape(-1, 3)
+    FT = wl.feat_dim + wl.slot_dim
     per_step = int(os.environ.get("MLPS_REF_PIXELS", "0"))  # 0: size the sample by calibration
 
     def one(pix):
         if do_bwd:
             idx = pix[:, 0].astype(np.int64) * wl.width * wl.height + pix[:, 2] * wl.width + pix[:, 1]
-            oracle.render_backward(wl, scene, cams, pix, g[idx].astype(np.float64), n_threads=cores)
+            oracle.render_backward(wl, scene, cams, pix, g[idx].astype(np.float64), None,
+                                   feat_grad_rows(wl, idx).astype(np.float64) if FT else None, n_threads=cores)
         else:
             oracle.render(wl, scene, cams, pix=pix, n_threads=cores)
 
@@ -505,6 +564,7 @@ def run_reference(a):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": tot / a.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{wl.name}: {wl.width}x{wl.height}, K={wl.K}, S={wl.samples}, "
+                                   f"{f'4 x {wl.slot_dim} feature slots, ' if wl.slot_dim else ''}"
                                    f"{wl.n_views} views", "pass": "fwd+bwd" if do_bwd else "fwd",
                        "sample_pixels_per_step": n},
             "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",

@@ -125,6 +125,92 @@ MLPS_DEV void st_row4(float* p, const float4& v, bool vec) {
   }
 }
 
+// Rays are walked tile by tile (one block per screen tile of the binning grid): the rays of a
+// tile meet the same few primitives, so their embeddings stay in the SM's L1 instead of being
+// fetched from L2 once per (ray, hit).
+struct TileRays {
+  int base, W, x0, y0, tw, th;  // ray_base of the view, its width, the tile's origin and extent
+};
+
+MLPS_DEV TileRays tile_rays(const Work& w, int t) {
+  int lo = 0, hi = w.V - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (w.views[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+  }
+  const ViewData& V = w.views[lo];
+  const int lt = t - V.tile_base;
+  TileRays r;
+  r.base = V.ray_base;
+  r.W = V.width;
+  r.x0 = (lt % V.ntx) * w.tile;
+  r.y0 = (lt / V.ntx) * w.tile;
+  r.tw = min(w.tile, V.width - r.x0);
+  r.th = min(w.tile, V.height - r.y0);
+  return r;
+}
+
+MLPS_DEV int tile_ray(const TileRays& T, int i) {  // i < tw * th, row-major in the tile
+  const int y = i / T.tw, x = i - y * T.tw;
+  return T.base + (T.y0 + y) * T.W + T.x0 + x;
+}
+
+// Per-hit scalars of one ray, held lane-parallel: lane l keeps hit l in set 0 and hit l + 32 in
+// set 1 (rays have at most 64 hits). The optical depths are summed in ray order exactly as the
+// colour composite does, so the early-termination cut and T_j are the same floats.
+struct HitSet {
+  float T, W, wgt;  // transmittance before the hit, 1 - e^{-a}, weight T W
+  float g[4];       // slot weights
+  float y[3];       // unclipped offset (for the clip mask of the reverse pass)
+  int prim;
+};
+
+MLPS_DEV void ray_hits(const Work& w, int s0, int n, int lane, HitSet (&hs)[2], int& used) {
+  float A = 0.f, aex[2] = {0.f, 0.f}, a[2] = {0.f, 0.f};
+  used = n;
+  for (int j = 0; j < n; ++j) {
+    const float aj = w.hit_out[s0 + j].w;
+    if (lane == (j & 31)) {
+      if (j < 32) { aex[0] = A; a[0] = aj; }
+      else { aex[1] = A; a[1] = aj; }
+    }
+    A += aj;
+    if (expf(-A) < w.t_eps) {
+      used = j + 1;
+      break;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int j = lane + 32 * q;
+    HitSet& H = hs[q];
+    H.T = H.W = H.wgt = 0.f;
+    H.prim = 0;
+    for (int k = 0; k < 4; ++k) H.g[k] = 0.f;
+    H.y[0] = H.y[1] = H.y[2] = 0.f;
+    if (j < used) {
+      const int h = s0 + j;
+      float u[3];
+      H.T = expf(-aex[q]);
+      H.W = -expm1f(-a[q]);
+      H.wgt = H.T * H.W;
+      hit_offset(w, h, H.y, u);
+      slot_softmax(u, H.g);
+      H.prim = w.hit_prim[h];
+    }
+  }
+}
+
+// Hit j's scalars broadcast from its lane (register selects, no local-memory indexing).
+MLPS_DEV void bcast_hit(const HitSet (&hs)[2], int j, float& wgt, float g[4], int& prim) {
+  const bool hi = j >= 32;
+  const int src = j & 31;
+  wgt = __shfl_sync(0xffffffffu, hi ? hs[1].wgt : hs[0].wgt, src);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) g[k] = __shfl_sync(0xffffffffu, hi ? hs[1].g[k] : hs[0].g[k], src);
+  prim = __shfl_sync(0xffffffffu, hi ? hs[1].prim : hs[0].prim, src);
+}
+
 // ------------------------------------------------------------------------------------------
 // Forward: F_r = sum_j w_j sum_k g_jk e_{p_j k}
 
@@ -132,40 +218,39 @@ __global__ void __launch_bounds__(32 * kSlotWarps) k_slots_fwd(Work w, int C, co
                                                               long long stride, long long slot_byte,
                                                               float* __restrict__ feat, int FT, int vec) {
   const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * kSlotWarps;
-  for (int r = blockIdx.x * kSlotWarps + (threadIdx.x >> 5); r < w.n_rays; r += nwarps) {
-    const int n = w.ray_count[r], s0 = w.ray_start[r];
-    float* out = feat + (size_t)r * FT;
-    for (int c0 = 0; c0 < C; c0 += kPassCh) {
-      float4 acc[4];
+  for (int t = blockIdx.x; t < w.n_tiles_all; t += gridDim.x) {
+    const TileRays TR = tile_rays(w, t);
+    for (int i = threadIdx.x >> 5; i < TR.tw * TR.th; i += kSlotWarps) {
+      const int r = tile_ray(TR, i);
+      HitSet hs[2];
+      int used;
+      ray_hits(w, w.ray_start[r], w.ray_count[r], lane, hs, used);
+      float* out = feat + (size_t)r * FT;
+      for (int c0 = 0; c0 < C; c0 += kPassCh) {
+        float4 acc[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      float A = 0.f;
-      for (int j = 0; j < n; ++j) {
-        const int h = s0 + j;
-        const float aj = w.hit_out[h].w;
-        const float wj = expf(-A) * -expm1f(-aj);
-        float y[3], u[3], g[4];
-        hit_offset(w, h, y, u);
-        slot_softmax(u, g);
-        const float* e = slot_emb(blob, stride, slot_byte, w.hit_prim[h]);
+        for (int q = 0; q < 4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < used; ++j) {
+          float wj, g[4];
+          int prim;
+          bcast_hit(hs, j, wj, g, prim);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) g[k] *= wj;
+          const float* e = slot_emb(blob, stride, slot_byte, prim);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = c0 + 128 * q + 4 * lane;
+            if (c < C) {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) fma4(acc[q], g[k], ld4(e + (size_t)k * C + c));
+            }
+          }
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int c = c0 + 128 * q + 4 * lane;
-          if (c < C) {
-            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) fma4(f, g[k], ld4(e + (size_t)k * C + c));
-            fma4(acc[q], wj, f);
-          }
+          if (c < C) st_row4(out + c, acc[q], vec);
         }
-        A += aj;
-        if (expf(-A) < w.t_eps) break;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int c = c0 + 128 * q + 4 * lane;
-        if (c < C) st_row4(out + c, acc[q], vec);
       }
     }
   }
@@ -174,65 +259,92 @@ __global__ void __launch_bounds__(32 * kSlotWarps) k_slots_fwd(Work w, int C, co
 // ------------------------------------------------------------------------------------------
 // Reverse, ray-major: dL/da_j (slot_ga) and (dL/du, w_j) (slot_gu) per hit
 
+MLPS_DEV float warp_excl_suffix(float v, int lane) {  // sum over higher lanes
+  float incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float u = __shfl_down_sync(0xffffffffu, incl, o);
+    if (lane + o < 32) incl += u;
+  }
+  return incl - v;
+}
+
 __global__ void __launch_bounds__(32 * kSlotWarps) k_slots_bwd_ray(Work w, int C, const unsigned char* blob,
                                                                   long long stride, long long slot_byte,
                                                                   const float* __restrict__ dF, int FT,
                                                                   int vec) {
   const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * kSlotWarps;
-  for (int r = blockIdx.x * kSlotWarps + (threadIdx.x >> 5); r < w.n_rays; r += nwarps) {
-    const int n = w.ray_count[r], s0 = w.ray_start[r];
-    const float* gF = dF + (size_t)r * FT;
-    // exclusive optical depth before hit j: lane (j & 31) of register j >> 5
-    float aex0 = 0.f, aex1 = 0.f;
-    float A = 0.f;
-    int used = 0;
-    for (int j = 0; j < n; ++j) {
-      if (lane == (j & 31)) {
-        if (j < 32) aex0 = A; else aex1 = A;
-      }
-      A += w.hit_out[s0 + j].w;
-      used = j + 1;
-      if (expf(-A) < w.t_eps) break;
-    }
-    float R = 0.f;  // sum over later hits of w_l s_l
-    for (int j = used - 1; j >= 0; --j) {
-      const int h = s0 + j;
-      const float Aex = __shfl_sync(0xffffffffu, j < 32 ? aex0 : aex1, j & 31);
-      const float aj = w.hit_out[h].w;
-      const float T = expf(-Aex);
-      const float wj = T * -expm1f(-aj);
-      float y[3], u[3], g[4];
-      hit_offset(w, h, y, u);
-      slot_softmax(u, g);
-      const float* e = slot_emb(blob, stride, slot_byte, w.hit_prim[h]);
-      float sk[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int c0 = 0; c0 < C; c0 += kPassCh) {
+  for (int t = blockIdx.x; t < w.n_tiles_all; t += gridDim.x) {
+    const TileRays TR = tile_rays(w, t);
+    for (int i = threadIdx.x >> 5; i < TR.tw * TR.th; i += kSlotWarps) {
+      const int r = tile_ray(TR, i);
+      const int n = w.ray_count[r], s0 = w.ray_start[r];
+      HitSet hs[2];
+      int used;
+      ray_hits(w, s0, n, lane, hs, used);
+      const float* gF = dF + (size_t)r * FT;
+      // s_jk = e_jk . dL/dF, kept by the hit's own lane
+      float my_s[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+      for (int j = 0; j < used; ++j) {
+        const int prim = __shfl_sync(0xffffffffu, j < 32 ? hs[0].prim : hs[1].prim, j & 31);
+        const float* e = slot_emb(blob, stride, slot_byte, prim);
+        float sk[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int c0 = 0; c0 < C; c0 += kPassCh) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int c = c0 + 128 * q + 4 * lane;
-          if (c < C) {
-            const float4 gv = ld_row4(gF + c, vec);
+          for (int q = 0; q < 4; ++q) {
+            const int c = c0 + 128 * q + 4 * lane;
+            if (c < C) {
+              const float4 gv = ld_row4(gF + c, vec);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) sk[k] += dot4(ld4(e + (size_t)k * C + c), gv);
+              for (int k = 0; k < 4; ++k) sk[k] += dot4(ld4(e + (size_t)k * C + c), gv);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sk[k] = warp_sum(sk[k]);
+        if (lane == (j & 31)) {
+          if (j < 32) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) my_s[0][k] = sk[k];
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) my_s[1][k] = sk[k];
           }
         }
       }
+      // per hit (lane-parallel): s_j, the suffix sum of w_l s_l over later hits, dL/da_j, dL/du
+      float ws[2], sj[2];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) sk[k] = warp_sum(sk[k]);
-      const float sj = g[0] * sk[0] + g[1] * sk[1] + g[2] * sk[2] + g[3] * sk[3];
-      if (lane == 0) {
-        w.slot_ga[h] = T * expf(-aj) * sj - R;
+      for (int q = 0; q < 2; ++q) {
+        const HitSet& H = hs[q];
+        sj[q] = H.g[0] * my_s[q][0] + H.g[1] * my_s[q][1] + H.g[2] * my_s[q][2] + H.g[3] * my_s[q][3];
+        ws[q] = H.wgt * sj[q];  // zero beyond `used`
+      }
+      const float tot1 = warp_sum(ws[1]);
+      const float R0 = warp_excl_suffix(ws[0], lane) + tot1;
+      const float R1 = warp_excl_suffix(ws[1], lane);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int j = lane + 32 * q;
+        if (j >= n) continue;
+        const int h = s0 + j;
+        if (j >= used) {  // beyond early termination: no gradient
+          w.slot_ga[h] = 0.f;
+          w.slot_gu[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+          continue;
+        }
+        const HitSet& H = hs[q];
+        w.slot_ga[h] = H.T * (1.f - H.W) * sj[q] - (q == 0 ? R0 : R1);
         // softmax and clip: dL/du
         float dg[4], mean = 0.f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          dg[k] = wj * sk[k];
-          mean = fmaf(g[k], dg[k], mean);
+          dg[k] = H.wgt * my_s[q][k];
+          mean = fmaf(H.g[k], dg[k], mean);
         }
         float dz[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) dz[k] = g[k] * (dg[k] - mean);
+        for (int k = 0; k < 4; ++k) dz[k] = H.g[k] * (dg[k] - mean);
         const float rr = 0.57735026918962576f;
         float gu[3];
         gu[0] = rr * (dz[0] + dz[1] - dz[2] - dz[3]);
@@ -240,14 +352,9 @@ __global__ void __launch_bounds__(32 * kSlotWarps) k_slots_bwd_ray(Work w, int C
         gu[2] = rr * (dz[0] - dz[1] - dz[2] + dz[3]);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          if (y[c] < -1.f || y[c] > 1.f) gu[c] = 0.f;
-        w.slot_gu[h] = make_float4(gu[0], gu[1], gu[2], wj);
+          if (H.y[c] < -1.f || H.y[c] > 1.f) gu[c] = 0.f;
+        w.slot_gu[h] = make_float4(gu[0], gu[1], gu[2], H.wgt);
       }
-      R = fmaf(wj, sj, R);
-    }
-    for (int j = used + lane; j < n; j += 32) {  // beyond early termination: no gradient
-      w.slot_ga[s0 + j] = 0.f;
-      w.slot_gu[s0 + j] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
 }
@@ -419,18 +526,18 @@ static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 void launch_slots_fwd(const Work& w, const Model& m, const Packed& pk, const unsigned char* weights,
                       float* feat, int row_stride, cudaStream_t st) {
-  if (w.n_rays == 0 || m.C == 0) return;
+  if (w.n_rays == 0 || w.n_tiles_all == 0 || m.C == 0) return;
   const int vec = aligned16(feat) && row_stride % 4 == 0;
-  const int grid = std::min((w.n_rays + kSlotWarps - 1) / kSlotWarps, 1 << 20);
+  const int grid = std::min(w.n_tiles_all, 1 << 20);
   k_slots_fwd<<<grid, 32 * kSlotWarps, 0, st>>>(
       w, m.C, weights, pk.stride, pk.slot_byte, feat, row_stride, vec);
 }
 
 void launch_slots_bwd_ray(const Work& w, const Model& m, const Packed& pk, const unsigned char* weights,
                           const float* d_feat, int row_stride, cudaStream_t st) {
-  if (w.n_rays == 0 || m.C == 0) return;
+  if (w.n_rays == 0 || w.n_tiles_all == 0 || m.C == 0) return;
   const int vec = aligned16(d_feat) && row_stride % 4 == 0;
-  const int grid = std::min((w.n_rays + kSlotWarps - 1) / kSlotWarps, 1 << 20);
+  const int grid = std::min(w.n_tiles_all, 1 << 20);
   k_slots_bwd_ray<<<grid, 32 * kSlotWarps, 0, st>>>(
       w, m.C, weights, pk.stride, pk.slot_byte, d_feat, row_stride, vec);
 }

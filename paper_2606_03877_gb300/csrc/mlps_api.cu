@@ -300,6 +300,7 @@ Work make_work(const mlps_config* c, const Layout& L, int K, int V, void* saved,
   w.tile = c->tile;
   w.n_pairs = (int)L.n_pairs;
   w.max_view_tiles = L.max_view_tiles;
+  w.n_tiles_all = (int)L.n_tiles_all;
   w.n_rays = (int)L.n_rays;
   w.hit_cap = (int)L.hit_cap;
   w.max_hits = c->max_hits_per_ray;

@@ -264,6 +264,7 @@ struct Work {
   int tile;
   int n_pairs;           // sum over views of prim_n
   int max_view_tiles;    // largest tile count of a view (grid size of the per-tile kernels)
+  int n_tiles_all;       // tiles of all views
   int n_rays;
   int hit_cap;
   int max_hits;

@@ -151,6 +151,9 @@ CONFIGS: Dict[str, SceneConfig] = {
     # the paper's own per-primitive model: gamma([d; delta]) with L = 6 (72 inputs), 32 x 2, S = 1,
     # on the views and primitives of the precision workload
     "contact": SceneConfig("contact", 1920, 1080, 256, 8, 6, 6, 32, 2, 0, 1, "fp32", 1),
+    # the paper's model with its semantic feature slots: four 512-d embeddings per primitive,
+    # 1080p x 2 views (a 512-channel FP32 feature map is 2 KB per pixel)
+    "slots": SceneConfig("slots", 1920, 1080, 256, 2, 6, 6, 32, 2, 0, 1, "fp32", 1, 512),
 }
 
 # Batched workload: 32 scenes, K ~ U{16..512}, resolution uniform over these four.
