@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: the test suite, the package smoke check and the benchm
 CPU-baseline leg are the only callers. The CUDA library and its Python binding never import
 this package, and this package imports nothing from them: configs are taken by duck typing
 (any object with ``xyz_freqs, dir_freqs, hidden_width, hidden_layers, feat_dim, samples`` and
-optional ``contact`` and ``slot_dim``) and
+optional ``contact``, ``slot_dim`` and ``tile_sort``) and
 scenes / cameras as plain numpy arrays and dicts.
 
 All inputs are converted to float64 before the call; outputs are float64.
@@ -30,7 +30,7 @@ _lib = None
 class _Cfg(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("xyz_freqs", "dir_freqs", "hidden_width", "hidden_layers", "feat_dim", "samples",
-                 "contact", "slot_dim")]
+                 "contact", "slot_dim", "tile_sort")]
 
 
 class _Cam(ctypes.Structure):
@@ -70,7 +70,7 @@ def _load():
                                                 P(_Cam), ctypes.c_int, i, d, d, d, d, d, d, d, d,
                                                 d, d, ctypes.c_int]
             lib.orc_ray_hits.argtypes = [ctypes.c_int, d, d, d, P(_Cam), ctypes.c_int, ctypes.c_int,
-                                         ctypes.c_int, i, d, d, d, d]
+                                         ctypes.c_int, ctypes.c_int, i, d, d, d, d]
             lib.orc_ray_m2.argtypes = [ctypes.c_int, d, d, d, P(_Cam), ctypes.c_int, ctypes.c_int, d, d]
             lib.orc_pixel_ray.argtypes = [P(_Cam), ctypes.c_int, ctypes.c_int, d, d]
             lib.orc_encode.argtypes = [P(_Cfg), d, d, d]
@@ -83,7 +83,7 @@ def _load():
 def _cfg(c) -> _Cfg:
     return _Cfg(int(c.xyz_freqs), int(c.dir_freqs), int(c.hidden_width), int(c.hidden_layers),
                 int(c.feat_dim), int(c.samples), int(getattr(c, "contact", 0)),
-                int(getattr(c, "slot_dim", 0)))
+                int(getattr(c, "slot_dim", 0)), int(getattr(c, "tile_sort", 0)))
 
 
 def _cam(c: Dict) -> _Cam:
@@ -204,15 +204,16 @@ def render_backward(cfg, scene, cams: Sequence[Dict], pix: Optional[np.ndarray],
             "d_scales": ds, "d_quats": dq}
 
 
-def ray_hits(scene, cam: Dict, x: int, y: int):
-    """Sorted hits of one pixel's ray: dict of arrays prim, key, t0, t1, m2."""
+def ray_hits(scene, cam: Dict, x: int, y: int, tile: int = 0):
+    """Sorted hits of one pixel's ray: dict of arrays prim, key, t0, t1, m2 (tile > 0: in the
+    tile-centre order of tile x tile tiles, key = the tile key)."""
     lib = _load()
     c, s, q = _geom(scene)
     K = c.shape[0]
     cap = max(K, 1)
     prim = np.zeros(cap, dtype=np.int32)
     key = np.zeros(cap); t0 = np.zeros(cap); t1 = np.zeros(cap); m2 = np.zeros(cap)
-    n = lib.orc_ray_hits(K, _dp(c), _dp(s), _dp(q), ctypes.byref(_cam(cam)), int(x), int(y), cap,
+    n = lib.orc_ray_hits(K, _dp(c), _dp(s), _dp(q), ctypes.byref(_cam(cam)), int(x), int(y), int(tile), cap,
                          prim.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(key), _dp(t0), _dp(t1),
                          _dp(m2))
     if n < 0:

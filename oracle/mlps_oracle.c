@@ -49,6 +49,12 @@
  * hit's compositing weight (the sum of T alpha over its samples; T_i alpha_i for S = 1). It is
  * returned after the MLP's extra outputs.
  *
+ * Tile-centre ordering (tile_sort = T > 0, Sec. 3.3 and App. A.4): the image is cut into T x T
+ * tiles, and every pixel composites its hits in the order of the sort key max(0, t*) computed
+ * for the virtual ray through its tile's centre (image point (T tx + T/2, T ty + T/2)) instead
+ * of its own ray, ties by primitive index. Hit sets, intervals, samples and MLP inputs stay the
+ * pixel's own.
+ *
  * Readings of points the paper leaves open (scalar delta of Eq. 6 = the sample step, support
  * = unit-Mahalanobis ellipsoid, falloff off, interval-by-interval compositing, tie-break,
  * camera model, background) are listed with the design notes of the repository.
@@ -73,6 +79,7 @@ typedef struct {
   int samples;       /* S midpoint samples per hit interval */
   int contact;       /* 1: contact-point mode (S = 1, input gamma([d; delta])) */
   int slot_dim;      /* C of the four slot embeddings per primitive (Sec. 3.4); 0 = none */
+  int tile_sort;     /* T > 0: order hits by the tile-centre virtual ray of T x T tiles; 0 = exact */
 } orc_cfg;
 
 typedef struct {
@@ -116,7 +123,7 @@ static int cfg_valid(const orc_cfg* c) {
       c->feat_dim < 0 || c->samples <= 0)
     return 0;
   if (c->contact != 0 && (c->contact != 1 || c->samples != 1)) return 0;
-  if (c->slot_dim < 0) return 0;
+  if (c->slot_dim < 0 || c->tile_sort < 0) return 0;
   if (orc_num_layers(c) > ORC_MAX_LAYERS) return 0;
   return 1;
 }
@@ -151,9 +158,10 @@ static void prim_setup(const double* mu, const double* s, const double* q, prim_
     for (int j = 0; j < 3; ++j) g->M[i * 3 + j] = g->R[j * 3 + i] / s[i];
 }
 
-static void make_ray(const orc_cam* cam, int x, int y, double* o, double* d) {
+/* Ray through the image point (u, v) (pixel x covers [x, x + 1); its centre is x + 1/2). */
+static void make_ray_uv(const orc_cam* cam, double u, double v, double* o, double* d) {
   const double* P = cam->w2c;
-  double dc[3] = {(x + 0.5 - cam->cx) / cam->fx, (y + 0.5 - cam->cy) / cam->fy, 1.0};
+  double dc[3] = {(u - cam->cx) / cam->fx, (v - cam->cy) / cam->fy, 1.0};
   double t[3] = {P[3], P[7], P[11]};
   for (int i = 0; i < 3; ++i) {
     /* R^T: column i of R = (P[i], P[4+i], P[8+i]) */
@@ -162,6 +170,10 @@ static void make_ray(const orc_cam* cam, int x, int y, double* o, double* d) {
   }
   double n = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
   for (int i = 0; i < 3; ++i) d[i] /= n;
+}
+
+static void make_ray(const orc_cam* cam, int x, int y, double* o, double* d) {
+  make_ray_uv(cam, x + 0.5, y + 0.5, o, d);
 }
 
 typedef struct {
@@ -216,6 +228,40 @@ static int hit_cmp(const void* pa, const void* pb) {
   if (a->t0 < b->t0) return -1;
   if (a->t0 > b->t0) return 1;
   return (a->prim > b->prim) - (a->prim < b->prim);
+}
+
+static int hit_cmp_tile(const void* pa, const void* pb) {
+  const hit_t* a = (const hit_t*)pa;
+  const hit_t* b = (const hit_t*)pb;
+  if (a->key < b->key) return -1;
+  if (a->key > b->key) return 1;
+  return (a->prim > b->prim) - (a->prim < b->prim);
+}
+
+/* Order a pixel's hits: by its own max(0, t*) (Eq. 2), or with tile > 0 by max(0, t*) of the
+ * virtual ray through the centre of the pixel's tile, d^T Lambda (mu - o) / d^T Lambda d with
+ * that ray's d (Sec. 3.3). The hits keep their own intervals; only key and order change. */
+static void order_hits(const prim_geo* geo, const orc_cam* cam, int x, int y, int tile, hit_t* hits, int nh) {
+  if (tile <= 0) {
+    qsort(hits, (size_t)nh, sizeof(hit_t), hit_cmp);
+    return;
+  }
+  double oc[3], dc[3];
+  make_ray_uv(cam, (double)(x / tile) * tile + 0.5 * tile, (double)(y / tile) * tile + 0.5 * tile, oc, dc);
+  for (int i = 0; i < nh; ++i) {
+    const prim_geo* g = &geo[hits[i].prim];
+    double op[3], dp[3];
+    for (int r = 0; r < 3; ++r) {
+      op[r] = 0; dp[r] = 0;
+      for (int cc = 0; cc < 3; ++cc) {
+        op[r] += g->M[r * 3 + cc] * (oc[cc] - g->mu[cc]);
+        dp[r] += g->M[r * 3 + cc] * dc[cc];
+      }
+    }
+    double ts = -(op[0] * dp[0] + op[1] * dp[1] + op[2] * dp[2]) / (dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2]);
+    hits[i].key = ts > 0 ? ts : 0;
+  }
+  qsort(hits, (size_t)nh, sizeof(hit_t), hit_cmp_tile);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -511,7 +557,7 @@ static int render_pixel(job_t* j, int idx, scratch_t* s) {
   int nh = 0;
   for (int p = 0; p < j->K; ++p)
     if (intersect(&j->geo[p], o, d, cam->near_t, p, &s->hits[nh], NULL)) ++nh;
-  qsort(s->hits, (size_t)nh, sizeof(hit_t), hit_cmp);
+  order_hits(j->geo, cam, x, y, c->tile_sort, s->hits, nh);
 
   int S = c->samples, F = c->feat_dim, NO = m->nout;
   long ns = (long)nh * S;
@@ -844,23 +890,25 @@ int orc_render_backward(const orc_cfg* cfg, int K, const double* centers, const 
   return st;
 }
 
-/* Sorted hit list of one pixel: up to max_out entries of (prim, key, t0, t1, m2). Returns the
- * number of hits (may exceed max_out; only max_out are written), or -1 on invalid input. */
+/* Sorted hit list of one pixel (tile > 0: in the tile-centre order of T x T tiles, `key` the
+ * tile key): up to max_out entries of (prim, key, t0, t1, m2). Returns the number of hits (may
+ * exceed max_out; only max_out are written), or -1 on invalid input. */
 int orc_ray_hits(int K, const double* centers, const double* scales, const double* quats,
-                 const orc_cam* cam, int x, int y, int max_out, int* prim, double* key, double* t0,
-                 double* t1, double* m2) {
-  if (K < 0 || x < 0 || y < 0 || x >= cam->width || y >= cam->height) return -1;
+                 const orc_cam* cam, int x, int y, int tile, int max_out, int* prim, double* key,
+                 double* t0, double* t1, double* m2) {
+  if (K < 0 || tile < 0 || x < 0 || y < 0 || x >= cam->width || y >= cam->height) return -1;
   hit_t* hits = (hit_t*)malloc(sizeof(hit_t) * (size_t)(K > 0 ? K : 1));
-  if (!hits) return -1;
+  prim_geo* geo = (prim_geo*)malloc(sizeof(prim_geo) * (size_t)(K > 0 ? K : 1));
+  if (!hits || !geo) { free(hits); free(geo); return -1; }
   double o[3], d[3];
   make_ray(cam, x, y, o, d);
   int nh = 0;
   for (int p = 0; p < K; ++p) {
-    prim_geo g;
-    prim_setup(centers + 3 * p, scales + 3 * p, quats + 4 * p, &g);
-    if (intersect(&g, o, d, cam->near_t, p, &hits[nh], NULL)) ++nh;
+    prim_setup(centers + 3 * p, scales + 3 * p, quats + 4 * p, &geo[p]);
+    if (intersect(&geo[p], o, d, cam->near_t, p, &hits[nh], NULL)) ++nh;
   }
-  qsort(hits, (size_t)nh, sizeof(hit_t), hit_cmp);
+  order_hits(geo, cam, x, y, tile, hits, nh);
+  free(geo);
   for (int i = 0; i < nh && i < max_out; ++i) {
     prim[i] = hits[i].prim; key[i] = hits[i].key; t0[i] = hits[i].t0; t1[i] = hits[i].t1;
     m2[i] = hits[i].m2;

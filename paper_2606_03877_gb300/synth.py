@@ -110,6 +110,7 @@ class SceneConfig:
     precision: str = "fp32"
     contact: int = 0  # 1: contact-point input gamma([d; mu - p*]), one sample per hit (S = 1)
     slot_dim: int = 0  # C of the four slot embeddings per primitive (feature slots); 0 = none
+    tile_sort: int = 0  # T > 0: hits ordered by the tile-centre ray of T x T tiles; 0 = per ray
 
     @property
     def input_dim(self) -> int:

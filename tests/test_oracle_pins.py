@@ -60,9 +60,21 @@ def _rot(q):
     return Rotation.from_quat([x, y, z, w]).as_matrix()  # scipy is scalar-last; normalises
 
 
-def _np_hits(scene, cam, x, y):
-    """Hits by the quadratic-formula roots of (o+td-mu)^T Lambda (o+td-mu) = 1 (Eq. 1-2)."""
+def _ray_np_uv(cam, u, v):
+    """Ray through the image point (u, v) (pixel centres at x + 1/2)."""
+    P = np.asarray(cam["w2c"], dtype=np.float64).reshape(3, 4)
+    R, t = P[:, :3], P[:, 3]
+    dc = np.array([(u - cam["cx"]) / cam["fx"], (v - cam["cy"]) / cam["fy"], 1.0])
+    d = R.T @ dc
+    return -R.T @ t, d / np.linalg.norm(d)
+
+
+def _np_hits(scene, cam, x, y, tile=0):
+    """Hits by the quadratic-formula roots of (o+td-mu)^T Lambda (o+td-mu) = 1 (Eq. 1-2). With
+    tile > 0 they are ordered by max(0, t*) of the ray through the tile centre (Sec. 3.3)."""
     o, d = _ray_np(cam, x, y)
+    if tile:
+        _, dcen = _ray_np_uv(cam, (x // tile) * tile + tile / 2.0, (y // tile) * tile + tile / 2.0)
     hits = []
     for i in range(scene["centers"].shape[0]):
         mu = scene["centers"][i].astype(np.float64)
@@ -81,8 +93,15 @@ def _np_hits(scene, cam, x, y):
         t0 = max(r0, cam.get("near", 0.0))
         if not r1 > t0:
             continue
-        hits.append((max(0.0, tstar), t0, i, r1, tstar, r0))
+        key = max(0.0, tstar)
+        if tile:
+            key = max(0.0, (dcen @ Lam @ (mu - o)) / (dcen @ Lam @ dcen))
+            hits.append((key, i, t0, r1, tstar, r0))
+        else:
+            hits.append((key, t0, i, r1, tstar, r0))
     hits.sort()
+    if tile:  # back to the (key, t0, i, ...) layout
+        hits = [(k, t0, i, r1, ts, r0) for k, i, t0, r1, ts, r0 in hits]
     return o, d, hits
 
 
@@ -156,11 +175,15 @@ def _np_slot_feature(cfg, scene, i, o, d, tstar):
 
 
 def _np_render_pixel(cfg, scene, cam, x, y):
+    return _np_render_pixel_hits(cfg, scene, cam, x, y, getattr(cfg, "tile_sort", 0))
+
+
+def _np_render_pixel_hits(cfg, scene, cam, x, y, tile):
     """Independent restatement: quadratic roots, library rotations, matmul MLP, and the
     product form T_j = prod_{l<j} (1 - alpha_l) of the discrete operator (App. D.1). In
     contact-point mode the input is gamma([d; mu - p*]) with p* = o + max(0, t*) d and t* in
     Eq. 2's world-frame form d^T Lambda (mu - o) / d^T Lambda d."""
-    o, d, hits = _np_hits(scene, cam, x, y)
+    o, d, hits = _np_hits(scene, cam, x, y, tile)
     C = np.zeros(3)
     F = np.zeros(cfg.feat_dim)
     Fs = np.zeros(cfg.slot_dim)
@@ -485,6 +508,58 @@ def test_slots_match_independent_restatement(contact, S, feat):
         assert np.allclose(Fo[n], F2, atol=1e-10), (x, y)
         hit += T2 < 1
     assert hit > 20
+
+
+@pytest.mark.parametrize("T", [8, 16])
+def test_tile_centre_order_matches_restatement(T):
+    """Sec. 3.3 / App. A.4: with T x T tiles every pixel composites its own hits in the order of
+    max(0, t*) along the virtual ray through its tile's centre. The oracle against the numpy
+    restatement (quadratic roots, Lambda-form t* of the centre ray); on this dense scene the order
+    differs from the exact one on some pixels, so the mode is not a no-op."""
+    cfg = synth.SceneConfig("t", 40, 30, 24, 1, 4, 2, 16, 2, 0, 3, tile_sort=T)
+    scene = synth.make_scene(cfg, 11)
+    scene = dict(scene, scales=scene["scales"] * 3.0)
+    cam = synth.make_camera(40, 30, 2, radius=2.6)
+    rgb, Tr, _ = oracle.render(cfg, scene, [cam])
+    rgb_x, Tr_x, _ = oracle.render(cfg.replace(tile_sort=0), scene, [cam])
+    assert np.allclose(Tr, Tr_x, atol=1e-12)  # the order changes no transmittance
+    differ = 0
+    for n, (v, x, y) in enumerate(oracle.all_pixels([cam])):
+        C2, T2, _ = _np_render_pixel(cfg, scene, cam, x, y)
+        assert np.allclose(rgb[n], C2, atol=1e-10), (x, y)
+        oh = oracle.ray_hits(scene, cam, x, y, tile=T)
+        assert list(oh["prim"]) == [h[2] for h in _np_hits(scene, cam, x, y, T)[2]]
+        differ += not np.allclose(rgb[n], rgb_x[n], atol=1e-9)
+    assert differ > 5
+
+
+def test_tile_centre_key_is_clamped_at_zero():
+    """Camera inside two large primitives whose centres lie behind it: along the tile-centre ray
+    both have t* < 0, so both keys are max(0, t*) = 0 and the tie goes to the lower primitive
+    index, whatever their unclamped t* (restatement with the clamp)."""
+    cfg = synth.SceneConfig("t", 16, 16, 2, 1, 4, 2, 16, 2, 0, 2, tile_sort=8)
+    cam = synth.make_camera(16, 16, 5, radius=2.5)
+    o, d = _ray_np(cam, 8, 8)
+    scene = synth.make_scene(cfg, 13)
+    scene["centers"] = np.stack([o - 0.05 * d, o - 0.35 * d]).astype(np.float32)  # unclamped: 1 first
+    scene["scales"] = np.array([[1.2, 1.0, 1.1], [0.9, 1.3, 1.0]], np.float32)
+    rgb, _, _ = oracle.render(cfg, scene, [cam])
+    for n, (v, x, y) in enumerate(oracle.all_pixels([cam])):
+        oh = oracle.ray_hits(scene, cam, x, y, tile=8)
+        assert list(oh["prim"]) == [0, 1] and np.all(oh["key"] == 0.0), (x, y, oh)
+        C2, _, _ = _np_render_pixel(cfg, scene, cam, x, y)
+        assert np.allclose(rgb[n], C2, atol=1e-10)
+
+
+def test_tile_of_one_pixel_is_the_exact_order():
+    """T = 1: the tile centre is the pixel centre, so the order is the exact one of Eq. 2."""
+    cfg = synth.SceneConfig("t", 24, 18, 16, 1, 4, 2, 16, 2, 0, 3, tile_sort=1)
+    scene = synth.make_scene(cfg, 12)
+    scene = dict(scene, scales=scene["scales"] * 3.0)
+    cam = synth.make_camera(24, 18, 3, radius=2.6)
+    rgb, Tr, _ = oracle.render(cfg, scene, [cam])
+    rgb_x, Tr_x, _ = oracle.render(cfg.replace(tile_sort=0), scene, [cam])
+    assert np.array_equal(rgb, rgb_x) and np.array_equal(Tr, Tr_x)
 
 
 def test_encoding_order_probe():
