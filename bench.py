@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--width", type=int, default=0, help="override (profiling captures only)")
     ap.add_argument("--height", type=int, default=0, help="override (profiling captures only)")
     ap.add_argument("--views", type=int, default=0, help="override (profiling captures only)")
+    ap.add_argument("--tile-sort", type=int, default=0,
+                    help="T > 0: hits ordered by the tile-centre ray of T x T tiles (8 or 16)")
     ap.add_argument("--mlp-groups", type=int, default=0,
                     help="forward tensor-core MLP samples per CTA in 128-row chunks (0 = library default)")
     ap.add_argument("--compare", action="store_true",
@@ -161,6 +163,8 @@ def _workload(a):
         kw["height"] = a.height
     if a.views:
         kw["n_views"] = a.views
+    if a.tile_sort:
+        kw["tile_sort"] = a.tile_sort
     return wl.replace(**kw) if kw else wl
 
 
@@ -398,6 +402,7 @@ def run_ours(a):
                                f"{'x'.join([str(wl.hidden_width)] * wl.hidden_layers)}-{wl.output_dim}, S={S}, "
                                f"{'contact-point input, ' if wl.contact else ''}"
                                f"{f'4 x {wl.slot_dim} feature slots, ' if wl.slot_dim else ''}"
+                               f"{f'tile-centre order ({wl.tile_sort}x{wl.tile_sort} tiles), ' if wl.tile_sort else ''}"
                                f"{wl.n_views} views/rank",
                    "pass": "fwd+bwd" if do_bwd else "fwd", "precision": precision,
                    "rays_per_step": n_rays * ws, "hits_per_step": n_hits,

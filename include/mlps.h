@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define MLPS_ABI_VERSION 4
+#define MLPS_ABI_VERSION 5
 #define MLPS_MAX_VIEWS 64
 
 typedef int32_t mlps_status;
@@ -106,7 +106,13 @@ typedef struct {
                                    F_slot = sum_i w_i f_i uses each hit's compositing weight w_i
                                    and is returned in the `feat` rows after the feat_dim MLP
                                    outputs (rows of feat_dim + slot_dim floats). */
-  int32_t reserved[2];          /* must be zero */
+  int32_t tile_sort;            /* 0: every ray composites its hits in its own order of
+                                   max(0, t*) (Eq. 2, exact); 1: in the order of max(0, t*) along
+                                   the virtual ray through the centre of its `tile` x `tile`
+                                   screen tile (the approximate order of Sec. 3.3 and App. A.4),
+                                   ties by primitive index. Hit intervals, samples and MLP inputs
+                                   stay per ray. */
+  int32_t reserved[1];          /* must be zero */
 } mlps_config;
 
 typedef struct {

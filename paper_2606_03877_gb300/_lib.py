@@ -40,7 +40,7 @@ class MlpsConfig(ctypes.Structure):
                 ("hit_capacity_per_ray", ctypes.c_float), ("t_eps", ctypes.c_float),
                 ("tile", ctypes.c_int32), ("mlp_groups", ctypes.c_int32),
                 ("contact", ctypes.c_int32), ("slot_dim", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("tile_sort", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class MlpsCamera(ctypes.Structure):

@@ -271,6 +271,7 @@ template <int TILE>
 __global__ void __launch_bounds__(TILE* TILE) k_intersect(Work w) {
   constexpr int NT = TILE * TILE;
   __shared__ CandGeo scand[kCandBatch];
+  __shared__ float skey[kCandBatch];  // tile-centre sort keys (tile_sort mode)
   __shared__ int shist[kHist];
   __shared__ int swarp[NT / 32];
   __shared__ int sbase;
@@ -307,6 +308,20 @@ __global__ void __launch_bounds__(TILE* TILE) k_intersect(Work w) {
       for (int k = 0; k < 9; ++k) { cg.Mhi[k] = g.Mhi[k]; cg.Mlo[k] = g.Mlo[k]; }
       for (int k = 0; k < 3; ++k) { cg.op_hi[k] = pv.op_hi[k]; cg.op_lo[k] = pv.op_lo[k]; }
       scand[i] = cg;
+      if (w.tile_sort) {
+        // max(0, t*) of the virtual ray through the tile centre, t* = -(o'.d'_c) / |d'_c|^2
+        dfl dc[3], dp[3], op[3];
+        ray_dir_df_uv(sv, (float)(tx * TILE) + 0.5f * TILE, (float)(ty * TILE) + 0.5f * TILE, dc);
+        for (int k = 0; k < 3; ++k) {
+          dfl a = df_mul({g.Mhi[k * 3 + 0], g.Mlo[k * 3 + 0]}, dc[0]);
+          a = df_add(a, df_mul({g.Mhi[k * 3 + 1], g.Mlo[k * 3 + 1]}, dc[1]));
+          a = df_add(a, df_mul({g.Mhi[k * 3 + 2], g.Mlo[k * 3 + 2]}, dc[2]));
+          dp[k] = a;
+          op[k] = {pv.op_hi[k], pv.op_lo[k]};
+        }
+        const float ts = df_to_f(df_neg(df_div(df_dot3(op, dp), df_dot3(dp, dp))));
+        skey[i] = ts > 0.f ? ts : 0.f;
+      }
     }
     __syncthreads();
     if (!inside) continue;
@@ -314,7 +329,8 @@ __global__ void __launch_bounds__(TILE* TILE) k_intersect(Work w) {
       const CandGeo& cg = scand[i];
       HitGeom hg = intersect_df(cg.Mhi, cg.Mlo, cg.op_hi, cg.op_lo, d, near_t);
       if (!hg.hit) continue;
-      const float key = hg.key, t0 = hg.tmid + hg.r0;
+      // exact order: the ray's own (key, t0); tile order: the tile-centre key, ties by index
+      const float key = w.tile_sort ? skey[i] : hg.key, t0 = w.tile_sort ? 0.f : hg.tmid + hg.r0;
       const int c = base + i;
       // insertion from the back; equal (key, t0) keeps the lower primitive index first
       int j = n;

@@ -91,8 +91,9 @@ mlps_status check_cfg(const mlps_config* c) {
   if (!finite_f(c->hit_capacity_per_ray) || !(c->hit_capacity_per_ray > 0.f))
     return MLPS_ERR_INVALID_ARGUMENT;
   if (!finite_f(c->t_eps) || c->t_eps < 0.f || c->t_eps >= 1.f) return MLPS_ERR_INVALID_ARGUMENT;
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 1; ++i)
     if (c->reserved[i] != 0) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->tile_sort != 0 && c->tile_sort != 1) return MLPS_ERR_INVALID_ARGUMENT;
   if (c->contact != 0 && (c->contact != 1 || c->samples != 1)) return MLPS_ERR_INVALID_ARGUMENT;
   if (c->slot_dim < 0 || c->slot_dim > kMaxSlotDim) return MLPS_ERR_INVALID_ARGUMENT;
   if (c->slot_dim % 4 != 0) return MLPS_ERR_UNSUPPORTED;  // float4 channel groups
@@ -298,6 +299,7 @@ Work make_work(const mlps_config* c, const Layout& L, int K, int V, void* saved,
   w.nty = L.nty0;
   w.n_tiles = L.ntx0 * L.nty0;
   w.tile = c->tile;
+  w.tile_sort = c->tile_sort;
   w.n_pairs = (int)L.n_pairs;
   w.max_view_tiles = L.max_view_tiles;
   w.n_tiles_all = (int)L.n_tiles_all;

@@ -158,10 +158,10 @@ struct PrimView {
 };
 
 // Unit ray direction of pixel (x, y) in double-float (the hit test's precision).
-MLPS_DEV void ray_dir_df(const ViewData& V, int x, int y, dfl d[3]) {
-  // x + 0.5 - cx and y + 0.5 - cy are exact in FP32 (half-integers, |.| < 2^22)
-  float nx = __fsub_rn(__fadd_rn((float)x, 0.5f), V.cx);
-  float ny = __fsub_rn(__fadd_rn((float)y, 0.5f), V.cy);
+// Unit direction of the ray through the image point (u, v) (pixel x spans [x, x + 1)).
+MLPS_DEV void ray_dir_df_uv(const ViewData& V, float u, float v, dfl d[3]) {
+  float nx = __fsub_rn(u, V.cx);
+  float ny = __fsub_rn(v, V.cy);
   dfl dc0 = df_div(df_make(nx), df_make(V.fx));
   dfl dc1 = df_div(df_make(ny), df_make(V.fy));
   // R^T dc: component i = R[0][i] dc0 + R[1][i] dc1 + R[2][i] * 1
@@ -173,6 +173,11 @@ MLPS_DEV void ray_dir_df(const ViewData& V, int x, int y, dfl d[3]) {
   }
   dfl n = df_sqrt(n2);
   for (int i = 0; i < 3; ++i) d[i] = df_div(d[i], n);
+}
+
+MLPS_DEV void ray_dir_df(const ViewData& V, int x, int y, dfl d[3]) {
+  // x + 0.5 is exact in FP32 (half-integers, |.| < 2^22)
+  ray_dir_df_uv(V, __fadd_rn((float)x, 0.5f), __fadd_rn((float)y, 0.5f), d);
 }
 
 // Unit ray direction in plain FP32 (inputs of the MLP; smooth, so FP32 suffices).
@@ -262,6 +267,7 @@ struct Work {
   int K, V;
   int H, W, ntx, nty, n_tiles;  // view 0's sizes (the single-scene inspection calls use them)
   int tile;
+  int tile_sort;         // 1: hits ordered by the tile-centre virtual ray (Sec. 3.3)
   int n_pairs;           // sum over views of prim_n
   int max_view_tiles;    // largest tile count of a view (grid size of the per-tile kernels)
   int n_tiles_all;       // tiles of all views

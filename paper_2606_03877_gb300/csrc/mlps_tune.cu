@@ -24,7 +24,7 @@ std::map<std::string, std::pair<int, int>> g_tune_cache;  // key -> (tile, mlp_g
 std::string tune_key(const mlps_config* c, const mlps_batch_item* items, int n, int do_backward) {
   std::string k;
   const int32_t head[] = {c->xyz_freqs, c->dir_freqs, c->hidden_width, c->hidden_layers, c->feat_dim,
-                          c->samples, c->precision, c->max_hits_per_ray, c->contact, c->slot_dim,
+                          c->samples, c->precision, c->max_hits_per_ray, c->contact, c->slot_dim, c->tile_sort,
                           do_backward};
   k.append(reinterpret_cast<const char*>(head), sizeof(head));
   for (int i = 0; i < n; ++i) {
@@ -116,7 +116,9 @@ extern "C" mlps_status mlps_autotune_batch(
   if (tc && cfg->hidden_width == 64 && cfg->feat_dim == 0) groups = {6, 5, 4, 3, 2};
   float best = -1.f;
   int best_tile = cfg->tile, best_groups = cfg->mlp_groups, nc = 0;
-  for (int tile : {16, 8}) {
+  // with the tile-centre order the tile edge is part of the result, not a schedule: keep it
+  const std::vector<int> tiles = cfg->tile_sort ? std::vector<int>{cfg->tile} : std::vector<int>{16, 8};
+  for (int tile : tiles) {
     for (int g : groups) {
       mlps_config c = *cfg;
       c.tile = tile;

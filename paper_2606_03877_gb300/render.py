@@ -27,6 +27,10 @@ def make_config(shape, precision: str = "fp32", t_eps: float = 1e-6, max_hits: i
     cfg.mlp_groups = int(mlp_groups)
     cfg.contact = int(getattr(shape, "contact", 0))
     cfg.slot_dim = int(getattr(shape, "slot_dim", 0))
+    T = int(getattr(shape, "tile_sort", 0))  # tile-centre order of T x T tiles (T = 8 or 16)
+    if T:
+        cfg.tile_sort = 1
+        cfg.tile = T
     return cfg
 
 

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert _lib.mlps_abi_version() == 4
+    assert _lib.mlps_abi_version() == 5
     for s in range(8):
         assert _lib.mlps_status_string(s)
     assert _lib.mlps_status_string(4) == "hit capacity overflow"
@@ -65,7 +65,7 @@ def test_config_validation(lib):
     cfg.hidden_width = 48
     assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_UNSUPPORTED
     cfg = make_config(base)
-    cfg.reserved[1] = 1
+    cfg.reserved[0] = 1
     assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_INVALID_ARGUMENT
 
 
