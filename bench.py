@@ -695,12 +695,119 @@ def run_batch(a):
         print(json.dumps(line), flush=True)
 
 
+def run_train(a):
+    """Training workload (Sec. 3.5, App. A.4): the paper's contact-point model with four 512-d
+    feature slots, K = 256. A step trains on 4 views of 1200 x 680 (the Replica resolution),
+    cycling through 16 seeded views. The targets are the colour and slot maps of a perturbed copy
+    of the scene, rendered once before timing. A seeded quarter of each view's 8 x 8 tiles enters
+    the loss. One step = pack + forward + L1/SSIM + L1 feature loss + backward + Adam, all
+    library kernels. value = rendered pixels per second."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_03877_gb300 import _lib, synth
+    from paper_2606_03877_gb300.render import Renderer
+    from paper_2606_03877_gb300.train import Trainer
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = _workload(a)
+    V, H, W, C = wl.n_views, wl.height, wl.width, wl.slot_dim
+    scene = synth.make_scene(wl, rank)
+    target = synth.perturb_scene(scene, wl, 1000 + rank)
+    pool = synth.make_cameras(wl.replace(n_views=16), first_view_seed=rank_view_seed(rank, 16))
+    batches = [pool[4 * b:4 * b + 4] for b in range(4)]
+    # targets: the perturbed scene rendered once per batch of views (inputs, not timed)
+    r_t = Renderer(wl, precision="fp32", device=str(dev))
+    dt = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in target.items()}
+    tgts = []
+    for cams in batches:
+        o = r_t.forward(dt["centers"], dt["scales"], dt["quats"], r_t.pack(dt["weights"]), cams)
+        tgts.append((o["rgb"].clone(), o["feat"].clone()))
+    del r_t
+    tr = Trainer(wl, scene, precision="fp32", device=str(dev), seed=rank)
+
+    def step(i):
+        cams = batches[i % 4]
+        return tr.step(cams, tgts[i % 4][0], tgts[i % 4][1])
+
+    first = float(step(0)[0])
+    for i in range(1, a.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    _lib.mlps_profiler_read(reset=True)
+    _lib.mlps_profiler_enable(True)
+    step(a.warmup)
+    torch.cuda.synchronize()
+    _lib.mlps_profiler_enable(False)
+    prof = _lib.mlps_profiler_read(reset=True)
+    flush = torch.zeros(64 * 1024 * 1024, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    clk = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    _lib.mlps_kernel_launches(reset=True)
+    clk.start()
+    for i in range(a.steps):
+        _flush_l2(flush)
+        ev[i][0].record()
+        step(a.warmup + 1 + i)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    launches = _lib.mlps_kernel_launches()
+    if ws > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    last = float(tr.loss_out[0])
+    if tr.status() != 0:
+        raise RuntimeError("device status after the timed steps")
+    total_ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev), ws, dev)
+    value = job_rays_per_s(V * H * W, ws, a.steps, total_ms)
+    stage_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1] > 0}
+    dom = max(stage_ms, key=stage_ms.get)
+    n_hits = tr.r.hit_count()
+    peaks, _ = _peaks()
+    clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+    flop_per_sample = 2 * sum(i * o for i, o in wl.layer_dims())
+    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": peak, "traffic": None,
+            "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_mhz:.0f} MHz",
+            "achieved": None, "frac": None}
+    if dom in ("mlp_fwd", "mlp_bwd"):
+        ach = n_hits * flop_per_sample * (1 if dom == "mlp_fwd" else 2) / (stage_ms[dom] / 1e3) / 1e12
+        roof.update(achieved=ach, frac=ach / peak)
+    roof["stage_ms_per_launch"] = {k: round(v, 4) for k, v in stage_ms.items()}
+    line = {
+        "metric": "training rays/s (pixels rendered per second), 4 views per step",
+        "value": value, "unit": "rays/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded scene; targets rendered from a perturbed copy)",
+        "config": {"workload": f"train: {W}x{H} x {V} views per step, K={wl.K}, MLP {wl.input_dim}-32x32-4, "
+                               f"contact-point input, 4 x {C} feature slots, a quarter of the 8x8 tiles "
+                               "in the L1 + SSIM (lambda 0.2) + feature L1 loss, Adam",
+                   "loss_first_step": first, "loss_after_timed_steps": last, "hits_per_step": n_hits,
+                   "l2": "flushed between timed steps (256 MiB write); per-step working set > L2",
+                   "parallelism": f"one scene per rank, {ws} rank(s), no data-path collective"},
+        "clocks": clocks, "gpu_launches": int(launches), "roofline": roof,
+    }
+    if ws > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "batch":
         run_batch(a)
+    elif a.workload == "train":
+        run_train(a)
     else:
         run_ours(a)
 

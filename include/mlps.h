@@ -330,6 +330,56 @@ void mlps_profiler_enable(int32_t on);
 int32_t mlps_profiler_read(const char** names, float* ms, int32_t* counts, int32_t max,
                            int32_t reset);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Training objective and optimizer (Sec. 3.5, App. A.4)                                      */
+
+/* A training step's images: rgb and its target [V, H, W, 3], optional feature rows
+ * [V, H, W, feat_dim] and their targets. Only the selected `tile` x `tile` screen tiles enter
+ * the loss (the paper's tile mini-batching): tile_mask [V, ceil(H/tile), ceil(W/tile)] bytes on
+ * the device, nonzero = selected, NULL = every pixel. */
+typedef struct {
+  int32_t n_views, height, width;
+  int32_t tile;                 /* edge of the mask tiles, >= 1 */
+  const uint8_t* tile_mask;     /* device, or NULL */
+  float lambda_ssim;            /* lambda of the photometric loss (Eq. 7), in [0, 1] */
+  int32_t feat_dim;             /* feature channels (0: no feature loss) */
+} mlps_loss_desc;
+
+/* Workspace bytes of mlps_loss (9 floats per pixel and the loss sums); 0 for an invalid desc. */
+size_t mlps_loss_workspace_size(const mlps_loss_desc* desc);
+
+/* The loss of Eq. 7 (plus Eq. 8 when feat_dim > 0) over the N selected pixels:
+ *   L = (1 - lambda) L1 + lambda (1 - SSIM) + L_f,
+ *   L1 = sum_p sum_c |C - C*| / (3 N), SSIM = mean of the per-pixel, per-channel SSIM map (11 x 11
+ *   Gaussian window, sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2), L_f = sum |F - F*| / (F N),
+ * and its gradient: OVERWRITES d_rgb [V, H, W, 3] (and d_feat when feat_dim > 0; may be NULL
+ * otherwise), and loss_out (device, 5 floats) = {L, L1, SSIM, N, L_f}. `workspace` is
+ * 256-byte aligned device memory of mlps_loss_workspace_size bytes. */
+mlps_status mlps_loss(const mlps_loss_desc* desc, const float* rgb, const float* rgb_target,
+                      const float* feat, const float* feat_target, float* d_rgb, float* d_feat,
+                      float* loss_out, void* workspace, size_t workspace_bytes, void* stream);
+
+/* One parameter group of an Adam step; all pointers are device memory of n floats. kind 0:
+ * plain; kind 1: log-parameter (param holds log x, grad is dL/dx, aux holds x: the step uses
+ * dL/dlog x = dL/dx * x and rewrites aux = exp(param)). m and v start at zero. */
+typedef struct {
+  float* param;
+  const float* grad;
+  float* m;
+  float* v;
+  float* aux;
+  int64_t n;
+  float lr;
+  int32_t kind;
+} mlps_adam_group;
+
+#define MLPS_MAX_ADAM_GROUPS 8
+
+/* One Adam step (Kingma and Ba) over n_groups <= MLPS_MAX_ADAM_GROUPS groups (HOST array),
+ * step = 1, 2, ... (bias corrections 1 - beta^step). One kernel launch. */
+mlps_status mlps_adam_step(const mlps_adam_group* groups, int32_t n_groups, float beta1, float beta2,
+                           float eps, int32_t step, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -114,7 +114,8 @@ def loss(rgb, rgb_target, lam: float, tile: int = 8, tile_mask=None, feat=None, 
         lf = (m[..., None] * (f - ft).abs()).sum() / (Fd * n)
         L = L + lf
     L.backward()
-    parts = {"l1": float(l1), "ssim": float(ss), "l_feat": float(lf), "n": n}
+    L = L.detach()
+    parts = {"l1": float(l1.detach()), "ssim": float(ss.detach()), "l_feat": float(lf.detach()), "n": n}
     return float(L), parts, x.grad.numpy(), (None if f is None else f.grad.numpy())
 
 

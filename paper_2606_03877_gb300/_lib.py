@@ -59,6 +59,21 @@ class MlpsScene(ctypes.Structure):
                 ("quats", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
 
 
+class MlpsLossDesc(ctypes.Structure):
+    _fields_ = [("n_views", ctypes.c_int32), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("tile_mask", ctypes.c_void_p), ("lambda_ssim", ctypes.c_float),
+                ("feat_dim", ctypes.c_int32)]
+
+
+class MlpsAdamGroup(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("aux", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("lr", ctypes.c_float), ("kind", ctypes.c_int32)]
+
+
+MLPS_MAX_ADAM_GROUPS = 8
+
+
 class MlpsError(RuntimeError):
     def __init__(self, fn: str, status: int):
         self.status = status
@@ -111,6 +126,11 @@ _SIGS = [
                                           ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mlps_export_tiles", ctypes.c_int32, [_P(MlpsConfig), ctypes.c_int32, _P(MlpsCamera),
                                            ctypes.c_int32, _vp, _vp, _vp, _vp]),
+    ("mlps_loss_workspace_size", ctypes.c_size_t, [_P(MlpsLossDesc)]),
+    ("mlps_loss", ctypes.c_int32, [_P(MlpsLossDesc), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                   _vp]),
+    ("mlps_adam_step", ctypes.c_int32, [_P(MlpsAdamGroup), ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, ctypes.c_int32, _vp]),
     ("mlps_kernel_launches", ctypes.c_int64, [ctypes.c_int32]),
     ("mlps_profiler_enable", None, [ctypes.c_int32]),
     ("mlps_profiler_read", ctypes.c_int32, [_P(ctypes.c_char_p), _P(ctypes.c_float),
@@ -333,3 +353,32 @@ def mlps_profiler_read(reset: bool = False) -> dict:
     cnt = (ctypes.c_int32 * n)()
     k = load().mlps_profiler_read(names, ms, cnt, n, 1 if reset else 0)
     return {names[i].decode(): (float(ms[i]), int(cnt[i])) for i in range(min(k, n))}
+
+
+def loss_desc(n_views: int, height: int, width: int, tile: int = 8, tile_mask=None, lambda_ssim: float = 0.2,
+              feat_dim: int = 0) -> MlpsLossDesc:
+    return MlpsLossDesc(int(n_views), int(height), int(width), int(tile), _ptr(tile_mask), float(lambda_ssim),
+                        int(feat_dim))
+
+
+def mlps_loss_workspace_size(desc: MlpsLossDesc) -> int:
+    return int(load().mlps_loss_workspace_size(ctypes.byref(desc)))
+
+
+def mlps_loss(desc: MlpsLossDesc, rgb, rgb_target, feat, feat_target, d_rgb, d_feat, loss_out, workspace,
+              workspace_bytes: int, stream: int = 0):
+    _check("mlps_loss", load().mlps_loss(ctypes.byref(desc), _ptr(rgb), _ptr(rgb_target), _ptr(feat),
+                                         _ptr(feat_target), _ptr(d_rgb), _ptr(d_feat), _ptr(loss_out),
+                                         _ptr(workspace), int(workspace_bytes), stream))
+
+
+def adam_group(param, grad, m, v, lr: float, aux=None, kind: int = 0) -> MlpsAdamGroup:
+    return MlpsAdamGroup(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), _ptr(aux), int(param.numel()), float(lr),
+                         int(kind))
+
+
+def mlps_adam_step(groups: Sequence[MlpsAdamGroup], beta1: float, beta2: float, eps: float, step: int,
+                   stream: int = 0):
+    arr = (MlpsAdamGroup * len(groups))(*groups)
+    _check("mlps_adam_step", load().mlps_adam_step(arr, len(groups), float(beta1), float(beta2), float(eps),
+                                                   int(step), stream))

@@ -25,7 +25,7 @@ struct ProfRec {
 };
 const char* kStageNames[] = {"setup", "tile_lists", "intersect", "prim_scan", "scatter",
                              "mlp_fwd", "composite_fwd", "composite_bwd", "mlp_bwd", "pose_bwd",
-                             "pack", "slots_fwd", "slots_bwd"};
+                             "pack", "slots_fwd", "slots_bwd", "loss", "adam"};
 constexpr int kNumStages = sizeof(kStageNames) / sizeof(kStageNames[0]);
 std::mutex g_prof_mu;
 bool g_prof_on = false;
@@ -68,7 +68,7 @@ std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 enum { ST_SETUP, ST_TILES, ST_INTERSECT, ST_SCAN, ST_SCATTER, ST_MLP_FWD, ST_COMP_FWD,
-       ST_COMP_BWD, ST_MLP_BWD, ST_POSE_BWD, ST_PACK, ST_SLOTS_FWD, ST_SLOTS_BWD };
+       ST_COMP_BWD, ST_MLP_BWD, ST_POSE_BWD, ST_PACK, ST_SLOTS_FWD, ST_SLOTS_BWD, ST_LOSS, ST_ADAM };
 
 // ------------------------------------------------------------------------------------------
 // Model and packing layouts
@@ -848,6 +848,59 @@ int32_t mlps_profiler_read(const char** names, float* ms, int32_t* counts, int32
     for (int i = 0; i < kNumStages; ++i) { g_prof_ms[i] = 0.f; g_prof_cnt[i] = 0; }
   }
   return kNumStages;
+}
+
+
+// ------------------------------------------------------------------------------------------
+// Training objective and optimizer (Sec. 3.5, App. A.4)
+
+static bool loss_desc_ok(const mlps_loss_desc* d) {
+  return d && d->n_views >= 1 && d->height >= 1 && d->width >= 1 && d->height <= 16384 &&
+         d->width <= 16384 && d->tile >= 1 && d->feat_dim >= 0 && std::isfinite(d->lambda_ssim) &&
+         d->lambda_ssim >= 0.f && d->lambda_ssim <= 1.f;
+}
+
+size_t mlps_loss_workspace_size(const mlps_loss_desc* d) {
+  if (!loss_desc_ok(d)) return 0;
+  const size_t pix = (size_t)d->n_views * d->height * d->width;
+  return 256 + ((9 * pix * sizeof(float) + 255) & ~size_t(255));
+}
+
+mlps_status mlps_loss(const mlps_loss_desc* d, const float* rgb, const float* rgb_target, const float* feat,
+                      const float* feat_target, float* d_rgb, float* d_feat, float* loss_out, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+  if (!loss_desc_ok(d) || !rgb || !rgb_target || !d_rgb || !loss_out || !workspace)
+    return MLPS_ERR_INVALID_ARGUMENT;
+  if (d->feat_dim > 0 && (!feat || !feat_target)) return MLPS_ERR_INVALID_ARGUMENT;
+  if (!aligned256(workspace)) return MLPS_ERR_INVALID_ARGUMENT;
+  if (workspace_bytes < mlps_loss_workspace_size(d)) return MLPS_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  StageTimer tm(ST_LOSS, st);
+  launch_loss(d->n_views, d->height, d->width, rgb, rgb_target, d->tile_mask, d->tile, d->lambda_ssim,
+              d->feat_dim, feat, feat_target, d_rgb, d_feat, reinterpret_cast<float*>(ws + 256),
+              reinterpret_cast<double*>(ws), loss_out, st);
+  count_launch(3 + (d->feat_dim > 0 ? 1 : 0));
+  return cuda_status(cudaGetLastError());
+}
+
+mlps_status mlps_adam_step(const mlps_adam_group* groups, int32_t n_groups, float beta1, float beta2, float eps,
+                           int32_t step, void* stream) {
+  if (!groups || n_groups < 1 || n_groups > MLPS_MAX_ADAM_GROUPS || step < 1) return MLPS_ERR_INVALID_ARGUMENT;
+  if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f))
+    return MLPS_ERR_INVALID_ARGUMENT;
+  AdamGroupDev g[MLPS_MAX_ADAM_GROUPS];
+  for (int k = 0; k < n_groups; ++k) {
+    const mlps_adam_group& a = groups[k];
+    if (a.n < 0 || (a.n > 0 && (!a.param || !a.grad || !a.m || !a.v)) || (a.kind != 0 && a.kind != 1) ||
+        (a.kind == 1 && a.n > 0 && !a.aux) || !std::isfinite(a.lr))
+      return MLPS_ERR_INVALID_ARGUMENT;
+    g[k] = {a.param, a.grad, a.m, a.v, a.aux, (long long)a.n, a.lr, a.kind};
+  }
+  StageTimer tm(ST_ADAM, static_cast<cudaStream_t>(stream));
+  launch_adam(g, n_groups, beta1, beta2, eps, step, num_sms(), static_cast<cudaStream_t>(stream));
+  count_launch(1);
+  return cuda_status(cudaGetLastError());
 }
 
 }  // extern "C"

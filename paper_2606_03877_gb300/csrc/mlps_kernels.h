@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "mlps_common.cuh"
 
 namespace mlps {
@@ -77,6 +79,25 @@ void launch_slots_bwd_ray(const Work& w, const Model& m, const Packed& pk, const
                           const float* d_feat, int row_stride, cudaStream_t st);
 void launch_slots_bwd_prim(const Work& w, const Model& m, const Packed& pk, const unsigned char* weights,
                            const float* d_feat, int row_stride, float* d_weights, int n_sm, cudaStream_t st);
+
+// k_train.cu (training objective and optimizer, Sec. 3.5)
+constexpr int kMaxAdamGroups = 8;
+struct AdamGroupDev {
+  float* param;
+  const float* grad;
+  float* m;
+  float* v;
+  float* aux;      // kind 1: x = exp(param), read for the chain rule and rewritten
+  long long n;
+  float lr;
+  int kind;        // 0: plain, 1: log-parameter
+};
+// abc: 9 floats per pixel workspace; sums: 4 doubles
+void launch_loss(int V, int H, int W, const float* rgb, const float* rgb_t, const uint8_t* tile_mask,
+                 int tile, float lam, int C, const float* feat, const float* feat_t, float* d_rgb,
+                 float* d_feat, float* abc, double* sums, float* loss_out, cudaStream_t st);
+void launch_adam(const AdamGroupDev* groups, int n, float beta1, float beta2, float eps, int step,
+                 int n_sm, cudaStream_t st);
 
 // k_mlp_simt.cu (FP32 path)
 size_t mlp_simt_smem(const MlpArgs& a, bool backward);

@@ -155,6 +155,8 @@ CONFIGS: Dict[str, SceneConfig] = {
     # the paper's model with its semantic feature slots: four 512-d embeddings per primitive,
     # 1080p x 2 views (a 512-channel FP32 feature map is 2 KB per pixel)
     "slots": SceneConfig("slots", 1920, 1080, 256, 2, 6, 6, 32, 2, 0, 1, "fp32", 1, 512),
+    # training: the same model, four views per step at the Replica resolution (1200 x 680)
+    "train": SceneConfig("train", 1200, 680, 256, 4, 6, 6, 32, 2, 0, 1, "fp32", 1, 512),
 }
 
 # Batched workload: 32 scenes, K ~ U{16..512}, resolution uniform over these four.
