@@ -170,13 +170,33 @@ MLPS_DEV void dgrad_layer(const float* __restrict__ D, int dout, const float* __
 }
 
 // First-layer input gradient, local-position part only: G[f][r] for f < nx.
+// G[f][r] = sum_o Wc[o][x0 + f] D[o][r] for the nx encoded position (or residual) features:
+// each lane owns two rows, each warp every 8th feature, up to 8 features per pass in registers.
 MLPS_DEV void dgrad_input(const float* __restrict__ D, int dout, const float* __restrict__ Wc,
                           int din, int x0, int nx, float* __restrict__ G) {
-  for (int i = threadIdx.x; i < kRB * nx; i += blockDim.x) {
-    const int r = i % kRB, f = i / kRB;
-    float acc = 0.f;
-    for (int o = 0; o < dout; ++o) acc = fmaf(D[o * kRS + r], Wc[o * din + x0 + f], acc);
-    G[f * kRS + r] = acc;
+  constexpr int kCols = 8;
+  const int cg = threadIdx.x >> 5, lane = threadIdx.x & 31, r0 = lane * 2;
+  const int ng = blockDim.x >> 5;
+  for (int f0 = cg; f0 < nx; f0 += ng * kCols) {
+    float acc[2][kCols];
+#pragma unroll
+    for (int j = 0; j < kCols; ++j) acc[0][j] = acc[1][j] = 0.f;
+    for (int o = 0; o < dout; ++o) {
+      const float2 dv = *reinterpret_cast<const float2*>(&D[o * kRS + r0]);
+      const float* wrow = Wc + o * din + x0;
+#pragma unroll
+      for (int j = 0; j < kCols; ++j) {
+        const int f = f0 + j * ng;
+        const float wv = f < nx ? wrow[f] : 0.f;
+        acc[0][j] = fmaf(dv.x, wv, acc[0][j]);
+        acc[1][j] = fmaf(dv.y, wv, acc[1][j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kCols; ++j) {
+      const int f = f0 + j * ng;
+      if (f < nx) *reinterpret_cast<float2*>(&G[f * kRS + r0]) = make_float2(acc[0][j], acc[1][j]);
+    }
   }
 }
 

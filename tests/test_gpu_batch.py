@@ -211,3 +211,26 @@ def test_batch_edge_cases_empty_items_and_tiny_images():
     out0 = br0.forward(d0["centers"], d0["scales"], d0["quats"], br0.pack(d0["weights"]))
     torch.cuda.synchronize()
     assert br0.status() == 0 and float(out0["rgb"].abs().max()) == 0.0
+
+
+def test_batch_with_contact_slots_and_tile_order():
+    """The batched call with the paper's contact-point model, feature slots and the tile-centre
+    order: every item against the oracle (colour, T and the slot map)."""
+    base = synth.CONFIGS["contact"].replace(slot_dim=16, tile_sort=8)
+    sizes = [(48, 40, 10), (40, 32, 14), (56, 24, 6)]
+    cfgs = [base.replace(width=w, height=h, K=k, n_views=1) for w, h, k in sizes]
+    cat, items, scenes = synth.make_batch(cfgs, 90)
+    cat = dict(cat, scales=(cat["scales"] * 2.0).astype(np.float32))
+    scenes = [dict(sc, scales=(sc["scales"] * 2.0).astype(np.float32)) for sc in scenes]
+    K = cat["centers"].shape[0]
+    br = BatchRenderer(base, items, K, precision="fp32")
+    d = to_dev(cat)
+    out = br.forward(d["centers"], d["scales"], d["quats"], br.pack(d["weights"]))
+    torch.cuda.synchronize()
+    assert br.status() == 0
+    for i, (c, sc, it) in enumerate(zip(cfgs, scenes, items)):
+        rgb_o, T_o, F_o = oracle.render(c, sc, [it[2]])
+        assert np.abs(br.split(out["rgb"])[i].cpu().numpy().reshape(-1, 3) - rgb_o).max() < 1e-4, i
+        assert np.abs(br.split(out["trans"])[i].cpu().numpy().reshape(-1) - T_o).max() < 1e-4, i
+        f = br.split(out["feat"])[i].cpu().numpy().reshape(-1, 16)
+        assert np.abs(f - F_o).max() < 1e-4, i
