@@ -226,7 +226,18 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
             st_shared_v4(A + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
         } else if (F8) {
           RowWriter8 rw{A, row, 0, 0.f, kInMul};
-          if (valid) {
+          if (valid && m.contact) {
+            const IntervalRec& I = T[iv];
+            float del[3];
+            contact_delta(w.geo[prim], I, del);
+            if (m.dirL > 0)
+              for (int u = 0; u < 3; ++u) put_gamma8(rw, I.d[u], m.dirL);
+            if (m.xyzL == 0) {
+              for (int u = 0; u < 3; ++u) rw.put(del[u]);
+            } else {
+              for (int u = 0; u < 3; ++u) put_gamma8(rw, del[u], m.xyzL);
+            }
+          } else if (valid) {
             const IntervalRec& I = T[iv];
             const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
             float xl[3];
@@ -258,7 +269,19 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
             st_shared_v4(A + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
         } else {
           RowWriter rw{A, row, 0, 0.f};
-          if (valid) {
+          if (valid && m.contact) {
+            // contact-point input gamma([d; delta]) (Eq. 4), one sample per hit
+            const IntervalRec& I = T[iv];
+            float del[3];
+            contact_delta(w.geo[prim], I, del);
+            if (m.dirL > 0)
+              for (int u = 0; u < 3; ++u) put_gamma(rw, I.d[u], m.dirL);
+            if (m.xyzL == 0) {
+              for (int u = 0; u < 3; ++u) rw.put(del[u]);
+            } else {
+              for (int u = 0; u < 3; ++u) put_gamma(rw, del[u], m.xyzL);
+            }
+          } else if (valid) {
             const IntervalRec& I = T[iv];
             const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
             float xl[3];
@@ -619,9 +642,21 @@ int tc_fwd_groups(int width, int F, int groups, bool e4m3) {
   return groups == def ? groups : 0;
 }
 
-size_t tc_smem_bytes(const TcPlan& P, int F, int groups, int S) {
+// The groups a plan runs with: an explicit choice as given; the default reduced (at width 64
+// without features, where 2..6 are allowed) until the shared memory fits, e.g. for wide encoded
+// inputs (two K atoms) with one sample per interval (128 interval records per chunk).
+int tc_fwd_groups_for(const TcPlan& P, int F, int groups, int S) {
   const int width = P.npad[0];  // hidden width = N of layer 0
-  const int neg = tc_fwd_groups(width, F, groups, P.w8_bytes > 0);
+  const bool e4m3 = P.w8_bytes > 0;
+  int g = tc_fwd_groups(width, F, groups, e4m3);
+  const int ipc = S <= 128 ? 128 / S : 1;
+  if (groups == 0 && width == 64 && F == 0)
+    while (g > 2 && tc::tc_smem(P, g, e4m3, ipc).total + 1024 > 227 * 1024) --g;
+  return g;
+}
+
+size_t tc_smem_bytes(const TcPlan& P, int F, int groups, int S) {
+  const int neg = tc_fwd_groups_for(P, F, groups, S);
   return tc::tc_smem(P, neg > 0 ? neg : 5, P.w8_bytes > 0, S <= 128 ? 128 / S : 1).total + 1024;
 }
 
@@ -657,13 +692,13 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const int neg = tc_fwd_groups(a.m.width, a.m.F, a.groups, P.w8_bytes > 0);
+  const int neg = tc_fwd_groups_for(P, a.m.F, a.groups, a.m.S);
   if (neg == 0) return cudaErrorNotSupported;
   const size_t smem = tc_smem_bytes(P, a.m.F, a.groups, a.m.S);
   if (smem > 227 * 1024) return cudaErrorNotSupported;
   const int xl = a.m.xyzL, dl = a.m.dirL;
-  const bool fast64 = xl == 6 && dl == 4 && P.kpad[0] == 64;
-  const bool raw = xl == 0 && dl == 0 && P.kpad[0] == 64;
+  const bool fast64 = xl == 6 && dl == 4 && P.kpad[0] == 64 && !a.m.contact;
+  const bool raw = xl == 0 && dl == 0 && P.kpad[0] == 64 && !a.m.contact;
   decltype(&tc::k_mlp_fwd_tc<64, 6, 4, 0, 4, false>) kern;
   const bool feat = a.m.F > 0;
 #define MLPS_BY_GROUPS(W, XL, DL, F8) \

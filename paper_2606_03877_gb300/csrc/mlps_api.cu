@@ -107,6 +107,21 @@ mlps_status check_cfg(const mlps_config* c) {
   return MLPS_OK;
 }
 
+// The tensor-core kernels are built for hidden widths 64 and 128. A 32-wide model (the paper's
+// 72-32-32-4) runs on them with its hidden layers zero-padded to 64 units: the extra units have
+// zero weights and bias, so their ReLU output is 0 and they change no result. The packer reads
+// the canonical (32-wide) weights and writes the padded tiles; the kernels see the padded shape.
+Model tc_model(const Model& m) {
+  if (m.width != 32) return m;
+  Model t = m;
+  t.width = 64;
+  for (int l = 0; l < m.nl; ++l) {
+    t.din[l] = l == 0 ? m.nin : 64;
+    t.dout[l] = l == m.nl - 1 ? m.nout : 64;
+  }
+  return t;
+}
+
 Model make_model(const mlps_config* c) {
   Model m;
   std::memset(&m, 0, sizeof(m));
@@ -144,7 +159,7 @@ Packed make_packed(const mlps_config* c, const Model& m) {
   if (c->precision == MLPS_BF16 || c->precision == MLPS_FP8_E4M3) {
     TcPlan P;
     long long stride = 0;
-    if (tc_plan(m, &P, &stride, c->precision == MLPS_FP8_E4M3)) {
+    if (tc_plan(tc_model(m), &P, &stride, c->precision == MLPS_FP8_E4M3)) {
       pk.stride = stride;
       pk.slot_byte = P.slot_byte;
     }
@@ -431,9 +446,10 @@ mlps_status forward_impl(const mlps_config* cfg, const mlps_scene* scene, const 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Work w = make_work(cfg, L, K, n_views, saved, scratch);
   Model m = make_model(cfg);
+  const bool tc_fwd = cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3;
   MlpArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.m = m;
+  a.m = tc_fwd ? tc_model(m) : m;
   a.pk = make_packed(cfg, m);
   a.weights = static_cast<const unsigned char*>(scene->weights);
   a.rows = 128;
@@ -472,7 +488,7 @@ mlps_status forward_impl(const mlps_config* cfg, const mlps_scene* scene, const 
     if (cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3) {
       TcPlan P;
       long long stride;
-      tc_plan(m, &P, &stride, cfg->precision == MLPS_FP8_E4M3);
+      tc_plan(a.m, &P, &stride, cfg->precision == MLPS_FP8_E4M3);
       e = launch_mlp_fwd_tc(w, a, P, n_sm, st);
     } else {
       e = launch_mlp_fwd_simt(w, a, n_sm, st);
@@ -526,6 +542,8 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
   // FP8 precision: the backward recomputes the MLP in BF16 from the BF16 tiles of the same blob
   const bool tc = cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3;
   if (tc) {
+    // the tensor-core backward takes the midpoint-sample input of 64-wide models only
+    if (cfg->contact || m.width == 32) return MLPS_ERR_UNSUPPORTED;
     if (!tc_plan(m, &P, &tc_stride, cfg->precision == MLPS_FP8_E4M3) || !tc_bwd_supported(m, P))
       return MLPS_ERR_UNSUPPORTED;
   } else if (cfg->precision != MLPS_FP32 || !simt_bwd_supported(a)) {
@@ -636,10 +654,9 @@ mlps_status mlps_check_config(const mlps_config* cfg) {
   mlps_status s = check_cfg(cfg);
   if (s != MLPS_OK) return s;
   if (cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3) {
-    if (cfg->contact) return MLPS_ERR_UNSUPPORTED;  // the tensor-core encoders take x' only
     TcPlan P;
     long long stride;
-    const Model m = make_model(cfg);
+    const Model m = tc_model(make_model(cfg));
     if (!tc_plan(m, &P, &stride, cfg->precision == MLPS_FP8_E4M3)) return MLPS_ERR_UNSUPPORTED;
     if (tc_fwd_groups(m.width, m.F, cfg->mlp_groups, cfg->precision == MLPS_FP8_E4M3) == 0)
       return MLPS_ERR_UNSUPPORTED;
@@ -663,8 +680,8 @@ mlps_status mlps_pack_weights(const mlps_config* cfg, int32_t K, const float* we
   if (cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3) {
     TcPlan P;
     long long stride;
-    tc_plan(m, &P, &stride, cfg->precision == MLPS_FP8_E4M3);
-    launch_pack_bf16(m, P, stride, K, weights_fp32, packed, st);
+    tc_plan(tc_model(m), &P, &stride, cfg->precision == MLPS_FP8_E4M3);
+    launch_pack_bf16(m, P, stride, K, weights_fp32, packed, st);  // canonical shape in, padded tiles out
   } else {
     launch_pack_fp32(m, pk, K, weights_fp32, packed, st);
   }

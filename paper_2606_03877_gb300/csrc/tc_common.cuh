@@ -49,6 +49,16 @@ MLPS_DEV void seg_scan(float (&v)[NV], int nv, int row, int S, float* scratch, i
 MLPS_DEV float sigmoid_fast(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 MLPS_DEV float softplus_fast(float z) { return fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z))); }
 
+// Contact-point residual delta = mu - p* = -R S p + min(t_mid, 0) d (Eq. 3) of an interval,
+// from its closest point p in the primitive's normalised frame.
+MLPS_DEV void contact_delta(const PrimGeo& G, const IntervalRec& I, float del[3]) {
+  const float tn = fminf(I.tmid, 0.f);
+  for (int q = 0; q < 3; ++q) {
+    const float y = G.R[q * 3] * G.s[0] * I.p[0] + G.R[q * 3 + 1] * G.s[1] * I.p[1] + G.R[q * 3 + 2] * G.s[2] * I.p[2];
+    del[q] = fmaf(tn, I.d[q], -y);
+  }
+}
+
 struct RowWriter {  // writes one sample row of a K-major swizzled BF16 A tile, two values at a time
   uint32_t base;
   int row, col;

@@ -131,16 +131,16 @@ def test_batch_item_validation(lib):
 
 
 def test_contact_mode_validation(lib):
-    """Contact-point mode (Sec. 3.2) takes one sample per hit and runs on the FP32 path."""
+    """Contact-point mode (Sec. 3.2) takes one sample per hit; its forward runs in every
+    precision, its backward on the FP32 path."""
     c = synth.CONFIGS["contact"]
     assert _lib.mlps_check_config(make_config(c)) == _lib.MLPS_OK
     assert _lib.mlps_check_config(make_config(c.replace(samples=2))) == _lib.MLPS_ERR_INVALID_ARGUMENT
     cfg = make_config(c)
     cfg.contact = 2
     assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_INVALID_ARGUMENT
-    for prec in ("bf16", "fp8"):
-        assert _lib.mlps_check_config(make_config(c.replace(hidden_width=64), prec)) == \
-            _lib.MLPS_ERR_UNSUPPORTED
+    for prec in ("bf16", "fp8"):  # forward on the tensor cores (32-wide hidden layers padded to 64)
+        assert _lib.mlps_check_config(make_config(c, prec)) == _lib.MLPS_OK
     assert _lib.mlps_param_count(make_config(c)) == 72 * 32 + 32 + 32 * 32 + 32 + 32 * 4 + 4
 
 

@@ -163,3 +163,62 @@ def test_contact_differs_from_midpoint_sampling():
     _, o0, _, _ = gpu_render(cfg.replace(contact=0), scene, cams, "fp32")
     assert float(np.abs(o1["rgb"] - o0["rgb"]).max()) > 1e-3
     assert np.array_equal(o1["trans"] < 1, o0["trans"] < 1)  # same hits
+
+
+@pytest.mark.parametrize("precision,bar", [("bf16", 45.0), ("fp8", 38.0)])
+def test_contact_tensor_core_forward(precision, bar):
+    """The paper's 32-wide model on the tensor cores: hidden layers zero-padded to the 64-wide
+    tiles, contact-point rows built in the tensor-core kernel. PSNR against the FP64 oracle."""
+    from helpers import psnr
+    cfg = CONTACT.replace(width=96, height=72, K=24, n_views=2)
+    scene = scaled_scene(cfg, 1, 2.0)
+    cams = synth.make_cameras(cfg, first_view_seed=1)
+    r, out, _, _ = gpu_render(cfg, scene, cams, precision)
+    assert r.status() == 0
+    rgb_o, T_o, _ = oracle.render(cfg, scene, cams)
+    p = psnr(out["rgb"].reshape(-1, 3), rgb_o)
+    print(f"contact {precision} forward PSNR {p:.1f} dB")
+    assert p >= bar
+
+
+def test_contact_tensor_core_full_size_sampled():
+    from helpers import psnr
+    cfg = CONTACT
+    scene = synth.make_scene(cfg, 0)
+    cams = synth.make_cameras(cfg)
+    r, out, _, _ = gpu_render(cfg, scene, cams, "bf16")
+    assert r.status() == 0
+    pix = synth.sample_pixels(cfg, 3000, seed=19)
+    rgb_o, _, _ = oracle.render(cfg, scene, cams, pix=pix)
+    idx = pixel_index(cfg.width, cfg.height, pix)
+    p = psnr(out["rgb"].reshape(-1, 3)[idx], rgb_o)
+    print(f"contact bf16 1080p x 8 sampled PSNR {p:.1f} dB")
+    assert p >= 45.0
+
+
+def test_width32_midpoint_model_on_tensor_cores():
+    """A 32-wide model without the contact input (3 -> 32 -> 32 -> 4, S = 16) through the padded
+    tensor-core forward; its tensor-core backward is not built and says so."""
+    from helpers import psnr
+    from paper_2606_03877_gb300 import _lib
+    cfg = synth.CONFIGS["pr1"]
+    scene = scaled_scene(cfg, 0, 2.0)
+    cams = synth.make_cameras(cfg)
+    r, out, d, packed = gpu_render(cfg, scene, cams, "bf16")
+    rgb_o, _, _ = oracle.render(cfg, scene, cams)
+    assert psnr(out["rgb"].reshape(-1, 3), rgb_o) >= 45.0
+    with pytest.raises(_lib.MlpsError) as e:
+        r.backward(torch.zeros(1, cfg.height, cfg.width, 3, device="cuda"))
+    assert e.value.status == _lib.MLPS_ERR_UNSUPPORTED
+
+
+def test_contact_bf16_with_slots():
+    cfg = CONTACT.replace(width=64, height=48, K=12, n_views=1, slot_dim=64)
+    scene = scaled_scene(cfg, 2, 2.0)
+    cams = synth.make_cameras(cfg, first_view_seed=2)
+    r, out, _, _ = gpu_render(cfg, scene, cams, "bf16")
+    assert r.status() == 0
+    _, _, F_o = oracle.render(cfg, scene, cams)
+    e = rel_l2(out["feat"].reshape(-1, 64), F_o)
+    print("contact bf16 slot map rel-L2", e)
+    assert e < 1e-2
