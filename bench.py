@@ -260,10 +260,12 @@ def run_ours(a):
     order = ["bf16", "fp32"] if a.precision == "auto" else [a.precision]
     r = None
     precision = None
-    for p in order:
+    for i, p in enumerate(order):
         try:
             r = make(p)
             out, bwd_ok = try_pass(r, a.pass_ == "fwdbwd")
+            if a.pass_ == "fwdbwd" and not bwd_ok and i + 1 < len(order):
+                continue  # auto: this precision has no backward for the model; take the next one
             precision = p
             break
         except _lib.MlpsError as e:

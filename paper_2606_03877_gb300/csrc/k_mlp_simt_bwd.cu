@@ -45,6 +45,7 @@ struct BwdPlan {
   int din_pad[kMaxLayers], dout_pad[kMaxLayers];
   int act_floats;
   int gbuf;                      // one gradient buffer [maxpad][kRS]
+  int zbuf;                      // the forward output [round4(nout)][kRS]
   int nxyz;                      // encoded local-position (contact mode: residual) features
   int x0;                        // their first input row (after the direction in contact mode)
   int tiles;                     // total 4x4 tiles over all layers
@@ -77,6 +78,7 @@ BwdPlan make_plan(const MlpArgs& a) {
   P.wc_floats = off;
   P.act_floats = act;
   P.gbuf = maxpad * kRS;
+  P.zbuf = round4(m.nout) * kRS;
   P.nxyz = m.xyzL > 0 ? 6 * m.xyzL : 3;
   P.x0 = m.contact && m.dirL > 0 ? 6 * m.dirL : 0;
   P.tiles = tiles;
@@ -85,7 +87,7 @@ BwdPlan make_plan(const MlpArgs& a) {
 
 size_t bwd_smem(const MlpArgs& a, const BwdPlan& P) {
   const Model& m = a.m;
-  size_t f = (size_t)P.wt_floats + P.wc_floats + P.act_floats + 3 * (size_t)P.gbuf;
+  size_t f = (size_t)P.wt_floats + P.wc_floats + P.act_floats + 2 * (size_t)P.gbuf + P.zbuf;
   f += 16;  // geometry accumulators
   const int ipcb = kRB / m.S;
   size_t bytes = f * sizeof(float) + (size_t)ipcb * (sizeof(IntervalInfo) + sizeof(float4)) +
@@ -318,8 +320,10 @@ MLPS_DEV void chain_pose(const PrimGeo& G, const IntervalInfo& I, const ChainAcc
 
 }  // namespace
 
-template <int TN>
-__global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a, BwdPlan P) {
+// MT: weight-gradient tiles per thread (1, 2 or 4). Models with at most 2 x 256 tiles are
+// compiled for two resident blocks per SM, so that one block's barriers overlap the other's work.
+template <int TN, int MT>
+__global__ void __launch_bounds__(kThreads, MT <= 2 ? 2 : 1) k_mlp_bwd_simt(Work w, MlpArgs a, BwdPlan P) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const Model& m = a.m;
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
   float* sG0 = sAct + P.act_floats;
   float* sG1 = sG0 + P.gbuf;
   float* sZ = sG1 + P.gbuf;
-  float* sGeo = sZ + P.gbuf;  // [0..8] dM, [9..11] dmu
+  float* sGeo = sZ + P.zbuf;  // [0..8] dM, [9..11] dmu
   float4* sGrad = reinterpret_cast<float4*>(sGeo + 16);
   IntervalInfo* sI = reinterpret_cast<IntervalInfo*>(sGrad + ipcb);
   float* sGF = reinterpret_cast<float*>(sI + ipcb);
@@ -342,11 +346,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
   if (cb >= ce) return;
 
   // this thread's weight-gradient tiles
-  int t_layer[kMaxTiles], t_o0[kMaxTiles], t_it[kMaxTiles];
-  float acc[kMaxTiles][16];
+  int t_layer[MT], t_o0[MT], t_it[MT];
+  float acc[MT][16];
   float bacc[kMaxBias];
   int nt = 0;
-  for (int t = threadIdx.x; t < P.tiles && nt < kMaxTiles; t += kThreads, ++nt) {
+  for (int t = threadIdx.x; t < P.tiles && nt < MT; t += kThreads, ++nt) {
     int l = 0;
     while (t >= P.tile_base[l + 1]) ++l;
     const int loc = t - P.tile_base[l];
@@ -356,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
   }
   auto zero_acc = [&]() {
 #pragma unroll
-    for (int j = 0; j < kMaxTiles; ++j)
+    for (int j = 0; j < MT; ++j)
 #pragma unroll
       for (int e = 0; e < 16; ++e) acc[j][e] = 0.f;
 #pragma unroll
@@ -373,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
   auto flush = [&](int p) {
     float* dW = a.d_weights + (size_t)p * m.Prow;
 #pragma unroll
-    for (int j = 0; j < kMaxTiles; ++j) {
+    for (int j = 0; j < MT; ++j) {
       if (j >= nt) break;
       const int l = t_layer[j], din = m.din[l], dout = m.dout[l], ni = P.ni[l];
 #pragma unroll
@@ -569,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(Work w, MlpArgs a,
       for (int l = nl - 1; l >= 0; --l) {
         const float* Al = sAct + P.act_off[l];
 #pragma unroll
-        for (int j = 0; j < kMaxTiles; ++j) {
+        for (int j = 0; j < MT; ++j) {
           if (j >= nt || t_layer[j] != l) continue;
           const int o0 = t_o0[j], it = t_it[j], ni = P.ni[l];
           for (int r = 0; r < kRB; r += 4) {
@@ -663,24 +667,37 @@ bool simt_bwd_supported(const MlpArgs& a) {
   return bwd_smem(a, P) <= 227 * 1024;
 }
 
+template <int TN, int MT>
+static cudaError_t launch_bwd_mt(const Work& w, const MlpArgs& a, const BwdPlan& P, size_t smem, int n_sm,
+                                 cudaStream_t st) {
+  auto kern = k_mlp_bwd_simt<TN, MT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  kern<<<n_sm * per_sm, kThreads, smem, st>>>(w, a, P);
+  return cudaGetLastError();
+}
+
+template <int TN>
+static cudaError_t launch_bwd_width(const Work& w, const MlpArgs& a, const BwdPlan& P, size_t smem, int n_sm,
+                                    cudaStream_t st) {
+  if (P.tiles <= kThreads) return launch_bwd_mt<TN, 1>(w, a, P, smem, n_sm, st);
+  if (P.tiles <= 2 * kThreads) return launch_bwd_mt<TN, 2>(w, a, P, smem, n_sm, st);
+  return launch_bwd_mt<TN, kMaxTiles>(w, a, P, smem, n_sm, st);
+}
+
 cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st) {
   const Model& m = a.m;
   if (!simt_bwd_supported(a)) return cudaErrorNotSupported;
   BwdPlan P = make_plan(a);
   const size_t smem = bwd_smem(a, P);
   switch (m.width) {
-#define MLPS_CASE(WID)                                                                      \
-  case WID: {                                                                               \
-    auto kern = k_mlp_bwd_simt<WID / 8>;                                                    \
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                         (int)smem);                                        \
-    if (e != cudaSuccess) return e;                                                         \
-    kern<<<n_sm, kThreads, smem, st>>>(w, a, P);                                            \
-    return cudaGetLastError();                                                              \
-  }
-    MLPS_CASE(32)
-    MLPS_CASE(64)
-#undef MLPS_CASE
+    case 32:
+      return launch_bwd_width<4>(w, a, P, smem, n_sm, st);
+    case 64:
+      return launch_bwd_width<8>(w, a, P, smem, n_sm, st);
     default:
       return cudaErrorNotSupported;
   }
