@@ -153,3 +153,30 @@ def test_slots_gradient_of_embeddings_only_from_the_slot_map():
     assert rel_l2(res[0]["d_weights"][:, :P], res[1]["d_weights"]) < 1e-6
     for k in ("d_centers", "d_scales", "d_quats"):
         assert rel_l2(res[0][k], res[1][k]) < 1e-6, k
+
+
+def test_slots_equal_embeddings_under_early_termination():
+    """With early termination active (T_eps = 0.3) the slot map uses the same hits and weights
+    as the colour composite: four equal slots give F = (1 - T) e with the GPU's own T."""
+    cfg = BASE.replace(width=40, height=32, K=6, n_views=1, slot_dim=8)
+    scene = synth.make_scene(cfg, 9)
+    scene["scales"] = (scene["scales"] * 4.0).astype(np.float32)
+    e = np.linspace(-1, 1, 8).astype(np.float32)
+    scene["weights"] = scene["weights"].copy()
+    scene["weights"][:, cfg.n_mlp_params:] = np.tile(e, 4)[None, :]
+    r, out, _, _ = gpu_render(cfg, scene, synth.make_cameras(cfg, first_view_seed=9), "fp32", t_eps=0.3)
+    T = out["trans"].reshape(-1).astype(np.float64)
+    f = out["feat"].reshape(-1, 8).astype(np.float64)
+    assert T.min() < 0.3  # termination fired on some rays
+    assert np.abs(f - (1 - T)[:, None] * e[None, :]).max() < 2e-6
+
+
+def test_slots_with_no_primitives():
+    cfg = BASE.replace(width=24, height=16, K=0, n_views=1, slot_dim=16)
+    scene = {"centers": np.zeros((0, 3), np.float32), "scales": np.zeros((0, 3), np.float32),
+             "quats": np.zeros((0, 4), np.float32), "weights": np.zeros((0, cfg.n_params), np.float32)}
+    r, out, d, packed = gpu_render(cfg, scene, synth.make_cameras(cfg), "fp32")
+    assert r.status() == 0 and float(np.abs(out["feat"]).max()) == 0.0
+    g = r.backward(torch.ones(1, 16, 24, 3, device="cuda"), None, torch.ones(1, 16, 24, 16, device="cuda"))
+    torch.cuda.synchronize()
+    assert r.status("scratch") == 0

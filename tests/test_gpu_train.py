@@ -140,3 +140,21 @@ def test_training_reduces_the_loss():
     torch.cuda.synchronize()
     print("loss before / after 41 steps:", losses)
     assert tr.status() == 0 and losses[1] < 0.8 * losses[0]
+
+
+def test_bf16_training_of_the_midpoint_model_reduces_the_loss():
+    """The tensor-core path trains too: the 60-64x64x64-4 midpoint model (S = 16) in BF16."""
+    cfg = synth.CONFIGS["prec"].replace(width=64, height=48, K=12, n_views=2, samples=16)
+    scene = scaled_scene(cfg, 2, 2.0)
+    cams = synth.make_cameras(cfg, first_view_seed=2)
+    rgb_t, _, _ = oracle.render(cfg, synth.perturb_scene(scene, cfg, 4), cams)
+    tgt = torch.from_numpy(rgb_t.reshape(2, 48, 64, 3).astype(np.float32)).cuda()
+    tr = Trainer(cfg, scene, precision="bf16")
+    full = np.ones((2, 6, 8), np.uint8)
+    first = float(tr.step(cams, tgt, tile_mask=full)[0])
+    for _ in range(40):
+        tr.step(cams, tgt)
+    last = float(tr.step(cams, tgt, tile_mask=full)[0])
+    torch.cuda.synchronize()
+    print("bf16 loss before / after 41 steps:", first, last)
+    assert tr.status() == 0 and last < 0.8 * first
