@@ -20,7 +20,10 @@
 //     where g_tm, g_h are the gradients on t_mid and h collected from t_k = t0 + (k + 1/2) Delta
 //     and Delta = (t1 - t0) / S. This form has no cancellation between the ~3-unit camera
 //     distances; it is the same derivative as the one written with o' and d'.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <cstring>
 
 #include "mlps_common.cuh"
 #include "mlps_kernels.h"
@@ -320,6 +323,159 @@ MLPS_DEV void chain_pose(const PrimGeo& G, const IntervalInfo& I, const ChainAcc
 
 }  // namespace
 
+// Reverse of the interval composite (the file header's step 2) for the sub-chunk's nint
+// intervals: dL/dZ of every sample row into sG0 (rows beyond the intervals zeroed), and
+// dL/dDelta of each interval into sGrad[i].w. Thread per interval for S = 1 (tau = 1 and no
+// later samples inside the interval), else warp per interval.
+MLPS_DEV void reverse_composite(const Model& m, int S, int F, int nint, const IntervalInfo* sI, float4* sGrad,
+                                const float* sGF, const float* sZ, float* sG0, int dout_pad_last) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (S == 1 && threadIdx.x < nint) {
+    const int i = threadIdx.x;
+    const float dt = sI[i].dt;
+    const float4 g = sGrad[i];
+    const float* gF = sGF + i * F;
+    const float zs = sZ[3 * kRS + i];
+    const float sig = softplusf_acc(zs);
+    const float ak = sig * dt;
+    const float ea = expf(-ak);
+    const float wk = -expm1f(-ak);
+    float cq[3];
+    for (int q = 0; q < 3; ++q) cq[q] = sigmoidf_acc(sZ[q * kRS + i]);
+    float ga = g.w;
+    ga += g.x * (ea * cq[0]) + g.y * (ea * cq[1]) + g.z * (ea * cq[2]);
+    for (int f = 0; f < F; ++f) {
+      ga += gF[f] * (ea * sZ[(4 + f) * kRS + i]);
+      sG0[(4 + f) * kRS + i] = wk * gF[f];
+    }
+    const float gcs[3] = {g.x, g.y, g.z};
+    for (int q = 0; q < 3; ++q) sG0[q * kRS + i] = wk * gcs[q] * cq[q] * (1.f - cq[q]);
+    sG0[3 * kRS + i] = ga * dt * sigmoidf_acc(zs);
+    sGrad[i].w = ga * sig;  // from here on: dL/dDelta of the interval
+  }
+  for (int i = warp; i < nint && S > 1; i += kThreads / 32) {
+    const IntervalInfo& I = sI[i];
+    const float4 g = sGrad[i];
+    const float* gF = sGF + i * F;
+    const int PL = (S + 31) / 32;
+    const int k0 = min(S, lane * PL), k1 = min(S, k0 + PL);
+    const int rb = i * S;
+    float aloc = 0.f;
+    for (int k = k0; k < k1; ++k) aloc += softplusf_acc(sZ[3 * kRS + rb + k]) * I.dt;
+    const float A0 = warp_excl_scan(aloc, lane);
+    // lane totals of w c and w f for the suffix sums
+    float wc[3] = {0.f, 0.f, 0.f};
+    float A = A0;
+    for (int k = k0; k < k1; ++k) {
+      const float ak = softplusf_acc(sZ[3 * kRS + rb + k]) * I.dt;
+      const float wk = expf(-A) * -expm1f(-ak);
+      for (int q = 0; q < 3; ++q) wc[q] = fmaf(wk, sigmoidf_acc(sZ[q * kRS + rb + k]), wc[q]);
+      A += ak;
+    }
+    float R[3];
+    for (int q = 0; q < 3; ++q) R[q] = warp_excl_suffix(wc[q], lane);
+    // feature suffix sums (one scan per feature)
+    float RFl[kMaxFeat];
+    for (int f = 0; f < F; ++f) {
+      float v = 0.f;
+      float A2 = A0;
+      for (int k = k0; k < k1; ++k) {
+        const float ak = softplusf_acc(sZ[3 * kRS + rb + k]) * I.dt;
+        v = fmaf(expf(-A2) * -expm1f(-ak), sZ[(4 + f) * kRS + rb + k], v);
+        A2 += ak;
+      }
+      RFl[f] = warp_excl_suffix(v, lane);
+    }
+    // backward over the lane's samples
+    float dDelta = 0.f;
+    float Aend = A;  // exclusive prefix after the lane's last sample
+    for (int k = k1 - 1; k >= k0; --k) {
+      const float zs = sZ[3 * kRS + rb + k];
+      const float sig = softplusf_acc(zs);
+      const float ak = sig * I.dt;
+      const float Aex = Aend - ak;
+      const float tau = expf(-Aex);
+      const float ea = expf(-ak);
+      const float wk = tau * -expm1f(-ak);
+      float cq[3];
+      for (int q = 0; q < 3; ++q) cq[q] = sigmoidf_acc(sZ[q * kRS + rb + k]);
+      float ga = g.w;
+      ga += g.x * (tau * ea * cq[0] - R[0]) + g.y * (tau * ea * cq[1] - R[1]) +
+            g.z * (tau * ea * cq[2] - R[2]);
+      for (int f = 0; f < F; ++f) {
+        const float fk = sZ[(4 + f) * kRS + rb + k];
+        ga += gF[f] * (tau * ea * fk - RFl[f]);
+        RFl[f] = fmaf(wk, fk, RFl[f]);
+        sG0[(4 + f) * kRS + rb + k] = wk * gF[f];
+      }
+      const float gcs[3] = {g.x, g.y, g.z};
+      for (int q = 0; q < 3; ++q) {
+        sG0[q * kRS + rb + k] = wk * gcs[q] * cq[q] * (1.f - cq[q]);
+        R[q] = fmaf(wk, cq[q], R[q]);
+      }
+      sG0[3 * kRS + rb + k] = ga * I.dt * sigmoidf_acc(zs);
+      dDelta = fmaf(ga, sig, dDelta);
+      Aend = Aex;
+    }
+    dDelta = warp_sum(dDelta);
+    if (lane == 0) sGrad[i].w = dDelta;  // from here on: dL/dDelta of the interval
+  }
+  // rows beyond the valid intervals carry zero gradient
+  for (int i = threadIdx.x; i < m.nout * kRB; i += kThreads) {
+    const int r = i % kRB, o = i / kRB;
+    if (r >= nint * S) sG0[o * kRS + r] = 0.f;
+  }
+  for (int i = threadIdx.x; i < (dout_pad_last - m.nout) * kRB; i += kThreads) {
+    const int r = i % kRB, o = m.nout + i / kRB;
+    sG0[o * kRS + r] = 0.f;
+  }
+}
+
+// Encoding derivative and pose chain (the file header's step 4) of the sub-chunk's intervals from
+// D = dL/d(encoded position or residual) rows [0, nxyz): thread per interval for S = 1 (warp
+// sums of the 12 contributions), else warp per interval with a lane per sample; the 12 pose
+// contributions are added into sGeo.
+MLPS_DEV void pose_step(const Model& m, int S, int nint, const IntervalInfo* sI, const float4* sGrad,
+                        const float* D, const PrimGeo& G, float* sGeo) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (S == 1) {
+    if (warp * 32 < nint) {
+      const int i = threadIdx.x;
+      float out[12];
+      for (int e = 0; e < 12; ++e) out[e] = 0.f;
+      if (i < nint) {
+        const IntervalInfo& I = sI[i];
+        ChainAcc c;
+        chain_zero(c);
+        if (m.contact) chain_contact(m, G, I, D, i, c);
+        else chain_sample(m, G, I, D, i, 0, 1, c);
+        chain_pose(G, I, c, sGrad[i].w, 1, out);
+      }
+      for (int e = 0; e < 12; ++e) {
+        const float v = warp_sum(out[e]);
+        if (lane == 0) atomicAdd(&sGeo[e], v);
+      }
+    }
+  } else {
+    for (int i = warp; i < nint; i += kThreads / 32) {
+      const IntervalInfo& I = sI[i];
+      const int rb = i * S;
+      ChainAcc c;
+      chain_zero(c);
+      for (int k = lane; k < S; k += 32) chain_sample(m, G, I, D, rb + k, k, S, c);
+      for (int q = 0; q < 3; ++q) c.sg[q] = warp_sum(c.sg[q]);
+      for (int e = 0; e < 9; ++e) c.gy[e] = warp_sum(c.gy[e]);
+      c.gt0 = warp_sum(c.gt0);
+      c.gt1 = warp_sum(c.gt1);
+      if (lane == 0) {
+        float out[12];
+        chain_pose(G, I, c, sGrad[i].w, S, out);
+        for (int e = 0; e < 12; ++e) atomicAdd(&sGeo[e], out[e]);
+      }
+    }
+  }
+}
+
 // MT: weight-gradient tiles per thread (1, 2 or 4). Models with at most 2 x 256 tiles are
 // compiled for two resident blocks per SM, so that one block's barriers overlap the other's work.
 template <int TN, int MT>
@@ -464,108 +620,8 @@ __global__ void __launch_bounds__(kThreads, MT <= 2 ? 2 : 1) k_mlp_bwd_simt(Work
         else fwd_small(Xl, m.din[l], Wt, bb, m.dout[l], sZ);
         __syncthreads();
       }
-      // 3. reverse of the interval composite -> dZ in sG0: thread per interval for S = 1
-      //    (tau = 1 and no later samples inside the interval), else warp per interval
-      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      if (S == 1 && threadIdx.x < nint) {
-        const int i = threadIdx.x;
-        const float dt = sI[i].dt;
-        const float4 g = sGrad[i];
-        const float* gF = sGF + i * F;
-        const float zs = sZ[3 * kRS + i];
-        const float sig = softplusf_acc(zs);
-        const float ak = sig * dt;
-        const float ea = expf(-ak);
-        const float wk = -expm1f(-ak);
-        float cq[3];
-        for (int q = 0; q < 3; ++q) cq[q] = sigmoidf_acc(sZ[q * kRS + i]);
-        float ga = g.w;
-        ga += g.x * (ea * cq[0]) + g.y * (ea * cq[1]) + g.z * (ea * cq[2]);
-        for (int f = 0; f < F; ++f) {
-          ga += gF[f] * (ea * sZ[(4 + f) * kRS + i]);
-          sG0[(4 + f) * kRS + i] = wk * gF[f];
-        }
-        const float gcs[3] = {g.x, g.y, g.z};
-        for (int q = 0; q < 3; ++q) sG0[q * kRS + i] = wk * gcs[q] * cq[q] * (1.f - cq[q]);
-        sG0[3 * kRS + i] = ga * dt * sigmoidf_acc(zs);
-        sGrad[i].w = ga * sig;  // from here on: dL/dDelta of the interval
-      }
-      for (int i = warp; i < nint && S > 1; i += kThreads / 32) {
-        const IntervalInfo& I = sI[i];
-        const float4 g = sGrad[i];
-        const float* gF = sGF + i * F;
-        const int PL = (S + 31) / 32;
-        const int k0 = min(S, lane * PL), k1 = min(S, k0 + PL);
-        const int rb = i * S;
-        float aloc = 0.f;
-        for (int k = k0; k < k1; ++k) aloc += softplusf_acc(sZ[3 * kRS + rb + k]) * I.dt;
-        const float A0 = warp_excl_scan(aloc, lane);
-        // lane totals of w c and w f for the suffix sums
-        float wc[3] = {0.f, 0.f, 0.f};
-        float A = A0;
-        for (int k = k0; k < k1; ++k) {
-          const float ak = softplusf_acc(sZ[3 * kRS + rb + k]) * I.dt;
-          const float wk = expf(-A) * -expm1f(-ak);
-          for (int q = 0; q < 3; ++q) wc[q] = fmaf(wk, sigmoidf_acc(sZ[q * kRS + rb + k]), wc[q]);
-          A += ak;
-        }
-        float R[3];
-        for (int q = 0; q < 3; ++q) R[q] = warp_excl_suffix(wc[q], lane);
-        // feature suffix sums (one scan per feature)
-        float RFl[kMaxFeat];
-        for (int f = 0; f < F; ++f) {
-          float v = 0.f;
-          float A2 = A0;
-          for (int k = k0; k < k1; ++k) {
-            const float ak = softplusf_acc(sZ[3 * kRS + rb + k]) * I.dt;
-            v = fmaf(expf(-A2) * -expm1f(-ak), sZ[(4 + f) * kRS + rb + k], v);
-            A2 += ak;
-          }
-          RFl[f] = warp_excl_suffix(v, lane);
-        }
-        // backward over the lane's samples
-        float dDelta = 0.f;
-        float Aend = A;  // exclusive prefix after the lane's last sample
-        for (int k = k1 - 1; k >= k0; --k) {
-          const float zs = sZ[3 * kRS + rb + k];
-          const float sig = softplusf_acc(zs);
-          const float ak = sig * I.dt;
-          const float Aex = Aend - ak;
-          const float tau = expf(-Aex);
-          const float ea = expf(-ak);
-          const float wk = tau * -expm1f(-ak);
-          float cq[3];
-          for (int q = 0; q < 3; ++q) cq[q] = sigmoidf_acc(sZ[q * kRS + rb + k]);
-          float ga = g.w;
-          ga += g.x * (tau * ea * cq[0] - R[0]) + g.y * (tau * ea * cq[1] - R[1]) +
-                g.z * (tau * ea * cq[2] - R[2]);
-          for (int f = 0; f < F; ++f) {
-            const float fk = sZ[(4 + f) * kRS + rb + k];
-            ga += gF[f] * (tau * ea * fk - RFl[f]);
-            RFl[f] = fmaf(wk, fk, RFl[f]);
-            sG0[(4 + f) * kRS + rb + k] = wk * gF[f];
-          }
-          const float gcs[3] = {g.x, g.y, g.z};
-          for (int q = 0; q < 3; ++q) {
-            sG0[q * kRS + rb + k] = wk * gcs[q] * cq[q] * (1.f - cq[q]);
-            R[q] = fmaf(wk, cq[q], R[q]);
-          }
-          sG0[3 * kRS + rb + k] = ga * I.dt * sigmoidf_acc(zs);
-          dDelta = fmaf(ga, sig, dDelta);
-          Aend = Aex;
-        }
-        dDelta = warp_sum(dDelta);
-        if (lane == 0) sGrad[i].w = dDelta;  // from here on: dL/dDelta of the interval
-      }
-      // rows beyond the valid intervals carry zero gradient
-      for (int i = threadIdx.x; i < m.nout * kRB; i += kThreads) {
-        const int r = i % kRB, o = i / kRB;
-        if (r >= nint * S) sG0[o * kRS + r] = 0.f;
-      }
-      for (int i = threadIdx.x; i < (P.dout_pad[nl - 1] - m.nout) * kRB; i += kThreads) {
-        const int r = i % kRB, o = m.nout + i / kRB;
-        sG0[o * kRS + r] = 0.f;
-      }
+      // 3. reverse of the interval composite -> dZ in sG0
+      reverse_composite(m, S, F, nint, sI, sGrad, sGF, sZ, sG0, P.dout_pad[nl - 1]);
       __syncthreads();
       // 4. layers, last to first: wgrad (+ bias) then dgrad
       float* D = sG0;
@@ -614,47 +670,328 @@ __global__ void __launch_bounds__(kThreads, MT <= 2 ? 2 : 1) k_mlp_bwd_simt(Work
         float* t = D; D = Gn; Gn = t;
       }
       // D now holds dL/d(encoded local position), or dL/d(encoded delta), rows [0, nxyz)
-      // 5. encoding derivative and pose chain: thread per interval for S = 1 (warp sums of
-      //    the 12 contributions), else warp per interval with a lane per sample
-      if (S == 1) {
-        if (warp * 32 < nint) {
-          const int i = threadIdx.x;
-          float out[12];
-          for (int e = 0; e < 12; ++e) out[e] = 0.f;
-          if (i < nint) {
-            const IntervalInfo& I = sI[i];
-            ChainAcc c;
-            chain_zero(c);
-            if (m.contact) chain_contact(m, G, I, D, i, c);
-            else chain_sample(m, G, I, D, i, 0, 1, c);
-            chain_pose(G, I, c, sGrad[i].w, 1, out);
-          }
-          for (int e = 0; e < 12; ++e) {
-            const float v = warp_sum(out[e]);
-            if (lane == 0) atomicAdd(&sGeo[e], v);
-          }
-        }
-      } else {
-        for (int i = warp; i < nint; i += kThreads / 32) {
-          const IntervalInfo& I = sI[i];
-          const int rb = i * S;
-          ChainAcc c;
-          chain_zero(c);
-          for (int k = lane; k < S; k += 32) chain_sample(m, G, I, D, rb + k, k, S, c);
-          for (int q = 0; q < 3; ++q) c.sg[q] = warp_sum(c.sg[q]);
-          for (int e = 0; e < 9; ++e) c.gy[e] = warp_sum(c.gy[e]);
-          c.gt0 = warp_sum(c.gt0);
-          c.gt1 = warp_sum(c.gt1);
-          if (lane == 0) {
-            float out[12];
-            chain_pose(G, I, c, sGrad[i].w, S, out);
-            for (int e = 0; e < 12; ++e) atomicAdd(&sGeo[e], out[e]);
-          }
-        }
-      }
+      // 5. encoding derivative and pose chain
+      pose_step(m, S, nint, sI, sGrad, D, G, sGeo);
     }
   }
   if (loaded >= 0) flush(loaded);
+}
+
+// ------------------------------------------------------------------------------------------
+// Wide models (hidden width 128, e.g. 4 x 128 with a feature head). Neither the weight
+// gradients (~60 k values per primitive) nor both weight copies fit on chip, so:
+//  * each layer's weights are streamed through shared memory, 64 output (forward) or input
+//    (dgrad) columns at a time, from the FP32 blob or, for the tensor-core precisions, from the
+//    BF16 tiles of their blob (the backward then recomputes with the BF16-rounded weights the
+//    forward used);
+//  * dgrad writes delta_{l-1} over H_l in place (each element's ReLU mask is read by the thread
+//    that overwrites it), and the encoded input is rebuilt for layer 0's wgrad, so every layer
+//    input has one buffer;
+//  * the 4 x 4 weight-gradient tiles are accumulated over a sub-chunk in registers and added
+//    into a block-private FP32 copy of dW in global memory (L2-resident), flushed with atomics
+//    when the block moves to another primitive. Bias gradients stay in registers as above.
+
+struct WidePlan {
+  int nl, nin, nout, nx, x0;
+  int act_floats;                  // (nl - 1) layer inputs of 128 rows
+  int gbuf_rows;                   // encoded input / dL/dZ / dL/dx buffer
+  int zrows;                       // forward output rows
+  int stage_floats;
+  int tile_base[kMaxLayers + 1], ni[kMaxLayers];
+  int bias_base[kMaxLayers + 1];
+  // weight sources
+  int bf16;                        // 1: BF16 tiles of a tensor-core blob
+  int gw_row[kMaxLayers], npad[kMaxLayers], bias_off[kMaxLayers], gbias_byte;
+};
+
+MLPS_HD int wide_rows(int n) { return round4(n); }
+
+WidePlan make_wide_plan(const MlpArgs& a, const TcPlan* tp) {
+  const Model& m = a.m;
+  WidePlan P;
+  std::memset(&P, 0, sizeof(P));
+  P.nl = m.nl;
+  P.nin = m.nin;
+  P.nout = m.nout;
+  P.nx = m.xyzL > 0 ? 6 * m.xyzL : 3;
+  P.x0 = m.contact && m.dirL > 0 ? 6 * m.dirL : 0;
+  P.act_floats = (m.nl - 1) * m.width * kRS;
+  P.gbuf_rows = max(max(wide_rows(m.nin), wide_rows(m.nout)), wide_rows(P.nx));
+  P.zrows = wide_rows(m.nout);
+  int tiles = 0, bias = 0;
+  for (int l = 0; l < m.nl; ++l) {
+    P.tile_base[l] = tiles;
+    P.ni[l] = wide_rows(m.din[l]) / 4;
+    tiles += (wide_rows(m.dout[l]) / 4) * P.ni[l];
+    P.bias_base[l] = bias;
+    bias += m.dout[l];
+  }
+  P.tile_base[m.nl] = tiles;
+  P.bias_base[m.nl] = bias;
+  P.stage_floats = m.width * 64 + 64;  // the largest staged block: 128 inputs x 64 columns + bias
+  if (tp) {
+    P.bf16 = 1;
+    for (int l = 0; l < m.nl; ++l) {
+      P.gw_row[l] = tp->gw_row[l];
+      P.npad[l] = tp->npad[l];
+      P.bias_off[l] = tp->bias_off[l];
+    }
+    P.gbias_byte = tp->gbias_byte;
+  }
+  return P;
+}
+
+size_t wide_smem(const MlpArgs& a, const WidePlan& P) {
+  const int S = a.m.S;
+  const int ipcb = kRB / S;
+  size_t f = (size_t)P.stage_floats + P.act_floats + (size_t)(P.gbuf_rows + P.zrows) * kRS + 16;
+  return f * sizeof(float) + (size_t)ipcb * (sizeof(IntervalInfo) + sizeof(float4)) +
+         (size_t)ipcb * a.m.F * sizeof(float) + 64;
+}
+
+// Canonical W_l[o][k] and b_l[o] of the staged primitive's blob.
+struct WideWeights {
+  const unsigned char* blob;
+  const float* f32;
+  const Model* m;
+  const Packed* pk;
+  const WidePlan* P;
+  MLPS_DEV float w(int l, int o, int k) const {
+    if (P->bf16) {
+      const __nv_bfloat16* t = reinterpret_cast<const __nv_bfloat16*>(blob + (size_t)P->gw_row[l] * 128);
+      return __bfloat162float(t[((k >> 6) * P->npad[l] + o) * 64 + (k & 63)]);
+    }
+    return f32[pk->woff[l] + k * m->dout[l] + o];  // FP32 blob: W^T [din][dout]
+  }
+  MLPS_DEV float b(int l, int o) const {
+    if (P->bf16) return reinterpret_cast<const float*>(blob + P->gbias_byte)[P->bias_off[l] + o];
+    return f32[pk->boff[l] + o];
+  }
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpArgs a, WidePlan P) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const Model& m = a.m;
+  const int S = m.S, F = m.F, nl = m.nl;
+  const int ipcb = kRB / S;
+  float* sStage = smem;
+  float* sAct = sStage + P.stage_floats;     // input of layer l >= 1 at (l - 1) * 128 rows
+  float* sG = sAct + P.act_floats;           // X, then dL/dZ, then X, then dL/dx
+  float* sZ = sG + P.gbuf_rows * kRS;
+  float* sGeo = sZ + P.zrows * kRS;
+  float4* sGrad = reinterpret_cast<float4*>(sGeo + 16);
+  IntervalInfo* sI = reinterpret_cast<IntervalInfo*>(sGrad + ipcb);
+  float* sGF = reinterpret_cast<float*>(sI + ipcb);
+  auto act = [&](int l) { return sAct + (size_t)(l - 1) * m.width * kRS; };
+
+  const int total = w.saved_hdr[2];
+  const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
+  const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
+  if (cb >= ce) return;
+  float* dwb = w.dwb + (size_t)blockIdx.x * m.P;  // this block's dW copy (canonical layout)
+  float bacc[kMaxBias];
+  for (int j = 0; j < kMaxBias; ++j) bacc[j] = 0.f;
+  if (threadIdx.x < 16) sGeo[threadIdx.x] = 0.f;
+  const int wstride = (int)(a.pk.stride / 4);
+  int prim = find_prim(w, cb);
+  int loaded = -1;
+  WideWeights W{nullptr, nullptr, &m, &a.pk, &P};
+
+  auto flush = [&](int p) {
+    float* dW = a.d_weights + (size_t)p * m.Prow;
+    __syncthreads();
+    for (int i = threadIdx.x; i < m.P; i += kThreads) {
+      const float v = dwb[i];
+      if (v != 0.f) {
+        atomicAdd(&dW[i], v);
+        dwb[i] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxBias; ++j) {
+      const int bi = threadIdx.x + j * kThreads;
+      if (bi < P.bias_base[nl] && bacc[j] != 0.f) {
+        int l = 0;
+        while (bi >= P.bias_base[l + 1]) ++l;
+        atomicAdd(&dW[m.boff[l] + (bi - P.bias_base[l])], bacc[j]);
+      }
+      bacc[j] = 0.f;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+      const float v = sGeo[threadIdx.x];
+      if (v != 0.f) atomicAdd(&w.dgeo[12 * (size_t)p + threadIdx.x], v);
+      sGeo[threadIdx.x] = 0.f;
+    }
+  };
+  // wgrad of layer l (D: dL/dZ_l rows, H: input rows) over the sub-chunk into dwb, and biases
+  auto wgrad = [&](int l, const float* D, const float* H) {
+    const int ni = P.ni[l], din = m.din[l], dout = m.dout[l];
+    const int n_t = P.tile_base[l + 1] - P.tile_base[l];
+    for (int t = threadIdx.x; t < n_t; t += kThreads) {
+      const int o0 = (t / ni) * 4, it = t % ni;
+      float acc[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+      for (int r = 0; r < kRB; r += 4) {
+        float4 dv[4], av[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          dv[u] = *reinterpret_cast<const float4*>(&D[(o0 + u) * kRS + r]);
+          av[u] = *reinterpret_cast<const float4*>(&H[(it + ni * u) * kRS + r]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            float s_ = acc[u * 4 + v];
+            s_ = fmaf(dv[u].x, av[v].x, s_);
+            s_ = fmaf(dv[u].y, av[v].y, s_);
+            s_ = fmaf(dv[u].z, av[v].z, s_);
+            s_ = fmaf(dv[u].w, av[v].w, s_);
+            acc[u * 4 + v] = s_;
+          }
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int o = o0 + (e >> 2), i = it + ni * (e & 3);
+        if (o < dout && i < din && acc[e] != 0.f) dwb[m.woff[l] + o * din + i] += acc[e];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxBias; ++j) {
+      const int bi = threadIdx.x + j * kThreads - P.bias_base[l];
+      if (bi >= 0 && bi < dout) {
+        float s_ = 0.f;
+        for (int r = 0; r < kRB; ++r) s_ += D[bi * kRS + r];
+        bacc[j] += s_;
+      }
+    }
+  };
+  // the encoded input of the sub-chunk's rows into sG (rows nin..gbuf_rows zero)
+  auto encode = [&](int nint, const PrimGeo& G) {
+    if (threadIdx.x < kRB) {
+      const int row = threadIdx.x, i = row / S, k = row - i * S;
+      if (i < nint) {
+        const IntervalInfo& I = sI[i];
+        const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+        float xl[3];
+        if (m.contact) contact_residual(G, I.p, I.tmid, I.d, xl);
+        else for (int q = 0; q < 3; ++q) xl[q] = fmaf(tr, I.dp[q], I.p[q]);
+        encode_row(m, xl, I.d, sG, row, kRS);
+        for (int f = m.nin; f < P.gbuf_rows; ++f) sG[f * kRS + row] = 0.f;
+      } else {
+        for (int f = 0; f < P.gbuf_rows; ++f) sG[f * kRS + row] = 0.f;
+      }
+    }
+  };
+
+  for (int c = cb; c < ce; ++c) {
+    while (c >= w.chunk_start[prim + 1]) ++prim;
+    const int first = (c - w.chunk_start[prim]) * w.ipc;
+    const int nint_c = min(w.ipc, w.prim_count[prim] - first);
+    if (prim != loaded) {
+      if (loaded >= 0) flush(loaded);
+      loaded = prim;
+    }
+    W.blob = a.weights + (size_t)prim * a.pk.stride;
+    W.f32 = reinterpret_cast<const float*>(a.weights) + (size_t)prim * wstride;
+    const PrimGeo& G = w.geo[prim];
+    for (int sub = 0; sub * ipcb < nint_c; ++sub) {
+      const int i0 = sub * ipcb;
+      const int nint = min(ipcb, nint_c - i0);
+      __syncthreads();
+      if (threadIdx.x < nint) {
+        const int slot = w.prim_start[prim] + first + i0 + threadIdx.x;
+        load_interval(w, m, slot, sI[threadIdx.x]);
+        sGrad[threadIdx.x] = w.hit_grad[slot];
+        for (int f = 0; f < F; ++f) sGF[threadIdx.x * F + f] = w.hit_gfeat[(size_t)slot * F + f];
+      }
+      __syncthreads();
+      encode(nint, G);
+      // forward recompute, hidden layers in two 64-column halves, then the head
+      for (int l = 0; l < nl - 1; ++l) {
+        const float* X = l == 0 ? sG : act(l);
+        const int din = m.din[l];
+        for (int h = 0; h < 2; ++h) {
+          __syncthreads();
+          for (int i = threadIdx.x; i < din * 64; i += kThreads) {
+            const int k = i >> 6, cc = i & 63;
+            sStage[i] = W.w(l, 64 * h + cc, k);
+          }
+          if (threadIdx.x < 64) sStage[din * 64 + threadIdx.x] = W.b(l, 64 * h + threadIdx.x);
+          __syncthreads();
+          fwd_layer<8>(X, din, sStage, sStage + din * 64, act(l + 1) + (size_t)64 * h * kRS, true);
+        }
+      }
+      {
+        const int l = nl - 1, din = m.din[l], dout = m.dout[l];
+        __syncthreads();
+        for (int i = threadIdx.x; i < din * dout; i += kThreads) {
+          const int k = i / dout, o = i - k * dout;
+          sStage[i] = W.w(l, o, k);
+        }
+        if (threadIdx.x < dout) sStage[din * dout + threadIdx.x] = W.b(l, threadIdx.x);
+        __syncthreads();
+        fwd_small(act(l), din, sStage, sStage + din * dout, dout, sZ);
+        __syncthreads();
+      }
+      // reverse of the interval composite: dL/dZ into sG (the encoded input is rebuilt later)
+      reverse_composite(m, S, F, nint, sI, sGrad, sGF, sZ, sG, P.zrows);
+      __syncthreads();
+      // layers, last to first: wgrad, then dgrad over H_l in place (two 64-column halves)
+      for (int l = nl - 1; l >= 1; --l) {
+        const float* D = l == nl - 1 ? sG : act(l + 1);
+        float* H = act(l);
+        const int dout = m.dout[l];
+        wgrad(l, D, H);
+        for (int h = 0; h < 2; ++h) {
+          __syncthreads();
+          for (int i = threadIdx.x; i < dout * 64; i += kThreads) {
+            const int o = i >> 6, cc = i & 63;
+            sStage[i] = W.w(l, o, 64 * h + cc);
+          }
+          __syncthreads();
+          dgrad_layer<8>(D, dout, sStage, H + (size_t)64 * h * kRS, H + (size_t)64 * h * kRS);
+        }
+        __syncthreads();
+      }
+      // layer 0: rebuild X, wgrad, then dL/dx of the encoded position (or residual) features
+      encode(nint, G);
+      __syncthreads();
+      wgrad(0, act(1), sG);
+      __syncthreads();
+      for (int i = threadIdx.x; i < m.dout[0] * P.nx; i += kThreads) {
+        const int o = i / P.nx, f = i - o * P.nx;
+        sStage[i] = W.w(0, o, P.x0 + f);
+      }
+      __syncthreads();
+      dgrad_input(act(1), m.dout[0], sStage, P.nx, 0, P.nx, sG);
+      __syncthreads();
+      pose_step(m, S, nint, sI, sGrad, sG, G, sGeo);
+    }
+  }
+  if (loaded >= 0) flush(loaded);
+}
+
+bool simt_bwd_wide_supported(const MlpArgs& a) {
+  const Model& m = a.m;
+  if (m.width != 128 || m.S > kRB || m.nl < 2) return false;
+  if (m.nin > 64 || m.nout > 64 || m.F > kMaxFeat) return false;
+  WidePlan P = make_wide_plan(a, nullptr);
+  if (P.bias_base[m.nl] > kMaxBias * kThreads || P.nx > 64) return false;
+  return wide_smem(a, P) <= 227 * 1024;
+}
+
+cudaError_t launch_mlp_bwd_simt_wide(const Work& w, const MlpArgs& a, const TcPlan* tp, int n_sm, cudaStream_t st) {
+  if (!simt_bwd_wide_supported(a) || !w.dwb) return cudaErrorNotSupported;
+  const WidePlan P = make_wide_plan(a, tp);
+  const size_t smem = wide_smem(a, P);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_bwd_simt_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_mlp_bwd_simt_wide<<<n_sm, kThreads, smem, st>>>(w, a, P);
+  return cudaGetLastError();
 }
 
 bool simt_bwd_supported(const MlpArgs& a) {

@@ -204,7 +204,7 @@ struct Layout {
       ray_count, prim_count, prim_start, chunk_start, prim_list, rec, slot_of, views, geo, pview,
       saved_total;
   // scratch
-  size_t prim_cursor, tile_count, tile_list, hit_grad, hit_gfeat, dgeo, slot_ga, slot_gu, scratch_total;
+  size_t prim_cursor, tile_count, tile_list, hit_grad, hit_gfeat, dgeo, slot_ga, slot_gu, dwb, scratch_total;
   long long hit_cap;
   long long n_rays, n_pairs, n_tiles_all, n_cand;
   int max_view_tiles;
@@ -264,6 +264,13 @@ bool make_layout(const mlps_config* c, int K, const ViewSpec* vs, int V, Layout*
   L->dgeo = t.take<float>((size_t)K * 12 + 1);
   L->slot_ga = t.take<float>(c->slot_dim > 0 ? hc : 1);
   L->slot_gu = t.take<float4>(c->slot_dim > 0 ? hc : 1);
+  {  // the wide backward's block-private weight gradients: one FP32 copy per SM
+    int dev = 0, n_sm = 1;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1) n_sm = 1;
+    const Model mm = make_model(c);
+    L->dwb = t.take<float>(c->hidden_width == 128 ? (size_t)n_sm * mm.P : 1);
+  }
   L->scratch_total = t.off;
   return true;
 }
@@ -305,6 +312,7 @@ Work make_work(const mlps_config* c, const Layout& L, int K, int V, void* saved,
       w.slot_ga = reinterpret_cast<float*>(sc + L.slot_ga);
       w.slot_gu = reinterpret_cast<float4*>(sc + L.slot_gu);
     }
+    if (c->hidden_width == 128) w.dwb = reinterpret_cast<float*>(sc + L.dwb);
   }
   w.K = K;
   w.V = V;
@@ -541,7 +549,13 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
   long long tc_stride = 0;
   // FP8 precision: the backward recomputes the MLP in BF16 from the BF16 tiles of the same blob
   const bool tc = cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3;
-  if (tc) {
+  // width 128: the FP32 wide backward, reading the FP32 blob or the BF16 tiles of the
+  // tensor-core precisions (their forward weights), for every precision
+  const bool wide = m.width == 128;
+  if (wide) {
+    if (tc && !tc_plan(m, &P, &tc_stride, cfg->precision == MLPS_FP8_E4M3)) return MLPS_ERR_UNSUPPORTED;
+    if (!simt_bwd_wide_supported(a) || !w.dwb) return MLPS_ERR_UNSUPPORTED;
+  } else if (tc) {
     // the tensor-core backward takes the midpoint-sample input of 64-wide models only
     if (cfg->contact || m.width == 32) return MLPS_ERR_UNSUPPORTED;
     if (!tc_plan(m, &P, &tc_stride, cfg->precision == MLPS_FP8_E4M3) || !tc_bwd_supported(m, P))
@@ -556,6 +570,7 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
     if (K > 0) {
       cudaMemsetAsync(w.dgeo, 0, sizeof(float) * 12 * (size_t)K, st);
       cudaMemsetAsync(d_weights, 0, sizeof(float) * (size_t)m.Prow * K, st);
+      if (wide) cudaMemsetAsync(w.dwb, 0, sizeof(float) * (size_t)m.P * n_sm, st);
     }
   }
   const int FT = cfg->feat_dim + m.C;  // feature row: the MLP's outputs, then the slot channels
@@ -575,7 +590,8 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
   }
   if (K > 0) {
     StageTimer tm(ST_MLP_BWD, st);
-    cudaError_t e = tc ? launch_mlp_bwd_tc(w, a, P, n_sm, st) : launch_mlp_bwd_simt(w, a, n_sm, st);
+    cudaError_t e = wide ? launch_mlp_bwd_simt_wide(w, a, tc ? &P : nullptr, n_sm, st)
+                    : tc ? launch_mlp_bwd_tc(w, a, P, n_sm, st) : launch_mlp_bwd_simt(w, a, n_sm, st);
     if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return MLPS_ERR_CUDA;
     count_launch(1);

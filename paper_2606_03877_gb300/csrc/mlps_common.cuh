@@ -263,6 +263,7 @@ struct Work {
   float* dgeo;           // [K, 12] dL/dM (9) and dL/dmu (3)
   float* slot_ga;        // [cap] feature slots: dL/da_j of each interval (hit order)
   float4* slot_gu;       // [cap] feature slots: (dL/du, compositing weight w_j) (hit order)
+  float* dwb;            // [n_sm, P] width-128 backward: per-block weight-gradient copies
   // sizes
   int K, V;
   int H, W, ntx, nty, n_tiles;  // view 0's sizes (the single-scene inspection calls use them)

@@ -104,6 +104,10 @@ size_t mlp_simt_smem(const MlpArgs& a, bool backward);
 cudaError_t launch_mlp_fwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st);
 bool simt_bwd_supported(const MlpArgs& a);
 cudaError_t launch_mlp_bwd_simt(const Work& w, const MlpArgs& a, int n_sm, cudaStream_t st);
+// hidden width 128 (weights streamed, weight gradients in per-block global copies w.dwb);
+// tp = the tensor-core plan when the blob holds BF16 tiles, else nullptr (FP32 blob)
+bool simt_bwd_wide_supported(const MlpArgs& a);
+cudaError_t launch_mlp_bwd_simt_wide(const Work& w, const MlpArgs& a, const TcPlan* tp, int n_sm, cudaStream_t st);
 
 // k_mlp_tc.cu (BF16 tensor-core path)
 bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3 = false);

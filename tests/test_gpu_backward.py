@@ -150,3 +150,48 @@ def test_full_size_prec_sampled_gradients_bf16():
     assert errs["d_weights"] < 2e-2, errs
     for k in ("d_centers", "d_scales", "d_quats"):
         assert errs[k] < 6e-2, (k, errs)
+
+
+def _stress_small(seed=3):
+    cfg = synth.CONFIGS["stress"].replace(width=64, height=48, K=8, n_views=1)
+    scene = scaled_scene(cfg, seed, 2.0)
+    cams = synth.make_cameras(cfg, first_view_seed=seed)
+    return cfg, scene, cams
+
+
+def _l2_grads(cfg, scene, cams):
+    """dL/dC and dL/dF of L = 1/2 |C - C*|^2 + 1/2 |F - F*|^2 against the perturbed scene."""
+    cur, _, Fc = oracle.render(cfg, scene, cams)
+    tgt, _, Ft = oracle.render(cfg, synth.perturb_scene(scene, cfg, 1), cams)
+    V, H, W = len(cams), cfg.height, cfg.width
+    return ((cur - tgt).reshape(V, H, W, 3).astype(np.float32),
+            (Fc - Ft).reshape(V, H, W, cfg.feat_dim).astype(np.float32))
+
+
+def test_stress_shape_gradients_fp32():
+    """Hidden width 128 x 4 with a 16-d feature head, S = 48: the wide FP32 backward (weights
+    streamed through shared memory, weight gradients in per-block global copies)."""
+    cfg, scene, cams = _stress_small()
+    g_rgb, g_F = _l2_grads(cfg, scene, cams)
+    errs = _check(cfg, scene, cams, g_rgb, None, g_F)
+    print("stress-shape FP32 gradient rel-L2:", errs)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_stress_shape_gradients_tensor_core_precisions(precision):
+    """BF16 / E4M3 forward on the tensor cores, then the wide FP32 backward recomputing with the
+    BF16 weights of the same blob: gradients within the BF16 bar of 2e-2 relative L2."""
+    cfg, scene, cams = _stress_small(4)
+    g_rgb, g_F = _l2_grads(cfg, scene, cams)
+    r = Renderer(cfg, precision=precision)
+    d = to_dev(scene)
+    r.forward(d["centers"], d["scales"], d["quats"], r.pack(d["weights"]), cams)
+    got = r.backward(torch.from_numpy(g_rgb).cuda(), None, torch.from_numpy(g_F).cuda())
+    torch.cuda.synchronize()
+    assert r.status() == 0 and r.status("scratch") == 0
+    ref = oracle.render_backward(cfg, scene, cams, oracle.all_pixels(cams), g_rgb.reshape(-1, 3), None,
+                                 g_F.reshape(-1, cfg.feat_dim))
+    errs = {k: rel_l2(got[k].cpu().numpy(), ref[k]) for k, _ in GROUPS}
+    print(f"stress-shape {precision} gradient rel-L2:", errs)
+    for k, e in errs.items():
+        assert e < 2e-2, (k, errs)
