@@ -155,3 +155,40 @@ def test_mlp_groups_validation(lib):
     assert _lib.mlps_check_config(make_config(synth.CONFIGS["stress"], "bf16", mlp_groups=2)) == _lib.MLPS_OK
     # the FP32 path has no groups; the field is accepted and ignored
     assert _lib.mlps_check_config(make_config(base, "fp32", mlp_groups=3)) == _lib.MLPS_OK
+
+
+def test_training_entry_points_validate_on_the_host(lib):
+    """mlps_loss_workspace_size / mlps_loss / mlps_adam_step reject bad arguments before any
+    device work (no GPU needed)."""
+    ok = _lib.loss_desc(2, 45, 70, 8, None, 0.2, 0)
+    assert _lib.mlps_loss_workspace_size(ok) == 256 + ((9 * 2 * 45 * 70 * 4 + 255) // 256) * 256
+    for bad in (_lib.loss_desc(0, 45, 70), _lib.loss_desc(1, 45, 70, 0), _lib.loss_desc(1, 45, 70, 8, None, 1.5),
+                _lib.loss_desc(1, 45, 70, 8, None, 0.2, -1)):
+        assert _lib.mlps_loss_workspace_size(bad) == 0
+    with pytest.raises(_lib.MlpsError) as e:
+        _lib.mlps_loss(ok, None, None, None, None, None, None, None, None, 0)
+    assert e.value.status == _lib.MLPS_ERR_INVALID_ARGUMENT
+    with pytest.raises(_lib.MlpsError) as e:  # no groups
+        _lib.mlps_adam_step([], 0.9, 0.999, 1e-15, 1)
+    assert e.value.status == _lib.MLPS_ERR_INVALID_ARGUMENT
+    g = _lib.MlpsAdamGroup(None, None, None, None, None, 10, 1e-3, 0)  # n > 0 without pointers
+    with pytest.raises(_lib.MlpsError) as e:
+        _lib.mlps_adam_step([g], 0.9, 0.999, 1e-15, 1)
+    assert e.value.status == _lib.MLPS_ERR_INVALID_ARGUMENT
+    g0 = _lib.MlpsAdamGroup(None, None, None, None, None, 0, 1e-3, 0)
+    for args in ((1.0, 0.999, 1e-15, 1), (0.9, 0.999, 1e-15, 0)):  # beta1 = 1, step 0
+        with pytest.raises(_lib.MlpsError) as e:
+            _lib.mlps_adam_step([g0], *args)
+        assert e.value.status == _lib.MLPS_ERR_INVALID_ARGUMENT
+
+
+def test_slot_and_tile_order_config_validation(lib):
+    c = synth.CONFIGS["contact"]
+    assert _lib.mlps_check_config(make_config(c.replace(slot_dim=512))) == _lib.MLPS_OK
+    assert _lib.mlps_check_config(make_config(c.replace(slot_dim=6))) == _lib.MLPS_ERR_UNSUPPORTED
+    assert _lib.mlps_check_config(make_config(c.replace(slot_dim=4096))) == _lib.MLPS_ERR_INVALID_ARGUMENT
+    assert _lib.mlps_param_count(make_config(c.replace(slot_dim=512))) == c.n_mlp_params + 4 * 512
+    cfg = make_config(c.replace(tile_sort=8))
+    assert cfg.tile_sort == 1 and cfg.tile == 8 and _lib.mlps_check_config(cfg) == _lib.MLPS_OK
+    cfg.tile_sort = 2
+    assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_INVALID_ARGUMENT
