@@ -161,3 +161,22 @@ def test_full_size_prec_sampled_pixels():
     T = out["trans"].reshape(-1)[idx]
     assert np.abs(rgb - rgb_o).max() < TOL and np.abs(T - T_o).max() < TOL
     assert (T_o < 1).sum() > 100
+
+
+def test_non_finite_and_degenerate_primitives_are_skipped_and_reported():
+    """A NaN centre, a zero scale and a zero quaternion make their primitives invalid: the
+    device status reports MLPS_ERR_NONFINITE and the image is the render of the valid ones."""
+    cfg = synth.CONFIGS["prec"].replace(width=40, height=32, K=9, n_views=1)
+    scene = scaled_scene(cfg, 12, 2.5)
+    bad = {k: v.copy() for k, v in scene.items()}
+    bad["centers"][1, 0] = np.nan
+    bad["scales"][4, 2] = 0.0
+    bad["quats"][7] = 0.0
+    cams = synth.make_cameras(cfg, first_view_seed=12)
+    r, out, _, _ = gpu_render(cfg, bad, cams)
+    assert r.status() == 6  # MLPS_ERR_NONFINITE
+    keep = [i for i in range(cfg.K) if i not in (1, 4, 7)]
+    valid = {k: v[keep] for k, v in scene.items()}
+    rgb_o, T_o, _ = oracle.render(cfg.replace(K=len(keep)), valid, cams)
+    assert np.abs(out["rgb"].reshape(-1, 3) - rgb_o).max() < 1e-4
+    assert np.abs(out["trans"].reshape(-1) - T_o).max() < 1e-4
