@@ -1,6 +1,7 @@
 // mlps_api.cu -- the C ABI of include/mlps.h: validation, workspace carving and the stage
 // sequence of the forward and backward passes.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cmath>
@@ -45,17 +46,21 @@ cudaEvent_t prof_event() {
   return e;
 }
 
+// A stage: an NVTX range for external profilers (a no-op without one attached) and, when the
+// library's profiler is on, a pair of CUDA events on the stream.
 struct StageTimer {
   int stage;
   cudaStream_t st;
   cudaEvent_t a = nullptr;
   StageTimer(int s, cudaStream_t stream) : stage(s), st(stream) {
+    nvtxRangePushA(kStageNames[s]);
     if (!g_prof_on) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     a = prof_event();
     cudaEventRecord(a, st);
   }
   ~StageTimer() {
+    nvtxRangePop();
     if (!a) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     cudaEvent_t b = prof_event();
