@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--width", type=int, default=0, help="override (profiling captures only)")
     ap.add_argument("--height", type=int, default=0, help="override (profiling captures only)")
     ap.add_argument("--views", type=int, default=0, help="override (profiling captures only)")
+    ap.add_argument("--hit-capacity", type=float, default=0.0,
+                    help="hit records per ray (0: 16 for K >= 1024, else 8)")
     ap.add_argument("--tile-sort", type=int, default=0,
                     help="T > 0: hits ordered by the tile-centre ray of T x T tiles (8 or 16)")
     ap.add_argument("--mlp-groups", type=int, default=0,
@@ -207,6 +209,12 @@ def feat_grad_device(wl, dev):
     return table[idx].reshape(wl.n_views, wl.height, wl.width, FT)
 
 
+def hit_capacity(a, wl) -> float:
+    """Hit records reserved per ray: the 1024-primitive stress scene averages about eight
+    hits per ray at 1080p and more at low resolution, so it gets sixteen."""
+    return float(a.hit_capacity) if a.hit_capacity else (16.0 if wl.K >= 1024 else 8.0)
+
+
 def _flush_l2(buf):
     buf.add_(1.0)  # writes 256 MiB (> 129 MB L2) between timed steps
 
@@ -236,6 +244,7 @@ def run_ours(a):
 
     def make(precision):
         kw = {"mlp_groups": a.mlp_groups} if a.mlp_groups and precision != "fp32" else {}
+        kw["hit_capacity"] = hit_capacity(a, wl)
         r = Renderer(wl, precision=precision, device=str(dev), **kw)
         return r
 
@@ -439,7 +448,7 @@ def run_e2e(a, wl, scene, cams, precision, do_bwd, dev):
     g_host = torch.from_numpy(synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100, scale=0.01)).pin_memory()
     dd = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()}
     g_dev = torch.empty(g_host.shape, device=dev)
-    r = Renderer(wl, precision=precision, device=str(dev))
+    r = Renderer(wl, precision=precision, device=str(dev), hit_capacity=hit_capacity(a, wl))
     rgb_h = torch.empty(wl.n_views, wl.height, wl.width, 3).pin_memory()
     tr_h = torch.empty(wl.n_views, wl.height, wl.width).pin_memory()
     FT = wl.feat_dim + wl.slot_dim

@@ -769,6 +769,25 @@ struct WideWeights {
   }
 };
 
+// dst[i] = src(i) for i < n <= kWideStageMax: every thread issues all of its loads before its
+// first store, so one staging pass costs one memory round trip rather than one per element.
+constexpr int kWideStageMax = 128 * 64;
+template <class Src>
+MLPS_DEV void wide_stage(int n, Src src, float* __restrict__ dst) {
+  constexpr int kPer = kWideStageMax / kThreads;
+  float r[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = threadIdx.x + j * kThreads;
+    r[j] = i < n ? src(i) : 0.f;
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = threadIdx.x + j * kThreads;
+    if (i < n) dst[i] = r[j];
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpArgs a, WidePlan P) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -825,16 +844,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
       sGeo[threadIdx.x] = 0.f;
     }
   };
-  // wgrad of layer l (D: dL/dZ_l rows, H: input rows) over the sub-chunk into dwb, and biases
-  auto wgrad = [&](int l, const float* D, const float* H) {
+  // wgrad of layer l (D: dL/dZ_l rows, H: input rows) over the first `rows` rows of the
+  // sub-chunk into dwb, and biases. The tile's dwb entries are read before the FMA loop so that
+  // their latency hides under it.
+  auto wgrad = [&](int l, const float* D, const float* H, int rows) {
     const int ni = P.ni[l], din = m.din[l], dout = m.dout[l];
     const int n_t = P.tile_base[l + 1] - P.tile_base[l];
+    float* dwl = dwb + m.woff[l];
     for (int t = threadIdx.x; t < n_t; t += kThreads) {
       const int o0 = (t / ni) * 4, it = t % ni;
-      float acc[16];
+      float acc[16], cur[16];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) acc[e] = 0.f;
-      for (int r = 0; r < kRB; r += 4) {
+      for (int e = 0; e < 16; ++e) {
+        const int o = o0 + (e >> 2), i = it + ni * (e & 3);
+        cur[e] = (o < dout && i < din) ? dwl[o * din + i] : 0.f;
+        acc[e] = 0.f;
+      }
+      for (int r = 0; r < rows; r += 4) {
         float4 dv[4], av[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -856,16 +882,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
         const int o = o0 + (e >> 2), i = it + ni * (e & 3);
-        if (o < dout && i < din && acc[e] != 0.f) dwb[m.woff[l] + o * din + i] += acc[e];
+        if (o < dout && i < din && acc[e] != 0.f) dwl[o * din + i] = cur[e] + acc[e];
       }
     }
 #pragma unroll
     for (int j = 0; j < kMaxBias; ++j) {
       const int bi = threadIdx.x + j * kThreads - P.bias_base[l];
       if (bi >= 0 && bi < dout) {
-        float s_ = 0.f;
-        for (int r = 0; r < kRB; ++r) s_ += D[bi * kRS + r];
-        bacc[j] += s_;
+        float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int r = 0; r < rows; r += 4) {
+          const float4 d = *reinterpret_cast<const float4*>(&D[bi * kRS + r]);
+          s4.x += d.x; s4.y += d.y; s4.z += d.z; s4.w += d.w;
+        }
+        bacc[j] += (s4.x + s4.y) + (s4.z + s4.w);
       }
     }
   };
@@ -901,6 +930,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
     for (int sub = 0; sub * ipcb < nint_c; ++sub) {
       const int i0 = sub * ipcb;
       const int nint = min(ipcb, nint_c - i0);
+      const int rows = round4(nint * S);  // rows past nint * S carry zero dL/dZ
       __syncthreads();
       if (threadIdx.x < nint) {
         const int slot = w.prim_start[prim] + first + i0 + threadIdx.x;
@@ -916,10 +946,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
         const int din = m.din[l];
         for (int h = 0; h < 2; ++h) {
           __syncthreads();
-          for (int i = threadIdx.x; i < din * 64; i += kThreads) {
-            const int k = i >> 6, cc = i & 63;
-            sStage[i] = W.w(l, 64 * h + cc, k);
-          }
+          wide_stage(din * 64, [&](int i) { return W.w(l, 64 * h + (i & 63), i >> 6); }, sStage);
           if (threadIdx.x < 64) sStage[din * 64 + threadIdx.x] = W.b(l, 64 * h + threadIdx.x);
           __syncthreads();
           fwd_layer<8>(X, din, sStage, sStage + din * 64, act(l + 1) + (size_t)64 * h * kRS, true);
@@ -928,10 +955,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
       {
         const int l = nl - 1, din = m.din[l], dout = m.dout[l];
         __syncthreads();
-        for (int i = threadIdx.x; i < din * dout; i += kThreads) {
-          const int k = i / dout, o = i - k * dout;
-          sStage[i] = W.w(l, o, k);
-        }
+        wide_stage(din * dout, [&](int i) { const int k = i / dout; return W.w(l, i - k * dout, k); }, sStage);
         if (threadIdx.x < dout) sStage[din * dout + threadIdx.x] = W.b(l, threadIdx.x);
         __syncthreads();
         fwd_small(act(l), din, sStage, sStage + din * dout, dout, sZ);
@@ -945,13 +969,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
         const float* D = l == nl - 1 ? sG : act(l + 1);
         float* H = act(l);
         const int dout = m.dout[l];
-        wgrad(l, D, H);
+        wgrad(l, D, H, rows);
         for (int h = 0; h < 2; ++h) {
           __syncthreads();
-          for (int i = threadIdx.x; i < dout * 64; i += kThreads) {
-            const int o = i >> 6, cc = i & 63;
-            sStage[i] = W.w(l, o, 64 * h + cc);
-          }
+          wide_stage(dout * 64, [&](int i) { return W.w(l, i >> 6, 64 * h + (i & 63)); }, sStage);
           __syncthreads();
           dgrad_layer<8>(D, dout, sStage, H + (size_t)64 * h * kRS, H + (size_t)64 * h * kRS);
         }
@@ -960,12 +981,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
       // layer 0: rebuild X, wgrad, then dL/dx of the encoded position (or residual) features
       encode(nint, G);
       __syncthreads();
-      wgrad(0, act(1), sG);
+      wgrad(0, act(1), sG, rows);
       __syncthreads();
-      for (int i = threadIdx.x; i < m.dout[0] * P.nx; i += kThreads) {
-        const int o = i / P.nx, f = i - o * P.nx;
-        sStage[i] = W.w(0, o, P.x0 + f);
-      }
+      wide_stage(m.dout[0] * P.nx, [&](int i) { const int o = i / P.nx; return W.w(0, o, P.x0 + i - o * P.nx); },
+                 sStage);
       __syncthreads();
       dgrad_input(act(1), m.dout[0], sStage, P.nx, 0, P.nx, sG);
       __syncthreads();
