@@ -98,11 +98,12 @@ size_t bwd_smem(const MlpArgs& a, const BwdPlan& P) {
   return bytes;
 }
 
-// Y[c][r] = act(b[c] + sum_k X[k][r] Wt[k][c]), dout = 8 * TN, 64 rows (2 per lane).
-template <int TN>
+// Y[c][r] = act(b[c] + sum_k X[k][r] Wt[k][c]), dout = 8 * TN, 64 rows (2 per lane); the rows
+// of Wt are WS floats apart.
+template <int TN, int WS = 8 * TN>
 MLPS_DEV void fwd_layer(const float* __restrict__ X, int din, const float* __restrict__ Wt,
                         const float* __restrict__ b, float* __restrict__ Y, bool relu) {
-  constexpr int DOUT = 8 * TN;
+  static_assert(WS % 4 == 0 && WS >= 8 * TN, "weight rows are read as float4");
   const int cg = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c0 = cg * TN, r0 = lane * 2;
   float acc[2][TN];
@@ -114,7 +115,7 @@ MLPS_DEV void fwd_layer(const float* __restrict__ X, int din, const float* __res
     float wr[TN];
 #pragma unroll
     for (int j4 = 0; j4 < TN / 4; ++j4) {
-      const float4 wv = *reinterpret_cast<const float4*>(&Wt[k * DOUT + c0 + 4 * j4]);
+      const float4 wv = *reinterpret_cast<const float4*>(&Wt[k * WS + c0 + 4 * j4]);
       wr[4 * j4] = wv.x; wr[4 * j4 + 1] = wv.y; wr[4 * j4 + 2] = wv.z; wr[4 * j4 + 3] = wv.w;
     }
 #pragma unroll
@@ -141,11 +142,12 @@ MLPS_DEV void fwd_small(const float* __restrict__ X, int din, const float* __res
   }
 }
 
-// G[i][r] = sum_o Wc[o][i] D[o][r], masked by act[i][r] > 0; din = 8 * TN.
-template <int TN>
+// G[i][r] = sum_o Wc[o][i] D[o][r], masked by act[i][r] > 0; din = 8 * TN; the rows of Wc are
+// WS floats apart.
+template <int TN, int WS = 8 * TN>
 MLPS_DEV void dgrad_layer(const float* __restrict__ D, int dout, const float* __restrict__ Wc,
                           const float* __restrict__ act, float* __restrict__ G) {
-  constexpr int DIN = 8 * TN;
+  static_assert(WS % 4 == 0 && WS >= 8 * TN, "weight rows are read as float4");
   const int cg = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c0 = cg * TN, r0 = lane * 2;
   float acc[2][TN];
@@ -157,7 +159,7 @@ MLPS_DEV void dgrad_layer(const float* __restrict__ D, int dout, const float* __
     float wr[TN];
 #pragma unroll
     for (int j4 = 0; j4 < TN / 4; ++j4) {
-      const float4 wv = *reinterpret_cast<const float4*>(&Wc[o * DIN + c0 + 4 * j4]);
+      const float4 wv = *reinterpret_cast<const float4*>(&Wc[o * WS + c0 + 4 * j4]);
       wr[4 * j4] = wv.x; wr[4 * j4 + 1] = wv.y; wr[4 * j4 + 2] = wv.z; wr[4 * j4 + 3] = wv.w;
     }
 #pragma unroll
@@ -683,13 +685,15 @@ __global__ void __launch_bounds__(kThreads, MT <= 2 ? 2 : 1) k_mlp_bwd_simt(Work
 //  * each layer's weights are streamed through shared memory, 64 output (forward) or input
 //    (dgrad) columns at a time, from the FP32 blob or, for the tensor-core precisions, from the
 //    BF16 tiles of their blob (the backward then recomputes with the BF16-rounded weights the
-//    forward used);
+//    forward used). Each thread issues all of its loads of a block before its first store;
 //  * dgrad writes delta_{l-1} over H_l in place (each element's ReLU mask is read by the thread
 //    that overwrites it), and the encoded input is rebuilt for layer 0's wgrad, so every layer
 //    input has one buffer;
 //  * the 4 x 4 weight-gradient tiles are accumulated over a sub-chunk in registers and added
 //    into a block-private FP32 copy of dW in global memory (L2-resident), flushed with atomics
 //    when the block moves to another primitive. Bias gradients stay in registers as above.
+
+constexpr int kWideWS = 68;  // row stride of a staged 64-column weight block (4-way store conflicts)
 
 struct WidePlan {
   int nl, nin, nout, nx, x0;
@@ -728,7 +732,7 @@ WidePlan make_wide_plan(const MlpArgs& a, const TcPlan* tp) {
   }
   P.tile_base[m.nl] = tiles;
   P.bias_base[m.nl] = bias;
-  P.stage_floats = m.width * 64 + 64;  // the largest staged block: 128 inputs x 64 columns + bias
+  P.stage_floats = m.width * kWideWS + 64;  // the largest staged block: 128 rows of 64 (+ pad), bias
   if (tp) {
     P.bf16 = 1;
     for (int l = 0; l < m.nl; ++l) {
@@ -749,31 +753,27 @@ size_t wide_smem(const MlpArgs& a, const WidePlan& P) {
          (size_t)ipcb * a.m.F * sizeof(float) + 64;
 }
 
-// Canonical W_l[o][k] and b_l[o] of the staged primitive's blob.
+// Weight sources of the staged primitive's blob: the FP32 W^T [din][dout] per layer, or the BF16
+// tiles (64-wide K blocks of W [npad][64]); b_l[o] from either.
 struct WideWeights {
   const unsigned char* blob;
   const float* f32;
   const Model* m;
   const Packed* pk;
   const WidePlan* P;
-  MLPS_DEV float w(int l, int o, int k) const {
-    if (P->bf16) {
-      const __nv_bfloat16* t = reinterpret_cast<const __nv_bfloat16*>(blob + (size_t)P->gw_row[l] * 128);
-      return __bfloat162float(t[((k >> 6) * P->npad[l] + o) * 64 + (k & 63)]);
-    }
-    return f32[pk->woff[l] + k * m->dout[l] + o];  // FP32 blob: W^T [din][dout]
-  }
   MLPS_DEV float b(int l, int o) const {
     if (P->bf16) return reinterpret_cast<const float*>(blob + P->gbias_byte)[P->bias_off[l] + o];
     return f32[pk->boff[l] + o];
   }
+  MLPS_DEV const __nv_bfloat16* tile(int l) const {
+    return reinterpret_cast<const __nv_bfloat16*>(blob + (size_t)P->gw_row[l] * 128);
+  }
 };
 
-// dst[i] = src(i) for i < n <= kWideStageMax: every thread issues all of its loads before its
-// first store, so one staging pass costs one memory round trip rather than one per element.
+// dst[i] = src(i) for i < n <= kWideStageMax, all of a thread's loads before its first store.
 constexpr int kWideStageMax = 128 * 64;
 template <class Src>
-MLPS_DEV void wide_stage(int n, Src src, float* __restrict__ dst) {
+MLPS_DEV void wide_stage_flat(int n, Src src, float* __restrict__ dst) {
   constexpr int kPer = kWideStageMax / kThreads;
   float r[kPer];
 #pragma unroll
@@ -788,7 +788,109 @@ MLPS_DEV void wide_stage(int n, Src src, float* __restrict__ dst) {
   }
 }
 
+// dst[at(a, b)] = src(a, b) over the n elements i = a * d + b (b < d) of a staged block. Element
+// i goes to thread i mod 256; (a, b) steps by (256 / d, 256 mod d) from one element of a thread to
+// the next, so no thread divides more than once. Every thread issues all of its loads before its
+// first store: one staging pass costs one memory round trip rather than one per element.
+template <class Src, class At>
+MLPS_DEV void wide_stage(int n, int d, Src src, At at, float* __restrict__ dst) {
+  constexpr int kPer = kWideStageMax / kThreads;
+  const int a0 = threadIdx.x / d, b0 = threadIdx.x - a0 * d;
+  const int qa = kThreads / d, qb = kThreads - qa * d;
+  float r[kPer];
+  int a = a0, b = b0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    r[j] = threadIdx.x + j * kThreads < n ? src(a, b) : 0.f;
+    a += qa;
+    b += qb;
+    if (b >= d) { b -= d; ++a; }
+  }
+  a = a0;
+  b = b0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    if (threadIdx.x + j * kThreads < n) dst[at(a, b)] = r[j];
+    a += qa;
+    b += qb;
+    if (b >= d) { b -= d; ++a; }
+  }
+}
+
+// The four staged blocks of the wide backward. FP32 blob: W^T [din][dout] per layer, staged
+// with consecutive threads on consecutive shared-memory words (rows WS = 64 apart; the dgrad
+// blocks then read the blob with a stride). BF16 blob:
+// 64-wide K blocks of W, [npad][64] each, staged with consecutive threads on consecutive global
+// addresses (rows WS = 68 apart, so the transposing stores meet at most 4-way bank conflicts).
+// Each was the faster of the two mappings for its source in a per-phase cycle count of the
+// 4 x 128 model.
+template <bool BF16>
+struct WideStager {
+  static constexpr int WS = BF16 ? kWideWS : 64;
+  const WideWeights& W;
+  const Model& m;
+  const WidePlan& P;
+  float* s;
+  // Wt[k][c] = W_l[64 h + c][k] (k < din, c < 64) at s[k * WS + c], then 64 biases
+  MLPS_DEV void fwd_half(int l, int h) const {
+    const int din = m.din[l];
+    if constexpr (BF16) {
+      const __nv_bfloat16* t = W.tile(l) + (size_t)64 * h * 64;
+      const int np64 = P.npad[l] * 64;
+      wide_stage(din * 64, din, [&](int c, int k) { return __bfloat162float(t[(k >> 6) * np64 + c * 64 + (k & 63)]); },
+                 [&](int c, int k) { return k * WS + c; }, s);
+    } else {
+      const int dout = m.dout[l];
+      const float* f = W.f32 + W.pk->woff[l] + 64 * h;
+      wide_stage_flat(din * 64, [&](int i) { return f[(i >> 6) * dout + (i & 63)]; }, s);
+    }
+    if (threadIdx.x < 64) s[din * WS + threadIdx.x] = W.b(l, 64 * h + threadIdx.x);
+  }
+  // Wc[o][c] = W_l[o][64 h + c] (o < dout, c < 64) at s[o * WS + c]
+  MLPS_DEV void dgrad_half(int l, int h) const {
+    const int dout = m.dout[l];
+    if constexpr (BF16) {
+      const __nv_bfloat16* t = W.tile(l) + (size_t)h * P.npad[l] * 64;
+      wide_stage(dout * 64, 64, [&](int o, int c) { return __bfloat162float(t[o * 64 + c]); },
+                 [&](int o, int c) { return o * WS + c; }, s);
+    } else {
+      const float* f = W.f32 + W.pk->woff[l] + (size_t)64 * h * dout;
+      wide_stage_flat(dout * 64, [&](int i) { return f[(i & 63) * dout + (i >> 6)]; }, s);
+    }
+  }
+  // the head, compact: Wt[k][o] at s[k * dout + o], then dout biases
+  MLPS_DEV void head(int l) const {
+    const int din = m.din[l], dout = m.dout[l];
+    if constexpr (BF16) {
+      const __nv_bfloat16* t = W.tile(l);
+      const int np64 = P.npad[l] * 64;
+      wide_stage(din * dout, din, [&](int o, int k) { return __bfloat162float(t[(k >> 6) * np64 + o * 64 + (k & 63)]); },
+                 [&](int o, int k) { return k * dout + o; }, s);
+    } else {
+      const float* f = W.f32 + W.pk->woff[l];
+      wide_stage_flat(din * dout, [&](int i) { return f[i]; }, s);
+    }
+    if (threadIdx.x < dout) s[din * dout + threadIdx.x] = W.b(l, threadIdx.x);
+  }
+  // layer 0's columns of the encoded position features: Wc[o][f] = W_0[o][x0 + f] at s[o * nx + f]
+  MLPS_DEV void input_cols() const {
+    const int dout = m.dout[0], nx = P.nx, x0 = P.x0;
+    if constexpr (BF16) {
+      const __nv_bfloat16* t = W.tile(0);
+      const int np64 = P.npad[0] * 64;
+      wide_stage(dout * nx, nx, [&](int o, int f) { const int k = x0 + f;
+                                                    return __bfloat162float(t[(k >> 6) * np64 + o * 64 + (k & 63)]); },
+                 [&](int o, int f) { return o * nx + f; }, s);
+    } else {
+      const float* f = W.f32 + W.pk->woff[0] + (size_t)x0 * dout;
+      wide_stage_flat(dout * nx, [&](int i) { const int o = i / nx; return f[(i - o * nx) * dout + o]; }, s);
+    }
+  }
+};
+
+template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpArgs a, WidePlan P) {
+  constexpr int WS = WideStager<BF16>::WS;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const Model& m = a.m;
@@ -816,6 +918,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
   int prim = find_prim(w, cb);
   int loaded = -1;
   WideWeights W{nullptr, nullptr, &m, &a.pk, &P};
+  const WideStager<BF16> stage{W, m, P, sStage};
 
   auto flush = [&](int p) {
     float* dW = a.d_weights + (size_t)p * m.Prow;
@@ -946,17 +1049,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
         const int din = m.din[l];
         for (int h = 0; h < 2; ++h) {
           __syncthreads();
-          wide_stage(din * 64, [&](int i) { return W.w(l, 64 * h + (i & 63), i >> 6); }, sStage);
-          if (threadIdx.x < 64) sStage[din * 64 + threadIdx.x] = W.b(l, 64 * h + threadIdx.x);
+          stage.fwd_half(l, h);
           __syncthreads();
-          fwd_layer<8>(X, din, sStage, sStage + din * 64, act(l + 1) + (size_t)64 * h * kRS, true);
+          fwd_layer<8, WS>(X, din, sStage, sStage + din * WS, act(l + 1) + (size_t)64 * h * kRS, true);
         }
       }
       {
         const int l = nl - 1, din = m.din[l], dout = m.dout[l];
         __syncthreads();
-        wide_stage(din * dout, [&](int i) { const int k = i / dout; return W.w(l, i - k * dout, k); }, sStage);
-        if (threadIdx.x < dout) sStage[din * dout + threadIdx.x] = W.b(l, threadIdx.x);
+        stage.head(l);
         __syncthreads();
         fwd_small(act(l), din, sStage, sStage + din * dout, dout, sZ);
         __syncthreads();
@@ -972,9 +1073,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
         wgrad(l, D, H, rows);
         for (int h = 0; h < 2; ++h) {
           __syncthreads();
-          wide_stage(dout * 64, [&](int i) { return W.w(l, i >> 6, 64 * h + (i & 63)); }, sStage);
+          stage.dgrad_half(l, h);
           __syncthreads();
-          dgrad_layer<8>(D, dout, sStage, H + (size_t)64 * h * kRS, H + (size_t)64 * h * kRS);
+          dgrad_layer<8, WS>(D, dout, sStage, H + (size_t)64 * h * kRS, H + (size_t)64 * h * kRS);
         }
         __syncthreads();
       }
@@ -983,8 +1084,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
       __syncthreads();
       wgrad(0, act(1), sG, rows);
       __syncthreads();
-      wide_stage(m.dout[0] * P.nx, [&](int i) { const int o = i / P.nx; return W.w(0, o, P.x0 + i - o * P.nx); },
-                 sStage);
+      stage.input_cols();
       __syncthreads();
       dgrad_input(act(1), m.dout[0], sStage, P.nx, 0, P.nx, sG);
       __syncthreads();
@@ -1007,9 +1107,10 @@ cudaError_t launch_mlp_bwd_simt_wide(const Work& w, const MlpArgs& a, const TcPl
   if (!simt_bwd_wide_supported(a) || !w.dwb) return cudaErrorNotSupported;
   const WidePlan P = make_wide_plan(a, tp);
   const size_t smem = wide_smem(a, P);
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_bwd_simt_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = P.bf16 ? k_mlp_bwd_simt_wide<true> : k_mlp_bwd_simt_wide<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_mlp_bwd_simt_wide<<<n_sm, kThreads, smem, st>>>(w, a, P);
+  kern<<<n_sm, kThreads, smem, st>>>(w, a, P);
   return cudaGetLastError();
 }
 
