@@ -67,3 +67,16 @@ def test_job_throughput_and_seeds():
     seeds = [set(range(bench.rank_view_seed(r, 8), bench.rank_view_seed(r, 8) + 8)) for r in range(4)]
     assert all(not (a & b) for i, a in enumerate(seeds) for b in seeds[i + 1:])
     assert bench.rank_scene_seed(1) == 32 and bench.rank_scene_seed(0) == 0
+
+
+def test_hit_capacity_per_workload():
+    """Hit records reserved per ray: 16 for the 1024-primitive scene (about eight hits per ray
+    at 1080p, more at low resolution), 8 otherwise, or the explicit --hit-capacity."""
+    import sys
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    auto = types.SimpleNamespace(hit_capacity=0.0)
+    assert bench.hit_capacity(auto, synth.CONFIGS["stress"]) == 16.0
+    assert bench.hit_capacity(auto, synth.CONFIGS["prec"]) == 8.0
+    assert bench.hit_capacity(types.SimpleNamespace(hit_capacity=12.0), synth.CONFIGS["prec"]) == 12.0
