@@ -690,10 +690,13 @@ __global__ void __launch_bounds__(kThreads, MT <= 2 ? 2 : 1) k_mlp_bwd_simt(Work
 //    that overwrites it), and the encoded input is rebuilt for layer 0's wgrad, so every layer
 //    input has one buffer;
 //  * the 4 x 4 weight-gradient tiles are accumulated over a sub-chunk in registers and added
-//    into a block-private FP32 copy of dW in global memory (L2-resident), flushed with atomics
-//    when the block moves to another primitive. Bias gradients stay in registers as above.
+//    into a block-private FP32 copy of dW in global memory (L2-resident; a tile's entries are
+//    read before its FMA loop), flushed with atomics when the block moves to another primitive.
+//    Bias gradients stay in registers as above.
 
-constexpr int kWideWS = 68;  // row stride of a staged 64-column weight block (4-way store conflicts)
+// Row stride of a staged 64-column block of BF16-tile weights: the transposing stores of the
+// coalesced reads meet at most 4-way bank conflicts. (FP32-blob blocks keep rows 64 apart.)
+constexpr int kWideWS = 68;
 
 struct WidePlan {
   int nl, nin, nout, nx, x0;
@@ -758,7 +761,6 @@ size_t wide_smem(const MlpArgs& a, const WidePlan& P) {
 struct WideWeights {
   const unsigned char* blob;
   const float* f32;
-  const Model* m;
   const Packed* pk;
   const WidePlan* P;
   MLPS_DEV float b(int l, int o) const {
@@ -917,7 +919,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
   const int wstride = (int)(a.pk.stride / 4);
   int prim = find_prim(w, cb);
   int loaded = -1;
-  WideWeights W{nullptr, nullptr, &m, &a.pk, &P};
+  WideWeights W{nullptr, nullptr, &a.pk, &P};
   const WideStager<BF16> stage{W, m, P, sStage};
 
   auto flush = [&](int p) {
