@@ -60,7 +60,11 @@ def _args():
     ap.add_argument("--mlp-groups", type=int, default=0,
                     help="forward tensor-core MLP samples per CTA in 128-row chunks (0 = library default)")
     ap.add_argument("--compare", action="store_true",
-                    help="also time the FP32 path and forward-only passes (extra lines in 'results')")
+                    help="time the other precisions and passes too (the default for the prec workload)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="time only the selected precision and pass")
+    ap.add_argument("--hit-check-rays", type=int, default=4000,
+                    help="rays sampled for the hit-list check against the oracle (0: none)")
     return ap.parse_args()
 
 
@@ -339,10 +343,13 @@ def run_ours(a):
     total_ms, ms, launches, prof, clocks = timed(r, do_bwd, a.steps, a.warmup, sample_clocks=True, profile=True)
     n_hits = r.hit_count()
     value = job_rays_per_s(n_rays, ws, a.steps, total_ms)
-    results = {f"{precision}_{'fwd_bwd' if do_bwd else 'fwd'}": value}
 
-    if a.compare:
-        for p2, b2 in [("fp32", True), ("fp32", False), ("bf16", True), ("bf16", False), ("fp8", True),
+    results = {f"{precision}_{'fwd_bwd' if do_bwd else 'fwd'}":
+               {"value": value, "ms_per_step": total_ms / a.steps, "steps": a.steps, "warmup": a.warmup}}
+    if (a.compare or a.workload == "prec") and not a.no_compare:
+        # the metric's other legs: each precision forward-only and forward+backward, 3 warm-up
+        # steps each; the FP32 forward+backward (seconds per step) gets 2 timed steps
+        for p2, b2 in [("bf16", True), ("bf16", False), ("fp32", True), ("fp32", False), ("fp8", True),
                        ("fp8", False)]:
             key = f"{p2}_{'fwd_bwd' if b2 else 'fwd'}"
             if key in results:
@@ -352,11 +359,17 @@ def run_ours(a):
                 _, ok2 = try_pass(r2, b2)
                 if b2 and not ok2:
                     continue
-                t2, _, _, _, _ = timed(r2, b2, max(2, a.steps // 2), 2)
-                results[key] = n_rays * ws * max(2, a.steps // 2) / (t2 / 1e3)
+                n2 = 2 if (p2 == "fp32" and b2) else max(3, a.steps // 2)
+                t2, _, _, _, _ = timed(r2, b2, n2, 3)
+                results[key] = {"value": job_rays_per_s(n_rays, ws, n2, t2), "ms_per_step": t2 / n2,
+                                "steps": n2, "warmup": 3}
                 del r2
             except _lib.MlpsError:
                 pass
+        if "bf16_fwd_bwd" in results and "fp32_fwd_bwd" in results:
+            results["bf16_over_fp32_fwd_bwd"] = results["bf16_fwd_bwd"]["value"] / results["fp32_fwd_bwd"]["value"]
+        if "bf16_fwd" in results and "fp32_fwd" in results:
+            results["bf16_over_fp32_fwd"] = results["bf16_fwd"]["value"] / results["fp32_fwd"]["value"]
 
     # ---- roofline of the dominant kernel stage (live CUDA events on the launching stream)
     peaks, peak_src = _peaks()
@@ -433,11 +446,47 @@ def run_ours(a):
         line["e2e"] = run_e2e(a, wl, scene, cams, precision, do_bwd, dev)
     if rank == 0 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, wl, scene, cams, do_bwd, r)
+        if a.hit_check_rays > 0:
+            line["hit_lists"] = hit_list_check(wl, scene, cams, r, a.hit_check_rays)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def hit_list_check(wl, scene, cams, r, n_rays):
+    """Hit lists of the timed launch against the oracle on sampled rays: rays with a primitive
+    within 1e-6 of tangency (|1 - m^2| < 1e-6, m^2 in FP64) are counted and excluded; every
+    other ray must list the same primitives in the same order."""
+    import oracle
+    from paper_2606_03877_gb300 import synth
+
+    t = time.perf_counter()
+    max_out = 32
+    h = r.hits(max_out)
+    pix = synth.sample_pixels(wl, n_rays, seed=4242)
+    idx = pix[:, 0].astype(np.int64) * wl.width * wl.height + pix[:, 2].astype(np.int64) * wl.width + pix[:, 1]
+    import torch
+    ii = torch.from_numpy(idx).to(h["count"].device)
+    count = h["count"][ii].cpu().numpy()
+    prim = h["prim"][ii].cpu().numpy()
+    del h
+    band = mism = hits = 0
+    for j, (v, x, y) in enumerate(pix):
+        m2, _ = oracle.ray_m2(scene, cams[v], int(x), int(y))
+        if np.any(np.abs(m2 - 1.0) < 1e-6):
+            band += 1
+            continue
+        oh = oracle.ray_hits(scene, cams[v], int(x), int(y), tile=int(wl.tile_sort))
+        n = int(count[j])
+        hits += len(oh["prim"])
+        if n != len(oh["prim"]) or n > max_out or list(prim[j, :n]) != list(oh["prim"]):
+            mism += 1
+    return {"rays_checked": int(len(pix)), "rays_in_tangency_band": int(band), "hits_compared": int(hits),
+            "mismatches_outside_band": int(mism), "seconds": round(time.perf_counter() - t, 2),
+            "rule": "same primitives in the same order as the FP64 oracle, except rays with a primitive "
+                    "within 1e-6 of tangency (counted here, excluded)"}
 
 
 def run_e2e(a, wl, scene, cams, precision, do_bwd, dev):

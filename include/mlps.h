@@ -93,8 +93,9 @@ typedef struct {
                                    hit (samples must be 1) whose MLP input is gamma([d; delta]),
                                    d the unit ray direction and delta = mu - p* the offset from
                                    the contact point p* = o + max(0, t*) d to the centre (Eq. 3);
-                                   the hit's alpha uses its chord length. FP32 only
-                                   (MLPS_ERR_UNSUPPORTED otherwise). */
+                                   the hit's alpha uses its chord length. The forward pass
+                                   runs in every precision; the backward pass in FP32 only
+                                   (MLPS_ERR_UNSUPPORTED from mlps_render_backward otherwise). */
   int32_t slot_dim;             /* C of the feature slots of Sec. 3.4 (0 = none; a multiple of 4,
                                    <= 2048): every primitive also carries four slot embeddings
                                    e_k in R^C, stored after its MLP parameters (canonical weights
@@ -210,14 +211,18 @@ mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene
  * held in a static device array of the library (every GPU that loads the library keeps it
  * until the process exits). Renders whose mlps_workspace_size() total (saved rounded up to 256
  * bytes, plus scratch) exceeds 32 MiB are rejected with MLPS_ERR_WORKSPACE_TOO_SMALL before
- * anything is enqueued. It allocates nothing and calls no allocating routine.
- * The first call on a device looks up the array's device address with that device current;
- * make that first call before any stream capture. All calls share the one array and it keeps
- * the last call's contents (each call clears what it needs), so calls that overlap on the GPU
- * (other streams, other host threads) race; serialise them. There is no backward pass for this
- * variant. If `device_status` (device pointer, may be NULL) is given, the call's device status
- * word (MLPS_OK or the device-detected error, as mlps_read_status would return) is copied
- * there asynchronously on `stream` at the end of the call. */
+ * anything is enqueued. It calls no cudaMalloc / cudaFree and no allocating routine.
+ * The first call on a device looks up the array's device address with that device current.
+ * Under CUDA's lazy module loading (the default) that lookup is also what loads the array's
+ * module on the device and reserves its 32 MiB there, so the first call can fail for lack of
+ * device memory (MLPS_ERR_CUDA) and can synchronise: make it once, before the frame loop and
+ * before any stream capture. Later calls reserve nothing. All calls share the one array and it
+ * keeps the last call's contents (each call clears what it needs), so calls that overlap on the
+ * GPU (other streams, other host threads) race; serialise them. There is no backward pass for
+ * this variant. If `device_status` (device pointer, may be NULL) is given and the call returns
+ * MLPS_OK, the call's device status word (MLPS_OK or the device-detected error, as
+ * mlps_read_status would return) is copied there asynchronously on `stream` at the end of the
+ * call; when the call returns any other status, `device_status` is not written. */
 mlps_status mlps_render_forward_static(const mlps_config* cfg, const mlps_scene* scene,
                                        const mlps_camera* cams, int32_t n_views, float* rgb,
                                        float* trans, float* feat, int32_t* device_status,

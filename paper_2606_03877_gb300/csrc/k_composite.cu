@@ -41,6 +41,10 @@ __global__ void k_composite_fwd(Work w, int F, int FT, float* __restrict__ rgb, 
 // Reverse pass. With C = sum_j T_j C_j, T_final = exp(-sum_j a_j):
 //   dL/dC_j = T_j dL/dC,   dL/dF_j = T_j dL/dF,
 //   dL/da_j = -dL/dC . sum_{l>j} T_l C_l - dL/dF . sum_{l>j} T_l F_l - dL/dT_final T_final.
+// Two forward sweeps, no per-hit array: the first repeats the forward composite (the same
+// operations, so the same T_j, early-termination cut and totals C, F); the second walks the
+// intervals again with the prefix P_j = sum_{l<j} T_l C_l and takes the suffix sums as
+// sum_{l>j} T_l C_l = C - P_j - T_j C_j.
 // Intervals skipped by early termination get zero gradient. The per-interval gradients are
 // written in the primitive-major order of the interval records, so that the MLP backward
 // reads one contiguous block per chunk. With feature slots, `slot_ga` adds the slot features'
@@ -52,41 +56,47 @@ __global__ void k_composite_bwd(Work w, int F, int FT, const float* __restrict__
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= w.n_rays) return;
   const int n = w.ray_count[r], s = w.ray_start[r];
-  float Aex[kMaxHits];
-  float A = 0.f;
+  float A = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  float RF[kMaxFeat];  // sweep 1: the totals F; sweep 2: the suffix sums
+  for (int f = 0; f < F; ++f) RF[f] = 0.f;
   int used = 0;
   for (int j = 0; j < n; ++j) {
-    Aex[j] = A;
-    A += w.hit_out[s + j].w;
+    const float4 o = w.hit_out[s + j];
+    const float T = expf(-A);
+    C0 = fmaf(T, o.x, C0);
+    C1 = fmaf(T, o.y, C1);
+    C2 = fmaf(T, o.z, C2);
+    for (int f = 0; f < F; ++f) RF[f] = fmaf(T, w.hit_feat[(size_t)(s + j) * F + f], RF[f]);
+    A += o.w;
     used = j + 1;
     if (expf(-A) < w.t_eps) break;
   }
   const float Tfin = expf(-A);
   const float g0 = d_rgb[3 * (size_t)r], g1 = d_rgb[3 * (size_t)r + 1], g2 = d_rgb[3 * (size_t)r + 2];
   const float gT = d_trans ? d_trans[r] : 0.f;
-  float gF[kMaxFeat], RF[kMaxFeat];
-  for (int f = 0; f < F; ++f) {
-    gF[f] = d_feat ? d_feat[(size_t)r * FT + f] : 0.f;
-    RF[f] = 0.f;
-  }
-  float R0 = 0.f, R1 = 0.f, R2 = 0.f;  // sum over later intervals of T_l C_l
-  for (int j = used - 1; j >= 0; --j) {
+  float gF[kMaxFeat];
+  for (int f = 0; f < F; ++f) gF[f] = d_feat ? d_feat[(size_t)r * FT + f] : 0.f;
+  float P0 = 0.f, P1 = 0.f, P2 = 0.f;  // prefix sums of T_l C_l over l < j
+  A = 0.f;
+  for (int j = 0; j < used; ++j) {
     const int h = s + j;
     const float4 o = w.hit_out[h];
-    const float T = expf(-Aex[j]);
-    float ga = -(g0 * R0 + g1 * R1 + g2 * R2) - gT * Tfin;
-    for (int f = 0; f < F; ++f) ga -= gF[f] * RF[f];
-    if (slot_ga) ga += slot_ga[h];
+    const float T = expf(-A);
+    const float Q0 = fmaf(T, o.x, P0), Q1 = fmaf(T, o.y, P1), Q2 = fmaf(T, o.z, P2);  // P_{j+1}
+    float ga = -(g0 * (C0 - Q0) + g1 * (C1 - Q1) + g2 * (C2 - Q2)) - gT * Tfin;
     const int sl = w.slot_of[h];
-    w.hit_grad[sl] = make_float4(T * g0, T * g1, T * g2, ga);
     for (int f = 0; f < F; ++f) {
-      const float Fj = w.hit_feat[(size_t)h * F + f];
+      const float TFj = T * w.hit_feat[(size_t)h * F + f];
+      RF[f] -= TFj;  // now sum over l > j
+      ga -= gF[f] * RF[f];
       w.hit_gfeat[(size_t)sl * F + f] = T * gF[f];
-      RF[f] = fmaf(T, Fj, RF[f]);
     }
-    R0 = fmaf(T, o.x, R0);
-    R1 = fmaf(T, o.y, R1);
-    R2 = fmaf(T, o.z, R2);
+    if (slot_ga) ga += slot_ga[h];
+    w.hit_grad[sl] = make_float4(T * g0, T * g1, T * g2, ga);
+    P0 = Q0;
+    P1 = Q1;
+    P2 = Q2;
+    A += o.w;
   }
   for (int j = used; j < n; ++j) {
     const int sl = w.slot_of[s + j];

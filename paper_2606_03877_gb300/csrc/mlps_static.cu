@@ -7,9 +7,13 @@
 // middle of a frame. The regular entry point asks the caller for `saved` and `scratch`
 // buffers; this one uses a fixed workspace that lives in a static device array instead.
 //
-// The array is part of the library image, so every GPU on which the library is loaded holds
-// kStaticBytes of device memory for it until the process exits, whether or not this entry
-// point is ever called.
+// The array belongs to this file's module of the library image. With CUDA's lazy module
+// loading (the default) that module is loaded on a device, and its kStaticBytes of device memory
+// reserved there, by the first call of this entry point on that device (the symbol lookup in
+// static_workspace); with eager loading it happens when the library loads. Either way the
+// memory stays reserved until the process exits. That first call can therefore fail for lack
+// of device memory (MLPS_ERR_CUDA) and can synchronise: make it once, before the frame loop
+// and before any stream capture. Later calls reserve nothing.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -30,7 +34,8 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
 // Device address of the array on the current device; looked up once per device, with that
-// device current. nullptr (and the CUDA error in *err) if the lookup fails.
+// device current (the lookup loads the module on that device, see above). nullptr (and the
+// CUDA error in *err) if the lookup fails.
 void* static_workspace(int dev, cudaError_t* err) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_addr[dev]) {
@@ -64,7 +69,7 @@ extern "C" mlps_status mlps_render_forward_static(const mlps_config* cfg, const 
   // per-call count it relies on before use, so the previous call's contents do no harm.
   s = mlps_render_forward(cfg, scene, cams, n_views, rgb, trans, feat, ws, saved_bytes,
                           ws + saved_al, scratch_bytes, stream);
-  if (s != MLPS_OK) return s;
+  if (s != MLPS_OK) return s;  // device_status is left as it was (documented in include/mlps.h)
   if (device_status) {
     // the status word is the first int of the region: hand it to the caller asynchronously
     if (cudaMemcpyAsync(device_status, ws, sizeof(int32_t), cudaMemcpyDeviceToDevice,

@@ -143,13 +143,13 @@ def test_full_size_prec_sampled_gradients_fp32():
 
 
 def test_full_size_prec_sampled_gradients_bf16():
-    """BF16: the weight gradients meet the 2e-2 bar. The pose gradients of these sparse samples
-    (~23 pixels per primitive) carry ReLU mask flips of BF16 rounding that do not average out
-    (2.6-3.9 % at 6000 pixels, falling with the pixel count); bounded loosely here."""
-    errs = _full_size_sampled("bf16", 6000)
-    assert errs["d_weights"] < 2e-2, errs
-    for k in ("d_centers", "d_scales", "d_quats"):
-        assert errs[k] < 6e-2, (k, errs)
+    """BF16 at the bench's full-size launch, every parameter group at the 2e-2 bar. The BF16
+    error of the pose groups comes from ReLU mask flips (pre-activations within BF16 rounding of
+    zero), which average out over the pixels a primitive covers: 48 000 sampled pixels (~190 per
+    primitive) keep them under the bar, where 6000 pixels (~23 per primitive) gave 2.6-3.9 %."""
+    errs = _full_size_sampled("bf16", 48000)
+    for k, e in errs.items():
+        assert e < 2e-2, (k, errs)
 
 
 def _stress_small(seed=3):

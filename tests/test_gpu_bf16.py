@@ -154,21 +154,22 @@ def test_bf16_backward_l2_loss(S):
 
 @pytest.mark.parametrize("S", [32, 16, 48])
 def test_bf16_backward_without_mask_flips_random_gradient(S):
-    """With every ReLU active the BF16 backward is a rounding-only approximation. Random dL/dC
-    and dL/dT cancel heavily in the pose sums, so rounding shows at the 1-2 % level there
-    (0.6 % on the weights); a wrong term in any formula gives O(1) errors."""
+    """With every ReLU active the BF16 backward is a rounding-only approximation, held to the
+    BF16 bar of 2e-2 even with random dL/dC and dL/dT, which cancel heavily in the pose sums;
+    a wrong term in any formula gives O(1) errors."""
     cfg = synth.CONFIGS["prec"].replace(width=64, height=48, K=12, n_views=2, samples=S)
     scene = _no_flip(scaled_scene(cfg, 1, 2.0), cfg)
     cams = synth.make_cameras(cfg, first_view_seed=1)
     g = synth.make_grad((2, 48, 64, 3), seed=5)
     gT = synth.make_grad((2, 48, 64), seed=6)
-    _check_bf16_grads(cfg, scene, cams, g, gT, tol=3e-2)
+    _check_bf16_grads(cfg, scene, cams, g, gT, tol=2e-2)
 
 
 def test_bf16_backward_random_gradient_reported():
-    """Random dL/dC cancels heavily; BF16 then flips ReLU masks of near-zero units, whose O(1)
-    per-element changes dominate the error (~3 % on the first layer, ~7 % on quaternions at
-    this size). Reported, with a loose bar."""
+    """Report only, not a parity claim: random dL/dC has no image loss behind it, so nothing
+    averages the O(1) per-unit changes of ReLU masks that BF16 rounding flips (~3 % on the
+    first layer, ~7 % on quaternions at this size). The bound of 0.1 only catches a broken
+    formula; the BF16 bar of 2e-2 is held by the L2-loss tests, including the full-size one."""
     cfg = synth.CONFIGS["prec"].replace(width=64, height=48, K=12, n_views=2)
     scene = scaled_scene(cfg, 1, 2.0)
     cams = synth.make_cameras(cfg, first_view_seed=1)
@@ -182,7 +183,7 @@ def test_bf16_backward_feature_head():
     cams = synth.make_cameras(cfg, first_view_seed=7)
     g = synth.make_grad((1, 32, 40, 3), seed=1)
     gF = synth.make_grad((1, 32, 40, 8), seed=2)
-    _check_bf16_grads(cfg, scene, cams, g, None, gF, tol=3e-2)
+    _check_bf16_grads(cfg, scene, cams, g, None, gF, tol=2e-2)
 
 
 def test_bf16_backward_many_chunks_per_primitive():

@@ -62,6 +62,50 @@ def test_static_forward_matches_regular_entry_point_on_two_calls(precision):
         assert (ref["trans"] < 1).sum() > 100
 
 
+def test_static_forward_allocates_nothing_after_the_first_call():
+    """The first call on a device reserves the static array (module load); from then on a call
+    leaves the device's free memory unchanged."""
+    cfg = synth.CONFIGS["prec"].replace(width=64, height=48, K=12, n_views=1)
+    scene = scaled_scene(cfg, 5, 2.0)
+    cams = synth.make_cameras(cfg, first_view_seed=5)
+    r = Renderer(cfg, precision="fp32")
+    d = to_dev(scene)
+    packed = r.pack(d["weights"])
+    rgb = torch.empty((1, cfg.height, cfg.width, 3), device="cuda")
+    trans = torch.empty((1, cfg.height, cfg.width), device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    scn = _lib.make_scene(cfg.K, d["centers"], d["scales"], d["quats"], packed)
+    cs = _lib.cameras(cams)
+    stream = torch.cuda.current_stream().cuda_stream
+    _lib.mlps_render_forward_static(r.cfg, scn, cs, 1, rgb, trans, None, status, stream)  # warm-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    _lib.mlps_render_forward_static(r.cfg, scn, cs, 1, rgb, trans, None, status, stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert int(status.item()) == 0
+
+
+def test_static_forward_reports_device_detected_error():
+    """A non-finite primitive centre, made on the host: the call returns MLPS_OK (nothing is
+    wrong on the host side) and the device status word it hands back says MLPS_ERR_NONFINITE."""
+    cfg = synth.CONFIGS["prec"].replace(width=64, height=48, K=12, n_views=1)
+    scene = scaled_scene(cfg, 6, 2.0)
+    scene["centers"][3, 1] = np.nan
+    cams = synth.make_cameras(cfg, first_view_seed=6)
+    r = Renderer(cfg, precision="fp32")
+    d = to_dev(scene)
+    packed = r.pack(d["weights"])
+    rgb = torch.empty((1, cfg.height, cfg.width, 3), device="cuda")
+    trans = torch.empty((1, cfg.height, cfg.width), device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    scn = _lib.make_scene(cfg.K, d["centers"], d["scales"], d["quats"], packed)
+    _lib.mlps_render_forward_static(r.cfg, scn, _lib.cameras(cams), 1, rgb, trans, None, status,
+                                    torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert int(status.item()) == _lib.MLPS_ERR_NONFINITE
+
+
 def test_static_forward_rejects_workspace_beyond_limit():
     cfg = synth.CONFIGS["prec"]  # 1080p x 8 views needs gigabytes
     r = Renderer(cfg.replace(n_views=1), precision="fp32")
