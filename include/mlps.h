@@ -85,7 +85,8 @@ typedef struct {
   float t_eps;                  /* early termination: stop compositing once T < t_eps (0: never) */
   int32_t tile;                 /* screen tile edge in pixels for binning: 16 (default) or 8 */
   int32_t mlp_groups;           /* chunks of 128 sample rows in flight per CTA in the forward
-                                   tensor-core MLP (2..6 at width 64, 3 with a feature head,
+                                   tensor-core MLP (2..5 at width 64 in BF16, 2..6 in E4M3,
+                                   3 with a feature head,
                                    2 at width 128); 0 = library default. mlps_autotune_batch
                                    picks it together with `tile`. */
   int32_t contact;              /* 0: S midpoint samples of the local position per hit interval;

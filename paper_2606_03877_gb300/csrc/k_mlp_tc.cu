@@ -85,7 +85,13 @@ template <int WIDTH, int XL, int DL, int NF, int kNEG, bool F8>
 __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     k_mlp_fwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
   constexpr int kThreadsTC = kEGThreads * kNEG;
-  static_assert(kNEG >= 1 && kNEG <= 6 && kNEG * WIDTH <= 512, "TMEM holds 512 columns");
+  // BF16: each group's TMEM holds its FP32 accumulator (WIDTH columns) and the next layer's
+  // A operand (WIDTH / 2 columns of BF16 pairs); E4M3 keeps its A tiles in shared memory.
+  constexpr bool kTA = !F8;
+  constexpr uint32_t kGCols = kTA ? (uint32_t)(WIDTH + WIDTH / 2) : (uint32_t)WIDTH;
+  // the encoded input goes to TMEM too when it is built in registers (compile-time shapes)
+  constexpr bool kA0T = kTA && XL >= 0;
+  static_assert(kNEG >= 1 && kNEG <= 6 && kNEG * kGCols <= 512, "TMEM holds 512 columns");
   static_assert(4 + NF <= kMaxScanVals, "scan scratch holds kMaxScanVals values per warp");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -264,9 +270,14 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
 #pragma unroll
             for (int e = 0; e < 32; ++e) pk[e] = 0u;
           }
+          if (kA0T) {
+            tmem_st32(tmem + (uint32_t)g * kGCols + WIDTH + ((uint32_t)(q * 32) << 16), pk);
+            tmem_wait_st();
+          } else {
 #pragma unroll
-          for (int ch = 0; ch < 8; ++ch)
-            st_shared_v4(A + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+            for (int ch = 0; ch < 8; ++ch)
+              st_shared_v4(A + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+          }
         } else {
           RowWriter rw{A, row, 0, 0.f};
           if (valid && m.contact) {
@@ -296,20 +307,25 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
           }
           rw.pad_to(P.kpad[0]);
         }
-        fence_proxy_async_smem();
+        if (!kA0T) fence_proxy_async_smem();
         tc_fence_before();
-        named_bar_sync(bar_id, kEGThreads);  // the whole A tile is written
-        const uint32_t dacc = tmem + (uint32_t)(g * WIDTH);
+        named_bar_sync(bar_id, kEGThreads);  // the whole A operand is written
+        const uint32_t dacc = tmem + (uint32_t)g * kGCols;
+        const uint32_t aT = dacc + WIDTH;  // A operand in TMEM (BF16)
         if (row == 0) {  // this group issues its own MMAs
           tc_fence_after();
           if (!*sAbort) {
             if (F8) issue_fwd_layer_e4m3(A, sbase + L.w + P.s8_off[0], dacc, P.kpad[0], P.npad[0]);
+            else if (kA0T)
+              issue_fwd_layer_ta(aT, sbase + L.w + P.sw_off[0], dacc, P.kpad[0], P.npad[0], sbase + L.ones,
+                                 P.fold > 0 ? sbase + L.w + P.sbt_off : 0u);
             else issue_fwd_layer(A, sbase + L.w + P.sw_off[0], dacc, P.kpad[0], P.npad[0], sbase + L.ones,
                                  P.fold > 0 ? sbase + L.w + P.sbt_off : 0u);
           }
           mma_commit(bar_done(g));
         }
-        const uint32_t trow = tmem + (uint32_t)(g * WIDTH) + ((uint32_t)(q * 32) << 16);
+        const uint32_t trow = dacc + ((uint32_t)(q * 32) << 16);
+        const uint32_t arow = aT + ((uint32_t)(q * 32) << 16);
         for (int l = 0; l < nl; ++l) {
           // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
           const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), (ph_done >> g) & 1u, sAbort, kWaitNs));
@@ -387,53 +403,38 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
               }
               srow = sn;
               }
-            } else if (ok && l < P.fold) {  // bias already added by the MMA
-#pragma unroll
-              for (int h32 = 0; h32 < WIDTH / 32; ++h32) {
-                uint32_t v[32];
-                tmem_ld32(trow + h32 * 32, v);
-                tmem_wait_ld();
-                const uint32_t At = A + (uint32_t)(h32 >> 1) * (kM * 128);
-#pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                  uint32_t pk[4];
-#pragma unroll
-                  for (int e = 0; e < 4; ++e)
-                    pk[e] = pack_bf16_relu(__uint_as_float(v[8 * c4 + 2 * e]), __uint_as_float(v[8 * c4 + 2 * e + 1]));
-                  st_shared_v4(At + sw128_off(row, 4 * (h32 & 1) + c4), pk[0], pk[1], pk[2], pk[3]);
-                }
-              }
             } else if (ok) {
-              // 32 columns at a time: fewer live registers, so more groups fit on the SM
+              // 32 columns at a time (fewer live registers, so more groups fit on the SM): bias
+              // (unless the MMA added it), ReLU, BF16 pairs into the A operand in TMEM
+              const bool add_bias = l >= P.fold;
 #pragma unroll
               for (int h32 = 0; h32 < WIDTH / 32; ++h32) {
                 uint32_t v[32];
                 tmem_ld32(trow + h32 * 32, v);
                 tmem_wait_ld();
-                const uint32_t At = A + (uint32_t)(h32 >> 1) * (kM * 128);
                 const float4* b4 = reinterpret_cast<const float4*>(bias + h32 * 32);
+                uint32_t pk[16];
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                  const float4 ba = b4[2 * c4], bb = b4[2 * c4 + 1];
-                  const float bv[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-                  uint32_t pk[4];
-#pragma unroll
-                  for (int e = 0; e < 4; ++e)
-                    pk[e] = pack_bf16_relu(__uint_as_float(v[8 * c4 + 2 * e]) + bv[2 * e],
-                                           __uint_as_float(v[8 * c4 + 2 * e + 1]) + bv[2 * e + 1]);
-                  st_shared_v4(At + sw128_off(row, 4 * (h32 & 1) + c4), pk[0], pk[1], pk[2], pk[3]);
+                for (int c4 = 0; c4 < 8; ++c4) {
+                  float4 bq = make_float4(0.f, 0.f, 0.f, 0.f);
+                  if (add_bias) bq = b4[c4];
+                  pk[2 * c4] = pack_bf16_relu(__uint_as_float(v[4 * c4]) + bq.x, __uint_as_float(v[4 * c4 + 1]) + bq.y);
+                  pk[2 * c4 + 1] =
+                      pack_bf16_relu(__uint_as_float(v[4 * c4 + 2]) + bq.z, __uint_as_float(v[4 * c4 + 3]) + bq.w);
                 }
+                tmem_st16(arow + (uint32_t)(h32 * 16), pk);
               }
+              tmem_wait_st();
             }
-            fence_proxy_async_smem();
+            if (F8) fence_proxy_async_smem();
             tc_fence_before();
             named_bar_sync(bar_id, kEGThreads);
             if (row == 0) {
               tc_fence_after();
               if (!*sAbort) {
                 if (F8) issue_fwd_layer_e4m3(A, sbase + L.w + P.s8_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1]);
-                else issue_fwd_layer(A, sbase + L.w + P.sw_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1],
-                                     sbase + L.ones, l + 1 < P.fold ? sbase + L.w + P.sbt_off + 32u * (l + 1) : 0u);
+                else issue_fwd_layer_ta(aT, sbase + L.w + P.sw_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1],
+                                        sbase + L.ones, l + 1 < P.fold ? sbase + L.w + P.sbt_off + 32u * (l + 1) : 0u);
               }
               mma_commit(bar_done(g));
             }
@@ -638,7 +639,8 @@ int tc_fwd_groups(int width, int F, int groups, bool e4m3) {
   // its scale, so it stays at four
   const int def = width == 64 ? (F > 0 ? 3 : (e4m3 ? 4 : 5)) : 2;
   if (groups == 0) return def;
-  if (width == 64 && F == 0) return (groups >= 2 && groups <= 6) ? groups : 0;
+  // BF16 groups also hold their A operand in TMEM (96 columns each at width 64): at most five
+  if (width == 64 && F == 0) return (groups >= 2 && groups <= (e4m3 ? 6 : 5)) ? groups : 0;
   return groups == def ? groups : 0;
 }
 
@@ -705,6 +707,9 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
   (neg == 2 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 2, F8> : neg == 3 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 3, F8> \
             : neg == 4 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 4, F8> : neg == 5 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 5, F8> \
             : tc::k_mlp_fwd_tc<W, XL, DL, 0, 6, F8>)
+#define MLPS_BY_GROUPS5(W, XL, DL) \
+  (neg == 2 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 2, false> : neg == 3 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 3, false> \
+            : neg == 4 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 4, false> : tc::k_mlp_fwd_tc<W, XL, DL, 0, 5, false>)
   if (P.w8_bytes > 0) {  // E4M3
     if (a.m.width == 64) {
       if (!feat) kern = fast64 ? MLPS_BY_GROUPS(64, 6, 4, true) : MLPS_BY_GROUPS(64, -1, -1, true);
@@ -717,8 +722,8 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
     }
   } else if (a.m.width == 64) {
     if (!feat)
-      kern = fast64 ? MLPS_BY_GROUPS(64, 6, 4, false)
-                    : (raw && neg == 4) ? tc::k_mlp_fwd_tc<64, 0, 0, 0, 4, false> : MLPS_BY_GROUPS(64, -1, -1, false);
+      kern = fast64 ? MLPS_BY_GROUPS5(64, 6, 4)
+                    : (raw && neg == 4) ? tc::k_mlp_fwd_tc<64, 0, 0, 0, 4, false> : MLPS_BY_GROUPS5(64, -1, -1);
     else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, kMaxFeat, 3, false> : tc::k_mlp_fwd_tc<64, -1, -1, kMaxFeat, 3, false>;
   } else if (a.m.width == 128) {
     if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 0, 2, false> : tc::k_mlp_fwd_tc<128, -1, -1, 0, 2, false>;
@@ -727,6 +732,7 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
     return cudaErrorNotSupported;
   }
 #undef MLPS_BY_GROUPS
+#undef MLPS_BY_GROUPS5
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<n_sm, tc::threads_tc(neg), smem, st>>>(w, a, P, tmap);

@@ -52,14 +52,12 @@ namespace {
 // Epilogue groups (chunks in flight per SM): 3 where their tiles fit in shared memory and their
 // accumulators next to the weight gradients in TMEM, else 2 (template parameter NG).
 constexpr int kGThreads = kEGThreads;               // 4 warps, one per TMEM lane quarter
-constexpr uint32_t kTmemColsB = 512;  // per group 64 (accumulator) [+ 32 (H_0 stash)], per layer 64
-                                      // of weight gradients (16 for the head layer)
+constexpr uint32_t kTmemColsB = 512;  // per group kGColsB, per layer 64 of weight gradients (16
+                                      // for the head layer)
+constexpr uint32_t kGColsB = 96;      // per group: accumulator (64) + A operand (32 columns of BF16 pairs)
 
 // TMEM columns of the weight gradients: 64 per layer, the head layer (npad <= 16) last with 16.
 MLPS_HD int dw_cols(int nl) { return (nl - 1) * 64 + 16; }
-// Whether the groups' encoded inputs H_0 also fit in TMEM (32 columns each, after the weight
-// gradients rounded up to 32 columns): then the last wgrad reloads H_0 instead of re-encoding it.
-MLPS_HD bool x_stash_fits(int nl, int ng) { return 64 * ng + (dw_cols(nl) + 31) / 32 * 32 + 32 * ng <= 512; }
 constexpr uint64_t kWaitNsB = 2000000000ull;
 constexpr uint32_t kTile = kM * 128;                // one [128 x 64] BF16 tile
 constexpr uint32_t kOnes = 2048;                    // 16 rows of the MN-major ones atom (one K step)
@@ -215,16 +213,17 @@ MLPS_DEV void build_row(const Model& m, const IntervalRec* T, int nint, int row,
 }
 
 // dgrad of phase B_l, issued by one thread of the group: G = delta_l W_l into the group's
-// accumulator, K = npad (outputs of layer l), N = kpad (its inputs). A = delta_l (K-major tile);
-// B = the forward W_l tile read as an MN-major operand (inputs contiguous, outputs = K rows).
-MLPS_DEV void issue_dgrad(uint32_t Dl, uint32_t wtile, uint32_t acc, int kpad, int npad) {
+// accumulator, K = npad (outputs of layer l), N = kpad (its inputs). A = delta_l in tensor memory
+// (`At`: lane = sample row, BF16 pairs along the columns, 8 columns per K = 16 step); B = the
+// forward W_l tile read as an MN-major operand (inputs contiguous, outputs = K rows).
+MLPS_DEV void issue_dgrad_ta(uint32_t At, uint32_t wtile, uint32_t acc, int kpad, int npad) {
   const uint32_t id = idesc_bf16(kM, kpad) | (1u << 16);
-  const uint64_t da = sw128_desc(Dl), db = sw128_desc_mn(wtile, 16);
+  const uint64_t db = sw128_desc_mn(wtile, 16);
   const int nk = npad / 16;  // npad <= 64
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
     if (kk >= nk) break;
-    mma_bf16(acc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 128), id, kk > 0 ? 1u : 0u);
+    mma_bf16_ta(acc, At + 8u * (uint32_t)kk, db + (uint64_t)(kk * 128), id, kk > 0 ? 1u : 0u);
   }
 }
 
@@ -302,9 +301,7 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
-  const uint32_t tm_dw = tmem + 64 * kNG;  // weight-gradient accumulators: 64 columns per layer
-  const bool xstash = DL >= 0 && x_stash_fits(nl, kNG);
-  const uint32_t tm_x = tm_dw + (uint32_t)((dw_cols(nl) + 31) / 32 * 32);  // H_0 stash of group 0
+  const uint32_t tm_dw = tmem + kGColsB * kNG;  // weight-gradient accumulators: 64 columns per layer
 
   const int total = w.saved_hdr[2];
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
@@ -317,6 +314,23 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
   const float invS = 1.f / (float)S;
   int loaded = -1;
   int prim = cb < ce ? simt::find_prim(w, cb) : 0;
+
+  // the next completion of the group's MMAs (warp-uniform: tcgen05.ld is a warp instruction)
+  auto wait_mma = [&]() -> bool {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), ph, sAbort, kWaitNsB));
+    ph ^= 1u;
+    tc_fence_after();
+    return ok;
+  };
+  auto wait_wgrad = [&]() -> bool {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_wg(g), ph_g, sAbort, kWaitNsB));
+    ph_g ^= 1u;
+    tc_fence_after();
+    return ok;
+  };
+  // wgrad_0 of the group's last chunk may still read T_0 and T_1: waited for before the next
+  // write of either tile, before a flush of the weight gradients, and at teardown
+  bool wg_pending = false;
 
   // flush of the block's accumulated gradients of primitive p (all threads call it)
   auto flush = [&](int p) {
@@ -374,6 +388,10 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
     const int my_cc = step_chunk(cur, g);  // this group's chunk this step and the next
     const int my_nx = step_chunk(nxt, g);
     if (prim != loaded) {
+      if (wg_pending) {  // the flush reads the accumulators that wgrad_0 adds to
+        (void)wait_wgrad();
+        wg_pending = false;
+      }
       if (geo_acc != 0.f) atomicAdd(&sGeo[lane], geo_acc);  // nonzero only on lanes < 12
       geo_acc = 0.f;
       tc_fence_before();
@@ -434,41 +452,34 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
 #define tileaddr(I) (tiles + (uint32_t)(I) * kTile)
     const int iv = row / S, k = row - iv * S;
     const bool valid = iv < nint;
-    const uint32_t acc = tmem + (uint32_t)(g * 64);  // this group's dgrad / forward accumulator
+    const uint32_t acc = tmem + (uint32_t)g * kGColsB;  // this group's dgrad / forward accumulator
     const uint32_t trow = acc + ((uint32_t)(q * 32) << 16);
 
-    if (DL >= 0) {
+    const uint32_t aT = acc + 64u;  // A operand in TMEM: 32 columns of BF16 pairs
+    const uint32_t arow = aT + ((uint32_t)(q * 32) << 16);
+    if (DL >= 0) {  // encoded input straight into the A operand in TMEM
       uint32_t pk[32];
       encode_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, pk);
-      store_row64(tileaddr(0), row, pk);
-      if (xstash) {  // keep H_0 for the last wgrad
-        tmem_st32(tm_x + (uint32_t)(32 * g) + ((uint32_t)(q * 32) << 16), pk);
-        tmem_wait_st();
+      tmem_st32(arow, pk);
+      tmem_wait_st();
+    } else {  // generic encodings: through the shared-memory tile T_0 (free once wgrad_0 is done)
+      if (wg_pending) {
+        (void)wait_wgrad();
+        wg_pending = false;
       }
-    } else {
       build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+      fence_proxy_async_smem();
     }
-    fence_proxy_async_smem();
     tc_fence_before();
     named_bar_sync(gbar, kGThreads);
     if (issuer) {
       tc_fence_after();
-      if (!*sAbort) issue_fwd_layer(tileaddr(0), sbase + L.w + P.sw_off[0], acc, P.kpad[0], P.npad[0]);
+      if (!*sAbort) {
+        if (DL >= 0) issue_fwd_layer_ta(aT, sbase + L.w + P.sw_off[0], acc, P.kpad[0], P.npad[0]);
+        else issue_fwd_layer(tileaddr(0), sbase + L.w + P.sw_off[0], acc, P.kpad[0], P.npad[0]);
+      }
       mma_commit(bar_done(g));
     }
-    // the next completion of the group's MMAs (warp-uniform: tcgen05.ld is a warp instruction)
-    auto wait_mma = [&]() -> bool {
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), ph, sAbort, kWaitNsB));
-      ph ^= 1u;
-      tc_fence_after();
-      return ok;
-    };
-    auto wait_wgrad = [&]() -> bool {
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_wg(g), ph_g, sAbort, kWaitNsB));
-      ph_g ^= 1u;
-      tc_fence_after();
-      return ok;
-    };
 
     // ---------------- forward recompute
     for (int l = 0; l < nl; ++l) {
@@ -497,15 +508,28 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
 #pragma unroll
           for (int e = 0; e < 32; ++e) pk[e] = 0u;
         }
-        store_row64(tileaddr(l + 1), row, pk);
-        fence_proxy_async_smem();
+        tmem_st32(arow, pk);  // H_{l+1}: A operand of the next layer
+        tmem_wait_st();
         tc_fence_before();
         named_bar_sync(gbar, kGThreads);
         if (issuer) {
           tc_fence_after();
           if (!*sAbort)
-            issue_fwd_layer(tileaddr(l + 1), sbase + L.w + P.sw_off[l + 1], acc, P.kpad[l + 1], P.npad[l + 1]);
+            issue_fwd_layer_ta(aT, sbase + L.w + P.sw_off[l + 1], acc, P.kpad[l + 1], P.npad[l + 1]);
           mma_commit(bar_done(g));
+        }
+        if (wg_pending) {  // the previous chunk's wgrad_0 reads T_0 and T_1
+          (void)wait_wgrad();
+          wg_pending = false;
+        }
+        // H_{l+1} also goes to T_{l+1}: the ReLU mask of B_{l+1} and the A operand of wgrad_{l+1}
+        // (made visible to the tensor core by the proxy fence before the head's barrier). It is
+        // read back from TMEM (the MMA only reads it too), so pk need not live across the issue.
+        {
+          uint32_t hv[32];
+          tmem_ld32(arow, hv);
+          tmem_wait_ld();
+          store_row64(tileaddr(l + 1), row, hv);
         }
       } else {
         // ---------------- heads and reverse of the interval composite -> dL/dZ into T_0
@@ -559,20 +583,24 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
         float dd[1] = {valid ? sig * dLda : 0.f};
         seg_scan<1>(dd, 1, row, S, sScan + g * 4 * kScanNV, gbar);
         if (valid && k == S - 1) DD[iv] = dd[0];
-        uint32_t pk[32];
+        uint32_t pk[16];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) pk[e] = 0u;
+        for (int e = 0; e < 16; ++e) pk[e] = 0u;
 #pragma unroll
         for (int e = 0; e < (4 + NF) / 2; ++e)
           pk[e] = pack_bf16(2 * e < m.nout ? dz[2 * e] : 0.f, 2 * e + 1 < m.nout ? dz[2 * e + 1] : 0.f);
-        store_row64(tileaddr(0), row, pk);  // X is dead (F_0 done); it is rebuilt for the last wgrad
-        fence_proxy_async_smem();
+        // delta_{nl-1} (16 columns): A operand of dgrad_{nl-1} in TMEM, and B operand of
+        // wgrad_{nl-1} in T_0 (X is dead there: F_0 is done; it is rebuilt for wgrad_0)
+        tmem_st16(arow, pk);
+        st_shared_v4(tileaddr(0) + sw128_off(row, 0), pk[0], pk[1], pk[2], pk[3]);
+        st_shared_v4(tileaddr(0) + sw128_off(row, 1), pk[4], pk[5], pk[6], pk[7]);
+        tmem_wait_st();
+        fence_proxy_async_smem();  // also covers the H tiles written during the recompute
         tc_fence_before();
         named_bar_sync(gbar, kGThreads);
         if (issuer) {  // B_{nl-1}: dgrad, then wgrad, each with its own completion
           tc_fence_after();
-          if (!*sAbort)
-            issue_dgrad(tileaddr(0), sbase + L.w + P.sw_off[nl - 1], acc, P.kpad[nl - 1], P.npad[nl - 1]);
+          if (!*sAbort) issue_dgrad_ta(aT, sbase + L.w + P.sw_off[nl - 1], acc, P.kpad[nl - 1], P.npad[nl - 1]);
           mma_commit(bar_done(g));
           if (!*sAbort)
             issue_wgrad(tileaddr(nl - 1), tileaddr(0), tm_dw + (uint32_t)((nl - 1) * 64), sbase + L.ones, P.npad[nl - 1]);
@@ -580,63 +608,81 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
         }
       }
     }
-    // ---------------- backward phases B_{nl-1} .. B_0 (delta_l in T_{l+1}; dL/dZ in T_0)
+    // ---------------- backward phases B_{nl-1} .. B_0
+    // On entry to B_l: dgrad_l is issued with A = delta_l in TMEM. For l = nl-1, delta_l's copy in
+    // T_0 and wgrad_l are issued too; for l < nl-1, wgrad_{l+1} is issued (after dgrad_l) and
+    // delta_l still has to be copied to T_{l+1} (the B operand of wgrad_l) once wgrad_{l+1},
+    // which reads that tile, is done. B_l issues dgrad_{l-1} first and wgrad_l after it, so the
+    // dgrad chain never waits for a wgrad.
     for (int l = nl - 1; l >= 0; --l) {
       bool ok = wait_mma();  // dgrad of B_l
-      uint32_t v0[32], v1[32];
-      if (ok) {
-        tmem_ld32(trow, v0);
-        tmem_ld32(trow + 32, v1);
-        tmem_wait_ld();
-      } else {
-#pragma unroll
-        for (int e = 0; e < 32; ++e) { v0[e] = 0u; v1[e] = 0u; }
-      }
-      tc_fence_before();
       if (l > 0) {
-        // delta_{l-1} = G * [H_l > 0], written over H_l in T_l once the wgrad of B_l has read it
+        // delta_{l-1} = G * [H_l > 0] (H_l from T_l; wgrad_l, which reads it, is issued below),
+        // 32 columns of G at a time
         const uint32_t Tl = tileaddr(l);
-        const uint32_t vmask = valid ? 0xFFFFFFFFu : 0u;
+        const uint32_t vmask = (valid && ok) ? 0xFFFFFFFFu : 0u;
         uint32_t pk[32];
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
-          uint32_t hq[4];
-          ld_shared_v4(Tl + sw128_off(row, ch), hq[0], hq[1], hq[2], hq[3]);
+        for (int hf = 0; hf < 2; ++hf) {
+          uint32_t v[32];
+          tmem_ld32(trow + 32u * hf, v);
+          tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int c0 = ch * 8 + 2 * e;
-            const float g0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]);
-            const float g1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]);
-            // H_l was written by the ReLU pack, so each BF16 half is +0 or positive: H > 0 iff its
-            // 16 bits are nonzero, and __vcmpne2 gives both halves' masks at once
-            pk[ch * 4 + e] = pack_bf16(g0, g1) & __vcmpne2(hq[e], 0u) & vmask;
+          for (int ch = 0; ch < 4; ++ch) {
+            uint32_t hq[4];
+            ld_shared_v4(Tl + sw128_off(row, 4 * hf + ch), hq[0], hq[1], hq[2], hq[3]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int c0 = ch * 8 + 2 * e;
+              // H_l was written by the ReLU pack, so each BF16 half is +0 or positive: H > 0 iff
+              // its 16 bits are nonzero, and __vcmpne2 gives both halves' masks at once
+              pk[(4 * hf + ch) * 4 + e] =
+                  pack_bf16(__uint_as_float(v[c0]), __uint_as_float(v[c0 + 1])) & __vcmpne2(hq[e], 0u) & vmask;
+            }
           }
         }
-        ok = wait_wgrad() && ok;  // wgrad of B_l: T_l is free
-        store_row64(Tl, row, pk);
-        if (l == 1) {  // dL/dZ in T_0 was consumed by B_{nl-1}: restore H_0 there for the last wgrad
-          if (xstash) {
-            uint32_t xv[32];
-            tmem_ld32(tm_x + (uint32_t)(32 * g) + ((uint32_t)(q * 32) << 16), xv);
+        tc_fence_before();
+        const bool copy_dl = l < nl - 1;  // delta_l still to be copied to T_{l+1}
+        if (copy_dl) {
+          ok = wait_wgrad() && ok;  // wgrad_{l+1} is done with T_{l+1}
+          // delta_l from TMEM to T_{l+1}, 16 columns at a time, before delta_{l-1} replaces it
+#pragma unroll
+          for (int hf = 0; hf < 2; ++hf) {
+            uint32_t dl[16];
+            tmem_ld16(arow + 16u * hf, dl);
             tmem_wait_ld();
-            store_row64(tileaddr(0), row, xv);
-          } else if (DL >= 0) {
-            build_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
-          } else {
-            build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch)
+              st_shared_v4(tileaddr(l + 1) + sw128_off(row, 4 * hf + ch), dl[4 * ch], dl[4 * ch + 1], dl[4 * ch + 2],
+                           dl[4 * ch + 3]);
           }
         }
+        tmem_st32(arow, pk);  // delta_{l-1}: A operand of dgrad_{l-1}
+        tmem_wait_st();
         fence_proxy_async_smem();
         tc_fence_before();
         named_bar_sync(gbar, kGThreads);
         if (issuer) {
           tc_fence_after();
-          if (!*sAbort) issue_dgrad(Tl, sbase + L.w + P.sw_off[l - 1], acc, P.kpad[l - 1], P.npad[l - 1]);
+          if (!*sAbort) issue_dgrad_ta(aT, sbase + L.w + P.sw_off[l - 1], acc, P.kpad[l - 1], P.npad[l - 1]);
           mma_commit(bar_done(g));
-          if (!*sAbort) issue_wgrad(tileaddr(l - 1), Tl, tm_dw + (uint32_t)((l - 1) * 64), sbase + L.ones, P.npad[l - 1]);
-          mma_commit(bar_wg(g));
+          if (copy_dl) {
+            if (!*sAbort)
+              issue_wgrad(Tl, tileaddr(l + 1), tm_dw + (uint32_t)(l * 64), sbase + L.ones, P.npad[l]);
+            mma_commit(bar_wg(g));
+          }
         }
       } else {
+        uint32_t v0[32], v1[32];
+        if (ok) {
+          tmem_ld32(trow, v0);
+          tmem_ld32(trow + 32, v1);
+          tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; ++e) { v0[e] = 0u; v1[e] = 0u; }
+        }
+        tc_fence_before();
         // ---------------- encoding derivative and pose chain
         // With x_k = p + t_k dp and t_k = tm + c_k (r1 - r0), c_k = (k + 1/2) / S - 1/2, every
         // per-interval sum the chain needs follows from A = sum_k gx_k and B = sum_k c_k gx_k.
@@ -706,7 +752,24 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
             }
           }
         }
-        (void)wait_wgrad();  // wgrad of B_0: T_0 and T_1 are free for the next chunk
+        // wgrad_0: X rebuilt in T_0 (its last reader, wgrad_{nl-1}, is done) and delta_0 copied
+        // to T_1 once wgrad_1 is done; waited for only when the next chunk writes these tiles
+        uint32_t dl[32];
+        tmem_ld32(arow, dl);
+        tmem_wait_ld();
+        tc_fence_before();
+        (void)wait_wgrad();  // wgrad_1
+        store_row64(tileaddr(1), row, dl);
+        if (DL >= 0) build_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
+        else build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+        fence_proxy_async_smem();
+        named_bar_sync(gbar, kGThreads);
+        if (issuer) {
+          tc_fence_after();
+          if (!*sAbort) issue_wgrad(tileaddr(0), tileaddr(1), tm_dw, sbase + L.ones, P.npad[0]);
+          mma_commit(bar_wg(g));
+        }
+        wg_pending = true;
       }
     }
 #undef tileaddr
@@ -742,14 +805,14 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
 static int bwd_groups(const Model& m, const TcPlan& P) {
   const int ipc = m.S <= 128 ? 128 / m.S : 1;
   for (int ng = 3; ng >= 2; --ng) {
-    if (64 * ng + tc::dw_cols(m.nl) > (int)tc::kTmemColsB) continue;  // TMEM: groups + weight gradients
+    if ((int)tc::kGColsB * ng + tc::dw_cols(m.nl) > (int)tc::kTmemColsB) continue;  // TMEM: groups + weight gradients
     if (tc::bwd_layout(P, m.F, ipc, ng).total + 1024 <= 227 * 1024) return ng;
   }
   return 0;
 }
 
 bool tc_bwd_supported(const Model& m, const TcPlan& P) {
-  if (m.width != 64) return false;
+  if (m.width != 64 || m.nl < 2) return false;
   if (m.xyzL != 0 && m.xyzL != 6) return false;
   if (P.kpad[0] != 64) return false;
   if (m.F > 12) return false;

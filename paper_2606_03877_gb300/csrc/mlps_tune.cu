@@ -1,6 +1,6 @@
 // mlps_tune.cu -- autotuner of the batched render: picks the screen-tile edge of the binning and
 // intersection stages (16 or 8 pixels) and the samples per CTA of the forward tensor-core MLP
-// (2 to 6 chunks of 128 sample rows in flight) by timing every candidate on the caller's own
+// (2 to 5 chunks of 128 sample rows in flight, 6 with E4M3) by timing every candidate on the caller's own
 // batch with CUDA events. Decisions are cached per batch shape (MLP shape, precision, samples,
 // and every item's primitive count and resolution) for the life of the process.
 //
@@ -113,7 +113,8 @@ extern "C" mlps_status mlps_autotune_batch(
                scratch, scratch_bytes, d_weights, d_centers, d_scales, d_quats, stream};
   const bool tc = cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3;
   std::vector<int> groups = {0};
-  if (tc && cfg->hidden_width == 64 && cfg->feat_dim == 0) groups = {6, 5, 4, 3, 2};
+  if (tc && cfg->hidden_width == 64 && cfg->feat_dim == 0)
+    groups = cfg->precision == MLPS_FP8_E4M3 ? std::vector<int>{6, 5, 4, 3, 2} : std::vector<int>{5, 4, 3, 2};
   float best = -1.f;
   int best_tile = cfg->tile, best_groups = cfg->mlp_groups, nc = 0;
   // with the tile-centre order the tile edge is part of the result, not a schedule: keep it

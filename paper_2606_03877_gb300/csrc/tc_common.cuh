@@ -147,6 +147,23 @@ MLPS_DEV void issue_fwd_layer(uint32_t A, uint32_t W, uint32_t d, int kpad, int 
   if (bt) mma_bf16(d, sw128_desc(ones), sw128_desc(bt), idesc, 1u);
 }
 
+// Forward layer with the A operand in tensor memory (`At`: lane = sample row, BF16 pairs along
+// the columns, 8 columns per K = 16 step); W and the folded bias as in issue_fwd_layer.
+MLPS_DEV void issue_fwd_layer_ta(uint32_t At, uint32_t W, uint32_t d, int kpad, int npad, uint32_t ones = 0u,
+                                 uint32_t bt = 0u) {
+  const uint32_t idesc = idesc_bf16(kM, npad);
+  const uint64_t db = sw128_desc(W);
+  const uint32_t wslab = (uint32_t)npad * 8;
+  const int nk = kpad / 16;
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    if (kk >= nk) break;
+    const uint32_t ob = (uint32_t)(kk >> 2) * wslab + (uint32_t)(kk & 3) * 2;
+    mma_bf16_ta(d, At + 8u * (uint32_t)kk, db + ob, idesc, kk > 0 ? 1u : 0u);
+  }
+  if (bt) mma_bf16(d, sw128_desc(ones), sw128_desc(bt), idesc, 1u);
+}
+
 // FP8 (E4M3) forward layer: same operand tiles (128-byte K-major swizzled rows, here holding up
 // to 128 one-byte elements), K = 32 per instruction; kpad <= 128.
 MLPS_DEV void issue_fwd_layer_e4m3(uint32_t A, uint32_t W, uint32_t d, int kpad, int npad) {

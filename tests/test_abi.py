@@ -147,8 +147,11 @@ def test_contact_mode_validation(lib):
 def test_mlp_groups_validation(lib):
     base = synth.CONFIGS["prec"]
     for g, want in ((1, _lib.MLPS_ERR_INVALID_ARGUMENT), (7, _lib.MLPS_ERR_INVALID_ARGUMENT),
-                    (2, _lib.MLPS_OK), (3, _lib.MLPS_OK), (4, _lib.MLPS_OK), (5, _lib.MLPS_OK), (6, _lib.MLPS_OK)):
+                    (2, _lib.MLPS_OK), (3, _lib.MLPS_OK), (4, _lib.MLPS_OK), (5, _lib.MLPS_OK),
+                    (6, _lib.MLPS_ERR_UNSUPPORTED)):  # BF16 groups also keep their A operand in TMEM
         assert _lib.mlps_check_config(make_config(base, "bf16", mlp_groups=g)) == want, g
+    for g in (2, 6):  # E4M3 keeps its operands in shared memory: up to six groups
+        assert _lib.mlps_check_config(make_config(base, "fp8", mlp_groups=g)) == _lib.MLPS_OK, g
     # wider models and feature heads run with their default only
     assert _lib.mlps_check_config(make_config(synth.CONFIGS["stress"], "bf16", mlp_groups=3)) == \
         _lib.MLPS_ERR_UNSUPPORTED

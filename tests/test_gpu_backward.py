@@ -145,9 +145,11 @@ def test_full_size_prec_sampled_gradients_fp32():
 def test_full_size_prec_sampled_gradients_bf16():
     """BF16 at the bench's full-size launch, every parameter group at the 2e-2 bar. The BF16
     error of the pose groups comes from ReLU mask flips (pre-activations within BF16 rounding of
-    zero), which average out over the pixels a primitive covers: 48 000 sampled pixels (~190 per
-    primitive) keep them under the bar, where 6000 pixels (~23 per primitive) gave 2.6-3.9 %."""
-    errs = _full_size_sampled("bf16", 48000)
+    zero), which average out over the pixels a primitive covers. Measured on GB300: 6000 sampled
+    pixels (~23 per primitive) gave 2.6-3.9 %; 48 000 gave 1.1 % (centres, scales) and 2.3 %
+    (quaternions, whose gradient is the small tangential part of the rotation gradient);
+    160 000 (~600 per primitive) are used here."""
+    errs = _full_size_sampled("bf16", 160000)
     for k, e in errs.items():
         assert e < 2e-2, (k, errs)
 
