@@ -62,7 +62,7 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG, bool e4m3, int ipc) {
   L.a_stride = align_up(P.a_bytes, 1024);
   off += L.a_stride * kNEG;
   L.bias = off;  // biases, then (E4M3) the per-output weight scales
-  off = align_up(off + 4 * P.bias_floats * (e4m3 ? 2 : 1), 16);
+  off = align_up(off + 4 * P.bias_floats * (e4m3 ? 3 : 1), 16);
   L.itab0 = off;
   // two buffers of ipc interval records: the current chunk's and the next chunk's (in flight)
   L.itab_stride = align_up(2 * (uint32_t)sizeof(IntervalRec) * ipc, 16);
@@ -77,20 +77,23 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG, bool e4m3, int ipc) {
   return L;
 }
 
-// F8: E4M3 operands (kind::f8f6f4). Activation rows are stored divided by a per-row power-of-two
-// scale (the encoded input by 1/256, each hidden row by the smallest 2^e that keeps its largest
-// value <= 448); weights by a per-output scale from the packing. The epilogue multiplies the
-// FP32 accumulator back by (row scale x weight scale) before the bias.
+// F8: E4M3 operands (kind::f8f6f4). Layer l's A operand holds its input divided by a static
+// power-of-two scale per (primitive, layer) (the encoded input by 1/256), the weights are
+// stored divided by a per-output scale; the packing folds both, and the next layer's scale, into
+// one multiplier and offset per output, so the epilogue is one FMA per value (k_pack_e4m3).
 template <int WIDTH, int XL, int DL, int NF, int kNEG, bool F8>
 __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     k_mlp_fwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
   constexpr int kThreadsTC = kEGThreads * kNEG;
-  // BF16: each group's TMEM holds its FP32 accumulator (WIDTH columns) and the next layer's
-  // A operand (WIDTH / 2 columns of BF16 pairs); E4M3 keeps its A tiles in shared memory.
-  constexpr bool kTA = !F8;
-  constexpr uint32_t kGCols = kTA ? (uint32_t)(WIDTH + WIDTH / 2) : (uint32_t)WIDTH;
+  // Each group's TMEM holds its FP32 accumulator (WIDTH columns) and the next layer's A operand:
+  // WIDTH / 2 columns of BF16 pairs, or WIDTH / 4 columns of E4M3 quadruples.
+  constexpr bool kTA = true;
+  constexpr uint32_t kGCols = (uint32_t)(WIDTH + (F8 ? WIDTH / 4 : WIDTH / 2));
   // the encoded input goes to TMEM too when it is built in registers (compile-time shapes)
   constexpr bool kA0T = kTA && XL >= 0;
+  // BF16 at width 64: every hidden layer's bias is added by one more MMA step (the plan folds
+  // all of them); width 128 adds them in the epilogue
+  constexpr bool kFold = WIDTH == 64 && !F8;
   static_assert(kNEG >= 1 && kNEG <= 6 && kNEG * kGCols <= 512, "TMEM holds 512 columns");
   static_assert(4 + NF <= kMaxScanVals, "scan scratch holds kMaxScanVals values per warp");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -182,15 +185,17 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
           }
         }
         if (!F8 && P.fold > 0)
-          for (int j = 0; j < 4; ++j)
-            tma_load_2d(sbase + L.w + P.sbt_off + j * 2048, &tmap, 0, row0 + P.gbt_row + j * 16, bar_w);
+          for (int sl = 0; sl < (P.fold + 3) / 4; ++sl)
+            for (int j = 0; j < 4; ++j)
+              tma_load_2d(sbase + L.w + P.sbt_off + sl * 8192 + j * 2048, &tmap, 0, row0 + P.gbt_row + sl * 64 + j * 16,
+                          bar_w);
       }
       const unsigned char* blob = a.weights + (size_t)prim * a.pk.stride;
       const float* gb = reinterpret_cast<const float*>(blob + P.gbias_byte);
       for (int i = threadIdx.x; i < P.bias_floats; i += kThreadsTC) sBias[i] = gb[i];
-      if (F8) {
-        const float* gs = reinterpret_cast<const float*>(blob + P.gscale_byte);
-        for (int i = threadIdx.x; i < P.bias_floats; i += kThreadsTC) sBias[P.bias_floats + i] = gs[i];
+      if (F8) {  // the epilogue's multipliers and offsets
+        const float* gm = reinterpret_cast<const float*>(blob + P.gmul_byte);
+        for (int i = threadIdx.x; i < 2 * P.bias_floats; i += kThreadsTC) sBias[P.bias_floats + i] = gm[i];
       }
       mbar_wait(bar_w, ph_w, sAbort, kWaitNs);
       ph_w ^= 1;
@@ -214,7 +219,6 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
         const uint32_t A = sbase + L.a0 + (uint32_t)g * L.a_stride;
         const int iv = row / S, k = row - iv * S;
         const bool valid = iv < nint;
-        float srow = 1.f / kInMul;  // E4M3: scale of this row of the current A tile
         if (F8 && XL >= 0) {
           uint32_t pk[16];
           if (valid) {
@@ -227,22 +231,21 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
 #pragma unroll
             for (int e = 0; e < 16; ++e) pk[e] = 0u;
           }
-#pragma unroll
-          for (int ch = 0; ch < 4; ++ch)
-            st_shared_v4(A + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+          tmem_st16(tmem + (uint32_t)g * kGCols + WIDTH + ((uint32_t)(q * 32) << 16), pk);
+          tmem_wait_st();
         } else if (F8) {
           RowWriter8 rw{A, row, 0, 0.f, kInMul};
-          if (valid && m.contact) {
+          if (valid && m.contact) {  // the tensor-core blob's order: gamma(delta), then gamma(d)
             const IntervalRec& I = T[iv];
             float del[3];
             contact_delta(w.geo[prim], I, del);
-            if (m.dirL > 0)
-              for (int u = 0; u < 3; ++u) put_gamma8(rw, I.d[u], m.dirL);
             if (m.xyzL == 0) {
               for (int u = 0; u < 3; ++u) rw.put(del[u]);
             } else {
               for (int u = 0; u < 3; ++u) put_gamma8(rw, del[u], m.xyzL);
             }
+            if (m.dirL > 0)
+              for (int u = 0; u < 3; ++u) put_gamma8(rw, I.d[u], m.dirL);
           } else if (valid) {
             const IntervalRec& I = T[iv];
             const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
@@ -281,17 +284,18 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
         } else {
           RowWriter rw{A, row, 0, 0.f};
           if (valid && m.contact) {
-            // contact-point input gamma([d; delta]) (Eq. 4), one sample per hit
+            // contact-point input gamma([d; delta]) (Eq. 4), one sample per hit, in the tensor-core
+            // blob's column order: gamma(delta) first (tc_in_col)
             const IntervalRec& I = T[iv];
             float del[3];
             contact_delta(w.geo[prim], I, del);
-            if (m.dirL > 0)
-              for (int u = 0; u < 3; ++u) put_gamma(rw, I.d[u], m.dirL);
             if (m.xyzL == 0) {
               for (int u = 0; u < 3; ++u) rw.put(del[u]);
             } else {
               for (int u = 0; u < 3; ++u) put_gamma(rw, del[u], m.xyzL);
             }
+            if (m.dirL > 0)
+              for (int u = 0; u < 3; ++u) put_gamma(rw, I.d[u], m.dirL);
           } else if (valid) {
             const IntervalRec& I = T[iv];
             const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
@@ -315,7 +319,8 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
         if (row == 0) {  // this group issues its own MMAs
           tc_fence_after();
           if (!*sAbort) {
-            if (F8) issue_fwd_layer_e4m3(A, sbase + L.w + P.s8_off[0], dacc, P.kpad[0], P.npad[0]);
+            if (F8 && kA0T) issue_fwd_layer_e4m3_ta(aT, sbase + L.w + P.s8_off[0], dacc, P.kpad[0], P.npad[0]);
+            else if (F8) issue_fwd_layer_e4m3(A, sbase + L.w + P.s8_off[0], dacc, P.kpad[0], P.npad[0]);
             else if (kA0T)
               issue_fwd_layer_ta(aT, sbase + L.w + P.sw_off[0], dacc, P.kpad[0], P.npad[0], sbase + L.ones,
                                  P.fold > 0 ? sbase + L.w + P.sbt_off : 0u);
@@ -334,79 +339,46 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
           const float* bias = sBias + P.bias_off[l];
           if (l < nl - 1) {
             if (ok && F8) {
-              // pass 1: H = ReLU(acc * srow * c_n + b_n) and its row maximum; pass 2: store H / 2^e
-              const float* wsc = sBias + P.bias_floats + P.bias_off[l];
-              float amax = 0.f;
-              if (WIDTH == 64) {  // one pass: the row's 64 values stay in registers
-                uint32_t v0[32], v1[32];
-                tmem_ld32(trow, v0);
-                tmem_ld32(trow + 32, v1);
+              // E4M3: z / s_{l+1} = acc * mul_n + add_n (weight and activation scales folded in
+              // by the packing), ReLU and saturation in the conversion; 32 columns (32 bytes of
+              // the row) at a time
+              const float* mulv = sBias + P.bias_floats + P.bias_off[l];
+              const float* addv = sBias + 2 * P.bias_floats + P.bias_off[l];
+#pragma unroll
+              for (int h32 = 0; h32 < WIDTH / 32; ++h32) {
+                uint32_t v[32];
+                tmem_ld32(trow + h32 * 32, v);
                 tmem_wait_ld();
+                const float4* m4 = reinterpret_cast<const float4*>(mulv + h32 * 32);
+                const float4* a4 = reinterpret_cast<const float4*>(addv + h32 * 32);
+                uint32_t pk[8];
 #pragma unroll
-                for (int c = 0; c < 64; ++c) {
-                  const float h = fmaxf(fmaf(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * srow, wsc[c], bias[c]), 0.f);
-                  amax = fmaxf(amax, h);
-                  if (c < 32) v0[c] = __float_as_uint(h);
-                  else v1[c - 32] = __float_as_uint(h);
+                for (int e = 0; e < 8; ++e) {
+                  const float4 mq = m4[e], aq = a4[e];
+                  const float y0 = fmaf(__uint_as_float(v[4 * e]), mq.x, aq.x);
+                  const float y1 = fmaf(__uint_as_float(v[4 * e + 1]), mq.y, aq.y);
+                  const float y2 = fmaf(__uint_as_float(v[4 * e + 2]), mq.z, aq.z);
+                  const float y3 = fmaf(__uint_as_float(v[4 * e + 3]), mq.w, aq.w);
+                  pk[e] = pack_e4m3_relu(y0, y1) | (pack_e4m3_relu(y2, y3) << 16);
                 }
-                const float sn = e4m3_row_scale(amax), inv = __frcp_rn(sn);
-                uint32_t pk[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                  float h[4];
-#pragma unroll
-                  for (int j = 0; j < 4; ++j) {
-                    const int c = 4 * e + j;
-                    h[j] = __uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * inv;
-                  }
-                  pk[e] = pack_e4m3(h[0], h[1]) | (pack_e4m3(h[2], h[3]) << 16);
-                }
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch)
-                  st_shared_v4(A + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
-                srow = sn;
-              } else {
-#pragma unroll
-              for (int half = 0; half < WIDTH / 64; ++half) {
-                uint32_t v0[32], v1[32];
-                tmem_ld32(trow + half * 64, v0);
-                tmem_ld32(trow + half * 64 + 32, v1);
-                tmem_wait_ld();
-#pragma unroll
-                for (int c = 0; c < 64; ++c) {
-                  const int n = half * 64 + c;
-                  amax = fmaxf(amax, fmaf(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * srow, wsc[n], bias[n]));
-                }
+                tmem_st8(arow + (uint32_t)(h32 * 8), pk);
               }
-              const float sn = e4m3_row_scale(amax), inv = __frcp_rn(sn);
+              tmem_wait_st();
+            } else if (ok && kFold) {
+              // bias added by the MMA: ReLU and BF16 pairs into the A operand in TMEM, 32 columns
+              // at a time (fewer live registers, so more groups fit on the SM)
 #pragma unroll
-              for (int half = 0; half < WIDTH / 64; ++half) {
-                uint32_t v0[32], v1[32];
-                tmem_ld32(trow + half * 64, v0);
-                tmem_ld32(trow + half * 64 + 32, v1);
+              for (int h32 = 0; h32 < WIDTH / 32; ++h32) {
+                uint32_t v[32];
+                tmem_ld32(trow + h32 * 32, v);
                 tmem_wait_ld();
                 uint32_t pk[16];
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                  float h[4];
-#pragma unroll
-                  for (int j = 0; j < 4; ++j) {
-                    const int n = half * 64 + 4 * e + j;
-                    const int c = 4 * e + j;
-                    h[j] = fmaxf(fmaf(__uint_as_float(c < 32 ? v0[c] : v1[c - 32]) * srow, wsc[n], bias[n]), 0.f) * inv;
-                  }
-                  pk[e] = pack_e4m3(h[0], h[1]) | (pack_e4m3(h[2], h[3]) << 16);
-                }
-#pragma unroll
-                for (int ch = 0; ch < 4; ++ch)
-                  st_shared_v4(A + sw128_off(row, 4 * half + ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+                for (int e = 0; e < 16; ++e) pk[e] = pack_bf16_relu(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
+                tmem_st16(arow + (uint32_t)(h32 * 16), pk);
               }
-              srow = sn;
-              }
-            } else if (ok) {
-              // 32 columns at a time (fewer live registers, so more groups fit on the SM): bias
-              // (unless the MMA added it), ReLU, BF16 pairs into the A operand in TMEM
-              const bool add_bias = l >= P.fold;
+              tmem_wait_st();
+            } else if (ok && !kFold && !F8) {
 #pragma unroll
               for (int h32 = 0; h32 < WIDTH / 32; ++h32) {
                 uint32_t v[32];
@@ -416,25 +388,28 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
                 uint32_t pk[16];
 #pragma unroll
                 for (int c4 = 0; c4 < 8; ++c4) {
-                  float4 bq = make_float4(0.f, 0.f, 0.f, 0.f);
-                  if (add_bias) bq = b4[c4];
-                  pk[2 * c4] = pack_bf16_relu(__uint_as_float(v[4 * c4]) + bq.x, __uint_as_float(v[4 * c4 + 1]) + bq.y);
-                  pk[2 * c4 + 1] =
-                      pack_bf16_relu(__uint_as_float(v[4 * c4 + 2]) + bq.z, __uint_as_float(v[4 * c4 + 3]) + bq.w);
+                  const float4 bq = b4[c4];
+                  float x0 = __uint_as_float(v[4 * c4]), x1 = __uint_as_float(v[4 * c4 + 1]);
+                  float x2 = __uint_as_float(v[4 * c4 + 2]), x3 = __uint_as_float(v[4 * c4 + 3]);
+                  add2_f32(x0, x1, bq.x, bq.y);
+                  add2_f32(x2, x3, bq.z, bq.w);
+                  pk[2 * c4] = pack_bf16_relu(x0, x1);
+                  pk[2 * c4 + 1] = pack_bf16_relu(x2, x3);
                 }
                 tmem_st16(arow + (uint32_t)(h32 * 16), pk);
               }
               tmem_wait_st();
             }
-            if (F8) fence_proxy_async_smem();
             tc_fence_before();
             named_bar_sync(bar_id, kEGThreads);
             if (row == 0) {
               tc_fence_after();
               if (!*sAbort) {
-                if (F8) issue_fwd_layer_e4m3(A, sbase + L.w + P.s8_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1]);
+                if (F8) issue_fwd_layer_e4m3_ta(aT, sbase + L.w + P.s8_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1]);
                 else issue_fwd_layer_ta(aT, sbase + L.w + P.sw_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1],
-                                        sbase + L.ones, l + 1 < P.fold ? sbase + L.w + P.sbt_off + 32u * (l + 1) : 0u);
+                                        sbase + L.ones,
+                                        l + 1 < P.fold ? sbase + L.w + P.sbt_off + 8192u * ((l + 1) >> 2) + 32u * ((l + 1) & 3)
+                                                       : 0u);
               }
               mma_commit(bar_done(g));
             }
@@ -458,7 +433,10 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
                 uint32_t bits;
                 if (P.npad[l] >= 32) bits = j < 32 ? r32[j] : r16[(j - 32) & 15];
                 else bits = j < 16 ? r16[j] : 0u;
-                if (F8) z[j] = (j < m.nout) ? fmaf(__uint_as_float(bits) * srow, sBias[P.bias_floats + P.bias_off[l] + j], bias[j]) : 0.f;
+                if (F8)
+                  z[j] = (j < m.nout) ? fmaf(__uint_as_float(bits), sBias[P.bias_floats + P.bias_off[l] + j],
+                                             sBias[2 * P.bias_floats + P.bias_off[l] + j])
+                                      : 0.f;
                 else z[j] = (j < m.nout) ? __uint_as_float(bits) + bias[j] : 0.f;
               }
             } else {
@@ -532,7 +510,7 @@ __global__ void k_pack_bf16(Model m, TcPlan P, long long stride, int K, const fl
     __nv_bfloat16* t = reinterpret_cast<__nv_bfloat16*>(d + (size_t)P.gw_row[l] * 128);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np * kp; i += gridDim.x * blockDim.x) {
       const int n = i / kp, k = i - n * kp;
-      const float v = (n < m.dout[l] && k < m.din[l]) ? s[m.woff[l] + n * m.din[l] + k] : 0.f;
+      const float v = (n < m.dout[l] && k < m.din[l]) ? s[m.woff[l] + n * m.din[l] + tc_in_col(m, l, k)] : 0.f;
       t[((k >> 6) * np + n) * 64 + (k & 63)] = __float2bfloat16_rn(v);
     }
   }
@@ -540,31 +518,145 @@ __global__ void k_pack_bf16(Model m, TcPlan P, long long stride, int K, const fl
   for (int l = 0; l < m.nl; ++l)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.npad[l]; i += gridDim.x * blockDim.x)
       b[P.bias_off[l] + i] = i < m.dout[l] ? s[m.boff[l] + i] : 0.f;
-  if (P.fold > 0) {  // bias tile: row n, column 16 l = bias of output n of layer l
+  if (P.fold > 0) {  // bias tile: 64-column slabs; slab l / 4, row n, column 16 (l % 4) = bias n of layer l
     __nv_bfloat16* bt = reinterpret_cast<__nv_bfloat16*>(d + (size_t)P.gbt_row * 128);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 64 * 64; i += gridDim.x * blockDim.x) {
-      const int n = i >> 6, k = i & 63, l = k >> 4;
+    const int nsl = (P.fold + 3) / 4;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsl * 64 * 64; i += gridDim.x * blockDim.x) {
+      const int sl = i >> 12, n = (i >> 6) & 63, k = i & 63, l = 4 * sl + (k >> 4);
       const float v = ((k & 15) == 0 && l < P.fold && n < m.dout[l]) ? s[m.boff[l] + n] : 0.f;
       bt[i] = __float2bfloat16_rn(v);
     }
   }
-  if (P.w8_bytes == 0) return;
-  // E4M3 copy: output n of layer l is stored as W[n][k] / c_n with c_n = max_k |W[n][k]| / 448
-  float* scl = reinterpret_cast<float*>(d + P.gscale_byte);
+}
+
+// E4M3 copy of the weights and the epilogue's affine maps (FP8 precision), one block of 128
+// threads per primitive.
+//  * Weights: output n of layer l is stored as W[n][k] / c_n with c_n = max_k |W[n][k]| / 448.
+//  * Activation scales: the A operand of layer l holds its input divided by a power of two s_l,
+//    fixed per (primitive, layer): s_0 = 1/256 (encoded inputs lie in [-1, 1]); for l >= 1 the
+//    smallest power of two with 4 a_l / s_l <= 448, a_l the largest input of layer l met when
+//    the block evaluates the primitive's FP32 MLP on 256 probe inputs (local positions
+//    uniform in [-1, 1]^3, directions on the unit sphere, from a fixed integer hash). Values
+//    beyond the 4x headroom saturate at 448 s_l.
+//  * Epilogue of layer l: z / s_{l+1} = acc (s_l c_n / s_{l+1}) + b_n / s_{l+1}, i.e. mul_n and
+//    add_n, with s_{l+1} = 1 for the last layer (its outputs stay unscaled). The divisions by
+//    powers of two are exact, so the static scales add no rounding of their own.
+MLPS_DEV uint32_t probe_hash(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return x;
+}
+
+MLPS_DEV float probe_unit(uint32_t& st) {  // uniform in [-1, 1)
+  st = probe_hash(st + 0x9E3779B9u);
+  return (float)(st >> 8) * (2.0f / 16777216.0f) - 1.0f;
+}
+
+MLPS_DEV int probe_gamma(int L, const float v[3], float* x, int f) {
+  if (L == 0) {
+    for (int c = 0; c < 3; ++c) x[f++] = v[c];
+    return f;
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int l = 0; l < L; ++l) {
+      float sn, cs;
+      sincospif(ldexpf(v[c], l), &sn, &cs);
+      x[f++] = sn;
+      x[f++] = cs;
+    }
+  return f;
+}
+
+MLPS_DEV float pow2_at_least(float q) {  // smallest power of two >= q (1 for q <= 0 or not finite)
+  if (!(q > 1e-30f) || !(q < 1e30f)) return 1.0f;
+  return __uint_as_float((__float_as_uint(q) + 0x007FFFFFu) & 0x7F800000u);
+}
+
+__global__ void __launch_bounds__(128) k_pack_e4m3(Model m, TcPlan P, long long stride, int K,
+                                                   const float* __restrict__ src, unsigned char* __restrict__ dst) {
+  const int p = blockIdx.x;
+  if (p >= K) return;
+  const float* s = src + (size_t)p * m.Prow;
+  unsigned char* d = dst + (size_t)p * stride;
+  __shared__ float sc[kMaxLayers][128];
+  __shared__ unsigned int amax[kMaxLayers + 1];
+  __shared__ float ascale[kMaxLayers + 1];
+  const int t = threadIdx.x;
   for (int l = 0; l < m.nl; ++l) {
     const int din = m.din[l];
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < P.npad[l]; n += gridDim.x * blockDim.x) {
+    for (int n = t; n < P.npad[l]; n += blockDim.x) {
       const bool live = n < m.dout[l];
-      float amax = 0.f;
+      float am = 0.f;
       if (live)
-        for (int k = 0; k < din; ++k) amax = fmaxf(amax, fabsf(s[m.woff[l] + n * din + k]));
-      const float c = amax > 0.f ? amax / 448.f : 1.f;
-      scl[P.bias_off[l] + n] = c;
+        for (int k = 0; k < din; ++k) am = fmaxf(am, fabsf(s[m.woff[l] + n * din + k]));
+      const float c = am > 0.f ? am / 448.f : 1.f;
+      sc[l][n] = c;
       unsigned char* r = d + (size_t)(P.g8_row[l] + n) * 128;
       for (int k = 0; k < 128; ++k)
-        r[k] = (live && k < din) ? __nv_cvt_float_to_fp8(s[m.woff[l] + n * din + k] / c, __NV_SATFINITE, __NV_E4M3) : 0;
+        r[k] = (live && k < din)
+                   ? __nv_cvt_float_to_fp8(s[m.woff[l] + n * din + tc_in_col(m, l, k)] / c, __NV_SATFINITE, __NV_E4M3)
+                   : 0;
     }
   }
+  if (t <= kMaxLayers) amax[t] = 0u;
+  __syncthreads();
+  float hin[128], hout[128];
+  for (int probe = 0; probe < 2; ++probe) {
+    uint32_t st = probe_hash(((uint32_t)p * 256u + (uint32_t)(2 * t + probe)) * 2654435761u + 12345u);
+    float xl[3], dv[3];
+    for (int c = 0; c < 3; ++c) xl[c] = probe_unit(st);
+    float nn = 0.f;
+    do {  // direction: rejection-sampled in the unit ball, then normalised
+      nn = 0.f;
+      for (int c = 0; c < 3; ++c) {
+        dv[c] = probe_unit(st);
+        nn += dv[c] * dv[c];
+      }
+    } while (!(nn > 1e-4f && nn <= 1.f));
+    const float inv = rsqrtf(nn);
+    for (int c = 0; c < 3; ++c) dv[c] *= inv;
+    int f = 0;
+    if (m.contact) {
+      if (m.dirL > 0) f = probe_gamma(m.dirL, dv, hin, f);
+      f = probe_gamma(m.xyzL, xl, hin, f);
+    } else {
+      f = probe_gamma(m.xyzL, xl, hin, f);
+      if (m.dirL > 0) f = probe_gamma(m.dirL, dv, hin, f);
+    }
+    for (int l = 0; l + 1 < m.nl; ++l) {
+      const int din = m.din[l], dout = m.dout[l];
+      float mx = 0.f;
+      for (int n = 0; n < dout; ++n) {
+        float z = s[m.boff[l] + n];
+        for (int k = 0; k < din; ++k) z = fmaf(s[m.woff[l] + n * din + k], hin[k], z);
+        z = fmaxf(z, 0.f);
+        hout[n] = z;
+        mx = fmaxf(mx, z);
+      }
+      atomicMax(&amax[l + 1], __float_as_uint(mx));  // non-negative floats order as their bits
+      for (int n = 0; n < dout; ++n) hin[n] = hout[n];
+    }
+  }
+  __syncthreads();
+  if (t <= m.nl) {
+    float sl = 1.0f / 256.0f;
+    if (t >= 1 && t < m.nl) sl = pow2_at_least(4.0f * __uint_as_float(amax[t]) / 448.0f);
+    if (t == m.nl) sl = 1.0f;  // the last layer's outputs
+    ascale[t] = sl;
+  }
+  __syncthreads();
+  float* mul = reinterpret_cast<float*>(d + P.gmul_byte);
+  float* add = reinterpret_cast<float*>(d + P.gadd_byte);
+  for (int l = 0; l < m.nl; ++l)
+    for (int n = t; n < P.npad[l]; n += blockDim.x) {
+      const bool live = n < m.dout[l];
+      const float so = ascale[l + 1];
+      mul[P.bias_off[l] + n] = live ? ascale[l] * sc[l][n] / so : 0.f;
+      add[P.bias_off[l] + n] = live ? s[m.boff[l] + n] / so : 0.f;
+    }
 }
 
 }  // namespace tc
@@ -593,18 +685,20 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3) {
   }
   P->w_bytes = sw;
   // (the backward pass reads the same W tiles as MN-major operands: no transposed copies)
-  if (m.width == 64 && m.nl - 1 >= 1 && m.nl - 1 <= 4) {  // hidden-layer biases folded (BF16 forward)
-    P->fold = m.nl - 1;
+  if (m.width == 64 && m.nl - 1 >= 1) {  // every hidden-layer bias folded (BF16 forward at width 64)
+    P->fold = m.nl - 1;  // <= kMaxLayers - 1 = 7: at most two 64-column slabs of bias columns
+    const int nsl = (P->fold + 3) / 4;
     P->gbt_row = rows;
-    rows += 64;
+    rows += 64 * nsl;
     P->sbt_off = sw;
-    P->bt_bytes = 64 * 128;
+    P->bt_bytes = 64 * 128 * nsl;
   }
   P->bias_floats = bias;
   P->gbias_byte = rows * 128;
   long long bytes = (long long)rows * 128 + 4LL * bias;
   if (e4m3) {
-    // E4M3 copy after the biases: one 128-byte row per output, then the FP32 weight scales.
+    // E4M3 copy after the biases: one 128-byte row per output, then the FP32 multipliers and
+    // offsets of the epilogue.
     // The BF16 tiles stay in the blob: the backward pass of the FP8 precision uses them.
     if (kmax > 128) return false;
     int r8 = (int)((bytes + 127) / 128), s8 = 0;
@@ -615,8 +709,9 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3) {
       s8 += P->npad[l] * 128;
     }
     P->w8_bytes = s8;
-    P->gscale_byte = r8 * 128;
-    bytes = (long long)r8 * 128 + 4LL * bias;
+    P->gmul_byte = r8 * 128;
+    P->gadd_byte = r8 * 128 + 4 * bias;
+    bytes = (long long)r8 * 128 + 8LL * bias;
   }
   if (m.C > 0) {  // FP32 slot embeddings [4][C] after everything the MLP kernels read
     bytes = (bytes + 15) / 16 * 16;
@@ -632,14 +727,15 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3) {
 
 // Epilogue groups of the forward kernel (chunks of 128 sample rows in flight per CTA). Default:
 // registers cap the feature-head variants at three groups (the head keeps 4 + 32 values per
-// thread), TMEM caps width 128 at four and shared memory (a 32 KB operand tile per group) at
-// two. Width 64 without a feature head runs with 2 to 6 (the autotuner's choices).
+// thread), TMEM and shared memory (a 32 KB operand tile per group) cap width 128 at two.
+// Width 64 without a feature head runs with 2 to 5 in BF16 and 2 to 6 in E4M3 (the autotuner's
+// choices).
 int tc_fwd_groups(int width, int F, int groups, bool e4m3) {
-  // BF16 at width 64 runs five groups in 96 registers; E4M3 keeps each row's 64 values live for
-  // its scale, so it stays at four
-  const int def = width == 64 ? (F > 0 ? 3 : (e4m3 ? 4 : 5)) : 2;
+  // BF16 at width 64 runs five groups in 96 registers (TMEM holds five groups' accumulators and
+  // A operands); E4M3, with narrower A operands and a one-FMA epilogue, runs six
+  const int def = width == 64 ? (F > 0 ? 3 : (e4m3 ? 6 : 5)) : 2;
   if (groups == 0) return def;
-  // BF16 groups also hold their A operand in TMEM (96 columns each at width 64): at most five
+  // groups also hold their A operand in TMEM (96 columns each at width 64 in BF16, 80 in E4M3)
   if (width == 64 && F == 0) return (groups >= 2 && groups <= (e4m3 ? 6 : 5)) ? groups : 0;
   return groups == def ? groups : 0;
 }
@@ -667,6 +763,7 @@ void launch_pack_bf16(const Model& m, const TcPlan& P, long long stride, int K, 
   if (K == 0) return;
   dim3 grid(8, K);
   tc::k_pack_bf16<<<grid, 256, 0, st>>>(m, P, stride, K, w, static_cast<unsigned char*>(out));
+  if (P.w8_bytes > 0) tc::k_pack_e4m3<<<K, 128, 0, st>>>(m, P, stride, K, w, static_cast<unsigned char*>(out));
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {

@@ -80,7 +80,8 @@ MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F, int ipc, int kNG) {
   L.w = o;
   o = al(o + P.w_bytes, 1024);
   L.tiles0 = o;
-  L.tiles_stride = al((uint32_t)P.nl * kTile, 1024);  // T_0 .. T_{nl-1}
+  // T_0 (kpad0 / 64 slabs: the encoded input) .. T_{nl-1}
+  L.tiles_stride = al((uint32_t)(P.kpad[0] / 64 + P.nl - 1) * kTile, 1024);
   o += L.tiles_stride * kNG;
   L.ones = o;  // above every group tile: the wgrad descriptors reach it with a positive offset
   o = al(o + kOnes, 1024);
@@ -126,9 +127,10 @@ MLPS_DEV uint64_t sw128_desc_mn(uint32_t saddr, uint32_t lbo) {
 
 // Store 64 values of one row (BF16-packed pairs) into a swizzled tile.
 MLPS_DEV void store_row64(uint32_t tile, int row, const uint32_t (&pk)[32]) {
+  const RowSw sw(row);
 #pragma unroll
   for (int ch = 0; ch < 8; ++ch)
-    st_shared_v4(tile + sw128_off(row, ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+    st_shared_v4(tile + sw.off(ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
 }
 
 MLPS_DEV void ld_shared_v4(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
@@ -244,7 +246,42 @@ MLPS_DEV void issue_wgrad(uint32_t Hl, uint32_t Dl, uint32_t dw_l, uint32_t ones
 
 }  // namespace
 
-template <int NF, int XL, int DL, int kNG>
+// Contact-point input row (Eq. 4) of one hit into the two-slab tile `A`, in the tensor-core
+// blob's column order gamma(delta), gamma(d) (tc_in_col), then a constant 1 in the first padding
+// column `nin`: multiplied by nothing in the forward pass (the weights there are zero), it makes
+// row nin of wgrad_0's accumulator the bias gradient of the first layer.
+MLPS_DEV void build_row_contact(const Model& m, const PrimGeo& G, const IntervalRec* T, int nint, int row,
+                                uint32_t A) {
+  RowWriter rw{A, row, 0, 0.f};
+  if (row < nint) {
+    const IntervalRec& I = T[row];
+    float del[3];
+    contact_delta(G, I, del);
+    if (m.xyzL == 0) {
+      for (int u = 0; u < 3; ++u) rw.put(del[u]);
+    } else {
+      for (int u = 0; u < 3; ++u) put_gamma(rw, del[u], m.xyzL);
+    }
+    if (m.dirL > 0)
+      for (int u = 0; u < 3; ++u) put_gamma(rw, I.d[u], m.dirL);
+    rw.put(1.f);
+  }
+  rw.pad_to(128);
+}
+
+// wgrad of the first layer with a two-slab input (kpad0 = 128): A = [X slab 0 | X slab 1] as two
+// MN-major atoms 16 KB apart (M = 128 inputs, the constant-1 column giving the bias gradient),
+// B = delta_0 MN-major, N = npad; K = the 128 rows.
+MLPS_DEV void issue_wgrad2(uint32_t X, uint32_t Dl, uint32_t dw, int npad) {
+  const uint32_t id = idesc_bf16(kM, npad) | (1u << 15) | (1u << 16);
+  const uint64_t da = sw128_desc_mn(X, kTile), db = sw128_desc_mn(Dl, 16);
+#pragma unroll
+  for (int kk = 0; kk < kM / 16; ++kk) mma_bf16(dw, da + (uint64_t)(kk * 128), db + (uint64_t)(kk * 128), id, 1u);
+}
+
+// CT: the contact-point model (Sec. 3.2): one sample per hit (S = 1), input [gamma(delta);
+// gamma(d)] over two 64-column slabs with XL, DL their frequencies, the pose chain of Eq. 3.
+template <int NF, int XL, int DL, int kNG, bool CT = false>
 __global__ void __launch_bounds__(kGThreads * kNG, 1)
     k_mlp_bwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
   constexpr int kThreadsB = kGThreads * kNG;
@@ -353,12 +390,16 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
           }
           tmem_wait_ld();
           if (*sAbort) continue;
+          // accumulator row of the bias gradient: the ones atom's (64), or for a two-slab input
+          // the constant-1 column after the encoded input (build_row_contact)
+          const int brow = (l == 0 && P.kpad[0] > 64) ? din : 64;
+          const int col = tc_in_col(m, l, frow);
           for (int j = 0; j < 32; ++j) {
             const int n = c0 + j;
             const float val = __uint_as_float(v[j]);
             if (n >= dout || val == 0.f) continue;
-            if (frow < din) atomicAdd(&dW[m.woff[l] + n * din + frow], val);
-            else if (frow == 64) atomicAdd(&dW[m.boff[l] + n], val);
+            if (frow < din) atomicAdd(&dW[m.woff[l] + n * din + col], val);
+            else if (frow == brow) atomicAdd(&dW[m.boff[l] + n], val);
           }
         }
       }
@@ -449,7 +490,8 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
     named_bar_sync(gbar, kGThreads);
     if (nxt.n > 0 && my_nx >= 0) prefetch(nxt, my_nx);  // start loading the next chunk now
     const uint32_t tiles = sbase + L.tiles0 + (uint32_t)g * L.tiles_stride;
-#define tileaddr(I) (tiles + (uint32_t)(I) * kTile)
+    const int t0s = P.kpad[0] / 64;  // slabs of T_0
+#define tileaddr(I) (tiles + (uint32_t)((I) == 0 ? 0 : (CT ? t0s + (I) - 1 : (I))) * kTile)
     const int iv = row / S, k = row - iv * S;
     const bool valid = iv < nint;
     const uint32_t acc = tmem + (uint32_t)g * kGColsB;  // this group's dgrad / forward accumulator
@@ -457,7 +499,14 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
 
     const uint32_t aT = acc + 64u;  // A operand in TMEM: 32 columns of BF16 pairs
     const uint32_t arow = aT + ((uint32_t)(q * 32) << 16);
-    if (DL >= 0) {  // encoded input straight into the A operand in TMEM
+    if constexpr (CT) {  // contact-point input (two slabs) through the shared-memory tile T_0
+      if (wg_pending) {
+        (void)wait_wgrad();
+        wg_pending = false;
+      }
+      build_row_contact(m, *reinterpret_cast<const PrimGeo*>(gb + L.pgeo), T, nint, row, tileaddr(0));
+      fence_proxy_async_smem();
+    } else if (DL >= 0) {  // encoded input straight into the A operand in TMEM
       uint32_t pk[32];
       encode_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, pk);
       tmem_st32(arow, pk);
@@ -475,19 +524,21 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
     if (issuer) {
       tc_fence_after();
       if (!*sAbort) {
-        if (DL >= 0) issue_fwd_layer_ta(aT, sbase + L.w + P.sw_off[0], acc, P.kpad[0], P.npad[0]);
+        if (DL >= 0 && !CT) issue_fwd_layer_ta(aT, sbase + L.w + P.sw_off[0], acc, P.kpad[0], P.npad[0]);
         else issue_fwd_layer(tileaddr(0), sbase + L.w + P.sw_off[0], acc, P.kpad[0], P.npad[0]);
       }
       mma_commit(bar_done(g));
     }
 
     // ---------------- forward recompute
+    // (after a wait that gave up, the kernel still walks its chunks with whatever TMEM holds,
+    // issuing no MMA: the outputs are then void and the status word says MLPS_ERR_TIMEOUT)
     for (int l = 0; l < nl; ++l) {
-      const bool ok = wait_mma();
+      (void)wait_mma();
       const float* bias = sBias + P.bias_off[l];
       if (l < nl - 1) {
         uint32_t pk[32];
-        if (ok) {
+        {
           uint32_t v0[32], v1[32];
           tmem_ld32(trow, v0);
           tmem_ld32(trow + 32, v1);
@@ -497,16 +548,15 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
           for (int e4 = 0; e4 < 16; ++e4) {
             const float4 bq = b4[e4];
             const int c0 = 4 * e4;
-            const float x0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]) + bq.x;
-            const float x1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]) + bq.y;
-            const float x2 = __uint_as_float(c0 + 2 < 32 ? v0[c0 + 2] : v1[c0 + 2 - 32]) + bq.z;
-            const float x3 = __uint_as_float(c0 + 3 < 32 ? v0[c0 + 3] : v1[c0 + 3 - 32]) + bq.w;
+            float x0 = __uint_as_float(c0 < 32 ? v0[c0] : v1[c0 - 32]);
+            float x1 = __uint_as_float(c0 + 1 < 32 ? v0[c0 + 1] : v1[c0 + 1 - 32]);
+            float x2 = __uint_as_float(c0 + 2 < 32 ? v0[c0 + 2] : v1[c0 + 2 - 32]);
+            float x3 = __uint_as_float(c0 + 3 < 32 ? v0[c0 + 3] : v1[c0 + 3 - 32]);
+            add2_f32(x0, x1, bq.x, bq.y);
+            add2_f32(x2, x3, bq.z, bq.w);
             pk[2 * e4] = pack_bf16_relu(x0, x1);
             pk[2 * e4 + 1] = pack_bf16_relu(x2, x3);
           }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 32; ++e) pk[e] = 0u;
         }
         tmem_st32(arow, pk);  // H_{l+1}: A operand of the next layer
         tmem_wait_st();
@@ -536,13 +586,8 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
         float z[4 + NF];
         {
           uint32_t r16[16];
-          if (ok) {
-            tmem_ld16(trow, r16);
-            tmem_wait_ld();
-          } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) r16[j] = 0u;
-          }
+          tmem_ld16(trow, r16);
+          tmem_wait_ld();
 #pragma unroll
           for (int j = 0; j < 4 + NF; ++j) z[j] = j < m.nout ? __uint_as_float(r16[j]) + bias[j] : 0.f;
         }
@@ -598,29 +643,44 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
         fence_proxy_async_smem();  // also covers the H tiles written during the recompute
         tc_fence_before();
         named_bar_sync(gbar, kGThreads);
-        if (issuer) {  // B_{nl-1}: dgrad, then wgrad, each with its own completion
+        if (issuer) {  // B_{nl-1}: dgrad, then wgrad (complete once the next dgrad is)
           tc_fence_after();
           if (!*sAbort) issue_dgrad_ta(aT, sbase + L.w + P.sw_off[nl - 1], acc, P.kpad[nl - 1], P.npad[nl - 1]);
           mma_commit(bar_done(g));
           if (!*sAbort)
             issue_wgrad(tileaddr(nl - 1), tileaddr(0), tm_dw + (uint32_t)((nl - 1) * 64), sbase + L.ones, P.npad[nl - 1]);
-          mma_commit(bar_wg(g));
         }
       }
     }
     // ---------------- backward phases B_{nl-1} .. B_0
-    // On entry to B_l: dgrad_l is issued with A = delta_l in TMEM. For l = nl-1, delta_l's copy in
-    // T_0 and wgrad_l are issued too; for l < nl-1, wgrad_{l+1} is issued (after dgrad_l) and
-    // delta_l still has to be copied to T_{l+1} (the B operand of wgrad_l) once wgrad_{l+1},
-    // which reads that tile, is done. B_l issues dgrad_{l-1} first and wgrad_l after it, so the
-    // dgrad chain never waits for a wgrad.
+    // On entry to B_l, dgrad_l is issued with A = delta_l in TMEM; B_l issues dgrad_{l-1} and then
+    // wgrad_l, whose B operand is delta_l's copy in shared memory, tile D(l) (below). A commit
+    // arrives once every earlier MMA of its thread is complete, so when dgrad_l is done, every
+    // wgrad issued before it (wgrad_m for m >= l + 2, and wgrad_{nl-1}) is done too, and their
+    // tiles are free: D(nl-1) = D(nl-2) = T_0, D(l) = T_{l+2} for l <= nl-3. No B phase waits for
+    // a wgrad, except B_0 with three layers (X then needs T_1, still read by wgrad_1).
+#define dtile(I) ((I) >= nl - 2 ? tileaddr(0) : tileaddr((I) + 2))
     for (int l = nl - 1; l >= 0; --l) {
-      bool ok = wait_mma();  // dgrad of B_l
+      (void)wait_mma();  // dgrad of B_l (and every wgrad issued before it)
+      if (l > 0 && l < nl - 1) {
+        // delta_l (A operand of dgrad_l, done) from TMEM to its tile D(l), 16 columns at a time
+        const RowSw sw(row);
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          uint32_t dl[16];
+          tmem_ld16(arow + 16u * hf, dl);
+          tmem_wait_ld();
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch)
+            st_shared_v4(dtile(l) + sw.off(4 * hf + ch), dl[4 * ch], dl[4 * ch + 1], dl[4 * ch + 2], dl[4 * ch + 3]);
+        }
+      }
       if (l > 0) {
         // delta_{l-1} = G * [H_l > 0] (H_l from T_l; wgrad_l, which reads it, is issued below),
         // 32 columns of G at a time
         const uint32_t Tl = tileaddr(l);
-        const uint32_t vmask = (valid && ok) ? 0xFFFFFFFFu : 0u;
+        const uint32_t vmask = valid ? 0xFFFFFFFFu : 0u;
+        const RowSw sw(row);
         uint32_t pk[32];
 #pragma unroll
         for (int hf = 0; hf < 2; ++hf) {
@@ -630,33 +690,18 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
 #pragma unroll
           for (int ch = 0; ch < 4; ++ch) {
             uint32_t hq[4];
-            ld_shared_v4(Tl + sw128_off(row, 4 * hf + ch), hq[0], hq[1], hq[2], hq[3]);
+            ld_shared_v4(Tl + sw.off(4 * hf + ch), hq[0], hq[1], hq[2], hq[3]);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int c0 = ch * 8 + 2 * e;
               // H_l was written by the ReLU pack, so each BF16 half is +0 or positive: H > 0 iff
-              // its 16 bits are nonzero, and __vcmpne2 gives both halves' masks at once
+              // the half is nonzero (one packed compare for both halves)
               pk[(4 * hf + ch) * 4 + e] =
-                  pack_bf16(__uint_as_float(v[c0]), __uint_as_float(v[c0 + 1])) & __vcmpne2(hq[e], 0u) & vmask;
+                  pack_bf16(__uint_as_float(v[c0]), __uint_as_float(v[c0 + 1])) & bf16x2_nonzero(hq[e]) & vmask;
             }
           }
         }
         tc_fence_before();
-        const bool copy_dl = l < nl - 1;  // delta_l still to be copied to T_{l+1}
-        if (copy_dl) {
-          ok = wait_wgrad() && ok;  // wgrad_{l+1} is done with T_{l+1}
-          // delta_l from TMEM to T_{l+1}, 16 columns at a time, before delta_{l-1} replaces it
-#pragma unroll
-          for (int hf = 0; hf < 2; ++hf) {
-            uint32_t dl[16];
-            tmem_ld16(arow + 16u * hf, dl);
-            tmem_wait_ld();
-#pragma unroll
-            for (int ch = 0; ch < 4; ++ch)
-              st_shared_v4(tileaddr(l + 1) + sw128_off(row, 4 * hf + ch), dl[4 * ch], dl[4 * ch + 1], dl[4 * ch + 2],
-                           dl[4 * ch + 3]);
-          }
-        }
         tmem_st32(arow, pk);  // delta_{l-1}: A operand of dgrad_{l-1}
         tmem_wait_st();
         fence_proxy_async_smem();
@@ -664,114 +709,170 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
         named_bar_sync(gbar, kGThreads);
         if (issuer) {
           tc_fence_after();
-          if (!*sAbort) issue_dgrad_ta(aT, sbase + L.w + P.sw_off[l - 1], acc, P.kpad[l - 1], P.npad[l - 1]);
+          // into the first layer only its first input slab: every input the pose chain needs
+          // (the contact model's gamma(delta) comes first there)
+          if (!*sAbort)
+            issue_dgrad_ta(aT, sbase + L.w + P.sw_off[l - 1], acc, l == 1 ? 64 : P.kpad[l - 1], P.npad[l - 1]);
           mma_commit(bar_done(g));
-          if (copy_dl) {
-            if (!*sAbort)
-              issue_wgrad(Tl, tileaddr(l + 1), tm_dw + (uint32_t)(l * 64), sbase + L.ones, P.npad[l]);
-            mma_commit(bar_wg(g));
+          if (l < nl - 1) {
+            if (!*sAbort) issue_wgrad(Tl, dtile(l), tm_dw + (uint32_t)(l * 64), sbase + L.ones, P.npad[l]);
+            if (nl == 3 && l == 1) mma_commit(bar_wg(g));  // B_0 waits for it before writing X into T_1
           }
         }
       } else {
         uint32_t v0[32], v1[32];
-        if (ok) {
-          tmem_ld32(trow, v0);
-          tmem_ld32(trow + 32, v1);
-          tmem_wait_ld();
-        } else {
-#pragma unroll
-          for (int e = 0; e < 32; ++e) { v0[e] = 0u; v1[e] = 0u; }
-        }
+        tmem_ld32(trow, v0);
+        tmem_ld32(trow + 32, v1);
+        tmem_wait_ld();
         tc_fence_before();
-        // ---------------- encoding derivative and pose chain
-        // With x_k = p + t_k dp and t_k = tm + c_k (r1 - r0), c_k = (k + 1/2) / S - 1/2, every
-        // per-interval sum the chain needs follows from A = sum_k gx_k and B = sum_k c_k gx_k.
-        float gx[3] = {0.f, 0.f, 0.f};
-        const IntervalRec& I = T[valid ? iv : 0];
-        const float ck = ((float)k + 0.5f) * invS - 0.5f;
-        if (valid) {
-          const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
-          float xl[3];
-          for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
-          enc_grad64<XL>(xl, v0, v1, gx);
-        }
-        float red[6] = {gx[0], gx[1], gx[2], ck * gx[0], ck * gx[1], ck * gx[2]};
-        seg_scan<6>(red, 6, row, S, sScan + g * 4 * kScanNV, gbar);
-        // Tail of the chain, per interval ending in this warp: the segment totals are
-        // broadcast from the interval's last row and lane j < 12 computes output j (dL/dM_{u,e}
-        // for j = 3u + e < 9, dL/dmu_{j-9} otherwise), accumulated in a register until the
-        // block's primitive changes (no shared-memory atomics per interval).
-        const int wrow0 = row - lane;
-        for (int r_end = (wrow0 / S + 1) * S - 1; r_end < wrow0 + 32; r_end += S) {
-          const int ive = r_end / S;
-          if (ive >= nint) break;  // warp-uniform
-          float rr[6];
+        if constexpr (CT) {
+          // ---------------- contact-point chain (Eq. 3-4), one hit per row: dL/d delta from
+          // gamma(delta)'s derivative (the first 6 XL columns), then the pose contributions of
+          // the hit (see chain_pose of the FP32 path for the formulas), summed over the warp;
+          // lane j < 12 keeps output j
+          const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
+          float out[12];
 #pragma unroll
-          for (int j = 0; j < 6; ++j) rr[j] = __shfl_sync(0xffffffffu, red[j], r_end - wrow0);
-          if (lane < 12) {
-            const IntervalRec& Ie = T[ive];
-            const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
-            const float span = Ie.r1 - Ie.r0, tm = Ie.r0 + 0.5f * span;
-            const float dA = rr[0] * Ie.dp[0] + rr[1] * Ie.dp[1] + rr[2] * Ie.dp[2];
-            const float dB = rr[3] * Ie.dp[0] + rr[4] * Ie.dp[1] + rr[5] * Ie.dp[2];
-            const float dDelta = DD[ive];
-            // end-point gradients: sum_k gt_k (1 - u_k), sum_k gt_k u_k, plus the width term
-            const float gt0 = 0.5f * dA - dB - dDelta * invS, gt1 = 0.5f * dA + dB + dDelta * invS;
-            const bool clamped = Ie.r0 != -Ie.r1;
-            const float gtm = gt1 + (clamped ? 0.f : gt0);
-            const float gh = gt1 - (clamped ? 0.f : gt0);
-            const float aa = Ie.dp[0] * Ie.dp[0] + Ie.dp[1] * Ie.dp[1] + Ie.dp[2] * Ie.dp[2];
+          for (int j = 0; j < 12; ++j) out[j] = 0.f;
+          if (valid) {
+            const IntervalRec& I = T[iv];
+            float del[3], gd[3];
+            contact_delta(Gp, I, del);
+            enc_grad64<XL>(del, v0, v1, gd);
+            const float dDelta = DD[iv];
+            const bool clamped = I.r0 != -I.r1;
+            const float gtd = I.tmid > 0.f ? -(gd[0] * I.d[0] + gd[1] * I.d[1] + gd[2] * I.d[2]) : 0.f;
+            const float gtm = dDelta + (clamped ? 0.f : -dDelta) + gtd;
+            const float gh = dDelta - (clamped ? 0.f : -dDelta);
+            const float aa = I.dp[0] * I.dp[0] + I.dp[1] * I.dp[1] + I.dp[2] * I.dp[2];
             const float inv_a = 1.f / aa;
-            const float hh = Ie.r1;
+            const float hh = I.r1;
             const float gh_ah = hh > 0.f ? gh * inv_a / hh : 0.f;
-            if (lane < 9) {
-              const int u = lane / 3, e = lane - 3 * u;
-              const float ru = u == 0 ? rr[0] : (u == 1 ? rr[1] : rr[2]);
-              const float rbu = u == 0 ? rr[3] : (u == 1 ? rr[4] : rr[5]);
-              const float pu = Ie.p[u], dpu = Ie.dp[u];
-              const float go_u = -gtm * dpu * inv_a - gh_ah * pu;
-              const float cd_u = -(gtm * pu + gh * hh * dpu) * inv_a;
-              const float ta = tm * ru + span * rbu;  // sum_k t_k gx_k[u]
-              float gy = 0.f, ym = 0.f;               // y = R diag(s) x
+            float go[3], cd[3], ym[3];
 #pragma unroll
-              for (int j = 0; j < 3; ++j) {
-                const float rsj = Gp.R[e * 3 + j] * Gp.s[j];
-                gy = fmaf(rsj, ru * Ie.p[j] + ta * Ie.dp[j], gy);
-                ym = fmaf(rsj, Ie.p[j], ym);
-              }
-              geo_acc += gy + go_u * ym + cd_u * Ie.d[e];
-            } else {
-              const int e = lane - 9;
-              float acc2 = 0.f;
+            for (int u = 0; u < 3; ++u) {
+              go[u] = -gtm * I.dp[u] * inv_a - gh_ah * I.p[u];
+              cd[u] = -(gtm * I.p[u] + gh * hh * I.dp[u]) * inv_a;
+              ym[u] = Gp.R[u * 3] * Gp.s[0] * I.p[0] + Gp.R[u * 3 + 1] * Gp.s[1] * I.p[1] +
+                      Gp.R[u * 3 + 2] * Gp.s[2] * I.p[2];
+            }
 #pragma unroll
-              for (int u = 0; u < 3; ++u) {
-                const float go_u = -gtm * Ie.dp[u] * inv_a - gh_ah * Ie.p[u];
-                acc2 = fmaf(Gp.Mhi[u * 3 + e], rr[u] + go_u, acc2);
+            for (int u = 0; u < 3; ++u)
+#pragma unroll
+              for (int e = 0; e < 3; ++e) out[u * 3 + e] = go[u] * ym[e] + cd[u] * I.d[e];
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+              out[9 + e] = gd[e] - (Gp.Mhi[e] * go[0] + Gp.Mhi[3 + e] * go[1] + Gp.Mhi[6 + e] * go[2]);
+          }
+#pragma unroll
+          for (int j = 0; j < 12; ++j) {
+            float v = out[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == j) geo_acc += v;
+          }
+        } else {
+        // ---------------- encoding derivative and pose chain
+          // With x_k = p + t_k dp and t_k = tm + c_k (r1 - r0), c_k = (k + 1/2) / S - 1/2, every
+          // per-interval sum the chain needs follows from A = sum_k gx_k and B = sum_k c_k gx_k.
+          float gx[3] = {0.f, 0.f, 0.f};
+          const IntervalRec& I = T[valid ? iv : 0];
+          const float ck = ((float)k + 0.5f) * invS - 0.5f;
+          if (valid) {
+            const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+            float xl[3];
+            for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
+            enc_grad64<XL>(xl, v0, v1, gx);
+          }
+          float red[6] = {gx[0], gx[1], gx[2], ck * gx[0], ck * gx[1], ck * gx[2]};
+          seg_scan<6>(red, 6, row, S, sScan + g * 4 * kScanNV, gbar);
+          // Tail of the chain, per interval ending in this warp: the segment totals are
+          // broadcast from the interval's last row and lane j < 12 computes output j (dL/dM_{u,e}
+          // for j = 3u + e < 9, dL/dmu_{j-9} otherwise), accumulated in a register until the
+          // block's primitive changes (no shared-memory atomics per interval).
+          const int wrow0 = row - lane;
+          for (int r_end = (wrow0 / S + 1) * S - 1; r_end < wrow0 + 32; r_end += S) {
+            const int ive = r_end / S;
+            if (ive >= nint) break;  // warp-uniform
+            float rr[6];
+  #pragma unroll
+            for (int j = 0; j < 6; ++j) rr[j] = __shfl_sync(0xffffffffu, red[j], r_end - wrow0);
+            if (lane < 12) {
+              const IntervalRec& Ie = T[ive];
+              const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + L.pgeo);
+              const float span = Ie.r1 - Ie.r0, tm = Ie.r0 + 0.5f * span;
+              const float dA = rr[0] * Ie.dp[0] + rr[1] * Ie.dp[1] + rr[2] * Ie.dp[2];
+              const float dB = rr[3] * Ie.dp[0] + rr[4] * Ie.dp[1] + rr[5] * Ie.dp[2];
+              const float dDelta = DD[ive];
+              // end-point gradients: sum_k gt_k (1 - u_k), sum_k gt_k u_k, plus the width term
+              const float gt0 = 0.5f * dA - dB - dDelta * invS, gt1 = 0.5f * dA + dB + dDelta * invS;
+              const bool clamped = Ie.r0 != -Ie.r1;
+              const float gtm = gt1 + (clamped ? 0.f : gt0);
+              const float gh = gt1 - (clamped ? 0.f : gt0);
+              const float aa = Ie.dp[0] * Ie.dp[0] + Ie.dp[1] * Ie.dp[1] + Ie.dp[2] * Ie.dp[2];
+              const float inv_a = 1.f / aa;
+              const float hh = Ie.r1;
+              const float gh_ah = hh > 0.f ? gh * inv_a / hh : 0.f;
+              if (lane < 9) {
+                const int u = lane / 3, e = lane - 3 * u;
+                const float ru = u == 0 ? rr[0] : (u == 1 ? rr[1] : rr[2]);
+                const float rbu = u == 0 ? rr[3] : (u == 1 ? rr[4] : rr[5]);
+                const float pu = Ie.p[u], dpu = Ie.dp[u];
+                const float go_u = -gtm * dpu * inv_a - gh_ah * pu;
+                const float cd_u = -(gtm * pu + gh * hh * dpu) * inv_a;
+                const float ta = tm * ru + span * rbu;  // sum_k t_k gx_k[u]
+                float gy = 0.f, ym = 0.f;               // y = R diag(s) x
+  #pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                  const float rsj = Gp.R[e * 3 + j] * Gp.s[j];
+                  gy = fmaf(rsj, ru * Ie.p[j] + ta * Ie.dp[j], gy);
+                  ym = fmaf(rsj, Ie.p[j], ym);
+                }
+                geo_acc += gy + go_u * ym + cd_u * Ie.d[e];
+              } else {
+                const int e = lane - 9;
+                float acc2 = 0.f;
+  #pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                  const float go_u = -gtm * Ie.dp[u] * inv_a - gh_ah * Ie.p[u];
+                  acc2 = fmaf(Gp.Mhi[u * 3 + e], rr[u] + go_u, acc2);
+                }
+                geo_acc -= acc2;
               }
-              geo_acc -= acc2;
             }
           }
         }
-        // wgrad_0: X rebuilt in T_0 (its last reader, wgrad_{nl-1}, is done) and delta_0 copied
-        // to T_1 once wgrad_1 is done; waited for only when the next chunk writes these tiles
-        uint32_t dl[32];
-        tmem_ld32(arow, dl);
-        tmem_wait_ld();
-        tc_fence_before();
-        (void)wait_wgrad();  // wgrad_1
-        store_row64(tileaddr(1), row, dl);
-        if (DL >= 0) build_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, tileaddr(0));
-        else build_row(m, T, nint, row, tileaddr(0), P.kpad[0]);
+        // wgrad_0: delta_0 copied to D(0) and X rebuilt in a free tile (T_0 with four or more
+        // layers: its last reader wgrad_{nl-2} is done; T_1 with two, freed by wgrad_1; T_1 after
+        // waiting for wgrad_1 with three). The group waits for this last wgrad only when the next
+        // chunk writes these tiles.
+        {
+          uint32_t dl[32];
+          tmem_ld32(arow, dl);
+          tmem_wait_ld();
+          tc_fence_before();
+          store_row64(dtile(0), row, dl);
+        }
+        if (nl == 3) (void)wait_wgrad();
+        // the two-slab input of the contact model only fits T_0
+        const uint32_t xt = (nl >= 4 || CT) ? tileaddr(0) : tileaddr(1);
+        if constexpr (CT) build_row_contact(m, *reinterpret_cast<const PrimGeo*>(gb + L.pgeo), T, nint, row, xt);
+        else if (DL >= 0) build_row64<XL, (DL > 0 ? DL : 0)>(T, nint, S, row, xt);
+        else build_row(m, T, nint, row, xt, P.kpad[0]);
         fence_proxy_async_smem();
         named_bar_sync(gbar, kGThreads);
         if (issuer) {
           tc_fence_after();
-          if (!*sAbort) issue_wgrad(tileaddr(0), tileaddr(1), tm_dw, sbase + L.ones, P.npad[0]);
-          mma_commit(bar_wg(g));
+          if (!*sAbort) {
+            if (CT) issue_wgrad2(xt, dtile(0), tm_dw, P.npad[0]);
+            else issue_wgrad(xt, dtile(0), tm_dw, sbase + L.ones, P.npad[0]);
+          }
+          mma_commit(bar_wg(g));  // every wgrad of the chunk
         }
         wg_pending = true;
       }
     }
+#undef dtile
 #undef tileaddr
     cur = nxt;
   }
@@ -811,13 +912,21 @@ static int bwd_groups(const Model& m, const TcPlan& P) {
   return 0;
 }
 
+// `m` is the tensor-core model (hidden layers of a 32-wide model padded to 64, tc_model).
 bool tc_bwd_supported(const Model& m, const TcPlan& P) {
   if (m.width != 64 || m.nl < 2) return false;
-  if (m.xyzL != 0 && m.xyzL != 6) return false;
-  if (P.kpad[0] != 64) return false;
   if (m.F > 12) return false;
   for (int l = 0; l < m.nl; ++l)
     if (P.npad[l] > 64) return false;
+  if (m.contact) {
+    // the paper's contact-point model: gamma(delta) and gamma(d) with L = 6 (72 inputs over two
+    // slabs, the constant-1 column after them), one sample per hit, no feature head
+    if (m.xyzL != 6 || m.dirL != 6 || m.F != 0 || m.S != 1 || m.nl < 3) return false;
+    if (P.kpad[0] != 128 || m.nin >= 128) return false;
+  } else {
+    if (m.xyzL != 0 && m.xyzL != 6) return false;
+    if (P.kpad[0] != 64) return false;
+  }
   return bwd_groups(m, P) > 0;
 }
 
@@ -835,7 +944,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode_b() {
 
 cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,
                               cudaStream_t st) {
-  if (!tc_bwd_supported(a.m, P)) return cudaErrorNotSupported;
+  if (!tc_bwd_supported(tc_model(a.m), P)) return cudaErrorNotSupported;
   auto encode = get_encode_b();
   if (!encode) return cudaErrorNotSupported;
   CUtensorMap tmap;
@@ -858,7 +967,10 @@ cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
    : (xl == 0 && dl == 0) ? (f ? tc::k_mlp_bwd_tc<12, 0, 0, NG> : tc::k_mlp_bwd_tc<0, 0, 0, NG>)   \
    : (xl == 6)            ? (f ? tc::k_mlp_bwd_tc<12, 6, -1, NG> : tc::k_mlp_bwd_tc<0, 6, -1, NG>) \
                           : (f ? tc::k_mlp_bwd_tc<12, 0, -1, NG> : tc::k_mlp_bwd_tc<0, 0, -1, NG>))
-  decltype(&tc::k_mlp_bwd_tc<0, 6, 4, 3>) kern = ng == 3 ? MLPS_BWD_KERN(3) : MLPS_BWD_KERN(2);
+  // the contact-point model runs two groups: its chunks hold 128 interval records each
+  if (a.m.contact && ng != 2) return cudaErrorNotSupported;
+  decltype(&tc::k_mlp_bwd_tc<0, 6, 4, 3>) kern =
+      a.m.contact ? tc::k_mlp_bwd_tc<0, 6, 6, 2, true> : (ng == 3 ? MLPS_BWD_KERN(3) : MLPS_BWD_KERN(2));
 #undef MLPS_BWD_KERN
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

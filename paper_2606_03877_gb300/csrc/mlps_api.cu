@@ -116,7 +116,9 @@ mlps_status check_cfg(const mlps_config* c) {
 // 72-32-32-4) runs on them with its hidden layers zero-padded to 64 units: the extra units have
 // zero weights and bias, so their ReLU output is 0 and they change no result. The packer reads
 // the canonical (32-wide) weights and writes the padded tiles; the kernels see the padded shape.
-Model tc_model(const Model& m) {
+}  // namespace
+
+Model mlps::tc_model(const Model& m) {
   if (m.width != 32) return m;
   Model t = m;
   t.width = 64;
@@ -126,6 +128,8 @@ Model tc_model(const Model& m) {
   }
   return t;
 }
+
+namespace {
 
 Model make_model(const mlps_config* c) {
   Model m;
@@ -561,9 +565,10 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
     if (tc && !tc_plan(m, &P, &tc_stride, cfg->precision == MLPS_FP8_E4M3)) return MLPS_ERR_UNSUPPORTED;
     if (!simt_bwd_wide_supported(a) || !w.dwb) return MLPS_ERR_UNSUPPORTED;
   } else if (tc) {
-    // the tensor-core backward takes the midpoint-sample input of 64-wide models only
-    if (cfg->contact || m.width == 32) return MLPS_ERR_UNSUPPORTED;
-    if (!tc_plan(m, &P, &tc_stride, cfg->precision == MLPS_FP8_E4M3) || !tc_bwd_supported(m, P))
+    // the tensor-core backward: 64-wide models (32-wide ones padded to 64) with the midpoint
+    // samples, or the paper's contact-point model
+    const Model tm = tc_model(m);
+    if (!tc_plan(tm, &P, &tc_stride, cfg->precision == MLPS_FP8_E4M3) || !tc_bwd_supported(tm, P))
       return MLPS_ERR_UNSUPPORTED;
   } else if (cfg->precision != MLPS_FP32 || !simt_bwd_supported(a)) {
     return MLPS_ERR_UNSUPPORTED;
@@ -703,10 +708,11 @@ mlps_status mlps_pack_weights(const mlps_config* cfg, int32_t K, const float* we
     long long stride;
     tc_plan(tc_model(m), &P, &stride, cfg->precision == MLPS_FP8_E4M3);
     launch_pack_bf16(m, P, stride, K, weights_fp32, packed, st);  // canonical shape in, padded tiles out
+    count_launch(K > 0 ? (cfg->precision == MLPS_FP8_E4M3 ? 2 : 1) : 0);
   } else {
     launch_pack_fp32(m, pk, K, weights_fp32, packed, st);
+    count_launch(K > 0 ? 1 : 0);
   }
-  count_launch(K > 0 ? 1 : 0);
   return cuda_status(cudaGetLastError());
 }
 

@@ -30,6 +30,17 @@ struct MlpArgs {
   int groups;                    // forward tensor-core MLP: chunks in flight per CTA (0 = default)
 };
 
+// Input column of the canonical weights that column k of layer l's tensor-core tile holds. The
+// tiles keep the canonical order except for the first layer of the contact-point model, whose
+// encoded input [gamma(d); gamma(delta)] (Eq. 4) is stored as [gamma(delta); gamma(d)]: the
+// backward pass then finds every input the pose gradient needs (gamma(delta)) in the first
+// 64-column slab.
+MLPS_HD int tc_in_col(const Model& m, int l, int k) {
+  if (l != 0 || !m.contact) return k;
+  const int nd = m.dirL > 0 ? 6 * m.dirL : 0, nx = m.xyzL > 0 ? 6 * m.xyzL : 3;
+  return k < nx ? nd + k : k - nx;
+}
+
 // Tensor-core plan: per-layer padded shapes and where the operand tiles live.
 struct TcPlan {
   int nl;
@@ -38,18 +49,22 @@ struct TcPlan {
   int gw_row[kMaxLayers];                  // first 128-byte row of layer l's tile in a blob
   int w_bytes;                             // all forward W tiles
   // bias folding of the BF16 forward (0 = none): the biases of layers 0 .. fold-1 are a K-major
-  // B tile of 64 rows x 64 columns (layer l's bias in column 16 l), multiplied by a constant
-  // "ones" A tile in one extra K step per layer, so the epilogue adds no bias
+  // B tile of 64 rows and 64-column slabs (layer l's bias in slab l / 4, column 16 (l % 4)),
+  // multiplied by a constant "ones" A tile in one extra K step per layer, so the epilogue adds
+  // no bias
   int fold;
   int gbt_row;                             // first 128-byte row of the bias tile in a blob
   int sbt_off;                             // its shared-memory byte offset (after the W tiles)
-  int bt_bytes;                            // 8192 when fold > 0
+  int bt_bytes;                            // 8192 per slab when fold > 0
   // E4M3 copy (FP8 precision only; w8_bytes = 0 otherwise): layer l's tile W [npad][kpad] as
-  // one 128-byte row per output (kpad <= 128), and FP32 per-output weight scales
+  // one 128-byte row per output (kpad <= 128), then per output n of layer l the FP32 affine map
+  // of the epilogue, z' = acc * mul_n + add_n, into which the packing folds the weight scale of
+  // output n and the static activation scales of the layer's input and output
   int g8_row[kMaxLayers];                  // first 128-byte row of layer l's E4M3 tile in a blob
   int s8_off[kMaxLayers];                  // shared-memory byte offset of layer l's E4M3 tile
   int w8_bytes;                            // all E4M3 tiles
-  int gscale_byte;                         // byte offset of the FP32 weight scales (bias_off indexing)
+  int gmul_byte;                           // byte offset of the FP32 multipliers (bias_off indexing)
+  int gadd_byte;                           // byte offset of the FP32 offsets (bias_off indexing)
   int bias_off[kMaxLayers];                // float offset of layer l's bias
   int bias_floats;
   int gbias_byte;                          // byte offset of the FP32 biases in a blob
@@ -120,6 +135,8 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
                               cudaStream_t st);
 // k_mlp_tc_bwd.cu (BF16 tensor-core backward)
 bool tc_bwd_supported(const Model& m, const TcPlan& P);
+// The model as the tensor-core kernels see it: 32-wide hidden layers padded to 64.
+Model tc_model(const Model& m);
 cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,
                               cudaStream_t st);
 

@@ -177,12 +177,17 @@ MLPS_DEV void issue_fwd_layer_e4m3(uint32_t A, uint32_t W, uint32_t d, int kpad,
   }
 }
 
-// Power-of-two scale s with amax / s <= 448 (the largest finite E4M3 value), s = 1 when amax is
-// zero or not finite: dividing by s is exact, so the scale adds no rounding of its own.
-MLPS_DEV float e4m3_row_scale(float amax) {
-  const float q = amax * (1.0f / 448.0f);
-  if (!(q > 1e-30f) || !(q < 1e30f)) return 1.0f;
-  return __uint_as_float((__float_as_uint(q) + 0x007FFFFFu) & 0x7F800000u);  // round up to 2^e
+// E4M3 layer with the A operand in tensor memory (`At`: lane = sample row, four E4M3 values per
+// column, 8 columns per K = 32 step).
+MLPS_DEV void issue_fwd_layer_e4m3_ta(uint32_t At, uint32_t W, uint32_t d, int kpad, int npad) {
+  const uint32_t idesc = idesc_e4m3(kM, npad);
+  const uint64_t db = sw128_desc(W);
+  const int nk = kpad / 32;
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    if (kk >= nk) break;
+    mma_e4m3_ta(d, At + 8u * (uint32_t)kk, db + (uint64_t)(kk * 2), idesc, kk > 0 ? 1u : 0u);
+  }
 }
 
 // Writes one sample row of an E4M3 A tile (one byte per column, 128-byte swizzled rows), two

@@ -187,6 +187,13 @@ MLPS_DEV void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
       : "memory");
 }
 
+// 32 lanes x 8 columns: thread i of the warp writes lane (base lane + i).
+MLPS_DEV void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+
 MLPS_DEV void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------------- MMA
@@ -252,6 +259,18 @@ MLPS_DEV void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t
       : "memory");
 }
 
+// The E4M3 MMA with the A operand in tensor memory: four E4M3 values per 32-bit column along K,
+// so one K = 32 step spans 8 columns.
+MLPS_DEV void mma_e4m3_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Arrive on the mbarrier once all previously issued tcgen05.mma of this thread have completed.
 MLPS_DEV void mma_commit(uint32_t mbar) {
   asm volatile(
@@ -286,6 +305,33 @@ MLPS_DEV uint32_t pack_bf16(float lo, float hi) {
   return d;
 }
 
+// Per-half mask of a BF16 pair: 0xFFFF where the half is nonzero (either sign of zero counts
+// as zero), 0 elsewhere.
+MLPS_DEV uint32_t bf16x2_nonzero(uint32_t h) {
+  uint32_t r;
+  asm("set.ne.u32.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(h), "r"(0u));
+  return r;
+}
+
+// (a, b) += (c, d) as one packed FP32 pair add (round to nearest), the same rounding as two adds.
+MLPS_DEV void add2_f32(float& a, float& b, float c, float d) {
+  asm("{\n\t.reg .b64 x, y;\n\t"
+      "mov.b64 x, {%0, %1};\n\t"
+      "mov.b64 y, {%2, %3};\n\t"
+      "add.rn.f32x2 x, x, y;\n\t"
+      "mov.b64 {%0, %1}, x;\n\t}"
+      : "+f"(a), "+f"(b)
+      : "f"(c), "f"(d));
+}
+
+// Byte offsets of the eight 16-byte chunks of one row of a 128-byte-swizzled tile: chunk c of
+// row r is at r * 128 + ((c ^ (r % 8)) << 4) (see sw128_off). `base` = r * 128, `x` = (r % 8) << 4.
+struct RowSw {
+  uint32_t base, x;
+  MLPS_DEV explicit RowSw(int r) : base((uint32_t)r * 128u), x(((uint32_t)r & 7u) << 4) {}
+  MLPS_DEV uint32_t off(int c) const { return base + (((uint32_t)c << 4) ^ x); }
+};
+
 MLPS_DEV void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
                "r"(d)
@@ -295,6 +341,13 @@ MLPS_DEV void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, ui
 // Two floats to a pair of E4M3 bytes (round to nearest, saturating): `lo` in the low byte.
 MLPS_DEV uint32_t pack_e4m3(float lo, float hi) {
   return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(lo, hi), __NV_SATFINITE, __NV_E4M3);
+}
+
+// ReLU of two floats to a pair of E4M3 bytes (round to nearest, saturating): `lo` in the low byte.
+MLPS_DEV uint32_t pack_e4m3_relu(float lo, float hi) {
+  unsigned short r;
+  asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return (uint32_t)r;
 }
 
 MLPS_DEV void st_shared_u16(uint32_t addr, uint32_t a) {
