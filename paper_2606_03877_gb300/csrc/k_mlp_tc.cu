@@ -62,7 +62,7 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG, bool e4m3, int ipc) {
   L.a_stride = align_up(P.a_bytes, 1024);
   off += L.a_stride * kNEG;
   L.bias = off;  // biases, then (E4M3) the per-output weight scales
-  off = align_up(off + 4 * P.bias_floats * (e4m3 ? 3 : 1), 16);
+  off = align_up(off + 4 * P.bias_floats * (e4m3 ? 3 : 1) + (e4m3 ? 16 : 0), 16);
   L.itab0 = off;
   // two buffers of ipc interval records: the current chunk's and the next chunk's (in flight)
   L.itab_stride = align_up(2 * (uint32_t)sizeof(IntervalRec) * ipc, 16);
@@ -78,9 +78,9 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG, bool e4m3, int ipc) {
 }
 
 // F8: E4M3 operands (kind::f8f6f4). Layer l's A operand holds its input divided by a static
-// power-of-two scale per (primitive, layer) (the encoded input by 1/256), the weights are
-// stored divided by a per-output scale; the packing folds both, and the next layer's scale, into
-// one multiplier and offset per output, so the epilogue is one FMA per value (k_pack_e4m3).
+// power-of-two scale s_l per (primitive, layer), the weights are stored divided by a power of two
+// c_l chosen so that s_{l+1} = s_l c_l, and the bias is one more K step: a hidden layer's
+// accumulator is the next A operand before ReLU and conversion (k_pack_e4m3).
 template <int WIDTH, int XL, int DL, int NF, int kNEG, bool F8>
 __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     k_mlp_fwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
@@ -94,14 +94,13 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
   // BF16 at width 64: every hidden layer's bias is added by one more MMA step (the plan folds
   // all of them); width 128 adds them in the epilogue
   constexpr bool kFold = WIDTH == 64 && !F8;
-  static_assert(kNEG >= 1 && kNEG <= 6 && kNEG * kGCols <= 512, "TMEM holds 512 columns");
+  static_assert(kNEG >= 1 && kNEG <= 6 && kNEG * kGCols + (F8 ? 8 : 0) <= 512, "TMEM holds 512 columns");
   static_assert(4 + NF <= kMaxScanVals, "scan scratch holds kMaxScanVals values per warp");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (sbase - raw);
   const TcSmem L = tc_smem(P, kNEG, F8, w.ipc);
-  constexpr float kInMul = 256.f;  // E4M3 encoded input: values in [-1, 1] stored times 256
   const Model& m = a.m;
   float* sBias = reinterpret_cast<float*>(gbase + L.bias);
   float* sScan = reinterpret_cast<float*>(gbase + L.scan);
@@ -136,6 +135,19 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
+  // E4M3: a constant-1 A operand after the groups' columns (8 columns = one K = 32 step; the
+  // first two elements of every row are 1.0, 0x38), shared by every group's bias step
+  const uint32_t ones_t = tmem + (uint32_t)kNEG * kGCols;
+  if (F8) {
+    if (warp < 4) {
+      const uint32_t o8[8] = {0x00003838u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+      tmem_st8(ones_t + ((uint32_t)(warp * 32) << 16), o8);
+      tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
 
   const int total = w.saved_hdr[2];
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
@@ -177,6 +189,9 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
           if (F8) {
             for (int j = 0; j < P.npad[l] / 16; ++j)
               tma_load_2d(sbase + L.w + P.s8_off[l] + j * 2048, &tmap, 0, row0 + P.g8_row[l] + j * 16, bar_w);
+            if (l == 0)  // the bias tile of the hidden layers
+              for (int r = 0; r < ((nl - 1 + 3) / 4) * WIDTH; r += 16)
+                tma_load_2d(sbase + L.w + P.s8b_off + r * 128, &tmap, 0, row0 + P.g8b_row + r, bar_w);
           } else {
             for (int sl = 0; sl < P.kpad[l] / 64; ++sl)
               for (int j = 0; j < P.npad[l] / 16; ++j)
@@ -193,9 +208,9 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
       const unsigned char* blob = a.weights + (size_t)prim * a.pk.stride;
       const float* gb = reinterpret_cast<const float*>(blob + P.gbias_byte);
       for (int i = threadIdx.x; i < P.bias_floats; i += kThreadsTC) sBias[i] = gb[i];
-      if (F8) {  // the epilogue's multipliers and offsets
+      if (F8) {  // the last layer's multipliers and offsets, then the input multiplier
         const float* gm = reinterpret_cast<const float*>(blob + P.gmul_byte);
-        for (int i = threadIdx.x; i < 2 * P.bias_floats; i += kThreadsTC) sBias[P.bias_floats + i] = gm[i];
+        for (int i = threadIdx.x; i <= 2 * P.bias_floats; i += kThreadsTC) sBias[P.bias_floats + i] = gm[i];
       }
       mbar_wait(bar_w, ph_w, sAbort, kWaitNs);
       ph_w ^= 1;
@@ -226,7 +241,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
             const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
             float xl[3], dd[3];
             for (int u = 0; u < 3; ++u) { xl[u] = fmaf(tr, I.dp[u], I.p[u]); dd[u] = I.d[u]; }
-            encode_e4m3_64<(XL > 0 ? XL : 0), (DL > 0 ? DL : 0)>(xl, dd, kInMul, pk);
+            encode_e4m3_64<(XL > 0 ? XL : 0), (DL > 0 ? DL : 0)>(xl, dd, sBias[3 * P.bias_floats], pk);
           } else {
 #pragma unroll
             for (int e = 0; e < 16; ++e) pk[e] = 0u;
@@ -234,7 +249,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
           tmem_st16(tmem + (uint32_t)g * kGCols + WIDTH + ((uint32_t)(q * 32) << 16), pk);
           tmem_wait_st();
         } else if (F8) {
-          RowWriter8 rw{A, row, 0, 0.f, kInMul};
+          RowWriter8 rw{A, row, 0, 0.f, sBias[3 * P.bias_floats]};
           if (valid && m.contact) {  // the tensor-core blob's order: gamma(delta), then gamma(d)
             const IntervalRec& I = T[iv];
             float del[3];
@@ -319,8 +334,9 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
         if (row == 0) {  // this group issues its own MMAs
           tc_fence_after();
           if (!*sAbort) {
-            if (F8 && kA0T) issue_fwd_layer_e4m3_ta(aT, sbase + L.w + P.s8_off[0], dacc, P.kpad[0], P.npad[0]);
-            else if (F8) issue_fwd_layer_e4m3(A, sbase + L.w + P.s8_off[0], dacc, P.kpad[0], P.npad[0]);
+            const uint32_t bt8 = nl > 1 ? sbase + L.w + P.s8b_off : 0u;  // E4M3 bias step of layer 0
+            if (F8 && kA0T) issue_fwd_layer_e4m3_ta(aT, sbase + L.w + P.s8_off[0], dacc, P.kpad[0], P.npad[0], ones_t, bt8);
+            else if (F8) issue_fwd_layer_e4m3(A, sbase + L.w + P.s8_off[0], dacc, P.kpad[0], P.npad[0], ones_t, bt8);
             else if (kA0T)
               issue_fwd_layer_ta(aT, sbase + L.w + P.sw_off[0], dacc, P.kpad[0], P.npad[0], sbase + L.ones,
                                  P.fold > 0 ? sbase + L.w + P.sbt_off : 0u);
@@ -339,28 +355,18 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
           const float* bias = sBias + P.bias_off[l];
           if (l < nl - 1) {
             if (ok && F8) {
-              // E4M3: z / s_{l+1} = acc * mul_n + add_n (weight and activation scales folded in
-              // by the packing), ReLU and saturation in the conversion; 32 columns (32 bytes of
-              // the row) at a time
-              const float* mulv = sBias + P.bias_floats + P.bias_off[l];
-              const float* addv = sBias + 2 * P.bias_floats + P.bias_off[l];
+              // E4M3: the accumulator already holds z / s_{l+1} (bias included, scales folded in
+              // by the packing): ReLU and conversion (saturating) only, 32 columns at a time
 #pragma unroll
               for (int h32 = 0; h32 < WIDTH / 32; ++h32) {
                 uint32_t v[32];
                 tmem_ld32(trow + h32 * 32, v);
                 tmem_wait_ld();
-                const float4* m4 = reinterpret_cast<const float4*>(mulv + h32 * 32);
-                const float4* a4 = reinterpret_cast<const float4*>(addv + h32 * 32);
                 uint32_t pk[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                  const float4 mq = m4[e], aq = a4[e];
-                  const float y0 = fmaf(__uint_as_float(v[4 * e]), mq.x, aq.x);
-                  const float y1 = fmaf(__uint_as_float(v[4 * e + 1]), mq.y, aq.y);
-                  const float y2 = fmaf(__uint_as_float(v[4 * e + 2]), mq.z, aq.z);
-                  const float y3 = fmaf(__uint_as_float(v[4 * e + 3]), mq.w, aq.w);
-                  pk[e] = pack_e4m3_relu(y0, y1) | (pack_e4m3_relu(y2, y3) << 16);
-                }
+                for (int e = 0; e < 8; ++e)
+                  pk[e] = pack_e4m3_relu(__uint_as_float(v[4 * e]), __uint_as_float(v[4 * e + 1])) |
+                          (pack_e4m3_relu(__uint_as_float(v[4 * e + 2]), __uint_as_float(v[4 * e + 3])) << 16);
                 tmem_st8(arow + (uint32_t)(h32 * 8), pk);
               }
               tmem_wait_st();
@@ -405,7 +411,11 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
             if (row == 0) {
               tc_fence_after();
               if (!*sAbort) {
-                if (F8) issue_fwd_layer_e4m3_ta(aT, sbase + L.w + P.s8_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1]);
+                if (F8)
+                  issue_fwd_layer_e4m3_ta(aT, sbase + L.w + P.s8_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1], ones_t,
+                                          l + 2 < nl ? sbase + L.w + P.s8b_off + (uint32_t)(((l + 1) >> 2) * WIDTH * 128) +
+                                                           32u * ((l + 1) & 3)
+                                                     : 0u);
                 else issue_fwd_layer_ta(aT, sbase + L.w + P.sw_off[l + 1], dacc, P.kpad[l + 1], P.npad[l + 1],
                                         sbase + L.ones,
                                         l + 1 < P.fold ? sbase + L.w + P.sbt_off + 8192u * ((l + 1) >> 2) + 32u * ((l + 1) & 3)
@@ -529,18 +539,21 @@ __global__ void k_pack_bf16(Model m, TcPlan P, long long stride, int K, const fl
   }
 }
 
-// E4M3 copy of the weights and the epilogue's affine maps (FP8 precision), one block of 128
-// threads per primitive.
-//  * Weights: output n of layer l is stored as W[n][k] / c_n with c_n = max_k |W[n][k]| / 448.
-//  * Activation scales: the A operand of layer l holds its input divided by a power of two s_l,
-//    fixed per (primitive, layer): s_0 = 1/256 (encoded inputs lie in [-1, 1]); for l >= 1 the
-//    smallest power of two with 4 a_l / s_l <= 448, a_l the largest input of layer l met when
-//    the block evaluates the primitive's FP32 MLP on 256 probe inputs (local positions
-//    uniform in [-1, 1]^3, directions on the unit sphere, from a fixed integer hash). Values
-//    beyond the 4x headroom saturate at 448 s_l.
-//  * Epilogue of layer l: z / s_{l+1} = acc (s_l c_n / s_{l+1}) + b_n / s_{l+1}, i.e. mul_n and
-//    add_n, with s_{l+1} = 1 for the last layer (its outputs stay unscaled). The divisions by
-//    powers of two are exact, so the static scales add no rounding of their own.
+// E4M3 copy of the weights, bias tile and scales (FP8 precision), one block of 128 threads per
+// primitive. Layer l's A operand holds its input divided by a power of two s_l; the stored weights
+// are W_l / c_l with c_l a power of two, so the FP32 accumulator of layer l (the bias added by one
+// more K step) holds z / (s_l c_l). The packing sets s_{l+1} = s_l c_l: the accumulator of a
+// hidden layer is then the next layer's A operand as it stands, and the epilogue only applies
+// ReLU and converts (no multiply, no bias). c_l is the smallest power of two with
+//  * 4 a_{l+1} / (s_l c_l) <= 448, a_{l+1} the largest input of layer l + 1 met when the block
+//    evaluates the primitive's FP32 MLP on 256 probe inputs (local positions uniform in
+//    [-1, 1]^3, directions on the unit sphere, from a fixed integer hash): 4x headroom below the
+//    largest finite E4M3 value, beyond which values saturate;
+//  * max |W_l| / c_l <= 448 (every weight representable), and max |b_l| / s_{l+1} <= 224 (the
+//    bias as hi + lo E4M3 bytes, hi = e4m3(v), lo = e4m3(v - hi)).
+// s_0 = 1/32: the encoded inputs lie in [-1, 1]. The last layer keeps an FP32 epilogue:
+// z = acc * (s_L c_L) + b, c_L = the smallest power of two with max |W_L| / c_L <= 448. Scaling by
+// powers of two is exact, so the scales add no rounding of their own.
 MLPS_DEV uint32_t probe_hash(uint32_t x) {
   x ^= x >> 16;
   x *= 0x7FEB352Du;
@@ -581,28 +594,23 @@ __global__ void __launch_bounds__(128) k_pack_e4m3(Model m, TcPlan P, long long 
   if (p >= K) return;
   const float* s = src + (size_t)p * m.Prow;
   unsigned char* d = dst + (size_t)p * stride;
-  __shared__ float sc[kMaxLayers][128];
-  __shared__ unsigned int amax[kMaxLayers + 1];
-  __shared__ float ascale[kMaxLayers + 1];
+  __shared__ unsigned int amax[kMaxLayers + 1], wmax[kMaxLayers], bmax[kMaxLayers];
+  __shared__ float sl[kMaxLayers + 1], cl[kMaxLayers];
   const int t = threadIdx.x;
+  if (t <= kMaxLayers) amax[t] = 0u;
+  if (t < kMaxLayers) wmax[t] = bmax[t] = 0u;
+  __syncthreads();
+  // largest |W_l| and |b_l| (non-negative floats order as their bits)
   for (int l = 0; l < m.nl; ++l) {
     const int din = m.din[l];
-    for (int n = t; n < P.npad[l]; n += blockDim.x) {
-      const bool live = n < m.dout[l];
+    for (int n = t; n < m.dout[l]; n += blockDim.x) {
       float am = 0.f;
-      if (live)
-        for (int k = 0; k < din; ++k) am = fmaxf(am, fabsf(s[m.woff[l] + n * din + k]));
-      const float c = am > 0.f ? am / 448.f : 1.f;
-      sc[l][n] = c;
-      unsigned char* r = d + (size_t)(P.g8_row[l] + n) * 128;
-      for (int k = 0; k < 128; ++k)
-        r[k] = (live && k < din)
-                   ? __nv_cvt_float_to_fp8(s[m.woff[l] + n * din + tc_in_col(m, l, k)] / c, __NV_SATFINITE, __NV_E4M3)
-                   : 0;
+      for (int k = 0; k < din; ++k) am = fmaxf(am, fabsf(s[m.woff[l] + n * din + k]));
+      atomicMax(&wmax[l], __float_as_uint(am));
+      atomicMax(&bmax[l], __float_as_uint(fabsf(s[m.boff[l] + n])));
     }
   }
-  if (t <= kMaxLayers) amax[t] = 0u;
-  __syncthreads();
+  // calibration: the largest input of every hidden layer's successor on the probes
   float hin[128], hout[128];
   for (int probe = 0; probe < 2; ++probe) {
     uint32_t st = probe_hash(((uint32_t)p * 256u + (uint32_t)(2 * t + probe)) * 2654435761u + 12345u);
@@ -636,27 +644,69 @@ __global__ void __launch_bounds__(128) k_pack_e4m3(Model m, TcPlan P, long long 
         hout[n] = z;
         mx = fmaxf(mx, z);
       }
-      atomicMax(&amax[l + 1], __float_as_uint(mx));  // non-negative floats order as their bits
+      atomicMax(&amax[l + 1], __float_as_uint(mx));
       for (int n = 0; n < dout; ++n) hin[n] = hout[n];
     }
   }
   __syncthreads();
-  if (t <= m.nl) {
-    float sl = 1.0f / 256.0f;
-    if (t >= 1 && t < m.nl) sl = pow2_at_least(4.0f * __uint_as_float(amax[t]) / 448.0f);
-    if (t == m.nl) sl = 1.0f;  // the last layer's outputs
-    ascale[t] = sl;
+  if (t == 0) {  // the scale chain (sequential: s_{l+1} = s_l c_l)
+    sl[0] = 1.0f / 32.0f;
+    for (int l = 0; l < m.nl; ++l) {
+      const float wm = __uint_as_float(wmax[l]);
+      float c = pow2_at_least(wm / 448.0f);
+      if (l + 1 < m.nl) {
+        c = fmaxf(c, pow2_at_least(4.0f * __uint_as_float(amax[l + 1]) / (448.0f * sl[l])));
+        const float bm = __uint_as_float(bmax[l]);
+        for (int it = 0; it < 64 && bm / (sl[l] * c) > 224.0f; ++it) c *= 2.0f;
+      }
+      cl[l] = c;
+      sl[l + 1] = sl[l] * c;
+    }
   }
   __syncthreads();
-  float* mul = reinterpret_cast<float*>(d + P.gmul_byte);
-  float* add = reinterpret_cast<float*>(d + P.gadd_byte);
-  for (int l = 0; l < m.nl; ++l)
+  for (int l = 0; l < m.nl; ++l) {
+    const int din = m.din[l];
+    const float ic = 1.0f / cl[l];
     for (int n = t; n < P.npad[l]; n += blockDim.x) {
       const bool live = n < m.dout[l];
-      const float so = ascale[l + 1];
-      mul[P.bias_off[l] + n] = live ? ascale[l] * sc[l][n] / so : 0.f;
-      add[P.bias_off[l] + n] = live ? s[m.boff[l] + n] / so : 0.f;
+      unsigned char* r = d + (size_t)(P.g8_row[l] + n) * 128;
+      for (int k = 0; k < 128; ++k)
+        r[k] = (live && k < din)
+                   ? __nv_cvt_float_to_fp8(s[m.woff[l] + n * din + tc_in_col(m, l, k)] * ic, __NV_SATFINITE, __NV_E4M3)
+                   : 0;
     }
+  }
+  // bias tile of the hidden layers: rows n < the (padded) hidden width, slab l / 4, bytes
+  // 32 (l % 4) and 32 (l % 4) + 1; rows of padded units stay zero
+  const int nsl8 = (m.nl - 1 + 3) / 4, wrows = P.npad[0];
+  for (int i = t; i < nsl8 * wrows; i += blockDim.x) {
+    const int sl_ = i / wrows, n = i - sl_ * wrows;
+    unsigned char* r = d + (size_t)(P.g8b_row + i) * 128;
+    for (int k = 0; k < 128; ++k) r[k] = 0;
+    for (int j = 0; j < 4; ++j) {
+      const int l = 4 * sl_ + j;
+      if (l + 1 >= m.nl || n >= m.dout[l]) continue;
+      const float v = s[m.boff[l] + n] / sl[l + 1];
+      const __nv_fp8_storage_t hi = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+      const float hv = __half2float(__half(__nv_cvt_fp8_to_halfraw(hi, __NV_E4M3)));
+      r[32 * j] = hi;
+      r[32 * j + 1] = __nv_cvt_float_to_fp8(v - hv, __NV_SATFINITE, __NV_E4M3);
+    }
+  }
+  // last layer's FP32 epilogue, and the input multiplier
+  float* mul = reinterpret_cast<float*>(d + P.gmul_byte);
+  float* add = reinterpret_cast<float*>(d + P.gadd_byte);
+  const int L = m.nl - 1;
+  for (int n = t; n < P.bias_floats; n += blockDim.x) {
+    mul[n] = 0.f;
+    add[n] = 0.f;
+  }
+  __syncthreads();
+  for (int n = t; n < m.dout[L]; n += blockDim.x) {
+    mul[P.bias_off[L] + n] = sl[L] * cl[L];
+    add[P.bias_off[L] + n] = s[m.boff[L] + n];
+  }
+  if (t == 0) *reinterpret_cast<float*>(d + P.gin_byte) = 1.0f / sl[0];
 }
 
 }  // namespace tc
@@ -708,10 +758,16 @@ bool tc_plan(const Model& m, TcPlan* P, long long* stride, bool e4m3) {
       P->s8_off[l] = s8;
       s8 += P->npad[l] * 128;
     }
+    const int nsl8 = (m.nl - 1 + 3) / 4;  // bias slabs of the hidden layers
+    P->g8b_row = r8;
+    r8 += m.width * nsl8;
+    P->s8b_off = s8;
+    s8 += m.width * 128 * nsl8;
     P->w8_bytes = s8;
     P->gmul_byte = r8 * 128;
     P->gadd_byte = r8 * 128 + 4 * bias;
-    bytes = (long long)r8 * 128 + 8LL * bias;
+    P->gin_byte = r8 * 128 + 8 * bias;
+    bytes = (long long)r8 * 128 + 8LL * bias + 16;
   }
   if (m.C > 0) {  // FP32 slot embeddings [4][C] after everything the MLP kernels read
     bytes = (bytes + 15) / 16 * 16;

@@ -56,15 +56,20 @@ struct TcPlan {
   int gbt_row;                             // first 128-byte row of the bias tile in a blob
   int sbt_off;                             // its shared-memory byte offset (after the W tiles)
   int bt_bytes;                            // 8192 per slab when fold > 0
-  // E4M3 copy (FP8 precision only; w8_bytes = 0 otherwise): layer l's tile W [npad][kpad] as
-  // one 128-byte row per output (kpad <= 128), then per output n of layer l the FP32 affine map
-  // of the epilogue, z' = acc * mul_n + add_n, into which the packing folds the weight scale of
-  // output n and the static activation scales of the layer's input and output
+  // E4M3 copy (FP8 precision only; w8_bytes = 0 otherwise): layer l's tile W [npad][kpad] / c_l
+  // as one 128-byte row per output (kpad <= 128); then a bias tile for the hidden layers (rows =
+  // hidden width, 64-column slabs: layer l's bias b / s_{l+1} as two E4M3 bytes hi + lo in
+  // columns 32 (l % 4) and 32 (l % 4) + 1 of slab l / 4), added by one more K step against a
+  // constant-1 operand; then FP32 mul_n / add_n of the last layer's epilogue (z = acc * mul + add,
+  // bias_off indexing) and the input multiplier 1 / s_0. k_pack_e4m3 chooses the scales.
   int g8_row[kMaxLayers];                  // first 128-byte row of layer l's E4M3 tile in a blob
   int s8_off[kMaxLayers];                  // shared-memory byte offset of layer l's E4M3 tile
-  int w8_bytes;                            // all E4M3 tiles
+  int g8b_row;                             // first 128-byte row of the E4M3 bias tile
+  int s8b_off;                             // its shared-memory byte offset
+  int w8_bytes;                            // all E4M3 tiles, the bias tile included
   int gmul_byte;                           // byte offset of the FP32 multipliers (bias_off indexing)
   int gadd_byte;                           // byte offset of the FP32 offsets (bias_off indexing)
+  int gin_byte;                            // byte offset of the FP32 input multiplier 1 / s_0
   int bias_off[kMaxLayers];                // float offset of layer l's bias
   int bias_floats;
   int gbias_byte;                          // byte offset of the FP32 biases in a blob

@@ -166,7 +166,8 @@ MLPS_DEV void issue_fwd_layer_ta(uint32_t At, uint32_t W, uint32_t d, int kpad, 
 
 // FP8 (E4M3) forward layer: same operand tiles (128-byte K-major swizzled rows, here holding up
 // to 128 one-byte elements), K = 32 per instruction; kpad <= 128.
-MLPS_DEV void issue_fwd_layer_e4m3(uint32_t A, uint32_t W, uint32_t d, int kpad, int npad) {
+MLPS_DEV void issue_fwd_layer_e4m3(uint32_t A, uint32_t W, uint32_t d, int kpad, int npad, uint32_t ones = 0u,
+                                   uint32_t bt = 0u) {
   const uint32_t idesc = idesc_e4m3(kM, npad);
   const uint64_t da = sw128_desc(A), db = sw128_desc(W);
   const int nk = kpad / 32;
@@ -175,11 +176,16 @@ MLPS_DEV void issue_fwd_layer_e4m3(uint32_t A, uint32_t W, uint32_t d, int kpad,
     if (kk >= nk) break;
     mma_e4m3(d, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, kk > 0 ? 1u : 0u);
   }
+  if (bt) mma_e4m3_ta(d, ones, sw128_desc(bt), idesc, 1u);
 }
 
 // E4M3 layer with the A operand in tensor memory (`At`: lane = sample row, four E4M3 values per
 // column, 8 columns per K = 32 step).
-MLPS_DEV void issue_fwd_layer_e4m3_ta(uint32_t At, uint32_t W, uint32_t d, int kpad, int npad) {
+// With `bt` nonzero one more K step adds the layer's bias: A = the constant-1 operand `ones` in
+// TMEM (1.0 in the first two elements of every row), B = the K step of the bias tile that holds
+// the layer's bias as hi and lo bytes in its first two columns.
+MLPS_DEV void issue_fwd_layer_e4m3_ta(uint32_t At, uint32_t W, uint32_t d, int kpad, int npad, uint32_t ones = 0u,
+                                      uint32_t bt = 0u) {
   const uint32_t idesc = idesc_e4m3(kM, npad);
   const uint64_t db = sw128_desc(W);
   const int nk = kpad / 32;
@@ -188,6 +194,7 @@ MLPS_DEV void issue_fwd_layer_e4m3_ta(uint32_t At, uint32_t W, uint32_t d, int k
     if (kk >= nk) break;
     mma_e4m3_ta(d, At + 8u * (uint32_t)kk, db + (uint64_t)(kk * 2), idesc, kk > 0 ? 1u : 0u);
   }
+  if (bt) mma_e4m3_ta(d, ones, sw128_desc(bt), idesc, 1u);
 }
 
 // Writes one sample row of an E4M3 A tile (one byte per column, 128-byte swizzled rows), two
