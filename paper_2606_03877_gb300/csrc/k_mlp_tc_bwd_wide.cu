@@ -1,0 +1,730 @@
+// k_mlp_tc_bwd_wide.cu -- BF16 tensor-core (tcgen05) backward of the grouped per-primitive MLP
+// at hidden width 128 (the stress configuration: 60 -> 128 x 4 -> 4 + 16).
+//
+// What does not fit on chip at this width, and how the kernel gets around it:
+//  * Weight gradients: four 128 x 128 layers and the head need 544 TMEM columns, more than the
+//    512 of an SM. Each layer's gradient is accumulated in one TMEM region for one chunk only
+//    and then added into the block's FP32 copy in global memory (L2-resident, laid out
+//    [input][output] per layer so that a thread adds one contiguous row with vector
+//    reductions); the copy goes into d_weights when the block's primitive changes.
+//  * Activations: the resident weights take 120 KB of shared memory, so only one H tile, one
+//    delta tile and the encoded input fit next to them. H_l, needed by wgrad_l and by the ReLU
+//    mask of delta_{l-1}, is recomputed from the input when phase B_l comes (recompute on
+//    demand); the next dgrad result waits in registers as BF16 pairs meanwhile.
+//  * Bias gradients: every input row of the wgrad accumulator is a feature, so the sum of
+//    delta_l over the rows is one more MMA: A = delta_l read as an MN-major operand (M = the
+//    outputs), B = a constant K-major operand whose first row is all ones (N = 16).
+// One epilogue group (4 warps, thread = sample row) per SM walks its range of the
+// primitive-major chunk list. Per chunk: encode X into shared memory; forward to the head with
+// activations in TMEM (A operand); reverse of the interval composite (Eq. 6) into delta of the
+// head; then for l = L .. 1: flush dW_l, delta_{l-1} = G_l * [H_l > 0], dgrad_{l-1}, recompute
+// H_{l-1}, wgrad_{l-1} and its bias sum; finally the encoding derivative and the pose chain
+// (as in k_mlp_tc_bwd.cu). Every wait is bounded by wall time; after a timeout the kernel runs
+// out its chunks without issuing MMAs, frees TMEM and reports MLPS_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "mlps_common.cuh"
+#include "mlps_kernels.h"
+#include "simt_common.cuh"
+#include "tc_bwd_common.cuh"
+#include "tc_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace mlps {
+namespace tc {
+
+namespace {
+
+constexpr int kWThreads = kEGThreads;          // one epilogue group
+constexpr uint32_t kSlab = kM * 128;           // one 64-column slab of 128 rows (16 KB)
+constexpr uint32_t kOnesMN = 2048;             // 16 rows of the MN-major ones atom (one K step)
+constexpr uint32_t kOnesK = 2048;              // K-major ones operand: 16 rows, the first all ones
+constexpr uint64_t kWaitNsW = 2000000000ull;
+// TMEM columns: accumulator (forward / dgrad), A operand (BF16 pairs), weight gradient, bias sums
+constexpr uint32_t kColD = 0, kColA = 128, kColR = 256, kColRb = 384, kTmemColsW = 512;
+
+struct WideSmem {
+  uint32_t w, xt, ht, dt, ones_mn, ones_k, bias, itab, giv, ddel, gf, scan, geo, pgeo, bars, misc, total;
+};
+
+MLPS_HD uint32_t alw(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+MLPS_HD WideSmem wide_layout(const TcPlan& P, int F, int ipc) {
+  WideSmem L;
+  uint32_t o = 0;
+  L.w = o;
+  o = alw(o + P.w_bytes, 1024);
+  L.xt = o;  // encoded input X: one slab (kpad0 = 64)
+  o += kSlab;
+  L.ht = o;  // H_l: two slabs
+  o += 2 * kSlab;
+  L.dt = o;  // delta_l: two slabs
+  o += 2 * kSlab;
+  L.ones_mn = o;  // after the X tile's reach: wgrad_0 finds it at a positive offset
+  o = alw(o + kOnesMN, 1024);
+  L.ones_k = o;
+  o = alw(o + kOnesK, 1024);
+  L.bias = o;
+  o = alw(o + 4 * P.bias_floats, 16);
+  L.itab = o;
+  o = alw(o + (uint32_t)sizeof(IntervalRec) * ipc, 16);
+  L.giv = o;
+  o = alw(o + 16 * ipc, 16);
+  L.ddel = o;
+  o = alw(o + 4 * ipc, 16);
+  L.gf = o;
+  o = alw(o + 4 * ipc * (F > 0 ? F : 1), 16);
+  L.scan = o;  // 4 warps x the widest segmented scan (3 + F values, or 6)
+  o = alw(o + 4 * 4 * (3 + (F > 3 ? F : 3)), 16);
+  L.geo = o;
+  o = alw(o + 4 * 16, 16);
+  L.pgeo = o;
+  o = alw(o + (uint32_t)sizeof(PrimGeo), 16);
+  L.bars = o;
+  o = alw(o + 8 * 4, 16);
+  L.misc = o;
+  o = alw(o + 16, 16);
+  L.total = o;
+  return L;
+}
+
+// dgrad G = delta W_l (M = rows, N = nin inputs, K = nout outputs): A = delta in TMEM (8 columns
+// per K = 16 step), B = the forward W_l tile read MN-major, its 64-input slabs `slab` bytes apart.
+MLPS_DEV void issue_dgrad_w(uint32_t At, uint32_t wtile, uint32_t d, int nin, int nout, uint32_t slab) {
+  const uint32_t id = idesc_bf16(kM, nin) | (1u << 16);
+  const uint64_t db = sw128_desc_mn(wtile, slab);
+  const int nk = nout / 16;
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    if (kk >= nk) break;
+    mma_bf16_ta(d, At + 8u * (uint32_t)kk, db + (uint64_t)(kk * 128), id, kk > 0 ? 1u : 0u);
+  }
+}
+
+// wgrad dW_l^T [inputs][outputs] = H_l^T delta_l over the chunk's 128 rows (K), overwriting the
+// region: A = H_l (M = 128 inputs, two slabs), B = delta_l (N = nout, slabs 16 KB apart), both
+// MN-major views of the row-major tiles.
+MLPS_DEV void issue_wgrad_w(uint32_t H, uint32_t Dt, uint32_t R, int nout) {
+  const uint32_t id = idesc_bf16(kM, nout) | (1u << 15) | (1u << 16);
+  const uint64_t da = sw128_desc_mn(H, kSlab), db = sw128_desc_mn(Dt, kSlab);
+#pragma unroll
+  for (int kk = 0; kk < kM / 16; ++kk) mma_bf16(R, da + (uint64_t)(kk * 128), db + (uint64_t)(kk * 128), id, kk > 0);
+}
+
+// wgrad of the first layer (64 inputs): A = [X | ones atom] (row 64 of the accumulator is the
+// bias gradient; the ones atom's offset shrinks by one K step per step, so one 16-row block
+// serves them all), B = delta_0 as above.
+MLPS_DEV void issue_wgrad_w0(uint32_t X, uint32_t Dt, uint32_t R, uint32_t ones, int nout) {
+  const uint32_t id = idesc_bf16(kM, nout) | (1u << 15) | (1u << 16);
+  const uint64_t da = sw128_desc_mn(X, ones - X), db = sw128_desc_mn(Dt, kSlab);
+#pragma unroll
+  for (int kk = 0; kk < kM / 16; ++kk) {
+    const uint64_t step = (uint64_t)(kk * 128);
+    mma_bf16(R, da + step - (step << 16), db + step, id, kk > 0);
+  }
+}
+
+// Bias sums: Rb[out][0] = sum over the rows of delta[row][out]: A = delta (M = 128 outputs,
+// MN-major, two slabs), B = the K-major ones operand (N = 16, its first row all ones; the same
+// 16 K values serve every step, so its descriptor does not move).
+MLPS_DEV void issue_bias_w(uint32_t Dt, uint32_t onesK, uint32_t Rb) {
+  const uint32_t id = idesc_bf16(kM, 16) | (1u << 15);
+  const uint64_t da = sw128_desc_mn(Dt, kSlab), db = sw128_desc(onesK);
+#pragma unroll
+  for (int kk = 0; kk < kM / 16; ++kk) mma_bf16(Rb, da + (uint64_t)(kk * 128), db, id, kk > 0);
+}
+
+// Four floats added to global memory without return (16-byte aligned address).
+MLPS_DEV void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+// Store / load one row of a two-slab (128-column) tile: pk[0..31] = columns 0..63 (slab 0),
+// pk[32..63] = columns 64..127 (slab 1).
+MLPS_DEV void store_row128(uint32_t tile, int row, const uint32_t (&pk)[64]) {
+  const RowSw sw(row);
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch)
+      st_shared_v4(tile + (uint32_t)s * kSlab + sw.off(ch), pk[32 * s + 4 * ch], pk[32 * s + 4 * ch + 1],
+                   pk[32 * s + 4 * ch + 2], pk[32 * s + 4 * ch + 3]);
+}
+
+}  // namespace
+
+template <int NF, int XL, int DL>
+__global__ void __launch_bounds__(kWThreads, 1)
+    k_mlp_bwd_tc_wide(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
+  static_assert(4 + NF <= 32 && NF % 2 == 0, "the head's outputs lie in the first 32 columns");
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  uint8_t* gb = smem_raw + (sbase - raw);
+  const Model& m = a.m;
+  const int F = m.F, nl = m.nl, S = m.S, L = m.nl - 1;  // L: the head layer
+  const WideSmem Lw = wide_layout(P, 32, w.ipc);  // the host sizes the same layout
+  float* sBias = reinterpret_cast<float*>(gb + Lw.bias);
+  float* sScan = reinterpret_cast<float*>(gb + Lw.scan);
+  float* sGeo = reinterpret_cast<float*>(gb + Lw.geo);
+  const uint32_t bar_w = sbase + Lw.bars, bar_m = bar_w + 8u, bar_e = bar_w + 16u;
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(gb + Lw.misc);
+  volatile int* sAbort = reinterpret_cast<volatile int*>(gb + Lw.misc + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = threadIdx.x;  // sample row of the chunk, TMEM lane
+  const bool issuer = row == 0;
+  const uint32_t xt = sbase + Lw.xt, ht = sbase + Lw.ht, dt = sbase + Lw.dt;
+  const uint32_t ones_mn = sbase + Lw.ones_mn, ones_k = sbase + Lw.ones_k;
+  constexpr int kScanNV = 3 + (NF > 3 ? NF : 3);
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar_w, 1);
+    mbar_init(bar_m, 1);
+    mbar_init(bar_e, 1);
+    *sAbort = 0;
+    fence_mbar_init();
+  }
+  // MN-major ones atom: element 0 of every row is 1.0 (BF16 0x3F80); K-major ones operand: the
+  // first of its 16 rows is all ones (the swizzle leaves row 0 in place)
+  for (int i = threadIdx.x; i < (int)(kOnesMN / 16); i += kWThreads) {
+    const int r = i >> 3, ch = i & 7;
+    st_shared_v4(ones_mn + (uint32_t)i * 16, ((ch ^ (r & 7)) == 0) ? 0x3F80u : 0u, 0u, 0u, 0u);
+    const uint32_t o = r == 0 ? 0x3F803F80u : 0u;
+    st_shared_v4(ones_k + (uint32_t)i * 16, o, o, o, o);
+  }
+  if (threadIdx.x < 16) sGeo[threadIdx.x] = 0.f;
+  fence_proxy_async_smem();
+  if (warp == 0) {
+    tmem_alloc(sbase + Lw.misc, kTmemColsW);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+  const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+  const uint32_t tD = tmem + kColD, tA = tmem + kColA, tR = tmem + kColR, tRb = tmem + kColRb;
+
+  const int total = w.saved_hdr[2];
+  const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
+  const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
+  float* dwb = w.dwb + (size_t)blockIdx.x * m.P;  // this block's dW copy: per layer [in][out]
+  uint32_t ph_w = 0, ph_m = 0;
+  float geo_acc = 0.f;  // pose output `lane` (< 12) of the current primitive, this warp's share
+  const float invS = 1.f / (float)S;
+  int loaded = -1;
+
+  // the next completion of this thread's MMAs (every thread waits: tcgen05.ld is warp-wide)
+  auto wait_m = [&]() -> bool {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_m, ph_m, sAbort, kWaitNsW));
+    ph_m ^= 1u;
+    tc_fence_after();
+    return ok;
+  };
+  auto commit_m = [&]() {
+    if (issuer) mma_commit(bar_m);
+  };
+  // the block's copy of primitive p's gradients into d_weights (canonical layout), then zeroed
+  auto flush_prim = [&](int p) {
+    __threadfence_block();  // the block's reductions into its copy before the reads below
+    __syncthreads();
+    float* dW = a.d_weights + (size_t)p * m.Prow;
+    for (int l = 0; l < nl; ++l) {
+      const int din = m.din[l], dout = m.dout[l];
+      // (the copy is updated by reductions at L2: read and clear it there, past the L1)
+      for (int i = threadIdx.x; i < din * dout; i += kWThreads) {
+        const int k = i / dout, n = i - k * dout;  // copy layout [in][out]
+        const float v = __ldcg(dwb + m.woff[l] + i);
+        if (v != 0.f) {
+          atomicAdd(&dW[m.woff[l] + n * din + k], v);
+          __stcg(dwb + m.woff[l] + i, 0.f);
+        }
+      }
+      for (int n = threadIdx.x; n < dout; n += kWThreads) {
+        const float v = __ldcg(dwb + m.boff[l] + n);
+        if (v != 0.f) {
+          atomicAdd(&dW[m.boff[l] + n], v);
+          __stcg(dwb + m.boff[l] + n, 0.f);
+        }
+      }
+    }
+    if (geo_acc != 0.f) atomicAdd(&sGeo[lane], geo_acc);
+    geo_acc = 0.f;
+    __syncthreads();
+    if (threadIdx.x < 12) {
+      const float v = sGeo[threadIdx.x];
+      if (v != 0.f) atomicAdd(&w.dgeo[12 * (size_t)p + threadIdx.x], v);
+      sGeo[threadIdx.x] = 0.f;
+    }
+    __syncthreads();
+  };
+  // chunk gradient of layer l (region R: input row = lane, outputs along the columns; layer 0's
+  // bias gradient in row 64; other layers' in Rb) into the block's copy
+  auto flush_layer = [&](int l) {
+    const int din = m.din[l], dout = m.dout[l];
+    float* cp = dwb + m.woff[l];
+    for (int c0 = 0; c0 < P.npad[l]; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tR + (uint32_t)c0 + lanes, v);
+      tmem_wait_ld();
+      if (*sAbort) continue;
+      if (row < din) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          if (c0 + j < dout)
+            red_add_v4(cp + (size_t)row * dout + c0 + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                       __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+      } else if (l == 0 && row == 64) {
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < dout) atomicAdd(&dwb[m.boff[0] + c0 + j], __uint_as_float(v[j]));
+      }
+    }
+    if (l > 0) {
+      uint32_t v16[16];
+      tmem_ld16(tRb + lanes, v16);
+      tmem_wait_ld();
+      if (!*sAbort && row < dout) atomicAdd(&dwb[m.boff[l] + row], __uint_as_float(v16[0]));
+    }
+    tc_fence_before();
+  };
+
+  IntervalRec* T = reinterpret_cast<IntervalRec*>(gb + Lw.itab);
+  float4* GI = reinterpret_cast<float4*>(gb + Lw.giv);
+  float* DD = reinterpret_cast<float*>(gb + Lw.ddel);
+  float* GF = reinterpret_cast<float*>(gb + Lw.gf);
+  const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + Lw.pgeo);
+  int prim = cb < ce ? simt::find_prim(w, cb) : 0;
+
+  for (int c = cb; c < ce; ++c) {
+    while (c >= w.chunk_start[prim + 1]) ++prim;
+    if (prim != loaded) {
+      if (loaded >= 0) flush_prim(loaded);
+      if (threadIdx.x == 0 && !*sAbort) {
+        mbar_arrive_expect_tx(bar_w, (uint32_t)P.w_bytes);
+        const int row0 = prim * P.rows_per_prim;
+        for (int l = 0; l < nl; ++l)
+          for (int sl = 0; sl < P.kpad[l] / 64; ++sl)
+            for (int j = 0; j < P.npad[l] / 16; ++j)
+              tma_load_2d(sbase + Lw.w + P.sw_off[l] + sl * P.npad[l] * 128 + j * 2048, &tmap, 0,
+                          row0 + P.gw_row[l] + sl * P.npad[l] + j * 16, bar_w);
+      }
+      const float* gbias = reinterpret_cast<const float*>(a.weights + (size_t)prim * a.pk.stride + P.gbias_byte);
+      for (int i = threadIdx.x; i < P.bias_floats; i += kWThreads) sBias[i] = gbias[i];
+      {
+        const int* src = reinterpret_cast<const int*>(w.geo + prim);
+        int* dst = reinterpret_cast<int*>(gb + Lw.pgeo);
+        for (int i = threadIdx.x; i < (int)(sizeof(PrimGeo) / 4); i += kWThreads) dst[i] = src[i];
+      }
+      mbar_wait(bar_w, ph_w, sAbort, kWaitNsW);
+      ph_w ^= 1;
+      __syncthreads();
+      loaded = prim;
+    }
+    // ---------------- the chunk's interval records and their gradients
+    const int first = (c - w.chunk_start[prim]) * w.ipc;
+    const int nint = min(w.ipc, w.prim_count[prim] - first);
+    __syncthreads();  // the previous chunk is done with the tables
+    for (int i = threadIdx.x; i < nint; i += kWThreads) {
+      const size_t slot = (size_t)w.prim_start[prim] + first + i;
+      T[i] = w.rec[slot];
+      GI[i] = w.hit_grad[slot];
+      for (int f = 0; f < F; ++f) GF[i * F + f] = w.hit_gfeat[slot * F + f];
+    }
+    __syncthreads();
+    const int iv = row / S, k = row - iv * S;
+    const bool valid = iv < nint;
+    const uint32_t vmask = valid ? 0xFFFFFFFFu : 0u;
+    const uint32_t trow = tD + lanes, arow = tA + lanes;
+
+    // ---------------- X into its tile, layer 0 of the recompute
+    {
+      uint32_t pk[32];
+      encode_row64<XL, DL>(T, nint, S, row, pk);
+      store_row64(xt, row, pk);
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (issuer) {
+      tc_fence_after();
+      if (!*sAbort) issue_fwd_layer(xt, sbase + Lw.w + P.sw_off[0], tD, P.kpad[0], P.npad[0]);
+    }
+    commit_m();
+    // epilogue of hidden layer l: H_{l+1} = ReLU(Z_l + b_l) as BF16 pairs, into the TMEM A
+    // operand (to_tmem) and / or the H tile (to_tile)
+    auto hidden_epilogue = [&](int l, bool to_tmem, bool to_tile) {
+      (void)wait_m();
+      const float* bias = sBias + P.bias_off[l];
+      uint32_t pk[64];
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        uint32_t v[32];
+        tmem_ld32(trow + 32u * q4, v);
+        tmem_wait_ld();
+        const float4* b4 = reinterpret_cast<const float4*>(bias + 32 * q4);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float4 bq = b4[e];
+          float x0 = __uint_as_float(v[4 * e]), x1 = __uint_as_float(v[4 * e + 1]);
+          float x2 = __uint_as_float(v[4 * e + 2]), x3 = __uint_as_float(v[4 * e + 3]);
+          add2_f32(x0, x1, bq.x, bq.y);
+          add2_f32(x2, x3, bq.z, bq.w);
+          pk[16 * q4 + 2 * e] = pack_bf16_relu(x0, x1);
+          pk[16 * q4 + 2 * e + 1] = pack_bf16_relu(x2, x3);
+        }
+      }
+      tc_fence_before();
+      if (to_tmem) {
+        uint32_t h0[32], h1[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          h0[e] = pk[e];
+          h1[e] = pk[32 + e];
+        }
+        tmem_st32(arow, h0);
+        tmem_st32(arow + 32, h1);
+        tmem_wait_st();
+      }
+      if (to_tile) {
+        store_row128(ht, row, pk);
+        fence_proxy_async_smem();
+      }
+    };
+    // recompute through hidden layer `upto` (H_{upto+1} ends in the H tile); layer 0's MMA is
+    // already issued
+    auto recompute_to = [&](int upto) {
+      for (int l = 0; l <= upto; ++l) {
+        hidden_epilogue(l, l < upto, l == upto);
+        tc_fence_before();
+        __syncthreads();
+        if (l < upto) {
+          if (issuer) {
+            tc_fence_after();
+            if (!*sAbort) issue_fwd_layer_ta(tA, sbase + Lw.w + P.sw_off[l + 1], tD, P.kpad[l + 1], P.npad[l + 1]);
+          }
+          commit_m();
+        }
+      }
+    };
+
+    // ---------------- forward to the head: H_1 .. H_L in TMEM, H_L also in the H tile
+    for (int l = 0; l < L; ++l) {
+      hidden_epilogue(l, true, l == L - 1);
+      tc_fence_before();
+      __syncthreads();
+      if (issuer) {
+        tc_fence_after();
+        if (!*sAbort) issue_fwd_layer_ta(tA, sbase + Lw.w + P.sw_off[l + 1], tD, P.kpad[l + 1], P.npad[l + 1]);
+      }
+      commit_m();
+    }
+    // ---------------- heads and reverse of the interval composite (Eq. 6) -> delta_L
+    (void)wait_m();
+    {
+      float z[4 + NF];
+      {
+        uint32_t r32[32];
+        tmem_ld32(trow, r32);
+        tmem_wait_ld();
+        const float* bias = sBias + P.bias_off[L];
+#pragma unroll
+        for (int j = 0; j < 4 + NF; ++j) z[j] = j < m.nout ? __uint_as_float(r32[j]) + bias[j] : 0.f;
+      }
+      tc_fence_before();
+      const IntervalRec& I = T[valid ? iv : 0];
+      const float dtv = valid ? I.dt : 0.f;
+      const float sig = softplus_fast(z[3]);
+      const float ak = valid ? sig * dtv : 0.f;
+      float sc1[1] = {ak};
+      seg_scan<1>(sc1, 1, row, S, sScan, 1);
+      const float Aex = sc1[0] - ak;
+      const float tau = __expf(-Aex), ea = __expf(-ak);
+      const float wk = valid ? tau * (1.f - ea) : 0.f;
+      float cq[3];
+      for (int u = 0; u < 3; ++u) cq[u] = sigmoid_fast(z[u]);
+      float sv[3 + NF];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) sv[u] = wk * cq[u];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) sv[3 + f] = f < F ? wk * z[4 + f] : 0.f;
+      seg_scan_rev<3 + NF>(sv, 3 + F, row, S, sScan, 1);
+      const float4 gI = valid ? GI[iv] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float gcs[3] = {gI.x, gI.y, gI.z};
+      float dLda = gI.w;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) dLda += gcs[u] * (tau * ea * cq[u] - (sv[u] - wk * cq[u]));
+      float dz[4 + NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const float gf = (valid && f < F) ? GF[iv * F + f] : 0.f;
+        const float fk = z[4 + f];
+        dLda += gf * (tau * ea * fk - (sv[3 + f] - wk * fk));
+        dz[4 + f] = wk * gf;
+      }
+#pragma unroll
+      for (int u = 0; u < 3; ++u) dz[u] = wk * gcs[u] * cq[u] * (1.f - cq[u]);
+      dz[3] = valid ? dLda * dtv * sigmoid_fast(z[3]) : 0.f;
+      float dd[1] = {valid ? sig * dLda : 0.f};
+      seg_scan<1>(dd, 1, row, S, sScan, 1);
+      if (valid && k == S - 1) DD[iv] = dd[0];
+      uint32_t pk[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        pk[e] = (2 * e < 4 + NF) ? pack_bf16(2 * e < m.nout ? dz[2 * e] : 0.f, 2 * e + 1 < m.nout ? dz[2 * e + 1] : 0.f)
+                                 : 0u;
+      // delta_L (32 columns): A operand of dgrad_L in TMEM; B of wgrad_L and A of its bias sum in
+      // the delta tile (chunks 0-3 of slab 0; the rest is never flushed)
+      tmem_st16(arow, pk);
+      const RowSw sw(row);
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) st_shared_v4(dt + sw.off(ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+      tmem_wait_st();
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (issuer) {
+        tc_fence_after();
+        if (!*sAbort) {
+          issue_dgrad_w(tA, sbase + Lw.w + P.sw_off[L], tD, P.kpad[L], P.npad[L], (uint32_t)P.npad[L] * 128u);
+          issue_wgrad_w(ht, dt, tR, P.npad[L]);
+          issue_bias_w(dt, ones_k, tRb);
+        }
+      }
+      commit_m();
+    }
+    // ---------------- backward phases: l = L .. 1 produce delta_{l-1}; then the pose chain
+    (void)wait_m();  // dgrad_L, wgrad_L and its bias sum
+    uint32_t G[64];  // G_l = dL/dH_l (unmasked) as BF16 pairs
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      uint32_t v[32];
+      tmem_ld32(trow + 32u * q4, v);
+      tmem_wait_ld();
+#pragma unroll
+      for (int e = 0; e < 16; ++e) G[16 * q4 + e] = pack_bf16(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
+    }
+    tc_fence_before();
+    for (int l = L; l >= 1; --l) {
+      if (l < L) (void)wait_m();  // wgrad_l and its bias sum
+      flush_layer(l);
+      // delta_{l-1} = G_l * [H_l > 0], in place
+      {
+        const RowSw sw(row);
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) {
+            uint32_t hq[4];
+            ld_shared_v4(ht + (uint32_t)s2 * kSlab + sw.off(ch), hq[0], hq[1], hq[2], hq[3]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) G[32 * s2 + 4 * ch + e] &= bf16x2_nonzero(hq[e]) & vmask;
+          }
+      }
+      {
+        uint32_t h0[32], h1[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+          h0[e] = G[e];
+          h1[e] = G[32 + e];
+        }
+        tmem_st32(arow, h0);
+        tmem_st32(arow + 32, h1);
+      }
+      store_row128(dt, row, G);
+      tmem_wait_st();
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (issuer) {
+        tc_fence_after();
+        if (!*sAbort)
+          issue_dgrad_w(tA, sbase + Lw.w + P.sw_off[l - 1], tD, P.kpad[l - 1], P.npad[l - 1],
+                        (uint32_t)P.npad[l - 1] * 128u);
+      }
+      commit_m();
+      (void)wait_m();  // dgrad_{l-1}
+      if (l - 1 >= 1) {
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          uint32_t v[32];
+          tmem_ld32(trow + 32u * q4, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) G[16 * q4 + e] = pack_bf16(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
+        }
+        // recompute H_{l-1} into the H tile (G_{l-1} waits in registers)
+        tc_fence_before();
+        __syncthreads();
+        if (issuer) {
+          tc_fence_after();
+          if (!*sAbort) issue_fwd_layer(xt, sbase + Lw.w + P.sw_off[0], tD, P.kpad[0], P.npad[0]);
+        }
+        commit_m();
+        recompute_to(l - 2);
+        if (issuer) {  // after recompute_to's last barrier: H_{l-1} and delta_{l-1} are in their tiles
+          tc_fence_after();
+          if (!*sAbort) {
+            issue_wgrad_w(ht, dt, tR, P.npad[l - 1]);
+            issue_bias_w(dt, ones_k, tRb);
+          }
+        }
+        commit_m();
+      } else {
+        // ---------------- encoding derivative and pose chain (midpoint samples), as in the
+        // 64-wide kernel: the per-interval sums A = sum_k gx_k and B = sum_k c_k gx_k
+        uint32_t v0[32], v1[32];
+        tmem_ld32(trow, v0);
+        tmem_ld32(trow + 32, v1);
+        tmem_wait_ld();
+        tc_fence_before();
+        float gx[3] = {0.f, 0.f, 0.f};
+        const IntervalRec& I = T[valid ? iv : 0];
+        const float ck = ((float)k + 0.5f) * invS - 0.5f;
+        if (valid) {
+          const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+          float xl[3];
+          for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
+          enc_grad64<XL>(xl, v0, v1, gx);
+        }
+        float red[6] = {gx[0], gx[1], gx[2], ck * gx[0], ck * gx[1], ck * gx[2]};
+        seg_scan<6>(red, 6, row, S, sScan, 1);
+        const int wrow0 = row - lane;
+        for (int r_end = (wrow0 / S + 1) * S - 1; r_end < wrow0 + 32; r_end += S) {
+          const int ive = r_end / S;
+          if (ive >= nint) break;  // warp-uniform
+          float rr[6];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) rr[j] = __shfl_sync(0xffffffffu, red[j], r_end - wrow0);
+          if (lane < 12) {
+            const IntervalRec& Ie = T[ive];
+            const float span = Ie.r1 - Ie.r0, tm = Ie.r0 + 0.5f * span;
+            const float dA = rr[0] * Ie.dp[0] + rr[1] * Ie.dp[1] + rr[2] * Ie.dp[2];
+            const float dB = rr[3] * Ie.dp[0] + rr[4] * Ie.dp[1] + rr[5] * Ie.dp[2];
+            const float dDelta = DD[ive];
+            const float gt0 = 0.5f * dA - dB - dDelta * invS, gt1 = 0.5f * dA + dB + dDelta * invS;
+            const bool clamped = Ie.r0 != -Ie.r1;
+            const float gtm = gt1 + (clamped ? 0.f : gt0);
+            const float gh = gt1 - (clamped ? 0.f : gt0);
+            const float aa = Ie.dp[0] * Ie.dp[0] + Ie.dp[1] * Ie.dp[1] + Ie.dp[2] * Ie.dp[2];
+            const float inv_a = 1.f / aa;
+            const float hh = Ie.r1;
+            const float gh_ah = hh > 0.f ? gh * inv_a / hh : 0.f;
+            if (lane < 9) {
+              const int u = lane / 3, e = lane - 3 * u;
+              const float ru = u == 0 ? rr[0] : (u == 1 ? rr[1] : rr[2]);
+              const float rbu = u == 0 ? rr[3] : (u == 1 ? rr[4] : rr[5]);
+              const float pu = Ie.p[u], dpu = Ie.dp[u];
+              const float go_u = -gtm * dpu * inv_a - gh_ah * pu;
+              const float cd_u = -(gtm * pu + gh * hh * dpu) * inv_a;
+              const float ta = tm * ru + span * rbu;
+              float gy = 0.f, ym = 0.f;
+#pragma unroll
+              for (int j = 0; j < 3; ++j) {
+                const float rsj = Gp.R[e * 3 + j] * Gp.s[j];
+                gy = fmaf(rsj, ru * Ie.p[j] + ta * Ie.dp[j], gy);
+                ym = fmaf(rsj, Ie.p[j], ym);
+              }
+              geo_acc += gy + go_u * ym + cd_u * Ie.d[e];
+            } else {
+              const int e = lane - 9;
+              float acc2 = 0.f;
+#pragma unroll
+              for (int u = 0; u < 3; ++u) {
+                const float go_u = -gtm * Ie.dp[u] * inv_a - gh_ah * Ie.p[u];
+                acc2 = fmaf(Gp.Mhi[u * 3 + e], rr[u] + go_u, acc2);
+              }
+              geo_acc -= acc2;
+            }
+          }
+        }
+        // wgrad_0 (bias gradient in accumulator row 64), then its flush
+        tc_fence_before();
+        __syncthreads();
+        if (issuer) {
+          tc_fence_after();
+          if (!*sAbort) issue_wgrad_w0(xt, dt, tR, ones_mn, P.npad[0]);
+        }
+        commit_m();
+        (void)wait_m();
+        flush_layer(0);
+      }
+    }
+  }
+  // teardown: no MMA may still write TMEM; the last primitive's gradients; TMEM freed
+  if (issuer) {
+    mma_commit(bar_e);
+    mbar_wait_limit(bar_e, 0, kWaitNsW);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (loaded >= 0) flush_prim(loaded);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemColsW);
+  }
+  if (threadIdx.x == 0 && *sAbort) set_status(w.scr_hdr, MLPS_ERR_TIMEOUT);
+}
+
+}  // namespace tc
+
+// ------------------------------------------------------------------------------------------
+// Host side
+
+// The tensor-core backward at hidden width 128 (tc model `m`): midpoint samples with the
+// configurations' encodings (xyz L = 6, direction L = 4: 60 inputs in one slab), up to 16
+// feature outputs, every output count and weight offset a multiple of 4 (vector reductions),
+// and its shared memory within the SM's.
+bool tc_bwd_wide_supported(const Model& m, const TcPlan& P) {
+  if (m.width != 128 || m.nl < 2 || m.contact) return false;
+  if (m.xyzL != 6 || m.dirL != 4 || P.kpad[0] != 64) return false;
+  if (m.F > 16 || m.nout > 32) return false;
+  if (m.P % 4 != 0) return false;
+  for (int l = 0; l < m.nl; ++l)
+    if (m.dout[l] % 4 != 0 || m.woff[l] % 4 != 0 || m.boff[l] % 4 != 0) return false;
+  const int ipc = m.S <= 128 ? 128 / m.S : 1;
+  return tc::wide_layout(P, 32, ipc).total + 1024 <= 227 * 1024;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode_w() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+cudaError_t launch_mlp_bwd_tc_wide(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,
+                                   cudaStream_t st) {
+  if (!tc_bwd_wide_supported(a.m, P) || !w.dwb) return cudaErrorNotSupported;
+  auto encode = get_encode_w();
+  if (!encode) return cudaErrorNotSupported;
+  CUtensorMap tmap;
+  const cuuint64_t dims[2] = {64, (cuuint64_t)w.K * (cuuint64_t)P.rows_per_prim};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {64, 16};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<unsigned char*>(a.weights),
+                      dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const size_t smem = tc::wide_layout(P, 32, w.ipc).total + 1024;
+  auto kern = a.m.F > 0 ? tc::k_mlp_bwd_tc_wide<16, 6, 4> : tc::k_mlp_bwd_tc_wide<0, 6, 4>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<n_sm, tc::kWThreads, smem, st>>>(w, a, P, tmap);
+  return cudaGetLastError();
+}
+
+}  // namespace mlps

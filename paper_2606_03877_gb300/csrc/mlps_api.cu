@@ -558,8 +558,8 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
   long long tc_stride = 0;
   // FP8 precision: the backward recomputes the MLP in BF16 from the BF16 tiles of the same blob
   const bool tc = cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3;
-  // width 128: the FP32 wide backward, reading the FP32 blob or the BF16 tiles of the
-  // tensor-core precisions (their forward weights), for every precision
+  // width 128: the BF16 tensor-core wide backward (BF16 / E4M3 precisions), or the FP32 wide
+  // backward reading the FP32 blob or the BF16 tiles
   const bool wide = m.width == 128;
   if (wide) {
     if (tc && !tc_plan(m, &P, &tc_stride, cfg->precision == MLPS_FP8_E4M3)) return MLPS_ERR_UNSUPPORTED;
@@ -600,8 +600,13 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
   }
   if (K > 0) {
     StageTimer tm(ST_MLP_BWD, st);
-    cudaError_t e = wide ? launch_mlp_bwd_simt_wide(w, a, tc ? &P : nullptr, n_sm, st)
-                    : tc ? launch_mlp_bwd_tc(w, a, P, n_sm, st) : launch_mlp_bwd_simt(w, a, n_sm, st);
+    // width 128: the tensor-core kernel for the tensor-core precisions where it applies, else
+    // the wide FP32 kernel
+    const bool wide_tc = wide && tc && tc_bwd_wide_supported(m, P);
+    cudaError_t e = wide_tc ? launch_mlp_bwd_tc_wide(w, a, P, n_sm, st)
+                    : wide  ? launch_mlp_bwd_simt_wide(w, a, tc ? &P : nullptr, n_sm, st)
+                    : tc    ? launch_mlp_bwd_tc(w, a, P, n_sm, st)
+                            : launch_mlp_bwd_simt(w, a, n_sm, st);
     if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return MLPS_ERR_CUDA;
     count_launch(1);

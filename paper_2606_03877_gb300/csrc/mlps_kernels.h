@@ -142,6 +142,11 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
 bool tc_bwd_supported(const Model& m, const TcPlan& P);
 // The model as the tensor-core kernels see it: 32-wide hidden layers padded to 64.
 Model tc_model(const Model& m);
+// BF16 tensor-core backward at hidden width 128 (weight gradients flushed per chunk into w.dwb,
+// activations recomputed on demand).
+bool tc_bwd_wide_supported(const Model& m, const TcPlan& P);
+cudaError_t launch_mlp_bwd_tc_wide(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,
+                                   cudaStream_t st);
 cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, int n_sm,
                               cudaStream_t st);
 
