@@ -5,22 +5,26 @@
 //  * Weight gradients: four 128 x 128 layers and the head need 544 TMEM columns, more than the
 //    512 of an SM. Each layer's gradient is accumulated in one TMEM region for one chunk only
 //    and then added into the block's FP32 copy in global memory (L2-resident, laid out
-//    [input][output] per layer so that a thread adds one contiguous row with vector
-//    reductions); the copy goes into d_weights when the block's primitive changes.
+//    [input][output] per layer so that a thread adds contiguous runs with vector reductions);
+//    the copy goes into d_weights when the block's primitive changes.
 //  * Activations: the resident weights take 120 KB of shared memory, so only one H tile, one
-//    delta tile and the encoded input fit next to them. H_l, needed by wgrad_l and by the ReLU
-//    mask of delta_{l-1}, is recomputed from the input when phase B_l comes (recompute on
-//    demand); the next dgrad result waits in registers as BF16 pairs meanwhile.
+//    delta tile and the encoded input fit next to them. The last hidden activation H_L stays
+//    in the H tile (it is also the head's A operand); H_{L-1} and H_{L-2} stay in TMEM (BF16
+//    pairs, 64 columns each) and are copied into the H tile when their wgrad comes; an earlier
+//    one (H_1 of a four-hidden-layer network) is recomputed from the input at that point. Each
+//    delta takes the TMEM slot its phase has freed.
 //  * Bias gradients: every input row of the wgrad accumulator is a feature, so the sum of
 //    delta_l over the rows is one more MMA: A = delta_l read as an MN-major operand (M = the
 //    outputs), B = a constant K-major operand whose first row is all ones (N = 16).
-// One epilogue group (4 warps, thread = sample row) per SM walks its range of the
-// primitive-major chunk list. Per chunk: encode X into shared memory; forward to the head with
-// activations in TMEM (A operand); reverse of the interval composite (Eq. 6) into delta of the
-// head; then for l = L .. 1: flush dW_l, delta_{l-1} = G_l * [H_l > 0], dgrad_{l-1}, recompute
-// H_{l-1}, wgrad_{l-1} and its bias sum; finally the encoding derivative and the pose chain
-// (as in k_mlp_tc_bwd.cu). Every wait is bounded by wall time; after a timeout the kernel runs
-// out its chunks without issuing MMAs, frees TMEM and reports MLPS_ERR_TIMEOUT.
+// Eight warps per SM: thread (row, half) owns TMEM lane `row` (the chunk's sample row) and the
+// columns [64 half, 64 half + 64) of every 128-wide activation, gradient and weight-gradient
+// row; the per-sample scalar work (the encoding, the composite reverse, the pose chain) runs in
+// half 0. Per chunk: encode X; forward to the head; reverse of the interval composite (Eq. 6)
+// into delta of the head; then for l = L .. 1: flush dW_l, delta_{l-1} = G_l * [H_l > 0],
+// dgrad_{l-1}, H_{l-1} into the H tile, wgrad_{l-1} and its bias sum; finally the encoding
+// derivative and the pose chain (as in k_mlp_tc_bwd.cu). Every wait is bounded by wall time;
+// after a timeout the kernel runs out its chunks without issuing MMAs, frees TMEM and reports
+// MLPS_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -40,13 +44,15 @@ namespace tc {
 
 namespace {
 
-constexpr int kWThreads = kEGThreads;          // one epilogue group
+constexpr int kWThreads = 2 * kEGThreads;      // two threads per TMEM lane (column halves)
 constexpr uint32_t kSlab = kM * 128;           // one 64-column slab of 128 rows (16 KB)
 constexpr uint32_t kOnesMN = 2048;             // 16 rows of the MN-major ones atom (one K step)
 constexpr uint32_t kOnesK = 2048;              // K-major ones operand: 16 rows, the first all ones
 constexpr uint64_t kWaitNsW = 2000000000ull;
-// TMEM columns: accumulator (forward / dgrad), A operand (BF16 pairs), weight gradient, bias sums
-constexpr uint32_t kColD = 0, kColA = 128, kColR = 256, kColRb = 384, kTmemColsW = 512;
+// TMEM columns: accumulator (forward / dgrad), three 64-column slots of BF16 pairs (activations
+// H_{L-2} in Sa and H_{L-1} in Sb, deltas as dgrad A operands), weight gradient, bias sums
+constexpr uint32_t kColD = 0, kColSa = 128, kColSb = 192, kColSc = 256, kColR = 320, kColRb = 448;
+constexpr uint32_t kTmemColsW = 512;
 
 struct WideSmem {
   uint32_t w, xt, ht, dt, ones_mn, ones_k, bias, itab, giv, ddel, gf, scan, geo, pgeo, bars, misc, total;
@@ -145,18 +151,6 @@ MLPS_DEV void red_add_v4(float* p, float a, float b, float c, float d) {
                : "memory");
 }
 
-// Store / load one row of a two-slab (128-column) tile: pk[0..31] = columns 0..63 (slab 0),
-// pk[32..63] = columns 64..127 (slab 1).
-MLPS_DEV void store_row128(uint32_t tile, int row, const uint32_t (&pk)[64]) {
-  const RowSw sw(row);
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int ch = 0; ch < 8; ++ch)
-      st_shared_v4(tile + (uint32_t)s * kSlab + sw.off(ch), pk[32 * s + 4 * ch], pk[32 * s + 4 * ch + 1],
-                   pk[32 * s + 4 * ch + 2], pk[32 * s + 4 * ch + 3]);
-}
-
 }  // namespace
 
 template <int NF, int XL, int DL>
@@ -177,11 +171,14 @@ __global__ void __launch_bounds__(kWThreads, 1)
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(gb + Lw.misc);
   volatile int* sAbort = reinterpret_cast<volatile int*>(gb + Lw.misc + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = threadIdx.x;  // sample row of the chunk, TMEM lane
-  const bool issuer = row == 0;
+  const int row = threadIdx.x & (kM - 1);  // sample row of the chunk, TMEM lane
+  const int half = threadIdx.x >> 7;       // column half (warp-uniform)
+  const bool lead = half == 0;             // the per-sample scalar work
+  const bool issuer = threadIdx.x == 0;
   const uint32_t xt = sbase + Lw.xt, ht = sbase + Lw.ht, dt = sbase + Lw.dt;
+  const uint32_t hs = (uint32_t)half * kSlab;  // this thread's slab of a two-slab tile
   const uint32_t ones_mn = sbase + Lw.ones_mn, ones_k = sbase + Lw.ones_k;
-  constexpr int kScanNV = 3 + (NF > 3 ? NF : 3);
+  auto wt = [&](int l) { return sbase + Lw.w + (uint32_t)P.sw_off[l]; };
 
   if (threadIdx.x == 0) {
     mbar_init(bar_w, 1);
@@ -208,8 +205,13 @@ __global__ void __launch_bounds__(kWThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
-  const uint32_t lanes = (uint32_t)(warp * 32) << 16;
-  const uint32_t tD = tmem + kColD, tA = tmem + kColA, tR = tmem + kColR, tRb = tmem + kColRb;
+  const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+  // MMA operand / accumulator addresses (lane 0) and this thread's row of them
+  const uint32_t mD = tmem + kColD, mR = tmem + kColR, mRb = tmem + kColRb;
+  const uint32_t mSa = tmem + kColSa, mSb = tmem + kColSb, mSc = tmem + kColSc;
+  const uint32_t rD = mD + lanes, rR = mR + lanes, rRb = mRb + lanes;
+  const uint32_t hc = 64u * (uint32_t)half;  // first FP32 column of this thread's half
+  const uint32_t hp = 32u * (uint32_t)half;  // first BF16-pair column of this thread's half
 
   const int total = w.saved_hdr[2];
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
   const float invS = 1.f / (float)S;
   int loaded = -1;
 
-  // the next completion of this thread's MMAs (every thread waits: tcgen05.ld is warp-wide)
+  // the next completion of the issuer's MMAs (every thread waits: tcgen05.ld is warp-wide)
   auto wait_m = [&]() -> bool {
     const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_m, ph_m, sAbort, kWaitNsW));
     ph_m ^= 1u;
@@ -264,14 +266,18 @@ __global__ void __launch_bounds__(kWThreads, 1)
     }
     __syncthreads();
   };
-  // chunk gradient of layer l (region R: input row = lane, outputs along the columns; layer 0's
-  // bias gradient in row 64; other layers' in Rb) into the block's copy
+  // chunk gradient of layer l (region R: input row = lane, outputs along the columns, this
+  // thread's half of them; layer 0's bias gradient in row 64, other layers' in Rb) into the
+  // block's copy
   auto flush_layer = [&](int l) {
     const int din = m.din[l], dout = m.dout[l];
     float* cp = dwb + m.woff[l];
-    for (int c0 = 0; c0 < P.npad[l]; c0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int c0 = (int)hc + 32 * q;
+      if (c0 >= P.npad[l]) break;  // warp-uniform (the head's 32 columns: half 0)
       uint32_t v[32];
-      tmem_ld32(tR + (uint32_t)c0 + lanes, v);
+      tmem_ld32(rR + (uint32_t)c0, v);
       tmem_wait_ld();
       if (*sAbort) continue;
       if (row < din) {
@@ -285,14 +291,51 @@ __global__ void __launch_bounds__(kWThreads, 1)
           if (c0 + j < dout) atomicAdd(&dwb[m.boff[0] + c0 + j], __uint_as_float(v[j]));
       }
     }
-    if (l > 0) {
+    if (l > 0 && lead) {
       uint32_t v16[16];
-      tmem_ld16(tRb + lanes, v16);
+      tmem_ld16(rRb, v16);
       tmem_wait_ld();
       if (!*sAbort && row < dout) atomicAdd(&dwb[m.boff[l] + row], __uint_as_float(v16[0]));
     }
     tc_fence_before();
   };
+  // epilogue of hidden layer l, this thread's half: H_{l+1} = ReLU(Z_l + b_l) from the
+  // accumulator row `src` as BF16 pairs, into the TMEM slot row `dst` or the H tile
+  auto hidden_epilogue = [&](int l, uint32_t src, bool to_tile, uint32_t dst) {
+    const float* bias = sBias + P.bias_off[l] + hc;
+    uint32_t pk[32];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      uint32_t v[32];
+      tmem_ld32(src + hc + 32u * q, v);
+      tmem_wait_ld();
+      const float4* b4 = reinterpret_cast<const float4*>(bias + 32 * q);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const float4 bq = b4[e];
+        float x0 = __uint_as_float(v[4 * e]), x1 = __uint_as_float(v[4 * e + 1]);
+        float x2 = __uint_as_float(v[4 * e + 2]), x3 = __uint_as_float(v[4 * e + 3]);
+        add2_f32(x0, x1, bq.x, bq.y);
+        add2_f32(x2, x3, bq.z, bq.w);
+        pk[16 * q + 2 * e] = pack_bf16_relu(x0, x1);
+        pk[16 * q + 2 * e + 1] = pack_bf16_relu(x2, x3);
+      }
+    }
+    tc_fence_before();
+    if (to_tile) {
+      store_row64(ht + hs, row, pk);
+      fence_proxy_async_smem();
+    } else {
+      tmem_st32(dst + hp, pk);
+      tmem_wait_st();
+    }
+  };
+  // TMEM slot of H_j (1 <= j < L) during the forward: H_{L-1} in Sb, H_{L-2} in Sa, an earlier
+  // one in Sa until the next overwrites it
+  auto fwd_slot = [&](int j) { return j == L - 1 ? mSb : mSa; };
+  // TMEM slot that receives delta_{l-1} in phase l (free by then: its activation has been
+  // copied to the H tile, or its delta consumed by an earlier dgrad)
+  auto delta_slot = [&](int l) { return (l == L || l == L - 3) ? mSc : (l == L - 1 ? mSb : mSa); };
 
   IntervalRec* T = reinterpret_cast<IntervalRec*>(gb + Lw.itab);
   float4* GI = reinterpret_cast<float4*>(gb + Lw.giv);
@@ -311,7 +354,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
         for (int l = 0; l < nl; ++l)
           for (int sl = 0; sl < P.kpad[l] / 64; ++sl)
             for (int j = 0; j < P.npad[l] / 16; ++j)
-              tma_load_2d(sbase + Lw.w + P.sw_off[l] + sl * P.npad[l] * 128 + j * 2048, &tmap, 0,
+              tma_load_2d(wt(l) + sl * P.npad[l] * 128 + j * 2048, &tmap, 0,
                           row0 + P.gw_row[l] + sl * P.npad[l] + j * 16, bar_w);
       }
       const float* gbias = reinterpret_cast<const float*>(a.weights + (size_t)prim * a.pk.stride + P.gbias_byte);
@@ -340,97 +383,44 @@ __global__ void __launch_bounds__(kWThreads, 1)
     const int iv = row / S, k = row - iv * S;
     const bool valid = iv < nint;
     const uint32_t vmask = valid ? 0xFFFFFFFFu : 0u;
-    const uint32_t trow = tD + lanes, arow = tA + lanes;
 
-    // ---------------- X into its tile, layer 0 of the recompute
-    {
+    // ---------------- X into its tile; forward to the head: H_1 .. H_{L-1} in TMEM slots, H_L
+    // in the H tile (the head's A operand)
+    if (lead) {
       uint32_t pk[32];
       encode_row64<XL, DL>(T, nint, S, row, pk);
       store_row64(xt, row, pk);
+      fence_proxy_async_smem();
     }
-    fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     if (issuer) {
       tc_fence_after();
-      if (!*sAbort) issue_fwd_layer(xt, sbase + Lw.w + P.sw_off[0], tD, P.kpad[0], P.npad[0]);
+      if (!*sAbort) issue_fwd_layer(xt, wt(0), mD, P.kpad[0], P.npad[0]);
     }
     commit_m();
-    // epilogue of hidden layer l: H_{l+1} = ReLU(Z_l + b_l) as BF16 pairs, into the TMEM A
-    // operand (to_tmem) and / or the H tile (to_tile)
-    auto hidden_epilogue = [&](int l, bool to_tmem, bool to_tile) {
-      (void)wait_m();
-      const float* bias = sBias + P.bias_off[l];
-      uint32_t pk[64];
-#pragma unroll
-      for (int q4 = 0; q4 < 4; ++q4) {
-        uint32_t v[32];
-        tmem_ld32(trow + 32u * q4, v);
-        tmem_wait_ld();
-        const float4* b4 = reinterpret_cast<const float4*>(bias + 32 * q4);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const float4 bq = b4[e];
-          float x0 = __uint_as_float(v[4 * e]), x1 = __uint_as_float(v[4 * e + 1]);
-          float x2 = __uint_as_float(v[4 * e + 2]), x3 = __uint_as_float(v[4 * e + 3]);
-          add2_f32(x0, x1, bq.x, bq.y);
-          add2_f32(x2, x3, bq.z, bq.w);
-          pk[16 * q4 + 2 * e] = pack_bf16_relu(x0, x1);
-          pk[16 * q4 + 2 * e + 1] = pack_bf16_relu(x2, x3);
-        }
-      }
-      tc_fence_before();
-      if (to_tmem) {
-        uint32_t h0[32], h1[32];
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          h0[e] = pk[e];
-          h1[e] = pk[32 + e];
-        }
-        tmem_st32(arow, h0);
-        tmem_st32(arow + 32, h1);
-        tmem_wait_st();
-      }
-      if (to_tile) {
-        store_row128(ht, row, pk);
-        fence_proxy_async_smem();
-      }
-    };
-    // recompute through hidden layer `upto` (H_{upto+1} ends in the H tile); layer 0's MMA is
-    // already issued
-    auto recompute_to = [&](int upto) {
-      for (int l = 0; l <= upto; ++l) {
-        hidden_epilogue(l, l < upto, l == upto);
-        tc_fence_before();
-        __syncthreads();
-        if (l < upto) {
-          if (issuer) {
-            tc_fence_after();
-            if (!*sAbort) issue_fwd_layer_ta(tA, sbase + Lw.w + P.sw_off[l + 1], tD, P.kpad[l + 1], P.npad[l + 1]);
-          }
-          commit_m();
-        }
-      }
-    };
-
-    // ---------------- forward to the head: H_1 .. H_L in TMEM, H_L also in the H tile
     for (int l = 0; l < L; ++l) {
-      hidden_epilogue(l, true, l == L - 1);
+      const int j = l + 1;  // H_j
+      (void)wait_m();
+      hidden_epilogue(l, rD, j == L, fwd_slot(j) + lanes);
       tc_fence_before();
       __syncthreads();
       if (issuer) {
         tc_fence_after();
-        if (!*sAbort) issue_fwd_layer_ta(tA, sbase + Lw.w + P.sw_off[l + 1], tD, P.kpad[l + 1], P.npad[l + 1]);
+        if (!*sAbort) {
+          if (j == L) issue_fwd_layer(ht, wt(L), mD, P.kpad[L], P.npad[L]);
+          else issue_fwd_layer_ta(fwd_slot(j), wt(j), mD, P.kpad[j], P.npad[j]);
+        }
       }
       commit_m();
     }
-    // ---------------- heads and reverse of the interval composite (Eq. 6) -> delta_L
+    // ---------------- heads and reverse of the interval composite (Eq. 6) -> delta_L (half 0)
     (void)wait_m();
-    {
+    if (lead) {
       float z[4 + NF];
       {
         uint32_t r32[32];
-        tmem_ld32(trow, r32);
+        tmem_ld32(rD, r32);
         tmem_wait_ld();
         const float* bias = sBias + P.bias_off[L];
 #pragma unroll
@@ -478,12 +468,64 @@ __global__ void __launch_bounds__(kWThreads, 1)
       for (int e = 0; e < 16; ++e)
         pk[e] = (2 * e < 4 + NF) ? pack_bf16(2 * e < m.nout ? dz[2 * e] : 0.f, 2 * e + 1 < m.nout ? dz[2 * e + 1] : 0.f)
                                  : 0u;
-      // delta_L (32 columns): A operand of dgrad_L in TMEM; B of wgrad_L and A of its bias sum in
-      // the delta tile (chunks 0-3 of slab 0; the rest is never flushed)
-      tmem_st16(arow, pk);
+      // delta_L (32 columns): A operand of dgrad_L in slot Sc; B of wgrad_L and A of its bias
+      // sum in the delta tile (chunks 0-3 of slab 0; the rest is never flushed)
+      tmem_st16(mSc + lanes, pk);
       const RowSw sw(row);
 #pragma unroll
       for (int ch = 0; ch < 4; ++ch) st_shared_v4(dt + sw.off(ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+      tmem_wait_st();
+      fence_proxy_async_smem();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (issuer) {
+      tc_fence_after();
+      if (!*sAbort) {
+        issue_dgrad_w(mSc, wt(L), mD, P.kpad[L], P.npad[L], (uint32_t)P.npad[L] * 128u);
+        issue_wgrad_w(ht, dt, mR, P.npad[L]);
+        issue_bias_w(dt, ones_k, mRb);
+      }
+    }
+    commit_m();
+    // ---------------- backward phases l = L .. 1: each starts when dgrad_l, wgrad_l and its bias
+    // sum are done and issues dgrad_{l-1} with wgrad_{l-1} and its bias sum
+    for (int l = L; l >= 1; --l) {
+      (void)wait_m();
+      uint32_t G[32];  // this thread's half of G_l = dL/dH_l (unmasked) as BF16 pairs
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        uint32_t v[32];
+        tmem_ld32(rD + hc + 32u * q, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) G[16 * q + e] = pack_bf16(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
+      }
+      flush_layer(l);
+      // delta_{l-1} = G_l * [H_l > 0] (H_l in the H tile), into its TMEM slot and the delta tile
+      {
+        const RowSw sw(row);
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          uint32_t hq[4];
+          ld_shared_v4(ht + hs + sw.off(ch), hq[0], hq[1], hq[2], hq[3]);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) G[4 * ch + e] &= bf16x2_nonzero(hq[e]) & vmask;
+        }
+      }
+      const uint32_t ds = delta_slot(l);
+      tmem_st32(ds + lanes + hp, G);
+      store_row64(dt + hs, row, G);
+      // H_{l-1} into the H tile from its TMEM slot (the mask above has read H_l: same thread,
+      // same row), or recomputed from X below
+      const bool from_slot = l - 1 >= 1 && l - 1 >= L - 2;
+      const bool recompute = l - 1 >= 1 && !from_slot;
+      if (from_slot) {
+        uint32_t h[32];
+        tmem_ld32(fwd_slot(l - 1) + lanes + hp, h);
+        tmem_wait_ld();
+        store_row64(ht + hs, row, h);
+      }
       tmem_wait_st();
       fence_proxy_async_smem();
       tc_fence_before();
@@ -491,170 +533,104 @@ __global__ void __launch_bounds__(kWThreads, 1)
       if (issuer) {
         tc_fence_after();
         if (!*sAbort) {
-          issue_dgrad_w(tA, sbase + Lw.w + P.sw_off[L], tD, P.kpad[L], P.npad[L], (uint32_t)P.npad[L] * 128u);
-          issue_wgrad_w(ht, dt, tR, P.npad[L]);
-          issue_bias_w(dt, ones_k, tRb);
-        }
-      }
-      commit_m();
-    }
-    // ---------------- backward phases: l = L .. 1 produce delta_{l-1}; then the pose chain
-    (void)wait_m();  // dgrad_L, wgrad_L and its bias sum
-    uint32_t G[64];  // G_l = dL/dH_l (unmasked) as BF16 pairs
-#pragma unroll
-    for (int q4 = 0; q4 < 4; ++q4) {
-      uint32_t v[32];
-      tmem_ld32(trow + 32u * q4, v);
-      tmem_wait_ld();
-#pragma unroll
-      for (int e = 0; e < 16; ++e) G[16 * q4 + e] = pack_bf16(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
-    }
-    tc_fence_before();
-    for (int l = L; l >= 1; --l) {
-      if (l < L) (void)wait_m();  // wgrad_l and its bias sum
-      flush_layer(l);
-      // delta_{l-1} = G_l * [H_l > 0], in place
-      {
-        const RowSw sw(row);
-#pragma unroll
-        for (int s2 = 0; s2 < 2; ++s2)
-#pragma unroll
-          for (int ch = 0; ch < 8; ++ch) {
-            uint32_t hq[4];
-            ld_shared_v4(ht + (uint32_t)s2 * kSlab + sw.off(ch), hq[0], hq[1], hq[2], hq[3]);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) G[32 * s2 + 4 * ch + e] &= bf16x2_nonzero(hq[e]) & vmask;
+          issue_dgrad_w(ds, wt(l - 1), mD, P.kpad[l - 1], P.npad[l - 1], (uint32_t)P.npad[l - 1] * 128u);
+          if (l == 1) {
+            issue_wgrad_w0(xt, dt, mR, ones_mn, P.npad[0]);  // bias gradient in row 64
+          } else if (recompute) {
+            issue_fwd_layer(xt, wt(0), mR, P.kpad[0], P.npad[0]);  // Z_0 into R
+          } else {
+            issue_wgrad_w(ht, dt, mR, P.npad[l - 1]);
+            issue_bias_w(dt, ones_k, mRb);
           }
-      }
-      {
-        uint32_t h0[32], h1[32];
-#pragma unroll
-        for (int e = 0; e < 32; ++e) {
-          h0[e] = G[e];
-          h1[e] = G[32 + e];
         }
-        tmem_st32(arow, h0);
-        tmem_st32(arow + 32, h1);
-      }
-      store_row128(dt, row, G);
-      tmem_wait_st();
-      fence_proxy_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (issuer) {
-        tc_fence_after();
-        if (!*sAbort)
-          issue_dgrad_w(tA, sbase + Lw.w + P.sw_off[l - 1], tD, P.kpad[l - 1], P.npad[l - 1],
-                        (uint32_t)P.npad[l - 1] * 128u);
       }
       commit_m();
-      (void)wait_m();  // dgrad_{l-1}
-      if (l - 1 >= 1) {
-#pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-          uint32_t v[32];
-          tmem_ld32(trow + 32u * q4, v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int e = 0; e < 16; ++e) G[16 * q4 + e] = pack_bf16(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
-        }
-        // recompute H_{l-1} into the H tile (G_{l-1} waits in registers)
+      if (recompute) {
+        // H_1 = ReLU(Z_0 + b_0) into the H tile, then wgrad_1 and its bias sum
+        (void)wait_m();
+        hidden_epilogue(0, rR, true, 0u);
         tc_fence_before();
         __syncthreads();
         if (issuer) {
-          tc_fence_after();
-          if (!*sAbort) issue_fwd_layer(xt, sbase + Lw.w + P.sw_off[0], tD, P.kpad[0], P.npad[0]);
-        }
-        commit_m();
-        recompute_to(l - 2);
-        if (issuer) {  // after recompute_to's last barrier: H_{l-1} and delta_{l-1} are in their tiles
           tc_fence_after();
           if (!*sAbort) {
-            issue_wgrad_w(ht, dt, tR, P.npad[l - 1]);
-            issue_bias_w(dt, ones_k, tRb);
+            issue_wgrad_w(ht, dt, mR, P.npad[1]);
+            issue_bias_w(dt, ones_k, mRb);
           }
         }
         commit_m();
-      } else {
-        // ---------------- encoding derivative and pose chain (midpoint samples), as in the
-        // 64-wide kernel: the per-interval sums A = sum_k gx_k and B = sum_k c_k gx_k
-        uint32_t v0[32], v1[32];
-        tmem_ld32(trow, v0);
-        tmem_ld32(trow + 32, v1);
-        tmem_wait_ld();
-        tc_fence_before();
-        float gx[3] = {0.f, 0.f, 0.f};
-        const IntervalRec& I = T[valid ? iv : 0];
-        const float ck = ((float)k + 0.5f) * invS - 0.5f;
-        if (valid) {
-          const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
-          float xl[3];
-          for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
-          enc_grad64<XL>(xl, v0, v1, gx);
-        }
-        float red[6] = {gx[0], gx[1], gx[2], ck * gx[0], ck * gx[1], ck * gx[2]};
-        seg_scan<6>(red, 6, row, S, sScan, 1);
-        const int wrow0 = row - lane;
-        for (int r_end = (wrow0 / S + 1) * S - 1; r_end < wrow0 + 32; r_end += S) {
-          const int ive = r_end / S;
-          if (ive >= nint) break;  // warp-uniform
-          float rr[6];
-#pragma unroll
-          for (int j = 0; j < 6; ++j) rr[j] = __shfl_sync(0xffffffffu, red[j], r_end - wrow0);
-          if (lane < 12) {
-            const IntervalRec& Ie = T[ive];
-            const float span = Ie.r1 - Ie.r0, tm = Ie.r0 + 0.5f * span;
-            const float dA = rr[0] * Ie.dp[0] + rr[1] * Ie.dp[1] + rr[2] * Ie.dp[2];
-            const float dB = rr[3] * Ie.dp[0] + rr[4] * Ie.dp[1] + rr[5] * Ie.dp[2];
-            const float dDelta = DD[ive];
-            const float gt0 = 0.5f * dA - dB - dDelta * invS, gt1 = 0.5f * dA + dB + dDelta * invS;
-            const bool clamped = Ie.r0 != -Ie.r1;
-            const float gtm = gt1 + (clamped ? 0.f : gt0);
-            const float gh = gt1 - (clamped ? 0.f : gt0);
-            const float aa = Ie.dp[0] * Ie.dp[0] + Ie.dp[1] * Ie.dp[1] + Ie.dp[2] * Ie.dp[2];
-            const float inv_a = 1.f / aa;
-            const float hh = Ie.r1;
-            const float gh_ah = hh > 0.f ? gh * inv_a / hh : 0.f;
-            if (lane < 9) {
-              const int u = lane / 3, e = lane - 3 * u;
-              const float ru = u == 0 ? rr[0] : (u == 1 ? rr[1] : rr[2]);
-              const float rbu = u == 0 ? rr[3] : (u == 1 ? rr[4] : rr[5]);
-              const float pu = Ie.p[u], dpu = Ie.dp[u];
-              const float go_u = -gtm * dpu * inv_a - gh_ah * pu;
-              const float cd_u = -(gtm * pu + gh * hh * dpu) * inv_a;
-              const float ta = tm * ru + span * rbu;
-              float gy = 0.f, ym = 0.f;
-#pragma unroll
-              for (int j = 0; j < 3; ++j) {
-                const float rsj = Gp.R[e * 3 + j] * Gp.s[j];
-                gy = fmaf(rsj, ru * Ie.p[j] + ta * Ie.dp[j], gy);
-                ym = fmaf(rsj, Ie.p[j], ym);
-              }
-              geo_acc += gy + go_u * ym + cd_u * Ie.d[e];
-            } else {
-              const int e = lane - 9;
-              float acc2 = 0.f;
-#pragma unroll
-              for (int u = 0; u < 3; ++u) {
-                const float go_u = -gtm * Ie.dp[u] * inv_a - gh_ah * Ie.p[u];
-                acc2 = fmaf(Gp.Mhi[u * 3 + e], rr[u] + go_u, acc2);
-              }
-              geo_acc -= acc2;
-            }
-          }
-        }
-        // wgrad_0 (bias gradient in accumulator row 64), then its flush
-        tc_fence_before();
-        __syncthreads();
-        if (issuer) {
-          tc_fence_after();
-          if (!*sAbort) issue_wgrad_w0(xt, dt, tR, ones_mn, P.npad[0]);
-        }
-        commit_m();
-        (void)wait_m();
-        flush_layer(0);
       }
     }
+    // ---------------- encoding derivative and pose chain (midpoint samples), as in the 64-wide
+    // kernel: the per-interval sums A = sum_k gx_k and B = sum_k c_k gx_k (half 0)
+    (void)wait_m();  // dgrad_0 and wgrad_0
+    if (lead) {
+      uint32_t v0[32], v1[32];
+      tmem_ld32(rD, v0);
+      tmem_ld32(rD + 32, v1);
+      tmem_wait_ld();
+      float gx[3] = {0.f, 0.f, 0.f};
+      const IntervalRec& I = T[valid ? iv : 0];
+      const float ck = ((float)k + 0.5f) * invS - 0.5f;
+      if (valid) {
+        const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
+        float xl[3];
+        for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
+        enc_grad64<XL>(xl, v0, v1, gx);
+      }
+      float red[6] = {gx[0], gx[1], gx[2], ck * gx[0], ck * gx[1], ck * gx[2]};
+      seg_scan<6>(red, 6, row, S, sScan, 1);
+      const int wrow0 = row - lane;
+      for (int r_end = (wrow0 / S + 1) * S - 1; r_end < wrow0 + 32; r_end += S) {
+        const int ive = r_end / S;
+        if (ive >= nint) break;  // warp-uniform
+        float rr[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) rr[j] = __shfl_sync(0xffffffffu, red[j], r_end - wrow0);
+        if (lane < 12) {
+          const IntervalRec& Ie = T[ive];
+          const float span = Ie.r1 - Ie.r0, tm = Ie.r0 + 0.5f * span;
+          const float dA = rr[0] * Ie.dp[0] + rr[1] * Ie.dp[1] + rr[2] * Ie.dp[2];
+          const float dB = rr[3] * Ie.dp[0] + rr[4] * Ie.dp[1] + rr[5] * Ie.dp[2];
+          const float dDelta = DD[ive];
+          const float gt0 = 0.5f * dA - dB - dDelta * invS, gt1 = 0.5f * dA + dB + dDelta * invS;
+          const bool clamped = Ie.r0 != -Ie.r1;
+          const float gtm = gt1 + (clamped ? 0.f : gt0);
+          const float gh = gt1 - (clamped ? 0.f : gt0);
+          const float aa = Ie.dp[0] * Ie.dp[0] + Ie.dp[1] * Ie.dp[1] + Ie.dp[2] * Ie.dp[2];
+          const float inv_a = 1.f / aa;
+          const float hh = Ie.r1;
+          const float gh_ah = hh > 0.f ? gh * inv_a / hh : 0.f;
+          if (lane < 9) {
+            const int u = lane / 3, e = lane - 3 * u;
+            const float ru = u == 0 ? rr[0] : (u == 1 ? rr[1] : rr[2]);
+            const float rbu = u == 0 ? rr[3] : (u == 1 ? rr[4] : rr[5]);
+            const float pu = Ie.p[u], dpu = Ie.dp[u];
+            const float go_u = -gtm * dpu * inv_a - gh_ah * pu;
+            const float cd_u = -(gtm * pu + gh * hh * dpu) * inv_a;
+            const float ta = tm * ru + span * rbu;
+            float gy = 0.f, ym = 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              const float rsj = Gp.R[e * 3 + j] * Gp.s[j];
+              gy = fmaf(rsj, ru * Ie.p[j] + ta * Ie.dp[j], gy);
+              ym = fmaf(rsj, Ie.p[j], ym);
+            }
+            geo_acc += gy + go_u * ym + cd_u * Ie.d[e];
+          } else {
+            const int e = lane - 9;
+            float acc2 = 0.f;
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+              const float go_u = -gtm * Ie.dp[u] * inv_a - gh_ah * Ie.p[u];
+              acc2 = fmaf(Gp.Mhi[u * 3 + e], rr[u] + go_u, acc2);
+            }
+            geo_acc -= acc2;
+          }
+        }
+      }
+    }
+    flush_layer(0);
   }
   // teardown: no MMA may still write TMEM; the last primitive's gradients; TMEM freed
   if (issuer) {
@@ -683,7 +659,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
 // feature outputs, every output count and weight offset a multiple of 4 (vector reductions),
 // and its shared memory within the SM's.
 bool tc_bwd_wide_supported(const Model& m, const TcPlan& P) {
-  if (m.width != 128 || m.nl < 2 || m.contact) return false;
+  if (m.width != 128 || m.nl < 2 || m.nl > 5 || m.contact) return false;
   if (m.xyzL != 6 || m.dirL != 4 || P.kpad[0] != 64) return false;
   if (m.F > 16 || m.nout > 32) return false;
   if (m.P % 4 != 0) return false;
