@@ -184,13 +184,14 @@ def _traffic(stage, precision, workload):
     import hashlib
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        e = d[stage]
-        if precision not in e["precision"] or workload != e["workload"]:
-            return None
-        for p, h in e["sources"].items():
-            if hashlib.sha256(open(os.path.join(ROOT, p), "rb").read()).hexdigest()[:16] != h:
-                return None
-        return float(e["bytes_per_launch"])
+        for e in d[stage]:
+            if precision not in e["precision"] or workload != e["workload"]:
+                continue
+            for p, h in e["sources"].items():
+                if hashlib.sha256(open(os.path.join(ROOT, p), "rb").read()).hexdigest()[:16] != h:
+                    return None
+            return float(e["bytes_per_launch"])
+        return None
     except Exception:
         return None
 
