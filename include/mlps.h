@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define MLPS_ABI_VERSION 5
+#define MLPS_ABI_VERSION 6
 #define MLPS_MAX_VIEWS 64
 
 typedef int32_t mlps_status;
@@ -95,8 +95,12 @@ typedef struct {
                                    d the unit ray direction and delta = mu - p* the offset from
                                    the contact point p* = o + max(0, t*) d to the centre (Eq. 3);
                                    the hit's alpha uses its chord length. The forward pass
-                                   runs in every precision; the backward pass in FP32 only
-                                   (MLPS_ERR_UNSUPPORTED from mlps_render_backward otherwise). */
+                                   runs in every precision. The backward pass runs in FP32,
+                                   and on the tensor cores (BF16 / E4M3 precisions) for the
+                                   paper's model (xyz_freqs = dir_freqs = 6, hidden width 32
+                                   or 64, at least two hidden layers, no feature head);
+                                   mlps_render_backward returns MLPS_ERR_UNSUPPORTED for other
+                                   contact models in those precisions. */
   int32_t slot_dim;             /* C of the feature slots of Sec. 3.4 (0 = none; a multiple of 4,
                                    <= 2048): every primitive also carries four slot embeddings
                                    e_k in R^C, stored after its MLP parameters (canonical weights
@@ -294,6 +298,56 @@ mlps_status mlps_autotune_batch(const mlps_config* cfg, const mlps_scene* scene,
 
 /* Forget every cached autotuner decision. */
 void mlps_autotune_clear(void);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Batched rendering with a device-resident item table                                       */
+/*
+ * The batch renderer above, with the item table (primitive ranges and cameras, resolutions
+ * included) read from DEVICE memory when the launches run, not from the host at call time.
+ * A graph captured around these calls can therefore be replayed with new items (other
+ * cameras, resolutions and primitive ranges within the caps) written into the same device
+ * table between replays; nothing is baked in but n_items and the caps.
+ *
+ * caps (host struct): every item must satisfy width <= max_width, height <= max_height and
+ * prim_count <= max_prim_count. The workspace is sized for n_items items at the caps
+ * (mlps_batch_workspace_size_dev), and the image buffers for n_items * max_width * max_height
+ * pixels. Items are concatenated at their actual sizes exactly as in the host-table calls
+ * (item i's pixels start at P_i = sum_{j < i} width_j * height_j); pixels past the batch's
+ * actual total are not written.
+ *
+ * dev_items: device array of n_items mlps_batch_item (1..MLPS_MAX_VIEWS), read by the first
+ * kernel of each call (it may be written by the same stream just before). An item that breaks
+ * the caps, names primitives outside [0, K) or has an invalid camera (the checks of
+ * mlps_render_forward) is rendered as an empty view and sets the device status word to
+ * MLPS_ERR_INVALID_ARGUMENT (mlps_read_status); the call itself returns MLPS_OK. Host-side
+ * checks (null pointers, caps < 1, n_items out of range, workspace sizes) return their status
+ * immediately. The backward call must use the same dev_items contents and saved region as the
+ * forward call. */
+typedef struct {
+  int32_t max_width, max_height;  /* largest item resolution */
+  int32_t max_prim_count;         /* largest item primitive range */
+} mlps_batch_caps;
+
+/* Workspace of a device-table batch of n_items items at the caps. */
+mlps_status mlps_batch_workspace_size_dev(const mlps_config* cfg, int32_t K, int32_t n_items,
+                                          const mlps_batch_caps* caps, size_t* saved_bytes,
+                                          size_t* scratch_bytes);
+
+/* Forward render of a device-table batch; other arguments as mlps_render_batch_forward. */
+mlps_status mlps_render_batch_forward_dev(const mlps_config* cfg, const mlps_scene* scene,
+                                          const mlps_batch_item* dev_items, int32_t n_items,
+                                          const mlps_batch_caps* caps, float* rgb, float* trans,
+                                          float* feat, void* saved, size_t saved_bytes, void* scratch,
+                                          size_t scratch_bytes, void* stream);
+
+/* Backward of a device-table batch (same items, caps and `saved` as the forward call). */
+mlps_status mlps_render_batch_backward_dev(const mlps_config* cfg, const mlps_scene* scene,
+                                           const mlps_batch_item* dev_items, int32_t n_items,
+                                           const mlps_batch_caps* caps, const float* d_rgb,
+                                           const float* d_trans, const float* d_feat, const void* saved,
+                                           size_t saved_bytes, float* d_weights, float* d_centers,
+                                           float* d_scales, float* d_quats, void* scratch,
+                                           size_t scratch_bytes, void* stream);
 
 /* Synchronise `stream`, return the device status word of a `saved` or `scratch` region
  * written by the calls above (MLPS_OK if none), and clear it. */

@@ -54,6 +54,10 @@ class MlpsBatchItem(ctypes.Structure):
     _fields_ = [("prim_offset", ctypes.c_int32), ("prim_count", ctypes.c_int32), ("cam", MlpsCamera)]
 
 
+class MlpsBatchCaps(ctypes.Structure):
+    _fields_ = [("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32), ("max_prim_count", ctypes.c_int32)]
+
+
 class MlpsScene(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("centers", ctypes.c_void_p), ("scales", ctypes.c_void_p),
                 ("quats", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
@@ -118,6 +122,15 @@ _SIGS = [
                                              _P(MlpsConfig), _P(ctypes.c_float), _P(ctypes.c_int32),
                                              _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_float), _vp]),
     ("mlps_autotune_clear", None, []),
+    ("mlps_batch_workspace_size_dev", ctypes.c_int32, [_P(MlpsConfig), ctypes.c_int32, ctypes.c_int32,
+                                                       _P(MlpsBatchCaps), _P(ctypes.c_size_t),
+                                                       _P(ctypes.c_size_t)]),
+    ("mlps_render_batch_forward_dev", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _vp, ctypes.c_int32,
+                                                       _P(MlpsBatchCaps), _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                                       _vp, ctypes.c_size_t, _vp]),
+    ("mlps_render_batch_backward_dev", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _vp, ctypes.c_int32,
+                                                        _P(MlpsBatchCaps), _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                                        _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     ("mlps_render_forward_static", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsScene), _P(MlpsCamera),
                                                     ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
     ("mlps_read_status", ctypes.c_int32, [_vp, _vp]),
@@ -286,6 +299,35 @@ def mlps_render_batch_backward(cfg, scene: MlpsScene, items, n_items, d_rgb, d_t
         ctypes.byref(cfg), ctypes.byref(scene), items, int(n_items), _ptr(d_rgb), _ptr(d_trans), _ptr(d_feat),
         _ptr(saved), int(saved_bytes), _ptr(d_weights), _ptr(d_centers), _ptr(d_scales), _ptr(d_quats),
         _ptr(scratch), int(scratch_bytes), stream or None))
+
+
+def batch_caps(max_width: int, max_height: int, max_prim_count: int) -> MlpsBatchCaps:
+    return MlpsBatchCaps(int(max_width), int(max_height), int(max_prim_count))
+
+
+def mlps_batch_workspace_size_dev(cfg: MlpsConfig, K: int, n_items: int, caps: MlpsBatchCaps):
+    s = ctypes.c_size_t()
+    t = ctypes.c_size_t()
+    _check("mlps_batch_workspace_size_dev", load().mlps_batch_workspace_size_dev(
+        ctypes.byref(cfg), int(K), int(n_items), ctypes.byref(caps), ctypes.byref(s), ctypes.byref(t)))
+    return int(s.value), int(t.value)
+
+
+def mlps_render_batch_forward_dev(cfg, scene: MlpsScene, dev_items, n_items, caps: MlpsBatchCaps, rgb, trans,
+                                  feat, saved, saved_bytes, scratch, scratch_bytes, stream: int = 0):
+    _check("mlps_render_batch_forward_dev", load().mlps_render_batch_forward_dev(
+        ctypes.byref(cfg), ctypes.byref(scene), _ptr(dev_items), int(n_items), ctypes.byref(caps), _ptr(rgb),
+        _ptr(trans), _ptr(feat), _ptr(saved), int(saved_bytes), _ptr(scratch), int(scratch_bytes),
+        stream or None))
+
+
+def mlps_render_batch_backward_dev(cfg, scene: MlpsScene, dev_items, n_items, caps: MlpsBatchCaps, d_rgb,
+                                   d_trans, d_feat, saved, saved_bytes, d_weights, d_centers, d_scales, d_quats,
+                                   scratch, scratch_bytes, stream: int = 0):
+    _check("mlps_render_batch_backward_dev", load().mlps_render_batch_backward_dev(
+        ctypes.byref(cfg), ctypes.byref(scene), _ptr(dev_items), int(n_items), ctypes.byref(caps), _ptr(d_rgb),
+        _ptr(d_trans), _ptr(d_feat), _ptr(saved), int(saved_bytes), _ptr(d_weights), _ptr(d_centers),
+        _ptr(d_scales), _ptr(d_quats), _ptr(scratch), int(scratch_bytes), stream or None))
 
 
 def mlps_autotune_batch(cfg, scene: MlpsScene, items, n_items, do_backward, d_rgb, rgb, trans, feat, saved,

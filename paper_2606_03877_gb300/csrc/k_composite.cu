@@ -16,7 +16,7 @@ namespace mlps {
 __global__ void k_composite_fwd(Work w, int F, int FT, float* __restrict__ rgb, float* __restrict__ trans,
                                 float* __restrict__ feat) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= w.n_rays) return;
+  if (r >= w.n_rays || r >= live_rays(w)) return;
   const int n = w.ray_count[r], s = w.ray_start[r];
   float A = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
   float Fv[kMaxFeat];
@@ -54,7 +54,7 @@ __global__ void k_composite_bwd(Work w, int F, int FT, const float* __restrict__
                                 const float* __restrict__ d_feat,
                                 const float* __restrict__ slot_ga) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= w.n_rays) return;
+  if (r >= w.n_rays || r >= live_rays(w)) return;
   const int n = w.ray_count[r], s = w.ray_start[r];
   float A = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
   float RF[kMaxFeat];  // sweep 1: the totals F; sweep 2: the suffix sums

@@ -20,9 +20,95 @@ namespace mlps {
 // ------------------------------------------------------------------------------------------
 // Views
 
+// Ray origin -R^T t of a view record in double-float: each product R_ji t_j is exact as a float
+// pair and their sum keeps ~48 bits (the hit test's precision).
+MLPS_DEV void view_origin(ViewData& d) {
+  for (int i = 0; i < 3; ++i) {
+    dfl s = df_add(df_add(two_prod(d.R[i], d.t[0]), two_prod(d.R[3 + i], d.t[1])), two_prod(d.R[6 + i], d.t[2]));
+    d.o_hi[i] = -s.hi;
+    d.o_lo[i] = -s.lo;
+  }
+}
+
+// Camera fields of a view record.
+MLPS_DEV void view_camera(const mlps_camera& c, ViewData& d) {
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) d.R[i * 3 + j] = c.world_to_cam[i * 4 + j];
+    d.t[i] = c.world_to_cam[i * 4 + 3];
+  }
+  d.fx = c.fx;
+  d.fy = c.fy;
+  d.cx = c.cx;
+  d.cy = c.cy;
+  d.near_t = c.near_t;
+  d.width = c.width;
+  d.height = c.height;
+  view_origin(d);
+}
+
+// Host item table: bases and camera fields come in the launch parameters; the origin is formed
+// here, as for a device table.
 __global__ void k_store_views(Work w, ViewArray va) {
   int v = threadIdx.x;
-  if (v < w.V) w.views[v] = va.v[v];
+  if (v < w.V) {
+    ViewData d = va.v[v];
+    view_origin(d);
+    w.views[v] = d;
+  }
+}
+
+// Device item table: each item checked against the caps and the scene (an invalid item becomes
+// an empty view and raises MLPS_ERR_INVALID_ARGUMENT in the status word), then the bases of all
+// views as running sums in item order (one thread: at most kMaxViews items).
+__global__ void k_views_from_items(Work w, const mlps_batch_item* __restrict__ items, int max_w, int max_h,
+                                   int max_p) {
+  __shared__ ViewData sv[kMaxViews];
+  const int v = threadIdx.x;
+  if (v < w.V) {
+    const mlps_batch_item it = items[v];
+    const mlps_camera& c = it.cam;
+    bool ok = c.width >= 1 && c.height >= 1 && c.width <= max_w && c.height <= max_h;
+    ok = ok && it.prim_offset >= 0 && it.prim_count >= 0 && it.prim_count <= max_p &&
+         (long long)it.prim_offset + it.prim_count <= (long long)w.K;
+    float vals[17] = {c.fx, c.fy, c.cx, c.cy, c.near_t};
+    for (int i = 0; i < 12; ++i) vals[5 + i] = c.world_to_cam[i];
+    for (int i = 0; i < 17; ++i) ok = ok && isfinite(vals[i]);
+    ok = ok && c.fx != 0.f && c.fy != 0.f && c.near_t >= 0.f;
+    ViewData d;
+    memset(&d, 0, sizeof(d));
+    view_camera(c, d);
+    if (ok) {
+      d.prim_base = it.prim_offset;
+      d.prim_n = it.prim_count;
+      d.ntx = (d.width + w.tile - 1) / w.tile;
+      d.nty = (d.height + w.tile - 1) / w.tile;
+    } else {
+      d.width = d.height = 0;
+      d.prim_base = 0;
+      d.prim_n = 0;
+      d.ntx = d.nty = 0;
+      set_status(w.saved_hdr, MLPS_ERR_INVALID_ARGUMENT);
+    }
+    sv[v] = d;
+  }
+  __syncthreads();
+  if (v == 0) {
+    int ray_base = 0, pv_base = 0, tile_base = 0;
+    long long cand_base = 0;
+    for (int i = 0; i < w.V; ++i) {
+      ViewData& d = sv[i];
+      d.ray_base = ray_base;
+      d.pv_base = pv_base;
+      d.tile_base = tile_base;
+      d.cand_base = cand_base;
+      ray_base += d.width * d.height;
+      pv_base += d.prim_n;
+      tile_base += d.ntx * d.nty;
+      cand_base += (long long)d.ntx * d.nty * d.prim_n;
+    }
+  }
+  __syncthreads();
+  if (v < w.V) w.views[v] = sv[v];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -92,6 +178,7 @@ __global__ void k_prim_view(Work w) {
     v = lo;
   }
   const ViewData& V = w.views[v];
+  if (j - V.pv_base >= V.prim_n) return;  // past the live total (device item table)
   const int p = V.prim_base + (j - V.pv_base);
   const PrimGeo& g = w.geo[p];
   const bool ok = g.valid != 0;
@@ -543,6 +630,11 @@ __global__ void k_export_tiles(Work w, int* count, int* list) {
 
 void launch_store_views(const Work& w, const ViewArray& va, cudaStream_t st) {
   k_store_views<<<1, kMaxViews, 0, st>>>(w, va);
+}
+
+void launch_views_from_items(const Work& w, const mlps_batch_item* items, int max_w, int max_h, int max_p,
+                             cudaStream_t st) {
+  k_views_from_items<<<1, kMaxViews, 0, st>>>(w, items, max_w, max_h, max_p);
 }
 
 int launch_prim_setup(const Work& w, const float* c, const float* s, const float* q,

@@ -141,6 +141,10 @@ MLPS_DEV TileRays tile_rays(const Work& w, int t) {
   const ViewData& V = w.views[lo];
   const int lt = t - V.tile_base;
   TileRays r;
+  if (lt >= V.ntx * V.nty) {  // past the live total (device item table): no rays
+    r.base = r.W = r.x0 = r.y0 = r.tw = r.th = 0;
+    return r;
+  }
   r.base = V.ray_base;
   r.W = V.width;
   r.x0 = (lt % V.ntx) * w.tile;

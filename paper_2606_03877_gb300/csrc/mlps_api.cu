@@ -383,6 +383,26 @@ mlps_status specs_from_items(const mlps_batch_item* items, int n, int K, std::ve
   return MLPS_OK;
 }
 
+// Device item table of the *_dev batch calls: the layout is sized from the caps (every item at
+// max_width x max_height with max_prim_count primitives); k_views_from_items reads the items.
+struct DevTable {
+  const mlps_batch_item* items;
+  mlps_batch_caps caps;
+};
+
+mlps_status specs_from_caps(int n, const mlps_batch_caps* caps, int K, std::vector<ViewSpec>* out) {
+  if (!caps || n < 1 || n > kMaxViews || K < 0) return MLPS_ERR_INVALID_ARGUMENT;
+  if (caps->max_width < 1 || caps->max_height < 1 || caps->max_width > 16384 || caps->max_height > 16384 ||
+      caps->max_prim_count < 0)
+    return MLPS_ERR_INVALID_ARGUMENT;
+  mlps_camera c;
+  std::memset(&c, 0, sizeof(c));
+  c.width = caps->max_width;
+  c.height = caps->max_height;
+  out->assign(n, ViewSpec{c, 0, std::min(caps->max_prim_count, K)});
+  return MLPS_OK;
+}
+
 ViewArray make_views(const ViewSpec* vs, int V, int tile) {
   ViewArray va;
   std::memset(&va, 0, sizeof(va));
@@ -411,14 +431,7 @@ ViewArray make_views(const ViewSpec* vs, int V, int tile) {
     pv_base += vs[v].prim_n;
     tile_base += d.ntx * d.nty;
     cand_base += (long long)d.ntx * d.nty * vs[v].prim_n;
-    for (int i = 0; i < 3; ++i) {
-      // origin -R^T t in FP64, split into hi + lo
-      double o = -((double)d.R[0 * 3 + i] * d.t[0] + (double)d.R[1 * 3 + i] * d.t[1] +
-                   (double)d.R[2 * 3 + i] * d.t[2]);
-      float hi = (float)o;
-      d.o_hi[i] = hi;
-      d.o_lo[i] = (float)(o - (double)hi);
-    }
+    // (the ray origin is formed on the device: k_store_views)
   }
   return va;
 }
@@ -446,7 +459,7 @@ mlps_status workspace_impl(const mlps_config* cfg, int K, const std::vector<View
 // Forward over views `vs` (validated cameras and primitive ranges).
 mlps_status forward_impl(const mlps_config* cfg, const mlps_scene* scene, const std::vector<ViewSpec>& vs,
                          float* rgb, float* trans, float* feat, void* saved, size_t saved_bytes,
-                         void* scratch, size_t scratch_bytes, void* stream) {
+                         void* scratch, size_t scratch_bytes, void* stream, const DevTable* dev = nullptr) {
   if (!scene || scene->K < 0 || !rgb || !trans || !saved || !scratch)
     return MLPS_ERR_INVALID_ARGUMENT;
   if (cfg->feat_dim + cfg->slot_dim > 0 && !feat) return MLPS_ERR_INVALID_ARGUMENT;
@@ -478,7 +491,11 @@ mlps_status forward_impl(const mlps_config* cfg, const mlps_scene* scene, const 
     StageTimer tm(ST_SETUP, st);
     cudaMemsetAsync(w.saved_hdr, 0, 256, st);
     cudaMemsetAsync(w.prim_count, 0, sizeof(int) * ((size_t)K + 1), st);
-    launch_store_views(w, make_views(vs.data(), n_views, cfg->tile), st);
+    if (dev)
+      launch_views_from_items(w, dev->items, dev->caps.max_width, dev->caps.max_height,
+                              dev->caps.max_prim_count, st);
+    else
+      launch_store_views(w, make_views(vs.data(), n_views, cfg->tile), st);
     count_launch(1 + launch_prim_setup(w, scene->centers, scene->scales, scene->quats, st));
   }
   {
@@ -797,6 +814,52 @@ mlps_status mlps_render_batch_backward(const mlps_config* cfg, const mlps_scene*
   std::vector<ViewSpec> vs;
   s = specs_from_items(items, n_items, scene->K, &vs);
   if (s != MLPS_OK) return s;
+  return backward_impl(cfg, scene, vs, d_rgb, d_trans, d_feat, saved, saved_bytes, d_weights, d_centers,
+                       d_scales, d_quats, scratch, scratch_bytes, stream);
+}
+
+mlps_status mlps_batch_workspace_size_dev(const mlps_config* cfg, int32_t K, int32_t n_items,
+                                          const mlps_batch_caps* caps, size_t* saved_bytes,
+                                          size_t* scratch_bytes) {
+  mlps_status s = mlps_check_config(cfg);
+  if (s != MLPS_OK) return s;
+  if (K < 0 || !saved_bytes || !scratch_bytes) return MLPS_ERR_INVALID_ARGUMENT;
+  std::vector<ViewSpec> vs;
+  s = specs_from_caps(n_items, caps, K, &vs);
+  if (s != MLPS_OK) return s;
+  return workspace_impl(cfg, K, vs, saved_bytes, scratch_bytes);
+}
+
+mlps_status mlps_render_batch_forward_dev(const mlps_config* cfg, const mlps_scene* scene,
+                                          const mlps_batch_item* dev_items, int32_t n_items,
+                                          const mlps_batch_caps* caps, float* rgb, float* trans,
+                                          float* feat, void* saved, size_t saved_bytes, void* scratch,
+                                          size_t scratch_bytes, void* stream) {
+  mlps_status s = mlps_check_config(cfg);
+  if (s != MLPS_OK) return s;
+  if (!scene || scene->K < 0 || !dev_items) return MLPS_ERR_INVALID_ARGUMENT;
+  std::vector<ViewSpec> vs;
+  s = specs_from_caps(n_items, caps, scene->K, &vs);
+  if (s != MLPS_OK) return s;
+  const DevTable dev{dev_items, *caps};
+  return forward_impl(cfg, scene, vs, rgb, trans, feat, saved, saved_bytes, scratch, scratch_bytes, stream,
+                      &dev);
+}
+
+mlps_status mlps_render_batch_backward_dev(const mlps_config* cfg, const mlps_scene* scene,
+                                           const mlps_batch_item* dev_items, int32_t n_items,
+                                           const mlps_batch_caps* caps, const float* d_rgb,
+                                           const float* d_trans, const float* d_feat, const void* saved,
+                                           size_t saved_bytes, float* d_weights, float* d_centers,
+                                           float* d_scales, float* d_quats, void* scratch,
+                                           size_t scratch_bytes, void* stream) {
+  mlps_status s = mlps_check_config(cfg);
+  if (s != MLPS_OK) return s;
+  if (!scene || scene->K < 0 || !dev_items) return MLPS_ERR_INVALID_ARGUMENT;
+  std::vector<ViewSpec> vs;
+  s = specs_from_caps(n_items, caps, scene->K, &vs);
+  if (s != MLPS_OK) return s;
+  // (the views the forward call stored in `saved` are reused)
   return backward_impl(cfg, scene, vs, d_rgb, d_trans, d_feat, saved, saved_bytes, d_weights, d_centers,
                        d_scales, d_quats, scratch, scratch_bytes, stream);
 }

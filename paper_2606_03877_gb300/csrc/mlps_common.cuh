@@ -280,6 +280,13 @@ struct Work {
   float t_eps;
 };
 
+// Rays of all views together (views are stored in ray order). With a device-resident item
+// table the ray arrays are sized for the caps and the live total can be smaller.
+MLPS_DEV int live_rays(const Work& w) {
+  const ViewData& V = w.views[w.V - 1];
+  return V.ray_base + V.width * V.height;
+}
+
 // View of a global ray (views are stored in ray order; at most kMaxViews, binary search).
 MLPS_DEV int view_of_ray(const Work& w, int ray) {
   int lo = 0, hi = w.V - 1;

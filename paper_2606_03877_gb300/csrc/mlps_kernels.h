@@ -81,6 +81,9 @@ struct TcPlan {
 
 // k_geometry.cu
 void launch_store_views(const Work& w, const ViewArray& va, cudaStream_t st);
+// View records from a device item table (checked against the caps; bases as running sums).
+void launch_views_from_items(const Work& w, const mlps_batch_item* items, int max_w, int max_h, int max_p,
+                             cudaStream_t st);
 // returns the number of kernels launched
 int launch_prim_setup(const Work& w, const float* c, const float* s, const float* q,
                       cudaStream_t st);

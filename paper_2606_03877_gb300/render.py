@@ -5,6 +5,7 @@ PyTorch supplies device memory and the stream only; every step of the render run
 """
 from __future__ import annotations
 
+import ctypes
 from typing import Dict, List, Optional, Sequence
 
 import torch
@@ -273,6 +274,99 @@ class BatchRenderer:
         """Per-item [H_i, W_i, ...] views of a concatenated per-pixel tensor."""
         return [t[self.offsets[i]:self.offsets[i + 1]].view(h, w, *t.shape[1:])
                 for i, (h, w) in enumerate(self.sizes)]
+
+    def status(self, region: str = "saved") -> int:
+        t = self.saved if region == "saved" else self.scratch
+        return _lib.mlps_read_status(t, _stream())
+
+
+class DeviceBatchRenderer:
+    """A batch whose item table lives in device memory (mlps_render_batch_*_dev).
+
+    ``n`` items of at most ``max_width`` x ``max_height`` pixels and ``max_prims`` primitives each,
+    over ONE concatenated set of scene arrays with ``K`` primitives. The item table is a device
+    tensor written by ``set_items`` (an ordinary stream copy), so a CUDA graph captured around
+    ``forward`` / ``backward`` renders whatever items the table holds at replay time. Outputs are
+    sized for the caps; items are concatenated at their actual sizes (``split``)."""
+
+    def __init__(self, shape, n: int, max_width: int, max_height: int, max_prims: int, K: int,
+                 precision: str = "bf16", device: str = "cuda", **kw):
+        self.shape = shape
+        self.precision = precision
+        self.cfg = make_config(shape, precision, **kw)
+        st = _lib.mlps_check_config(self.cfg)
+        if st != _lib.MLPS_OK:
+            raise _lib.MlpsError("mlps_check_config", st)
+        self.device = torch.device(device)
+        self.P = _lib.mlps_param_count(self.cfg)
+        self.stride = _lib.mlps_weight_stride(self.cfg)
+        self.F = int(shape.feat_dim) + int(getattr(shape, "slot_dim", 0))
+        self.K = int(K)
+        self.n = int(n)
+        self.caps = _lib.batch_caps(max_width, max_height, max_prims)
+        self.cap_pixels = self.n * int(max_width) * int(max_height)
+        sb, tb = _lib.mlps_batch_workspace_size_dev(self.cfg, self.K, self.n, self.caps)
+        self.saved = torch.empty(sb, dtype=torch.uint8, device=self.device)
+        self.scratch = torch.empty(tb, dtype=torch.uint8, device=self.device)
+        self.item_bytes = ctypes.sizeof(_lib.MlpsBatchItem)
+        self.items_dev = torch.zeros(self.n * self.item_bytes, dtype=torch.uint8, device=self.device)
+        self.sizes = []
+        self._scene = None
+
+    def set_items(self, items: Sequence[tuple]):
+        """Write (prim_offset, prim_count, camera) tuples into the device table (stream-ordered)."""
+        assert len(items) == self.n
+        arr = _lib.batch_items(items)
+        host = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
+        self.items_dev.copy_(host.to(self.device))
+        self.sizes = [(int(c["height"]), int(c["width"])) for _, _, c in items]
+
+    def pack(self, weights: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        w = weights.detach().to(self.device, torch.float32).contiguous()
+        assert w.shape == (self.K, self.P), (w.shape, self.K, self.P)
+        if out is None:
+            out = torch.empty(max(self.K, 1) * self.stride, dtype=torch.uint8, device=self.device)
+        _lib.mlps_pack_weights(self.cfg, self.K, w, out, _stream())
+        return out
+
+    def new_outputs(self) -> Dict[str, torch.Tensor]:
+        P, dev = self.cap_pixels, self.device
+        return {"rgb": torch.zeros(P, 3, device=dev), "trans": torch.zeros(P, device=dev),
+                "feat": torch.zeros(P, self.F, device=dev) if self.F else None}
+
+    def new_grads(self) -> Dict[str, torch.Tensor]:
+        K, dev = self.K, self.device
+        return {"d_weights": torch.empty(K, self.P, device=dev), "d_centers": torch.empty(K, 3, device=dev),
+                "d_scales": torch.empty(K, 3, device=dev), "d_quats": torch.empty(K, 4, device=dev)}
+
+    def forward(self, centers, scales, quats, packed, out: Optional[Dict[str, torch.Tensor]] = None):
+        if out is None:
+            out = self.new_outputs()
+        self._scene = _lib.make_scene(self.K, centers, scales, quats, packed)
+        self._keep = (centers, scales, quats, packed)
+        _lib.mlps_render_batch_forward_dev(self.cfg, self._scene, self.items_dev, self.n, self.caps, out["rgb"],
+                                           out["trans"], out.get("feat"), self.saved, self.saved.numel(),
+                                           self.scratch, self.scratch.numel(), _stream())
+        return out
+
+    def backward(self, d_rgb, d_trans=None, d_feat=None, out: Optional[Dict[str, torch.Tensor]] = None):
+        if out is None:
+            out = self.new_grads()
+        _lib.mlps_render_batch_backward_dev(self.cfg, self._scene, self.items_dev, self.n, self.caps,
+                                            d_rgb.contiguous(), None if d_trans is None else d_trans.contiguous(),
+                                            None if d_feat is None else d_feat.contiguous(), self.saved,
+                                            self.saved.numel(), out["d_weights"], out["d_centers"],
+                                            out["d_scales"], out["d_quats"], self.scratch, self.scratch.numel(),
+                                            _stream())
+        return out
+
+    def split(self, t: torch.Tensor) -> List[torch.Tensor]:
+        """Per-item [H_i, W_i, ...] views (sizes of the last set_items) of a per-pixel tensor."""
+        outs, o = [], 0
+        for h, w in self.sizes:
+            outs.append(t[o:o + h * w].view(h, w, *t.shape[1:]))
+            o += h * w
+        return outs
 
     def status(self, region: str = "saved") -> int:
         t = self.saved if region == "saved" else self.scratch

@@ -1,6 +1,7 @@
 """CPU-only checks of the C ABI: the library builds, loads and exports every declared symbol,
 and its host-side shape/validation logic agrees with the documented layouts. No CUDA work is
 enqueued here."""
+import ctypes
 import os
 import re
 
@@ -34,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert _lib.mlps_abi_version() == 5
+    assert _lib.mlps_abi_version() == 6
     for s in range(8):
         assert _lib.mlps_status_string(s)
     assert _lib.mlps_status_string(4) == "hit capacity overflow"
@@ -130,9 +131,30 @@ def test_batch_item_validation(lib):
     _lib.mlps_batch_workspace_size(cfg, 30, _lib.batch_items([(0, 10, cams[0]), (10, 20, big)]), 2)
 
 
+def test_device_table_workspace_and_validation(lib):
+    """A device-table batch is sized as a host table whose items all sit at the caps; the host
+    checks the caps and the item count (the items themselves are checked on the device)."""
+    c = synth.CONFIGS["prec"].replace(width=80, height=64, n_views=3)
+    cfg = make_config(c)
+    cams = synth.make_cameras(c)
+    host = _lib.mlps_batch_workspace_size(cfg, 90, _lib.batch_items([(0, 30, cam) for cam in cams]), 3)
+    assert _lib.mlps_batch_workspace_size_dev(cfg, 90, 3, _lib.batch_caps(80, 64, 30)) == host
+    for n, caps in ((3, (0, 64, 30)), (3, (80, -1, 30)), (3, (80, 64, -1)), (0, (80, 64, 30)),
+                    (65, (80, 64, 30)), (3, (20000, 64, 30))):
+        with pytest.raises(_lib.MlpsError) as e:
+            _lib.mlps_batch_workspace_size_dev(cfg, 90, n, _lib.batch_caps(*caps))
+        assert e.value.status == _lib.MLPS_ERR_INVALID_ARGUMENT
+    # a null item table is refused before any launch
+    scene = _lib.MlpsScene(0, None, None, None, None)
+    st = lib.mlps_render_batch_forward_dev(ctypes.byref(cfg), ctypes.byref(scene), None, 3,
+                                           ctypes.byref(_lib.batch_caps(80, 64, 30)), None, None, None, None, 0,
+                                           None, 0, None)
+    assert st == _lib.MLPS_ERR_INVALID_ARGUMENT
+
+
 def test_contact_mode_validation(lib):
-    """Contact-point mode (Sec. 3.2) takes one sample per hit; its forward runs in every
-    precision, its backward on the FP32 path."""
+    """Contact-point mode (Sec. 3.2) takes one sample per hit; its forward and backward run in
+    every precision."""
     c = synth.CONFIGS["contact"]
     assert _lib.mlps_check_config(make_config(c)) == _lib.MLPS_OK
     assert _lib.mlps_check_config(make_config(c.replace(samples=2))) == _lib.MLPS_ERR_INVALID_ARGUMENT
