@@ -97,6 +97,27 @@ def max_over_ranks(ms: float, ws: int, device=None) -> float:
     return float(t.item())
 
 
+def grad_buffers(K: int, P: int, device=None):
+    """One flat FP32 buffer holding the per-primitive gradients (dL/dweights [K, P], dL/dcentres,
+    dL/dscales [K, 3], dL/dquats [K, 4]) and its named views, so that the data-parallel step
+    sums them across ranks with one all-reduce."""
+    import torch
+    flat = torch.zeros(K * (P + 10), device=device)
+    views, o = {}, 0
+    for name, n in (("d_weights", P), ("d_centers", 3), ("d_scales", 3), ("d_quats", 4)):
+        views[name] = flat[o:o + K * n].view(K, n)
+        o += K * n
+    return flat, views
+
+
+def allreduce_grads(flat, ws: int) -> None:
+    """The backward's one exchange: every rank renders its own views of the same scene, so the
+    job's gradient is the SUM of the ranks' (no-op for one rank)."""
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(flat)
+
+
 def job_rays_per_s(rays_per_rank: int, ws: int, steps: int, total_ms: float) -> float:
     """Whole-job throughput: the rays of all ranks and steps over the max-over-ranks time."""
     return rays_per_rank * ws * steps / (total_ms / 1e3)
@@ -297,6 +318,7 @@ def run_ours(a):
         rr.forward(d["centers"], d["scales"], d["quats"], packed, cams, out=rr._out_buf)
         if bwd:
             rr.backward(g_rgb, None, g_feat, out=rr._grad_buf)
+            allreduce_grads(rr._grad_flat, ws)  # data-parallel: sum the ranks' gradients
 
     def bind_buffers(rr):
         rr._packed_buf = torch.empty(max(wl.K, 1) * rr.stride, dtype=torch.uint8, device=dev)
@@ -304,8 +326,7 @@ def run_ours(a):
                        "trans": torch.empty(wl.n_views, wl.height, wl.width, device=dev),
                        "feat": torch.empty(wl.n_views, wl.height, wl.width, FT, device=dev)
                        if FT else None}
-        rr._grad_buf = {"d_weights": torch.empty(wl.K, rr.P, device=dev), "d_centers": torch.empty(wl.K, 3, device=dev),
-                        "d_scales": torch.empty(wl.K, 3, device=dev), "d_quats": torch.empty(wl.K, 4, device=dev)}
+        rr._grad_flat, rr._grad_buf = grad_buffers(wl.K, rr.P, dev)
 
     def timed(rr, bwd, steps, warmup, sample_clocks=False, profile=False):
         bind_buffers(rr)
@@ -435,7 +456,9 @@ def run_ours(a):
                    "pass": "fwd+bwd" if do_bwd else "fwd", "precision": precision,
                    "rays_per_step": n_rays * ws, "hits_per_step": n_hits,
                    "l2": "flushed between timed steps (256 MiB write); per-step working set > L2",
-                   "parallelism": f"views sharded, {ws} rank(s), no data-path collective"},
+                   "parallelism": f"views sharded, {ws} rank(s), " +
+                                  ("one gradient sum all-reduce (NCCL) per step" if do_bwd and ws > 1
+                                   else "no data-path collective")},
         "results": results,
         "clocks": clocks,
         "gpu_launches": int(launches),

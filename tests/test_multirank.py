@@ -1,7 +1,8 @@
 """The multi-rank (one process per GPU) host logic of the benchmark, on CPU with gloo and two
-ranks: each rank renders its own views (weak scaling, no data-path collective), the job's time
-is the slowest rank's, and the sharded renders together equal one render of all the views.
-Rendering here is the FP64 oracle on a tiny image (what needs no GPU)."""
+ranks: each rank renders its own views (weak scaling), the job's time is the slowest rank's,
+the sharded renders together equal one render of all the views, and the backward's one
+exchange (the sum all-reduce of the per-primitive gradients) gives the gradient of the whole
+job. Rendering here is the FP64 oracle on a tiny image (what needs no GPU)."""
 import os
 import socket
 
@@ -80,3 +81,50 @@ def test_hit_capacity_per_workload():
     assert bench.hit_capacity(auto, synth.CONFIGS["stress"]) == 16.0
     assert bench.hit_capacity(auto, synth.CONFIGS["prec"]) == 8.0
     assert bench.hit_capacity(types.SimpleNamespace(hit_capacity=12.0), synth.CONFIGS["prec"]) == 12.0
+
+
+def _grad_worker(rank, ws, port, out_dir):
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        wl = synth.CONFIGS["prec"].replace(width=12, height=10, K=6, n_views=1)
+        scene = synth.make_scene(wl, 0)
+        scene = dict(scene, scales=(scene["scales"] * 3.0))
+        cams = synth.make_cameras(wl, first_view_seed=bench.rank_view_seed(rank, wl.n_views))
+        g = synth.make_grad((ws, wl.height * wl.width, 3), seed=9)[rank]
+        ref = oracle.render_backward(wl, scene, cams, oracle.all_pixels(cams), g, None, None)
+        P = ref["d_weights"].shape[1]
+        flat, views = bench.grad_buffers(wl.K, P)
+        for k, v in views.items():
+            v.copy_(torch.from_numpy(np.asarray(ref[k], dtype=np.float32)))
+        bench.allreduce_grads(flat, ws)
+        np.save(os.path.join(out_dir, f"grad{rank}.npy"), flat.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_gradient_allreduce_is_the_job_gradient(tmp_path):
+    """Data-parallel backward: rank r renders view r with its share of dL/dC; after the sum
+    all-reduce every rank holds the gradient of the loss over both views (the oracle's, one
+    process, both cameras)."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    ws, port = 2, _free_port()
+    mp.start_processes(_grad_worker, args=(ws, port, str(tmp_path)), nprocs=ws, join=True, start_method="spawn")
+    wl = synth.CONFIGS["prec"].replace(width=12, height=10, K=6, n_views=ws)
+    scene = synth.make_scene(wl, 0)
+    scene = dict(scene, scales=(scene["scales"] * 3.0))
+    cams = synth.make_cameras(wl)
+    g = synth.make_grad((ws, wl.height * wl.width, 3), seed=9).reshape(-1, 3)
+    ref = oracle.render_backward(wl, scene, cams, oracle.all_pixels(cams), g, None, None)
+    want = np.concatenate([np.asarray(ref[k], dtype=np.float64).reshape(-1)
+                           for k in ("d_weights", "d_centers", "d_scales", "d_quats")])
+    assert np.abs(want).max() > 0
+    for r in range(ws):
+        got = np.load(tmp_path / f"grad{r}.npy").astype(np.float64)
+        assert np.allclose(got, want, rtol=1e-5, atol=1e-6 * np.abs(want).max())
