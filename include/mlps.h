@@ -349,6 +349,13 @@ mlps_status mlps_render_batch_backward_dev(const mlps_config* cfg, const mlps_sc
                                            float* d_scales, float* d_quats, void* scratch,
                                            size_t scratch_bytes, void* stream);
 
+/* Inspection of the last backward pass: *chunks = the MLP chunks of the forward pass (<= ipc
+ * intervals of one primitive each), *live = those the backward pass walked (the chunks holding
+ * an interval with a nonzero gradient: intervals behind a ray's early-termination point, and
+ * rays with zero dL/dC, have none). Synchronises `stream`. */
+mlps_status mlps_backward_chunk_counts(const void* saved, const void* scratch, int64_t* chunks,
+                                       int64_t* live, void* stream);
+
 /* Synchronise `stream`, return the device status word of a `saved` or `scratch` region
  * written by the calls above (MLPS_OK if none), and clear it. */
 mlps_status mlps_read_status(const void* region, void* stream);

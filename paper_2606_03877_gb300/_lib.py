@@ -135,6 +135,7 @@ _SIGS = [
                                                     ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
     ("mlps_read_status", ctypes.c_int32, [_vp, _vp]),
     ("mlps_saved_hit_count", ctypes.c_int32, [_vp, _P(ctypes.c_int64), _vp]),
+    ("mlps_backward_chunk_counts", ctypes.c_int32, [_vp, _vp, _P(ctypes.c_int64), _P(ctypes.c_int64), _vp]),
     ("mlps_export_hits", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsCamera), ctypes.c_int32, _vp,
                                           ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mlps_export_tiles", ctypes.c_int32, [_P(MlpsConfig), ctypes.c_int32, _P(MlpsCamera),
@@ -185,6 +186,15 @@ def _ptr(x) -> Optional[int]:
 def _check(fn: str, st: int):
     if st != MLPS_OK:
         raise MlpsError(fn, st)
+
+
+def mlps_backward_chunk_counts(saved, scratch, stream: int = 0):
+    """(chunks of the forward pass, chunks the last backward pass walked)."""
+    a = ctypes.c_int64()
+    b = ctypes.c_int64()
+    _check("mlps_backward_chunk_counts", load().mlps_backward_chunk_counts(
+        _ptr(saved), _ptr(scratch), ctypes.byref(a), ctypes.byref(b), stream or None))
+    return int(a.value), int(b.value)
 
 
 def mlps_abi_version() -> int:

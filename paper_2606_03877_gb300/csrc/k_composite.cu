@@ -149,6 +149,186 @@ void launch_composite_bwd(const Work& w, int F, int FT, const float* d_rgb, cons
   k_composite_bwd<<<(w.n_rays + 255) / 256, 256, 0, st>>>(w, F, FT, d_rgb, d_trans, d_feat, slot_ga);
 }
 
+// ------------------------------------------------------------------------------------------
+// The MLP backward's interval lists. An interval is live when it has a nonzero gradient:
+// dL/dC_j, dL/da_j or a feature gradient. Intervals behind a ray's early-termination point get
+// none from the reverse composite, nor do the intervals of rays whose dL/dC is zero (pixels
+// outside a training step's tile mask); such an interval adds nothing to any weight or pose
+// gradient (its delta rows and its pose-chain terms are all zero). The backward therefore gets
+// lists of the live intervals only, in the forward's primitive-major order: per primitive its
+// live count, start and chunk start, and for each list position the interval's forward
+// position. Four passes: flags with per-block counts, one scan of the counts, the ordered
+// write, and per primitive its range in the list (binary search) with the scan of its chunks.
+
+MLPS_DEV bool interval_live(const Work& w, int j, int F) {
+  const float4 g = w.hit_grad[j];
+  bool live = g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f;
+  for (int f = 0; f < F && !live; ++f) live = w.hit_gfeat[(size_t)j * F + f] != 0.f;
+  return live;
+}
+
+MLPS_DEV int n_intervals(const Work& w) { return min(w.saved_hdr[1], w.hit_cap); }
+
+constexpr int kLivePer = 4;  // intervals per thread (consecutive)
+
+// Live flags of this thread's intervals as bits, and their count.
+MLPS_DEV int live_bits(const Work& w, int j0, int F) {
+  const int n = n_intervals(w);
+  int bits = 0;
+#pragma unroll
+  for (int e = 0; e < kLivePer; ++e)
+    if (j0 + e < n && interval_live(w, j0 + e, F)) bits |= 1 << e;
+  return bits;
+}
+
+// Block-wide exclusive scan of one value per thread (kLiveBlock threads).
+MLPS_DEV int block_excl_scan(int v, int* swarp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += u;
+  }
+  if (lane == 31) swarp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int t = swarp[lane];
+    int y = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += u;
+    }
+    swarp[lane] = y - t;  // exclusive over warps
+  }
+  __syncthreads();
+  return swarp[warp] + x - v;
+}
+
+__global__ void __launch_bounds__(kLiveBlock) k_live_count(Work w, int F) {
+  __shared__ int scount;
+  const int j0 = (blockIdx.x * kLiveBlock + threadIdx.x) * kLivePer;
+  if (threadIdx.x == 0) scount = 0;
+  __syncthreads();
+  int c = __popc(live_bits(w, j0, F));
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&scount, c);
+  __syncthreads();
+  if (threadIdx.x == 0) w.live_bcount[blockIdx.x] = scount;
+}
+
+// Exclusive scan of the per-block counts (one block); the total goes to scratch header word 2.
+__global__ void __launch_bounds__(1024) k_live_scan(Work w, int nb) {
+  __shared__ int swarp[32];
+  __shared__ int carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? w.live_bcount[i] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    if (lane == 31) swarp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int y = swarp[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += u;
+      }
+      swarp[lane] = y;  // inclusive over warps
+    }
+    __syncthreads();
+    const int before = carry + (warp > 0 ? swarp[warp - 1] : 0) + x - v;
+    if (i < nb) w.live_bcount[i] = before;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = before + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) w.scr_hdr[2] = carry;
+}
+
+__global__ void __launch_bounds__(kLiveBlock) k_live_write(Work w, int F) {
+  __shared__ int swarp[32];
+  const int j0 = (blockIdx.x * kLiveBlock + threadIdx.x) * kLivePer;
+  const int bits = live_bits(w, j0, F);
+  int pos = w.live_bcount[blockIdx.x] + block_excl_scan(__popc(bits), swarp);
+#pragma unroll
+  for (int e = 0; e < kLivePer; ++e)
+    if (bits & (1 << e)) w.live_slot[pos++] = j0 + e;
+}
+
+// First list position whose forward position is >= x.
+MLPS_DEV int live_lower_bound(const int* a, int n, int x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Per primitive: its range of live intervals and (scan over the primitives, one block) its first
+// chunk; the chunk total goes to scratch header word 1.
+__global__ void __launch_bounds__(1024) k_live_prims(Work w) {
+  __shared__ int swarp[32];
+  __shared__ int carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n_live = w.scr_hdr[2];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < w.K; base += 1024) {
+    const int p = base + threadIdx.x;
+    int cnt = 0, ch = 0;
+    if (p < w.K) {
+      const int s0 = live_lower_bound(w.live_slot, n_live, w.prim_start[p]);
+      const int s1 = live_lower_bound(w.live_slot, n_live, w.prim_start[p] + w.prim_count[p]);
+      cnt = s1 - s0;
+      ch = (cnt + w.ipc - 1) / w.ipc;
+      w.live_prim_start[p] = s0;
+      w.live_prim_count[p] = cnt;
+    }
+    int x = ch;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    if (lane == 31) swarp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int y = swarp[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += u;
+      }
+      swarp[lane] = y;
+    }
+    __syncthreads();
+    const int before = carry + (warp > 0 ? swarp[warp - 1] : 0) + x - ch;
+    if (p < w.K) w.live_chunk_start[p] = before;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = before + ch;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    w.live_chunk_start[w.K] = carry;
+    w.live_prim_start[w.K] = n_live;
+    w.scr_hdr[1] = carry;
+  }
+}
+
+void launch_live_lists(const Work& w, int F, cudaStream_t st) {
+  const int nb = (w.hit_cap + kLiveBlock * kLivePer - 1) / (kLiveBlock * kLivePer);
+  k_live_count<<<nb, kLiveBlock, 0, st>>>(w, F);
+  k_live_scan<<<1, 1024, 0, st>>>(w, nb);
+  k_live_write<<<nb, kLiveBlock, 0, st>>>(w, F);
+  k_live_prims<<<1, 1024, 0, st>>>(w);
+}
+
 void launch_pose_bwd(const Work& w, float* d_centers, float* d_scales, float* d_quats,
                      cudaStream_t st) {
   if (w.K == 0) return;

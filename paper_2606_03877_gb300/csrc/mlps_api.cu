@@ -213,7 +213,8 @@ struct Layout {
       ray_count, prim_count, prim_start, chunk_start, prim_list, rec, slot_of, views, geo, pview,
       saved_total;
   // scratch
-  size_t prim_cursor, tile_count, tile_list, hit_grad, hit_gfeat, dgeo, slot_ga, slot_gu, dwb, scratch_total;
+  size_t prim_cursor, tile_count, tile_list, hit_grad, hit_gfeat, dgeo, slot_ga, slot_gu, dwb, live_slot,
+      live_bcount, live_prim_count, live_prim_start, live_chunk_start, scratch_total;
   long long hit_cap;
   long long n_rays, n_pairs, n_tiles_all, n_cand;
   int max_view_tiles;
@@ -280,6 +281,12 @@ bool make_layout(const mlps_config* c, int K, const ViewSpec* vs, int V, Layout*
     const Model mm = make_model(c);
     L->dwb = t.take<float>(c->hidden_width == 128 ? (size_t)n_sm * mm.P : 1);
   }
+  // the MLP backward's interval lists (live intervals only)
+  L->live_slot = t.take<int>(hc);
+  L->live_bcount = t.take<int>(hc / kLiveBlock + 2);
+  L->live_prim_count = t.take<int>((size_t)K + 1);
+  L->live_prim_start = t.take<int>((size_t)K + 1);
+  L->live_chunk_start = t.take<int>((size_t)K + 1);
   L->scratch_total = t.off;
   return true;
 }
@@ -322,6 +329,12 @@ Work make_work(const mlps_config* c, const Layout& L, int K, int V, void* saved,
       w.slot_gu = reinterpret_cast<float4*>(sc + L.slot_gu);
     }
     if (c->hidden_width == 128) w.dwb = reinterpret_cast<float*>(sc + L.dwb);
+    w.live_slot = reinterpret_cast<int*>(sc + L.live_slot);
+    w.live_bcount = reinterpret_cast<int*>(sc + L.live_bcount);
+    w.live_prim_count = reinterpret_cast<int*>(sc + L.live_prim_count);
+    w.live_prim_start = reinterpret_cast<int*>(sc + L.live_prim_start);
+    w.live_chunk_start = reinterpret_cast<int*>(sc + L.live_chunk_start);
+    // w.bslot stays null: only the MLP backward's copy of the Work points at the live lists
   }
   w.K = K;
   w.V = V;
@@ -615,15 +628,26 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
                          slot_grad ? w.slot_ga : nullptr, st);
     count_launch(w.n_rays > 0 ? 1 : 0);
   }
+  // the MLP backward walks its own lists: the intervals with a nonzero gradient only
+  Work wb = w;
+  if (K > 0) {
+    StageTimer tm(ST_COMP_BWD, st);
+    launch_live_lists(w, cfg->feat_dim, st);
+    count_launch(4);
+    wb.prim_count = w.live_prim_count;
+    wb.prim_start = w.live_prim_start;
+    wb.chunk_start = w.live_chunk_start;
+    wb.bslot = w.live_slot;
+  }
   if (K > 0) {
     StageTimer tm(ST_MLP_BWD, st);
     // width 128: the tensor-core kernel for the tensor-core precisions where it applies, else
     // the wide FP32 kernel
     const bool wide_tc = wide && tc && tc_bwd_wide_supported(m, P);
-    cudaError_t e = wide_tc ? launch_mlp_bwd_tc_wide(w, a, P, n_sm, st)
-                    : wide  ? launch_mlp_bwd_simt_wide(w, a, tc ? &P : nullptr, n_sm, st)
-                    : tc    ? launch_mlp_bwd_tc(w, a, P, n_sm, st)
-                            : launch_mlp_bwd_simt(w, a, n_sm, st);
+    cudaError_t e = wide_tc ? launch_mlp_bwd_tc_wide(wb, a, P, n_sm, st)
+                    : wide  ? launch_mlp_bwd_simt_wide(wb, a, tc ? &P : nullptr, n_sm, st)
+                    : tc    ? launch_mlp_bwd_tc(wb, a, P, n_sm, st)
+                            : launch_mlp_bwd_simt(wb, a, n_sm, st);
     if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
     if (e != cudaSuccess) return MLPS_ERR_CUDA;
     count_launch(1);
@@ -877,6 +901,20 @@ mlps_status mlps_read_status(const void* region, void* stream) {
     cudaStreamSynchronize(st);
   }
   return h;
+}
+
+mlps_status mlps_backward_chunk_counts(const void* saved, const void* scratch, int64_t* chunks,
+                                       int64_t* live, void* stream) {
+  if (!saved || !scratch || !chunks || !live) return MLPS_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h[3] = {0, 0, 0}, t[3] = {0, 0, 0};
+  if (cudaMemcpyAsync(h, saved, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(t, scratch, sizeof(t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MLPS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MLPS_ERR_CUDA;
+  *chunks = h[2];
+  *live = t[1];
+  return MLPS_OK;
 }
 
 mlps_status mlps_saved_hit_count(const void* saved, int64_t* n_hits, void* stream) {

@@ -157,6 +157,10 @@ cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
 // F MLP feature channels in rows of FT floats (FT = F + slot channels)
 void launch_composite_fwd(const Work& w, int F, int FT, float* rgb, float* trans, float* feat,
                           cudaStream_t st);
+// The MLP backward's interval lists (the intervals with a nonzero gradient, in the forward's
+// primitive-major order) into w.live_*; chunk total in scratch header word 1, interval total in
+// word 2 (4 launches).
+void launch_live_lists(const Work& w, int F, cudaStream_t st);
 void launch_composite_bwd(const Work& w, int F, int FT, const float* d_rgb, const float* d_trans,
                           const float* d_feat, const float* slot_ga, cudaStream_t st);
 void launch_pose_bwd(const Work& w, float* d_centers, float* d_scales, float* d_quats,

@@ -122,6 +122,10 @@ class Renderer:
     def hit_count(self) -> int:
         return _lib.mlps_saved_hit_count(self.saved, _stream())
 
+    def chunk_counts(self):
+        """(MLP chunks of the last forward pass, chunks its last backward pass walked)."""
+        return _lib.mlps_backward_chunk_counts(self.saved, self.scratch, _stream())
+
     def hits(self, max_out: int = 64):
         _, cs, V, K, _ = self._last
         n_rays = V * cs[0].width * cs[0].height
