@@ -538,38 +538,77 @@ def run_e2e(a, wl, scene, cams, precision, do_bwd, dev):
     bo = rgb_h.numel() * 4 + tr_h.numel() * 4 + ((gw_h.numel() + gp_h.numel()) * 4 if do_bwd else 0)
     bo += ft_h.numel() * 4 if FT else 0
 
+    # Copies on two streams of their own, double-buffered on the device: each step's dL/dC
+    # upload runs during its forward pass and its image download during its backward pass; the
+    # small scene upload and gradient download stay on the compute stream. Every copy is inside
+    # the timed region (the compute stream joins both copy streams before the end event).
+    main = torch.cuda.current_stream(dev)
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    outs = [{"rgb": torch.empty(wl.n_views, wl.height, wl.width, 3, device=dev),
+             "trans": torch.empty(wl.n_views, wl.height, wl.width, device=dev),
+             "feat": torch.empty(wl.n_views, wl.height, wl.width, FT, device=dev) if FT else None}
+            for _ in range(2)]
+    g_devs = [g_dev, torch.empty_like(g_dev)]
+    gf_devs = [gf_dev, torch.empty_like(gf_dev)] if FT else [None, None]
+    ev = {k: [torch.cuda.Event(), torch.cuda.Event()] for k in ("g_ready", "g_free", "fwd", "out_done")}
+    for b in range(2):
+        ev["g_free"][b].record(main)
+        ev["out_done"][b].record(main)
+    it = [0]
+
     def step():
+        b = it[0] & 1
+        it[0] += 1
         for k in dd:
             dd[k].copy_(host[k], non_blocking=True)
-        packed = r.pack(dd["weights"])
-        out = r.forward(dd["centers"], dd["scales"], dd["quats"], packed, cams)
         if do_bwd:
-            g_dev.copy_(g_host, non_blocking=True)
+            with torch.cuda.stream(s_in):
+                s_in.wait_event(ev["g_free"][b])  # the backward that read this buffer is done
+                g_devs[b].copy_(g_host, non_blocking=True)
+                if FT:
+                    gf_devs[b].copy_(gf_host, non_blocking=True)
+                ev["g_ready"][b].record(s_in)
+        packed = r.pack(dd["weights"])
+        main.wait_event(ev["out_done"][b])  # the download of this output buffer is done
+        out = r.forward(dd["centers"], dd["scales"], dd["quats"], packed, cams, out=outs[b])
+        ev["fwd"][b].record(main)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev["fwd"][b])
+            rgb_h.copy_(out["rgb"], non_blocking=True)
+            tr_h.copy_(out["trans"], non_blocking=True)
             if FT:
-                gf_dev.copy_(gf_host, non_blocking=True)
-            g = r.backward(g_dev, None, gf_dev)
+                ft_h.copy_(out["feat"], non_blocking=True)
+            ev["out_done"][b].record(s_out)
+        if do_bwd:
+            main.wait_event(ev["g_ready"][b])
+            g = r.backward(g_devs[b], None, gf_devs[b])
+            ev["g_free"][b].record(main)
             gw_h.copy_(g["d_weights"], non_blocking=True)
             gp_h[:, 0:3].copy_(g["d_centers"], non_blocking=True)
             gp_h[:, 3:6].copy_(g["d_scales"], non_blocking=True)
             gp_h[:, 6:10].copy_(g["d_quats"], non_blocking=True)
-        rgb_h.copy_(out["rgb"], non_blocking=True)
-        tr_h.copy_(out["trans"], non_blocking=True)
-        if FT:
-            ft_h.copy_(out["feat"], non_blocking=True)
+
+    def join():
+        main.wait_stream(s_in)
+        main.wait_stream(s_out)
 
     for _ in range(2):
         step()
+    join()
     torch.cuda.synchronize()
     steps = max(3, a.steps // 2)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    e0.record(main)
     for _ in range(steps):
         step()
-    e1.record()
+    join()
+    e1.record(main)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     return {"value": wl.n_rays * steps / (ms / 1e3), "unit": "rays/s", "h2d_bytes_per_step": int(bi),
-            "d2h_bytes_per_step": int(bo), "steps": steps}
+            "d2h_bytes_per_step": int(bo), "steps": steps,
+            "copies": "dL/dC upload overlapped with the forward pass, image download with the backward pass "
+                      "(two copy streams, double-buffered); scene upload and gradient download on the compute stream"}
 
 
 def cpu_baseline(a, wl, scene, cams, do_bwd, r=None):
