@@ -63,6 +63,23 @@ MLPS_DEV bool mbar_try_wait(uint32_t addr, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait with an explicit suspend-time hint: a thread whose phase is not complete sleeps until
+// it completes or `kSuspendNs` pass (instead of the short system-dependent limit), so a waiting
+// warp takes no issue slots from the warps that are working.
+constexpr uint32_t kSuspendNs = 20000;
+
+MLPS_DEV bool mbar_try_wait_sleep(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity), "n"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for phase `parity` of the barrier, giving up after `limit_ns` of wall time or as soon as
 // another role has raised the block's abort flag. Returns false when it gave up (and raises
 // the flag itself on a timeout).
@@ -70,14 +87,12 @@ MLPS_DEV bool mbar_wait(uint32_t addr, uint32_t parity, volatile int* abort_flag
                         uint64_t limit_ns) {
   if (mbar_try_wait(addr, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(addr, parity)) return true;
-    if ((it & 63u) == 0u) {
-      if (*abort_flag) return false;
-      if (globaltimer_ns() - t0 > limit_ns) {
-        *abort_flag = 1;
-        return false;
-      }
+  for (;;) {
+    if (mbar_try_wait_sleep(addr, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer_ns() - t0 > limit_ns) {
+      *abort_flag = 1;
+      return false;
     }
   }
 }
@@ -87,9 +102,9 @@ MLPS_DEV bool mbar_wait(uint32_t addr, uint32_t parity, volatile int* abort_flag
 MLPS_DEV bool mbar_wait_limit(uint32_t addr, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(addr, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(addr, parity)) return true;
-    if ((it & 63u) == 0u && globaltimer_ns() - t0 > limit_ns) return false;
+  for (;;) {
+    if (mbar_try_wait_sleep(addr, parity)) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
 
