@@ -154,6 +154,58 @@ def test_full_size_prec_sampled_gradients_bf16():
         assert e < 2e-2, (k, errs)
 
 
+def test_full_size_stress_sampled_gradients_fp32():
+    """The stress network (4 x 128, 16-d feature head, S = 48, K = 1024) at 1080p (one view):
+    L2 loss on 1500 sampled pixels against the perturbed scene's oracle render, the oracle's
+    reverse mode on those pixels; the backward walks only their intervals."""
+    cfg = synth.CONFIGS["stress"].replace(n_views=1)
+    scene = synth.make_scene(cfg, 0)
+    cams = synth.make_cameras(cfg)
+    pix = synth.sample_pixels(cfg, 1500, seed=23)
+    cur, _, Fc = oracle.render(cfg, scene, cams, pix=pix)
+    tgt, _, Ft = oracle.render(cfg, synth.perturb_scene(scene, cfg, 1), cams, pix=pix)
+    idx = pixel_index(cfg.width, cfg.height, pix)
+    g = np.zeros((1, cfg.height, cfg.width, 3), np.float32)
+    gF = np.zeros((1, cfg.height, cfg.width, cfg.feat_dim), np.float32)
+    gl, gFl = (cur - tgt).astype(np.float32), (Fc - Ft).astype(np.float32)
+    g.reshape(-1, 3)[idx] = gl
+    gF.reshape(-1, cfg.feat_dim)[idx] = gFl
+    got, _ = _run(cfg, scene, cams, g, None, gF)
+    ref = oracle.render_backward(cfg, scene, cams, pix, gl, None, gFl)
+    errs = {k: rel_l2(got[k], ref[rk]) for k, rk in GROUPS}
+    print("stress full-size sampled FP32 gradient rel-L2:", errs)
+    for k, e in errs.items():
+        assert e < TOL, (k, errs)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_stress_many_chunks_tensor_core_backward_matches_fp32(precision):
+    """The width-128 tensor-core backward over many chunks per primitive and SM (960 x 540,
+    K = 1024: ~4 M intervals), dense L2-loss gradient against the GPU FP32 render of the
+    perturbed scene, compared with the FP32 wide backward (itself within 2e-5 of the oracle on
+    the small stress shape): every group within the BF16 bar."""
+    cfg = synth.CONFIGS["stress"].replace(width=960, height=540, n_views=1)
+    scene = synth.make_scene(cfg, 0)
+    cams = synth.make_cameras(cfg)
+
+    def render32(sc):
+        r = Renderer(cfg, precision="fp32")
+        d = to_dev(sc)
+        out = r.forward(d["centers"], d["scales"], d["quats"], r.pack(d["weights"]), cams)
+        torch.cuda.synchronize()
+        return out["rgb"].cpu().numpy(), out["feat"].cpu().numpy()
+
+    c32, f32 = render32(scene)
+    ct, ft = render32(synth.perturb_scene(scene, cfg, 1))
+    g, gF = (c32 - ct).astype(np.float32), (f32 - ft).astype(np.float32)
+    ref, _ = _run(cfg, scene, cams, g, None, gF, precision="fp32")
+    got, _ = _run(cfg, scene, cams, g, None, gF, precision=precision)
+    errs = {k: rel_l2(got[k], ref[k]) for k, _ in GROUPS}
+    print(f"stress 960x540 {precision} vs FP32 gradient rel-L2:", errs)
+    for k, e in errs.items():
+        assert e < 2e-2, (k, errs)
+
+
 def _stress_small(seed=3):
     cfg = synth.CONFIGS["stress"].replace(width=64, height=48, K=8, n_views=1)
     scene = scaled_scene(cfg, seed, 2.0)
@@ -181,8 +233,8 @@ def test_stress_shape_gradients_fp32():
 
 @pytest.mark.parametrize("precision", ["bf16", "fp8"])
 def test_stress_shape_gradients_tensor_core_precisions(precision):
-    """BF16 / E4M3 forward on the tensor cores, then the wide FP32 backward recomputing with the
-    BF16 weights of the same blob: gradients within the BF16 bar of 2e-2 relative L2."""
+    """BF16 / E4M3 forward and the width-128 backward on the tensor cores (BF16 recompute,
+    dgrad and wgrad): gradients within the BF16 bar of 2e-2 relative L2."""
     cfg, scene, cams = _stress_small(4)
     g_rgb, g_F = _l2_grads(cfg, scene, cams)
     r = Renderer(cfg, precision=precision)
