@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
             vals[3] = a_k;
 #pragma unroll
             for (int f = 0; f < NF; ++f) vals[4 + f] = f < m.F ? wk * z[4 + f] : 0.f;
-            seg_scan<NZ>(vals, 4 + m.F, row, S, sScan + g * 4 * kMaxScanVals, bar_id);
+            seg_sum<NZ>(vals, 4 + m.F, row, S, sScan + g * 4 * kMaxScanVals, bar_id);  // interval totals
             if (valid && k == S - 1 && ok) {
               const int h = T[iv].h;
               w.hit_out[h] = make_float4(vals[0], vals[1], vals[2], vals[3]);

@@ -46,6 +46,25 @@ MLPS_DEV void seg_scan(float (&v)[NV], int nv, int row, int S, float* scratch, i
   named_bar_sync(bar_id, kEGThreads);
 }
 
+// Segmented sum of NV values over the 128 rows: the segment's last row gets its total. With S
+// dividing 32 a segment lives inside one warp and the sum is a butterfly over its lanes (every
+// row gets the total); otherwise it is the inclusive scan.
+template <int NV>
+MLPS_DEV void seg_sum(float (&v)[NV], int nv, int row, int S, float* scratch, int bar_id) {
+  if (S <= 32 && (32 % S) == 0) {
+    for (int o = 1; o < S; o <<= 1) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    }
+    (void)nv;
+    (void)row;
+    (void)scratch;
+    (void)bar_id;
+    return;
+  }
+  seg_scan<NV>(v, nv, row, S, scratch, bar_id);
+}
+
 MLPS_DEV float sigmoid_fast(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 MLPS_DEV float softplus_fast(float z) { return fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z))); }
 
