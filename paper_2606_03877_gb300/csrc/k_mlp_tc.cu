@@ -81,7 +81,7 @@ MLPS_HD TcSmem tc_smem(const TcPlan& P, int kNEG, bool e4m3, int ipc) {
 // power-of-two scale s_l per (primitive, layer), the weights are stored divided by a power of two
 // c_l chosen so that s_{l+1} = s_l c_l, and the bias is one more K step: a hidden layer's
 // accumulator is the next A operand before ReLU and conversion (k_pack_e4m3).
-template <int WIDTH, int XL, int DL, int NF, int kNEG, bool F8>
+template <int WIDTH, int XL, int DL, int NF, int kNEG, bool F8, int NL = 0>
 __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     k_mlp_fwd_tc(Work w, MlpArgs a, TcPlan P, const __grid_constant__ CUtensorMap tmap) {
   constexpr int kThreadsTC = kEGThreads * kNEG;
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   const int S = m.S;
-  const int nl = m.nl;
+  const int nl = NL > 0 ? NL : m.nl;  // (NL > 0: the layer count fixed at compile time)
   const int g = warp >> 2;               // epilogue group of this warp (< kNEG)
   const int q = warp & 3;                // TMEM lane quarter
   const int row = q * 32 + lane;         // sample row within the chunk
@@ -347,7 +347,8 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
         }
         const uint32_t trow = dacc + ((uint32_t)(q * 32) << 16);
         const uint32_t arow = aT + ((uint32_t)(q * 32) << 16);
-        for (int l = 0; l < nl; ++l) {
+#pragma unroll
+        for (int l = 0; l < (NL > 0 ? NL : nl); ++l) {
           // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
           const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_done(g), (ph_done >> g) & 1u, sAbort, kWaitNs));
           ph_done ^= 1u << g;
@@ -862,7 +863,8 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
             : tc::k_mlp_fwd_tc<W, XL, DL, 0, 6, F8>)
 #define MLPS_BY_GROUPS5(W, XL, DL) \
   (neg == 2 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 2, false> : neg == 3 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 3, false> \
-            : neg == 4 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 4, false> : tc::k_mlp_fwd_tc<W, XL, DL, 0, 5, false>)
+            : neg == 4 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 4, false> \
+            : a.m.nl == 4 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 5, false, 4> : tc::k_mlp_fwd_tc<W, XL, DL, 0, 5, false>)
   if (P.w8_bytes > 0) {  // E4M3
     if (a.m.width == 64) {
       if (!feat) kern = fast64 ? MLPS_BY_GROUPS(64, 6, 4, true) : MLPS_BY_GROUPS(64, -1, -1, true);
