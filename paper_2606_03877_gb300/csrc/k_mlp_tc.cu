@@ -860,7 +860,7 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
 #define MLPS_BY_GROUPS(W, XL, DL, F8) \
   (neg == 2 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 2, F8> : neg == 3 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 3, F8> \
             : neg == 4 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 4, F8> : neg == 5 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 5, F8> \
-            : tc::k_mlp_fwd_tc<W, XL, DL, 0, 6, F8>)
+            : a.m.nl == 4 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 6, F8, 4> : tc::k_mlp_fwd_tc<W, XL, DL, 0, 6, F8>)
 #define MLPS_BY_GROUPS5(W, XL, DL) \
   (neg == 2 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 2, false> : neg == 3 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 3, false> \
             : neg == 4 ? tc::k_mlp_fwd_tc<W, XL, DL, 0, 4, false> \
