@@ -200,7 +200,17 @@ mlps_status mlps_render_forward(const mlps_config* cfg, const mlps_scene* scene,
  * d_scales [K,3], d_quats [K,4]. The slot features' gradient reaches the embeddings, the
  * compositing weights (and through them the MLP) and the pose (through u).
  * The MLP is recomputed, not stored. Hit sets and orders are piecewise constant and are not
- * differentiated. */
+ * differentiated.
+ * Shapes the backward covers (others return MLPS_ERR_UNSUPPORTED before anything is enqueued;
+ * the forward covers every valid configuration):
+ *  - FP32: samples <= 64; hidden width 32 or 64 while both layouts of a primitive's weights fit
+ *    in shared memory (up to three 64-wide hidden layers) and its weight gradient fits 1024 tiles
+ *    of 4 x 4; hidden width 128 with input and output widths <= 64.
+ *  - BF16 / E4M3 (the backward recomputes in BF16): hidden width 32 or 64 with up to six hidden
+ *    layers, at most 12 feature outputs and the midpoint encodings (xyz_freqs 0 or 6), or the
+ *    paper's contact-point model; hidden width 128 with up to four hidden layers on the tensor
+ *    cores (xyz_freqs 6, dir_freqs 4, at most 16 feature outputs), other width-128 networks with
+ *    samples <= 64 in an FP32-FMA kernel reading the BF16 weights. */
 mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene,
                                  const mlps_camera* cams, int32_t n_views, const float* d_rgb,
                                  const float* d_trans, const float* d_feat, const void* saved,

@@ -807,7 +807,7 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
 // their accumulators in TMEM, else 2; 0 when not even 2 fit.
 static int bwd_groups(const Model& m, const TcPlan& P) {
   const int ipc = m.S <= 128 ? 128 / m.S : 1;
-  for (int ng = 3; ng >= 2; --ng) {
+  for (int ng = 3; ng >= 1; --ng) {  // one group: the deep networks (5 or 6 hidden layers)
     if ((int)tc::kGColsB * ng + tc::dw_cols(m.nl) > (int)tc::kTmemColsB) continue;  // TMEM: groups + weight gradients
     if (tc::bwd_layout(P, m.F, ipc, ng).total + 1024 <= 227 * 1024) return ng;
   }
@@ -872,7 +872,8 @@ cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
   // the contact-point model runs two groups: its chunks hold 128 interval records each
   if (a.m.contact && ng != 2) return cudaErrorNotSupported;
   decltype(&tc::k_mlp_bwd_tc<0, 6, 4, 3>) kern =
-      a.m.contact ? tc::k_mlp_bwd_tc<0, 6, 6, 2, true> : (ng == 3 ? MLPS_BWD_KERN(3) : MLPS_BWD_KERN(2));
+      a.m.contact ? tc::k_mlp_bwd_tc<0, 6, 6, 2, true>
+                  : (ng == 3 ? MLPS_BWD_KERN(3) : ng == 2 ? MLPS_BWD_KERN(2) : MLPS_BWD_KERN(1));
 #undef MLPS_BWD_KERN
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -503,6 +503,7 @@ mlps_status forward_impl(const mlps_config* cfg, const mlps_scene* scene, const 
   {
     StageTimer tm(ST_SETUP, st);
     cudaMemsetAsync(w.saved_hdr, 0, 256, st);
+    cudaMemsetAsync(w.scr_hdr, 0, 256, st);  // both regions' status words start clear
     cudaMemsetAsync(w.prim_count, 0, sizeof(int) * ((size_t)K + 1), st);
     if (dev)
       launch_views_from_items(w, dev->items, dev->caps.max_width, dev->caps.max_height,
