@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define MLPS_ABI_VERSION 6
+#define MLPS_ABI_VERSION 7
 #define MLPS_MAX_VIEWS 64
 
 typedef int32_t mlps_status;
@@ -118,7 +118,14 @@ typedef struct {
                                    screen tile (the approximate order of Sec. 3.3 and App. A.4),
                                    ties by primitive index. Hit intervals, samples and MLP inputs
                                    stay per ray. */
-  int32_t reserved[1];          /* must be zero */
+  int32_t early_stop_wave;      /* 0: the MLP forward evaluates every hit interval, and early
+                                   termination (t_eps) only stops the composite. k > 0 (at most
+                                   max_hits_per_ray): it runs in two depth waves, first the
+                                   first k hits of every ray, then the later hits of the rays
+                                   whose composite has not stopped within their first k, so
+                                   that the intervals behind a ray's termination point are not
+                                   evaluated (App. B.2). The outputs are the same as with 0.
+                                   Not with feature slots (MLPS_ERR_UNSUPPORTED). */
 } mlps_config;
 
 typedef struct {
@@ -365,6 +372,12 @@ mlps_status mlps_render_batch_backward_dev(const mlps_config* cfg, const mlps_sc
  * rays with zero dL/dC, have none). Synchronises `stream`. */
 mlps_status mlps_backward_chunk_counts(const void* saved, const void* scratch, int64_t* chunks,
                                        int64_t* live, void* stream);
+
+/* Inspection of the last forward pass with depth waves (early_stop_wave > 0): *intervals = its
+ * hit intervals, *evaluated = those the MLP evaluated over both waves (0 without waves, where
+ * every interval is evaluated). Synchronises `stream`. */
+mlps_status mlps_forward_wave_counts(const void* saved, const void* scratch, int64_t* intervals,
+                                     int64_t* evaluated, void* stream);
 
 /* Synchronise `stream`, return the device status word of a `saved` or `scratch` region
  * written by the calls above (MLPS_OK if none), and clear it. */

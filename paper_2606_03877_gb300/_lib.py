@@ -40,7 +40,7 @@ class MlpsConfig(ctypes.Structure):
                 ("hit_capacity_per_ray", ctypes.c_float), ("t_eps", ctypes.c_float),
                 ("tile", ctypes.c_int32), ("mlp_groups", ctypes.c_int32),
                 ("contact", ctypes.c_int32), ("slot_dim", ctypes.c_int32),
-                ("tile_sort", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("tile_sort", ctypes.c_int32), ("early_stop_wave", ctypes.c_int32)]
 
 
 class MlpsCamera(ctypes.Structure):
@@ -136,6 +136,7 @@ _SIGS = [
     ("mlps_read_status", ctypes.c_int32, [_vp, _vp]),
     ("mlps_saved_hit_count", ctypes.c_int32, [_vp, _P(ctypes.c_int64), _vp]),
     ("mlps_backward_chunk_counts", ctypes.c_int32, [_vp, _vp, _P(ctypes.c_int64), _P(ctypes.c_int64), _vp]),
+    ("mlps_forward_wave_counts", ctypes.c_int32, [_vp, _vp, _P(ctypes.c_int64), _P(ctypes.c_int64), _vp]),
     ("mlps_export_hits", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsCamera), ctypes.c_int32, _vp,
                                           ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mlps_export_tiles", ctypes.c_int32, [_P(MlpsConfig), ctypes.c_int32, _P(MlpsCamera),
@@ -193,6 +194,15 @@ def mlps_backward_chunk_counts(saved, scratch, stream: int = 0):
     a = ctypes.c_int64()
     b = ctypes.c_int64()
     _check("mlps_backward_chunk_counts", load().mlps_backward_chunk_counts(
+        _ptr(saved), _ptr(scratch), ctypes.byref(a), ctypes.byref(b), stream or None))
+    return int(a.value), int(b.value)
+
+
+def mlps_forward_wave_counts(saved, scratch, stream: int = 0):
+    """(hit intervals of the last forward pass, intervals its depth waves evaluated)."""
+    a = ctypes.c_int64()
+    b = ctypes.c_int64()
+    _check("mlps_forward_wave_counts", load().mlps_forward_wave_counts(
         _ptr(saved), _ptr(scratch), ctypes.byref(a), ctypes.byref(b), stream or None))
     return int(a.value), int(b.value)
 

@@ -169,15 +169,26 @@ MLPS_DEV bool interval_live(const Work& w, int j, int F) {
 
 MLPS_DEV int n_intervals(const Work& w) { return min(w.saved_hdr[1], w.hit_cap); }
 
+// Whether list `mode` takes the interval at primitive-major position j: 0 = a nonzero gradient
+// (the backward's list); 1 = among its ray's first k1 hits (the first depth wave); 2 = later
+// than its ray's first k1 hits, on a ray still open after the first wave (the second wave).
+MLPS_DEV bool list_takes(const Work& w, int j, int F, int mode, int k1) {
+  if (mode == 0) return interval_live(w, j, F);
+  const int h = w.prim_list[j];
+  const int r = w.hit_ray[h];
+  const int rank = h - w.ray_start[r];
+  return mode == 1 ? rank < k1 : (rank >= k1 && w.ray_alive[r] != 0);
+}
+
 constexpr int kLivePer = 4;  // intervals per thread (consecutive)
 
 // Live flags of this thread's intervals as bits, and their count.
-MLPS_DEV int live_bits(const Work& w, int j0, int F) {
+MLPS_DEV int live_bits(const Work& w, int j0, int F, int mode, int k1) {
   const int n = n_intervals(w);
   int bits = 0;
 #pragma unroll
   for (int e = 0; e < kLivePer; ++e)
-    if (j0 + e < n && interval_live(w, j0 + e, F)) bits |= 1 << e;
+    if (j0 + e < n && list_takes(w, j0 + e, F, mode, k1)) bits |= 1 << e;
   return bits;
 }
 
@@ -204,12 +215,12 @@ MLPS_DEV int block_excl_scan(int v, int* swarp) {
   return swarp[warp] + x - v;
 }
 
-__global__ void __launch_bounds__(kLiveBlock) k_live_count(Work w, int F) {
+__global__ void __launch_bounds__(kLiveBlock) k_live_count(Work w, int F, int mode, int k1) {
   __shared__ int scount;
   const int j0 = (blockIdx.x * kLiveBlock + threadIdx.x) * kLivePer;
   if (threadIdx.x == 0) scount = 0;
   __syncthreads();
-  int c = __popc(live_bits(w, j0, F));
+  int c = __popc(live_bits(w, j0, F, mode, k1));
   for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(&scount, c);
   __syncthreads();
@@ -251,10 +262,10 @@ __global__ void __launch_bounds__(1024) k_live_scan(Work w, int nb) {
   if (threadIdx.x == 0) w.scr_hdr[2] = carry;
 }
 
-__global__ void __launch_bounds__(kLiveBlock) k_live_write(Work w, int F) {
+__global__ void __launch_bounds__(kLiveBlock) k_live_write(Work w, int F, int mode, int k1) {
   __shared__ int swarp[32];
   const int j0 = (blockIdx.x * kLiveBlock + threadIdx.x) * kLivePer;
-  const int bits = live_bits(w, j0, F);
+  const int bits = live_bits(w, j0, F, mode, k1);
   int pos = w.live_bcount[blockIdx.x] + block_excl_scan(__popc(bits), swarp);
 #pragma unroll
   for (int e = 0; e < kLivePer; ++e)
@@ -273,8 +284,9 @@ MLPS_DEV int live_lower_bound(const int* a, int n, int x) {
 }
 
 // Per primitive: its range of live intervals and (scan over the primitives, one block) its first
-// chunk; the chunk total goes to scratch header word 1.
-__global__ void __launch_bounds__(1024) k_live_prims(Work w) {
+// chunk; the chunk total goes to scratch header word 1. With `count`, the list's intervals are
+// added to scratch header word 3 (the forward's evaluated intervals).
+__global__ void __launch_bounds__(1024) k_live_prims(Work w, int count) {
   __shared__ int swarp[32];
   __shared__ int carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -318,15 +330,34 @@ __global__ void __launch_bounds__(1024) k_live_prims(Work w) {
     w.live_chunk_start[w.K] = carry;
     w.live_prim_start[w.K] = n_live;
     w.scr_hdr[1] = carry;
+    if (count) w.scr_hdr[3] += n_live;
   }
 }
 
-void launch_live_lists(const Work& w, int F, cudaStream_t st) {
+// After the first depth wave: a ray stays open when it has hits past its first k1 and the
+// composite would not have stopped within them. The optical depth is summed in the composite's
+// own order with its own operations, and it only grows along the ray, so "T < t_eps after the
+// first k1 intervals" holds exactly when the composite stops at or before interval k1.
+__global__ void k_wave_alive(Work w, int k1) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= w.n_rays || r >= live_rays(w)) return;
+  const int n = w.ray_count[r], s = w.ray_start[r];
+  float A = 0.f;
+  for (int j = 0; j < n && j < k1; ++j) A += w.hit_out[s + j].w;
+  w.ray_alive[r] = (n > k1 && !(expf(-A) < w.t_eps)) ? 1 : 0;
+}
+
+void launch_live_lists(const Work& w, int F, int mode, int k1, cudaStream_t st) {
   const int nb = (w.hit_cap + kLiveBlock * kLivePer - 1) / (kLiveBlock * kLivePer);
-  k_live_count<<<nb, kLiveBlock, 0, st>>>(w, F);
+  k_live_count<<<nb, kLiveBlock, 0, st>>>(w, F, mode, k1);
   k_live_scan<<<1, 1024, 0, st>>>(w, nb);
-  k_live_write<<<nb, kLiveBlock, 0, st>>>(w, F);
-  k_live_prims<<<1, 1024, 0, st>>>(w);
+  k_live_write<<<nb, kLiveBlock, 0, st>>>(w, F, mode, k1);
+  k_live_prims<<<1, 1024, 0, st>>>(w, mode != 0);
+}
+
+void launch_wave_alive(const Work& w, int k1, cudaStream_t st) {
+  if (w.n_rays == 0) return;
+  k_wave_alive<<<(w.n_rays + 255) / 256, 256, 0, st>>>(w, k1);
 }
 
 void launch_pose_bwd(const Work& w, float* d_centers, float* d_scales, float* d_quats,

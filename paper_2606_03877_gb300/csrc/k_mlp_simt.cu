@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fwd_simt(Work w, MlpArgs a)
   float* sB = sA + kRows * L.maxdim;
   IntervalInfo* sI = reinterpret_cast<IntervalInfo*>(sB + kRows * L.maxdim);
 
-  const int total = w.saved_hdr[2];
+  const int total = walk_chunk_count(w);  // (a depth wave's lists, or every chunk)
+  const int* const bmap = walk_map(w);    // list position -> primitive-major position
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   if (cb >= ce) return;
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_fwd_simt(Work w, MlpArgs a)
       loaded = prim;
     }
     if (threadIdx.x < nint)
-      load_interval(w, m, w.prim_start[prim] + first + threadIdx.x, sI[threadIdx.x]);
+      load_interval(w, m, walk_slot(bmap, w.prim_start[prim] + first + threadIdx.x), sI[threadIdx.x]);
     __syncthreads();
     if (threadIdx.x < kRows) {
       const int row = threadIdx.x, i = row / S, k = row - i * S;

@@ -498,8 +498,8 @@ __global__ void __launch_bounds__(kThreads, MT <= 2 ? 2 : 1) k_mlp_bwd_simt(Work
   IntervalInfo* sI = reinterpret_cast<IntervalInfo*>(sGrad + ipcb);
   float* sGF = reinterpret_cast<float*>(sI + ipcb);
 
-  const int total = bwd_chunk_count(w);
-  const int* const bmap = bwd_map(w);  // list position -> forward position
+  const int total = walk_chunk_count(w);
+  const int* const bmap = walk_map(w);  // list position -> forward position
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   if (cb >= ce) return;
@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(kThreads, MT <= 2 ? 2 : 1) k_mlp_bwd_simt(Work
       const int nint = min(ipcb, nint_c - i0);
       __syncthreads();
       if (threadIdx.x < nint) {
-        const int slot = bwd_slot(bmap, w.prim_start[prim] + first + i0 + threadIdx.x);
+        const int slot = walk_slot(bmap, w.prim_start[prim] + first + i0 + threadIdx.x);
         load_interval(w, m, slot, sI[threadIdx.x]);
         sGrad[threadIdx.x] = w.hit_grad[slot];
         for (int f = 0; f < F; ++f) sGF[threadIdx.x * F + f] = w.hit_gfeat[(size_t)slot * F + f];
@@ -909,8 +909,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
   float* sGF = reinterpret_cast<float*>(sI + ipcb);
   auto act = [&](int l) { return sAct + (size_t)(l - 1) * m.width * kRS; };
 
-  const int total = bwd_chunk_count(w);
-  const int* const bmap = bwd_map(w);  // list position -> forward position
+  const int total = walk_chunk_count(w);
+  const int* const bmap = walk_map(w);  // list position -> forward position
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   if (cb >= ce) return;
@@ -1040,7 +1040,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt_wide(Work w, MlpAr
       const int rows = round4(nint * S);  // rows past nint * S carry zero dL/dZ
       __syncthreads();
       if (threadIdx.x < nint) {
-        const int slot = bwd_slot(bmap, w.prim_start[prim] + first + i0 + threadIdx.x);
+        const int slot = walk_slot(bmap, w.prim_start[prim] + first + i0 + threadIdx.x);
         load_interval(w, m, slot, sI[threadIdx.x]);
         sGrad[threadIdx.x] = w.hit_grad[slot];
         for (int f = 0; f < F; ++f) sGF[threadIdx.x * F + f] = w.hit_gfeat[(size_t)slot * F + f];

@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
     tc_fence_after();
   }
 
-  const int total = w.saved_hdr[2];
+  const int total = walk_chunk_count(w);  // (a depth wave's lists, or every chunk)
+  const int* const bmap = walk_map(w);    // list position -> primitive-major position
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   const int S = m.S;
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(kEGThreads * kNEG, 1)
   auto prefetch = [&](const ChunkStep<kNEG>& st, int c) {
     const int f = (c - w.chunk_start[st.prim]) * w.ipc;
     if (row < min(w.ipc, w.prim_count[st.prim] - f))
-      rec_copy_async(w, w.prim_start[st.prim] + f + row,
+      rec_copy_async(w, walk_slot(bmap, w.prim_start[st.prim] + f + row),
                      itab_s + (uint32_t)((pb * w.ipc + row) * sizeof(IntervalRec)), 0u);
   };
   ChunkStep<kNEG> cur = chunk_step<kNEG>(w, cb, ce, prim);

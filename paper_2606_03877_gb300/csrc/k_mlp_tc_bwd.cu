@@ -240,8 +240,8 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
   const uint32_t tmem = *sTmem;
   const uint32_t tm_dw = tmem + kGColsB * kNG;  // weight-gradient accumulators: 64 columns per layer
 
-  const int total = bwd_chunk_count(w);
-  const int* const bmap = bwd_map(w);  // list position -> forward position
+  const int total = walk_chunk_count(w);
+  const int* const bmap = walk_map(w);  // list position -> forward position
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   // phase parities of bar_w and of this group's bar_done (forward layers and dgrad) and bar_wg
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
   auto prefetch = [&](const ChunkStep<kNG>& st, int c) {
     const int f = (c - w.chunk_start[st.prim]) * w.ipc;
     if (row < min(w.ipc, w.prim_count[st.prim] - f))
-      rec_prefetch(w, bwd_slot(bmap, w.prim_start[st.prim] + f + row), true, pre);
+      rec_prefetch(w, walk_slot(bmap, w.prim_start[st.prim] + f + row), true, pre);
   };
 
   ChunkStep<kNG> cur = chunk_step<kNG>(w, cb, ce, prim);
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
     if (row < nint) {
       rec_store(pre, T, row);  // prefetched during the previous step
       GI[row] = pre.g;
-      const size_t slot = bwd_slot(bmap, w.prim_start[prim] + first + row);
+      const size_t slot = walk_slot(bmap, w.prim_start[prim] + first + row);
       for (int f = 0; f < F; ++f) GF[row * F + f] = w.hit_gfeat[slot * F + f];
     }
     named_bar_sync(gbar, kGThreads);

@@ -213,8 +213,8 @@ __global__ void __launch_bounds__(kWThreads, 1)
   const uint32_t hc = 64u * (uint32_t)half;  // first FP32 column of this thread's half
   const uint32_t hp = 32u * (uint32_t)half;  // first BF16-pair column of this thread's half
 
-  const int total = bwd_chunk_count(w);
-  const int* const bmap = bwd_map(w);  // list position -> forward position
+  const int total = walk_chunk_count(w);
+  const int* const bmap = walk_map(w);  // list position -> forward position
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   float* dwb = w.dwb + (size_t)blockIdx.x * m.P;  // this block's dW copy: per layer [in][out]
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
     const int nint = min(w.ipc, w.prim_count[prim] - first);
     __syncthreads();  // the previous chunk is done with the tables
     for (int i = threadIdx.x; i < nint; i += kWThreads) {
-      const size_t slot = bwd_slot(bmap, w.prim_start[prim] + first + i);
+      const size_t slot = walk_slot(bmap, w.prim_start[prim] + first + i);
       T[i] = w.rec[slot];
       GI[i] = w.hit_grad[slot];
       for (int f = 0; f < F; ++f) GF[i * F + f] = w.hit_gfeat[slot * F + f];

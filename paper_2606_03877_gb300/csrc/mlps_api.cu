@@ -96,8 +96,8 @@ mlps_status check_cfg(const mlps_config* c) {
   if (!finite_f(c->hit_capacity_per_ray) || !(c->hit_capacity_per_ray > 0.f))
     return MLPS_ERR_INVALID_ARGUMENT;
   if (!finite_f(c->t_eps) || c->t_eps < 0.f || c->t_eps >= 1.f) return MLPS_ERR_INVALID_ARGUMENT;
-  for (int i = 0; i < 1; ++i)
-    if (c->reserved[i] != 0) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->early_stop_wave < 0 || c->early_stop_wave > c->max_hits_per_ray) return MLPS_ERR_INVALID_ARGUMENT;
+  if (c->early_stop_wave > 0 && c->slot_dim > 0) return MLPS_ERR_UNSUPPORTED;
   if (c->tile_sort != 0 && c->tile_sort != 1) return MLPS_ERR_INVALID_ARGUMENT;
   if (c->contact != 0 && (c->contact != 1 || c->samples != 1)) return MLPS_ERR_INVALID_ARGUMENT;
   if (c->slot_dim < 0 || c->slot_dim > kMaxSlotDim) return MLPS_ERR_INVALID_ARGUMENT;
@@ -214,7 +214,7 @@ struct Layout {
       saved_total;
   // scratch
   size_t prim_cursor, tile_count, tile_list, hit_grad, hit_gfeat, dgeo, slot_ga, slot_gu, dwb, live_slot,
-      live_bcount, live_prim_count, live_prim_start, live_chunk_start, scratch_total;
+      live_bcount, live_prim_count, live_prim_start, live_chunk_start, ray_alive, scratch_total;
   long long hit_cap;
   long long n_rays, n_pairs, n_tiles_all, n_cand;
   int max_view_tiles;
@@ -287,6 +287,7 @@ bool make_layout(const mlps_config* c, int K, const ViewSpec* vs, int V, Layout*
   L->live_prim_count = t.take<int>((size_t)K + 1);
   L->live_prim_start = t.take<int>((size_t)K + 1);
   L->live_chunk_start = t.take<int>((size_t)K + 1);
+  L->ray_alive = t.take<unsigned char>(c->early_stop_wave > 0 ? nr + 1 : 1);
   L->scratch_total = t.off;
   return true;
 }
@@ -334,6 +335,7 @@ Work make_work(const mlps_config* c, const Layout& L, int K, int V, void* saved,
     w.live_prim_count = reinterpret_cast<int*>(sc + L.live_prim_count);
     w.live_prim_start = reinterpret_cast<int*>(sc + L.live_prim_start);
     w.live_chunk_start = reinterpret_cast<int*>(sc + L.live_chunk_start);
+    w.ray_alive = reinterpret_cast<unsigned char*>(sc + L.ray_alive);
     // w.bslot stays null: only the MLP backward's copy of the Work points at the live lists
   }
   w.K = K;
@@ -532,18 +534,42 @@ mlps_status forward_impl(const mlps_config* cfg, const mlps_scene* scene, const 
   }
   if (K > 0) {
     StageTimer tm(ST_MLP_FWD, st);
-    cudaError_t e;
-    if (cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3) {
-      TcPlan P;
+    TcPlan P;
+    const bool tc = cfg->precision == MLPS_BF16 || cfg->precision == MLPS_FP8_E4M3;
+    if (tc) {
       long long stride;
       tc_plan(a.m, &P, &stride, cfg->precision == MLPS_FP8_E4M3);
-      e = launch_mlp_fwd_tc(w, a, P, n_sm, st);
-    } else {
-      e = launch_mlp_fwd_simt(w, a, n_sm, st);
     }
-    if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
-    if (e != cudaSuccess) return MLPS_ERR_CUDA;
-    count_launch(1);
+    auto mlp = [&](const Work& wk) -> mlps_status {
+      const cudaError_t e = tc ? launch_mlp_fwd_tc(wk, a, P, n_sm, st) : launch_mlp_fwd_simt(wk, a, n_sm, st);
+      if (e == cudaErrorNotSupported) return MLPS_ERR_UNSUPPORTED;
+      if (e != cudaSuccess) return MLPS_ERR_CUDA;
+      count_launch(1);
+      return MLPS_OK;
+    };
+    const int k1 = cfg->early_stop_wave;
+    if (k1 == 0) {
+      const mlps_status ms = mlp(w);
+      if (ms != MLPS_OK) return ms;
+    } else {
+      // depth waves (App. B.2): each ray's first k1 hits; then the later hits of the rays whose
+      // composite does not stop within them. The intervals behind a termination point are not
+      // evaluated; the composite below never reaches them.
+      Work wv = w;
+      wv.prim_count = w.live_prim_count;
+      wv.prim_start = w.live_prim_start;
+      wv.chunk_start = w.live_chunk_start;
+      wv.bslot = w.live_slot;
+      launch_live_lists(w, 0, 1, k1, st);
+      count_launch(4);
+      mlps_status ms = mlp(wv);
+      if (ms != MLPS_OK) return ms;
+      launch_wave_alive(w, k1, st);
+      launch_live_lists(w, 0, 2, k1, st);
+      count_launch(w.n_rays > 0 ? 5 : 4);
+      ms = mlp(wv);
+      if (ms != MLPS_OK) return ms;
+    }
   }
   {
     StageTimer tm(ST_COMP_FWD, st);
@@ -633,7 +659,7 @@ mlps_status backward_impl(const mlps_config* cfg, const mlps_scene* scene, const
   Work wb = w;
   if (K > 0) {
     StageTimer tm(ST_COMP_BWD, st);
-    launch_live_lists(w, cfg->feat_dim, st);
+    launch_live_lists(w, cfg->feat_dim, 0, 0, st);
     count_launch(4);
     wb.prim_count = w.live_prim_count;
     wb.prim_start = w.live_prim_start;
@@ -915,6 +941,20 @@ mlps_status mlps_backward_chunk_counts(const void* saved, const void* scratch, i
   if (cudaStreamSynchronize(st) != cudaSuccess) return MLPS_ERR_CUDA;
   *chunks = h[2];
   *live = t[1];
+  return MLPS_OK;
+}
+
+mlps_status mlps_forward_wave_counts(const void* saved, const void* scratch, int64_t* intervals,
+                                     int64_t* evaluated, void* stream) {
+  if (!saved || !scratch || !intervals || !evaluated) return MLPS_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h[2] = {0, 0}, t[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(h, saved, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(t, scratch, sizeof(t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MLPS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MLPS_ERR_CUDA;
+  *intervals = h[1];
+  *evaluated = t[3];
   return MLPS_OK;
 }
 

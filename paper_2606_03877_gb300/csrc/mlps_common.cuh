@@ -265,16 +265,18 @@ struct Work {
   float* slot_ga;        // [cap] feature slots: dL/da_j of each interval (hit order)
   float4* slot_gu;       // [cap] feature slots: (dL/du, compositing weight w_j) (hit order)
   float* dwb;            // [n_sm, P] width-128 backward: per-block weight-gradient copies
-  // The MLP backward's own interval lists: the intervals with a nonzero gradient only (see
-  // launch_live_lists). The backward kernels get a Work whose prim_count / prim_start /
-  // chunk_start are these lists' and whose bslot maps a list position to the interval's position
-  // in the forward's primitive-major order (null: the forward's lists, identity).
+  // Interval lists that select some intervals of the primitive-major order (launch_live_lists):
+  // the backward's (the intervals with a nonzero gradient) and, with depth waves, the forward's
+  // (a wave's intervals). An MLP kernel walking such lists gets a Work whose prim_count /
+  // prim_start / chunk_start are the lists' and whose bslot maps a list position to the
+  // interval's position in the primitive-major order (null: every interval, identity).
   const int* bslot;      // [hit_cap]
   int* live_slot;        // [hit_cap] storage of bslot
   int* live_bcount;      // [hit_cap / kLiveBlock + 2] per-block live counts, then their offsets
   int* live_prim_count;  // [K + 1]
   int* live_prim_start;  // [K + 1]
   int* live_chunk_start; // [K + 1]
+  unsigned char* ray_alive;  // [n_rays] depth waves: the ray is still open after the first wave
   // sizes
   int K, V;
   int H, W, ntx, nty, n_tiles;  // view 0's sizes (the single-scene inspection calls use them)
@@ -291,14 +293,14 @@ struct Work {
   float t_eps;
 };
 
-// Chunks the MLP backward walks (its own lists: count in scratch header word 1).
-MLPS_DEV int bwd_chunk_count(const Work& w) { return w.bslot ? w.scr_hdr[1] : w.saved_hdr[2]; }
+// Chunks an MLP kernel walks (interval lists: count in scratch header word 1).
+MLPS_DEV int walk_chunk_count(const Work& w) { return w.bslot ? w.scr_hdr[1] : w.saved_hdr[2]; }
 // The map from list positions to forward positions, or null when it is the identity (no lists,
 // or every interval is live: the lists are then the forward's).
-MLPS_DEV const int* bwd_map(const Work& w) {
+MLPS_DEV const int* walk_map(const Work& w) {
   return (w.bslot && w.scr_hdr[2] != min(w.saved_hdr[1], w.hit_cap)) ? w.bslot : nullptr;
 }
-MLPS_DEV int bwd_slot(const int* map, int j) { return map ? map[j] : j; }
+MLPS_DEV int walk_slot(const int* map, int j) { return map ? map[j] : j; }
 
 // Rays of all views together (views are stored in ray order). With a device-resident item
 // table the ray arrays are sized for the caps and the live total can be smaller.

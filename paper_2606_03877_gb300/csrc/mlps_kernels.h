@@ -157,10 +157,15 @@ cudaError_t launch_mlp_bwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
 // F MLP feature channels in rows of FT floats (FT = F + slot channels)
 void launch_composite_fwd(const Work& w, int F, int FT, float* rgb, float* trans, float* feat,
                           cudaStream_t st);
-// The MLP backward's interval lists (the intervals with a nonzero gradient, in the forward's
-// primitive-major order) into w.live_*; chunk total in scratch header word 1, interval total in
-// word 2 (4 launches).
-void launch_live_lists(const Work& w, int F, cudaStream_t st);
+// Interval lists (a selection of the primitive-major order, kept in that order) into w.live_*;
+// chunk total in scratch header word 1, interval total in word 2 (4 launches). mode 0: the
+// intervals with a nonzero gradient (the backward); 1: each ray's first k1 hits; 2: the later
+// hits of the rays w.ray_alive marks (the forward's depth waves, whose intervals are also added
+// up in word 3).
+void launch_live_lists(const Work& w, int F, int mode, int k1, cudaStream_t st);
+// After the first depth wave: w.ray_alive[r] = ray r has hits past its first k1 and its
+// composite does not stop within them.
+void launch_wave_alive(const Work& w, int k1, cudaStream_t st);
 void launch_composite_bwd(const Work& w, int F, int FT, const float* d_rgb, const float* d_trans,
                           const float* d_feat, const float* slot_ga, cudaStream_t st);
 void launch_pose_bwd(const Work& w, float* d_centers, float* d_scales, float* d_quats,

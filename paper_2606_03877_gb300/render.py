@@ -14,7 +14,8 @@ from . import _lib
 
 
 def make_config(shape, precision: str = "fp32", t_eps: float = 1e-6, max_hits: int = 64,
-                hit_capacity: float = 8.0, tile: int = 16, mlp_groups: int = 0) -> _lib.MlpsConfig:
+                hit_capacity: float = 8.0, tile: int = 16, mlp_groups: int = 0,
+                early_stop_wave: int = 0) -> _lib.MlpsConfig:
     """mlps_config from any object with xyz_freqs, dir_freqs, hidden_width, hidden_layers,
     feat_dim, samples and optionally contact and slot_dim (e.g. :class:`synth.SceneConfig`)."""
     cfg = _lib.mlps_config_default(int(shape.xyz_freqs), int(shape.dir_freqs), int(shape.hidden_width),
@@ -26,6 +27,7 @@ def make_config(shape, precision: str = "fp32", t_eps: float = 1e-6, max_hits: i
     cfg.hit_capacity_per_ray = float(hit_capacity)
     cfg.tile = int(tile)
     cfg.mlp_groups = int(mlp_groups)
+    cfg.early_stop_wave = int(early_stop_wave)
     cfg.contact = int(getattr(shape, "contact", 0))
     cfg.slot_dim = int(getattr(shape, "slot_dim", 0))
     T = int(getattr(shape, "tile_sort", 0))  # tile-centre order of T x T tiles (T = 8 or 16)
@@ -121,6 +123,10 @@ class Renderer:
 
     def hit_count(self) -> int:
         return _lib.mlps_saved_hit_count(self.saved, _stream())
+
+    def wave_counts(self):
+        """(hit intervals of the last forward pass, intervals its depth waves evaluated)."""
+        return _lib.mlps_forward_wave_counts(self.saved, self.scratch, _stream())
 
     def chunk_counts(self):
         """(MLP chunks of the last forward pass, chunks its last backward pass walked)."""

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert _lib.mlps_abi_version() == 6
+    assert _lib.mlps_abi_version() == 7
     for s in range(8):
         assert _lib.mlps_status_string(s)
     assert _lib.mlps_status_string(4) == "hit capacity overflow"
@@ -65,9 +65,14 @@ def test_config_validation(lib):
     cfg = make_config(base)
     cfg.hidden_width = 48
     assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_UNSUPPORTED
-    cfg = make_config(base)
-    cfg.reserved[0] = 1
-    assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_INVALID_ARGUMENT
+    for wave in (-1, 65):
+        cfg = make_config(base)
+        cfg.early_stop_wave = wave
+        assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_INVALID_ARGUMENT
+    cfg = make_config(base, early_stop_wave=4)
+    assert _lib.mlps_check_config(cfg) == _lib.MLPS_OK
+    cfg.slot_dim = 8
+    assert _lib.mlps_check_config(cfg) == _lib.MLPS_ERR_UNSUPPORTED
 
 
 def test_camera_validation(lib):
