@@ -63,6 +63,10 @@ def _args():
                     help="time the other precisions and passes too (the default for the prec workload)")
     ap.add_argument("--no-compare", action="store_true",
                     help="time only the selected precision and pass")
+    ap.add_argument("--early-stop-wave", type=int, default=0,
+                    help="k > 0: the MLP forward in two depth waves (each ray's first k hits first)")
+    ap.add_argument("--sigma-shift", type=float, default=0.0,
+                    help="added to every primitive's density pre-activation (an opaque scene variant)")
     ap.add_argument("--hit-check-rays", type=int, default=4000,
                     help="rays sampled for the hit-list check against the oracle (0: none)")
     return ap.parse_args()
@@ -238,6 +242,17 @@ def feat_grad_device(wl, dev):
     return table[idx].reshape(wl.n_views, wl.height, wl.width, FT)
 
 
+def opaque_variant(scene, wl, shift: float):
+    """The scene with `shift` added to every primitive's density pre-activation (the bias of the
+    sigma output): shift ~ 60 makes a ray's transmittance fall below 1e-6 inside its first
+    interval, the case early termination is for."""
+    if not shift:
+        return scene
+    w = scene["weights"].copy()
+    w[:, wl.n_params - wl.output_dim + 3] += shift
+    return dict(scene, weights=w)
+
+
 def hit_capacity(a, wl) -> float:
     """Hit records reserved per ray: the 1024-primitive stress scene averages about eight
     hits per ray at 1080p and more at low resolution, so it gets sixteen."""
@@ -261,7 +276,7 @@ def run_ours(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = _workload(a)
-    scene = synth.make_scene(wl, 0)
+    scene = opaque_variant(synth.make_scene(wl, 0), wl, a.sigma_shift)
     cams = synth.make_cameras(wl, first_view_seed=rank_view_seed(rank, wl.n_views))
     d = {k: torch.from_numpy(v).to(dev) for k, v in scene.items()}
     g_rgb = torch.from_numpy(synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100 + rank,
@@ -274,6 +289,7 @@ def run_ours(a):
     def make(precision):
         kw = {"mlp_groups": a.mlp_groups} if a.mlp_groups and precision != "fp32" else {}
         kw["hit_capacity"] = hit_capacity(a, wl)
+        kw["early_stop_wave"] = a.early_stop_wave
         r = Renderer(wl, precision=precision, device=str(dev), **kw)
         return r
 
@@ -364,6 +380,12 @@ def run_ours(a):
 
     total_ms, ms, launches, prof, clocks = timed(r, do_bwd, a.steps, a.warmup, sample_clocks=True, profile=True)
     n_hits = r.hit_count()
+
+    def wave_evaluated(rr):
+        # the intervals the forward's depth waves evaluated (one more forward after the timed
+        # steps: a backward pass clears the count)
+        rr.forward(d["centers"], d["scales"], d["quats"], rr.pack(d["weights"]), cams)
+        return rr.wave_counts()[1]
     value = job_rays_per_s(n_rays, ws, a.steps, total_ms)
 
     results = {f"{precision}_{'fwd_bwd' if do_bwd else 'fwd'}":
@@ -452,9 +474,12 @@ def run_ours(a):
                                f"{'contact-point input, ' if wl.contact else ''}"
                                f"{f'4 x {wl.slot_dim} feature slots, ' if wl.slot_dim else ''}"
                                f"{f'tile-centre order ({wl.tile_sort}x{wl.tile_sort} tiles), ' if wl.tile_sort else ''}"
+                               f"{f'density pre-activations +{a.sigma_shift:g} (opaque variant), ' if a.sigma_shift else ''}"
+                               f"{f'MLP forward in depth waves (first {a.early_stop_wave} hits per ray), ' if a.early_stop_wave else ''}"
                                f"{wl.n_views} views/rank",
                    "pass": "fwd+bwd" if do_bwd else "fwd", "precision": precision,
                    "rays_per_step": n_rays * ws, "hits_per_step": n_hits,
+                   **({"intervals_evaluated_per_step": wave_evaluated(r)} if a.early_stop_wave else {}),
                    "l2": "flushed between timed steps (256 MiB write); per-step working set > L2",
                    "parallelism": f"views sharded, {ws} rank(s), " +
                                   ("one gradient sum all-reduce (NCCL) per step" if do_bwd and ws > 1
@@ -524,7 +549,8 @@ def run_e2e(a, wl, scene, cams, precision, do_bwd, dev):
     g_host = torch.from_numpy(synth.make_grad((wl.n_views, wl.height, wl.width, 3), seed=100, scale=0.01)).pin_memory()
     dd = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()}
     g_dev = torch.empty(g_host.shape, device=dev)
-    r = Renderer(wl, precision=precision, device=str(dev), hit_capacity=hit_capacity(a, wl))
+    r = Renderer(wl, precision=precision, device=str(dev), hit_capacity=hit_capacity(a, wl),
+                 early_stop_wave=a.early_stop_wave)
     rgb_h = torch.empty(wl.n_views, wl.height, wl.width, 3).pin_memory()
     tr_h = torch.empty(wl.n_views, wl.height, wl.width).pin_memory()
     FT = wl.feat_dim + wl.slot_dim
