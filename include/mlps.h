@@ -410,6 +410,14 @@ mlps_status mlps_export_tiles(const mlps_config* cfg, int32_t K, const mlps_came
  * reset != 0 zeroes the counter after reading. */
 int64_t mlps_kernel_launches(int32_t reset);
 
+/* Self-test of the bounded waits (no counterpart in the paper). Every wait of the persistent
+ * tensor-core kernels gives up after a wall-time limit and ends its kernel with MLPS_ERR_TIMEOUT
+ * in the status word instead of hanging. This call runs that wait on a barrier nothing arrives
+ * at, for limit_us microseconds (1 .. 1e6), and writes its outcome to the status word of
+ * `scratch` (>= 256 bytes, 256-byte aligned): mlps_read_status(scratch) then returns
+ * MLPS_ERR_TIMEOUT. Nothing faults; the device stays usable. */
+mlps_status mlps_selftest_bounded_wait(int32_t limit_us, void* scratch, size_t scratch_bytes, void* stream);
+
 /* Enable (1) or disable (0). When enabled every call records CUDA events around each kernel
  * stage on its stream. */
 void mlps_profiler_enable(int32_t on);

@@ -137,6 +137,7 @@ _SIGS = [
     ("mlps_saved_hit_count", ctypes.c_int32, [_vp, _P(ctypes.c_int64), _vp]),
     ("mlps_backward_chunk_counts", ctypes.c_int32, [_vp, _vp, _P(ctypes.c_int64), _P(ctypes.c_int64), _vp]),
     ("mlps_forward_wave_counts", ctypes.c_int32, [_vp, _vp, _P(ctypes.c_int64), _P(ctypes.c_int64), _vp]),
+    ("mlps_selftest_bounded_wait", ctypes.c_int32, [ctypes.c_int32, _vp, ctypes.c_size_t, _vp]),
     ("mlps_export_hits", ctypes.c_int32, [_P(MlpsConfig), _P(MlpsCamera), ctypes.c_int32, _vp,
                                           ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("mlps_export_tiles", ctypes.c_int32, [_P(MlpsConfig), ctypes.c_int32, _P(MlpsCamera),
@@ -205,6 +206,11 @@ def mlps_forward_wave_counts(saved, scratch, stream: int = 0):
     _check("mlps_forward_wave_counts", load().mlps_forward_wave_counts(
         _ptr(saved), _ptr(scratch), ctypes.byref(a), ctypes.byref(b), stream or None))
     return int(a.value), int(b.value)
+
+
+def mlps_selftest_bounded_wait(limit_us: int, scratch, stream: int = 0):
+    _check("mlps_selftest_bounded_wait", load().mlps_selftest_bounded_wait(
+        int(limit_us), _ptr(scratch), int(scratch.numel() * scratch.element_size()), stream or None))
 
 
 def mlps_abi_version() -> int:

@@ -157,6 +157,16 @@ def test_device_table_workspace_and_validation(lib):
     assert st == _lib.MLPS_ERR_INVALID_ARGUMENT
 
 
+def test_selftest_bounded_wait_validates_on_the_host(lib):
+    """Argument errors come back before any launch (no GPU needed)."""
+    assert lib.mlps_selftest_bounded_wait(1000, None, 4096, None) == _lib.MLPS_ERR_INVALID_ARGUMENT
+    assert lib.mlps_selftest_bounded_wait(0, ctypes.c_void_p(256), 4096, None) == _lib.MLPS_ERR_INVALID_ARGUMENT
+    assert lib.mlps_selftest_bounded_wait(2000000, ctypes.c_void_p(256), 4096, None) == \
+        _lib.MLPS_ERR_INVALID_ARGUMENT
+    assert lib.mlps_selftest_bounded_wait(1000, ctypes.c_void_p(256), 128, None) == _lib.MLPS_ERR_INVALID_ARGUMENT
+    assert lib.mlps_selftest_bounded_wait(1000, ctypes.c_void_p(260), 4096, None) == _lib.MLPS_ERR_INVALID_ARGUMENT
+
+
 def test_contact_mode_validation(lib):
     """Contact-point mode (Sec. 3.2) takes one sample per hit; its forward and backward run in
     every precision."""
