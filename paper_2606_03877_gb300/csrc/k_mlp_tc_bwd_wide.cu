@@ -167,7 +167,9 @@ __global__ void __launch_bounds__(kWThreads, 1)
   float* sBias = reinterpret_cast<float*>(gb + Lw.bias);
   float* sScan = reinterpret_cast<float*>(gb + Lw.scan);
   float* sGeo = reinterpret_cast<float*>(gb + Lw.geo);
-  const uint32_t bar_w = sbase + Lw.bars, bar_m = bar_w + 8u, bar_e = bar_w + 16u;
+  // barriers: weights (TMA), MMA chain (forward layers, dgrads), weight gradients (wgrad and
+  // bias sums), teardown
+  const uint32_t bar_w = sbase + Lw.bars, bar_m = bar_w + 8u, bar_e = bar_w + 16u, bar_g = bar_w + 24u;
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(gb + Lw.misc);
   volatile int* sAbort = reinterpret_cast<volatile int*>(gb + Lw.misc + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -184,6 +186,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
     mbar_init(bar_w, 1);
     mbar_init(bar_m, 1);
     mbar_init(bar_e, 1);
+    mbar_init(bar_g, 1);
     *sAbort = 0;
     fence_mbar_init();
   }
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   float* dwb = w.dwb + (size_t)blockIdx.x * m.P;  // this block's dW copy: per layer [in][out]
-  uint32_t ph_w = 0, ph_m = 0;
+  uint32_t ph_w = 0, ph_m = 0, ph_g = 0;
   float geo_acc = 0.f;  // pose output `lane` (< 12) of the current primitive, this warp's share
   const float invS = 1.f / (float)S;
   int loaded = -1;
@@ -232,6 +235,13 @@ __global__ void __launch_bounds__(kWThreads, 1)
   };
   auto commit_m = [&]() {
     if (issuer) mma_commit(bar_m);
+  };
+  // the next completion of the weight-gradient MMAs (wgrad and bias sum of a layer)
+  auto wait_g = [&]() -> bool {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(bar_g, ph_g, sAbort, kWaitNsW));
+    ph_g ^= 1u;
+    tc_fence_after();
+    return ok;
   };
   // the block's copy of primitive p's gradients into d_weights (canonical layout), then zeroed
   auto flush_prim = [&](int p) {
@@ -482,17 +492,21 @@ __global__ void __launch_bounds__(kWThreads, 1)
     __syncthreads();
     if (issuer) {
       tc_fence_after();
+      if (!*sAbort) issue_dgrad_w(mSc, wt(L), mD, P.kpad[L], P.npad[L], (uint32_t)P.npad[L] * 128u);
+      mma_commit(bar_m);
       if (!*sAbort) {
-        issue_dgrad_w(mSc, wt(L), mD, P.kpad[L], P.npad[L], (uint32_t)P.npad[L] * 128u);
         issue_wgrad_w(ht, dt, mR, P.npad[L]);
         issue_bias_w(dt, ones_k, mRb);
       }
+      mma_commit(bar_g);
     }
-    commit_m();
-    // ---------------- backward phases l = L .. 1: each starts when dgrad_l, wgrad_l and its bias
-    // sum are done and issues dgrad_{l-1} with wgrad_{l-1} and its bias sum
+    // ---------------- backward phases l = L .. 1: each starts when dgrad_l is done (bar_m),
+    // reads G_l and masks it while wgrad_l and its bias sum run, waits for them (bar_g), flushes
+    // them, and issues dgrad_{l-1} (bar_m) and wgrad_{l-1} with its bias sum (bar_g)
+    bool dgrad_waited = false;  // (the recompute step has already waited for dgrad_1)
     for (int l = L; l >= 1; --l) {
-      (void)wait_m();
+      if (!dgrad_waited) (void)wait_m();
+      dgrad_waited = false;
       uint32_t G[32];  // this thread's half of G_l = dL/dH_l (unmasked) as BF16 pairs
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -502,8 +516,8 @@ __global__ void __launch_bounds__(kWThreads, 1)
 #pragma unroll
         for (int e = 0; e < 16; ++e) G[16 * q + e] = pack_bf16(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
       }
-      flush_layer(l);
-      // delta_{l-1} = G_l * [H_l > 0] (H_l in the H tile), into its TMEM slot and the delta tile
+      // delta_{l-1} = G_l * [H_l > 0] (H_l in the H tile, still read by wgrad_l), into its TMEM
+      // slot now and into the delta tile once wgrad_l is done
       {
         const RowSw sw(row);
 #pragma unroll
@@ -516,39 +530,47 @@ __global__ void __launch_bounds__(kWThreads, 1)
       }
       const uint32_t ds = delta_slot(l);
       tmem_st32(ds + lanes + hp, G);
-      store_row64(dt + hs, row, G);
       // H_{l-1} into the H tile from its TMEM slot (the mask above has read H_l: same thread,
       // same row), or recomputed from X below
       const bool from_slot = l - 1 >= 1 && l - 1 >= L - 2;
       const bool recompute = l - 1 >= 1 && !from_slot;
+      uint32_t h[32];
       if (from_slot) {
-        uint32_t h[32];
         tmem_ld32(fwd_slot(l - 1) + lanes + hp, h);
         tmem_wait_ld();
-        store_row64(ht + hs, row, h);
       }
+      (void)wait_g();  // wgrad_l and its bias sum: R, Rb final; the H and delta tiles free
+      flush_layer(l);
+      store_row64(dt + hs, row, G);
+      if (from_slot) store_row64(ht + hs, row, h);
       tmem_wait_st();
       fence_proxy_async_smem();
       tc_fence_before();
       __syncthreads();
       if (issuer) {
         tc_fence_after();
-        if (!*sAbort) {
+        if (!*sAbort)
           issue_dgrad_w(ds, wt(l - 1), mD, P.kpad[l - 1], P.npad[l - 1], (uint32_t)P.npad[l - 1] * 128u);
-          if (l == 1) {
-            issue_wgrad_w0(xt, dt, mR, ones_mn, P.npad[0]);  // bias gradient in row 64
-          } else if (recompute) {
-            issue_fwd_layer(xt, wt(0), mR, P.kpad[0], P.npad[0]);  // Z_0 into R
-          } else {
-            issue_wgrad_w(ht, dt, mR, P.npad[l - 1]);
-            issue_bias_w(dt, ones_k, mRb);
+        if (recompute) {
+          if (!*sAbort) issue_fwd_layer(xt, wt(0), mR, P.kpad[0], P.npad[0]);  // Z_0 into R
+          mma_commit(bar_m);  // dgrad_{l-1} and Z_0
+        } else {
+          mma_commit(bar_m);
+          if (!*sAbort) {
+            if (l == 1) {
+              issue_wgrad_w0(xt, dt, mR, ones_mn, P.npad[0]);  // bias gradient in row 64
+            } else {
+              issue_wgrad_w(ht, dt, mR, P.npad[l - 1]);
+              issue_bias_w(dt, ones_k, mRb);
+            }
           }
+          mma_commit(bar_g);
         }
       }
-      commit_m();
       if (recompute) {
         // H_1 = ReLU(Z_0 + b_0) into the H tile, then wgrad_1 and its bias sum
         (void)wait_m();
+        dgrad_waited = true;
         hidden_epilogue(0, rR, true, 0u);
         tc_fence_before();
         __syncthreads();
@@ -558,13 +580,13 @@ __global__ void __launch_bounds__(kWThreads, 1)
             issue_wgrad_w(ht, dt, mR, P.npad[1]);
             issue_bias_w(dt, ones_k, mRb);
           }
+          mma_commit(bar_g);
         }
-        commit_m();
       }
     }
     // ---------------- encoding derivative and pose chain (midpoint samples), as in the 64-wide
     // kernel: the per-interval sums A = sum_k gx_k and B = sum_k c_k gx_k (half 0)
-    (void)wait_m();  // dgrad_0 and wgrad_0
+    (void)wait_m();  // dgrad_0 (wgrad_0 may still run)
     if (lead) {
       uint32_t v0[32], v1[32];
       tmem_ld32(rD, v0);
@@ -631,6 +653,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
         }
       }
     }
+    (void)wait_g();  // wgrad_0
     flush_layer(0);
   }
   // teardown: no MMA may still write TMEM; the last primitive's gradients; TMEM freed
