@@ -880,7 +880,9 @@ def run_train(a):
         o = r_t.forward(dt["centers"], dt["scales"], dt["quats"], r_t.pack(dt["weights"]), cams)
         tgts.append((o["rgb"].clone(), o["feat"].clone()))
     del r_t
-    tr = Trainer(wl, scene, precision="fp32", device=str(dev), seed=rank)
+    # auto: the tensor cores (the contact model's BF16 forward and backward)
+    prec = "bf16" if a.precision == "auto" else a.precision
+    tr = Trainer(wl, scene, precision=prec, device=str(dev), seed=rank)
 
     def step(i):
         cams = batches[i % 4]
@@ -922,13 +924,18 @@ def run_train(a):
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1] > 0}
     dom = max(stage_ms, key=stage_ms.get)
     n_hits = tr.r.hit_count()
-    peaks, _ = _peaks()
-    clk_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+    peaks, peak_src = _peaks()
     flop_per_sample = 2 * sum(i * o for i, o in wl.layer_dims())
-    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": peak, "traffic": None,
-            "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_mhz:.0f} MHz",
-            "achieved": None, "frac": None}
+    if prec == "fp32":
+        clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": peak, "traffic": None,
+                "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clk_mhz:.0f} MHz",
+                "achieved": None, "frac": None}
+    else:
+        roof = {"bound": "tensor", "kernel": dom, "unit": "TFLOP/s", "peak": peaks["bf16_tflops_sustained"],
+                "traffic": None, "peak_source": f"{peak_src} bf16_tflops_sustained", "achieved": None, "frac": None}
+        peak = roof["peak"]
     if dom in ("mlp_fwd", "mlp_bwd"):
         ach = n_hits * flop_per_sample * (1 if dom == "mlp_fwd" else 2) / (stage_ms[dom] / 1e3) / 1e12
         roof.update(achieved=ach, frac=ach / peak)
@@ -937,11 +944,12 @@ def run_train(a):
         "metric": "training rays/s (pixels rendered per second), 4 views per step",
         "value": value, "unit": "rays/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic (seeded scene; targets rendered from a perturbed copy)",
+        "dtype": "f32" if prec == "fp32" else prec, "data": "synthetic (seeded scene; targets rendered from a perturbed copy)",
         "config": {"workload": f"train: {W}x{H} x {V} views per step, K={wl.K}, MLP {wl.input_dim}-32x32-4, "
                                f"contact-point input, 4 x {C} feature slots, a quarter of the 8x8 tiles "
                                "in the L1 + SSIM (lambda 0.2) + feature L1 loss, Adam",
-                   "loss_first_step": first, "loss_after_timed_steps": last, "hits_per_step": n_hits,
+                   "precision": prec, "loss_first_step": first, "loss_after_timed_steps": last,
+                   "hits_per_step": n_hits,
                    "l2": "flushed between timed steps (256 MiB write); per-step working set > L2",
                    "parallelism": f"one scene per rank, {ws} rank(s), no data-path collective"},
         "clocks": clocks, "gpu_launches": int(launches), "roofline": roof,

@@ -267,3 +267,28 @@ def test_contact_bf16_with_slots():
     e = rel_l2(out["feat"].reshape(-1, 64), F_o)
     print("contact bf16 slot map rel-L2", e)
     assert e < 1e-2
+
+
+def test_contact_bf16_with_slots_gradients():
+    """The paper's model with feature slots on the tensor-core path: L2 loss on the image and the
+    slot map against the perturbed scene; every group, slot embeddings included, within the
+    BF16 bar of the oracle's reverse mode."""
+    cfg = CONTACT.replace(width=64, height=48, K=12, n_views=1, slot_dim=64)
+    scene = scaled_scene(cfg, 5, 2.0)
+    cams = synth.make_cameras(cfg, first_view_seed=5)
+    cur, _, Fc = oracle.render(cfg, scene, cams)
+    tgt, _, Ft = oracle.render(cfg, synth.perturb_scene(scene, cfg, 1), cams)
+    g = (cur - tgt).astype(np.float32)
+    gF = (Fc - Ft).astype(np.float32)
+    r = Renderer(cfg, precision="bf16")
+    d = to_dev(scene)
+    r.forward(d["centers"], d["scales"], d["quats"], r.pack(d["weights"]), cams)
+    got = r.backward(torch.from_numpy(g.reshape(1, 48, 64, 3)).cuda(), None,
+                     torch.from_numpy(gF.reshape(1, 48, 64, 64)).cuda())
+    torch.cuda.synchronize()
+    assert r.status() == 0 and r.status("scratch") == 0
+    ref = oracle.render_backward(cfg, scene, cams, oracle.all_pixels(cams), g, None, gF)
+    errs = {k: rel_l2(got[k].cpu().numpy(), ref[k]) for k in ("d_weights", "d_centers", "d_scales", "d_quats")}
+    print("contact + slots BF16 gradient rel-L2:", errs)
+    for k, e in errs.items():
+        assert e < 2e-2, (k, errs)
