@@ -917,8 +917,9 @@ def run_train(a):
         dist.barrier()
     clocks = clk.stop()
     last = float(tr.loss_out[0])
-    if tr.status() != 0:
-        raise RuntimeError("device status after the timed steps")
+    st = tr.status()
+    if st != 0:
+        raise RuntimeError(f"device status after the timed steps: {_lib.mlps_status_string(st)}")
     total_ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev), ws, dev)
     value = job_rays_per_s(V * H * W, ws, a.steps, total_ms)
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1] > 0}
