@@ -566,16 +566,10 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
       (void)wait_mma();  // dgrad of B_l (and every wgrad issued before it)
       if (l > 0 && l < nl - 1) {
         // delta_l (A operand of dgrad_l, done) from TMEM to its tile D(l), 16 columns at a time
-        const RowSw sw(row);
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-          uint32_t dl[16];
-          tmem_ld16(arow + 16u * hf, dl);
-          tmem_wait_ld();
-#pragma unroll
-          for (int ch = 0; ch < 4; ++ch)
-            st_shared_v4(dtile(l) + sw.off(4 * hf + ch), dl[4 * ch], dl[4 * ch + 1], dl[4 * ch + 2], dl[4 * ch + 3]);
-        }
+        uint32_t dl[32];
+        tmem_ld32(arow, dl);
+        tmem_wait_ld();
+        store_row64(dtile(l), row, dl);
       }
       if (l > 0) {
         // delta_{l-1} = G * [H_l > 0] (H_l from T_l; wgrad_l, which reads it, is issued below),
@@ -584,11 +578,13 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
         const uint32_t vmask = valid ? 0xFFFFFFFFu : 0u;
         const RowSw sw(row);
         uint32_t pk[32];
+        uint32_t v2[2][32];
+        tmem_ld32(trow, v2[0]);
+        tmem_ld32(trow + 32u, v2[1]);
+        tmem_wait_ld();
 #pragma unroll
         for (int hf = 0; hf < 2; ++hf) {
-          uint32_t v[32];
-          tmem_ld32(trow + 32u * hf, v);
-          tmem_wait_ld();
+          const uint32_t (&v)[32] = v2[hf];
 #pragma unroll
           for (int ch = 0; ch < 4; ++ch) {
             uint32_t hq[4];

@@ -4,9 +4,10 @@
 // What does not fit on chip at this width, and how the kernel gets around it:
 //  * Weight gradients: four 128 x 128 layers and the head need 544 TMEM columns, more than the
 //    512 of an SM. Each layer's gradient is accumulated in one TMEM region for one chunk only
-//    and then added into the block's FP32 copy in global memory (L2-resident, laid out
-//    [input][output] per layer so that a thread adds contiguous runs with vector reductions);
-//    the copy goes into d_weights when the block's primitive changes.
+//    and then added into the block's FP32 copy in global memory (L2-resident, laid out as
+//    [out / 4][in][4] per layer, so that one vector reduction instruction of a warp covers four
+//    outputs of 32 consecutive inputs, 512 contiguous bytes); the copy goes into d_weights when
+//    the block's primitive changes.
 //  * Activations: the resident weights take 120 KB of shared memory, so only one H tile, one
 //    delta tile and the encoded input fit next to them. The last hidden activation H_L stays
 //    in the H tile (it is also the head's A operand); H_{L-1} and H_{L-2} stay in TMEM (BF16
@@ -16,10 +17,10 @@
 //  * Bias gradients: every input row of the wgrad accumulator is a feature, so the sum of
 //    delta_l over the rows is one more MMA: A = delta_l read as an MN-major operand (M = the
 //    outputs), B = a constant K-major operand whose first row is all ones (N = 16).
-// Eight warps per SM: thread (row, half) owns TMEM lane `row` (the chunk's sample row) and the
-// columns [64 half, 64 half + 64) of every 128-wide activation, gradient and weight-gradient
+// Sixteen warps per SM: thread (row, part) owns TMEM lane `row` (the chunk's sample row) and
+// the columns [32 part, 32 part + 32) of every 128-wide activation, gradient and weight-gradient
 // row; the per-sample scalar work (the encoding, the composite reverse, the pose chain) runs in
-// half 0. Per chunk: encode X; forward to the head; reverse of the interval composite (Eq. 6)
+// part 0. Per chunk: encode X; forward to the head; reverse of the interval composite (Eq. 6)
 // into delta of the head; then for l = L .. 1: flush dW_l, delta_{l-1} = G_l * [H_l > 0],
 // dgrad_{l-1}, H_{l-1} into the H tile, wgrad_{l-1} and its bias sum; finally the encoding
 // derivative and the pose chain (as in k_mlp_tc_bwd.cu). Every wait is bounded by wall time;
@@ -44,7 +45,9 @@ namespace tc {
 
 namespace {
 
-constexpr int kWThreads = 2 * kEGThreads;      // two threads per TMEM lane (column halves)
+constexpr int kParts = 4;                      // threads per TMEM lane (column quarters)
+constexpr int kWThreads = kParts * kEGThreads;
+constexpr int kPartCols = 128 / kParts;        // FP32 columns of a 128-wide row per thread
 constexpr uint32_t kSlab = kM * 128;           // one 64-column slab of 128 rows (16 KB)
 constexpr uint32_t kOnesMN = 2048;             // 16 rows of the MN-major ones atom (one K step)
 constexpr uint32_t kOnesK = 2048;              // K-major ones operand: 16 rows, the first all ones
@@ -174,11 +177,13 @@ __global__ void __launch_bounds__(kWThreads, 1)
   volatile int* sAbort = reinterpret_cast<volatile int*>(gb + Lw.misc + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = threadIdx.x & (kM - 1);  // sample row of the chunk, TMEM lane
-  const int half = threadIdx.x >> 7;       // column half (warp-uniform)
-  const bool lead = half == 0;             // the per-sample scalar work
+  const int part = threadIdx.x >> 7;       // column quarter (warp-uniform)
+  const bool lead = part == 0;             // the per-sample scalar work
   const bool issuer = threadIdx.x == 0;
   const uint32_t xt = sbase + Lw.xt, ht = sbase + Lw.ht, dt = sbase + Lw.dt;
-  const uint32_t hs = (uint32_t)half * kSlab;  // this thread's slab of a two-slab tile
+  // this thread's columns in a two-slab row-major tile: slab, first 16-byte chunk of the row
+  const uint32_t hs = (uint32_t)(part * kPartCols / 64) * kSlab;
+  const int hch = (part * kPartCols % 64) / 8;
   const uint32_t ones_mn = sbase + Lw.ones_mn, ones_k = sbase + Lw.ones_k;
   auto wt = [&](int l) { return sbase + Lw.w + (uint32_t)P.sw_off[l]; };
 
@@ -213,14 +218,21 @@ __global__ void __launch_bounds__(kWThreads, 1)
   const uint32_t mD = tmem + kColD, mR = tmem + kColR, mRb = tmem + kColRb;
   const uint32_t mSa = tmem + kColSa, mSb = tmem + kColSb, mSc = tmem + kColSc;
   const uint32_t rD = mD + lanes, rR = mR + lanes, rRb = mRb + lanes;
-  const uint32_t hc = 64u * (uint32_t)half;  // first FP32 column of this thread's half
-  const uint32_t hp = 32u * (uint32_t)half;  // first BF16-pair column of this thread's half
+  const uint32_t hc = (uint32_t)(kPartCols * part);  // first FP32 column of this thread's part
+  const uint32_t hp = hc / 2;                        // first BF16-pair column of this thread's part
+  // this thread's 32 columns (16 BF16 pairs) of row `row` of a two-slab tile
+  auto store_part = [&](uint32_t tile, const uint32_t(&pk)[16]) {
+    const RowSw sw(row);
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch)
+      st_shared_v4(tile + hs + sw.off(hch + ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+  };
 
   const int total = walk_chunk_count(w);
   const int* const bmap = walk_map(w);  // list position -> forward position
   const int cb = (int)((long long)total * blockIdx.x / gridDim.x);
   const int ce = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
-  float* dwb = w.dwb + (size_t)blockIdx.x * m.P;  // this block's dW copy: per layer [in][out]
+  float* dwb = w.dwb + (size_t)blockIdx.x * m.P;  // this block's dW copy, per layer [out / 4][in][4]
   uint32_t ph_w = 0, ph_m = 0, ph_g = 0;
   float geo_acc = 0.f;  // pose output `lane` (< 12) of the current primitive, this warp's share
   const float invS = 1.f / (float)S;
@@ -250,11 +262,12 @@ __global__ void __launch_bounds__(kWThreads, 1)
     float* dW = a.d_weights + (size_t)p * m.Prow;
     for (int l = 0; l < nl; ++l) {
       const int din = m.din[l], dout = m.dout[l];
-      // (the copy is updated by reductions at L2: read and clear it there, past the L1)
+      // (the copy is updated by reductions at L2: read and clear it there, past the L1; its
+      // layout is [out / 4][in][4], d_weights' is [out][in])
       for (int i = threadIdx.x; i < din * dout; i += kWThreads) {
-        const int k = i / dout, n = i - k * dout;  // copy layout [in][out]
         const float v = __ldcg(dwb + m.woff[l] + i);
         if (v != 0.f) {
+          const int g4 = i / (4 * din), r = i - g4 * 4 * din, k = r >> 2, n = 4 * g4 + (r & 3);
           atomicAdd(&dW[m.woff[l] + n * din + k], v);
           __stcg(dwb + m.woff[l] + i, 0.f);
         }
@@ -278,49 +291,52 @@ __global__ void __launch_bounds__(kWThreads, 1)
     __syncthreads();
   };
   // chunk gradient of layer l (region R: input row = lane, outputs along the columns, this
-  // thread's half of them; layer 0's bias gradient in row 64, other layers' in Rb) into the
-  // block's copy
-  auto flush_layer = [&](int l) {
+  // thread's part of them; layer 0's bias gradient in row 64, other layers' in Rb) into the
+  // block's copy, in two steps: flush_take reads R and Rb into registers (before the barrier
+  // after which the next wgrad overwrites them), flush_put adds them to the copy. The
+  // reductions go out after that barrier: a barrier waits until the earlier global memory
+  // operations of its threads are performed, so reductions issued before it would put their
+  // whole round trip to the L2 on the chunk's serial chain.
+  auto flush_take = [&](int l, uint32_t(&v)[32], float& b) {
+    uint32_t bb = 0u;
+    tmem_ld32(rR + hc, v);  // (R has 128 columns; only the head's first 32 are used below)
+    if (l > 0 && lead) bb = tmem_ld1(rRb);
+    tmem_wait_ld();
+    b = __uint_as_float(bb);
+  };
+  auto flush_put = [&](int l, const uint32_t(&v)[32], float b) {
+    if (*sAbort) return;
     const int din = m.din[l], dout = m.dout[l];
-    float* cp = dwb + m.woff[l];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int c0 = (int)hc + 32 * q;
-      if (c0 >= P.npad[l]) break;  // warp-uniform (the head's 32 columns: half 0)
-      uint32_t v[32];
-      tmem_ld32(rR + (uint32_t)c0, v);
-      tmem_wait_ld();
-      if (*sAbort) continue;
+    const int c0 = (int)hc;
+    if (c0 < P.npad[l]) {
       if (row < din) {
+        // copy layout [out / 4][in][4]: the four outputs 4g .. 4g + 3 of input `row` are one
+        // 16-byte vector, and the warp's 32 consecutive inputs make one 512-byte run
+        float* cp = dwb + m.woff[l] + ((size_t)(c0 / 4) * din + row) * 4;
+        const int nj = min(32, dout - c0);
 #pragma unroll
-        for (int j = 0; j < 32; j += 4)
-          if (c0 + j < dout)
-            red_add_v4(cp + (size_t)row * dout + c0 + j, __uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                       __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+        for (int j = 0; j < 32; j += 4) {
+          if (j < nj)
+            red_add_v4(cp, __uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
+                       __uint_as_float(v[j + 3]));
+          cp += 4 * din;
+        }
       } else if (l == 0 && row == 64) {
         for (int j = 0; j < 32; ++j)
           if (c0 + j < dout) atomicAdd(&dwb[m.boff[0] + c0 + j], __uint_as_float(v[j]));
       }
     }
-    if (l > 0 && lead) {
-      uint32_t v16[16];
-      tmem_ld16(rRb, v16);
-      tmem_wait_ld();
-      if (!*sAbort && row < dout) atomicAdd(&dwb[m.boff[l] + row], __uint_as_float(v16[0]));
-    }
-    tc_fence_before();
+    if (l > 0 && lead && row < dout) atomicAdd(&dwb[m.boff[l] + row], b);
   };
-  // epilogue of hidden layer l, this thread's half: H_{l+1} = ReLU(Z_l + b_l) from the
+  // epilogue of hidden layer l, this thread's part: H_{l+1} = ReLU(Z_l + b_l) from the
   // accumulator row `src` as BF16 pairs, into the TMEM slot row `dst` or the H tile
   auto hidden_epilogue = [&](int l, uint32_t src, bool to_tile, uint32_t dst) {
-    const float* bias = sBias + P.bias_off[l] + hc;
-    uint32_t pk[32];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    const float4* b4 = reinterpret_cast<const float4*>(sBias + P.bias_off[l] + hc);
+    uint32_t pk[16];
+    {
       uint32_t v[32];
-      tmem_ld32(src + hc + 32u * q, v);
+      tmem_ld32(src + hc, v);
       tmem_wait_ld();
-      const float4* b4 = reinterpret_cast<const float4*>(bias + 32 * q);
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const float4 bq = b4[e];
@@ -328,16 +344,16 @@ __global__ void __launch_bounds__(kWThreads, 1)
         float x2 = __uint_as_float(v[4 * e + 2]), x3 = __uint_as_float(v[4 * e + 3]);
         add2_f32(x0, x1, bq.x, bq.y);
         add2_f32(x2, x3, bq.z, bq.w);
-        pk[16 * q + 2 * e] = pack_bf16_relu(x0, x1);
-        pk[16 * q + 2 * e + 1] = pack_bf16_relu(x2, x3);
+        pk[2 * e] = pack_bf16_relu(x0, x1);
+        pk[2 * e + 1] = pack_bf16_relu(x2, x3);
       }
     }
     tc_fence_before();
     if (to_tile) {
-      store_row64(ht + hs, row, pk);
+      store_part(ht, pk);
       fence_proxy_async_smem();
     } else {
-      tmem_st32(dst + hp, pk);
+      tmem_st16(dst + hp, pk);
       tmem_wait_st();
     }
   };
@@ -355,9 +371,22 @@ __global__ void __launch_bounds__(kWThreads, 1)
   const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + Lw.pgeo);
   int prim = cb < ce ? simt::find_prim(w, cb) : 0;
 
+  // Layer 0's gradient of the previous chunk stays in R until the next chunk has issued its
+  // first layer (R is next written by that chunk's wgrad of the head), so that its reductions
+  // overlap the first forward layer instead of the next barrier; earlier on a primitive change
+  bool pend0 = false;
+  auto flush0 = [&]() {
+    uint32_t rv[32];
+    float rb;
+    flush_take(0, rv, rb);
+    tc_fence_before();
+    flush_put(0, rv, rb);
+    pend0 = false;
+  };
   for (int c = cb; c < ce; ++c) {
     while (c >= w.chunk_start[prim + 1]) ++prim;
     if (prim != loaded) {
+      if (pend0) flush0();
       if (loaded >= 0) flush_prim(loaded);
       if (threadIdx.x == 0 && !*sAbort) {
         mbar_arrive_expect_tx(bar_w, (uint32_t)P.w_bytes);
@@ -410,6 +439,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
       if (!*sAbort) issue_fwd_layer(xt, wt(0), mD, P.kpad[0], P.npad[0]);
     }
     commit_m();
+    if (pend0) flush0();
     for (int l = 0; l < L; ++l) {
       const int j = l + 1;  // H_j
       (void)wait_m();
@@ -425,7 +455,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
       }
       commit_m();
     }
-    // ---------------- heads and reverse of the interval composite (Eq. 6) -> delta_L (half 0)
+    // ---------------- heads and reverse of the interval composite (Eq. 6) -> delta_L (part 0)
     (void)wait_m();
     if (lead) {
       float z[4 + NF];
@@ -507,42 +537,43 @@ __global__ void __launch_bounds__(kWThreads, 1)
     for (int l = L; l >= 1; --l) {
       if (!dgrad_waited) (void)wait_m();
       dgrad_waited = false;
-      uint32_t G[32];  // this thread's half of G_l = dL/dH_l (unmasked) as BF16 pairs
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
+      uint32_t G[16];  // this thread's part of G_l = dL/dH_l (unmasked) as BF16 pairs
+      {
         uint32_t v[32];
-        tmem_ld32(rD + hc + 32u * q, v);
+        tmem_ld32(rD + hc, v);
         tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 16; ++e) G[16 * q + e] = pack_bf16(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
+        for (int e = 0; e < 16; ++e) G[e] = pack_bf16(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
       }
       // delta_{l-1} = G_l * [H_l > 0] (H_l in the H tile, still read by wgrad_l), into its TMEM
       // slot now and into the delta tile once wgrad_l is done
       {
         const RowSw sw(row);
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
+        for (int ch = 0; ch < 4; ++ch) {
           uint32_t hq[4];
-          ld_shared_v4(ht + hs + sw.off(ch), hq[0], hq[1], hq[2], hq[3]);
+          ld_shared_v4(ht + hs + sw.off(hch + ch), hq[0], hq[1], hq[2], hq[3]);
 #pragma unroll
           for (int e = 0; e < 4; ++e) G[4 * ch + e] &= bf16x2_nonzero(hq[e]) & vmask;
         }
       }
       const uint32_t ds = delta_slot(l);
-      tmem_st32(ds + lanes + hp, G);
+      tmem_st16(ds + lanes + hp, G);
       // H_{l-1} into the H tile from its TMEM slot (the mask above has read H_l: same thread,
       // same row), or recomputed from X below
       const bool from_slot = l - 1 >= 1 && l - 1 >= L - 2;
       const bool recompute = l - 1 >= 1 && !from_slot;
-      uint32_t h[32];
+      uint32_t h[16];
       if (from_slot) {
-        tmem_ld32(fwd_slot(l - 1) + lanes + hp, h);
+        tmem_ld16(fwd_slot(l - 1) + lanes + hp, h);
         tmem_wait_ld();
       }
       (void)wait_g();  // wgrad_l and its bias sum: R, Rb final; the H and delta tiles free
-      flush_layer(l);
-      store_row64(dt + hs, row, G);
-      if (from_slot) store_row64(ht + hs, row, h);
+      store_part(dt, G);
+      if (from_slot) store_part(ht, h);
+      uint32_t rv[32];
+      float rb;
+      flush_take(l, rv, rb);
       tmem_wait_st();
       fence_proxy_async_smem();
       tc_fence_before();
@@ -567,6 +598,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
           mma_commit(bar_g);
         }
       }
+      flush_put(l, rv, rb);
       if (recompute) {
         // H_1 = ReLU(Z_0 + b_0) into the H tile, then wgrad_1 and its bias sum
         (void)wait_m();
@@ -585,7 +617,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
       }
     }
     // ---------------- encoding derivative and pose chain (midpoint samples), as in the 64-wide
-    // kernel: the per-interval sums A = sum_k gx_k and B = sum_k c_k gx_k (half 0)
+    // kernel: the per-interval sums A = sum_k gx_k and B = sum_k c_k gx_k (part 0)
     (void)wait_m();  // dgrad_0 (wgrad_0 may still run)
     if (lead) {
       uint32_t v0[32], v1[32];
@@ -653,9 +685,10 @@ __global__ void __launch_bounds__(kWThreads, 1)
         }
       }
     }
-    (void)wait_g();  // wgrad_0
-    flush_layer(0);
+    (void)wait_g();  // wgrad_0 (also before the next chunk writes X)
+    pend0 = true;
   }
+  if (pend0) flush0();
   // teardown: no MMA may still write TMEM; the last primitive's gradients; TMEM freed
   if (issuer) {
     mma_commit(bar_e);
@@ -680,15 +713,15 @@ __global__ void __launch_bounds__(kWThreads, 1)
 
 // The tensor-core backward at hidden width 128 (tc model `m`): midpoint samples with the
 // configurations' encodings (xyz L = 6, direction L = 4: 60 inputs in one slab), up to 16
-// feature outputs, every output count and weight offset a multiple of 4 (vector reductions),
-// and its shared memory within the SM's.
+// feature outputs, every output count and weight offset a multiple of 4 (the weight-gradient
+// copy's 16-byte vectors), and its shared memory within the SM's.
 bool tc_bwd_wide_supported(const Model& m, const TcPlan& P) {
   if (m.width != 128 || m.nl < 2 || m.nl > 5 || m.contact) return false;
   if (m.xyzL != 6 || m.dirL != 4 || P.kpad[0] != 64) return false;
   if (m.F > 16 || m.nout > 32) return false;
   if (m.P % 4 != 0) return false;
   for (int l = 0; l < m.nl; ++l)
-    if (m.dout[l] % 4 != 0 || m.woff[l] % 4 != 0 || m.boff[l] % 4 != 0) return false;
+    if (m.dout[l] % 4 != 0 || m.woff[l] % 4 != 0) return false;
   const int ipc = m.S <= 128 ? 128 / m.S : 1;
   return tc::wide_layout(P, 32, ipc).total + 1024 <= 227 * 1024;
 }
