@@ -48,6 +48,7 @@ namespace {
 constexpr int kParts = 4;                      // threads per TMEM lane (column quarters)
 constexpr int kWThreads = kParts * kEGThreads;
 constexpr int kPartCols = 128 / kParts;        // FP32 columns of a 128-wide row per thread
+constexpr int kScanPart = 4 * 8;               // scan scratch floats per part (4 warps x 8 values)
 constexpr uint32_t kSlab = kM * 128;           // one 64-column slab of 128 rows (16 KB)
 constexpr uint32_t kOnesMN = 2048;             // 16 rows of the MN-major ones atom (one K step)
 constexpr uint32_t kOnesK = 2048;              // K-major ones operand: 16 rows, the first all ones
@@ -58,7 +59,10 @@ constexpr uint32_t kColD = 0, kColSa = 128, kColSb = 192, kColSc = 256, kColR = 
 constexpr uint32_t kTmemColsW = 512;
 
 struct WideSmem {
-  uint32_t w, xt, ht, dt, ones_mn, ones_k, bias, itab, giv, ddel, gf, scan, geo, pgeo, bars, misc, total;
+  // tab: two buffers (tab_stride apart) of the chunk tables, each holding the interval records
+  // (itab), their gradients (giv) and feature gradients (gf) at these offsets
+  uint32_t w, xt, ht, dt, ones_mn, ones_k, bias, tab, tab_stride, itab, giv, gf, ddel, scan, share, geo, pgeo, bars,
+      misc, total;
 };
 
 MLPS_HD uint32_t alw(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -80,16 +84,22 @@ MLPS_HD WideSmem wide_layout(const TcPlan& P, int F, int ipc) {
   o = alw(o + kOnesK, 1024);
   L.bias = o;
   o = alw(o + 4 * P.bias_floats, 16);
-  L.itab = o;
-  o = alw(o + (uint32_t)sizeof(IntervalRec) * ipc, 16);
-  L.giv = o;
-  o = alw(o + 16 * ipc, 16);
+  L.tab = o;
+  uint32_t q = 0;
+  L.itab = q;
+  q = alw(q + (uint32_t)sizeof(IntervalRec) * ipc, 16);
+  L.giv = q;
+  q = alw(q + 16 * ipc, 16);
+  L.gf = q;
+  q = alw(q + 4 * ipc * (F > 0 ? F : 1), 16);
+  L.tab_stride = q;
+  o += 2 * q;
   L.ddel = o;
   o = alw(o + 4 * ipc, 16);
-  L.gf = o;
-  o = alw(o + 4 * ipc * (F > 0 ? F : 1), 16);
-  L.scan = o;  // 4 warps x the widest segmented scan (3 + F values, or 6)
-  o = alw(o + 4 * 4 * (3 + (F > 3 ? F : 3)), 16);
+  L.scan = o;  // per part: 4 warps x the widest segmented scan of that part (at most 8 values)
+  o = alw(o + 4 * kParts * kScanPart, 16);
+  L.share = o;  // parts 1-3: their shares of dL/d alpha per row
+  o = alw(o + 4 * (kParts - 1) * kM, 16);
   L.geo = o;
   o = alw(o + 4 * 16, 16);
   L.pgeo = o;
@@ -148,6 +158,42 @@ MLPS_DEV void issue_bias_w(uint32_t Dt, uint32_t onesK, uint32_t Rb) {
   for (int kk = 0; kk < kM / 16; ++kk) mma_bf16(Rb, da + (uint64_t)(kk * 128), db, id, kk > 0);
 }
 
+// Part P's share of the reverse of the interval composite (Eq. 6) for one sample row: of the
+// 3 + NF weighted head outputs w_k c_k (colours) and w_k f_k (features), the values
+// [P kHeadPer, (P + 1) kHeadPer), reverse-scanned over the interval with the part's scratch and
+// named barrier, and their terms of dL/d alpha_k: g (tau_k e^{-alpha_k} c_k - (suffix - w_k c_k)).
+// `gf` is the row's feature gradient (nullptr: zero); outputs past 3 + F are zero.
+template <int NF>
+constexpr int head_per() { return (3 + NF + kParts - 1) / kParts; }
+
+template <int NF, int P>
+MLPS_DEV float head_share(const float (&z)[4 + NF], const float (&cq)[3], const float (&gcs)[3], const float* gf, int F,
+                          float wk, float te, int row, int S, float* scratch, int bar_id) {
+  constexpr int kPer = head_per<NF>(), v0 = P * kPer;
+  float sv[kPer], val[kPer], g[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int v = v0 + j;
+    if (v < 3) {
+      val[j] = cq[v < 3 ? v : 0];
+      g[j] = gcs[v < 3 ? v : 0];
+    } else if (v < 3 + NF && v - 3 < F) {
+      val[j] = z[v < 3 + NF ? v + 1 : 0];
+      g[j] = gf ? gf[v - 3] : 0.f;
+    } else {
+      val[j] = 0.f;
+      g[j] = 0.f;
+    }
+    sv[j] = wk * val[j];
+  }
+  const int nv = min(kPer, 3 + F - v0);  // the same for the whole part
+  if (nv > 0) seg_scan_rev<kPer>(sv, nv, row, S, scratch, bar_id);
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) acc += g[j] * (te * val[j] - (sv[j] - wk * val[j]));
+  return acc;
+}
+
 // Four floats added to global memory without return (16-byte aligned address).
 MLPS_DEV void red_add_v4(float* p, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
@@ -169,6 +215,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
   const WideSmem Lw = wide_layout(P, 32, w.ipc);  // the host sizes the same layout
   float* sBias = reinterpret_cast<float*>(gb + Lw.bias);
   float* sScan = reinterpret_cast<float*>(gb + Lw.scan);
+  float* sShare = reinterpret_cast<float*>(gb + Lw.share);
   float* sGeo = reinterpret_cast<float*>(gb + Lw.geo);
   // barriers: weights (TMA), MMA chain (forward layers, dgrads), weight gradients (wgrad and
   // bias sums), teardown
@@ -364,10 +411,22 @@ __global__ void __launch_bounds__(kWThreads, 1)
   // copied to the H tile, or its delta consumed by an earlier dgrad)
   auto delta_slot = [&](int l) { return (l == L || l == L - 3) ? mSc : (l == L - 1 ? mSb : mSa); };
 
-  IntervalRec* T = reinterpret_cast<IntervalRec*>(gb + Lw.itab);
-  float4* GI = reinterpret_cast<float4*>(gb + Lw.giv);
   float* DD = reinterpret_cast<float*>(gb + Lw.ddel);
-  float* GF = reinterpret_cast<float*>(gb + Lw.gf);
+  // Chunk c's tables are in buffer (c - cb) & 1. From the block's second chunk on, part 1 copies
+  // them with cp.async while part 0 reverses the previous chunk's composite.
+  auto tab = [&](int cc) { return gb + Lw.tab + (uint32_t)((cc - cb) & 1) * Lw.tab_stride; };
+  auto prefetch_tab = [&](int cn, int pc) {
+    int pn = pc;
+    while (cn >= w.chunk_start[pn + 1]) ++pn;
+    const int fst = (cn - w.chunk_start[pn]) * w.ipc;
+    const int i = threadIdx.x - kEGThreads;  // part 1's thread i copies interval i
+    if (i < 0 || i >= min(w.ipc, w.prim_count[pn] - fst)) return;
+    const int slot = walk_slot(bmap, w.prim_start[pn] + fst + i);
+    const uint32_t t = smem_u32(tab(cn));
+    // (F is a multiple of 4 on this path: the head's output count is)
+    for (int f = 0; f < F; f += 4) cp_async16(t + Lw.gf + 4u * (uint32_t)(i * F + f), w.hit_gfeat + (size_t)slot * F + f);
+    rec_copy_async(w, slot, t + Lw.itab + 64u * (uint32_t)i, t + Lw.giv + 16u * (uint32_t)i);
+  };
   const PrimGeo& Gp = *reinterpret_cast<const PrimGeo*>(gb + Lw.pgeo);
   int prim = cb < ce ? simt::find_prim(w, cb) : 0;
 
@@ -412,12 +471,18 @@ __global__ void __launch_bounds__(kWThreads, 1)
     // ---------------- the chunk's interval records and their gradients
     const int first = (c - w.chunk_start[prim]) * w.ipc;
     const int nint = min(w.ipc, w.prim_count[prim] - first);
-    __syncthreads();  // the previous chunk is done with the tables
-    for (int i = threadIdx.x; i < nint; i += kWThreads) {
-      const size_t slot = walk_slot(bmap, w.prim_start[prim] + first + i);
-      T[i] = w.rec[slot];
-      GI[i] = w.hit_grad[slot];
-      for (int f = 0; f < F; ++f) GF[i * F + f] = w.hit_gfeat[slot * F + f];
+    IntervalRec* T = reinterpret_cast<IntervalRec*>(tab(c) + Lw.itab);
+    float4* GI = reinterpret_cast<float4*>(tab(c) + Lw.giv);
+    float* GF = reinterpret_cast<float*>(tab(c) + Lw.gf);
+    if (c == cb) {
+      for (int i = threadIdx.x; i < nint; i += kWThreads) {
+        const size_t slot = walk_slot(bmap, w.prim_start[prim] + first + i);
+        T[i] = w.rec[slot];
+        GI[i] = w.hit_grad[slot];
+        for (int f = 0; f < F; ++f) GF[i * F + f] = w.hit_gfeat[slot * F + f];
+      }
+    } else {
+      cp_async_wait_all();  // this thread's copies of the chunk's tables (if any) have landed
     }
     __syncthreads();
     const int iv = row / S, k = row - iv * S;
@@ -455,9 +520,12 @@ __global__ void __launch_bounds__(kWThreads, 1)
       }
       commit_m();
     }
-    // ---------------- heads and reverse of the interval composite (Eq. 6) -> delta_L (part 0)
+    // ---------------- heads and reverse of the interval composite (Eq. 6) -> delta_L. Every part
+    // evaluates the head of its row and the interval's transmittance; the reverse scan of the
+    // 3 + F weighted outputs is shared out, kHeadPer values per part, and part 0 gathers the
+    // parts' contributions to dL/d alpha and writes delta_L.
     (void)wait_m();
-    if (lead) {
+    {
       float z[4 + NF];
       {
         uint32_t r32[32];
@@ -468,55 +536,58 @@ __global__ void __launch_bounds__(kWThreads, 1)
         for (int j = 0; j < 4 + NF; ++j) z[j] = j < m.nout ? __uint_as_float(r32[j]) + bias[j] : 0.f;
       }
       tc_fence_before();
+      float* scr = sScan + part * kScanPart;  // this part's scan scratch and named barrier
+      const int pbar = 1 + part;
       const IntervalRec& I = T[valid ? iv : 0];
       const float dtv = valid ? I.dt : 0.f;
       const float sig = softplus_fast(z[3]);
       const float ak = valid ? sig * dtv : 0.f;
       float sc1[1] = {ak};
-      seg_scan<1>(sc1, 1, row, S, sScan, 1);
+      seg_scan<1>(sc1, 1, row, S, scr, pbar);
       const float Aex = sc1[0] - ak;
       const float tau = __expf(-Aex), ea = __expf(-ak);
       const float wk = valid ? tau * (1.f - ea) : 0.f;
       float cq[3];
       for (int u = 0; u < 3; ++u) cq[u] = sigmoid_fast(z[u]);
-      float sv[3 + NF];
-#pragma unroll
-      for (int u = 0; u < 3; ++u) sv[u] = wk * cq[u];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) sv[3 + f] = f < F ? wk * z[4 + f] : 0.f;
-      seg_scan_rev<3 + NF>(sv, 3 + F, row, S, sScan, 1);
       const float4 gI = valid ? GI[iv] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float gcs[3] = {gI.x, gI.y, gI.z};
-      float dLda = gI.w;
-#pragma unroll
-      for (int u = 0; u < 3; ++u) dLda += gcs[u] * (tau * ea * cq[u] - (sv[u] - wk * cq[u]));
-      float dz[4 + NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const float gf = (valid && f < F) ? GF[iv * F + f] : 0.f;
-        const float fk = z[4 + f];
-        dLda += gf * (tau * ea * fk - (sv[3 + f] - wk * fk));
-        dz[4 + f] = wk * gf;
+      const float* gfr = valid ? GF + iv * F : nullptr;
+      float share = 0.f;
+      switch (part) {
+        case 0: share = head_share<NF, 0>(z, cq, gcs, gfr, F, wk, tau * ea, row, S, scr, pbar); break;
+        case 1: share = head_share<NF, 1>(z, cq, gcs, gfr, F, wk, tau * ea, row, S, scr, pbar); break;
+        case 2: share = head_share<NF, 2>(z, cq, gcs, gfr, F, wk, tau * ea, row, S, scr, pbar); break;
+        default: share = head_share<NF, 3>(z, cq, gcs, gfr, F, wk, tau * ea, row, S, scr, pbar); break;
       }
+      if (!lead) sShare[(part - 1) * kM + row] = share;
+      __syncthreads();
+      if (lead) {
+        const float dLda = gI.w + share + sShare[row] + sShare[kM + row] + sShare[2 * kM + row];
+        float dz[4 + NF];
 #pragma unroll
-      for (int u = 0; u < 3; ++u) dz[u] = wk * gcs[u] * cq[u] * (1.f - cq[u]);
-      dz[3] = valid ? dLda * dtv * sigmoid_fast(z[3]) : 0.f;
-      float dd[1] = {valid ? sig * dLda : 0.f};
-      seg_scan<1>(dd, 1, row, S, sScan, 1);
-      if (valid && k == S - 1) DD[iv] = dd[0];
-      uint32_t pk[16];
+        for (int f = 0; f < NF; ++f) dz[4 + f] = (valid && f < F) ? wk * gfr[f] : 0.f;
 #pragma unroll
-      for (int e = 0; e < 16; ++e)
-        pk[e] = (2 * e < 4 + NF) ? pack_bf16(2 * e < m.nout ? dz[2 * e] : 0.f, 2 * e + 1 < m.nout ? dz[2 * e + 1] : 0.f)
-                                 : 0u;
-      // delta_L (32 columns): A operand of dgrad_L in slot Sc; B of wgrad_L and A of its bias
-      // sum in the delta tile (chunks 0-3 of slab 0; the rest is never flushed)
-      tmem_st16(mSc + lanes, pk);
-      const RowSw sw(row);
+        for (int u = 0; u < 3; ++u) dz[u] = wk * gcs[u] * cq[u] * (1.f - cq[u]);
+        dz[3] = valid ? dLda * dtv * sigmoid_fast(z[3]) : 0.f;
+        float dd[1] = {valid ? sig * dLda : 0.f};
+        seg_scan<1>(dd, 1, row, S, scr, pbar);
+        if (valid && k == S - 1) DD[iv] = dd[0];
+        uint32_t pk[16];
 #pragma unroll
-      for (int ch = 0; ch < 4; ++ch) st_shared_v4(dt + sw.off(ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
-      tmem_wait_st();
-      fence_proxy_async_smem();
+        for (int e = 0; e < 16; ++e)
+          pk[e] = (2 * e < 4 + NF) ? pack_bf16(2 * e < m.nout ? dz[2 * e] : 0.f, 2 * e + 1 < m.nout ? dz[2 * e + 1] : 0.f)
+                                   : 0u;
+        // delta_L (32 columns): A operand of dgrad_L in slot Sc; B of wgrad_L and A of its bias
+        // sum in the delta tile (chunks 0-3 of slab 0; the rest is never flushed)
+        tmem_st16(mSc + lanes, pk);
+        const RowSw sw(row);
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) st_shared_v4(dt + sw.off(ch), pk[4 * ch], pk[4 * ch + 1], pk[4 * ch + 2], pk[4 * ch + 3]);
+        tmem_wait_st();
+        fence_proxy_async_smem();
+      } else if (part == 1 && c + 1 < ce) {
+        prefetch_tab(c + 1, prim);  // the next chunk's tables, into the other buffer
+      }
     }
     tc_fence_before();
     __syncthreads();
