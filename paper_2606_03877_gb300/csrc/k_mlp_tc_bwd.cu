@@ -66,7 +66,7 @@ constexpr uint32_t kOnes = 2048;                    // 16 rows of the MN-major o
 // Byte offsets in dynamic shared memory; per-group regions are base + g * stride. The group's
 // interval tables hold ipc = 128 / S entries.
 struct BwdSmem {
-  uint32_t w, tiles0, tiles_stride, ones, bias, grp0, grp_stride, itab, giv, ddel, gf, scan, geo,
+  uint32_t w, tiles0, tiles_stride, ones, bias, grp0, grp_stride, tab_stride, itab, giv, ddel, gf, scan, geo,
       pgeo, bars, misc, total;  // itab/giv/ddel/gf: offsets inside one group's block
 };
 
@@ -88,15 +88,19 @@ MLPS_HD BwdSmem bwd_layout(const TcPlan& P, int F, int ipc, int kNG) {
   o = al(o + kOnes, 1024);
   L.bias = o;
   o = al(o + 4 * P.bias_floats, 16);
+  // per group: two buffers (tab_stride apart) of the chunk's interval records (itab),
+  // gradients (giv) and feature gradients (gf), then the per-interval dL/d delta (ddel)
   uint32_t q = 0;
   L.itab = q;
   q = al(q + (uint32_t)sizeof(IntervalRec) * ipc, 16);
   L.giv = q;
   q = al(q + 16 * ipc, 16);
-  L.ddel = q;
-  q = al(q + 4 * ipc, 16);
   L.gf = q;
   q = al(q + 4 * ipc * (F > 0 ? F : 1), 16);
+  L.tab_stride = q;
+  q += q;
+  L.ddel = q;
+  q = al(q + 4 * ipc, 16);
   L.grp0 = o;
   L.grp_stride = q;
   o += q * kNG;
@@ -312,14 +316,17 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
       sGeo[threadIdx.x] = 0.f;
     }
   };
-  // the next chunk's interval record and interval gradient, one step ahead, in registers
+  // the next chunk's interval records and interval gradients, one step ahead, copied with
+  // cp.async into the group's pending table buffer `pb` (no registers held across the chunk)
   uint8_t* grp = gb + L.grp0 + (uint32_t)g * L.grp_stride;
-  RecPrefetch pre;
-  pre.valid = 0;
+  int pb = 0;
   auto prefetch = [&](const ChunkStep<kNG>& st, int c) {
     const int f = (c - w.chunk_start[st.prim]) * w.ipc;
-    if (row < min(w.ipc, w.prim_count[st.prim] - f))
-      rec_prefetch(w, walk_slot(bmap, w.prim_start[st.prim] + f + row), true, pre);
+    if (row < min(w.ipc, w.prim_count[st.prim] - f)) {
+      const uint32_t t = smem_u32(grp) + (uint32_t)pb * L.tab_stride;
+      rec_copy_async(w, walk_slot(bmap, w.prim_start[st.prim] + f + row), t + L.itab + 64u * (uint32_t)row,
+                     t + L.giv + 16u * (uint32_t)row);
+    }
   };
 
   ChunkStep<kNG> cur = chunk_step<kNG>(w, cb, ce, prim);
@@ -378,18 +385,21 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
     // ============================================================ epilogue group g
     const int first = (my_cc - w.chunk_start[prim]) * w.ipc;
     const int nint = min(w.ipc, w.prim_count[prim] - first);
-    IntervalRec* T = reinterpret_cast<IntervalRec*>(grp + L.itab);
-    float4* GI = reinterpret_cast<float4*>(grp + L.giv);
+    // this chunk's tables are in buffer pb (copied during the previous step); the other buffer
+    // was last read by the chunk before the previous one, so no barrier is needed before it is
+    // refilled
+    uint8_t* tb = grp + (uint32_t)pb * L.tab_stride;
+    IntervalRec* T = reinterpret_cast<IntervalRec*>(tb + L.itab);
+    float4* GI = reinterpret_cast<float4*>(tb + L.giv);
     float* DD = reinterpret_cast<float*>(grp + L.ddel);
-    float* GF = reinterpret_cast<float*>(grp + L.gf);
-    named_bar_sync(gbar, kGThreads);  // the group is done with the previous chunk's tables
-    if (row < nint) {
-      rec_store(pre, T, row);  // prefetched during the previous step
-      GI[row] = pre.g;
+    float* GF = reinterpret_cast<float*>(tb + L.gf);
+    cp_async_wait_all();  // this thread's copies of the chunk's records and gradients landed
+    if (F > 0 && row < nint) {
       const size_t slot = walk_slot(bmap, w.prim_start[prim] + first + row);
       for (int f = 0; f < F; ++f) GF[row * F + f] = w.hit_gfeat[slot * F + f];
     }
-    named_bar_sync(gbar, kGThreads);
+    named_bar_sync(gbar, kGThreads);  // everyone's did
+    pb ^= 1;
     if (nxt.n > 0 && my_nx >= 0) prefetch(nxt, my_nx);  // start loading the next chunk now
     const uint32_t tiles = sbase + L.tiles0 + (uint32_t)g * L.tiles_stride;
     const int t0s = P.kpad[0] / 64;  // slabs of T_0
@@ -774,6 +784,7 @@ __global__ void __launch_bounds__(kGThreads * kNG, 1)
 #undef tileaddr
     cur = nxt;
   }
+  cp_async_wait_all();  // (every prefetch is for a chunk this group consumes; kept for safety)
   // teardown: none of this group's MMAs may still write TMEM (after an abort a group may have
   // stopped waiting for them); then the final flush, and TMEM is freed
   if (issuer) {
