@@ -19,11 +19,14 @@
 //    outputs), B = a constant K-major operand whose first row is all ones (N = 16).
 // Sixteen warps per SM: thread (row, part) owns TMEM lane `row` (the chunk's sample row) and
 // the columns [32 part, 32 part + 32) of every 128-wide activation, gradient and weight-gradient
-// row; the per-sample scalar work (the encoding, the composite reverse, the pose chain) runs in
-// part 0. Per chunk: encode X; forward to the head; reverse of the interval composite (Eq. 6)
-// into delta of the head; then for l = L .. 1: flush dW_l, delta_{l-1} = G_l * [H_l > 0],
-// dgrad_{l-1}, H_{l-1} into the H tile, wgrad_{l-1} and its bias sum; finally the encoding
-// derivative and the pose chain (as in k_mlp_tc_bwd.cu). Every wait is bounded by wall time;
+// row; the per-sample scalar work (the encoding, the pose chain) runs in part 0, the reverse
+// scan of the composite is shared out over the parts, and part 1 copies the next chunk's
+// interval tables with cp.async meanwhile. Per chunk: encode X; forward to the head; reverse of
+// the interval composite (Eq. 6) into delta of the head; then for l = L .. 1:
+// delta_{l-1} = G_l * [H_l > 0], dgrad_{l-1}, H_{l-1} into the H tile, wgrad_{l-1} and its bias
+// sum, with dW_l read out of TMEM before that batch is issued and added into the copy after
+// it; finally the encoding derivative and the pose chain (as in k_mlp_tc_bwd.cu). Every wait
+// is bounded by wall time;
 // after a timeout the kernel runs out its chunks without issuing MMAs, frees TMEM and reports
 // MLPS_ERR_TIMEOUT.
 #include <cuda.h>
