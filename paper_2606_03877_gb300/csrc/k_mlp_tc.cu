@@ -872,7 +872,9 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
       else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, kMaxFeat, 3, true> : tc::k_mlp_fwd_tc<64, -1, -1, kMaxFeat, 3, true>;
     } else if (a.m.width == 128) {
       if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 0, 2, true> : tc::k_mlp_fwd_tc<128, -1, -1, 0, 2, true>;
-      else kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, kMaxFeat, 2, true> : tc::k_mlp_fwd_tc<128, -1, -1, kMaxFeat, 2, true>;
+      else kern = !fast64 ? tc::k_mlp_fwd_tc<128, -1, -1, kMaxFeat, 2, true>
+                  : (a.m.nl == 5 && a.m.F <= 16) ? tc::k_mlp_fwd_tc<128, 6, 4, 16, 2, true, 5>  // (the stress network)
+                                : tc::k_mlp_fwd_tc<128, 6, 4, kMaxFeat, 2, true>;
     } else {
       return cudaErrorNotSupported;
     }
@@ -883,7 +885,9 @@ cudaError_t launch_mlp_fwd_tc(const Work& w, const MlpArgs& a, const TcPlan& P, 
     else kern = fast64 ? tc::k_mlp_fwd_tc<64, 6, 4, kMaxFeat, 3, false> : tc::k_mlp_fwd_tc<64, -1, -1, kMaxFeat, 3, false>;
   } else if (a.m.width == 128) {
     if (!feat) kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, 0, 2, false> : tc::k_mlp_fwd_tc<128, -1, -1, 0, 2, false>;
-    else kern = fast64 ? tc::k_mlp_fwd_tc<128, 6, 4, kMaxFeat, 2, false> : tc::k_mlp_fwd_tc<128, -1, -1, kMaxFeat, 2, false>;
+    else kern = !fast64 ? tc::k_mlp_fwd_tc<128, -1, -1, kMaxFeat, 2, false>
+                : (a.m.nl == 5 && a.m.F <= 16) ? tc::k_mlp_fwd_tc<128, 6, 4, 16, 2, false, 5>  // (the stress network)
+                              : tc::k_mlp_fwd_tc<128, 6, 4, kMaxFeat, 2, false>;
   } else {
     return cudaErrorNotSupported;
   }
