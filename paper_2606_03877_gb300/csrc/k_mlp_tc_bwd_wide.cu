@@ -64,8 +64,8 @@ constexpr uint32_t kTmemColsW = 512;
 struct WideSmem {
   // tab: two buffers (tab_stride apart) of the chunk tables, each holding the interval records
   // (itab), their gradients (giv) and feature gradients (gf) at these offsets
-  uint32_t w, xt, ht, dt, ones_mn, ones_k, bias, tab, tab_stride, itab, giv, gf, ddel, scan, share, geo, pgeo, bars,
-      misc, total;
+  uint32_t w, xt, ht, dt, ones_mn, ones_k, bias, tab, tab_stride, itab, giv, gf, ddel, pose, scan, share, geo, pgeo,
+      bars, misc, total;
 };
 
 MLPS_HD uint32_t alw(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -99,6 +99,8 @@ MLPS_HD WideSmem wide_layout(const TcPlan& P, int F, int ipc) {
   o += 2 * q;
   L.ddel = o;
   o = alw(o + 4 * ipc, 16);
+  L.pose = o;  // per interval: the six sums of the pose chain
+  o = alw(o + 4 * 6 * ipc, 16);
   L.scan = o;  // per part: 4 warps x the widest segmented scan of that part (at most 8 values)
   o = alw(o + 4 * kParts * kScanPart, 16);
   L.share = o;  // parts 1-3: their shares of dL/d alpha per row
@@ -415,6 +417,7 @@ __global__ void __launch_bounds__(kWThreads, 1)
   auto delta_slot = [&](int l) { return (l == L || l == L - 3) ? mSc : (l == L - 1 ? mSb : mSa); };
 
   float* DD = reinterpret_cast<float*>(gb + Lw.ddel);
+  float* sPose = reinterpret_cast<float*>(gb + Lw.pose);
   // Chunk c's tables are in buffer (c - cb) & 1. From the block's second chunk on, part 1 copies
   // them with cp.async while part 0 reverses the previous chunk's composite.
   auto tab = [&](int cc) { return gb + Lw.tab + (uint32_t)((cc - cb) & 1) * Lw.tab_stride; };
@@ -691,31 +694,40 @@ __global__ void __launch_bounds__(kWThreads, 1)
       }
     }
     // ---------------- encoding derivative and pose chain (midpoint samples), as in the 64-wide
-    // kernel: the per-interval sums A = sum_k gx_k and B = sum_k c_k gx_k (part 0)
+    // kernel: the per-interval sums A = sum_k gx_k and B = sum_k c_k gx_k, coordinate u of
+    // both in part u (u < 3); part 0 then runs the per-interval tail
     (void)wait_m();  // dgrad_0 (wgrad_0 may still run)
-    if (lead) {
+    if (part < 3) {
       uint32_t v0[32], v1[32];
       tmem_ld32(rD, v0);
       tmem_ld32(rD + 32, v1);
       tmem_wait_ld();
-      float gx[3] = {0.f, 0.f, 0.f};
       const IntervalRec& I = T[valid ? iv : 0];
       const float ck = ((float)k + 0.5f) * invS - 0.5f;
+      float gxu = 0.f;
       if (valid) {
         const float tr = I.r0 + ((float)k + 0.5f) * I.dt;
-        float xl[3];
-        for (int u = 0; u < 3; ++u) xl[u] = fmaf(tr, I.dp[u], I.p[u]);
-        enc_grad64<XL>(xl, v0, v1, gx);
+        const float xu = fmaf(tr, I.dp[part], I.p[part]);
+        gxu = part == 0 ? enc_grad_coord<XL, 0>(xu, v0, v1)
+            : part == 1 ? enc_grad_coord<XL, 1>(xu, v0, v1)
+                        : enc_grad_coord<XL, 2>(xu, v0, v1);
       }
-      float red[6] = {gx[0], gx[1], gx[2], ck * gx[0], ck * gx[1], ck * gx[2]};
-      seg_scan<6>(red, 6, row, S, sScan, 1);
+      float red[2] = {gxu, ck * gxu};
+      seg_scan<2>(red, 2, row, S, sScan + part * kScanPart, 1 + part);
+      if (valid && k == S - 1) {  // the interval's totals
+        sPose[6 * iv + part] = red[0];
+        sPose[6 * iv + 3 + part] = red[1];
+      }
+    }
+    __syncthreads();
+    if (lead) {
       const int wrow0 = row - lane;
       for (int r_end = (wrow0 / S + 1) * S - 1; r_end < wrow0 + 32; r_end += S) {
         const int ive = r_end / S;
         if (ive >= nint) break;  // warp-uniform
         float rr[6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) rr[j] = __shfl_sync(0xffffffffu, red[j], r_end - wrow0);
+        for (int j = 0; j < 6; ++j) rr[j] = sPose[6 * ive + j];
         if (lane < 12) {
           const IntervalRec& Ie = T[ive];
           const float span = Ie.r1 - Ie.r0, tm = Ie.r0 + 0.5f * span;

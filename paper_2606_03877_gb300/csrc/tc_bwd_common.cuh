@@ -92,6 +92,27 @@ MLPS_DEV void enc_grad64(const float (&xl)[3], const uint32_t (&v0)[32], const u
   }
 }
 
+// The same for coordinate U alone: the terms of enc_grad64 that make gx[U], in the same order.
+template <int XL, int U>
+MLPS_DEV float enc_grad_coord(float xu, const uint32_t (&v0)[32], const uint32_t (&v1)[32]) {
+  if (XL == 0) return __uint_as_float(v0[U]);
+  float sn, cs;
+  __sincosf(3.14159265358979f * xu, &sn, &cs);
+  float wq = 3.14159265358979f, acc = 0.f;
+#pragma unroll
+  for (int l = 0; l < (XL > 0 ? XL : 1); ++l) {
+    const int c = 2 * (U * XL + l);
+    const float g0 = __uint_as_float(c < 32 ? v0[c] : v1[(c - 32) & 31]);
+    const float g1 = __uint_as_float(c + 1 < 32 ? v0[c + 1] : v1[(c + 1 - 32) & 31]);
+    acc += wq * (g0 * cs - g1 * sn);
+    const float s2 = 2.f * sn * cs;
+    cs = fmaf(-2.f * sn, sn, 1.f);
+    sn = s2;
+    wq *= 2.f;
+  }
+  return acc;
+}
+
 MLPS_DEV void build_row(const Model& m, const IntervalRec* T, int nint, int row, uint32_t A,
                         int kpad0) {
   const int S = m.S;
