@@ -281,29 +281,6 @@ MLPS_DEV int step_chunk(const ChunkStep<NG>& s, int g) {
   return g == 0 ? s.c[0] : g == 1 ? s.c[1] : g == 2 ? s.c[2] : g == 3 ? s.c[3] : g == 4 ? s.c[4] : s.c[5];
 }
 
-// Interval record (and, for the backward pass, its gradient) of one chunk row, loaded one
-// chunk ahead into registers.
-struct RecPrefetch {
-  float4 v[4];
-  float4 g;
-  int valid;
-};
-
-MLPS_DEV void rec_store(const RecPrefetch& r, IntervalRec* T, int row) {
-  float4* dst = reinterpret_cast<float4*>(T + row);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) dst[i] = r.v[i];
-}
-
-MLPS_DEV void rec_prefetch(const Work& w, int slot, bool want_grad, RecPrefetch& r) {
-  // independent loads only: they stay in flight while the current chunk is processed
-  const float4* src = reinterpret_cast<const float4*>(w.rec + slot);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) r.v[i] = __ldg(src + i);
-  r.valid = 1;
-  if (want_grad) r.g = w.hit_grad[slot];
-}
-
 // Asynchronous global -> shared copies (cp.async, 16 bytes each): the next chunk's interval
 // records travel to shared memory while the current chunk is processed, holding no registers.
 MLPS_DEV void cp_async16(uint32_t dst, const void* src) {
