@@ -40,3 +40,22 @@ def test_reference_arm_json_line():
 def test_reference_arm_forward_only():
     d = _reference_line("--steps", "1", "--warmup", "0", "--pass", "fwd")
     assert d["config"]["pass"] == "fwd" and d["value"] > 0
+
+
+def test_traffic_table_entries_expire_with_their_sources(tmp_path, monkeypatch):
+    """`roofline.traffic` comes from a committed ncu capture only while every source file the
+    entry lists still hashes to the value recorded with it."""
+    import hashlib
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1\n")
+    h = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    entry = {"kernel": "k", "precision": ["bf16"], "workload": "prec", "bytes_per_launch": 1.5e9,
+             "sources": {"k.cu": h}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"mlp_bwd": [entry], "mlp_fwd": []}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._traffic("mlp_bwd", "bf16", "prec") == 1.5e9
+    assert bench._traffic("mlp_bwd", "fp8", "prec") is None      # no capture for this precision
+    assert bench._traffic("mlp_bwd", "bf16", "stress") is None   # nor for this workload
+    src.write_text("kernel v2\n")
+    assert bench._traffic("mlp_bwd", "bf16", "prec") is None      # the kernel changed since
