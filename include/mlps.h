@@ -216,8 +216,8 @@ mlps_status mlps_render_forward(const mlps_config* cfg, const mlps_scene* scene,
  *  - BF16 / E4M3 (the backward recomputes in BF16): hidden width 32 or 64 with up to six hidden
  *    layers, at most 12 feature outputs and the midpoint encodings (xyz_freqs 0 or 6), or the
  *    paper's contact-point model; hidden width 128 with up to four hidden layers on the tensor
- *    cores (xyz_freqs 6, dir_freqs 4, at most 16 feature outputs), other width-128 networks with
- *    samples <= 64 in an FP32-FMA kernel reading the BF16 weights. */
+ *    cores (xyz_freqs 6, dir_freqs 4, at most 16 feature outputs, a multiple of 4), other
+ *    width-128 networks with samples <= 64 in an FP32-FMA kernel reading the BF16 weights. */
 mlps_status mlps_render_backward(const mlps_config* cfg, const mlps_scene* scene,
                                  const mlps_camera* cams, int32_t n_views, const float* d_rgb,
                                  const float* d_trans, const float* d_feat, const void* saved,
